@@ -1,0 +1,245 @@
+/*
+ * lst.h -- C ABI of the GB300 Line Segment Tracking library (liblst.so).
+ *
+ * The library runs the data-parallel hot path of Line Segment Tracking
+ * (arXiv:2407.18231, Sec. 1) on one NVIDIA GB300 (sm_103a): per event it bins the
+ * outer-tracker hits by module, pairs the hits of each module's two sensors into Mini
+ * Doublets (MD), links MDs on connected modules into Line Segments (LS), joins LSs that
+ * share an MD into T3s and T3s that share an MD into T5s, combines T3s/T5s with
+ * inner-tracker seeds (pLS) into pT3s/pT5s, removes duplicates and emits track
+ * candidates (TC): pT5s, pT3s, T5s and unlinked pLSs.  Every step runs in the library's
+ * own CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *   - Return LST_OK (0) or a negative lst_status; no C++ exception crosses the ABI.
+ *   - Pointers marked "host" are read during the call only; the caller keeps ownership.
+ *     Pointers marked "device" must be device memory of the context's GPU.
+ *   - A context is used by one host thread at a time (the serving loop owns its context
+ *     while it runs).  After a per-event error the context stays usable.
+ *   - lst_last_error(ctx) describes the last failure on that context.
+ *   - Units: cm, GeV, tesla (B = 3.8 T); floats are IEEE binary32.
+ */
+#ifndef LST_H
+#define LST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lst_status;
+#define LST_OK 0
+#define LST_ERR_INVALID_ARG (-1)      /* null pointer, zero count where one is required, bad kind */
+#define LST_ERR_BAD_INPUT (-2)        /* module id out of range, non-finite coordinate, bad seed */
+#define LST_ERR_NO_MAP (-3)           /* lst_build_connection_map has not run */
+#define LST_ERR_OOM (-4)              /* device or host allocation failed */
+#define LST_ERR_BUDGET (-5)           /* serving: event does not fit the memory budget */
+#define LST_ERR_CUDA (-6)             /* a CUDA runtime call failed */
+#define LST_ERR_TIMEOUT (-7)          /* a bounded wait for the device ran out */
+#define LST_ERR_BUFFER_TOO_SMALL (-8) /* caller buffer smaller than the result */
+#define LST_ERR_NOT_FOUND (-9)        /* unknown or released result id */
+
+/* One detector module (48 bytes).  Both sensors of a doublet module form one module
+ * (Sec. 1, Fig. 1: every outer-tracker layer is two closely spaced sensors).  A hit names
+ * its sensor as det = 2 * module_index + sensor (0 lower, 1 upper).
+ *   barrel: surf = lower-sensor radius, gap = radial sensor spacing, [emin, emax) = z extent
+ *   endcap: surf = lower-sensor signed z, gap = |z| spacing, [emin, emax) = r extent
+ *   (e0x, e0y) / (e1x, e1y): unit vectors of the lower / upper phi edge of the module.
+ * Rows (ieta = barrel z bin or endcap ring) must be uniform in length within a surface;
+ * iphi < nphi numbers the sectors of a row. */
+typedef struct lst_module_desc {
+  uint8_t subdet;  /* 0 barrel, 1 endcap */
+  uint8_t layer;   /* barrel layer 1..6, endcap disk 1..5 */
+  int8_t side;     /* 0 barrel, -1 / +1 endcap */
+  uint8_t stype;   /* 0 PS (z measured), 1 2S (z = strip centre) */
+  uint16_t ieta;
+  uint16_t iphi;
+  uint16_t nphi;
+  uint16_t pad;
+  float surf, gap, emin, emax;
+  float e0x, e0y, e1x, e1y;
+  uint32_t reserved;
+} lst_module_desc;
+
+/* Inner-tracker seed, the pLS of Sec. 1 (80 bytes): helix parameters at a reference point
+ * and its four pixel hits.  Pixel hits get the ids 4 * pls_index + k in track candidates. */
+typedef struct lst_pls {
+  float px, py, pz;  /* momentum at the reference point, GeV; px = py = 0 is rejected */
+  float x0, y0, z0;  /* reference point, cm */
+  float hx[4], hy[4], hz[4];
+  int32_t charge;    /* +1 or -1 */
+  uint32_t reserved;
+} lst_pls;
+
+/* One event as host arrays (the library copies them during the call). */
+typedef struct lst_event {
+  uint32_t n_hits;
+  const float *x, *y, *z;  /* host, n_hits each */
+  const uint32_t *det;     /* host, n_hits: 2 * module + sensor */
+  uint32_t n_pls;
+  const lst_pls *pls;      /* host, n_pls (may be NULL when n_pls == 0) */
+} lst_event;
+
+/* A batch whose inputs already sit in device memory (events concatenated). */
+typedef struct lst_batch_dev {
+  uint32_t n_events;
+  uint32_t n_hits;         /* total over the batch */
+  uint32_t n_pls;          /* total over the batch */
+  uint32_t max_event_hits; /* largest event (sizing hint; 0 = unknown) */
+  const float *x, *y, *z;  /* device, n_hits */
+  const uint32_t *det;     /* device, n_hits */
+  const uint32_t *hit_off; /* device, n_events + 1 (hit_off[0] = 0) */
+  const lst_pls *pls;      /* device, n_pls */
+  const uint32_t *pls_off; /* device, n_events + 1 */
+} lst_batch_dev;
+
+/* Context options.  Zero-initialised means defaults. */
+typedef struct lst_config {
+  int32_t device;        /* CUDA device ordinal (default 0) */
+  uint32_t keep_objects; /* 1: every result also keeps all intermediate objects (tests) */
+  uint32_t use_graph;    /* lst_run_batch: 0 default (graph on), 1 force on, 2 force off */
+  uint32_t block_size;   /* threads per block of the stage kernels (0 = tuned default) */
+  uint32_t blocks_per_sm;/* resident blocks per SM of the persistent grids (0 = default) */
+  uint32_t profile;      /* 1: run kernels eagerly with a CUDA event after each (per-kernel times) */
+  uint32_t reserved[10];
+} lst_config;
+
+/* Track candidate (Sec. 1 list: pT5, pT3, T5, unlinked pLS).  76 bytes. */
+typedef struct lst_tc {
+  uint8_t type;        /* LST_TC_PT5 / PT3 / T5 / PLS */
+  uint8_t n_ot;        /* outer-tracker hits used (10, 6 or 0) */
+  uint8_t n_pix;       /* pixel hits used (4 or 0) */
+  uint8_t pad;
+  uint32_t obj;        /* index of the object in its own list (pT5, pT3, T5 or pLS) */
+  uint32_t pls;        /* pLS index, or 0xFFFFFFFF */
+  uint32_t ot[10];     /* input hit indices, 0xFFFFFFFF padded (MD lower, upper, ...) */
+  uint32_t pix[4];     /* 4 * pls + k, or 0xFFFFFFFF */
+  float pt;            /* GeV: the pLS pT, or for a T5 0.0113922 / |curvature| */
+  float score;         /* selection score (lower is better) */
+} lst_tc;
+
+#define LST_TC_PT5 0
+#define LST_TC_PT3 1
+#define LST_TC_T5 2
+#define LST_TC_PLS 3
+
+/* Intermediate objects of one event, for parity checks (keep_objects = 1).
+ * All indices are event-local: hits = input order, MDs/T3s/T5s/pLSs = their list. */
+#define LST_OBJ_MD 0   /* lst_md_rec */
+#define LST_OBJ_LS 1   /* lst_ls_rec */
+#define LST_OBJ_T3 2   /* lst_t3_rec */
+#define LST_OBJ_T5 3   /* lst_t5_rec */
+#define LST_OBJ_PT3 4  /* lst_px_rec */
+#define LST_OBJ_PT5 5  /* lst_px_rec */
+#define LST_OBJ_PLS 6  /* lst_pls_rec */
+typedef struct { uint32_t module, lo, up; } lst_md_rec;
+typedef struct { uint32_t md[2]; } lst_ls_rec;
+typedef struct { uint32_t md[3]; } lst_t3_rec;
+typedef struct { uint32_t md[5]; float score, kfull; uint32_t alive; } lst_t5_rec;
+typedef struct { uint32_t pls, obj; float score; uint32_t alive; } lst_px_rec;
+typedef struct { uint32_t n_cand; uint32_t cand[36]; uint32_t is_tc; } lst_pls_rec;
+
+typedef struct lst_ctx lst_ctx;
+typedef uint64_t lst_result_id;
+
+/* Creates a context on cfg->device (cfg may be NULL), copies the module table to the
+ * device and derives every per-module constant the selections need.
+ * mods: host, n_mods records.  *out_ctx receives the context (free with lst_destroy).
+ * Errors: INVALID_ARG (null, n_mods == 0), BAD_INPUT (bad module record), CUDA, OOM. */
+lst_status lst_load_geometry(const lst_module_desc *mods, uint32_t n_mods, const lst_config *cfg,
+                             lst_ctx **out_ctx);
+
+/* Builds the module connection map on the host and keeps it resident on the device
+ * (Sec. 1: MDs are only linked between modules a precomputed map marks as reachable).
+ * The map is a conservative superset: it only prunes module pairs whose anchors can never
+ * pass the LS selection.  Errors: INVALID_ARG, OOM, CUDA. */
+lst_status lst_build_connection_map(lst_ctx *ctx);
+
+/* Runs the whole chain on one event with plain stream-ordered launches (the per-event
+ * path).  ev: host arrays.  *out receives a result id (free with lst_release_result).
+ * Errors: INVALID_ARG, BAD_INPUT (checked on the device), NO_MAP, OOM, CUDA, TIMEOUT. */
+lst_status lst_run_event(lst_ctx *ctx, const lst_event *ev, lst_result_id *out);
+
+/* Runs n events as one batch: one packed upload, one persistent launch per stage, replayed
+ * from a CUDA graph.  evs: host array of n events; outs: host array of n result ids. */
+lst_status lst_run_batch(lst_ctx *ctx, const lst_event *evs, uint32_t n, lst_result_id *outs);
+
+/* Same as lst_run_batch for inputs already in device memory.  stream: a cudaStream_t of
+ * the context's device on which the work is enqueued, or NULL for the context's own
+ * stream.  Results stay on the device until lst_batch_finish; the call only enqueues work.
+ * Errors: INVALID_ARG, NO_MAP, OOM, CUDA. */
+lst_status lst_run_batch_device(lst_ctx *ctx, const lst_batch_dev *batch, void *stream);
+
+/* Waits (bounded by timeout_ms, 0 = no bound) for the last lst_run_batch_device, re-runs it
+ * with larger buffers if an object list outgrew its storage, and reports the number of
+ * track candidates per event.  n_tc_per_event: host array of batch->n_events (may be NULL).
+ * outs: host array of n_events result ids, or NULL to keep nothing on the host. */
+lst_status lst_batch_finish(lst_ctx *ctx, uint32_t timeout_ms, uint32_t *n_tc_per_event,
+                            lst_result_id *outs);
+
+/* Copies the track candidates of a result into buf (host, cap records).  With buf == NULL
+ * only *n_out is set (size query).  Errors: NOT_FOUND, BUFFER_TOO_SMALL, INVALID_ARG. */
+lst_status lst_get_candidates(lst_ctx *ctx, lst_result_id id, lst_tc *buf, uint32_t cap, uint32_t *n_out);
+
+/* Copies one kind of intermediate object (LST_OBJ_*) of a result kept with keep_objects = 1.
+ * buf == NULL is a size query.  Errors: NOT_FOUND, INVALID_ARG (kind, or objects not kept),
+ * BUFFER_TOO_SMALL. */
+lst_status lst_get_objects(lst_ctx *ctx, lst_result_id id, int32_t kind, void *buf, uint32_t cap,
+                           uint32_t *n_out);
+
+/* Frees a result's host storage.  Errors: NOT_FOUND. */
+lst_status lst_release_result(lst_ctx *ctx, lst_result_id id);
+
+/* Frees the context, its device memory and streams.  NULL is a no-op. */
+void lst_destroy(lst_ctx *ctx);
+
+/* Text of the last error on ctx (never NULL; valid until the next call on ctx). */
+const char *lst_last_error(lst_ctx *ctx);
+
+/* Static text for a status code. */
+const char *lst_status_string(lst_status s);
+
+/* Per-call statistics of the last run on the context (object counts of the whole batch,
+ * candidate tests are not counted on the device).  Any pointer may be NULL. */
+typedef struct lst_stats {
+  uint32_t n_events, n_hits, n_pls, n_md, n_ls, n_t3, n_t5, n_pt3, n_pt5, n_tc;
+  uint32_t reruns;        /* re-runs after an object list outgrew its storage */
+  uint32_t kernels;       /* kernels launched per run */
+  uint64_t device_bytes;  /* device memory held by the context */
+} lst_stats;
+lst_status lst_get_stats(lst_ctx *ctx, lst_stats *out);
+
+/* Per-kernel device time of the last run in profile mode (CUDA events on the launching
+ * stream, summed over the kernel's launches in that run).  buf == NULL is a size query. */
+typedef struct lst_profile_entry {
+  char name[24];
+  uint32_t launches;
+  float ms;
+} lst_profile_entry;
+lst_status lst_get_profile(lst_ctx *ctx, lst_profile_entry *buf, uint32_t cap, uint32_t *n_out);
+
+/* ---- serving: continuous batching of a stream of events (Sec. 2 context: trigger
+ * farms reconstruct events as they arrive).  Events are admitted while the device-memory
+ * budget allows, packed into open batch slots, and run concurrently on several streams;
+ * results are bit-identical to lst_run_event on the same event. ---- */
+typedef struct lst_serve_config {
+  uint32_t n_slots;          /* concurrent batch slots (streams), >= 1 */
+  uint32_t max_batch;        /* events per slot launch, >= 1 */
+  uint64_t memory_budget;    /* bytes of device memory all slots may hold, 0 = unbounded */
+  uint32_t reserved[8];
+} lst_serve_config;
+
+/* Replays a stream of events: event i becomes visible at arrival_s[i] seconds after the
+ * call starts (host clock).  latency_s[i] receives completion time - arrival time and
+ * n_tc[i] the number of track candidates.  outs (may be NULL) receives result ids.
+ * Errors: INVALID_ARG, NO_MAP, BUDGET (an event alone exceeds the budget), OOM, CUDA. */
+lst_status lst_serve_replay(lst_ctx *ctx, const lst_serve_config *cfg, const lst_event *evs,
+                            const double *arrival_s, uint32_t n, double *latency_s, uint32_t *n_tc,
+                            lst_result_id *outs, double *wall_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LST_H */

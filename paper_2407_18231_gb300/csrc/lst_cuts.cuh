@@ -1,0 +1,230 @@
+// Selection arithmetic of the LST chain, device side.
+//
+// Every predicate is IEEE binary32 with + - * / sqrtf fabsf and comparisons only, compiled
+// with --fmad=false -prec-div=true -prec-sqrt=true -ftz=false, and every expression keeps
+// one fixed evaluation order, so the results are reproducible bit for bit.  Points are
+// float4 (x, y, z, r = sqrtf(x*x + y*y)); a point's module tolerances come as float4
+// (zeta: z, rho: radial, delta: transverse, T: bending slope of the module).
+//
+// The paper (arXiv:2407.18231, Sec. 1) defines the objects (MD, LS, T3, T5, pT3, pT5) and
+// the order they are built in but prints no cut; the selections here are this project's
+// reading, derived from helix geometry: a prompt track of curvature radius R >= Rmin
+// (pT >= 0.8 GeV at 3.8 T) crosses radius r at an angle asin(r / 2R) to the radial
+// direction, and its z grows linearly with arc length.
+#pragma once
+#include <cstdint>
+
+namespace lst {
+
+struct MethodConst {
+  float KB;      // pT [GeV] per cm of curvature radius (0.0029979 * 3.8)
+  float Z0MAX;   // luminous-region half length used for r-z pointing (cm)
+  float E0;      // r-phi tolerance of a hit pair (cm)
+  float KARC;    // bound on (arc - chord) effects: 2 / (24 Rmin^2)
+  float K3;      // 2 Rmin (1 - 5 %)
+  float KMAX;    // largest accepted curvature 1 / (Rmin (1 - 5 %))
+  float KAPPA;   // relative curvature agreement of T5 sub-triples
+  float KAPPA0;  // absolute curvature slack (1/cm)
+  float KPT5;    // pT5: T5 versus pLS curvature (relative)
+  float W0;      // pLS r-phi window floor (cm)
+  float PI;
+  float HINV;    // 1 / (2 Rmin): sine of the tangent-chord angle per cm of chord
+  float EDIR;    // error of an MD direction across a chord (cm)
+};
+
+struct PointTol {
+  float4 p;  // x, y, z, r
+  float4 t;  // zeta, rho, delta, T
+};
+
+// Transverse bending of a hit pair a (inner) -> b (outer): the step's component across
+// a's radial direction (u) against its radial component (v), |u| <= v T + e.
+__device__ __forceinline__ bool pair_bend(const MethodConst& C, const PointTol& a, const PointTol& b, float T) {
+  const float dx = b.p.x - a.p.x;
+  const float dy = b.p.y - a.p.y;
+  const float u = (a.p.x * dy - a.p.y * dx) / a.p.w;
+  const float v = (a.p.x * dx + a.p.y * dy) / a.p.w;
+  const float rs = a.t.y + b.t.y;
+  const float veff = v + rs;
+  const float sphi = fabsf(a.p.x * b.p.y - a.p.y * b.p.x) / (a.p.w * b.p.w);
+  const float e = C.E0 + rs * (sphi + 0.05f);
+  return (veff > 0.0f) && (fabsf(u) <= veff * T + e);
+}
+
+// r-z pointing of a hit pair: za rb - ra zb = z0 (rb - ra) for a line from (0, z0).
+__device__ __forceinline__ bool pair_rz(const MethodConst& C, const PointTol& a, const PointTol& b) {
+  const float f = a.p.z * b.p.w - a.p.w * b.p.z;
+  const float dr = fabsf(b.p.w - a.p.w);
+  const float dz = fabsf(b.p.z - a.p.z);
+  const float tol = C.Z0MAX * dr + (a.t.x * b.p.w + b.t.x * a.p.w + a.t.y * fabsf(b.p.z) + b.t.y * fabsf(a.p.z)) +
+                    C.KARC * dz * a.p.w * b.p.w * (a.p.w + b.p.w);
+  return fabsf(f) <= tol;
+}
+
+// Direction of an MD (upper minus lower hit) against a chord c that starts or ends at it:
+// tangent and chord of length |c| differ by asin(|c| / 2R).
+__device__ __forceinline__ bool md_dir(const MethodConst& C, const PointTol& lo, const PointTol& up, float cx, float cy,
+                                       float clen) {
+  const float dx = up.p.x - lo.p.x;
+  const float dy = up.p.y - lo.p.y;
+  const float dlen = sqrtf(dx * dx + dy * dy);
+  const float crs = fabsf(dx * cy - dy * cx);
+  const float tol = clen * (dlen * clen * C.HINV + C.EDIR + (lo.t.y + up.t.y));
+  return crs <= tol;
+}
+
+// Barrel-to-disk LS: the anchors' r-z line must leave the barrel before the next layer.
+__device__ __forceinline__ bool exit_ok(const PointTol& a, const PointTol& b, float rnext, float zb_half) {
+  const float Zb = b.p.z > 0.0f ? zb_half : -zb_half;
+  const float dzab = b.p.z - a.p.z;
+  const float t = (Zb - a.p.z) / dzab;
+  const float rexit = a.p.w + (b.p.w - a.p.w) * t;
+  const float ez = fabsf(Zb - b.p.z);
+  const float tol = rnext + b.t.y + 0.5f + a.t.x * fabsf(b.p.w - a.p.w) * ez / (dzab * dzab);
+  return rexit <= tol;
+}
+
+__device__ __forceinline__ bool ls_select(const MethodConst& C, const PointTol& a, const PointTol& au, const PointTol& b,
+                                          const PointTol& bu, float rnext_a, bool barrel_to_disk, float zb_half) {
+  if (!(pair_bend(C, a, b, b.t.w) && pair_rz(C, a, b))) return false;
+  if (barrel_to_disk && !exit_ok(a, b, rnext_a, zb_half)) return false;
+  const float cx = b.p.x - a.p.x;
+  const float cy = b.p.y - a.p.y;
+  const float clen = sqrtf(cx * cx + cy * cy);
+  return md_dir(C, a, au, cx, cy, clen) && md_dir(C, b, bu, cx, cy, clen);
+}
+
+// r-z straightness of p, q, s along the transverse chord (z linear in arc length).
+__device__ __forceinline__ bool rz3(const MethodConst& C, const PointTol& p, const PointTol& q, const PointTol& s) {
+  const float dxq = q.p.x - p.p.x, dyq = q.p.y - p.p.y;
+  const float dxs = s.p.x - p.p.x, dys = s.p.y - p.p.y;
+  const float dpq = sqrtf(dxq * dxq + dyq * dyq);
+  const float dps = sqrtf(dxs * dxs + dys * dys);
+  const float zqp = q.p.z - p.p.z;
+  const float zsp = s.p.z - p.p.z;
+  const float lhs = fabsf(zqp * dps - zsp * dpq);
+  const float tol = C.KARC * dps * dps * fabsf(zsp) * dpq + p.t.x * fabsf(dps - dpq) + q.t.x * dps + s.t.x * dpq +
+                    (p.t.y + s.t.y) * fabsf(zqp) + (p.t.y + q.t.y) * fabsf(zsp);
+  return lhs <= tol;
+}
+
+// Middle MD direction against chord a -> c (inscribed-angle relation).
+__device__ __forceinline__ bool mid_dir(const MethodConst& C, const PointTol& a, const PointTol& b, const PointTol& bu,
+                                        const PointTol& c) {
+  const float cx = c.p.x - a.p.x;
+  const float cy = c.p.y - a.p.y;
+  const float clen = sqrtf(cx * cx + cy * cy);
+  const float abx = b.p.x - a.p.x, aby = b.p.y - a.p.y;
+  const float bcx = c.p.x - b.p.x, bcy = c.p.y - b.p.y;
+  const float dab = sqrtf(abx * abx + aby * aby);
+  const float dbc = sqrtf(bcx * bcx + bcy * bcy);
+  const float dx = bu.p.x - b.p.x;
+  const float dy = bu.p.y - b.p.y;
+  const float dlen = sqrtf(dx * dx + dy * dy);
+  const float crs = fabsf(dx * cy - dy * cx);
+  const float tol = clen * (dlen * (fabsf(dbc - dab) + 0.02f * clen) * C.HINV + C.EDIR + (b.t.y + bu.t.y));
+  return crs <= tol;
+}
+
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  const float m = a > b ? a : b;
+  return m > c ? m : c;
+}
+
+struct Circle3 {
+  float k, tol, cross, prod, perim;
+};
+
+// Signed curvature of the circle through p, q, s, centred at q.
+__device__ __forceinline__ Circle3 circle3(const PointTol& p, const PointTol& q, const PointTol& s) {
+  const float ax = p.p.x - q.p.x, ay = p.p.y - q.p.y;
+  const float cx = s.p.x - q.p.x, cy = s.p.y - q.p.y;
+  const float cross = ax * cy - ay * cx;
+  const float dpq = sqrtf(ax * ax + ay * ay);
+  const float dqs = sqrtf(cx * cx + cy * cy);
+  const float ex = s.p.x - p.p.x, ey = s.p.y - p.p.y;
+  const float dsp = sqrtf(ex * ex + ey * ey);
+  const float prod = dpq * dqs * dsp;
+  const float dmax = max3(p.t.z, q.t.z, s.t.z);
+  Circle3 r;
+  r.k = 2.0f * cross / prod;
+  r.tol = 8.0f * dmax / (dsp * dsp);
+  r.cross = cross;
+  r.prod = prod;
+  r.perim = dpq + dqs + dsp;
+  return r;
+}
+
+__device__ __forceinline__ bool t3_select(const MethodConst& C, const PointTol& a, const PointTol& b, const PointTol& bu,
+                                          const PointTol& c) {
+  if (!rz3(C, a, b, c)) return false;
+  if (!mid_dir(C, a, b, bu, c)) return false;
+  const Circle3 k = circle3(a, b, c);
+  const float dmax = max3(a.t.z, b.t.z, c.t.z);
+  const float slack = fabsf(k.cross) - dmax * k.perim;
+  return (slack <= 0.0f) || (k.prod >= C.K3 * slack);
+}
+
+__device__ __forceinline__ bool t5_select(const MethodConst& C, const PointTol& A, const PointTol& B, const PointTol& Cc,
+                                          const PointTol& D, const PointTol& E, float& score, float& kfull) {
+  const Circle3 in = circle3(A, B, Cc);
+  const Circle3 out = circle3(Cc, D, E);
+  const Circle3 br = circle3(B, Cc, D);
+  const Circle3 fu = circle3(A, Cc, E);
+  const float d1 = fabsf(in.k - out.k);
+  const float d2 = fabsf(br.k - fu.k);
+  const bool c1 = d1 <= C.KAPPA * (fabsf(in.k) + fabsf(out.k)) + in.tol + out.tol + C.KAPPA0;
+  const bool c2 = d2 <= C.KAPPA * (fabsf(br.k) + fabsf(fu.k)) + br.tol + fu.tol + C.KAPPA0;
+  const bool c3 = fabsf(fu.k) <= C.KMAX + fu.tol;
+  const bool c4 = rz3(C, A, Cc, E);
+  score = d1 + d2;
+  kfull = fu.k;
+  return c1 && c2 && c3 && c4;
+}
+
+// ---- pLS helix ----
+struct PlsHelix {
+  float x0, y0, z0, R, cx, cy, cot, q, pt;
+};
+
+// Arc length of a chord on a circle of radius R: 2 R asin(chord / 2R), asin from two
+// half-angle reductions and its Taylor series to the ninth power.
+__device__ __forceinline__ float arc_length(float chord, float R) {
+  float x = chord / (2.0f * R);
+  if (x > 1.0f) x = 1.0f;
+  const float x1 = x / sqrtf(2.0f * (1.0f + sqrtf(1.0f - x * x)));
+  const float x2 = x1 / sqrtf(2.0f * (1.0f + sqrtf(1.0f - x1 * x1)));
+  const float t = x2 * x2;
+  const float as = x2 * (1.0f + t * (0.16666667f + t * (0.075f + t * (0.044642857f + t * 0.030381944f))));
+  return 8.0f * R * as;
+}
+
+// sin and cos of a in [0, pi]: Taylor series at a / 4, then two angle doublings.
+__device__ __forceinline__ void sin_cos_series(float a, float& s_out, float& c_out) {
+  const float h = 0.25f * a;
+  const float h2 = h * h;
+  const float s = h * (1.0f - h2 / 6.0f * (1.0f - h2 / 20.0f * (1.0f - h2 / 42.0f * (1.0f - h2 / 72.0f * (1.0f - h2 / 110.0f)))));
+  const float c = 1.0f - h2 / 2.0f * (1.0f - h2 / 12.0f * (1.0f - h2 / 30.0f * (1.0f - h2 / 56.0f * (1.0f - h2 / 90.0f * (1.0f - h2 / 132.0f)))));
+  const float s2 = 2.0f * s * c;
+  const float c2 = c * c - s * s;
+  s_out = 2.0f * s2 * c2;
+  c_out = c2 * c2 - s2 * s2;
+}
+
+// One anchor against the pLS helix: r-phi and r-z residuals inside windows that grow with
+// the arc length from the reference point.  Adds the normalised squared residuals to score.
+__device__ __forceinline__ bool pls_anchor(const MethodConst& C, const PlsHelix& h, const PointTol& X, float& score) {
+  const float ddx = X.p.x - h.x0, ddy = X.p.y - h.y0;
+  const float chord = sqrtf(ddx * ddx + ddy * ddy);
+  const float s = arc_length(chord, h.R);
+  const float ex = X.p.x - h.cx, ey = X.p.y - h.cy;
+  const float dphi = sqrtf(ex * ex + ey * ey) - h.R;
+  const float wphi = C.W0 + 0.003f * s + 0.015f * s * s / h.R + X.t.y;
+  const float ez = X.p.z - (h.z0 + s * h.cot);
+  const float wz = 0.05f + 0.002f * s + X.t.x + X.t.y * fabsf(h.cot);
+  const float a = dphi / wphi, b = ez / wz;
+  score = score + (a * a + b * b);
+  return (fabsf(dphi) <= wphi) && (fabsf(ez) <= wz);
+}
+
+}  // namespace lst

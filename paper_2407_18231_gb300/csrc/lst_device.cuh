@@ -1,0 +1,103 @@
+// Device-side data views shared by the kernels and the host runtime of liblst.
+#pragma once
+#include <cstdint>
+
+#include "lst_cuts.cuh"
+
+namespace lst {
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr int NSURF = 16;
+constexpr int MAX_CAND = 36;
+
+// Totals written by the scans into the batch header.
+enum Total : int {
+  T_HITS = 0, T_MD, T_LS, T_T3, T_T5, T_PT3, T_PT5, T_C5, T_C3, T_CT, T_A5, T_A3, T_AT, T_AP, T_TC, N_TOTALS
+};
+constexpr uint32_t ERR_BAD_INPUT = 1u;
+constexpr uint32_t ERR_OVERFLOW_SHIFT = 8;  // bit (8 + Total) = that list outgrew its storage
+
+// pLS record as the device reads it (layout of lst_pls).
+struct PlsIn {
+  float px, py, pz, x0, y0, z0;
+  float hx[4], hy[4], hz[4];
+  int32_t charge;
+  uint32_t reserved;
+};
+
+// Per-batch header in device memory: input pointers, sizes, totals, error word.
+struct Hdr {
+  const float *x, *y, *z;
+  const uint32_t *det, *hit_off;
+  const PlsIn *pls;
+  const uint32_t *pls_off;
+  uint32_t n_ev, n_hits, n_pls, pad;
+  uint32_t tot[N_TOTALS];
+  uint32_t err;
+  uint32_t pad2[3];
+};
+
+// Geometry tables (device pointers) and per-geometry scalars.
+struct GeoView {
+  uint32_t nm;
+  float zb_half;
+  const float4 *modc;   // zeta, rho, delta, T
+  const float *rnext;   // next barrel layer radius (1e30 if none)
+  const uint8_t *subdet;
+  const uint32_t *conn_off, *conn;
+  const float4 *mod_e;  // e0x, e0y, e1x, e1y
+  const float4 *mod_g;  // surf, gap, emin, emax
+  int32_t surf_first[NSURF];
+  uint32_t surf_nrows[NSURF];
+  uint32_t surf_row_base[NSURF];
+  const uint32_t *row_nphi, *row_mod_base, *row_mods;
+};
+
+// Pipeline buffers (device pointers) and capacities.
+struct BufView {
+  Hdr *hdr;
+  uint32_t cap_ev, cap_hits, cap_md, cap_ls, cap_t3, cap_t5, cap_pls, cap_pt3, cap_pt5, cap_tc;
+  // hits
+  uint32_t *sen_cnt, *sen_off, *hit_tmp, *hit_ev, *hit_idx;
+  float4 *hit4;
+  // MD
+  uint32_t *md_cnt, *md_off, *md_unit, *md_lo_idx, *md_up_idx;
+  float4 *md_lo4, *md_up4, *md_cst;
+  // LS
+  uint32_t *ls_cnt, *ls_off, *ls_in, *ls_out;
+  // T3
+  uint32_t *t3_cnt, *t3_off, *t3_a, *t3_b, *t3_c;
+  // T5
+  uint32_t *t5_cnt, *t5_off, *t5_m0, *t5_m1, *t5_m2, *t5_m3, *t5_m4;
+  float *t5_score, *t5_kfull;
+  // pLS
+  uint32_t *pls_ev, *pls_ncand, *pls_cand;
+  float4 *pls_h0, *pls_h1;  // (x0, y0, z0, R), (cx, cy, cot, q)
+  float *pls_pt;
+  // pT3 / pT5
+  uint32_t *pt3_cnt, *pt3_off, *pt3_pls, *pt3_obj;
+  float *pt3_score;
+  uint32_t *pt5_cnt, *pt5_off, *pt5_pls, *pt5_obj;
+  float *pt5_score;
+  // duplicate removal: MD -> object lists and flags (u32 so they can be scanned)
+  uint32_t *c5_cnt, *c5_off, *c5_list, *c3_cnt, *c3_off, *c3_list, *ct_cnt, *ct_off, *ct_list;
+  uint32_t *alive5, *alive3, *alivet, *plstc, *used5, *used3, *cross3, *crosst;
+  uint32_t *sa5, *sa3, *sat, *sap;  // exclusive scans of the alive flags
+  // track candidates
+  uint32_t *tc_ev_off;
+  void *tc;  // lst_tc records
+  // scan scratch
+  uint32_t *scan_part;
+};
+
+typedef void (*MarkFn)(void* arg, int kernel_name);
+extern const char* const kKernelNames[];
+extern const int kNumKernelNames;
+
+struct Launch {
+  uint32_t grid;   // persistent grid (blocks)
+  uint32_t block;  // threads per block
+  uint32_t scan_grid;
+};
+
+}  // namespace lst

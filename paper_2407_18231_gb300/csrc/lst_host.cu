@@ -1,0 +1,1283 @@
+// Host runtime of liblst: geometry tables, connection map, device buffers, CUDA-graph
+// replay, results, the C ABI and the continuous-batching serving loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lst.h"
+#include "lst_device.cuh"
+
+namespace lst {
+int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
+                     MarkFn mark, void* arg);
+}
+
+using namespace lst;
+
+namespace {
+
+// ------------------------------------------------------------------ method constants
+// pT = KB * R with KB = 0.0029979 * 3.8; Rmin is the radius of a 0.8 GeV track (Sec. 1).
+const double KB_D = 0.0029979245800 * 3.8;
+const double RMIN_D = 0.8 / KB_D;
+
+MethodConst method_constants() {
+  MethodConst c;
+  c.KB = (float)KB_D;
+  c.Z0MAX = 15.0f;
+  c.E0 = 0.03f;
+  c.KARC = (float)(2.0 / (24.0 * RMIN_D * RMIN_D));
+  c.K3 = (float)(2.0 * RMIN_D * 0.95);
+  c.KMAX = (float)(1.0 / (RMIN_D * 0.95));
+  c.KAPPA = 0.05f;
+  c.KAPPA0 = 1.0e-4f;
+  c.KPT5 = 0.15f;
+  c.W0 = 0.02f;
+  c.PI = 3.14159265f;
+  c.HINV = (float)(1.0 / (2.0 * RMIN_D));
+  c.EDIR = 0.013f;
+  return c;
+}
+
+// ------------------------------------------------------------------ helpers
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+};
+#define CK(x)                                         \
+  do {                                                \
+    cudaError_t _e = (x);                             \
+    if (_e != cudaSuccess) throw CudaError{_e, #x};   \
+  } while (0)
+
+struct StatusError {
+  lst_status s;
+  std::string msg;
+};
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+int surface_of(const lst_module_desc& m) {
+  if (m.subdet == 0) return (m.layer >= 1 && m.layer <= 6) ? m.layer - 1 : -1;
+  if (m.subdet == 1 && m.layer >= 1 && m.layer <= 5) {
+    if (m.side < 0) return 6 + m.layer - 1;
+    if (m.side > 0) return 11 + m.layer - 1;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------ device buffer
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void ensure(size_t b, uint64_t& total) {
+    if (b <= bytes) return;
+    if (p) {
+      cudaFree(p);
+      total -= bytes;
+    }
+    p = nullptr;
+    bytes = 0;
+    CK(cudaMalloc(&p, b));
+    bytes = b;
+    total += b;
+  }
+};
+
+// ------------------------------------------------------------------ geometry
+struct Geometry {
+  std::vector<lst_module_desc> mods;
+  uint32_t nm = 0;
+  std::vector<float4> modc;  // zeta, rho, delta, T
+  std::vector<float> rnext;
+  std::vector<uint8_t> subdet;
+  std::vector<int> surface;
+  float zb_half = 0.0f;
+  int32_t surf_first[NSURF];
+  uint32_t surf_nrows[NSURF];
+  uint32_t surf_row_base[NSURF];
+  std::vector<uint32_t> row_nphi, row_mod_base, row_mods;
+  std::vector<uint32_t> conn_off, conn;
+  bool have_map = false;
+  // device copies
+  DevBuf d_modc, d_rnext, d_subdet, d_mod_e, d_mod_g, d_row_nphi, d_row_base, d_row_mods, d_conn_off, d_conn;
+  uint64_t dev_bytes = 0;
+
+  ~Geometry() {
+    DevBuf* all[] = {&d_modc, &d_rnext, &d_subdet, &d_mod_e, &d_mod_g, &d_row_nphi,
+                     &d_row_base, &d_row_mods, &d_conn_off, &d_conn};
+    for (DevBuf* b : all) b->release();
+  }
+
+  void load(const lst_module_desc* m, uint32_t n) {
+    mods.assign(m, m + n);
+    nm = n;
+    modc.resize(n);
+    rnext.resize(n);
+    subdet.resize(n);
+    surface.resize(n);
+    for (int s = 0; s < NSURF; s++) {
+      surf_first[s] = -1;
+      surf_nrows[s] = 0;
+    }
+    float rlay[6] = {0, 0, 0, 0, 0, 0};
+    bool have[6] = {false, false, false, false, false, false};
+    zb_half = 0.0f;
+    for (uint32_t i = 0; i < n; i++) {
+      const lst_module_desc& d = mods[i];
+      const int s = surface_of(d);
+      if (s < 0 || d.nphi == 0 || d.iphi >= d.nphi || !std::isfinite(d.surf) || !std::isfinite(d.gap) ||
+          !std::isfinite(d.emin) || !std::isfinite(d.emax) || !(d.emax > d.emin))
+        throw StatusError{LST_ERR_BAD_INPUT, "module " + std::to_string(i) + " is malformed"};
+      surface[i] = s;
+      subdet[i] = d.subdet;
+      // bending slope at the module's largest radius, tolerances of its hits
+      const double rmax = d.subdet == 0 ? (double)d.surf + (double)d.gap : (double)d.emax;
+      const double sq = rmax / (2.0 * RMIN_D);
+      const float T = (float)(sq < 1.0 ? sq / std::sqrt(1.0 - sq * sq) : 1.0e30);
+      float zeta, rho;
+      if (d.subdet == 0) {
+        zeta = d.stype == 0 ? 0.15f : 1.30f;
+        rho = 0.0f;
+      } else {
+        zeta = 0.0f;
+        rho = 0.15f;
+      }
+      const float delta = 0.01f + rho;
+      modc[i] = make_float4(zeta, rho, delta, T);
+      if (surf_first[s] < 0) surf_first[s] = (int32_t)i;
+      surf_nrows[s] = std::max<uint32_t>(surf_nrows[s], d.ieta + 1u);
+      if (d.subdet == 0) {
+        rlay[d.layer - 1] = d.surf;
+        have[d.layer - 1] = true;
+        zb_half = std::max(zb_half, std::fabs(d.emin));
+        zb_half = std::max(zb_half, std::fabs(d.emax));
+      }
+    }
+    for (uint32_t i = 0; i < n; i++) {
+      const lst_module_desc& d = mods[i];
+      rnext[i] = 1.0e30f;
+      if (d.subdet == 0 && d.layer < 6 && have[d.layer]) rnext[i] = rlay[d.layer];
+    }
+    // rows (z bins / rings) of each surface, indexed by iphi
+    uint32_t nrows = 0;
+    for (int s = 0; s < NSURF; s++) {
+      surf_row_base[s] = nrows;
+      nrows += surf_nrows[s];
+    }
+    row_nphi.assign(nrows, 0);
+    row_mod_base.assign(nrows, 0);
+    for (uint32_t i = 0; i < n; i++) {
+      const uint32_t r = surf_row_base[surface[i]] + mods[i].ieta;
+      if (row_nphi[r] != 0 && row_nphi[r] != mods[i].nphi)
+        throw StatusError{LST_ERR_BAD_INPUT, "row with two sector counts"};
+      row_nphi[r] = mods[i].nphi;
+    }
+    uint32_t tot = 0;
+    for (uint32_t r = 0; r < nrows; r++) {
+      row_mod_base[r] = tot;
+      tot += row_nphi[r];
+    }
+    row_mods.assign(std::max<uint32_t>(tot, 1), NONE);
+    for (uint32_t i = 0; i < n; i++) {
+      const uint32_t r = surf_row_base[surface[i]] + mods[i].ieta;
+      uint32_t& slot = row_mods[row_mod_base[r] + mods[i].iphi];
+      if (slot != NONE) throw StatusError{LST_ERR_BAD_INPUT, "two modules share a row and sector"};
+      slot = i;
+    }
+  }
+
+  // ---- connection map: conservative bound of the LS selection over module pairs ----
+  struct Box {
+    double r0, r1, z0, z1;  // anchor ranges
+    double phic, phih;      // wedge centre and half width
+  };
+  Box box_of(uint32_t i) const {
+    const lst_module_desc& d = mods[i];
+    Box b;
+    if (d.subdet == 0) {
+      b.r0 = d.surf - 0.01; b.r1 = d.surf + 0.01;
+      b.z0 = d.emin - 0.5; b.z1 = d.emax + 0.5;
+    } else {
+      b.z0 = d.surf - 0.01; b.z1 = d.surf + 0.01;
+      b.r0 = d.emin - 0.5; b.r1 = d.emax + 0.5;
+    }
+    const double a0 = std::atan2((double)d.e0y, (double)d.e0x);
+    double w = std::atan2((double)d.e1y, (double)d.e1x) - a0;
+    while (w <= 0) w += 2 * M_PI;
+    b.phih = 0.5 * w;
+    b.phic = a0 + 0.5 * w;
+    return b;
+  }
+
+  // Can some anchor in A and some anchor in B pass the LS bending and r-z cuts?
+  bool reachable(uint32_t A, uint32_t Bm, const Box& a, const Box& b) const {
+    const double rs = (double)modc[A].y + (double)modc[Bm].y;
+    // bending cut => |tan(phi_b - phi_a)| <= T_B + e_max / (r_a - rs)
+    const double emax = 0.03 + 1.05 * rs;
+    const double dphi = std::atan((double)modc[Bm].w + emax / (a.r0 - rs)) + 3.0e-3;
+    double d = std::fmod(a.phic - b.phic, 2 * M_PI);
+    if (d > M_PI) d -= 2 * M_PI;
+    if (d < -M_PI) d += 2 * M_PI;
+    if (std::fabs(d) > a.phih + b.phih + dphi) return false;
+    // r-z cut: za rb - ra zb is multilinear, so its range over the box is spanned by the
+    // 16 corners; the tolerance is bounded by its largest value over the box
+    double lo = 1e300, hi = -1e300;
+    for (int c = 0; c < 16; c++) {
+      const double za = (c & 1) ? a.z1 : a.z0, ra = (c & 2) ? a.r1 : a.r0;
+      const double zb = (c & 4) ? b.z1 : b.z0, rb = (c & 8) ? b.r1 : b.r0;
+      const double f = za * rb - ra * zb;
+      lo = std::min(lo, f);
+      hi = std::max(hi, f);
+    }
+    const double fmin = (lo <= 0 && hi >= 0) ? 0.0 : std::min(std::fabs(lo), std::fabs(hi));
+    const double drmax = std::max(std::fabs(b.r1 - a.r0), std::fabs(b.r0 - a.r1));
+    const double zbm = std::max(std::fabs(b.z0), std::fabs(b.z1));
+    const double zam = std::max(std::fabs(a.z0), std::fabs(a.z1));
+    const double dzm = std::max(std::fabs(b.z1 - a.z0), std::fabs(b.z0 - a.z1));
+    const double karc = 2.0 / (24.0 * RMIN_D * RMIN_D);
+    const double tol = 15.0 * drmax + modc[A].x * b.r1 + modc[Bm].x * a.r1 + modc[A].y * zbm + modc[Bm].y * zam +
+                       karc * dzm * a.r1 * b.r1 * (a.r1 + b.r1);
+    return fmin <= tol * 1.01 + 0.01;
+  }
+
+  void build_map() {
+    std::vector<Box> boxes(nm);
+    for (uint32_t i = 0; i < nm; i++) boxes[i] = box_of(i);
+    std::vector<std::vector<uint32_t>> by_surface(NSURF);
+    for (uint32_t i = 0; i < nm; i++) by_surface[surface[i]].push_back(i);
+    conn_off.assign(nm + 1, 0);
+    conn.clear();
+    for (uint32_t A = 0; A < nm; A++) {
+      conn_off[A] = (uint32_t)conn.size();
+      const int s = surface[A];
+      int next[3], k = 0;
+      if (s < 6) {  // barrel layer: next layer, or out through the first disk of either side
+        if (s < 5) next[k++] = s + 1;
+        next[k++] = 6;
+        next[k++] = 11;
+      } else if ((s < 11 && s < 10) || (s >= 11 && s < 15)) {
+        next[k++] = s + 1;  // next disk on the same side
+      }
+      const size_t start = conn.size();
+      for (int t = 0; t < k; t++)
+        for (uint32_t Bm : by_surface[next[t]])
+          if (reachable(A, Bm, boxes[A], boxes[Bm])) conn.push_back(Bm);
+      std::sort(conn.begin() + start, conn.end());
+    }
+    conn_off[nm] = (uint32_t)conn.size();
+    have_map = true;
+  }
+
+  template <typename T>
+  void upload(DevBuf& b, const std::vector<T>& v) {
+    b.ensure(std::max<size_t>(v.size(), 1) * sizeof(T), dev_bytes);
+    if (!v.empty()) CK(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  }
+
+  void upload_tables() {
+    std::vector<float4> e(nm), g(nm);
+    for (uint32_t i = 0; i < nm; i++) {
+      e[i] = make_float4(mods[i].e0x, mods[i].e0y, mods[i].e1x, mods[i].e1y);
+      g[i] = make_float4(mods[i].surf, mods[i].gap, mods[i].emin, mods[i].emax);
+    }
+    upload(d_modc, modc);
+    upload(d_rnext, rnext);
+    upload(d_subdet, subdet);
+    upload(d_mod_e, e);
+    upload(d_mod_g, g);
+    upload(d_row_nphi, row_nphi);
+    upload(d_row_base, row_mod_base);
+    upload(d_row_mods, row_mods);
+  }
+
+  void upload_map() {
+    upload(d_conn_off, conn_off);
+    upload(d_conn, conn);
+  }
+
+  GeoView view() const {
+    GeoView v;
+    v.nm = nm;
+    v.zb_half = zb_half;
+    v.modc = (const float4*)d_modc.p;
+    v.rnext = (const float*)d_rnext.p;
+    v.subdet = (const uint8_t*)d_subdet.p;
+    v.conn_off = (const uint32_t*)d_conn_off.p;
+    v.conn = (const uint32_t*)d_conn.p;
+    v.mod_e = (const float4*)d_mod_e.p;
+    v.mod_g = (const float4*)d_mod_g.p;
+    for (int s = 0; s < NSURF; s++) {
+      v.surf_first[s] = surf_first[s];
+      v.surf_nrows[s] = surf_nrows[s];
+      v.surf_row_base[s] = surf_row_base[s];
+    }
+    v.row_nphi = (const uint32_t*)d_row_nphi.p;
+    v.row_mod_base = (const uint32_t*)d_row_base.p;
+    v.row_mods = (const uint32_t*)d_row_mods.p;
+    return v;
+  }
+};
+
+// ------------------------------------------------------------------ results
+struct Result {
+  std::vector<lst_tc> tcs;
+  bool has_objects = false;
+  std::vector<lst_md_rec> md;
+  std::vector<lst_ls_rec> ls;
+  std::vector<lst_t3_rec> t3;
+  std::vector<lst_t5_rec> t5;
+  std::vector<lst_px_rec> pt3, pt5;
+  std::vector<lst_pls_rec> pls;
+};
+
+// ------------------------------------------------------------------ capacities
+struct Caps {
+  uint32_t ev = 0, hits = 0, pls = 0, md = 0, ls = 0, t3 = 0, t5 = 0, pt3 = 0, pt5 = 0, tc = 0;
+};
+
+// ------------------------------------------------------------------ pipeline (one batch slot)
+struct Pipeline {
+  Geometry* geo = nullptr;
+  MethodConst C;
+  Launch L;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  Caps cap;
+  uint64_t dev_bytes = 0;
+  // learned object-per-hit ratios for sizing (grow only)
+  double r_md = 0.6, r_ls = 1.5, r_t3 = 1.0, r_t5 = 0.3, r_pt3 = 6.0, r_pt5 = 6.0;
+  // buffers
+  DevBuf hdr, in_x, in_y, in_z, in_det, in_hoff, in_pls, in_poff;
+  DevBuf sen_cnt, sen_off, hit_tmp, hit_ev, hit_idx, hit4;
+  DevBuf md_cnt, md_off, md_unit, md_lo_idx, md_up_idx, md_lo4, md_up4, md_cst;
+  DevBuf ls_cnt, ls_off, ls_in, ls_out;
+  DevBuf t3_cnt, t3_off, t3_a, t3_b, t3_c;
+  DevBuf t5_cnt, t5_off, t5_m[5], t5_score, t5_kfull;
+  DevBuf pls_ev, pls_ncand, pls_cand, pls_h0, pls_h1, pls_pt;
+  DevBuf pt3_cnt, pt3_off, pt3_pls, pt3_obj, pt3_score;
+  DevBuf pt5_cnt, pt5_off, pt5_pls, pt5_obj, pt5_score;
+  DevBuf c5_cnt, c5_off, c5_list, c3_cnt, c3_off, c3_list, ct_cnt, ct_off, ct_list;
+  DevBuf alive5, alive3, alivet, plstc, used5, used3, cross3, crosst, sa5, sa3, sat, sap;
+  DevBuf tc_ev_off, tc, scan_part;
+  // host staging (pinned)
+  Hdr* h_hdr = nullptr;        // header to upload
+  Hdr* h_hdr_out = nullptr;    // header read back
+  std::vector<char> stage_dummy;
+  void* h_stage = nullptr;
+  size_t h_stage_bytes = 0;
+  // graph
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
+  int kernels = 0;
+  // profile mode: one event after every kernel of an eager run
+  bool profile = false;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_name;
+  cudaEvent_t prof_start = nullptr;
+  // in-flight batch bookkeeping (serving / device path)
+  uint32_t n_ev = 0, n_hits = 0, n_pls = 0;
+  Hdr dev_inputs{};  // input pointers and sizes of the batch being run
+  bool pending = false;
+
+  ~Pipeline() { release(); }
+
+  std::vector<DevBuf*> all_buffers() {
+    std::vector<DevBuf*> v = {&hdr, &in_x, &in_y, &in_z, &in_det, &in_hoff, &in_pls, &in_poff, &sen_cnt, &sen_off,
+                              &hit_tmp, &hit_ev, &hit_idx, &hit4, &md_cnt, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
+                              &md_lo4, &md_up4, &md_cst, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_cnt, &t3_off, &t3_a,
+                              &t3_b, &t3_c, &t5_cnt, &t5_off, &t5_score, &t5_kfull, &pls_ev, &pls_ncand, &pls_cand,
+                              &pls_h0, &pls_h1, &pls_pt, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
+                              &pt5_cnt, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
+                              &c3_cnt, &c3_off, &c3_list, &ct_cnt, &ct_off, &ct_list, &alive5, &alive3, &alivet,
+                              &plstc, &used5, &used3, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
+                              &scan_part};
+    for (auto& b : t5_m) v.push_back(&b);
+    return v;
+  }
+
+  void release() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    graph_valid = false;
+    for (DevBuf* b : all_buffers()) b->release();
+    dev_bytes = 0;
+    if (h_hdr) cudaFreeHost(h_hdr);
+    if (h_hdr_out) cudaFreeHost(h_hdr_out);
+    if (h_stage) cudaFreeHost(h_stage);
+    h_hdr = h_hdr_out = nullptr;
+    h_stage = nullptr;
+    h_stage_bytes = 0;
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    prof_ev.clear();
+    if (prof_start) cudaEventDestroy(prof_start);
+    prof_start = nullptr;
+    if (done) cudaEventDestroy(done);
+    if (stream) cudaStreamDestroy(stream);
+    done = nullptr;
+    stream = nullptr;
+  }
+
+  void init(Geometry* g, const lst_config& cfg, int n_sm) {
+    geo = g;
+    C = method_constants();
+    const uint32_t bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
+    L.block = cfg.block_size ? cfg.block_size : 256;
+    L.grid = (uint32_t)n_sm * bps;
+    uint32_t sg = ((2u * (uint32_t)n_sm) + 31u) / 32u * 32u;
+    L.scan_grid = std::min<uint32_t>(sg, 1024u);
+    CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    profile = cfg.profile != 0;
+    if (profile) {
+      CK(cudaEventCreate(&prof_start));
+      prof_ev.resize(160);
+      for (auto& e : prof_ev) CK(cudaEventCreate(&e));
+    }
+    CK(cudaMallocHost((void**)&h_hdr, sizeof(Hdr)));
+    CK(cudaMallocHost((void**)&h_hdr_out, sizeof(Hdr)));
+    hdr.ensure(sizeof(Hdr), dev_bytes);
+    scan_part.ensure(1024 * sizeof(uint32_t), dev_bytes);
+  }
+
+  template <typename T>
+  void need(DevBuf& b, size_t n) {
+    const size_t before = b.bytes;
+    b.ensure(std::max<size_t>(n, 1) * sizeof(T), dev_bytes);
+    if (b.bytes != before) graph_valid = false;
+  }
+
+  // Grow every buffer to the capacities in c (never shrinks).
+  void ensure_caps(const Caps& c_in) {
+    Caps c = c_in;
+    c.ev = std::max(c.ev, cap.ev);
+    c.hits = std::max(c.hits, cap.hits);
+    c.pls = std::max(c.pls, cap.pls);
+    c.md = std::max(c.md, cap.md);
+    c.ls = std::max(c.ls, cap.ls);
+    c.t3 = std::max(c.t3, cap.t3);
+    c.t5 = std::max(c.t5, cap.t5);
+    c.pt3 = std::max(c.pt3, cap.pt3);
+    c.pt5 = std::max(c.pt5, cap.pt5);
+    c.tc = std::max(c.tc, cap.tc);
+    const size_t nm = geo->nm;
+    need<uint32_t>(sen_cnt, c.ev * 2 * nm + 1);
+    need<uint32_t>(sen_off, c.ev * 2 * nm + 1);
+    need<uint32_t>(hit_tmp, c.hits);
+    need<uint32_t>(hit_ev, c.hits);
+    need<uint32_t>(hit_idx, c.hits);
+    need<float4>(hit4, c.hits);
+    need<uint32_t>(md_cnt, c.ev * nm);
+    need<uint32_t>(md_off, c.ev * nm + 1);
+    need<uint32_t>(md_unit, c.md);
+    need<uint32_t>(md_lo_idx, c.md);
+    need<uint32_t>(md_up_idx, c.md);
+    need<float4>(md_lo4, c.md);
+    need<float4>(md_up4, c.md);
+    need<float4>(md_cst, c.md);
+    need<uint32_t>(ls_cnt, c.md);
+    need<uint32_t>(ls_off, c.md + 1);
+    need<uint32_t>(ls_in, c.ls);
+    need<uint32_t>(ls_out, c.ls);
+    need<uint32_t>(t3_cnt, c.md);
+    need<uint32_t>(t3_off, c.md + 1);
+    need<uint32_t>(t3_a, c.t3);
+    need<uint32_t>(t3_b, c.t3);
+    need<uint32_t>(t3_c, c.t3);
+    need<uint32_t>(t5_cnt, c.md);
+    need<uint32_t>(t5_off, c.md + 1);
+    for (auto& b : t5_m) need<uint32_t>(b, c.t5);
+    need<float>(t5_score, c.t5);
+    need<float>(t5_kfull, c.t5);
+    need<uint32_t>(pls_ev, c.pls);
+    need<uint32_t>(pls_ncand, c.pls);
+    need<uint32_t>(pls_cand, (size_t)c.pls * MAX_CAND);
+    need<float4>(pls_h0, c.pls);
+    need<float4>(pls_h1, c.pls);
+    need<float>(pls_pt, c.pls);
+    need<uint32_t>(pt3_cnt, c.pls);
+    need<uint32_t>(pt3_off, c.pls + 1);
+    need<uint32_t>(pt3_pls, c.pt3);
+    need<uint32_t>(pt3_obj, c.pt3);
+    need<float>(pt3_score, c.pt3);
+    need<uint32_t>(pt5_cnt, c.pls);
+    need<uint32_t>(pt5_off, c.pls + 1);
+    need<uint32_t>(pt5_pls, c.pt5);
+    need<uint32_t>(pt5_obj, c.pt5);
+    need<float>(pt5_score, c.pt5);
+    need<uint32_t>(c5_cnt, c.md + 1);
+    need<uint32_t>(c5_off, c.md + 1);
+    need<uint32_t>(c5_list, (size_t)5 * c.pt5);
+    need<uint32_t>(c3_cnt, c.md + 1);
+    need<uint32_t>(c3_off, c.md + 1);
+    need<uint32_t>(c3_list, (size_t)3 * c.pt3);
+    need<uint32_t>(ct_cnt, c.md + 1);
+    need<uint32_t>(ct_off, c.md + 1);
+    need<uint32_t>(ct_list, (size_t)5 * c.t5);
+    need<uint32_t>(alive5, c.pt5);
+    need<uint32_t>(alive3, c.pt3);
+    need<uint32_t>(alivet, c.t5);
+    need<uint32_t>(plstc, c.pls);
+    need<uint32_t>(used5, c.pls);
+    need<uint32_t>(used3, c.pls);
+    need<uint32_t>(cross3, c.pt3);
+    need<uint32_t>(crosst, c.t5);
+    need<uint32_t>(sa5, c.pt5 + 1);
+    need<uint32_t>(sa3, c.pt3 + 1);
+    need<uint32_t>(sat, c.t5 + 1);
+    need<uint32_t>(sap, c.pls + 1);
+    need<uint32_t>(tc_ev_off, c.ev + 1);
+    need<lst_tc>(tc, c.tc);
+    cap = c;
+  }
+
+  void ensure_inputs(uint32_t ne, uint32_t nh, uint32_t np) {
+    need<float>(in_x, nh);
+    need<float>(in_y, nh);
+    need<float>(in_z, nh);
+    need<uint32_t>(in_det, nh);
+    need<uint32_t>(in_hoff, ne + 1);
+    need<PlsIn>(in_pls, np);
+    need<uint32_t>(in_poff, ne + 1);
+  }
+
+  Caps estimate(uint32_t ne, uint32_t nh, uint32_t np) const {
+    Caps c;
+    c.ev = ne;
+    c.hits = nh;
+    c.pls = np;
+    auto f = [](double r, uint32_t n) { return (uint32_t)std::min(4.0e9, r * n * 1.25 + 1024); };
+    c.md = f(r_md, nh);
+    c.ls = f(r_ls, nh);
+    c.t3 = f(r_t3, nh);
+    c.t5 = f(r_t5, nh);
+    c.pt3 = f(r_pt3, np);
+    c.pt5 = f(r_pt5, np);
+    c.tc = c.t5 + np + 1024;
+    return c;
+  }
+
+  // Learn sizes from a finished run so that the next estimate is large enough.
+  void learn(const Hdr& h) {
+    if (h.n_hits) {
+      r_md = std::max(r_md, (double)h.tot[T_MD] / h.n_hits);
+      r_ls = std::max(r_ls, (double)h.tot[T_LS] / h.n_hits);
+      r_t3 = std::max(r_t3, (double)h.tot[T_T3] / h.n_hits);
+      r_t5 = std::max(r_t5, (double)h.tot[T_T5] / h.n_hits);
+    }
+    if (h.n_pls) {
+      r_pt3 = std::max(r_pt3, (double)h.tot[T_PT3] / h.n_pls);
+      r_pt5 = std::max(r_pt5, (double)h.tot[T_PT5] / h.n_pls);
+    }
+  }
+
+  BufView view() {
+    BufView v;
+    v.hdr = (Hdr*)hdr.p;
+    v.cap_ev = cap.ev; v.cap_hits = cap.hits; v.cap_md = cap.md; v.cap_ls = cap.ls; v.cap_t3 = cap.t3;
+    v.cap_t5 = cap.t5; v.cap_pls = cap.pls; v.cap_pt3 = cap.pt3; v.cap_pt5 = cap.pt5; v.cap_tc = cap.tc;
+#define P32(x) (uint32_t*)x.p
+    v.sen_cnt = P32(sen_cnt); v.sen_off = P32(sen_off); v.hit_tmp = P32(hit_tmp); v.hit_ev = P32(hit_ev);
+    v.hit_idx = P32(hit_idx); v.hit4 = (float4*)hit4.p;
+    v.md_cnt = P32(md_cnt); v.md_off = P32(md_off); v.md_unit = P32(md_unit); v.md_lo_idx = P32(md_lo_idx);
+    v.md_up_idx = P32(md_up_idx); v.md_lo4 = (float4*)md_lo4.p; v.md_up4 = (float4*)md_up4.p;
+    v.md_cst = (float4*)md_cst.p;
+    v.ls_cnt = P32(ls_cnt); v.ls_off = P32(ls_off); v.ls_in = P32(ls_in); v.ls_out = P32(ls_out);
+    v.t3_cnt = P32(t3_cnt); v.t3_off = P32(t3_off); v.t3_a = P32(t3_a); v.t3_b = P32(t3_b); v.t3_c = P32(t3_c);
+    v.t5_cnt = P32(t5_cnt); v.t5_off = P32(t5_off);
+    v.t5_m0 = P32(t5_m[0]); v.t5_m1 = P32(t5_m[1]); v.t5_m2 = P32(t5_m[2]); v.t5_m3 = P32(t5_m[3]);
+    v.t5_m4 = P32(t5_m[4]);
+    v.t5_score = (float*)t5_score.p; v.t5_kfull = (float*)t5_kfull.p;
+    v.pls_ev = P32(pls_ev); v.pls_ncand = P32(pls_ncand); v.pls_cand = P32(pls_cand);
+    v.pls_h0 = (float4*)pls_h0.p; v.pls_h1 = (float4*)pls_h1.p; v.pls_pt = (float*)pls_pt.p;
+    v.pt3_cnt = P32(pt3_cnt); v.pt3_off = P32(pt3_off); v.pt3_pls = P32(pt3_pls); v.pt3_obj = P32(pt3_obj);
+    v.pt3_score = (float*)pt3_score.p;
+    v.pt5_cnt = P32(pt5_cnt); v.pt5_off = P32(pt5_off); v.pt5_pls = P32(pt5_pls); v.pt5_obj = P32(pt5_obj);
+    v.pt5_score = (float*)pt5_score.p;
+    v.c5_cnt = P32(c5_cnt); v.c5_off = P32(c5_off); v.c5_list = P32(c5_list);
+    v.c3_cnt = P32(c3_cnt); v.c3_off = P32(c3_off); v.c3_list = P32(c3_list);
+    v.ct_cnt = P32(ct_cnt); v.ct_off = P32(ct_off); v.ct_list = P32(ct_list);
+    v.alive5 = P32(alive5); v.alive3 = P32(alive3); v.alivet = P32(alivet); v.plstc = P32(plstc);
+    v.used5 = P32(used5); v.used3 = P32(used3); v.cross3 = P32(cross3); v.crosst = P32(crosst);
+    v.sa5 = P32(sa5); v.sa3 = P32(sa3); v.sat = P32(sat); v.sap = P32(sap);
+    v.tc_ev_off = P32(tc_ev_off); v.tc = tc.p; v.scan_part = P32(scan_part);
+#undef P32
+    return v;
+  }
+
+  static void mark_cb(void* arg, int name) {
+    Pipeline* P = (Pipeline*)arg;
+    const size_t k = P->prof_name.size();
+    if (k < P->prof_ev.size()) {
+      cudaEventRecord(P->prof_ev[k], P->cur_stream);
+      P->prof_name.push_back(name);
+    }
+  }
+  cudaStream_t cur_stream = nullptr;
+
+  // Enqueue header upload, the kernels and the header read-back (eagerly or as one graph)
+  // on stream `on` (null: the pipeline's own stream).
+  void launch(bool use_graph, cudaStream_t on = nullptr) {
+    *h_hdr = dev_inputs;
+    const GeoView G = geo->view();
+    const BufView B = view();
+    cudaStream_t st = on ? on : stream;
+    cur_stream = st;
+    if (profile) {
+      prof_name.clear();
+      CK(cudaMemcpyAsync(hdr.p, h_hdr, sizeof(Hdr), cudaMemcpyHostToDevice, st));
+      CK(cudaEventRecord(prof_start, st));
+      kernels = enqueue_pipeline(C, G, B, L, st, &Pipeline::mark_cb, this);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(h_hdr_out, hdr.p, sizeof(Hdr), cudaMemcpyDeviceToHost, st));
+      CK(cudaEventRecord(done, st));
+      return;
+    }
+    if (use_graph) {
+      if (!graph_valid) {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        cudaMemcpyAsync(hdr.p, h_hdr, sizeof(Hdr), cudaMemcpyHostToDevice, stream);
+        kernels = enqueue_pipeline(C, G, B, L, stream, nullptr, nullptr);
+        cudaMemcpyAsync(h_hdr_out, hdr.p, sizeof(Hdr), cudaMemcpyDeviceToHost, stream);
+        CK(cudaStreamEndCapture(stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        graph_valid = true;
+      }
+      CK(cudaGraphLaunch(graph, st));
+    } else {
+      CK(cudaMemcpyAsync(hdr.p, h_hdr, sizeof(Hdr), cudaMemcpyHostToDevice, st));
+      kernels = enqueue_pipeline(C, G, B, L, st, nullptr, nullptr);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(h_hdr_out, hdr.p, sizeof(Hdr), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaEventRecord(done, st));
+  }
+
+  // Per-kernel times of the last profiled run, summed by kernel name.
+  std::vector<lst_profile_entry> profile_entries() {
+    std::vector<lst_profile_entry> out;
+    if (!profile) return out;
+    std::map<int, std::pair<uint32_t, float>> acc;
+    cudaEvent_t prev = prof_start;
+    for (size_t k = 0; k < prof_name.size(); k++) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, prev, prof_ev[k]));
+      auto& a = acc[prof_name[k]];
+      a.first += 1;
+      a.second += ms;
+      prev = prof_ev[k];
+    }
+    for (auto& kv : acc) {
+      lst_profile_entry e{};
+      snprintf(e.name, sizeof(e.name), "%s", kKernelNames[kv.first]);
+      e.launches = kv.second.first;
+      e.ms = kv.second.second;
+      out.push_back(e);
+    }
+    return out;
+  }
+
+  // Bounded wait for the launched batch; false on timeout.
+  bool wait(uint32_t timeout_ms) {
+    if (timeout_ms == 0) {
+      CK(cudaEventSynchronize(done));
+      return true;
+    }
+    const double t_end = now_s() + timeout_ms * 1e-3;
+    for (;;) {
+      const cudaError_t e = cudaEventQuery(done);
+      if (e == cudaSuccess) return true;
+      if (e != cudaErrorNotReady) throw CudaError{e, "cudaEventQuery"};
+      if (now_s() > t_end) return false;
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+
+  // Grow whatever overflowed (from the header) and report whether a re-run is needed.
+  bool grow_after_overflow(const Hdr& h) {
+    const uint32_t bits = h.err >> ERR_OVERFLOW_SHIFT;
+    if (!bits) return false;
+    Caps c = cap;
+    auto g = [](uint32_t need) { return (uint32_t)std::min<uint64_t>(4000000000ull, (uint64_t)need * 5 / 4 + 4096); };
+    if (bits & (1u << T_MD)) c.md = g(h.tot[T_MD]);
+    if (bits & (1u << T_LS)) c.ls = g(h.tot[T_LS]);
+    if (bits & (1u << T_T3)) c.t3 = g(h.tot[T_T3]);
+    if (bits & (1u << T_T5)) c.t5 = g(h.tot[T_T5]);
+    if (bits & (1u << T_PT3)) c.pt3 = g(h.tot[T_PT3]);
+    if (bits & (1u << T_PT5)) c.pt5 = g(h.tot[T_PT5]);
+    if (bits & (1u << T_C5)) c.pt5 = g(h.tot[T_C5] / 5 + 1);
+    if (bits & (1u << T_C3)) c.pt3 = g(h.tot[T_C3] / 3 + 1);
+    if (bits & (1u << T_CT)) c.t5 = g(h.tot[T_CT] / 5 + 1);
+    if (bits & (1u << T_TC)) c.tc = g(h.tot[T_TC]);
+    ensure_caps(c);
+    return true;
+  }
+};
+
+void pack_host_events(Pipeline& P, const lst_event* evs, uint32_t n) {
+  uint64_t nh = 0, np = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    if ((!evs[i].x || !evs[i].y || !evs[i].z || !evs[i].det) && evs[i].n_hits)
+      throw StatusError{LST_ERR_INVALID_ARG, "event with null hit arrays"};
+    if (!evs[i].pls && evs[i].n_pls) throw StatusError{LST_ERR_INVALID_ARG, "event with null pLS array"};
+    nh += evs[i].n_hits;
+    np += evs[i].n_pls;
+  }
+  if (nh > 0xF0000000ull || np > 0x0F000000ull) throw StatusError{LST_ERR_INVALID_ARG, "batch too large"};
+  P.ensure_inputs(n, (uint32_t)nh, (uint32_t)np);
+  const size_t bytes = nh * 16 + np * sizeof(PlsIn) + 2 * (n + 1) * 4 + 64;
+  if (bytes > P.h_stage_bytes) {
+    if (P.h_stage) cudaFreeHost(P.h_stage);
+    P.h_stage = nullptr;
+    P.h_stage_bytes = 0;
+    CK(cudaMallocHost(&P.h_stage, bytes * 3 / 2));
+    P.h_stage_bytes = bytes * 3 / 2;
+  }
+  char* s = (char*)P.h_stage;
+  float* hx = (float*)s;
+  float* hy = hx + nh;
+  float* hz = hy + nh;
+  uint32_t* hd = (uint32_t*)(hz + nh);
+  uint32_t* hoff = hd + nh;
+  uint32_t* poff = hoff + (n + 1);
+  PlsIn* hp = (PlsIn*)(((uintptr_t)(poff + n + 1) + 15) & ~(uintptr_t)15);
+  uint64_t oh = 0, op = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    hoff[i] = (uint32_t)oh;
+    poff[i] = (uint32_t)op;
+    const lst_event& e = evs[i];
+    if (e.n_hits) {
+      memcpy(hx + oh, e.x, e.n_hits * 4);
+      memcpy(hy + oh, e.y, e.n_hits * 4);
+      memcpy(hz + oh, e.z, e.n_hits * 4);
+      memcpy(hd + oh, e.det, e.n_hits * 4);
+    }
+    if (e.n_pls) memcpy(hp + op, e.pls, e.n_pls * sizeof(PlsIn));
+    oh += e.n_hits;
+    op += e.n_pls;
+  }
+  hoff[n] = (uint32_t)oh;
+  poff[n] = (uint32_t)op;
+  cudaStream_t st = P.stream;
+  if (nh) {
+    CK(cudaMemcpyAsync(P.in_x.p, hx, nh * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P.in_y.p, hy, nh * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P.in_z.p, hz, nh * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P.in_det.p, hd, nh * 4, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(P.in_hoff.p, hoff, (n + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(P.in_poff.p, poff, (n + 1) * 4, cudaMemcpyHostToDevice, st));
+  if (np) CK(cudaMemcpyAsync(P.in_pls.p, hp, np * sizeof(PlsIn), cudaMemcpyHostToDevice, st));
+  Hdr h{};
+  h.x = (const float*)P.in_x.p;
+  h.y = (const float*)P.in_y.p;
+  h.z = (const float*)P.in_z.p;
+  h.det = (const uint32_t*)P.in_det.p;
+  h.hit_off = (const uint32_t*)P.in_hoff.p;
+  h.pls = (const PlsIn*)P.in_pls.p;
+  h.pls_off = (const uint32_t*)P.in_poff.p;
+  h.n_ev = n;
+  h.n_hits = (uint32_t)nh;
+  h.n_pls = (uint32_t)np;
+  P.dev_inputs = h;
+  P.n_ev = n;
+  P.n_hits = (uint32_t)nh;
+  P.n_pls = (uint32_t)np;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct lst_ctx {
+  lst_config cfg{};
+  int device = 0;
+  int n_sm = 0;
+  Geometry geo;
+  Pipeline main;
+  std::map<lst_result_id, Result> results;
+  lst_result_id next_id = 1;
+  std::string err;
+  lst_stats stats{};
+  uint32_t reruns = 0;
+};
+
+namespace {
+
+lst_status fail(lst_ctx* c, lst_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+template <typename F>
+lst_status guarded(lst_ctx* c, F&& f) {
+  try {
+    if (c) cudaSetDevice(c->device);
+    return f();
+  } catch (const CudaError& e) {
+    return fail(c, LST_ERR_CUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+  } catch (const StatusError& e) {
+    return fail(c, e.s, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(c, LST_ERR_OOM, "host allocation failed");
+  }
+}
+
+// Copy the per-event results of a finished batch to the host.
+void collect(lst_ctx* c, Pipeline& P, lst_result_id* outs, uint32_t* n_tc_per_event) {
+  const Hdr& h = *P.h_hdr_out;
+  const uint32_t ne = P.n_ev;
+  std::vector<uint32_t> evoff(ne + 1);
+  CK(cudaMemcpyAsync(evoff.data(), P.tc_ev_off.p, (ne + 1) * 4, cudaMemcpyDeviceToHost, P.stream));
+  std::vector<lst_tc> tcs(h.tot[T_TC]);
+  if (!tcs.empty())
+    CK(cudaMemcpyAsync(tcs.data(), P.tc.p, tcs.size() * sizeof(lst_tc), cudaMemcpyDeviceToHost, P.stream));
+  const bool keep = c->cfg.keep_objects != 0 && outs;
+  std::vector<uint32_t> md_off, md_unit, md_lo, md_up, ls_in, ls_out, t3a, t3b, t3c, t5m[5], t3_off, t5_off, pt3p,
+      pt3o, pt5p, pt5o, a5, a3, at, ptc, pncand, pcand, pt3_off, pt5_off, poff;
+  std::vector<float> t5s, t5k, pt3s, pt5s;
+  auto get = [&](auto& v, DevBuf& b, size_t n) {
+    v.resize(n);
+    if (n) CK(cudaMemcpyAsync(v.data(), b.p, n * sizeof(v[0]), cudaMemcpyDeviceToHost, P.stream));
+  };
+  if (keep) {
+    const size_t nm = c->geo.nm;
+    get(md_off, P.md_off, ne * nm + 1);
+    get(md_unit, P.md_unit, h.tot[T_MD]);
+    get(md_lo, P.md_lo_idx, h.tot[T_MD]);
+    get(md_up, P.md_up_idx, h.tot[T_MD]);
+    get(ls_in, P.ls_in, h.tot[T_LS]);
+    get(ls_out, P.ls_out, h.tot[T_LS]);
+    get(t3a, P.t3_a, h.tot[T_T3]);
+    get(t3b, P.t3_b, h.tot[T_T3]);
+    get(t3c, P.t3_c, h.tot[T_T3]);
+    for (int k = 0; k < 5; k++) get(t5m[k], P.t5_m[k], h.tot[T_T5]);
+    get(t5s, P.t5_score, h.tot[T_T5]);
+    get(t5k, P.t5_kfull, h.tot[T_T5]);
+    get(t3_off, P.t3_off, h.tot[T_MD] + 1);
+    get(t5_off, P.t5_off, h.tot[T_MD] + 1);
+    get(pt3p, P.pt3_pls, h.tot[T_PT3]);
+    get(pt3o, P.pt3_obj, h.tot[T_PT3]);
+    get(pt3s, P.pt3_score, h.tot[T_PT3]);
+    get(pt5p, P.pt5_pls, h.tot[T_PT5]);
+    get(pt5o, P.pt5_obj, h.tot[T_PT5]);
+    get(pt5s, P.pt5_score, h.tot[T_PT5]);
+    get(a5, P.alive5, h.tot[T_PT5]);
+    get(a3, P.alive3, h.tot[T_PT3]);
+    get(at, P.alivet, h.tot[T_T5]);
+    get(ptc, P.plstc, P.n_pls);
+    get(pncand, P.pls_ncand, P.n_pls);
+    get(pcand, P.pls_cand, (size_t)P.n_pls * MAX_CAND);
+    get(pt3_off, P.pt3_off, P.n_pls + 1);
+    get(pt5_off, P.pt5_off, P.n_pls + 1);
+    get(poff, P.in_poff, ne + 1);
+  }
+  CK(cudaStreamSynchronize(P.stream));
+  const uint32_t nm = c->geo.nm;
+  for (uint32_t e = 0; e < ne; e++) {
+    if (n_tc_per_event) n_tc_per_event[e] = evoff[e + 1] - evoff[e];
+    if (!outs) continue;
+    Result r;
+    r.tcs.assign(tcs.begin() + evoff[e], tcs.begin() + evoff[e + 1]);
+    if (keep) {
+      r.has_objects = true;
+      const uint32_t mb = md_off[(size_t)e * nm], me = md_off[(size_t)(e + 1) * nm];
+      for (uint32_t i = mb; i < me; i++) r.md.push_back({md_unit[i] - e * nm, md_lo[i], md_up[i]});
+      // LS of this event: those whose inner MD is in [mb, me)
+      for (size_t i = 0; i < ls_in.size(); i++)
+        if (ls_in[i] >= mb && ls_in[i] < me) r.ls.push_back({{ls_in[i] - mb, ls_out[i] - mb}});
+      const uint32_t tb = t3_off[mb], te = t3_off[me];
+      for (uint32_t i = tb; i < te; i++) r.t3.push_back({{t3a[i] - mb, t3b[i] - mb, t3c[i] - mb}});
+      const uint32_t fb = t5_off[mb], fe = t5_off[me];
+      for (uint32_t i = fb; i < fe; i++)
+        r.t5.push_back({{t5m[0][i] - mb, t5m[1][i] - mb, t5m[2][i] - mb, t5m[3][i] - mb, t5m[4][i] - mb},
+                        t5s[i], t5k[i], at[i]});
+      const uint32_t pb = poff[e], pe = poff[e + 1];
+      for (uint32_t i = pt3_off[pb]; i < pt3_off[pe]; i++) r.pt3.push_back({pt3p[i] - pb, pt3o[i] - tb, pt3s[i], a3[i]});
+      for (uint32_t i = pt5_off[pb]; i < pt5_off[pe]; i++) r.pt5.push_back({pt5p[i] - pb, pt5o[i] - fb, pt5s[i], a5[i]});
+      for (uint32_t p = pb; p < pe; p++) {
+        lst_pls_rec pr{};
+        pr.n_cand = pncand[p];
+        for (uint32_t k = 0; k < pr.n_cand && k < MAX_CAND; k++) pr.cand[k] = pcand[(size_t)p * MAX_CAND + k];
+        pr.is_tc = ptc[p];
+        r.pls.push_back(pr);
+      }
+    }
+    const lst_result_id id = c->next_id++;
+    c->results.emplace(id, std::move(r));
+    outs[e] = id;
+  }
+  c->stats.n_events = ne;
+  c->stats.n_hits = h.n_hits;
+  c->stats.n_pls = h.n_pls;
+  c->stats.n_md = h.tot[T_MD];
+  c->stats.n_ls = h.tot[T_LS];
+  c->stats.n_t3 = h.tot[T_T3];
+  c->stats.n_t5 = h.tot[T_T5];
+  c->stats.n_pt3 = h.tot[T_PT3];
+  c->stats.n_pt5 = h.tot[T_PT5];
+  c->stats.n_tc = h.tot[T_TC];
+  c->stats.kernels = (uint32_t)P.kernels;
+  c->stats.device_bytes = P.dev_bytes + c->geo.dev_bytes;
+}
+
+// Runs the already-packed batch of P to completion: launch, bounded wait, re-run with
+// larger buffers while a list overflows.
+lst_status run_packed(lst_ctx* c, Pipeline& P, bool use_graph, uint32_t timeout_ms) {
+  for (int attempt = 0; attempt < 12; attempt++) {
+    P.launch(use_graph);
+    if (!P.wait(timeout_ms)) return fail(c, LST_ERR_TIMEOUT, "device did not finish within the time limit");
+    const Hdr& h = *P.h_hdr_out;
+    if (h.err & ERR_BAD_INPUT)
+      return fail(c, LST_ERR_BAD_INPUT, "bad input: module id out of range, non-finite value or invalid pLS");
+    if (!P.grow_after_overflow(h)) {
+      P.learn(h);
+      return LST_OK;
+    }
+    c->reruns++;
+    c->stats.reruns++;
+  }
+  return fail(c, LST_ERR_OOM, "object lists kept outgrowing their storage");
+}
+
+lst_status run_host_batch(lst_ctx* c, const lst_event* evs, uint32_t n, lst_result_id* outs, bool use_graph) {
+  if (!c->geo.have_map) return fail(c, LST_ERR_NO_MAP, "lst_build_connection_map has not run");
+  Pipeline& P = c->main;
+  pack_host_events(P, evs, n);
+  P.ensure_caps(P.estimate(n, P.n_hits, P.n_pls));
+  const lst_status s = run_packed(c, P, use_graph, 0);
+  if (s != LST_OK) return s;
+  collect(c, P, outs, nullptr);
+  return LST_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* lst_status_string(lst_status s) {
+  switch (s) {
+    case LST_OK: return "ok";
+    case LST_ERR_INVALID_ARG: return "invalid argument";
+    case LST_ERR_BAD_INPUT: return "bad input";
+    case LST_ERR_NO_MAP: return "connection map not built";
+    case LST_ERR_OOM: return "out of memory";
+    case LST_ERR_BUDGET: return "memory budget exceeded";
+    case LST_ERR_CUDA: return "CUDA error";
+    case LST_ERR_TIMEOUT: return "timeout";
+    case LST_ERR_BUFFER_TOO_SMALL: return "buffer too small";
+    case LST_ERR_NOT_FOUND: return "result not found";
+    default: return "unknown status";
+  }
+}
+
+lst_status lst_load_geometry(const lst_module_desc* mods, uint32_t n_mods, const lst_config* cfg, lst_ctx** out_ctx) {
+  if (!mods || n_mods == 0 || !out_ctx) return LST_ERR_INVALID_ARG;
+  *out_ctx = nullptr;
+  lst_ctx* c = nullptr;
+  try {
+    c = new lst_ctx();
+  } catch (...) {
+    return LST_ERR_OOM;
+  }
+  if (cfg) c->cfg = *cfg;
+  c->device = c->cfg.device;
+  const lst_status s = guarded(c, [&]() -> lst_status {
+    CK(cudaSetDevice(c->device));
+    CK(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    c->geo.load(mods, n_mods);
+    c->geo.upload_tables();
+    c->main.init(&c->geo, c->cfg, c->n_sm);
+    return LST_OK;
+  });
+  if (s != LST_OK) {
+    delete c;
+    return s;
+  }
+  *out_ctx = c;
+  return LST_OK;
+}
+
+lst_status lst_build_connection_map(lst_ctx* c) {
+  if (!c) return LST_ERR_INVALID_ARG;
+  return guarded(c, [&]() -> lst_status {
+    c->geo.build_map();
+    c->geo.upload_map();
+    c->main.graph_valid = false;
+    return LST_OK;
+  });
+}
+
+lst_status lst_run_event(lst_ctx* c, const lst_event* ev, lst_result_id* out) {
+  if (!c || !ev || !out) return LST_ERR_INVALID_ARG;
+  return guarded(c, [&]() { return run_host_batch(c, ev, 1, out, false); });
+}
+
+lst_status lst_run_batch(lst_ctx* c, const lst_event* evs, uint32_t n, lst_result_id* outs) {
+  if (!c || !evs || !outs || n == 0) return LST_ERR_INVALID_ARG;
+  const bool g = c->cfg.use_graph != 2;
+  return guarded(c, [&]() { return run_host_batch(c, evs, n, outs, g); });
+}
+
+lst_status lst_run_batch_device(lst_ctx* c, const lst_batch_dev* b, void* stream) {
+  if (!c || !b || b->n_events == 0 || !b->hit_off || !b->pls_off) return LST_ERR_INVALID_ARG;
+  if (b->n_hits && (!b->x || !b->y || !b->z || !b->det)) return LST_ERR_INVALID_ARG;
+  if (b->n_pls && !b->pls) return LST_ERR_INVALID_ARG;
+  return guarded(c, [&]() -> lst_status {
+    if (!c->geo.have_map) return fail(c, LST_ERR_NO_MAP, "lst_build_connection_map has not run");
+    Pipeline& P = c->main;
+    Hdr h{};
+    h.x = b->x; h.y = b->y; h.z = b->z; h.det = b->det; h.hit_off = b->hit_off;
+    h.pls = (const PlsIn*)b->pls; h.pls_off = b->pls_off;
+    h.n_ev = b->n_events; h.n_hits = b->n_hits; h.n_pls = b->n_pls;
+    P.dev_inputs = h;
+    P.n_ev = b->n_events;
+    P.n_hits = b->n_hits;
+    P.n_pls = b->n_pls;
+    P.ensure_caps(P.estimate(P.n_ev, P.n_hits, P.n_pls));
+    P.launch(c->cfg.use_graph != 2, (cudaStream_t)stream);
+    P.pending = true;
+    return LST_OK;
+  });
+}
+
+lst_status lst_batch_finish(lst_ctx* c, uint32_t timeout_ms, uint32_t* n_tc_per_event, lst_result_id* outs) {
+  if (!c) return LST_ERR_INVALID_ARG;
+  return guarded(c, [&]() -> lst_status {
+    Pipeline& P = c->main;
+    if (!P.pending) return fail(c, LST_ERR_INVALID_ARG, "no batch in flight");
+    P.pending = false;
+    if (!P.wait(timeout_ms)) return fail(c, LST_ERR_TIMEOUT, "device did not finish within the time limit");
+    const Hdr& h = *P.h_hdr_out;
+    if (h.err & ERR_BAD_INPUT)
+      return fail(c, LST_ERR_BAD_INPUT, "bad input: module id out of range, non-finite value or invalid pLS");
+    if (P.grow_after_overflow(h)) {
+      c->reruns++;
+      c->stats.reruns++;
+      const lst_status s = run_packed(c, P, c->cfg.use_graph != 2, timeout_ms);
+      if (s != LST_OK) return s;
+    } else {
+      P.learn(h);
+    }
+    if (n_tc_per_event || outs) collect(c, P, outs, n_tc_per_event);
+    return LST_OK;
+  });
+}
+
+lst_status lst_get_candidates(lst_ctx* c, lst_result_id id, lst_tc* buf, uint32_t cap, uint32_t* n_out) {
+  if (!c || !n_out) return LST_ERR_INVALID_ARG;
+  auto it = c->results.find(id);
+  if (it == c->results.end()) return fail(c, LST_ERR_NOT_FOUND, "unknown result id");
+  const auto& v = it->second.tcs;
+  *n_out = (uint32_t)v.size();
+  if (!buf) return LST_OK;
+  if (cap < v.size()) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "candidate buffer too small");
+  if (!v.empty()) memcpy(buf, v.data(), v.size() * sizeof(lst_tc));
+  return LST_OK;
+}
+
+lst_status lst_get_objects(lst_ctx* c, lst_result_id id, int32_t kind, void* buf, uint32_t cap, uint32_t* n_out) {
+  if (!c || !n_out) return LST_ERR_INVALID_ARG;
+  auto it = c->results.find(id);
+  if (it == c->results.end()) return fail(c, LST_ERR_NOT_FOUND, "unknown result id");
+  const Result& r = it->second;
+  if (!r.has_objects) return fail(c, LST_ERR_INVALID_ARG, "objects were not kept (keep_objects = 0)");
+  const void* src = nullptr;
+  size_t n = 0, sz = 0;
+  switch (kind) {
+    case LST_OBJ_MD: src = r.md.data(); n = r.md.size(); sz = sizeof(lst_md_rec); break;
+    case LST_OBJ_LS: src = r.ls.data(); n = r.ls.size(); sz = sizeof(lst_ls_rec); break;
+    case LST_OBJ_T3: src = r.t3.data(); n = r.t3.size(); sz = sizeof(lst_t3_rec); break;
+    case LST_OBJ_T5: src = r.t5.data(); n = r.t5.size(); sz = sizeof(lst_t5_rec); break;
+    case LST_OBJ_PT3: src = r.pt3.data(); n = r.pt3.size(); sz = sizeof(lst_px_rec); break;
+    case LST_OBJ_PT5: src = r.pt5.data(); n = r.pt5.size(); sz = sizeof(lst_px_rec); break;
+    case LST_OBJ_PLS: src = r.pls.data(); n = r.pls.size(); sz = sizeof(lst_pls_rec); break;
+    default: return fail(c, LST_ERR_INVALID_ARG, "unknown object kind");
+  }
+  *n_out = (uint32_t)n;
+  if (!buf) return LST_OK;
+  if (cap < n) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "object buffer too small");
+  if (n) memcpy(buf, src, n * sz);
+  return LST_OK;
+}
+
+lst_status lst_release_result(lst_ctx* c, lst_result_id id) {
+  if (!c) return LST_ERR_INVALID_ARG;
+  if (!c->results.erase(id)) return fail(c, LST_ERR_NOT_FOUND, "unknown result id");
+  return LST_OK;
+}
+
+void lst_destroy(lst_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  delete c;
+}
+
+const char* lst_last_error(lst_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+lst_status lst_get_profile(lst_ctx* c, lst_profile_entry* buf, uint32_t cap, uint32_t* n_out) {
+  if (!c || !n_out) return LST_ERR_INVALID_ARG;
+  return guarded(c, [&]() -> lst_status {
+    const std::vector<lst_profile_entry> v = c->main.profile_entries();
+    *n_out = (uint32_t)v.size();
+    if (!buf) return LST_OK;
+    if (cap < v.size()) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "profile buffer too small");
+    if (!v.empty()) memcpy(buf, v.data(), v.size() * sizeof(lst_profile_entry));
+    return LST_OK;
+  });
+}
+
+lst_status lst_get_stats(lst_ctx* c, lst_stats* out) {
+  if (!c || !out) return LST_ERR_INVALID_ARG;
+  *out = c->stats;
+  out->reruns = c->reruns;
+  out->device_bytes = c->main.dev_bytes + c->geo.dev_bytes;
+  return LST_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ serving
+namespace {
+
+struct Slot {
+  std::unique_ptr<Pipeline> P;
+  std::vector<uint32_t> events;  // indices of the events in flight
+  bool busy = false;
+};
+
+}  // namespace
+
+extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, const lst_event* evs,
+                                       const double* arrival_s, uint32_t n, double* latency_s, uint32_t* n_tc,
+                                       lst_result_id* outs, double* wall_s) {
+  if (!c || !cfg || !evs || !arrival_s || n == 0 || !latency_s || cfg->n_slots == 0 || cfg->max_batch == 0)
+    return LST_ERR_INVALID_ARG;
+  return guarded(c, [&]() -> lst_status {
+    if (!c->geo.have_map) return fail(c, LST_ERR_NO_MAP, "lst_build_connection_map has not run");
+    std::vector<Slot> slots(cfg->n_slots);
+    for (auto& s : slots) {
+      s.P.reset(new Pipeline());
+      s.P->init(&c->geo, c->cfg, c->n_sm);
+      // start from what the main pipeline has learned about object sizes
+      s.P->r_md = c->main.r_md; s.P->r_ls = c->main.r_ls; s.P->r_t3 = c->main.r_t3; s.P->r_t5 = c->main.r_t5;
+      s.P->r_pt3 = c->main.r_pt3; s.P->r_pt5 = c->main.r_pt5;
+    }
+    const uint64_t budget = cfg->memory_budget;
+    auto held = [&]() {
+      uint64_t t = c->geo.dev_bytes + c->main.dev_bytes;
+      for (auto& s : slots) t += s.P->dev_bytes;
+      return t;
+    };
+    std::deque<uint32_t> queue;
+    uint32_t next = 0, done = 0;
+    const double t0 = now_s();
+    std::vector<uint32_t> tcn;
+    while (done < n) {
+      bool progress = false;
+      const double now = now_s() - t0;
+      while (next < n && arrival_s[next] <= now) queue.push_back(next++);
+      // completions
+      for (auto& s : slots) {
+        if (!s.busy) continue;
+        const cudaError_t q = cudaEventQuery(s.P->done);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) throw CudaError{q, "cudaEventQuery"};
+        const Hdr& h = *s.P->h_hdr_out;
+        if (h.err & ERR_BAD_INPUT)
+          return fail(c, LST_ERR_BAD_INPUT, "bad input in a served event");
+        if (s.P->grow_after_overflow(h)) {
+          c->reruns++;
+          if (budget && held() > budget) return fail(c, LST_ERR_BUDGET, "memory budget exceeded by a batch");
+          s.P->launch(true);
+          continue;
+        }
+        s.P->learn(h);
+        tcn.assign(s.events.size(), 0);
+        std::vector<lst_result_id> ids(s.events.size());
+        collect(c, *s.P, outs ? ids.data() : nullptr, tcn.data());
+        const double tdone = now_s() - t0;
+        for (size_t k = 0; k < s.events.size(); k++) {
+          const uint32_t e = s.events[k];
+          latency_s[e] = tdone - arrival_s[e];
+          if (n_tc) n_tc[e] = tcn[k];
+          if (outs) outs[e] = ids[k];
+        }
+        done += (uint32_t)s.events.size();
+        s.busy = false;
+        s.events.clear();
+        progress = true;
+      }
+      // admissions: idle slots take what has arrived, within the memory budget
+      for (auto& s : slots) {
+        if (s.busy || queue.empty()) continue;
+        std::vector<lst_event> batch;
+        uint64_t nh = 0, np = 0;
+        while (!queue.empty() && batch.size() < cfg->max_batch) {
+          const lst_event& e = evs[queue.front()];
+          if (budget && !batch.empty()) {
+            const Caps est = s.P->estimate((uint32_t)batch.size() + 1, (uint32_t)(nh + e.n_hits),
+                                           (uint32_t)(np + e.n_pls));
+            // rough bytes of the buffers this batch would need
+            const uint64_t bytes = (uint64_t)est.hits * 48 + (uint64_t)est.md * 96 + (uint64_t)est.ls * 16 +
+                                   (uint64_t)est.t3 * 24 + (uint64_t)est.t5 * 80 + (uint64_t)est.pls * 220 +
+                                   (uint64_t)(est.pt3 + est.pt5) * 40 + (uint64_t)est.ev * c->geo.nm * 24;
+            if (held() - s.P->dev_bytes + bytes > budget) break;
+          }
+          batch.push_back(e);
+          s.events.push_back(queue.front());
+          nh += e.n_hits;
+          np += e.n_pls;
+          queue.pop_front();
+        }
+        if (batch.empty()) continue;
+        pack_host_events(*s.P, batch.data(), (uint32_t)batch.size());
+        s.P->ensure_caps(s.P->estimate((uint32_t)batch.size(), s.P->n_hits, s.P->n_pls));
+        if (budget && held() > budget) {
+          if (batch.size() == 1) return fail(c, LST_ERR_BUDGET, "one event alone exceeds the memory budget");
+        }
+        s.P->launch(true);
+        s.busy = true;
+        progress = true;
+      }
+      if (!progress) {
+        bool any_busy = false;
+        for (auto& s : slots) any_busy |= s.busy;
+        if (!any_busy && queue.empty() && next < n) {
+          const double wait = arrival_s[next] - (now_s() - t0);
+          if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.001)));
+        } else {
+          std::this_thread::sleep_for(std::chrono::microseconds(10));
+        }
+      }
+    }
+    if (wall_s) *wall_s = now_s() - t0;
+    return LST_OK;
+  });
+}

@@ -1,0 +1,1063 @@
+// Stage kernels of the LST chain on sm_103a (arXiv:2407.18231, Sec. 1).
+//
+// Design: every object-producing stage is a "join" over a work unit (a module, an MD or a
+// pLS) whose candidates are the concatenation of a few contiguous index ranges.  One warp
+// owns a unit: it scans the range lengths with shuffles, walks the flattened candidates 32
+// at a time (each lane finds its range by a shuffle binary search), tests them, and
+// compacts the passing ones with ballot + popc into the unit's slice of the output.  A
+// count pass sizes every unit, a device-wide scan turns sizes into offsets, and a fill
+// pass re-runs the tests and writes.  Output order is therefore fixed by the inputs (unit
+// order, then candidate order) and never by scheduling, no list is truncated, and every
+// object list ends up sorted by its first MD -- which makes "all T3s starting on module M"
+// a single contiguous range for the pLS joins.  All grids are persistent (a multiple of the
+// SM count) and read their sizes from the device-side batch header, so one CUDA graph
+// replays any batch that fits the buffers.
+#include <cuda_runtime.h>
+
+#include "../../include/lst.h"
+#include "lst_device.cuh"
+
+namespace lst {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (uint32_t o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Number of lanes whose inclusive prefix is <= cand (the lane owning candidate cand).
+__device__ __forceinline__ uint32_t owner_lane(uint32_t incl, uint32_t cand) {
+  uint32_t o = 0;
+#pragma unroll
+  for (uint32_t s = 16; s >= 1; s >>= 1) {
+    const uint32_t v = __shfl_sync(FULL, incl, o + s - 1);
+    if (v <= cand) o += s;
+  }
+  return o;
+}
+
+struct NoPayload {};
+struct ScorePayload {
+  float score, kfull;
+};
+
+// Walks all (outer i, inner j) candidates of one unit; outer(i, begin, count) gives the
+// inner index range of outer item i.  Returns the number of passing candidates; with FILL
+// it also emits them at base + rank in candidate order.
+template <bool FILL, typename P, typename OuterFn, typename TestFn, typename EmitFn>
+__device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, OuterFn outer, TestFn test,
+                                              EmitFn emit) {
+  const uint32_t lane = lane_id();
+  uint32_t count = 0;
+  for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
+    uint32_t b = 0, c = 0;
+    if (g0 + lane < n_outer) outer(g0 + lane, b, c);
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t bo = __shfl_sync(FULL, b, o);
+      const uint32_t co = __shfl_sync(FULL, c, o);
+      const uint32_t io = __shfl_sync(FULL, incl, o);
+      const uint32_t j = bo + (cc - (io - co));
+      P pl;
+      bool pass = false;
+      if (cand < total) pass = test(g0 + o, j, pl);
+      const uint32_t bal = __ballot_sync(FULL, pass);
+      if (FILL && pass) emit(base + count + __popc(bal & ((1u << lane) - 1u)), g0 + o, j, pl);
+      count += __popc(bal);
+    }
+  }
+  return count;
+}
+
+__device__ __forceinline__ uint32_t find_slot(const uint32_t* off, uint32_t n, uint32_t x) {
+  // largest e in [0, n) with off[e] <= x (off non-decreasing, off[0] = 0)
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+#define WARP_LOOP(unit, n)                                                                         \
+  for (uint32_t unit = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; unit < (n);                   \
+       unit += (gridDim.x * blockDim.x) >> 5)
+#define THREAD_LOOP(i, n) \
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------------ scans
+// Exclusive scan of n = (*nptr) * mul u32 values into out[0..n], out[n] = total; the total
+// goes to hdr->tot[tot] and a total above cap raises that list's overflow bit.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sm, uint32_t& total) {
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t incl = warp_incl_scan(v);
+  if (lane == 31) sm[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t x = lane < nw ? sm[lane] : 0u;
+    const uint32_t xi = warp_incl_scan(x);
+    sm[lane] = xi - x;
+    if (lane == 31) sm[32] = xi;
+  }
+  __syncthreads();
+  const uint32_t r = sm[w] + incl - v;
+  total = sm[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul, const Hdr* H,
+                              uint32_t* part) {
+  if (H->err) return;
+  __shared__ uint32_t sm[33];
+  const uint32_t n = (*nptr) * mul;
+  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = blockIdx.x * chunk;
+  const uint32_t hi = min(n, lo + chunk);
+  uint32_t s = 0;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += in[i];
+  uint32_t tot;
+  block_excl_scan(s, sm, tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(uint32_t* part, const uint32_t* nptr, uint32_t mul, uint32_t* out, Hdr* H, int tot_idx,
+                           uint32_t cap) {
+  if (H->err) return;
+  __shared__ uint32_t sm[33];
+  const uint32_t np = blockDim.x;  // one partial per thread (grid of the other passes)
+  const uint32_t v = part[threadIdx.x];
+  uint32_t tot;
+  const uint32_t ex = block_excl_scan(v, sm, tot);
+  part[threadIdx.x] = ex;
+  (void)np;
+  if (threadIdx.x == 0) {
+    const uint32_t n = (*nptr) * mul;
+    out[n] = tot;
+    if (tot_idx >= 0) {
+      H->tot[tot_idx] = tot;
+      if (tot > cap) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + tot_idx));
+    }
+  }
+}
+
+__global__ void k_scan_apply(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul, const Hdr* H,
+                             const uint32_t* part, uint32_t* __restrict__ out) {
+  if (H->err) return;
+  __shared__ uint32_t sm[33];
+  const uint32_t n = (*nptr) * mul;
+  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = blockIdx.x * chunk;
+  const uint32_t hi = min(n, lo + chunk);
+  uint32_t carry = part[blockIdx.x];
+  const uint32_t tile = blockDim.x * 4;
+  for (uint32_t t = lo; t < hi; t += tile) {
+    const uint32_t i0 = t + threadIdx.x * 4;
+    uint32_t v[4];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      v[k] = (i0 + k < hi) ? in[i0 + k] : 0u;
+      s += v[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(s, sm, tot) + carry;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (i0 + k < hi) out[i0 + k] = ex;
+      ex += v[k];
+    }
+    carry += tot;
+  }
+}
+
+__global__ void k_zero(uint32_t* p, const uint32_t* nptr, uint32_t mul, uint32_t add) {
+  const uint32_t n = (*nptr) * mul + add;
+  THREAD_LOOP(i, n) p[i] = 0u;
+}
+
+__global__ void k_zero3(uint32_t* a, uint32_t* b, uint32_t* c, const Hdr* H) {
+  if (H->err) return;
+  const uint32_t n = H->tot[T_MD] + 1;
+  THREAD_LOOP(i, n) {
+    a[i] = 0u;
+    b[i] = 0u;
+    c[i] = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ hit binning
+// Count hits per (event, sensor); validate module ids and coordinates.
+__global__ void k_hits_count(GeoView G, BufView B) {
+  Hdr* H = B.hdr;
+  const uint32_t n = H->n_hits, ne = H->n_ev, two_nm = 2u * G.nm;
+  THREAD_LOOP(h, n) {
+    const uint32_t e = find_slot(H->hit_off, ne, h);
+    const uint32_t det = H->det[h];
+    const float x = H->x[h], y = H->y[h], z = H->z[h];
+    B.hit_ev[h] = e;
+    if (det >= two_nm || !isfinite(x) || !isfinite(y) || !isfinite(z)) {
+      atomicOr(&H->err, ERR_BAD_INPUT);
+      continue;
+    }
+    atomicAdd(&B.sen_cnt[e * two_nm + det], 1u);
+  }
+}
+
+__global__ void k_hits_scatter(GeoView G, BufView B) {
+  Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->n_hits, two_nm = 2u * G.nm;
+  THREAD_LOOP(h, n) {
+    const uint32_t bkt = B.hit_ev[h] * two_nm + H->det[h];
+    const uint32_t pos = B.sen_off[bkt] + atomicSub(&B.sen_cnt[bkt], 1u) - 1u;
+    B.hit_tmp[pos] = h;
+  }
+}
+
+// Stable order inside each sensor bucket: rank by input index.
+__global__ void k_hits_sort(GeoView G, BufView B) {
+  Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->n_hits, two_nm = 2u * G.nm;
+  THREAD_LOOP(p, n) {
+    const uint32_t h = B.hit_tmp[p];
+    const uint32_t e = B.hit_ev[h];
+    const uint32_t bkt = e * two_nm + H->det[h];
+    const uint32_t lo = B.sen_off[bkt], hi = B.sen_off[bkt + 1];
+    uint32_t rank = 0;
+    for (uint32_t q = lo; q < hi; q++) rank += B.hit_tmp[q] < h;
+    const float x = H->x[h], y = H->y[h], z = H->z[h];
+    B.hit4[lo + rank] = make_float4(x, y, z, sqrtf(x * x + y * y));
+    B.hit_idx[lo + rank] = h - H->hit_off[e];
+  }
+}
+
+// ------------------------------------------------------------------ Mini Doublets
+// Unit = (event, module); candidates = lower-sensor hits x upper-sensor hits (Sec. 1).
+template <bool FILL>
+__global__ void __launch_bounds__(512) k_md(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t nu = H->n_ev * G.nm;
+  WARP_LOOP(u, nu) {
+    const uint32_t lo_b = B.sen_off[2 * u], up_b = B.sen_off[2 * u + 1], up_e = B.sen_off[2 * u + 2];
+    const uint32_t n_lo = up_b - lo_b, n_up = up_e - up_b;
+    const uint32_t m = u % G.nm;
+    const float4 cst = G.modc[m];
+    const uint32_t base = FILL ? B.md_off[u] : 0u;
+    const uint32_t cnt = warp_join<FILL, NoPayload>(
+        n_lo, base, [&](uint32_t, uint32_t& b, uint32_t& c) { b = up_b; c = n_up; },
+        [&](uint32_t i, uint32_t j, NoPayload&) {
+          const PointTol a{B.hit4[lo_b + i], cst}, b{B.hit4[j], cst};
+          return pair_bend(C, a, b, cst.w) && pair_rz(C, a, b);
+        },
+        [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
+          B.md_unit[pos] = u;
+          B.md_lo4[pos] = B.hit4[lo_b + i];
+          B.md_up4[pos] = B.hit4[j];
+          B.md_cst[pos] = cst;
+          B.md_lo_idx[pos] = B.hit_idx[lo_b + i];
+          B.md_up_idx[pos] = B.hit_idx[j];
+        });
+    if (!FILL && lane_id() == 0) B.md_cnt[u] = cnt;
+  }
+}
+
+__device__ __forceinline__ PointTol md_point(const BufView& B, uint32_t m) { return PointTol{B.md_lo4[m], B.md_cst[m]}; }
+__device__ __forceinline__ PointTol md_upper(const BufView& B, uint32_t m) { return PointTol{B.md_up4[m], B.md_cst[m]}; }
+
+// ------------------------------------------------------------------ Line Segments
+// Unit = MD a on module A; candidates = MDs of every module B in the connection map of A.
+template <bool FILL>
+__global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_MD];
+  WARP_LOOP(a, n) {
+    const uint32_t unit = B.md_unit[a];
+    const uint32_t ev = unit / G.nm, A = unit - ev * G.nm;
+    const PointTol pa = md_point(B, a), pau = md_upper(B, a);
+    const float rnext = G.rnext[A];
+    const bool a_barrel = G.subdet[A] == 0;
+    const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
+    const uint32_t base = FILL ? B.ls_off[a] : 0u;
+    const uint32_t ubase = ev * G.nm;
+    const uint32_t cnt = warp_join<FILL, NoPayload>(
+        nb, base,
+        [&](uint32_t i, uint32_t& b, uint32_t& c) {
+          const uint32_t u = ubase + G.conn[nb0 + i];
+          b = B.md_off[u];
+          c = B.md_off[u + 1] - b;
+        },
+        [&](uint32_t, uint32_t j, NoPayload&) {
+          const uint32_t Bm = B.md_unit[j] - ubase;
+          const bool b2d = a_barrel && G.subdet[Bm] == 1;
+          return ls_select(C, pa, pau, md_point(B, j), md_upper(B, j), rnext, b2d, G.zb_half);
+        },
+        [&](uint32_t pos, uint32_t, uint32_t j, const NoPayload&) {
+          B.ls_in[pos] = a;
+          B.ls_out[pos] = j;
+        });
+    if (!FILL && lane_id() == 0) B.ls_cnt[a] = cnt;
+  }
+}
+
+// ------------------------------------------------------------------ T3
+// Unit = MD a; candidates = LS (a -> b) x LS (b -> c).
+template <bool FILL>
+__global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_MD];
+  WARP_LOOP(a, n) {
+    const PointTol pa = md_point(B, a);
+    const uint32_t l0 = B.ls_off[a], nl = B.ls_off[a + 1] - l0;
+    const uint32_t base = FILL ? B.t3_off[a] : 0u;
+    const uint32_t cnt = warp_join<FILL, NoPayload>(
+        nl, base,
+        [&](uint32_t i, uint32_t& b, uint32_t& c) {
+          const uint32_t mb = B.ls_out[l0 + i];
+          b = B.ls_off[mb];
+          c = B.ls_off[mb + 1] - b;
+        },
+        [&](uint32_t i, uint32_t j, NoPayload&) {
+          const uint32_t mb = B.ls_out[l0 + i], mc = B.ls_out[j];
+          return t3_select(C, pa, md_point(B, mb), md_upper(B, mb), md_point(B, mc));
+        },
+        [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
+          B.t3_a[pos] = a;
+          B.t3_b[pos] = B.ls_out[l0 + i];
+          B.t3_c[pos] = B.ls_out[j];
+        });
+    if (!FILL && lane_id() == 0) B.t3_cnt[a] = cnt;
+  }
+}
+
+// ------------------------------------------------------------------ T5
+// Unit = MD a; candidates = T3 (a, b, c) x T3 (c, d, e).
+template <bool FILL>
+__global__ void __launch_bounds__(512) k_t5(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_MD];
+  WARP_LOOP(a, n) {
+    const PointTol pa = md_point(B, a);
+    const uint32_t s0 = B.t3_off[a], ns = B.t3_off[a + 1] - s0;
+    const uint32_t base = FILL ? B.t5_off[a] : 0u;
+    const uint32_t cnt = warp_join<FILL, ScorePayload>(
+        ns, base,
+        [&](uint32_t i, uint32_t& b, uint32_t& c) {
+          const uint32_t mc = B.t3_c[s0 + i];
+          b = B.t3_off[mc];
+          c = B.t3_off[mc + 1] - b;
+        },
+        [&](uint32_t i, uint32_t j, ScorePayload& pl) {
+          const uint32_t mb = B.t3_b[s0 + i], mc = B.t3_c[s0 + i], md = B.t3_b[j], me = B.t3_c[j];
+          return t5_select(C, pa, md_point(B, mb), md_point(B, mc), md_point(B, md), md_point(B, me), pl.score,
+                           pl.kfull);
+        },
+        [&](uint32_t pos, uint32_t i, uint32_t j, const ScorePayload& pl) {
+          B.t5_m0[pos] = a;
+          B.t5_m1[pos] = B.t3_b[s0 + i];
+          B.t5_m2[pos] = B.t3_c[s0 + i];
+          B.t5_m3[pos] = B.t3_b[j];
+          B.t5_m4[pos] = B.t3_c[j];
+          B.t5_score[pos] = pl.score;
+          B.t5_kfull[pos] = pl.kfull;
+        });
+    if (!FILL && lane_id() == 0) B.t5_cnt[a] = cnt;
+  }
+}
+
+// ------------------------------------------------------------------ pLS module lookup
+__device__ __forceinline__ void add_cand(uint32_t* list, uint32_t& n, uint32_t id) {
+  if (id == NONE) return;
+  for (uint32_t i = 0; i < n; i++)
+    if (list[i] == id) return;
+  list[n++] = id;
+}
+
+__device__ int find_sector(const GeoView& G, uint32_t row, float px, float py) {
+  const uint32_t nphi = G.row_nphi[row], base = G.row_mod_base[row];
+  for (uint32_t k = 0; k < nphi; k++) {
+    const uint32_t id = G.row_mods[base + k];
+    if (id == NONE) continue;
+    const float4 e = G.mod_e[id];
+    const float c0 = e.x * py - e.y * px;
+    const float c1 = e.z * py - e.w * px;
+    if (c0 >= 0.0f && c1 < 0.0f) return (int)k;
+  }
+  return -1;
+}
+
+__device__ void add_row_cands(const GeoView& G, int s, int row, float px, float py, uint32_t* list, uint32_t& n) {
+  if (row < 0 || (uint32_t)row >= G.surf_nrows[s]) return;
+  const uint32_t r = G.surf_row_base[s] + (uint32_t)row;
+  if (G.row_nphi[r] == 0) return;
+  const int k = find_sector(G, r, px, py);
+  if (k < 0) return;
+  const int nphi = (int)G.row_nphi[r];
+  for (int d = -1; d <= 1; d++) {
+    const int kk = ((k + d) % nphi + nphi) % nphi;
+    add_cand(list, n, G.row_mods[G.row_mod_base[r] + kk]);
+  }
+}
+
+__device__ __forceinline__ uint32_t row0_module(const GeoView& G, int s) {
+  if (G.surf_nrows[s] == 0) return NONE;
+  const uint32_t r = G.surf_row_base[s];
+  if (G.row_nphi[r] == 0) return NONE;
+  return G.row_mods[G.row_mod_base[r]];
+}
+
+// Unit = pLS: helix parameters, then the modules of barrel layers 1-2 and disks 1-2 its
+// helix crosses first, each with its +-1 neighbours (Sec. 1: pLSs join T3s and T5s).
+__global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
+  Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->n_pls;
+  THREAD_LOOP(p, n) {
+    const PlsIn s = H->pls[p];
+    B.pls_ev[p] = find_slot(H->pls_off, H->n_ev, p);
+    bool bad = !(isfinite(s.px) && isfinite(s.py) && isfinite(s.pz) && isfinite(s.x0) && isfinite(s.y0) &&
+                 isfinite(s.z0)) ||
+               (s.charge != 1 && s.charge != -1);
+    PlsHelix h;
+    h.pt = sqrtf(s.px * s.px + s.py * s.py);
+    if (!(h.pt > 0.0f)) bad = true;
+    if (bad) {
+      atomicOr(&H->err, ERR_BAD_INPUT);
+      B.pls_ncand[p] = 0;
+      continue;
+    }
+    h.R = h.pt / C.KB;
+    const float ux = s.px / h.pt;
+    const float uy = s.py / h.pt;
+    h.q = (float)s.charge;
+    const float qR = h.q * h.R;
+    h.x0 = s.x0; h.y0 = s.y0; h.z0 = s.z0;
+    h.cx = s.x0 + qR * uy;
+    h.cy = s.y0 - qR * ux;
+    h.cot = s.pz / h.pt;
+    B.pls_h0[p] = make_float4(h.x0, h.y0, h.z0, h.R);
+    B.pls_h1[p] = make_float4(h.cx, h.cy, h.cot, h.q);
+    B.pls_pt[p] = h.pt;
+    uint32_t list[MAX_CAND];
+    uint32_t nc = 0;
+    for (int sf = 0; sf < 2; sf++) {
+      if (G.surf_nrows[sf] == 0) continue;
+      const float rl = G.mod_g[G.surf_first[sf]].x;
+      const float d2 = h.cx * h.cx + h.cy * h.cy;
+      const float d = sqrtf(d2);
+      const float a = (rl * rl - h.R * h.R + d2) / (2.0f * d);
+      const float h2 = rl * rl - a * a;
+      if (!(h2 >= 0.0f)) continue;
+      const float hh = sqrtf(h2);
+      const float ex = h.cx / d, ey = h.cy / d;
+      const float P1x = a * ex - hh * ey, P1y = a * ey + hh * ex;
+      const float P2x = a * ex + hh * ey, P2y = a * ey - hh * ex;
+      const float wx = h.x0 - h.cx, wy = h.y0 - h.cy;
+      const float cr1 = wx * (P1y - h.cy) - wy * (P1x - h.cx);
+      const float cr2 = wx * (P2y - h.cy) - wy * (P2x - h.cx);
+      const bool f1 = -h.q * cr1 > 0.0f;
+      const bool f2 = -h.q * cr2 > 0.0f;
+      const float dt1 = wx * (P1x - h.cx) + wy * (P1y - h.cy);
+      const float dt2 = wx * (P2x - h.cx) + wy * (P2y - h.cy);
+      float Px, Py;
+      if (f1 && f2) {
+        if (dt1 >= dt2) { Px = P1x; Py = P1y; } else { Px = P2x; Py = P2y; }
+      } else if (f1) {
+        Px = P1x; Py = P1y;
+      } else if (f2) {
+        Px = P2x; Py = P2y;
+      } else {
+        continue;
+      }
+      const float dxc = Px - h.x0, dyc = Py - h.y0;
+      const float chord = sqrtf(dxc * dxc + dyc * dyc);
+      const float sarc = arc_length(chord, h.R);
+      const float zP = h.z0 + sarc * h.cot;
+      const uint32_t m0 = row0_module(G, sf);
+      if (m0 == NONE) continue;
+      const float4 g0 = G.mod_g[m0];
+      const float zlen = g0.w - g0.z;
+      const float zhi = g0.z + (float)G.surf_nrows[sf] * zlen;
+      if (!(zP > g0.z - 2.0f * zlen && zP < zhi + 2.0f * zlen)) continue;
+      const int iz = (int)floorf((zP - g0.z) / zlen);
+      for (int dz = -1; dz <= 1; dz++) add_row_cands(G, sf, iz + dz, Px, Py, list, nc);
+    }
+    if (h.cot != 0.0f) {
+      const int side0 = h.cot > 0.0f ? 11 : 6;
+      for (int di = 0; di < 2; di++) {
+        const int sf = side0 + di;
+        const uint32_t m0 = row0_module(G, sf);
+        if (m0 == NONE) continue;
+        const float4 g0 = G.mod_g[m0];
+        const float zd = g0.x;
+        const float sarc = (zd - h.z0) / h.cot;
+        if (!(sarc > 0.0f)) continue;
+        const float alpha = sarc / h.R;
+        if (!(alpha < C.PI)) continue;
+        float sa, ca;
+        sin_cos_series(alpha, sa, ca);
+        const float sn = -h.q * sa;
+        const float wx = h.x0 - h.cx, wy = h.y0 - h.cy;
+        const float Px = h.cx + (wx * ca - wy * sn);
+        const float Py = h.cy + (wx * sn + wy * ca);
+        const float rP = sqrtf(Px * Px + Py * Py);
+        const float rlen = g0.w - g0.z;
+        const float rhi = g0.z + (float)G.surf_nrows[sf] * rlen;
+        if (!(rP > g0.z - 2.0f * rlen && rP < rhi + 2.0f * rlen)) continue;
+        const int ir = (int)floorf((rP - g0.z) / rlen);
+        for (int dr = -1; dr <= 1; dr++) add_row_cands(G, sf, ir + dr, Px, Py, list, nc);
+      }
+    }
+    for (uint32_t i = 1; i < nc; i++) {  // ascending module id
+      const uint32_t v = list[i];
+      uint32_t k = i;
+      while (k > 0 && list[k - 1] > v) {
+        list[k] = list[k - 1];
+        k--;
+      }
+      list[k] = v;
+    }
+    B.pls_ncand[p] = nc;
+    for (uint32_t i = 0; i < nc; i++) B.pls_cand[(size_t)p * MAX_CAND + i] = list[i];
+  }
+}
+
+__device__ __forceinline__ PlsHelix load_helix(const BufView& B, uint32_t p) {
+  const float4 a = B.pls_h0[p], b = B.pls_h1[p];
+  PlsHelix h;
+  h.x0 = a.x; h.y0 = a.y; h.z0 = a.z; h.R = a.w;
+  h.cx = b.x; h.cy = b.y; h.cot = b.z; h.q = b.w;
+  h.pt = B.pls_pt[p];
+  return h;
+}
+
+// ------------------------------------------------------------------ pT3 / pT5
+// Unit = pLS p; candidates = T3s (T5s) whose first MD sits on one of p's candidate modules.
+template <bool FILL>
+__global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->n_pls;
+  WARP_LOOP(p, n) {
+    const PlsHelix h = load_helix(B, p);
+    const uint32_t ubase = B.pls_ev[p] * G.nm;
+    const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
+    const uint32_t base = FILL ? B.pt3_off[p] : 0u;
+    const uint32_t cnt = warp_join<FILL, ScorePayload>(
+        B.pls_ncand[p], base,
+        [&](uint32_t i, uint32_t& b, uint32_t& c) {
+          const uint32_t u = ubase + cand[i];
+          b = B.t3_off[B.md_off[u]];
+          c = B.t3_off[B.md_off[u + 1]] - b;
+        },
+        [&](uint32_t, uint32_t t, ScorePayload& pl) {
+          float score = 0.0f;
+          bool ok = true;
+          ok &= pls_anchor(C, h, md_point(B, B.t3_a[t]), score);
+          ok &= pls_anchor(C, h, md_point(B, B.t3_b[t]), score);
+          ok &= pls_anchor(C, h, md_point(B, B.t3_c[t]), score);
+          pl.score = score;
+          return ok;
+        },
+        [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
+          B.pt3_pls[pos] = p;
+          B.pt3_obj[pos] = t;
+          B.pt3_score[pos] = pl.score;
+        });
+    if (!FILL && lane_id() == 0) B.pt3_cnt[p] = cnt;
+  }
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->n_pls;
+  WARP_LOOP(p, n) {
+    const PlsHelix h = load_helix(B, p);
+    const uint32_t ubase = B.pls_ev[p] * G.nm;
+    const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
+    const uint32_t base = FILL ? B.pt5_off[p] : 0u;
+    const uint32_t cnt = warp_join<FILL, ScorePayload>(
+        B.pls_ncand[p], base,
+        [&](uint32_t i, uint32_t& b, uint32_t& c) {
+          const uint32_t u = ubase + cand[i];
+          b = B.t5_off[B.md_off[u]];
+          c = B.t5_off[B.md_off[u + 1]] - b;
+        },
+        [&](uint32_t, uint32_t t, ScorePayload& pl) {
+          const PointTol P0 = md_point(B, B.t5_m0[t]), P1 = md_point(B, B.t5_m1[t]), P2 = md_point(B, B.t5_m2[t]),
+                         P3 = md_point(B, B.t5_m3[t]), P4 = md_point(B, B.t5_m4[t]);
+          float score = 0.0f;
+          bool ok = true;
+          ok &= pls_anchor(C, h, P0, score);
+          ok &= pls_anchor(C, h, P1, score);
+          ok &= pls_anchor(C, h, P2, score);
+          ok &= pls_anchor(C, h, P3, score);
+          ok &= pls_anchor(C, h, P4, score);
+          const float kf = B.t5_kfull[t];
+          const Circle3 fu = circle3(P0, P2, P4);
+          const bool c5 = fabsf(fabsf(kf) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
+          pl.score = score;
+          return ok && c5;
+        },
+        [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
+          B.pt5_pls[pos] = p;
+          B.pt5_obj[pos] = t;
+          B.pt5_score[pos] = pl.score;
+        });
+    if (!FILL && lane_id() == 0) B.pt5_cnt[p] = cnt;
+  }
+}
+
+// ------------------------------------------------------------------ duplicate removal
+__device__ __forceinline__ void t5_mds(const BufView& B, uint32_t t, uint32_t m[5]) {
+  m[0] = B.t5_m0[t]; m[1] = B.t5_m1[t]; m[2] = B.t5_m2[t]; m[3] = B.t5_m3[t]; m[4] = B.t5_m4[t];
+}
+__device__ __forceinline__ void t3_mds(const BufView& B, uint32_t t, uint32_t m[3]) {
+  m[0] = B.t3_a[t]; m[1] = B.t3_b[t]; m[2] = B.t3_c[t];
+}
+template <int NA, int NB>
+__device__ __forceinline__ int shared_mds(const uint32_t (&a)[NA], const uint32_t (&b)[NB]) {
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < NA; i++)
+#pragma unroll
+    for (int j = 0; j < NB; j++) c += a[i] == b[j];
+  return c;
+}
+__device__ __forceinline__ bool better(float sy, uint32_t y, float sx, uint32_t x) {
+  return sy < sx || (sy == sx && y < x);
+}
+
+// MD -> object lists for pT5 (5 MDs each), pT3 (3) and T5 (5).
+__global__ void k_csr_count(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n5 = H->tot[T_PT5], n3 = H->tot[T_PT3], nt = H->tot[T_T5];
+  THREAD_LOOP(i, n5 + n3 + nt) {
+    if (i < n5) {
+      uint32_t m[5];
+      t5_mds(B, B.pt5_obj[i], m);
+      for (int k = 0; k < 5; k++) atomicAdd(&B.c5_cnt[m[k]], 1u);
+    } else if (i < n5 + n3) {
+      uint32_t m[3];
+      t3_mds(B, B.pt3_obj[i - n5], m);
+      for (int k = 0; k < 3; k++) atomicAdd(&B.c3_cnt[m[k]], 1u);
+    } else {
+      uint32_t m[5];
+      t5_mds(B, i - n5 - n3, m);
+      for (int k = 0; k < 5; k++) atomicAdd(&B.ct_cnt[m[k]], 1u);
+    }
+  }
+}
+
+__global__ void k_csr_fill(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n5 = H->tot[T_PT5], n3 = H->tot[T_PT3], nt = H->tot[T_T5];
+  THREAD_LOOP(i, n5 + n3 + nt) {
+    if (i < n5) {
+      uint32_t m[5];
+      t5_mds(B, B.pt5_obj[i], m);
+      for (int k = 0; k < 5; k++) B.c5_list[B.c5_off[m[k]] + atomicSub(&B.c5_cnt[m[k]], 1u) - 1u] = i;
+    } else if (i < n5 + n3) {
+      uint32_t m[3];
+      t3_mds(B, B.pt3_obj[i - n5], m);
+      for (int k = 0; k < 3; k++) B.c3_list[B.c3_off[m[k]] + atomicSub(&B.c3_cnt[m[k]], 1u) - 1u] = i - n5;
+    } else {
+      uint32_t m[5];
+      const uint32_t x = i - n5 - n3;
+      t5_mds(B, x, m);
+      for (int k = 0; k < 5; k++) B.ct_list[B.ct_off[m[k]] + atomicSub(&B.ct_cnt[m[k]], 1u) - 1u] = x;
+    }
+  }
+}
+
+// pT5 stage: dies iff a better pT5 shares its pLS or >= 3 MDs.
+__global__ void k_kill_pt5(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_PT5];
+  THREAD_LOOP(x, n) {
+    const uint32_t p = B.pt5_pls[x];
+    const float sx = B.pt5_score[x];
+    bool dead = false;
+    for (uint32_t y = B.pt5_off[p]; y < B.pt5_off[p + 1] && !dead; y++)
+      if (y != x && better(B.pt5_score[y], y, sx, x)) dead = true;
+    uint32_t mx[5];
+    t5_mds(B, B.pt5_obj[x], mx);
+    for (int k = 0; k < 5 && !dead; k++) {
+      const uint32_t m = mx[k];
+      for (uint32_t j = B.c5_off[m]; j < B.c5_off[m + 1] && !dead; j++) {
+        const uint32_t y = B.c5_list[j];
+        if (y == x) continue;
+        uint32_t my[5];
+        t5_mds(B, B.pt5_obj[y], my);
+        if (shared_mds(mx, my) >= 3 && better(B.pt5_score[y], y, sx, x)) dead = true;
+      }
+    }
+    B.alive5[x] = dead ? 0u : 1u;
+  }
+}
+
+__global__ void k_used5(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(p, H->n_pls) {
+    uint32_t u = 0;
+    for (uint32_t y = B.pt5_off[p]; y < B.pt5_off[p + 1]; y++) u |= B.alive5[y];
+    B.used5[p] = u;
+  }
+}
+
+// pT3 across stages: its pLS is used by a surviving pT5, or it shares >= 2 MDs with one.
+__global__ void k_cross_pt3(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(x, H->tot[T_PT3]) {
+    bool dead = B.used5[B.pt3_pls[x]] != 0;
+    uint32_t mx[3];
+    t3_mds(B, B.pt3_obj[x], mx);
+    for (int k = 0; k < 3 && !dead; k++) {
+      const uint32_t m = mx[k];
+      for (uint32_t j = B.c5_off[m]; j < B.c5_off[m + 1] && !dead; j++) {
+        const uint32_t z = B.c5_list[j];
+        if (!B.alive5[z]) continue;
+        uint32_t mz[5];
+        t5_mds(B, B.pt5_obj[z], mz);
+        if (shared_mds(mx, mz) >= 2) dead = true;
+      }
+    }
+    B.cross3[x] = dead ? 1u : 0u;
+  }
+}
+
+// pT3 stage among those left: dies iff a better one shares its pLS or >= 2 MDs.
+__global__ void k_kill_pt3(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(x, H->tot[T_PT3]) {
+    bool dead = B.cross3[x] != 0;
+    const uint32_t p = B.pt3_pls[x];
+    const float sx = B.pt3_score[x];
+    for (uint32_t y = B.pt3_off[p]; y < B.pt3_off[p + 1] && !dead; y++)
+      if (y != x && !B.cross3[y] && better(B.pt3_score[y], y, sx, x)) dead = true;
+    uint32_t mx[3];
+    t3_mds(B, B.pt3_obj[x], mx);
+    for (int k = 0; k < 3 && !dead; k++) {
+      const uint32_t m = mx[k];
+      for (uint32_t j = B.c3_off[m]; j < B.c3_off[m + 1] && !dead; j++) {
+        const uint32_t y = B.c3_list[j];
+        if (y == x || B.cross3[y]) continue;
+        uint32_t my[3];
+        t3_mds(B, B.pt3_obj[y], my);
+        if (shared_mds(mx, my) >= 2 && better(B.pt3_score[y], y, sx, x)) dead = true;
+      }
+    }
+    B.alive3[x] = dead ? 0u : 1u;
+  }
+}
+
+__global__ void k_used3(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(p, H->n_pls) {
+    uint32_t u = 0;
+    for (uint32_t y = B.pt3_off[p]; y < B.pt3_off[p + 1]; y++) u |= B.alive3[y];
+    B.used3[p] = u;
+    B.plstc[p] = (u | B.used5[p]) ? 0u : 1u;
+  }
+}
+
+// T5 across stages: shares >= 3 MDs with a surviving pT5 or pT3.
+__global__ void k_cross_t5(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(x, H->tot[T_T5]) {
+    bool dead = false;
+    uint32_t mx[5];
+    t5_mds(B, x, mx);
+    for (int k = 0; k < 5 && !dead; k++) {
+      const uint32_t m = mx[k];
+      for (uint32_t j = B.c5_off[m]; j < B.c5_off[m + 1] && !dead; j++) {
+        const uint32_t z = B.c5_list[j];
+        if (!B.alive5[z]) continue;
+        uint32_t mz[5];
+        t5_mds(B, B.pt5_obj[z], mz);
+        if (shared_mds(mx, mz) >= 3) dead = true;
+      }
+      for (uint32_t j = B.c3_off[m]; j < B.c3_off[m + 1] && !dead; j++) {
+        const uint32_t z = B.c3_list[j];
+        if (!B.alive3[z]) continue;
+        uint32_t mz[3];
+        t3_mds(B, B.pt3_obj[z], mz);
+        if (shared_mds(mx, mz) >= 3) dead = true;
+      }
+    }
+    B.crosst[x] = dead ? 1u : 0u;
+  }
+}
+
+__global__ void k_kill_t5(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(x, H->tot[T_T5]) {
+    bool dead = B.crosst[x] != 0;
+    const float sx = B.t5_score[x];
+    uint32_t mx[5];
+    t5_mds(B, x, mx);
+    for (int k = 0; k < 5 && !dead; k++) {
+      const uint32_t m = mx[k];
+      for (uint32_t j = B.ct_off[m]; j < B.ct_off[m + 1] && !dead; j++) {
+        const uint32_t y = B.ct_list[j];
+        if (y == x || B.crosst[y]) continue;
+        uint32_t my[5];
+        t5_mds(B, y, my);
+        if (shared_mds(mx, my) >= 3 && better(B.t5_score[y], y, sx, x)) dead = true;
+      }
+    }
+    B.alivet[x] = dead ? 0u : 1u;
+  }
+}
+
+// ------------------------------------------------------------------ track candidates
+struct EvCounts {
+  uint32_t n5, n3, nt, np, b5, b3, bt, bp;  // counts and first object index of the event
+};
+
+__device__ __forceinline__ EvCounts ev_counts(const GeoView& G, const BufView& B, const Hdr* H, uint32_t e) {
+  EvCounts c;
+  const uint32_t p0 = H->pls_off[e], p1 = H->pls_off[e + 1];
+  c.b5 = B.pt5_off[p0];
+  c.n5 = B.sa5[B.pt5_off[p1]] - B.sa5[c.b5];
+  c.b3 = B.pt3_off[p0];
+  c.n3 = B.sa3[B.pt3_off[p1]] - B.sa3[c.b3];
+  const uint32_t m0 = B.md_off[e * G.nm], m1 = B.md_off[(e + 1) * G.nm];
+  c.bt = B.t5_off[m0];
+  c.nt = B.sat[B.t5_off[m1]] - B.sat[c.bt];
+  c.bp = p0;
+  c.np = B.sap[p1] - B.sap[p0];
+  return c;
+}
+
+__global__ void k_tc_offsets(GeoView G, BufView B) {
+  Hdr* H = B.hdr;
+  if (H->err) return;
+  __shared__ uint32_t sm[33];
+  const uint32_t ne = H->n_ev;
+  uint32_t carry = 0;
+  for (uint32_t e0 = 0; e0 < ne; e0 += blockDim.x) {
+    const uint32_t e = e0 + threadIdx.x;
+    uint32_t v = 0;
+    if (e < ne) {
+      const EvCounts c = ev_counts(G, B, H, e);
+      v = c.n5 + c.n3 + c.nt + c.np;
+    }
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(v, sm, tot);
+    if (e < ne) B.tc_ev_off[e] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    B.tc_ev_off[ne] = carry;
+    H->tot[T_TC] = carry;
+    if (carry > B.cap_tc) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + T_TC));
+  }
+}
+
+__device__ __forceinline__ void write_tc(lst_tc* tc, uint8_t type, uint32_t obj, uint32_t pls, const uint32_t* mds,
+                                         int nmd, const BufView& B, float pt, float score) {
+  lst_tc r;
+  r.type = type;
+  r.n_ot = (uint8_t)(2 * nmd);
+  r.n_pix = pls != NONE ? 4 : 0;
+  r.pad = 0;
+  r.obj = obj;
+  r.pls = pls;
+  for (int k = 0; k < 10; k++) r.ot[k] = NONE;
+  for (int k = 0; k < nmd; k++) {
+    r.ot[2 * k] = B.md_lo_idx[mds[k]];
+    r.ot[2 * k + 1] = B.md_up_idx[mds[k]];
+  }
+  for (int k = 0; k < 4; k++) r.pix[k] = pls != NONE ? 4 * pls + (uint32_t)k : NONE;
+  r.pt = pt;
+  r.score = score;
+  *tc = r;
+}
+
+// Survivors -> track candidates: per event pT5s, pT3s, T5s, then unused pLSs (Sec. 1 list).
+__global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n5 = H->tot[T_PT5], n3 = H->tot[T_PT3], nt = H->tot[T_T5], np = H->n_pls;
+  lst_tc* tc = (lst_tc*)B.tc;
+  THREAD_LOOP(i, n5 + n3 + nt + np) {
+    if (i < n5) {
+      const uint32_t x = i;
+      if (!B.alive5[x]) continue;
+      const uint32_t p = B.pt5_pls[x], e = B.pls_ev[p];
+      const EvCounts c = ev_counts(G, B, H, e);
+      const uint32_t pos = B.tc_ev_off[e] + (B.sa5[x] - B.sa5[c.b5]);
+      uint32_t m[5];
+      t5_mds(B, B.pt5_obj[x], m);
+      write_tc(tc + pos, LST_TC_PT5, x - c.b5, p - c.bp, m, 5, B, B.pls_pt[p], B.pt5_score[x]);
+    } else if (i < n5 + n3) {
+      const uint32_t x = i - n5;
+      if (!B.alive3[x]) continue;
+      const uint32_t p = B.pt3_pls[x], e = B.pls_ev[p];
+      const EvCounts c = ev_counts(G, B, H, e);
+      const uint32_t pos = B.tc_ev_off[e] + c.n5 + (B.sa3[x] - B.sa3[c.b3]);
+      uint32_t m[3];
+      t3_mds(B, B.pt3_obj[x], m);
+      write_tc(tc + pos, LST_TC_PT3, x - c.b3, p - c.bp, m, 3, B, B.pls_pt[p], B.pt3_score[x]);
+    } else if (i < n5 + n3 + nt) {
+      const uint32_t x = i - n5 - n3;
+      if (!B.alivet[x]) continue;
+      const uint32_t e = B.md_unit[B.t5_m0[x]] / G.nm;
+      const EvCounts c = ev_counts(G, B, H, e);
+      const uint32_t pos = B.tc_ev_off[e] + c.n5 + c.n3 + (B.sat[x] - B.sat[c.bt]);
+      uint32_t m[5];
+      t5_mds(B, x, m);
+      write_tc(tc + pos, LST_TC_T5, x - c.bt, NONE, m, 5, B, C.KB / fabsf(B.t5_kfull[x]), B.t5_score[x]);
+    } else {
+      const uint32_t p = i - n5 - n3 - nt;
+      if (!B.plstc[p]) continue;
+      const uint32_t e = B.pls_ev[p];
+      const EvCounts c = ev_counts(G, B, H, e);
+      const uint32_t pos = B.tc_ev_off[e] + c.n5 + c.n3 + c.nt + (B.sap[p] - B.sap[c.bp]);
+      write_tc(tc + pos, LST_TC_PLS, p - c.bp, p - c.bp, nullptr, 0, B, B.pls_pt[p], 0.0f);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host-side enqueue
+// Kernel names in launch order (profile mode records one CUDA event after each).
+const char* const kKernelNames[] = {
+    "zero_sensor_counts", "hits_count", "scan_reduce", "scan_top", "scan_apply", "hits_scatter", "hits_sort",
+    "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
+    "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "zero_md_lists", "md_lists_count", "md_lists_fill",
+    "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write"};
+const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
+
+struct Marker {
+  MarkFn fn;
+  void* arg;
+  int nk;
+  void operator()(int name) {
+    nk++;
+    if (fn) fn(arg, name);
+  }
+};
+
+static void scan(const BufView& B, const Launch& L, cudaStream_t s, const uint32_t* in, uint32_t* out,
+                 const uint32_t* nptr, uint32_t mul, int tot, uint32_t cap, Marker& mk) {
+  k_scan_reduce<<<L.scan_grid, 512, 0, s>>>(in, nptr, mul, B.hdr, B.scan_part);
+  mk(2);
+  k_scan_top<<<1, L.scan_grid, 0, s>>>(B.scan_part, nptr, mul, out, B.hdr, tot, cap);
+  mk(3);
+  k_scan_apply<<<L.scan_grid, 512, 0, s>>>(in, nptr, mul, B.hdr, B.scan_part, out);
+  mk(4);
+}
+
+// Enqueues the whole chain on stream s; returns the number of kernels launched.  mark (may
+// be null) is called after every launch with the index of its name in kKernelNames.
+int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
+                     MarkFn mark, void* arg) {
+  Marker mk{mark, arg, 0};
+  Hdr* H = B.hdr;
+  const uint32_t g = L.grid, bs = L.block;
+  const uint32_t two_nm = 2 * G.nm;
+  k_zero<<<g, 256, 0, s>>>(B.sen_cnt, &H->n_ev, two_nm, 1);
+  mk(0);
+  k_hits_count<<<g, 256, 0, s>>>(G, B);
+  mk(1);
+  scan(B, L, s, B.sen_cnt, B.sen_off, &H->n_ev, two_nm, T_HITS, 0xFFFFFFFFu, mk);
+  k_hits_scatter<<<g, 256, 0, s>>>(G, B);
+  mk(5);
+  k_hits_sort<<<g, 256, 0, s>>>(G, B);
+  mk(6);
+  k_md<false><<<g, bs, 0, s>>>(C, G, B);
+  mk(7);
+  scan(B, L, s, B.md_cnt, B.md_off, &H->n_ev, G.nm, T_MD, B.cap_md, mk);
+  k_md<true><<<g, bs, 0, s>>>(C, G, B);
+  mk(8);
+  k_ls<false><<<g, bs, 0, s>>>(C, G, B);
+  mk(9);
+  scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
+  k_ls<true><<<g, bs, 0, s>>>(C, G, B);
+  mk(10);
+  k_t3<false><<<g, bs, 0, s>>>(C, G, B);
+  mk(11);
+  scan(B, L, s, B.t3_cnt, B.t3_off, &H->tot[T_MD], 1, T_T3, B.cap_t3, mk);
+  k_t3<true><<<g, bs, 0, s>>>(C, G, B);
+  mk(12);
+  k_t5<false><<<g, bs, 0, s>>>(C, G, B);
+  mk(13);
+  scan(B, L, s, B.t5_cnt, B.t5_off, &H->tot[T_MD], 1, T_T5, B.cap_t5, mk);
+  k_t5<true><<<g, bs, 0, s>>>(C, G, B);
+  mk(14);
+  k_pls_prep<<<g, 128, 0, s>>>(C, G, B);
+  mk(15);
+  k_pt3<false><<<g, bs, 0, s>>>(C, G, B);
+  mk(16);
+  scan(B, L, s, B.pt3_cnt, B.pt3_off, &H->n_pls, 1, T_PT3, B.cap_pt3, mk);
+  k_pt3<true><<<g, bs, 0, s>>>(C, G, B);
+  mk(17);
+  k_pt5<false><<<g, bs, 0, s>>>(C, G, B);
+  mk(18);
+  scan(B, L, s, B.pt5_cnt, B.pt5_off, &H->n_pls, 1, T_PT5, B.cap_pt5, mk);
+  k_pt5<true><<<g, bs, 0, s>>>(C, G, B);
+  mk(19);
+  k_zero3<<<g, 256, 0, s>>>(B.c5_cnt, B.c3_cnt, B.ct_cnt, H);
+  mk(20);
+  k_csr_count<<<g, 256, 0, s>>>(B);
+  mk(21);
+  scan(B, L, s, B.c5_cnt, B.c5_off, &H->tot[T_MD], 1, T_C5, 5u * B.cap_pt5, mk);
+  scan(B, L, s, B.c3_cnt, B.c3_off, &H->tot[T_MD], 1, T_C3, 3u * B.cap_pt3, mk);
+  scan(B, L, s, B.ct_cnt, B.ct_off, &H->tot[T_MD], 1, T_CT, 5u * B.cap_t5, mk);
+  k_csr_fill<<<g, 256, 0, s>>>(B);
+  mk(22);
+  k_kill_pt5<<<g, 256, 0, s>>>(B);
+  mk(23);
+  k_used5<<<g, 256, 0, s>>>(B);
+  mk(24);
+  k_cross_pt3<<<g, 256, 0, s>>>(B);
+  mk(25);
+  k_kill_pt3<<<g, 256, 0, s>>>(B);
+  mk(26);
+  k_used3<<<g, 256, 0, s>>>(B);
+  mk(27);
+  k_cross_t5<<<g, 256, 0, s>>>(B);
+  mk(28);
+  k_kill_t5<<<g, 256, 0, s>>>(B);
+  mk(29);
+  scan(B, L, s, B.alive5, B.sa5, &H->tot[T_PT5], 1, T_A5, 0xFFFFFFFFu, mk);
+  scan(B, L, s, B.alive3, B.sa3, &H->tot[T_PT3], 1, T_A3, 0xFFFFFFFFu, mk);
+  scan(B, L, s, B.alivet, B.sat, &H->tot[T_T5], 1, T_AT, 0xFFFFFFFFu, mk);
+  scan(B, L, s, B.plstc, B.sap, &H->n_pls, 1, T_AP, 0xFFFFFFFFu, mk);
+  k_tc_offsets<<<1, 1024, 0, s>>>(G, B);
+  mk(30);
+  k_tc_write<<<g, 256, 0, s>>>(C, G, B);
+  mk(31);
+  return mk.nk;
+}
+
+}  // namespace lst

@@ -1,0 +1,243 @@
+"""GPU parity: every object list of the CUDA path equals the oracle's element by element.
+
+Integer fields (hit, MD, object indices, flags) must be identical; float fields (scores,
+curvatures, pT) must be identical bit for bit -- the cut arithmetic is IEEE binary32 with
+one fixed evaluation order on both sides and no contraction, so the tolerance is zero.
+Object order is canonical on both sides (sorted by first MD, then candidate order).
+"""
+import numpy as np
+import pytest
+
+import lst_synth as S
+import oracle
+import paper_2407_18231_gb300 as lst
+from lst_synth import events as E
+
+pytestmark = pytest.mark.gpu
+
+
+def _bits(a):
+    return np.ascontiguousarray(a, np.float32).view(np.uint32)
+
+
+def compare(sess, rid, ora, ev, label=""):
+    md = sess.objects(rid, lst.OBJ_MD)
+    assert len(md) == len(ora["md"]), f"{label} MD count {len(md)} vs {len(ora['md'])}"
+    assert np.array_equal(np.stack([md["module"], md["lo"], md["up"]], 1), ora["md"]), label
+    ls = sess.objects(rid, lst.OBJ_LS)
+    assert len(ls) == len(ora["ls"]), f"{label} LS count {len(ls)} vs {len(ora['ls'])}"
+    assert np.array_equal(ls["md"], ora["ls"]), label
+    t3 = sess.objects(rid, lst.OBJ_T3)
+    assert len(t3) == len(ora["t3"]), f"{label} T3 count {len(t3)} vs {len(ora['t3'])}"
+    assert np.array_equal(t3["md"], ora["t3"]), label
+    t5 = sess.objects(rid, lst.OBJ_T5)
+    assert len(t5) == len(ora["t5"]), f"{label} T5 count {len(t5)} vs {len(ora['t5'])}"
+    assert np.array_equal(t5["md"], ora["t5"]), label
+    assert np.array_equal(_bits(t5["score"]), _bits(ora["t5_score"])), label
+    assert np.array_equal(_bits(t5["kfull"]), _bits(ora["t5_kfull"])), label
+    assert np.array_equal(t5["alive"], ora["alive_t5"]), label
+    pl = sess.objects(rid, lst.OBJ_PLS)
+    assert len(pl) == ev.n_pls
+    assert np.array_equal(pl["n_cand"], ora["pls_cand_n"]), label
+    for p in range(ev.n_pls):
+        n = ora["pls_cand_n"][p]
+        assert np.array_equal(pl["cand"][p][:n], ora["pls_cand"][p][:n]), (label, p)
+    assert np.array_equal(pl["is_tc"], ora["pls_tc"]), label
+    for kind, key in ((lst.OBJ_PT3, "pt3"), (lst.OBJ_PT5, "pt5")):
+        o = sess.objects(rid, kind)
+        assert len(o) == len(ora[key]), f"{label} {key} count {len(o)} vs {len(ora[key])}"
+        assert np.array_equal(np.stack([o["pls"], o["obj"]], 1), ora[key]), label
+        assert np.array_equal(_bits(o["score"]), _bits(ora[key + "_score"])), label
+        assert np.array_equal(o["alive"], ora["alive_" + key]), label
+    tc = sess.candidates(rid)
+    assert len(tc) == len(ora["tc_type"]), f"{label} TC count {len(tc)} vs {len(ora['tc_type'])}"
+    assert np.array_equal(tc["type"], ora["tc_type"]), label
+    assert np.array_equal(tc["obj"], ora["tc_obj"]), label
+    assert np.array_equal(tc["pls"], ora["tc_pls"]), label
+    assert np.array_equal(tc["ot"], ora["tc_ot"]), label
+    assert np.array_equal(tc["pix"], ora["tc_pix"]), label
+    assert np.array_equal(_bits(tc["pt"]), _bits(ora["tc_pt"])), label
+    assert np.array_equal(_bits(tc["score"]), _bits(ora["tc_score"])), label
+    assert np.all(tc["n_ot"] == (tc["ot"] != lst.NONE).sum(1))
+
+
+@pytest.fixture(scope="module")
+def built():
+    lst.build()
+    return True
+
+
+@pytest.fixture(scope="module")
+def sess_barrel(built, barrel_geom):
+    return lst.Session(barrel_geom.modules, keep_objects=True)
+
+
+@pytest.fixture(scope="module")
+def sess_full(built, full_geom):
+    return lst.Session(full_geom.modules, keep_objects=True)
+
+
+def test_tiny_parity(sess_barrel, ora_barrel):
+    for pls in (False, True):
+        ev = S.make_event("tiny", with_pls=pls)
+        compare(sess_barrel, sess_barrel.run_event(ev), oracle.run(ora_barrel, ev), ev, f"tiny pls={pls}")
+
+
+@pytest.mark.parametrize("n_tracks", [1000, 4000])
+def test_pu200_parity(sess_full, ora_full, n_tracks):
+    ev = S.make_event("pu200", 0, n_tracks=n_tracks, with_pls=True)
+    compare(sess_full, sess_full.run_event(ev), oracle.run(ora_full, ev), ev, f"pu200 {n_tracks}")
+
+
+def test_highocc_full_size_parity(sess_full, ora_full):
+    ev = S.make_event("highocc", 0)  # 12000 tracks, 30 % noise, pixel seeds
+    compare(sess_full, sess_full.run_event(ev), oracle.run(ora_full, ev), ev, "highocc")
+
+
+def test_batch_equals_oracle_per_event(sess_full, ora_full):
+    evs = [S.make_event("pu200", 1, n_tracks=300, with_pls=True),
+           E.Event(np.zeros(0, np.float32), np.zeros(0, np.float32), np.zeros(0, np.float32),
+                   np.zeros(0, np.uint32), np.zeros(0, np.int32), np.zeros(0, E.TRACK_DTYPE)),
+           S.make_event("serving", 2, n_tracks=2500, with_pls=True),
+           S.make_event("pu200", 3, n_tracks=50, with_pls=False),
+           S.make_event("highocc", 1, n_tracks=3000)]
+    ids = sess_full.run_batch(evs)
+    for i, (ev, rid) in enumerate(zip(evs, ids)):
+        compare(sess_full, rid, oracle.run(ora_full, ev), ev, f"batch event {i}")
+    # replaying the captured graph on the same batch gives the same answer
+    ids2 = sess_full.run_batch(evs)
+    for a, b in zip(ids, ids2):
+        assert sess_full.candidates(a).tobytes() == sess_full.candidates(b).tobytes()
+
+
+def test_bench_workload_sampled_parity(sess_full, ora_full):
+    # the benchmark's batch (PU200-like events with pixel seeds), 3 events checked in full
+    evs = [S.make_event("pu200", i, with_pls=True) for i in range(16)]
+    ids = sess_full.run_batch(evs)
+    for i in (0, 7, 15):
+        compare(sess_full, ids[i], oracle.run(ora_full, evs[i]), evs[i], f"bench event {i}")
+
+
+def test_batched_barrel_workload(sess_barrel, ora_barrel):
+    evs = [S.make_event("batched", i) for i in range(8)]  # 500-6000 tracks each
+    ids = sess_barrel.run_batch(evs)
+    for i in (0, 3, 7):
+        compare(sess_barrel, ids[i], oracle.run(ora_barrel, evs[i]), evs[i], f"batched {i}")
+
+
+def test_edge_cases(sess_full, ora_full, full_geom):
+    z = np.zeros(0, np.float32)
+    empty = E.Event(z, z, z, np.zeros(0, np.uint32), np.zeros(0, np.int32), np.zeros(0, E.TRACK_DTYPE))
+    compare(sess_full, sess_full.run_event(empty), oracle.run(ora_full, empty), empty, "empty")
+    one = S.make_event("pu200", 5, n_tracks=1)
+    compare(sess_full, sess_full.run_event(one), oracle.run(ora_full, one), one, "one track")
+    seeds_only = S.make_event("pu200", 6, n_tracks=200, with_pls=True)
+    seeds_only = E.Event(z, z, z, np.zeros(0, np.uint32), np.zeros(0, np.int32), seeds_only.tracks,
+                         seeds_only.pls, seeds_only.pls_sim)
+    r = sess_full.run_event(seeds_only)
+    compare(sess_full, r, oracle.run(ora_full, seeds_only), seeds_only, "seeds only")
+    assert np.all(sess_full.candidates(r)["type"] == lst.TC_PLS)
+
+
+def test_bad_input_is_rejected_and_context_survives(sess_full, ora_full):
+    ev = S.make_event("pu200", 7, n_tracks=100)
+    bad = E.Event(ev.x.copy(), ev.y, ev.z, ev.det.copy(), ev.sim, ev.tracks)
+    bad.det[3] = 2 * len(S.geometry(False).modules)  # module id out of range
+    with pytest.raises(lst.LstError) as e:
+        sess_full.run_event(bad)
+    assert e.value.status == -2
+    nan = E.Event(ev.x.copy(), ev.y, ev.z, ev.det, ev.sim, ev.tracks)
+    nan.x[5] = np.nan
+    with pytest.raises(lst.LstError) as e:
+        sess_full.run_event(nan)
+    assert e.value.status == -2
+    compare(sess_full, sess_full.run_event(ev), oracle.run(ora_full, ev), ev, "after errors")
+
+
+def test_buffer_too_small_and_release(sess_full):
+    ev = S.make_event("pu200", 8, n_tracks=200)
+    rid = sess_full.run_event(ev)
+    L = lst.load_library()
+    import ctypes as C
+    n = C.c_uint32()
+    assert L.lst_get_candidates(sess_full.ctx, rid, None, 0, C.byref(n)) == 0 and n.value > 1
+    buf = np.zeros(1, lst.TC_DTYPE)
+    assert L.lst_get_candidates(sess_full.ctx, rid, buf.ctypes.data, 1, C.byref(n)) == -8
+    sess_full.release(rid)
+    assert L.lst_get_candidates(sess_full.ctx, rid, None, 0, C.byref(n)) == -9
+
+
+def test_overflow_rerun_keeps_results(built, full_geom, ora_full):
+    # 80 lower + 80 upper hits at almost one point of one module: 6400 MDs from 160 hits,
+    # far beyond the sizing estimate -> the run must grow its buffers and re-run
+    sess = lst.Session(full_geom.modules, keep_objects=True)
+    m = 1000
+    mod = full_geom.modules[m]
+    r0 = float(mod["surf"])
+    phi = 0.5 * (np.arctan2(mod["e0y"], mod["e0x"]) + np.arctan2(mod["e1y"], mod["e1x"]))
+    rng = np.random.default_rng(0)
+    n = 80
+    rr = np.concatenate([np.full(n, r0), np.full(n, r0 + float(mod["gap"]))])
+    ph = phi + rng.normal(0, 1e-5, 2 * n)
+    zz = 0.5 * (mod["emin"] + mod["emax"]) + rng.normal(0, 0.01, 2 * n)
+    ev = E.Event((rr * np.cos(ph)).astype(np.float32), (rr * np.sin(ph)).astype(np.float32), zz.astype(np.float32),
+                 np.concatenate([np.full(n, 2 * m), np.full(n, 2 * m + 1)]).astype(np.uint32),
+                 np.full(2 * n, -1, np.int32), np.zeros(0, E.TRACK_DTYPE))
+    ora = oracle.run(ora_full, ev)
+    assert len(ora["md"]) > 3000
+    compare(sess, sess.run_event(ev), ora, ev, "overflow")
+    assert sess.stats()["reruns"] >= 1
+    sess.close()
+
+
+def test_launch_configuration_invariance(built, full_geom):
+    ev = S.make_event("pu200", 9, n_tracks=1500, with_pls=True)
+    ref = None
+    for bs, bps in ((64, 2), (128, 8), (256, 4), (512, 2)):
+        s = lst.Session(full_geom.modules, block_size=bs, blocks_per_sm=bps)
+        tc = s.candidates(s.run_event(ev)).tobytes()
+        s.close()
+        if ref is None:
+            ref = tc
+        assert tc == ref, (bs, bps)
+
+
+def test_repeat_runs_identical(sess_full):
+    ev = S.make_event("pu200", 10, with_pls=True)
+    a = sess_full.candidates(sess_full.run_event(ev)).tobytes()
+    for _ in range(3):
+        assert sess_full.candidates(sess_full.run_event(ev)).tobytes() == a
+
+
+def test_device_resident_batch(built, full_geom):
+    torch = pytest.importorskip("torch")
+    evs = [S.make_event("pu200", 11 + i, n_tracks=800, with_pls=True) for i in range(4)]
+    s = lst.Session(full_geom.modules)
+    ref = [s.candidates(r) for r in s.run_batch(evs)]
+    dev = torch.device("cuda:0")
+    cat = lambda k: torch.from_numpy(np.concatenate([getattr(e, k) for e in evs])).to(dev)  # noqa: E731
+    x, y, zz = cat("x"), cat("y"), cat("z")
+    det = torch.from_numpy(np.concatenate([e.det for e in evs]).view(np.int32)).to(dev)
+    pls = torch.from_numpy(np.concatenate([e.pls for e in evs]).view(np.uint8)).to(dev)
+    hoff = torch.tensor(np.concatenate([[0], np.cumsum([e.n_hits for e in evs])]).astype(np.int32), device=dev)
+    poff = torch.tensor(np.concatenate([[0], np.cumsum([e.n_pls for e in evs])]).astype(np.int32), device=dev)
+    b = lst.lst_batch_dev(len(evs), int(hoff[-1]), int(poff[-1]), 0, x.data_ptr(), y.data_ptr(), zz.data_ptr(),
+                          det.data_ptr(), hoff.data_ptr(), pls.data_ptr(), poff.data_ptr())
+    s.run_batch_device(b)
+    ntc, ids = s.batch_finish(len(evs), timeout_ms=60000, keep_results=True)
+    for i in range(len(evs)):
+        assert ntc[i] == len(ref[i])
+        assert s.candidates(ids[i]).tobytes() == ref[i].tobytes()
+    s.close()
+
+
+def test_serving_results_equal_alone(built, full_geom):
+    evs = [S.make_event("serving", i, n_tracks=1500 + 300 * i, with_pls=True) for i in range(12)]
+    s = lst.Session(full_geom.modules)
+    alone = [s.candidates(s.run_event(e)).tobytes() for e in evs]
+    arrival = np.cumsum(np.full(len(evs), 2e-4))
+    lat, ntc, ids, wall = s.serve_replay(evs, arrival, n_slots=3, max_batch=4, keep_results=True)
+    for i in range(len(evs)):
+        assert s.candidates(ids[i]).tobytes() == alone[i], i
+        assert lat[i] > 0
+    s.close()
