@@ -179,7 +179,8 @@ def test_overflow_rerun_keeps_results(built, full_geom, ora_full):
     n = 80
     rr = np.concatenate([np.full(n, r0), np.full(n, r0 + float(mod["gap"]))])
     ph = phi + rng.normal(0, 1e-5, 2 * n)
-    zz = 0.5 * (mod["emin"] + mod["emax"]) + rng.normal(0, 0.01, 2 * n)
+    z0 = 0.5 * (mod["emin"] + mod["emax"]) + rng.normal(0, 0.01, 2 * n)
+    zz = z0 * rr / r0  # both sensors on lines through the beam spot
     ev = E.Event((rr * np.cos(ph)).astype(np.float32), (rr * np.sin(ph)).astype(np.float32), zz.astype(np.float32),
                  np.concatenate([np.full(n, 2 * m), np.full(n, 2 * m + 1)]).astype(np.uint32),
                  np.full(2 * n, -1, np.int32), np.zeros(0, E.TRACK_DTYPE))
