@@ -220,6 +220,28 @@ typedef struct lst_profile_entry {
 } lst_profile_entry;
 lst_status lst_get_profile(lst_ctx *ctx, lst_profile_entry *buf, uint32_t cap, uint32_t *n_out);
 
+/* Allocation-free variant of lst_run_event for one small event, for callers that may not
+ * allocate device memory while they run (a host framework whose pool allocator owns the
+ * GPU, a latency-critical loop that cannot take cudaMalloc's implicit synchronisation, a
+ * plug-in in a process that forbids device allocations after start-up).  The paper has no
+ * counterpart; this is a deployment convenience.
+ * All intermediate lists live in one file-scope device array of 6 MiB that every GPU which
+ * loads the library holds until the process exits.  Limits per call: 8192 hits, 512 pLS,
+ * 16384 modules in the context, 8192 MDs, 32768 LS, 32768 T3, 16384 T5, 16384 pT3,
+ * 16384 pT5; anything larger returns LST_ERR_BUDGET with the list named in lst_last_error.
+ * ev: one event (n_events = 1) with device input pointers.  tc_out: device buffer of tc_cap
+ * records receiving the track candidates (same records and order as lst_run_event);
+ * *n_tc (host) receives their number (also when it exceeds tc_cap, with
+ * LST_ERR_BUFFER_TOO_SMALL).  stream: cudaStream_t to run on (NULL = default stream); the
+ * call waits for it.  The call performs no cudaMalloc/cudaFree and no allocating library
+ * call.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and should come before any stream
+ * capture.  Every call shares the one array and resets what must start at zero, so calls
+ * whose work overlaps on the GPU (other streams, other threads) race and must not be
+ * issued.  Errors: INVALID_ARG, NO_MAP, BUDGET, BAD_INPUT, BUFFER_TOO_SMALL, CUDA. */
+lst_status lst_run_event_static(lst_ctx *ctx, const lst_batch_dev *ev, lst_tc *tc_out, uint32_t tc_cap,
+                                uint32_t *n_tc, void *stream);
+
 /* ---- serving: continuous batching of a stream of events (Sec. 2 context: trigger
  * farms reconstruct events as they arrive).  Events are admitted while the device-memory
  * budget allows, packed into open batch slots, and run concurrently on several streams;

@@ -85,6 +85,7 @@ EXPORTS = [
     "lst_load_geometry", "lst_build_connection_map", "lst_run_event", "lst_run_batch", "lst_run_batch_device",
     "lst_batch_finish", "lst_get_candidates", "lst_get_objects", "lst_release_result", "lst_destroy",
     "lst_last_error", "lst_status_string", "lst_get_stats", "lst_get_profile", "lst_serve_replay",
+    "lst_run_event_static",
 ]
 
 _lib = None
@@ -117,6 +118,7 @@ def load_library(path: str = LIB_PATH):
             "lst_get_stats": (i32, [P, P]),
             "lst_get_profile": (i32, [P, P, u32, C.POINTER(u32)]),
             "lst_serve_replay": (i32, [P, P, P, P, u32, P, P, P, P]),
+            "lst_run_event_static": (i32, [P, P, P, u32, C.POINTER(u32), P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

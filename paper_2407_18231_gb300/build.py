@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liblst.so")
-SOURCES = ["lst_kernels.cu", "lst_host.cu"]
+SOURCES = ["lst_kernels.cu", "lst_host.cu", "lst_static.cu"]
 HEADERS = ["lst_cuts.cuh", "lst_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-prec-div=true", "-prec-sqrt=true",

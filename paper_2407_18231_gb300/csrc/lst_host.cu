@@ -1281,3 +1281,19 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
     return LST_OK;
   });
 }
+
+// ------------------------------------------------------------------ views for lst_static.cu
+namespace lst {
+bool ctx_views(lst_ctx* c, GeoView* g, MethodConst* m, Launch* l, int* device, bool* have_map) {
+  if (!c) return false;
+  *g = c->geo.view();
+  *m = c->main.C;
+  *l = c->main.L;
+  *device = c->device;
+  *have_map = c->geo.have_map;
+  return true;
+}
+void ctx_set_error(lst_ctx* c, const std::string& msg) {
+  if (c) c->err = msg;
+}
+}  // namespace lst
