@@ -86,7 +86,7 @@ __device__ __forceinline__ bool exit_ok(const PointTol& a, const PointTol& b, fl
 
 __device__ __forceinline__ bool ls_select(const MethodConst& C, const PointTol& a, const PointTol& au, const PointTol& b,
                                           const PointTol& bu, float rnext_a, bool barrel_to_disk, float zb_half) {
-  if (!(pair_bend(C, a, b, b.t.w) && pair_rz(C, a, b))) return false;
+  if (!(pair_rz(C, a, b) && pair_bend(C, a, b, b.t.w))) return false;  // cheaper test first
   if (barrel_to_disk && !exit_ok(a, b, rnext_a, zb_half)) return false;
   const float cx = b.p.x - a.p.x;
   const float cy = b.p.y - a.p.y;
@@ -182,6 +182,22 @@ __device__ __forceinline__ bool t5_select(const MethodConst& C, const PointTol& 
   return c1 && c2 && c3 && c4;
 }
 
+// Same decision as t5_select without the score: stops at the first failing condition
+// (inner/outer curvatures first), so most rejected candidates skip half the circles.
+__device__ __forceinline__ bool t5_accept(const MethodConst& C, const PointTol& A, const PointTol& B, const PointTol& Cc,
+                                          const PointTol& D, const PointTol& E) {
+  const Circle3 in = circle3(A, B, Cc);
+  const Circle3 out = circle3(Cc, D, E);
+  const float d1 = fabsf(in.k - out.k);
+  if (!(d1 <= C.KAPPA * (fabsf(in.k) + fabsf(out.k)) + in.tol + out.tol + C.KAPPA0)) return false;
+  const Circle3 br = circle3(B, Cc, D);
+  const Circle3 fu = circle3(A, Cc, E);
+  const float d2 = fabsf(br.k - fu.k);
+  if (!(d2 <= C.KAPPA * (fabsf(br.k) + fabsf(fu.k)) + br.tol + fu.tol + C.KAPPA0)) return false;
+  if (!(fabsf(fu.k) <= C.KMAX + fu.tol)) return false;
+  return rz3(C, A, Cc, E);
+}
+
 // ---- pLS helix ----
 struct PlsHelix {
   float x0, y0, z0, R, cx, cy, cot, q, pt;
@@ -225,6 +241,31 @@ __device__ __forceinline__ bool pls_anchor(const MethodConst& C, const PlsHelix&
   const float a = dphi / wphi, b = ez / wz;
   score = score + (a * a + b * b);
   return (fabsf(dphi) <= wphi) && (fabsf(ez) <= wz);
+}
+
+}  // namespace lst
+
+namespace lst {
+
+// Same decision as pls_anchor without the score.  The r-phi window grows with the arc
+// length s from the reference point, and s <= (pi / 2) chord for any arc up to half a turn,
+// so a residual beyond the window at s = 1.6 chord can never pass: that case is rejected
+// before the arc-length series is evaluated.  Exact: the bound only removes candidates
+// the full test rejects too.
+__device__ __forceinline__ bool pls_anchor_accept(const MethodConst& C, const PlsHelix& h, const PointTol& X) {
+  const float ddx = X.p.x - h.x0, ddy = X.p.y - h.y0;
+  const float chord = sqrtf(ddx * ddx + ddy * ddy);
+  const float ex = X.p.x - h.cx, ey = X.p.y - h.cy;
+  const float dphi = sqrtf(ex * ex + ey * ey) - h.R;
+  const float smax = 1.6f * chord;
+  const float wmax = (C.W0 + 0.003f * smax + 0.015f * smax * smax / h.R + X.t.y) * 1.001f;
+  if (fabsf(dphi) > wmax) return false;
+  const float s = arc_length(chord, h.R);
+  const float wphi = C.W0 + 0.003f * s + 0.015f * s * s / h.R + X.t.y;
+  if (!(fabsf(dphi) <= wphi)) return false;
+  const float ez = X.p.z - (h.z0 + s * h.cot);
+  const float wz = 0.05f + 0.002f * s + X.t.x + X.t.y * fabsf(h.cot);
+  return fabsf(ez) <= wz;
 }
 
 }  // namespace lst

@@ -35,6 +35,7 @@ struct Hdr {
   uint32_t tot[N_TOTALS];
   uint32_t err;
   uint32_t pad2[3];
+  uint32_t mask_used[8];  // join scratch words taken per stage (MD, LS, T3, T5, pT3, pT5)
 };
 
 // Geometry tables (device pointers) and per-geometry scalars.
@@ -51,6 +52,11 @@ struct GeoView {
   uint32_t surf_nrows[NSURF];
   uint32_t surf_row_base[NSURF];
   const uint32_t *row_nphi, *row_mod_base, *row_mods;
+  // rows whose wedges partition the circle (every sector present, each upper edge equal
+  // bit for bit to the next sector's lower edge): at most one sector can hold a point, so a
+  // guessed sector checked with the exact test gives the linear scan's answer
+  const uint8_t *row_fast;
+  const float *row_phi0;  // angle of sector 0's lower edge
 };
 
 // Pipeline buffers (device pointers) and capacities.
@@ -88,6 +94,9 @@ struct BufView {
   void *tc;  // lst_tc records
   // scan scratch
   uint32_t *scan_part;
+  // join scratch: chunk ballots of the count passes, and each unit's slice of them
+  uint32_t *mask, *mask_off;
+  uint32_t cap_mask;
 };
 
 typedef void (*MarkFn)(void* arg, int kernel_name);

@@ -115,15 +115,18 @@ struct Geometry {
   uint32_t surf_nrows[NSURF];
   uint32_t surf_row_base[NSURF];
   std::vector<uint32_t> row_nphi, row_mod_base, row_mods;
+  std::vector<uint8_t> row_fast;
+  std::vector<float> row_phi0;
   std::vector<uint32_t> conn_off, conn;
   bool have_map = false;
   // device copies
-  DevBuf d_modc, d_rnext, d_subdet, d_mod_e, d_mod_g, d_row_nphi, d_row_base, d_row_mods, d_conn_off, d_conn;
+  DevBuf d_modc, d_rnext, d_subdet, d_mod_e, d_mod_g, d_row_nphi, d_row_base, d_row_mods, d_conn_off, d_conn,
+      d_row_fast, d_row_phi0;
   uint64_t dev_bytes = 0;
 
   ~Geometry() {
-    DevBuf* all[] = {&d_modc, &d_rnext, &d_subdet, &d_mod_e, &d_mod_g, &d_row_nphi,
-                     &d_row_base, &d_row_mods, &d_conn_off, &d_conn};
+    DevBuf* all[] = {&d_modc, &d_rnext, &d_subdet, &d_mod_e, &d_mod_g, &d_row_nphi, &d_row_base,
+                     &d_row_mods, &d_conn_off, &d_conn, &d_row_fast, &d_row_phi0};
     for (DevBuf* b : all) b->release();
   }
 
@@ -202,6 +205,25 @@ struct Geometry {
       uint32_t& slot = row_mods[row_mod_base[r] + mods[i].iphi];
       if (slot != NONE) throw StatusError{LST_ERR_BAD_INPUT, "two modules share a row and sector"};
       slot = i;
+    }
+    // rows whose sectors partition the circle
+    row_fast.assign(nrows, 0);
+    row_phi0.assign(nrows, 0.0f);
+    for (uint32_t r = 0; r < nrows; r++) {
+      const uint32_t n = row_nphi[r];
+      if (n < 3) continue;
+      bool ok = true;
+      for (uint32_t k = 0; k < n && ok; k++) {
+        const uint32_t a = row_mods[row_mod_base[r] + k], b = row_mods[row_mod_base[r] + (k + 1) % n];
+        if (a == NONE || b == NONE) { ok = false; break; }
+        const lst_module_desc &ma = mods[a], &mb = mods[b];
+        ok = ma.e1x == mb.e0x && ma.e1y == mb.e0y &&
+             (double)ma.e0x * ma.e1y - (double)ma.e0y * ma.e1x > 0.0;
+      }
+      if (!ok) continue;
+      row_fast[r] = 1;
+      const lst_module_desc& m0 = mods[row_mods[row_mod_base[r]]];
+      row_phi0[r] = (float)std::atan2((double)m0.e0y, (double)m0.e0x);
     }
   }
 
@@ -307,6 +329,8 @@ struct Geometry {
     upload(d_row_nphi, row_nphi);
     upload(d_row_base, row_mod_base);
     upload(d_row_mods, row_mods);
+    upload(d_row_fast, row_fast);
+    upload(d_row_phi0, row_phi0);
   }
 
   void upload_map() {
@@ -333,6 +357,8 @@ struct Geometry {
     v.row_nphi = (const uint32_t*)d_row_nphi.p;
     v.row_mod_base = (const uint32_t*)d_row_base.p;
     v.row_mods = (const uint32_t*)d_row_mods.p;
+    v.row_fast = (const uint8_t*)d_row_fast.p;
+    v.row_phi0 = (const float*)d_row_phi0.p;
     return v;
   }
 };
@@ -377,7 +403,8 @@ struct Pipeline {
   DevBuf pt5_cnt, pt5_off, pt5_pls, pt5_obj, pt5_score;
   DevBuf c5_cnt, c5_off, c5_list, c3_cnt, c3_off, c3_list, ct_cnt, ct_off, ct_list;
   DevBuf alive5, alive3, alivet, plstc, used5, used3, cross3, crosst, sa5, sa3, sat, sap;
-  DevBuf tc_ev_off, tc, scan_part;
+  DevBuf tc_ev_off, tc, scan_part, mask, mask_off;
+  uint32_t cap_mask = 0;
   // host staging (pinned)
   Hdr* h_hdr = nullptr;        // header to upload
   Hdr* h_hdr_out = nullptr;    // header read back
@@ -409,7 +436,7 @@ struct Pipeline {
                               &pt5_cnt, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
                               &c3_cnt, &c3_off, &c3_list, &ct_cnt, &ct_off, &ct_list, &alive5, &alive3, &alivet,
                               &plstc, &used5, &used3, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
-                              &scan_part};
+                              &scan_part, &mask, &mask_off};
     for (auto& b : t5_m) v.push_back(&b);
     return v;
   }
@@ -546,7 +573,23 @@ struct Pipeline {
     need<uint32_t>(sap, c.pls + 1);
     need<uint32_t>(tc_ev_off, c.ev + 1);
     need<lst_tc>(tc, c.tc);
+    need<uint32_t>(mask_off, std::max<size_t>(std::max<size_t>(c.ev * nm, c.md), c.pls));
+    // join scratch: about two ballot words per hit suffice for PU200-like events; runs that
+    // need more fall back to re-testing and the next run gets the learned size
+    const uint32_t want = std::max<uint32_t>(cap_mask, (uint32_t)std::min<uint64_t>(4000000000ull, 4ull * c.hits + 65536));
+    need<uint32_t>(mask, want);
+    cap_mask = want;
     cap = c;
+  }
+
+  void learn_mask(const Hdr& h) {
+    uint32_t mx = 0;
+    for (int k = 0; k < 6; k++) mx = std::max(mx, h.mask_used[k]);
+    if (mx > cap_mask) {
+      const uint32_t want = (uint32_t)std::min<uint64_t>(4000000000ull, (uint64_t)mx * 5 / 4 + 65536);
+      need<uint32_t>(mask, want);
+      cap_mask = want;
+    }
   }
 
   void ensure_inputs(uint32_t ne, uint32_t nh, uint32_t np) {
@@ -577,6 +620,7 @@ struct Pipeline {
 
   // Learn sizes from a finished run so that the next estimate is large enough.
   void learn(const Hdr& h) {
+    learn_mask(h);
     if (h.n_hits) {
       r_md = std::max(r_md, (double)h.tot[T_MD] / h.n_hits);
       r_ls = std::max(r_ls, (double)h.tot[T_LS] / h.n_hits);
@@ -619,6 +663,7 @@ struct Pipeline {
     v.used5 = P32(used5); v.used3 = P32(used3); v.cross3 = P32(cross3); v.crosst = P32(crosst);
     v.sa5 = P32(sa5); v.sa3 = P32(sa3); v.sat = P32(sat); v.sap = P32(sap);
     v.tc_ev_off = P32(tc_ev_off); v.tc = tc.p; v.scan_part = P32(scan_part);
+    v.mask = P32(mask); v.mask_off = P32(mask_off); v.cap_mask = cap_mask;
 #undef P32
     return v;
   }
@@ -1195,6 +1240,27 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
       for (auto& s : slots) t += s.P->dev_bytes;
       return t;
     };
+    // Before the clock starts: size every slot for a full batch of typical events (from the
+    // first events of the stream) and capture its graph, unless that alone breaks the budget.
+    {
+      const uint32_t m = std::min<uint32_t>(n, 64);
+      uint64_t sh = 0, sp = 0;
+      for (uint32_t i = 0; i < m; i++) {
+        sh += evs[i].n_hits;
+        sp += evs[i].n_pls;
+      }
+      const uint32_t bh = (uint32_t)std::min<uint64_t>(0xF0000000ull, sh * 3 / 2 * cfg->max_batch / m + 1);
+      const uint32_t bp = (uint32_t)std::min<uint64_t>(0x0F000000ull, sp * 3 / 2 * cfg->max_batch / m + 1);
+      for (auto& s : slots) {
+        s.P->ensure_caps(s.P->estimate(cfg->max_batch, bh, bp));
+        s.P->ensure_inputs(cfg->max_batch, bh, bp);
+        if (budget && held() > budget) break;
+        lst_event empty{};
+        pack_host_events(*s.P, &empty, 1);
+        s.P->launch(true);
+        if (!s.P->wait(0)) return fail(c, LST_ERR_TIMEOUT, "slot warm-up timed out");
+      }
+    }
     std::deque<uint32_t> queue;
     uint32_t next = 0, done = 0;
     const double t0 = now_s();

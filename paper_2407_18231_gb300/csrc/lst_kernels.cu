@@ -49,20 +49,58 @@ struct ScorePayload {
   float score, kfull;
 };
 
+// Scratch of the joins: the count pass stores every 32-candidate chunk's ballot word in a
+// slice of `mask` reserved for the unit (an atomic bump of *used); the fill pass replays
+// those words and only touches chunks that hold passing candidates.  A unit that finds
+// the mask full records NONE and its fill pass simply re-runs the tests.
+struct JoinScratch {
+  uint32_t* mask;
+  uint32_t cap;
+  uint32_t* used;
+  uint32_t* unit_base;  // this unit's slot in the per-unit mask offsets
+};
+
 // Walks all (outer i, inner j) candidates of one unit; outer(i, begin, count) gives the
-// inner index range of outer item i.  Returns the number of passing candidates; with FILL
-// it also emits them at base + rank in candidate order.
-template <bool FILL, typename P, typename OuterFn, typename TestFn, typename EmitFn>
-__device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, OuterFn outer, TestFn test,
-                                              EmitFn emit) {
+// inner index range of outer item i.  Count pass (FILL = false): test(i, j) decides, the
+// number of passes is returned and the ballots are recorded.  Fill pass: the passing
+// candidates are emitted at base + rank in candidate order, with score(i, j, payload)
+// computing what the emitter needs.
+template <bool FILL, typename P, typename OuterFn, typename TestFn, typename ScoreFn, typename EmitFn>
+__device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, const JoinScratch& js, OuterFn outer,
+                                              TestFn test, ScoreFn score, EmitFn emit) {
   const uint32_t lane = lane_id();
-  uint32_t count = 0;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t mbase;
+  if (!FILL) {
+    uint32_t nch = 0;
+    for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
+      uint32_t b = 0, c = 0;
+      if (g0 + lane < n_outer) outer(g0 + lane, b, c);
+      const uint32_t tot = __shfl_sync(FULL, warp_incl_scan(c), 31);
+      nch += (tot + 31u) >> 5;
+    }
+    uint32_t mb = NONE;
+    if (nch && lane == 0) {
+      const uint32_t b0 = atomicAdd(js.used, nch);
+      if (b0 < js.cap && nch <= js.cap - b0) mb = b0;
+    }
+    mbase = __shfl_sync(FULL, mb, 0);
+    if (lane == 0) *js.unit_base = mbase;
+  } else {
+    mbase = *js.unit_base;
+  }
+  uint32_t count = 0, ci = 0;
   for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
     uint32_t b = 0, c = 0;
     if (g0 + lane < n_outer) outer(g0 + lane, b, c);
     const uint32_t incl = warp_incl_scan(c);
     const uint32_t total = __shfl_sync(FULL, incl, 31);
-    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+    for (uint32_t t0 = 0; t0 < total; t0 += 32, ci++) {
+      uint32_t bal = 0;
+      if (FILL && mbase != NONE) {
+        bal = js.mask[mbase + ci];
+        if (bal == 0u) continue;  // warp-uniform
+      }
       const uint32_t cand = t0 + lane;
       const uint32_t cc = cand < total ? cand : total - 1;
       const uint32_t o = owner_lane(incl, cc);
@@ -70,11 +108,19 @@ __device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, O
       const uint32_t co = __shfl_sync(FULL, c, o);
       const uint32_t io = __shfl_sync(FULL, incl, o);
       const uint32_t j = bo + (cc - (io - co));
-      P pl;
-      bool pass = false;
-      if (cand < total) pass = test(g0 + o, j, pl);
-      const uint32_t bal = __ballot_sync(FULL, pass);
-      if (FILL && pass) emit(base + count + __popc(bal & ((1u << lane) - 1u)), g0 + o, j, pl);
+      bool pass;
+      if (FILL && mbase != NONE) {
+        pass = (bal >> lane) & 1u;
+      } else {
+        pass = cand < total && test(g0 + o, j);
+        bal = __ballot_sync(FULL, pass);
+        if (!FILL && mbase != NONE && lane == 0) js.mask[mbase + ci] = bal;
+      }
+      if (FILL && pass) {
+        P pl;
+        score(g0 + o, j, pl);
+        emit(base + count + __popc(bal & lt), g0 + o, j, pl);
+      }
       count += __popc(bal);
     }
   }
@@ -258,12 +304,14 @@ __global__ void __launch_bounds__(512) k_md(MethodConst C, GeoView G, BufView B)
     const uint32_t m = u % G.nm;
     const float4 cst = G.modc[m];
     const uint32_t base = FILL ? B.md_off[u] : 0u;
+    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[0], &B.mask_off[u]};
     const uint32_t cnt = warp_join<FILL, NoPayload>(
-        n_lo, base, [&](uint32_t, uint32_t& b, uint32_t& c) { b = up_b; c = n_up; },
-        [&](uint32_t i, uint32_t j, NoPayload&) {
+        n_lo, base, js, [&](uint32_t, uint32_t& b, uint32_t& c) { b = up_b; c = n_up; },
+        [&](uint32_t i, uint32_t j) {
           const PointTol a{B.hit4[lo_b + i], cst}, b{B.hit4[j], cst};
-          return pair_bend(C, a, b, cst.w) && pair_rz(C, a, b);
+          return pair_rz(C, a, b) && pair_bend(C, a, b, cst.w);
         },
+        [&](uint32_t, uint32_t, NoPayload&) {},
         [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
           B.md_unit[pos] = u;
           B.md_lo4[pos] = B.hit4[lo_b + i];
@@ -295,18 +343,20 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B)
     const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
     const uint32_t base = FILL ? B.ls_off[a] : 0u;
     const uint32_t ubase = ev * G.nm;
+    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[1], &B.mask_off[a]};
     const uint32_t cnt = warp_join<FILL, NoPayload>(
-        nb, base,
+        nb, base, js,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t u = ubase + G.conn[nb0 + i];
           b = B.md_off[u];
           c = B.md_off[u + 1] - b;
         },
-        [&](uint32_t, uint32_t j, NoPayload&) {
+        [&](uint32_t, uint32_t j) {
           const uint32_t Bm = B.md_unit[j] - ubase;
           const bool b2d = a_barrel && G.subdet[Bm] == 1;
           return ls_select(C, pa, pau, md_point(B, j), md_upper(B, j), rnext, b2d, G.zb_half);
         },
+        [&](uint32_t, uint32_t, NoPayload&) {},
         [&](uint32_t pos, uint32_t, uint32_t j, const NoPayload&) {
           B.ls_in[pos] = a;
           B.ls_out[pos] = j;
@@ -326,17 +376,19 @@ __global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B)
     const PointTol pa = md_point(B, a);
     const uint32_t l0 = B.ls_off[a], nl = B.ls_off[a + 1] - l0;
     const uint32_t base = FILL ? B.t3_off[a] : 0u;
+    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[2], &B.mask_off[a]};
     const uint32_t cnt = warp_join<FILL, NoPayload>(
-        nl, base,
+        nl, base, js,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t mb = B.ls_out[l0 + i];
           b = B.ls_off[mb];
           c = B.ls_off[mb + 1] - b;
         },
-        [&](uint32_t i, uint32_t j, NoPayload&) {
+        [&](uint32_t i, uint32_t j) {
           const uint32_t mb = B.ls_out[l0 + i], mc = B.ls_out[j];
           return t3_select(C, pa, md_point(B, mb), md_upper(B, mb), md_point(B, mc));
         },
+        [&](uint32_t, uint32_t, NoPayload&) {},
         [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
           B.t3_a[pos] = a;
           B.t3_b[pos] = B.ls_out[l0 + i];
@@ -357,17 +409,21 @@ __global__ void __launch_bounds__(512) k_t5(MethodConst C, GeoView G, BufView B)
     const PointTol pa = md_point(B, a);
     const uint32_t s0 = B.t3_off[a], ns = B.t3_off[a + 1] - s0;
     const uint32_t base = FILL ? B.t5_off[a] : 0u;
+    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[3], &B.mask_off[a]};
     const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        ns, base,
+        ns, base, js,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t mc = B.t3_c[s0 + i];
           b = B.t3_off[mc];
           c = B.t3_off[mc + 1] - b;
         },
+        [&](uint32_t i, uint32_t j) {
+          const uint32_t mb = B.t3_b[s0 + i], mc = B.t3_c[s0 + i], md = B.t3_b[j], me = B.t3_c[j];
+          return t5_accept(C, pa, md_point(B, mb), md_point(B, mc), md_point(B, md), md_point(B, me));
+        },
         [&](uint32_t i, uint32_t j, ScorePayload& pl) {
           const uint32_t mb = B.t3_b[s0 + i], mc = B.t3_c[s0 + i], md = B.t3_b[j], me = B.t3_c[j];
-          return t5_select(C, pa, md_point(B, mb), md_point(B, mc), md_point(B, md), md_point(B, me), pl.score,
-                           pl.kfull);
+          t5_select(C, pa, md_point(B, mb), md_point(B, mc), md_point(B, md), md_point(B, me), pl.score, pl.kfull);
         },
         [&](uint32_t pos, uint32_t i, uint32_t j, const ScorePayload& pl) {
           B.t5_m0[pos] = a;
@@ -390,8 +446,26 @@ __device__ __forceinline__ void add_cand(uint32_t* list, uint32_t& n, uint32_t i
   list[n++] = id;
 }
 
+__device__ __forceinline__ bool in_sector(const GeoView& G, uint32_t id, float px, float py) {
+  const float4 e = G.mod_e[id];
+  const float c0 = e.x * py - e.y * px;
+  const float c1 = e.z * py - e.w * px;
+  return c0 >= 0.0f && c1 < 0.0f;
+}
+
 __device__ int find_sector(const GeoView& G, uint32_t row, float px, float py) {
   const uint32_t nphi = G.row_nphi[row], base = G.row_mod_base[row];
+  if (G.row_fast[row]) {
+    const float two_pi = 6.28318531f;
+    float a = atan2f(py, px) - G.row_phi0[row];
+    a = a - two_pi * floorf(a / two_pi);
+    int k0 = (int)(a * (float)nphi / two_pi);
+    k0 = k0 < 0 ? 0 : (k0 >= (int)nphi ? (int)nphi - 1 : k0);
+    for (int d = 0; d < 3; d++) {
+      const int kk = ((k0 + (d == 0 ? 0 : (d == 1 ? -1 : 1))) % (int)nphi + (int)nphi) % (int)nphi;
+      if (in_sector(G, G.row_mods[base + kk], px, py)) return kk;
+    }
+  }
   for (uint32_t k = 0; k < nphi; k++) {
     const uint32_t id = G.row_mods[base + k];
     if (id == NONE) continue;
@@ -560,21 +634,24 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
     const uint32_t ubase = B.pls_ev[p] * G.nm;
     const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
     const uint32_t base = FILL ? B.pt3_off[p] : 0u;
+    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[4], &B.mask_off[p]};
     const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        B.pls_ncand[p], base,
+        B.pls_ncand[p], base, js,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t u = ubase + cand[i];
           b = B.t3_off[B.md_off[u]];
           c = B.t3_off[B.md_off[u + 1]] - b;
         },
+        [&](uint32_t, uint32_t t) {
+          return pls_anchor_accept(C, h, md_point(B, B.t3_a[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) &&
+                 pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
+        },
         [&](uint32_t, uint32_t t, ScorePayload& pl) {
           float score = 0.0f;
-          bool ok = true;
-          ok &= pls_anchor(C, h, md_point(B, B.t3_a[t]), score);
-          ok &= pls_anchor(C, h, md_point(B, B.t3_b[t]), score);
-          ok &= pls_anchor(C, h, md_point(B, B.t3_c[t]), score);
+          pls_anchor(C, h, md_point(B, B.t3_a[t]), score);
+          pls_anchor(C, h, md_point(B, B.t3_b[t]), score);
+          pls_anchor(C, h, md_point(B, B.t3_c[t]), score);
           pl.score = score;
-          return ok;
         },
         [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
           B.pt3_pls[pos] = p;
@@ -595,28 +672,35 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
     const uint32_t ubase = B.pls_ev[p] * G.nm;
     const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
     const uint32_t base = FILL ? B.pt5_off[p] : 0u;
+    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[5], &B.mask_off[p]};
     const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        B.pls_ncand[p], base,
+        B.pls_ncand[p], base, js,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t u = ubase + cand[i];
           b = B.t5_off[B.md_off[u]];
           c = B.t5_off[B.md_off[u + 1]] - b;
         },
-        [&](uint32_t, uint32_t t, ScorePayload& pl) {
-          const PointTol P0 = md_point(B, B.t5_m0[t]), P1 = md_point(B, B.t5_m1[t]), P2 = md_point(B, B.t5_m2[t]),
-                         P3 = md_point(B, B.t5_m3[t]), P4 = md_point(B, B.t5_m4[t]);
-          float score = 0.0f;
-          bool ok = true;
-          ok &= pls_anchor(C, h, P0, score);
-          ok &= pls_anchor(C, h, P1, score);
-          ok &= pls_anchor(C, h, P2, score);
-          ok &= pls_anchor(C, h, P3, score);
-          ok &= pls_anchor(C, h, P4, score);
+        [&](uint32_t, uint32_t t) {
+          const PointTol P0 = md_point(B, B.t5_m0[t]);
+          if (!pls_anchor_accept(C, h, P0)) return false;
+          const PointTol P2 = md_point(B, B.t5_m2[t]);
+          if (!pls_anchor_accept(C, h, P2)) return false;
+          const PointTol P4 = md_point(B, B.t5_m4[t]);
+          if (!pls_anchor_accept(C, h, P4)) return false;
+          if (!pls_anchor_accept(C, h, md_point(B, B.t5_m1[t]))) return false;
+          if (!pls_anchor_accept(C, h, md_point(B, B.t5_m3[t]))) return false;
           const float kf = B.t5_kfull[t];
           const Circle3 fu = circle3(P0, P2, P4);
-          const bool c5 = fabsf(fabsf(kf) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
+          return fabsf(fabsf(kf) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
+        },
+        [&](uint32_t, uint32_t t, ScorePayload& pl) {
+          float score = 0.0f;
+          pls_anchor(C, h, md_point(B, B.t5_m0[t]), score);
+          pls_anchor(C, h, md_point(B, B.t5_m1[t]), score);
+          pls_anchor(C, h, md_point(B, B.t5_m2[t]), score);
+          pls_anchor(C, h, md_point(B, B.t5_m3[t]), score);
+          pls_anchor(C, h, md_point(B, B.t5_m4[t]), score);
           pl.score = score;
-          return ok && c5;
         },
         [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
           B.pt5_pls[pos] = p;

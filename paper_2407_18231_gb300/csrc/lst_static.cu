@@ -37,6 +37,7 @@ constexpr uint32_t MAX_T3 = 32768;
 constexpr uint32_t MAX_T5 = 16384;
 constexpr uint32_t MAX_PT3 = 16384;
 constexpr uint32_t MAX_PT5 = 16384;
+constexpr uint32_t MASK_WORDS = 65536;  // join ballots; a fuller event just re-tests in its fill passes
 constexpr size_t SCRATCH_BYTES = size_t(6) << 20;  // every GPU that loads the library holds this until exit
 
 // The scratch.  In host code `g_scratch` is only a stand-in symbol: its device address
@@ -136,6 +137,9 @@ size_t carve(char* base, BufView& B) {
   B.sap = c.take<uint32_t>(MAX_PLS + 1);
   B.tc_ev_off = c.take<uint32_t>(2);
   B.scan_part = c.take<uint32_t>(1024);
+  B.mask_off = c.take<uint32_t>(MAX_MODULES);  // >= MAX_MD and MAX_PLS
+  B.cap_mask = MASK_WORDS;
+  B.mask = c.take<uint32_t>(MASK_WORDS);
   return c.off;
 }
 
