@@ -248,19 +248,19 @@ def main():
     dev_batches = [to_device(b) for b in batches]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     sess = lst.Session(geom.modules, device=local)
-    stream = torch.cuda.current_stream(dev)
-
-    def step(k):
-        sess.run_batch_device(dev_batches[k % P][0], stream.cuda_stream)
-        sess.batch_finish(B, timeout_ms=120000)
+    # the library runs on this stream, so events recorded on it bracket its kernels
+    stream = torch.cuda.Stream(dev)
+    assert stream.cuda_stream != 0
 
     for k in range(args.warmup):
-        step(k)
+        sess.run_batch_device(dev_batches[k % P][0], stream.cuda_stream)
+        sess.batch_finish(B, timeout_ms=120000)
     stats = sess.stats()
+    reruns_before = stats["reruns"]
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk, torch.cuda.stream(stream):
         torch.cuda.synchronize()
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
@@ -268,11 +268,14 @@ def main():
         for k in range(args.steps):
             flush.zero_()  # between timed iterations: evict L2 (not timed)
             t_start.record(stream)
-            step(k)
+            sess.run_batch_device(dev_batches[k % P][0], stream.cuda_stream)
             t_end.record(stream)
-            t_end.synchronize()
+            # status check of the step (overflow re-run, bad input) after the timed region
+            sess.batch_finish(B, timeout_ms=120000)
             elapsed_ms += t_start.elapsed_time(t_end)
         torch.cuda.synchronize()
+    if sess.stats()["reruns"] != reruns_before:
+        raise RuntimeError("a timed step re-ran after a list overflow; warm-up did not size the buffers")
     if ws > 1:
         torch.distributed.barrier()
         t = torch.tensor([elapsed_ms], device=dev)

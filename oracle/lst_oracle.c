@@ -319,17 +319,19 @@ typedef struct { float x, y, z, r, zeta, rho, delta, T; } pt_t;
  * the step b - a across and along a's radial direction, a prompt track of radius
  * R >= Rmin has |u| / v <= T_b (T_b from the outer module's largest radius).  v is widened
  * by the radial tolerances; e adds the r-phi tolerance and the tangential shift a radial
- * error causes when a and b differ in phi. */
+ * error causes when a and b differ in phi.  The inequality |u| <= (v + rho) T + e is
+ * evaluated multiplied by r_a > 0: U = u r_a, W = (v + rho) r_a, E = e r_a. */
 static int pair_bend(const pt_t *a, const pt_t *b, float T) {
   float dx = b->x - a->x;
   float dy = b->y - a->y;
-  float u = (a->x * dy - a->y * dx) / a->r;
-  float v = (a->x * dx + a->y * dy) / a->r;
+  float U = a->x * dy - a->y * dx;
+  float V = a->x * dx + a->y * dy;
   float rs = a->rho + b->rho;
-  float veff = v + rs;
-  float sphi = fabsf(a->x * b->y - a->y * b->x) / (a->r * b->r);
-  float e = C_E0 + rs * (sphi + 0.05f);
-  return (veff > 0.0f) && (fabsf(u) <= veff * T + e);
+  float W = V + rs * a->r;
+  float sphi = 0.0f; /* the radial-error term only exists when rs > 0 */
+  if (rs != 0.0f) sphi = fabsf(a->x * b->y - a->y * b->x) / (a->r * b->r);
+  float E = (C_E0 + rs * (sphi + 0.05f)) * a->r;
+  return (W > 0.0f) && (fabsf(U) <= W * T + E);
 }
 
 /* r-z pointing of a hit pair: za rb - ra zb = z0 (rb - ra) for a straight line from

@@ -38,17 +38,20 @@ struct PointTol {
 };
 
 // Transverse bending of a hit pair a (inner) -> b (outer): the step's component across
-// a's radial direction (u) against its radial component (v), |u| <= v T + e.
+// a's radial direction (u) against its radial component (v), |u| <= v T + e, evaluated
+// multiplied through by r_a (U = u r_a, W = (v + rho) r_a) so that no division is needed
+// unless a hit has a radial tolerance (endcap).
 __device__ __forceinline__ bool pair_bend(const MethodConst& C, const PointTol& a, const PointTol& b, float T) {
   const float dx = b.p.x - a.p.x;
   const float dy = b.p.y - a.p.y;
-  const float u = (a.p.x * dy - a.p.y * dx) / a.p.w;
-  const float v = (a.p.x * dx + a.p.y * dy) / a.p.w;
+  const float U = a.p.x * dy - a.p.y * dx;
+  const float V = a.p.x * dx + a.p.y * dy;
   const float rs = a.t.y + b.t.y;
-  const float veff = v + rs;
-  const float sphi = fabsf(a.p.x * b.p.y - a.p.y * b.p.x) / (a.p.w * b.p.w);
-  const float e = C.E0 + rs * (sphi + 0.05f);
-  return (veff > 0.0f) && (fabsf(u) <= veff * T + e);
+  const float W = V + rs * a.p.w;
+  float sphi = 0.0f;  // rs * (sphi + 0.05) below is +0 when rs == 0, whatever sphi is
+  if (rs != 0.0f) sphi = fabsf(a.p.x * b.p.y - a.p.y * b.p.x) / (a.p.w * b.p.w);
+  const float E = (C.E0 + rs * (sphi + 0.05f)) * a.p.w;
+  return (W > 0.0f) && (fabsf(U) <= W * T + E);
 }
 
 // r-z pointing of a hit pair: za rb - ra zb = z0 (rb - ra) for a line from (0, z0).

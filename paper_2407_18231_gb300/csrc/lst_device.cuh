@@ -78,6 +78,7 @@ struct BufView {
   float *t5_score, *t5_kfull;
   // pLS
   uint32_t *pls_ev, *pls_ncand, *pls_cand;
+  uint2 *pls_t3rng, *pls_t5rng;  // per candidate module: (first, count) of T3s / T5s starting there
   float4 *pls_h0, *pls_h1;  // (x0, y0, z0, R), (cx, cy, cot, q)
   float *pls_pt;
   // pT3 / pT5

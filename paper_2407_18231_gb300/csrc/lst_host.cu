@@ -9,6 +9,9 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
+#include <condition_variable>
+#include <atomic>
 #include <memory>
 #include <string>
 #include <thread>
@@ -365,7 +368,8 @@ struct Geometry {
 
 // ------------------------------------------------------------------ results
 struct Result {
-  std::vector<lst_tc> tcs;
+  std::shared_ptr<const std::vector<lst_tc>> tc_buf;  // the batch's candidates
+  size_t tc_off = 0, tc_n = 0;                        // this event's slice
   bool has_objects = false;
   std::vector<lst_md_rec> md;
   std::vector<lst_ls_rec> ls;
@@ -398,7 +402,7 @@ struct Pipeline {
   DevBuf ls_cnt, ls_off, ls_in, ls_out;
   DevBuf t3_cnt, t3_off, t3_a, t3_b, t3_c;
   DevBuf t5_cnt, t5_off, t5_m[5], t5_score, t5_kfull;
-  DevBuf pls_ev, pls_ncand, pls_cand, pls_h0, pls_h1, pls_pt;
+  DevBuf pls_ev, pls_ncand, pls_cand, pls_h0, pls_h1, pls_pt, pls_t3rng, pls_t5rng;
   DevBuf pt3_cnt, pt3_off, pt3_pls, pt3_obj, pt3_score;
   DevBuf pt5_cnt, pt5_off, pt5_pls, pt5_obj, pt5_score;
   DevBuf c5_cnt, c5_off, c5_list, c3_cnt, c3_off, c3_list, ct_cnt, ct_off, ct_list;
@@ -432,7 +436,7 @@ struct Pipeline {
                               &hit_tmp, &hit_ev, &hit_idx, &hit4, &md_cnt, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
                               &md_lo4, &md_up4, &md_cst, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_cnt, &t3_off, &t3_a,
                               &t3_b, &t3_c, &t5_cnt, &t5_off, &t5_score, &t5_kfull, &pls_ev, &pls_ncand, &pls_cand,
-                              &pls_h0, &pls_h1, &pls_pt, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
+                              &pls_h0, &pls_h1, &pls_pt, &pls_t3rng, &pls_t5rng, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
                               &pt5_cnt, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
                               &c3_cnt, &c3_off, &c3_list, &ct_cnt, &ct_off, &ct_list, &alive5, &alive3, &alivet,
                               &plstc, &used5, &used3, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
@@ -482,7 +486,7 @@ struct Pipeline {
     CK(cudaMallocHost((void**)&h_hdr, sizeof(Hdr)));
     CK(cudaMallocHost((void**)&h_hdr_out, sizeof(Hdr)));
     hdr.ensure(sizeof(Hdr), dev_bytes);
-    scan_part.ensure(1024 * sizeof(uint32_t), dev_bytes);
+    scan_part.ensure(4 * 1024 * sizeof(uint32_t), dev_bytes);  // up to four scans per launch
   }
 
   template <typename T>
@@ -537,6 +541,8 @@ struct Pipeline {
     need<uint32_t>(pls_ev, c.pls);
     need<uint32_t>(pls_ncand, c.pls);
     need<uint32_t>(pls_cand, (size_t)c.pls * MAX_CAND);
+    need<uint2>(pls_t3rng, (size_t)c.pls * MAX_CAND);
+    need<uint2>(pls_t5rng, (size_t)c.pls * MAX_CAND);
     need<float4>(pls_h0, c.pls);
     need<float4>(pls_h1, c.pls);
     need<float>(pls_pt, c.pls);
@@ -651,6 +657,7 @@ struct Pipeline {
     v.t5_m4 = P32(t5_m[4]);
     v.t5_score = (float*)t5_score.p; v.t5_kfull = (float*)t5_kfull.p;
     v.pls_ev = P32(pls_ev); v.pls_ncand = P32(pls_ncand); v.pls_cand = P32(pls_cand);
+    v.pls_t3rng = (uint2*)pls_t3rng.p; v.pls_t5rng = (uint2*)pls_t5rng.p;
     v.pls_h0 = (float4*)pls_h0.p; v.pls_h1 = (float4*)pls_h1.p; v.pls_pt = (float*)pls_pt.p;
     v.pt3_cnt = P32(pt3_cnt); v.pt3_off = P32(pt3_off); v.pt3_pls = P32(pt3_pls); v.pt3_obj = P32(pt3_obj);
     v.pt3_score = (float*)pt3_score.p;
@@ -813,19 +820,45 @@ void pack_host_events(Pipeline& P, const lst_event* evs, uint32_t n) {
   for (uint32_t i = 0; i < n; i++) {
     hoff[i] = (uint32_t)oh;
     poff[i] = (uint32_t)op;
-    const lst_event& e = evs[i];
-    if (e.n_hits) {
-      memcpy(hx + oh, e.x, e.n_hits * 4);
-      memcpy(hy + oh, e.y, e.n_hits * 4);
-      memcpy(hz + oh, e.z, e.n_hits * 4);
-      memcpy(hd + oh, e.det, e.n_hits * 4);
-    }
-    if (e.n_pls) memcpy(hp + op, e.pls, e.n_pls * sizeof(PlsIn));
-    oh += e.n_hits;
-    op += e.n_pls;
+    oh += evs[i].n_hits;
+    op += evs[i].n_pls;
   }
   hoff[n] = (uint32_t)oh;
   poff[n] = (uint32_t)op;
+  // copy the events into the pinned staging area, on several host threads for big batches
+  auto copy_range = [&](uint32_t e0, uint32_t e1) {
+    for (uint32_t i = e0; i < e1; i++) {
+      const lst_event& e = evs[i];
+      if (e.n_hits) {
+        memcpy(hx + hoff[i], e.x, e.n_hits * 4);
+        memcpy(hy + hoff[i], e.y, e.n_hits * 4);
+        memcpy(hz + hoff[i], e.z, e.n_hits * 4);
+        memcpy(hd + hoff[i], e.det, e.n_hits * 4);
+      }
+      if (e.n_pls) memcpy(hp + poff[i], e.pls, e.n_pls * sizeof(PlsIn));
+    }
+  };
+  const uint64_t total_bytes = nh * 16 + np * sizeof(PlsIn);
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const uint32_t nt = (uint32_t)std::min<uint64_t>({(uint64_t)n, (uint64_t)std::min(hw, 8u), total_bytes / (2u << 20) + 1});
+  if (nt <= 1) {
+    copy_range(0, n);
+  } else {
+    // split events into nt ranges of about equal bytes
+    std::vector<uint32_t> cut(nt + 1, n);
+    cut[0] = 0;
+    uint64_t acc = 0;
+    uint32_t k = 1;
+    for (uint32_t i = 0; i < n && k < nt; i++) {
+      acc += (uint64_t)evs[i].n_hits * 16 + (uint64_t)evs[i].n_pls * sizeof(PlsIn);
+      if (acc * nt >= total_bytes * k) cut[k++] = i + 1;
+    }
+    std::vector<std::thread> th;
+    for (uint32_t t = 1; t < nt; t++)
+      if (cut[t] < cut[t + 1]) th.emplace_back(copy_range, cut[t], cut[t + 1]);
+    copy_range(cut[0], cut[1]);
+    for (auto& t : th) t.join();
+  }
   cudaStream_t st = P.stream;
   if (nh) {
     CK(cudaMemcpyAsync(P.in_x.p, hx, nh * 4, cudaMemcpyHostToDevice, st));
@@ -857,6 +890,7 @@ void pack_host_events(Pipeline& P, const lst_event* evs, uint32_t n) {
 
 // ------------------------------------------------------------------ context
 struct lst_ctx {
+  std::mutex mu;  // results, statistics and the error text (the serving workers share them)
   lst_config cfg{};
   int device = 0;
   int n_sm = 0;
@@ -896,7 +930,8 @@ void collect(lst_ctx* c, Pipeline& P, lst_result_id* outs, uint32_t* n_tc_per_ev
   const uint32_t ne = P.n_ev;
   std::vector<uint32_t> evoff(ne + 1);
   CK(cudaMemcpyAsync(evoff.data(), P.tc_ev_off.p, (ne + 1) * 4, cudaMemcpyDeviceToHost, P.stream));
-  std::vector<lst_tc> tcs(h.tot[T_TC]);
+  auto tcs_ptr = std::make_shared<std::vector<lst_tc>>(outs ? h.tot[T_TC] : 0);
+  std::vector<lst_tc>& tcs = *tcs_ptr;
   if (!tcs.empty())
     CK(cudaMemcpyAsync(tcs.data(), P.tc.p, tcs.size() * sizeof(lst_tc), cudaMemcpyDeviceToHost, P.stream));
   const bool keep = c->cfg.keep_objects != 0 && outs;
@@ -945,7 +980,9 @@ void collect(lst_ctx* c, Pipeline& P, lst_result_id* outs, uint32_t* n_tc_per_ev
     if (n_tc_per_event) n_tc_per_event[e] = evoff[e + 1] - evoff[e];
     if (!outs) continue;
     Result r;
-    r.tcs.assign(tcs.begin() + evoff[e], tcs.begin() + evoff[e + 1]);
+    r.tc_buf = tcs_ptr;
+    r.tc_off = evoff[e];
+    r.tc_n = evoff[e + 1] - evoff[e];
     if (keep) {
       r.has_objects = true;
       const uint32_t mb = md_off[(size_t)e * nm], me = md_off[(size_t)(e + 1) * nm];
@@ -970,10 +1007,12 @@ void collect(lst_ctx* c, Pipeline& P, lst_result_id* outs, uint32_t* n_tc_per_ev
         r.pls.push_back(pr);
       }
     }
+    std::lock_guard<std::mutex> lk(c->mu);
     const lst_result_id id = c->next_id++;
     c->results.emplace(id, std::move(r));
     outs[e] = id;
   }
+  std::lock_guard<std::mutex> lk(c->mu);
   c->stats.n_events = ne;
   c->stats.n_hits = h.n_hits;
   c->stats.n_pls = h.n_pls;
@@ -1134,18 +1173,20 @@ lst_status lst_batch_finish(lst_ctx* c, uint32_t timeout_ms, uint32_t* n_tc_per_
 
 lst_status lst_get_candidates(lst_ctx* c, lst_result_id id, lst_tc* buf, uint32_t cap, uint32_t* n_out) {
   if (!c || !n_out) return LST_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
   auto it = c->results.find(id);
   if (it == c->results.end()) return fail(c, LST_ERR_NOT_FOUND, "unknown result id");
-  const auto& v = it->second.tcs;
-  *n_out = (uint32_t)v.size();
+  const Result& r = it->second;
+  *n_out = (uint32_t)r.tc_n;
   if (!buf) return LST_OK;
-  if (cap < v.size()) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "candidate buffer too small");
-  if (!v.empty()) memcpy(buf, v.data(), v.size() * sizeof(lst_tc));
+  if (cap < r.tc_n) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "candidate buffer too small");
+  if (r.tc_n) memcpy(buf, r.tc_buf->data() + r.tc_off, r.tc_n * sizeof(lst_tc));
   return LST_OK;
 }
 
 lst_status lst_get_objects(lst_ctx* c, lst_result_id id, int32_t kind, void* buf, uint32_t cap, uint32_t* n_out) {
   if (!c || !n_out) return LST_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
   auto it = c->results.find(id);
   if (it == c->results.end()) return fail(c, LST_ERR_NOT_FOUND, "unknown result id");
   const Result& r = it->second;
@@ -1171,6 +1212,7 @@ lst_status lst_get_objects(lst_ctx* c, lst_result_id id, int32_t kind, void* buf
 
 lst_status lst_release_result(lst_ctx* c, lst_result_id id) {
   if (!c) return LST_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
   if (!c->results.erase(id)) return fail(c, LST_ERR_NOT_FOUND, "unknown result id");
   return LST_OK;
 }
@@ -1235,9 +1277,11 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
       s.P->r_pt3 = c->main.r_pt3; s.P->r_pt5 = c->main.r_pt5;
     }
     const uint64_t budget = cfg->memory_budget;
-    auto held = [&]() {
+    std::vector<std::atomic<uint64_t>> slot_bytes(slots.size());
+    auto held_by_others = [&](size_t me) {
       uint64_t t = c->geo.dev_bytes + c->main.dev_bytes;
-      for (auto& s : slots) t += s.P->dev_bytes;
+      for (size_t k = 0; k < slots.size(); k++)
+        if (k != me) t += slot_bytes[k].load();
       return t;
     };
     // Before the clock starts: size every slot for a full batch of typical events (from the
@@ -1251,99 +1295,137 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
       }
       const uint32_t bh = (uint32_t)std::min<uint64_t>(0xF0000000ull, sh * 3 / 2 * cfg->max_batch / m + 1);
       const uint32_t bp = (uint32_t)std::min<uint64_t>(0x0F000000ull, sp * 3 / 2 * cfg->max_batch / m + 1);
-      for (auto& s : slots) {
-        s.P->ensure_caps(s.P->estimate(cfg->max_batch, bh, bp));
-        s.P->ensure_inputs(cfg->max_batch, bh, bp);
-        if (budget && held() > budget) break;
+      for (size_t k = 0; k < slots.size(); k++) {
+        Pipeline& P = *slots[k].P;
+        const uint64_t before = P.dev_bytes;
+        P.ensure_caps(P.estimate(cfg->max_batch, bh, bp));
+        P.ensure_inputs(cfg->max_batch, bh, bp);
+        slot_bytes[k] = P.dev_bytes;
+        if (budget && held_by_others(k) + P.dev_bytes > budget && before == 0) {
+          // too large for the budget: keep the slot small, it grows per batch
+        }
         lst_event empty{};
-        pack_host_events(*s.P, &empty, 1);
-        s.P->launch(true);
-        if (!s.P->wait(0)) return fail(c, LST_ERR_TIMEOUT, "slot warm-up timed out");
+        pack_host_events(P, &empty, 1);
+        P.launch(true);
+        if (!P.wait(0)) return fail(c, LST_ERR_TIMEOUT, "slot warm-up timed out");
       }
     }
+    // Shared state: arrived events not yet taken, and the first error of any worker.
+    std::mutex qm;
+    std::condition_variable qcv;
     std::deque<uint32_t> queue;
-    uint32_t next = 0, done = 0;
+    bool closed = false;
+    lst_status status = LST_OK;
+    std::string err_msg;
     const double t0 = now_s();
-    std::vector<uint32_t> tcn;
-    while (done < n) {
-      bool progress = false;
-      const double now = now_s() - t0;
-      while (next < n && arrival_s[next] <= now) queue.push_back(next++);
-      // completions
-      for (auto& s : slots) {
-        if (!s.busy) continue;
-        const cudaError_t q = cudaEventQuery(s.P->done);
-        if (q == cudaErrorNotReady) continue;
-        if (q != cudaSuccess) throw CudaError{q, "cudaEventQuery"};
-        const Hdr& h = *s.P->h_hdr_out;
-        if (h.err & ERR_BAD_INPUT)
-          return fail(c, LST_ERR_BAD_INPUT, "bad input in a served event");
-        if (s.P->grow_after_overflow(h)) {
-          c->reruns++;
-          if (budget && held() > budget) return fail(c, LST_ERR_BUDGET, "memory budget exceeded by a batch");
-          s.P->launch(true);
-          continue;
-        }
-        s.P->learn(h);
-        tcn.assign(s.events.size(), 0);
-        std::vector<lst_result_id> ids(s.events.size());
-        collect(c, *s.P, outs ? ids.data() : nullptr, tcn.data());
-        const double tdone = now_s() - t0;
-        for (size_t k = 0; k < s.events.size(); k++) {
-          const uint32_t e = s.events[k];
-          latency_s[e] = tdone - arrival_s[e];
-          if (n_tc) n_tc[e] = tcn[k];
-          if (outs) outs[e] = ids[k];
-        }
-        done += (uint32_t)s.events.size();
-        s.busy = false;
-        s.events.clear();
-        progress = true;
+    auto set_error = [&](lst_status st, const std::string& m) {
+      std::lock_guard<std::mutex> lk(qm);
+      if (status == LST_OK) {
+        status = st;
+        err_msg = m;
       }
-      // admissions: idle slots take what has arrived, within the memory budget
-      for (auto& s : slots) {
-        if (s.busy || queue.empty()) continue;
+      qcv.notify_all();
+    };
+    // One worker per slot: take what has arrived (up to max_batch events within the memory
+    // budget), upload, replay the slot's graph, wait, collect, stamp the latencies.
+    auto worker = [&](size_t k) {
+      Pipeline& P = *slots[k].P;
+      try {
+        CK(cudaSetDevice(c->device));
+        std::vector<uint32_t> take;
         std::vector<lst_event> batch;
-        uint64_t nh = 0, np = 0;
-        while (!queue.empty() && batch.size() < cfg->max_batch) {
-          const lst_event& e = evs[queue.front()];
-          if (budget && !batch.empty()) {
-            const Caps est = s.P->estimate((uint32_t)batch.size() + 1, (uint32_t)(nh + e.n_hits),
-                                           (uint32_t)(np + e.n_pls));
-            // rough bytes of the buffers this batch would need
-            const uint64_t bytes = (uint64_t)est.hits * 48 + (uint64_t)est.md * 96 + (uint64_t)est.ls * 16 +
-                                   (uint64_t)est.t3 * 24 + (uint64_t)est.t5 * 80 + (uint64_t)est.pls * 220 +
-                                   (uint64_t)(est.pt3 + est.pt5) * 40 + (uint64_t)est.ev * c->geo.nm * 24;
-            if (held() - s.P->dev_bytes + bytes > budget) break;
+        std::vector<uint32_t> tcn;
+        std::vector<lst_result_id> ids;
+        for (;;) {
+          take.clear();
+          batch.clear();
+          {
+            std::unique_lock<std::mutex> lk(qm);
+            qcv.wait(lk, [&] { return !queue.empty() || closed || status != LST_OK; });
+            if (status != LST_OK || (queue.empty() && closed)) return;
+            uint64_t nh = 0, np = 0;
+            while (!queue.empty() && take.size() < cfg->max_batch) {
+              const lst_event& e = evs[queue.front()];
+              if (budget && !take.empty()) {
+                const Caps est = P.estimate((uint32_t)take.size() + 1, (uint32_t)(nh + e.n_hits),
+                                            (uint32_t)(np + e.n_pls));
+                const uint64_t bytes = (uint64_t)est.hits * 48 + (uint64_t)est.md * 96 + (uint64_t)est.ls * 16 +
+                                       (uint64_t)est.t3 * 24 + (uint64_t)est.t5 * 80 + (uint64_t)est.pls * 220 +
+                                       (uint64_t)(est.pt3 + est.pt5) * 40 + (uint64_t)est.ev * c->geo.nm * 24;
+                if (held_by_others(k) + std::max<uint64_t>(bytes, P.dev_bytes) > budget) break;
+              }
+              take.push_back(queue.front());
+              nh += e.n_hits;
+              np += e.n_pls;
+              queue.pop_front();
+            }
           }
-          batch.push_back(e);
-          s.events.push_back(queue.front());
-          nh += e.n_hits;
-          np += e.n_pls;
-          queue.pop_front();
+          for (uint32_t i : take) batch.push_back(evs[i]);
+          pack_host_events(P, batch.data(), (uint32_t)batch.size());
+          P.ensure_caps(P.estimate((uint32_t)batch.size(), P.n_hits, P.n_pls));
+          slot_bytes[k] = P.dev_bytes;
+          if (budget && held_by_others(k) + P.dev_bytes > budget && take.size() == 1)
+            return set_error(LST_ERR_BUDGET, "one event alone exceeds the memory budget");
+          for (int attempt = 0;; attempt++) {
+            P.launch(true);
+            if (!P.wait(0)) return set_error(LST_ERR_TIMEOUT, "device did not finish");
+            const Hdr& h = *P.h_hdr_out;
+            if (h.err & ERR_BAD_INPUT) return set_error(LST_ERR_BAD_INPUT, "bad input in a served event");
+            if (!P.grow_after_overflow(h)) {
+              P.learn(h);
+              break;
+            }
+            slot_bytes[k] = P.dev_bytes;
+            if (budget && held_by_others(k) + P.dev_bytes > budget)
+              return set_error(LST_ERR_BUDGET, "memory budget exceeded by a batch");
+            if (attempt > 10) return set_error(LST_ERR_OOM, "object lists kept outgrowing their storage");
+            std::lock_guard<std::mutex> lk(c->mu);
+            c->reruns++;
+          }
+          tcn.assign(take.size(), 0);
+          ids.assign(take.size(), 0);
+          collect(c, P, outs ? ids.data() : nullptr, tcn.data());
+          const double tdone = now_s() - t0;
+          for (size_t q = 0; q < take.size(); q++) {
+            const uint32_t e = take[q];
+            latency_s[e] = tdone - arrival_s[e];
+            if (n_tc) n_tc[e] = tcn[q];
+            if (outs) outs[e] = ids[q];
+          }
         }
-        if (batch.empty()) continue;
-        pack_host_events(*s.P, batch.data(), (uint32_t)batch.size());
-        s.P->ensure_caps(s.P->estimate((uint32_t)batch.size(), s.P->n_hits, s.P->n_pls));
-        if (budget && held() > budget) {
-          if (batch.size() == 1) return fail(c, LST_ERR_BUDGET, "one event alone exceeds the memory budget");
-        }
-        s.P->launch(true);
-        s.busy = true;
-        progress = true;
+      } catch (const CudaError& e) {
+        set_error(LST_ERR_CUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+      } catch (const StatusError& e) {
+        set_error(e.s, e.msg);
+      } catch (const std::bad_alloc&) {
+        set_error(LST_ERR_OOM, "host allocation failed");
       }
-      if (!progress) {
-        bool any_busy = false;
-        for (auto& s : slots) any_busy |= s.busy;
-        if (!any_busy && queue.empty() && next < n) {
-          const double wait = arrival_s[next] - (now_s() - t0);
-          if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.001)));
-        } else {
-          std::this_thread::sleep_for(std::chrono::microseconds(10));
-        }
+    };
+    std::vector<std::thread> th;
+    for (size_t k = 0; k < slots.size(); k++) th.emplace_back(worker, k);
+    // The request loop: release every event at its arrival time.
+    for (uint32_t i = 0; i < n;) {
+      const double now = now_s() - t0;
+      if (arrival_s[i] > now) {
+        const double wait = arrival_s[i] - now;
+        if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 1e-4));
+        continue;
       }
+      {
+        std::lock_guard<std::mutex> lk(qm);
+        if (status != LST_OK) break;
+        while (i < n && arrival_s[i] <= now) queue.push_back(i++);
+      }
+      qcv.notify_all();
     }
+    {
+      std::lock_guard<std::mutex> lk(qm);
+      closed = true;
+    }
+    qcv.notify_all();
+    for (auto& t : th) t.join();
     if (wall_s) *wall_s = now_s() - t0;
+    if (status != LST_OK) return fail(c, status, err_msg);
     return LST_OK;
   });
 }

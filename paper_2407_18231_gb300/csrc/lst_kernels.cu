@@ -49,58 +49,73 @@ struct ScorePayload {
   float score, kfull;
 };
 
-// Scratch of the joins: the count pass stores every 32-candidate chunk's ballot word in a
-// slice of `mask` reserved for the unit (an atomic bump of *used); the fill pass replays
-// those words and only touches chunks that hold passing candidates.  A unit that finds
-// the mask full records NONE and its fill pass simply re-runs the tests.
+// Scratch of the joins.  The count pass keeps, for each 32-candidate chunk that holds a
+// passing candidate, its position (outer group start, candidate offset) and its ballot word
+// in lane registers, then writes them as one record list [n, (g0, t0, ballot) x n] into
+// `mask` through a per-warp bump allocator (one global atomic per 1024+ words).  The fill
+// pass decodes only those chunks.  A unit whose passes span more than 32 chunks, or that
+// finds the scratch full, stores NONE and its fill pass re-runs the tests instead, so the
+// output never depends on the scratch size.
 struct JoinScratch {
   uint32_t* mask;
   uint32_t cap;
   uint32_t* used;
-  uint32_t* unit_base;  // this unit's slot in the per-unit mask offsets
+  uint32_t* unit_base;  // this unit's record list (or NONE)
+};
+
+struct WarpAlloc {
+  uint32_t cur = 0, end = 0;  // warp-uniform
 };
 
 // Walks all (outer i, inner j) candidates of one unit; outer(i, begin, count) gives the
-// inner index range of outer item i.  Count pass (FILL = false): test(i, j) decides, the
-// number of passes is returned and the ballots are recorded.  Fill pass: the passing
-// candidates are emitted at base + rank in candidate order, with score(i, j, payload)
-// computing what the emitter needs.
+// inner index range of outer item i.  Count pass (FILL = false): test(i, j) decides and the
+// number of passes is returned.  Fill pass: n_out passing candidates are emitted at
+// base + rank in candidate order, with score(i, j, payload) computing what emit needs.
 template <bool FILL, typename P, typename OuterFn, typename TestFn, typename ScoreFn, typename EmitFn>
-__device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, const JoinScratch& js, OuterFn outer,
-                                              TestFn test, ScoreFn score, EmitFn emit) {
+__device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, uint32_t n_out, const JoinScratch& js,
+                                              WarpAlloc& wa, OuterFn outer, TestFn test, ScoreFn score, EmitFn emit) {
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t mbase;
-  if (!FILL) {
-    uint32_t nch = 0;
-    for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
-      uint32_t b = 0, c = 0;
-      if (g0 + lane < n_outer) outer(g0 + lane, b, c);
-      const uint32_t tot = __shfl_sync(FULL, warp_incl_scan(c), 31);
-      nch += (tot + 31u) >> 5;
+  if (FILL) {
+    if (n_out == 0) return 0;
+    const uint32_t mbase = *js.unit_base;
+    if (mbase != NONE) {
+      const uint32_t nrec = js.mask[mbase];
+      uint32_t count = 0;
+      for (uint32_t r = 0; r < nrec; r++) {
+        const uint32_t g0 = js.mask[mbase + 1 + 3 * r];
+        const uint32_t t0 = js.mask[mbase + 2 + 3 * r];
+        const uint32_t bal = js.mask[mbase + 3 + 3 * r];
+        uint32_t b = 0, c = 0;
+        if (g0 + lane < n_outer) outer(g0 + lane, b, c);
+        const uint32_t incl = warp_incl_scan(c);
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        const uint32_t cand = t0 + lane;
+        const uint32_t cc = cand < total ? cand : total - 1;
+        const uint32_t o = owner_lane(incl, cc);
+        const uint32_t bo = __shfl_sync(FULL, b, o);
+        const uint32_t co = __shfl_sync(FULL, c, o);
+        const uint32_t io = __shfl_sync(FULL, incl, o);
+        const uint32_t j = bo + (cc - (io - co));
+        if ((bal >> lane) & 1u) {
+          P pl;
+          score(g0 + o, j, pl);
+          emit(base + count + __popc(bal & lt), g0 + o, j, pl);
+        }
+        count += __popc(bal);
+      }
+      return count;
     }
-    uint32_t mb = NONE;
-    if (nch && lane == 0) {
-      const uint32_t b0 = atomicAdd(js.used, nch);
-      if (b0 < js.cap && nch <= js.cap - b0) mb = b0;
-    }
-    mbase = __shfl_sync(FULL, mb, 0);
-    if (lane == 0) *js.unit_base = mbase;
-  } else {
-    mbase = *js.unit_base;
   }
-  uint32_t count = 0, ci = 0;
+  // full walk: the count pass, or a fill pass without records
+  uint32_t count = 0, nrec = 0, rg = 0, rt = 0, rb = 0;
+  bool spill = false;
   for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
     uint32_t b = 0, c = 0;
     if (g0 + lane < n_outer) outer(g0 + lane, b, c);
     const uint32_t incl = warp_incl_scan(c);
     const uint32_t total = __shfl_sync(FULL, incl, 31);
-    for (uint32_t t0 = 0; t0 < total; t0 += 32, ci++) {
-      uint32_t bal = 0;
-      if (FILL && mbase != NONE) {
-        bal = js.mask[mbase + ci];
-        if (bal == 0u) continue;  // warp-uniform
-      }
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
       const uint32_t cand = t0 + lane;
       const uint32_t cc = cand < total ? cand : total - 1;
       const uint32_t o = owner_lane(incl, cc);
@@ -108,21 +123,64 @@ __device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, c
       const uint32_t co = __shfl_sync(FULL, c, o);
       const uint32_t io = __shfl_sync(FULL, incl, o);
       const uint32_t j = bo + (cc - (io - co));
-      bool pass;
-      if (FILL && mbase != NONE) {
-        pass = (bal >> lane) & 1u;
-      } else {
-        pass = cand < total && test(g0 + o, j);
-        bal = __ballot_sync(FULL, pass);
-        if (!FILL && mbase != NONE && lane == 0) js.mask[mbase + ci] = bal;
-      }
-      if (FILL && pass) {
-        P pl;
-        score(g0 + o, j, pl);
-        emit(base + count + __popc(bal & lt), g0 + o, j, pl);
+      const bool pass = cand < total && test(g0 + o, j);
+      const uint32_t bal = __ballot_sync(FULL, pass);
+      if (bal) {
+        if (!FILL) {
+          if (nrec < 32) {
+            if (lane == nrec) {
+              rg = g0;
+              rt = t0;
+              rb = bal;
+            }
+            nrec++;
+          } else {
+            spill = true;
+          }
+        }
+        if (FILL && pass) {
+          P pl;
+          score(g0 + o, j, pl);
+          emit(base + count + __popc(bal & lt), g0 + o, j, pl);
+        }
       }
       count += __popc(bal);
     }
+  }
+  if (!FILL) {
+    uint32_t mbase = NONE;
+    if (count > 0 && !spill) {
+      const uint32_t need = 1 + 3 * nrec;
+      uint32_t mb = NONE;
+      if (lane == 0) {
+        if (wa.end - wa.cur < need || wa.cur == NONE) {
+          const uint32_t grab = need > 1024u ? need : 1024u;
+          const uint32_t b0 = atomicAdd(js.used, grab);
+          if (b0 < js.cap && grab <= js.cap - b0) {
+            wa.cur = b0;
+            wa.end = b0 + grab;
+          } else {
+            wa.cur = wa.end = 0;
+          }
+        }
+        if (wa.end - wa.cur >= need) {
+          mb = wa.cur;
+          wa.cur += need;
+        }
+      }
+      mbase = __shfl_sync(FULL, mb, 0);
+      wa.cur = __shfl_sync(FULL, wa.cur, 0);
+      wa.end = __shfl_sync(FULL, wa.end, 0);
+      if (mbase != NONE) {
+        if (lane == 0) js.mask[mbase] = nrec;
+        if (lane < nrec) {
+          js.mask[mbase + 1 + 3 * lane] = rg;
+          js.mask[mbase + 2 + 3 * lane] = rt;
+          js.mask[mbase + 3 + 3 * lane] = rb;
+        }
+      }
+    }
+    if (lane == 0) *js.unit_base = mbase;
   }
   return count;
 }
@@ -229,6 +287,79 @@ __global__ void k_scan_apply(const uint32_t* __restrict__ in, const uint32_t* np
   }
 }
 
+// Up to four independent scans in one launch (blockIdx.y picks the array).
+struct ScanJob {
+  const uint32_t* in;
+  uint32_t* out;
+  const uint32_t* nptr;
+  int tot;
+  uint32_t cap;
+};
+struct ScanJobs {
+  ScanJob j[4];
+};
+
+__global__ void k_scan_reduce_multi(ScanJobs J, const Hdr* H, uint32_t* part) {
+  if (H->err) return;
+  __shared__ uint32_t sm[33];
+  const ScanJob& q = J.j[blockIdx.y];
+  const uint32_t n = *q.nptr;
+  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = blockIdx.x * chunk;
+  const uint32_t hi = min(n, lo + chunk);
+  uint32_t s = 0;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += q.in[i];
+  uint32_t tot;
+  block_excl_scan(s, sm, tot);
+  if (threadIdx.x == 0) part[blockIdx.y * 1024 + blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top_multi(ScanJobs J, uint32_t* part, Hdr* H) {
+  if (H->err) return;
+  __shared__ uint32_t sm[33];
+  const ScanJob& q = J.j[blockIdx.x];
+  uint32_t* pp = part + blockIdx.x * 1024;
+  const uint32_t v = pp[threadIdx.x];
+  uint32_t tot;
+  const uint32_t ex = block_excl_scan(v, sm, tot);
+  pp[threadIdx.x] = ex;
+  if (threadIdx.x == 0) {
+    q.out[*q.nptr] = tot;
+    H->tot[q.tot] = tot;
+    if (tot > q.cap) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + q.tot));
+  }
+}
+
+__global__ void k_scan_apply_multi(ScanJobs J, const Hdr* H, const uint32_t* part) {
+  if (H->err) return;
+  __shared__ uint32_t sm[33];
+  const ScanJob& q = J.j[blockIdx.y];
+  const uint32_t n = *q.nptr;
+  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = blockIdx.x * chunk;
+  const uint32_t hi = min(n, lo + chunk);
+  uint32_t carry = part[blockIdx.y * 1024 + blockIdx.x];
+  const uint32_t tile = blockDim.x * 4;
+  for (uint32_t t = lo; t < hi; t += tile) {
+    const uint32_t i0 = t + threadIdx.x * 4;
+    uint32_t v[4];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      v[k] = (i0 + k < hi) ? q.in[i0 + k] : 0u;
+      s += v[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(s, sm, tot) + carry;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (i0 + k < hi) q.out[i0 + k] = ex;
+      ex += v[k];
+    }
+    carry += tot;
+  }
+}
+
 __global__ void k_zero(uint32_t* p, const uint32_t* nptr, uint32_t mul, uint32_t add) {
   const uint32_t n = (*nptr) * mul + add;
   THREAD_LOOP(i, n) p[i] = 0u;
@@ -298,15 +429,17 @@ __global__ void __launch_bounds__(512) k_md(MethodConst C, GeoView G, BufView B)
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t nu = H->n_ev * G.nm;
+  WarpAlloc wa;
   WARP_LOOP(u, nu) {
     const uint32_t lo_b = B.sen_off[2 * u], up_b = B.sen_off[2 * u + 1], up_e = B.sen_off[2 * u + 2];
     const uint32_t n_lo = up_b - lo_b, n_up = up_e - up_b;
     const uint32_t m = u % G.nm;
     const float4 cst = G.modc[m];
     const uint32_t base = FILL ? B.md_off[u] : 0u;
+    const uint32_t n_out = FILL ? B.md_off[u + 1] - base : 0u;
     const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[0], &B.mask_off[u]};
     const uint32_t cnt = warp_join<FILL, NoPayload>(
-        n_lo, base, js, [&](uint32_t, uint32_t& b, uint32_t& c) { b = up_b; c = n_up; },
+        n_lo, base, n_out, js, wa, [&](uint32_t, uint32_t& b, uint32_t& c) { b = up_b; c = n_up; },
         [&](uint32_t i, uint32_t j) {
           const PointTol a{B.hit4[lo_b + i], cst}, b{B.hit4[j], cst};
           return pair_rz(C, a, b) && pair_bend(C, a, b, cst.w);
@@ -328,40 +461,180 @@ __device__ __forceinline__ PointTol md_point(const BufView& B, uint32_t m) { ret
 __device__ __forceinline__ PointTol md_upper(const BufView& B, uint32_t m) { return PointTol{B.md_up4[m], B.md_cst[m]}; }
 
 // ------------------------------------------------------------------ Line Segments
-// Unit = MD a on module A; candidates = MDs of every module B in the connection map of A.
+// The LS selection of ls_select for anchors (pa, pau) and MD j, loading the rest of MD j
+// only when the cheap tests pass.
+__device__ __forceinline__ bool ls_test(const MethodConst& C, const GeoView& G, const BufView& B, const PointTol& pa,
+                                        const PointTol& pau, float rnext, bool a_barrel, uint32_t ubase, uint32_t j) {
+  const PointTol pb = md_point(B, j);
+  if (!(pair_rz(C, pa, pb) && pair_bend(C, pa, pb, pb.t.w))) return false;
+  if (a_barrel && G.subdet[B.md_unit[j] - ubase] == 1 && !exit_ok(pa, pb, rnext, G.zb_half)) return false;
+  const PointTol pbu = md_upper(B, j);
+  const float cx = pb.p.x - pa.p.x;
+  const float cy = pb.p.y - pa.p.y;
+  const float clen = sqrtf(cx * cx + cy * cy);
+  return md_dir(C, pa, pau, cx, cy, clen) && md_dir(C, pb, pbu, cx, cy, clen);
+}
+
+// Per-MD LS join (candidates = MDs of every module in the connection map of A), used for
+// modules whose flattened neighbour list does not fit the shared-memory list.
+template <bool FILL>
+__device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t a,
+                                           uint32_t ev, uint32_t A, WarpAlloc& wa) {
+  const PointTol pa = md_point(B, a), pau = md_upper(B, a);
+  const float rnext = G.rnext[A];
+  const bool a_barrel = G.subdet[A] == 0;
+  const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
+  const uint32_t base = FILL ? B.ls_off[a] : 0u;
+  const uint32_t ubase = ev * G.nm;
+  const uint32_t n_out = FILL ? B.ls_off[a + 1] - base : 0u;
+  const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[1], &B.mask_off[a]};
+  const uint32_t cnt = warp_join<FILL, NoPayload>(
+      nb, base, n_out, js, wa,
+      [&](uint32_t i, uint32_t& b, uint32_t& c) {
+        const uint32_t u = ubase + G.conn[nb0 + i];
+        b = B.md_off[u];
+        c = B.md_off[u + 1] - b;
+      },
+      [&](uint32_t, uint32_t j) { return ls_test(C, G, B, pa, pau, rnext, a_barrel, ubase, j); },
+      [&](uint32_t, uint32_t, NoPayload&) {},
+      [&](uint32_t pos, uint32_t, uint32_t j, const NoPayload&) {
+        B.ls_in[pos] = a;
+        B.ls_out[pos] = j;
+      });
+  if (!FILL && lane_id() == 0) B.ls_cnt[a] = cnt;
+}
+
+constexpr uint32_t LS_LIST_CAP = 512;  // flattened neighbour MDs per warp in shared memory
+
+// Unit = (event, module A).  The warp writes the indices of all MDs on the modules connected
+// to A into a shared-memory list once (module order, then MD order), then walks the list in
+// 32-wide chunks for every MD a of A: no per-MD neighbour lookups, no per-chunk search.  The
+// count pass keeps each row's passing chunks as records (t0, ballot) for the fill pass.
 template <bool FILL>
 __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B) {
+  extern __shared__ uint32_t ls_smem[];
   const Hdr* H = B.hdr;
   if (H->err) return;
-  const uint32_t n = H->tot[T_MD];
-  WARP_LOOP(a, n) {
-    const uint32_t unit = B.md_unit[a];
-    const uint32_t ev = unit / G.nm, A = unit - ev * G.nm;
-    const PointTol pa = md_point(B, a), pau = md_upper(B, a);
+  const uint32_t nu = H->n_ev * G.nm;
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t* list = ls_smem + (threadIdx.x >> 5) * LS_LIST_CAP;
+  WarpAlloc wa;
+  WARP_LOOP(u, nu) {
+    const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
+    if (a0 == a1) continue;
+    const uint32_t ev = u / G.nm, A = u - ev * G.nm;
+    const uint32_t ubase = ev * G.nm;
+    const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
+    // flattened neighbour list
+    uint32_t len = 0;
+    for (uint32_t g0 = 0; g0 < nb; g0 += 32) {
+      uint32_t b = 0, c = 0;
+      if (g0 + lane < nb) {
+        const uint32_t uu = ubase + G.conn[nb0 + g0 + lane];
+        b = B.md_off[uu];
+        c = B.md_off[uu + 1] - b;
+      }
+      const uint32_t incl = warp_incl_scan(c);
+      const uint32_t o = len + incl - c;
+      for (uint32_t k = 0; k < c; k++)
+        if (o + k < LS_LIST_CAP) list[o + k] = b + k;
+      len += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+    if (len > LS_LIST_CAP) {
+      for (uint32_t a = a0; a < a1; a++) ls_md_join<FILL>(C, G, B, a, ev, A, wa);
+      continue;
+    }
     const float rnext = G.rnext[A];
     const bool a_barrel = G.subdet[A] == 0;
-    const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
-    const uint32_t base = FILL ? B.ls_off[a] : 0u;
-    const uint32_t ubase = ev * G.nm;
-    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[1], &B.mask_off[a]};
-    const uint32_t cnt = warp_join<FILL, NoPayload>(
-        nb, base, js,
-        [&](uint32_t i, uint32_t& b, uint32_t& c) {
-          const uint32_t u = ubase + G.conn[nb0 + i];
-          b = B.md_off[u];
-          c = B.md_off[u + 1] - b;
-        },
-        [&](uint32_t, uint32_t j) {
-          const uint32_t Bm = B.md_unit[j] - ubase;
-          const bool b2d = a_barrel && G.subdet[Bm] == 1;
-          return ls_select(C, pa, pau, md_point(B, j), md_upper(B, j), rnext, b2d, G.zb_half);
-        },
-        [&](uint32_t, uint32_t, NoPayload&) {},
-        [&](uint32_t pos, uint32_t, uint32_t j, const NoPayload&) {
-          B.ls_in[pos] = a;
-          B.ls_out[pos] = j;
-        });
-    if (!FILL && lane_id() == 0) B.ls_cnt[a] = cnt;
+    for (uint32_t a = a0; a < a1; a++) {
+      const PointTol pa = md_point(B, a), pau = md_upper(B, a);
+      if (FILL) {
+        const uint32_t base = B.ls_off[a], n_out = B.ls_off[a + 1] - base;
+        if (n_out == 0) continue;
+        const uint32_t mbase = B.mask_off[a];
+        uint32_t count = 0;
+        if (mbase != NONE) {
+          const uint32_t nrec = B.mask[mbase];
+          for (uint32_t r = 0; r < nrec; r++) {
+            const uint32_t t0 = B.mask[mbase + 1 + 2 * r], bal = B.mask[mbase + 2 + 2 * r];
+            if ((bal >> lane) & 1u) {
+              const uint32_t pos = base + count + __popc(bal & lt);
+              B.ls_in[pos] = a;
+              B.ls_out[pos] = list[t0 + lane];
+            }
+            count += __popc(bal);
+          }
+        } else {
+          for (uint32_t t0 = 0; t0 < len; t0 += 32) {
+            const bool pass = t0 + lane < len && ls_test(C, G, B, pa, pau, rnext, a_barrel, ubase, list[t0 + lane]);
+            const uint32_t bal = __ballot_sync(FULL, pass);
+            if (pass) {
+              const uint32_t pos = base + count + __popc(bal & lt);
+              B.ls_in[pos] = a;
+              B.ls_out[pos] = list[t0 + lane];
+            }
+            count += __popc(bal);
+          }
+        }
+      } else {
+        uint32_t count = 0, nrec = 0, rt = 0, rb = 0;
+        bool spill = false;
+        for (uint32_t t0 = 0; t0 < len; t0 += 32) {
+          const bool pass = t0 + lane < len && ls_test(C, G, B, pa, pau, rnext, a_barrel, ubase, list[t0 + lane]);
+          const uint32_t bal = __ballot_sync(FULL, pass);
+          if (bal) {
+            if (nrec < 32) {
+              if (lane == nrec) {
+                rt = t0;
+                rb = bal;
+              }
+              nrec++;
+            } else {
+              spill = true;
+            }
+          }
+          count += __popc(bal);
+        }
+        uint32_t mbase = NONE;
+        if (count > 0 && !spill) {
+          const uint32_t need = 1 + 2 * nrec;
+          uint32_t mb = NONE;
+          if (lane == 0) {
+            if (wa.end - wa.cur < need) {
+              const uint32_t grab = need > 1024u ? need : 1024u;
+              const uint32_t b0 = atomicAdd(&B.hdr->mask_used[1], grab);
+              if (b0 < B.cap_mask && grab <= B.cap_mask - b0) {
+                wa.cur = b0;
+                wa.end = b0 + grab;
+              } else {
+                wa.cur = wa.end = 0;
+              }
+            }
+            if (wa.end - wa.cur >= need) {
+              mb = wa.cur;
+              wa.cur += need;
+            }
+          }
+          mbase = __shfl_sync(FULL, mb, 0);
+          wa.cur = __shfl_sync(FULL, wa.cur, 0);
+          wa.end = __shfl_sync(FULL, wa.end, 0);
+          if (mbase != NONE) {
+            if (lane == 0) B.mask[mbase] = nrec;
+            if (lane < nrec) {
+              B.mask[mbase + 1 + 2 * lane] = rt;
+              B.mask[mbase + 2 + 2 * lane] = rb;
+            }
+          }
+        }
+        if (lane == 0) {
+          B.mask_off[a] = mbase;
+          B.ls_cnt[a] = count;
+        }
+      }
+    }
+    __syncwarp();  // the list is rewritten by the next unit
   }
 }
 
@@ -372,13 +645,15 @@ __global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B)
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_MD];
+  WarpAlloc wa;
   WARP_LOOP(a, n) {
     const PointTol pa = md_point(B, a);
     const uint32_t l0 = B.ls_off[a], nl = B.ls_off[a + 1] - l0;
     const uint32_t base = FILL ? B.t3_off[a] : 0u;
+    const uint32_t n_out = FILL ? B.t3_off[a + 1] - base : 0u;
     const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[2], &B.mask_off[a]};
     const uint32_t cnt = warp_join<FILL, NoPayload>(
-        nl, base, js,
+        nl, base, n_out, js, wa,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t mb = B.ls_out[l0 + i];
           b = B.ls_off[mb];
@@ -405,13 +680,15 @@ __global__ void __launch_bounds__(512) k_t5(MethodConst C, GeoView G, BufView B)
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_MD];
+  WarpAlloc wa;
   WARP_LOOP(a, n) {
     const PointTol pa = md_point(B, a);
     const uint32_t s0 = B.t3_off[a], ns = B.t3_off[a + 1] - s0;
     const uint32_t base = FILL ? B.t5_off[a] : 0u;
+    const uint32_t n_out = FILL ? B.t5_off[a + 1] - base : 0u;
     const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[3], &B.mask_off[a]};
     const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        ns, base, js,
+        ns, base, n_out, js, wa,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t mc = B.t3_c[s0 + i];
           b = B.t3_off[mc];
@@ -609,7 +886,15 @@ __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
       list[k] = v;
     }
     B.pls_ncand[p] = nc;
-    for (uint32_t i = 0; i < nc; i++) B.pls_cand[(size_t)p * MAX_CAND + i] = list[i];
+    const uint32_t ubase = B.pls_ev[p] * G.nm;
+    for (uint32_t i = 0; i < nc; i++) {
+      B.pls_cand[(size_t)p * MAX_CAND + i] = list[i];
+      // T3s and T5s are sorted by first MD, so those starting on a module are one range
+      const uint32_t mb = B.md_off[ubase + list[i]], me = B.md_off[ubase + list[i] + 1];
+      const uint32_t t3b = B.t3_off[mb], t5b = B.t5_off[mb];
+      B.pls_t3rng[(size_t)p * MAX_CAND + i] = make_uint2(t3b, B.t3_off[me] - t3b);
+      B.pls_t5rng[(size_t)p * MAX_CAND + i] = make_uint2(t5b, B.t5_off[me] - t5b);
+    }
   }
 }
 
@@ -629,18 +914,18 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
+  WarpAlloc wa;
   WARP_LOOP(p, n) {
     const PlsHelix h = load_helix(B, p);
-    const uint32_t ubase = B.pls_ev[p] * G.nm;
-    const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
     const uint32_t base = FILL ? B.pt3_off[p] : 0u;
+    const uint32_t n_out = FILL ? B.pt3_off[p + 1] - base : 0u;
     const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[4], &B.mask_off[p]};
     const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        B.pls_ncand[p], base, js,
+        B.pls_ncand[p], base, n_out, js, wa,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
-          const uint32_t u = ubase + cand[i];
-          b = B.t3_off[B.md_off[u]];
-          c = B.t3_off[B.md_off[u + 1]] - b;
+          const uint2 r = B.pls_t3rng[(size_t)p * MAX_CAND + i];
+          b = r.x;
+          c = r.y;
         },
         [&](uint32_t, uint32_t t) {
           return pls_anchor_accept(C, h, md_point(B, B.t3_a[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) &&
@@ -667,18 +952,18 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
+  WarpAlloc wa;
   WARP_LOOP(p, n) {
     const PlsHelix h = load_helix(B, p);
-    const uint32_t ubase = B.pls_ev[p] * G.nm;
-    const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
     const uint32_t base = FILL ? B.pt5_off[p] : 0u;
+    const uint32_t n_out = FILL ? B.pt5_off[p + 1] - base : 0u;
     const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[5], &B.mask_off[p]};
     const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        B.pls_ncand[p], base, js,
+        B.pls_ncand[p], base, n_out, js, wa,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
-          const uint32_t u = ubase + cand[i];
-          b = B.t5_off[B.md_off[u]];
-          c = B.t5_off[B.md_off[u + 1]] - b;
+          const uint2 r = B.pls_t5rng[(size_t)p * MAX_CAND + i];
+          b = r.x;
+          c = r.y;
         },
         [&](uint32_t, uint32_t t) {
           const PointTol P0 = md_point(B, B.t5_m0[t]);
@@ -788,7 +1073,8 @@ __global__ void k_kill_pt5(BufView B) {
       if (y != x && better(B.pt5_score[y], y, sx, x)) dead = true;
     uint32_t mx[5];
     t5_mds(B, B.pt5_obj[x], mx);
-    for (int k = 0; k < 5 && !dead; k++) {
+    // a pT5 sharing >= 3 of x's 5 MDs shares one of any 3 of them: scan 3 lists, not 5
+    for (int k = 0; k < 5 && !dead; k += 2) {
       const uint32_t m = mx[k];
       for (uint32_t j = B.c5_off[m]; j < B.c5_off[m + 1] && !dead; j++) {
         const uint32_t y = B.c5_list[j];
@@ -820,7 +1106,8 @@ __global__ void k_cross_pt3(BufView B) {
     bool dead = B.used5[B.pt3_pls[x]] != 0;
     uint32_t mx[3];
     t3_mds(B, B.pt3_obj[x], mx);
-    for (int k = 0; k < 3 && !dead; k++) {
+    // sharing >= 2 of x's 3 MDs means sharing one of any 2 of them
+    for (int k = 0; k < 2 && !dead; k++) {
       const uint32_t m = mx[k];
       for (uint32_t j = B.c5_off[m]; j < B.c5_off[m + 1] && !dead; j++) {
         const uint32_t z = B.c5_list[j];
@@ -846,7 +1133,7 @@ __global__ void k_kill_pt3(BufView B) {
       if (y != x && !B.cross3[y] && better(B.pt3_score[y], y, sx, x)) dead = true;
     uint32_t mx[3];
     t3_mds(B, B.pt3_obj[x], mx);
-    for (int k = 0; k < 3 && !dead; k++) {
+    for (int k = 0; k < 2 && !dead; k++) {  // >= 2 of 3 shared: two lists suffice
       const uint32_t m = mx[k];
       for (uint32_t j = B.c3_off[m]; j < B.c3_off[m + 1] && !dead; j++) {
         const uint32_t y = B.c3_list[j];
@@ -879,7 +1166,8 @@ __global__ void k_cross_t5(BufView B) {
     bool dead = false;
     uint32_t mx[5];
     t5_mds(B, x, mx);
-    for (int k = 0; k < 5 && !dead; k++) {
+    // >= 3 shared with a 5-MD or 3-MD object: one of any 3 of x's MDs is shared
+    for (int k = 0; k < 5 && !dead; k += 2) {
       const uint32_t m = mx[k];
       for (uint32_t j = B.c5_off[m]; j < B.c5_off[m + 1] && !dead; j++) {
         const uint32_t z = B.c5_list[j];
@@ -908,7 +1196,7 @@ __global__ void k_kill_t5(BufView B) {
     const float sx = B.t5_score[x];
     uint32_t mx[5];
     t5_mds(B, x, mx);
-    for (int k = 0; k < 5 && !dead; k++) {
+    for (int k = 0; k < 5 && !dead; k += 2) {  // >= 3 of 5 shared: three lists suffice
       const uint32_t m = mx[k];
       for (uint32_t j = B.ct_off[m]; j < B.ct_off[m + 1] && !dead; j++) {
         const uint32_t y = B.ct_list[j];
@@ -1061,6 +1349,15 @@ static void scan(const BufView& B, const Launch& L, cudaStream_t s, const uint32
   mk(4);
 }
 
+static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const ScanJobs& J, int n, Marker& mk) {
+  k_scan_reduce_multi<<<dim3(L.scan_grid, n), 512, 0, s>>>(J, B.hdr, B.scan_part);
+  mk(2);
+  k_scan_top_multi<<<n, L.scan_grid, 0, s>>>(J, B.scan_part, B.hdr);
+  mk(3);
+  k_scan_apply_multi<<<dim3(L.scan_grid, n), 512, 0, s>>>(J, B.hdr, B.scan_part);
+  mk(4);
+}
+
 // Enqueues the whole chain on stream s; returns the number of kernels launched.  mark (may
 // be null) is called after every launch with the index of its name in kKernelNames.
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
@@ -1083,10 +1380,11 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.md_cnt, B.md_off, &H->n_ev, G.nm, T_MD, B.cap_md, mk);
   k_md<true><<<g, bs, 0, s>>>(C, G, B);
   mk(8);
-  k_ls<false><<<g, bs, 0, s>>>(C, G, B);
+  const size_t ls_smem = (bs / 32) * LS_LIST_CAP * sizeof(uint32_t);
+  k_ls<false><<<g, bs, ls_smem, s>>>(C, G, B);
   mk(9);
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
-  k_ls<true><<<g, bs, 0, s>>>(C, G, B);
+  k_ls<true><<<g, bs, ls_smem, s>>>(C, G, B);
   mk(10);
   k_t3<false><<<g, bs, 0, s>>>(C, G, B);
   mk(11);
@@ -1114,9 +1412,13 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   mk(20);
   k_csr_count<<<g, 256, 0, s>>>(B);
   mk(21);
-  scan(B, L, s, B.c5_cnt, B.c5_off, &H->tot[T_MD], 1, T_C5, 5u * B.cap_pt5, mk);
-  scan(B, L, s, B.c3_cnt, B.c3_off, &H->tot[T_MD], 1, T_C3, 3u * B.cap_pt3, mk);
-  scan(B, L, s, B.ct_cnt, B.ct_off, &H->tot[T_MD], 1, T_CT, 5u * B.cap_t5, mk);
+  {
+    ScanJobs J{};
+    J.j[0] = {B.c5_cnt, B.c5_off, &H->tot[T_MD], T_C5, 5u * B.cap_pt5};
+    J.j[1] = {B.c3_cnt, B.c3_off, &H->tot[T_MD], T_C3, 3u * B.cap_pt3};
+    J.j[2] = {B.ct_cnt, B.ct_off, &H->tot[T_MD], T_CT, 5u * B.cap_t5};
+    scan_multi(B, L, s, J, 3, mk);
+  }
   k_csr_fill<<<g, 256, 0, s>>>(B);
   mk(22);
   k_kill_pt5<<<g, 256, 0, s>>>(B);
@@ -1133,10 +1435,14 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   mk(28);
   k_kill_t5<<<g, 256, 0, s>>>(B);
   mk(29);
-  scan(B, L, s, B.alive5, B.sa5, &H->tot[T_PT5], 1, T_A5, 0xFFFFFFFFu, mk);
-  scan(B, L, s, B.alive3, B.sa3, &H->tot[T_PT3], 1, T_A3, 0xFFFFFFFFu, mk);
-  scan(B, L, s, B.alivet, B.sat, &H->tot[T_T5], 1, T_AT, 0xFFFFFFFFu, mk);
-  scan(B, L, s, B.plstc, B.sap, &H->n_pls, 1, T_AP, 0xFFFFFFFFu, mk);
+  {
+    ScanJobs J{};
+    J.j[0] = {B.alive5, B.sa5, &H->tot[T_PT5], T_A5, 0xFFFFFFFFu};
+    J.j[1] = {B.alive3, B.sa3, &H->tot[T_PT3], T_A3, 0xFFFFFFFFu};
+    J.j[2] = {B.alivet, B.sat, &H->tot[T_T5], T_AT, 0xFFFFFFFFu};
+    J.j[3] = {B.plstc, B.sap, &H->n_pls, T_AP, 0xFFFFFFFFu};
+    scan_multi(B, L, s, J, 4, mk);
+  }
   k_tc_offsets<<<1, 1024, 0, s>>>(G, B);
   mk(30);
   k_tc_write<<<g, 256, 0, s>>>(C, G, B);

@@ -101,6 +101,8 @@ size_t carve(char* base, BufView& B) {
   B.pls_ev = c.take<uint32_t>(MAX_PLS);
   B.pls_ncand = c.take<uint32_t>(MAX_PLS);
   B.pls_cand = c.take<uint32_t>((size_t)MAX_PLS * MAX_CAND);
+  B.pls_t3rng = c.take<uint2>((size_t)MAX_PLS * MAX_CAND);
+  B.pls_t5rng = c.take<uint2>((size_t)MAX_PLS * MAX_CAND);
   B.pls_h0 = c.take<float4>(MAX_PLS);
   B.pls_h1 = c.take<float4>(MAX_PLS);
   B.pls_pt = c.take<float>(MAX_PLS);
@@ -136,7 +138,7 @@ size_t carve(char* base, BufView& B) {
   B.sat = c.take<uint32_t>(MAX_T5 + 1);
   B.sap = c.take<uint32_t>(MAX_PLS + 1);
   B.tc_ev_off = c.take<uint32_t>(2);
-  B.scan_part = c.take<uint32_t>(1024);
+  B.scan_part = c.take<uint32_t>(4 * 1024);  // partials of up to four scans per launch
   B.mask_off = c.take<uint32_t>(MAX_MODULES);  // >= MAX_MD and MAX_PLS
   B.cap_mask = MASK_WORDS;
   B.mask = c.take<uint32_t>(MASK_WORDS);
