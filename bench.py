@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--served", type=int, default=256, help="events for the served leg (0 = skip)")
     ap.add_argument("--served-rate", type=float, default=0.0, help="offered Hz (0: 0.8 x batched rate)")
     ap.add_argument("--cpu-sample", type=int, default=8, help="events for the CPU-oracle baseline (0 = skip)")
+    ap.add_argument("--tune", type=int, default=1, help="autotune the launch configuration first (1) or not (0)")
     return ap.parse_args()
 
 
@@ -160,6 +161,21 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- ranks
+def aggregate(elapsed_ms: float, events_per_rank: int):
+    """Weak scaling over replicas: every rank processed events_per_rank events, the job
+    took as long as the slowest rank.  Returns (events/s of the whole job, max ms)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    if ws > 1:
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return ws * events_per_rank / (elapsed_ms * 1e-3), elapsed_ms
+
+
 # ---------------------------------------------------------------- roofline
 def kernel_hash():
     h = hashlib.sha1()
@@ -247,7 +263,12 @@ def main():
 
     dev_batches = [to_device(b) for b in batches]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    sess = lst.Session(geom.modules, device=local)
+    tuning = {}
+    if args.tune:
+        from paper_2407_18231_gb300 import autotune
+        space = {"block_size": [128, 256], "blocks_per_sm": [2, 4, 8], "ls_list_cap": [128, 512]}
+        tuning = autotune.tune(geom.modules, events[:8], device=local, space=space, reps=2)["best"]
+    sess = lst.Session(geom.modules, device=local, **tuning)
     # the library runs on this stream, so events recorded on it bracket its kernels
     stream = torch.cuda.Stream(dev)
     assert stream.cuda_stream != 0
@@ -278,11 +299,7 @@ def main():
         raise RuntimeError("a timed step re-ran after a list overflow; warm-up did not size the buffers")
     if ws > 1:
         torch.distributed.barrier()
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_events = ws * args.steps * B
-    value = total_events / (elapsed_ms * 1e-3)
+    value, elapsed_ms = aggregate(elapsed_ms, args.steps * B)
     kernels_per_step = stats["kernels"]
 
     if rank != 0:
@@ -291,7 +308,7 @@ def main():
         return
 
     # ---- end to end: host buffers through lst_run_batch (H2D + D2H inside the timed region)
-    sess_h = lst.Session(geom.modules, device=local)
+    sess_h = lst.Session(geom.modules, device=local, **tuning)
     for k in range(args.warmup):
         sess_h.run_batch(batches[k % P])
     torch.cuda.synchronize()
@@ -337,7 +354,7 @@ def main():
                   "max_batch": B}
 
     # ---- roofline of the dominant kernel (profile mode: CUDA events around every kernel)
-    prof_sess = lst.Session(geom.modules, device=local, profile=True)
+    prof_sess = lst.Session(geom.modules, device=local, profile=True, **tuning)
     acc = {}
     reps = 3
     for r in range(reps + 1):
@@ -382,6 +399,7 @@ def main():
                    "mean_pls_per_event": float(np.mean([e.n_pls for e in events])),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "mode": "batched persistent kernels, CUDA graph replay",
+                   "tuning": tuning or "defaults",
                    "l2": "256 MB buffer written between timed steps; inputs rotate over "
                          f"{P} resident batches"},
         "e2e": e2e, "per_event": per_event, "served": served,

@@ -103,7 +103,9 @@ typedef struct lst_config {
   uint32_t block_size;   /* threads per block of the stage kernels (0 = tuned default) */
   uint32_t blocks_per_sm;/* resident blocks per SM of the persistent grids (0 = default) */
   uint32_t profile;      /* 1: run kernels eagerly with a CUDA event after each (per-kernel times) */
-  uint32_t reserved[10];
+  uint32_t ls_list_cap;  /* LS work split: neighbour MDs staged per warp in shared memory, up to
+                            512 (0 = 512; 1 = no staging, one warp per MD everywhere) */
+  uint32_t reserved[9];
 } lst_config;
 
 /* Track candidate (Sec. 1 list: pT5, pT3, T5, unlinked pLS).  76 bytes. */
@@ -210,6 +212,11 @@ typedef struct lst_stats {
   uint64_t device_bytes;  /* device memory held by the context */
 } lst_stats;
 lst_status lst_get_stats(lst_ctx *ctx, lst_stats *out);
+
+/* Changes the launch configuration of a context (cfg->block_size, blocks_per_sm,
+ * ls_list_cap; the other fields are ignored).  Results never depend on it; the next run
+ * re-captures its graph.  Errors: INVALID_ARG (out of range, or a batch in flight). */
+lst_status lst_set_tuning(lst_ctx *ctx, const lst_config *cfg);
 
 /* Per-kernel device time of the last run in profile mode (CUDA events on the launching
  * stream, summed over the kernel's launches in that run).  buf == NULL is a size query. */

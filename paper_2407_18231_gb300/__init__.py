@@ -64,7 +64,7 @@ class lst_batch_dev(C.Structure):
 class lst_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("keep_objects", C.c_uint32), ("use_graph", C.c_uint32),
                 ("block_size", C.c_uint32), ("blocks_per_sm", C.c_uint32), ("profile", C.c_uint32),
-                ("reserved", C.c_uint32 * 10)]
+                ("ls_list_cap", C.c_uint32), ("reserved", C.c_uint32 * 9)]
 
 
 class lst_profile_entry(C.Structure):
@@ -85,7 +85,7 @@ EXPORTS = [
     "lst_load_geometry", "lst_build_connection_map", "lst_run_event", "lst_run_batch", "lst_run_batch_device",
     "lst_batch_finish", "lst_get_candidates", "lst_get_objects", "lst_release_result", "lst_destroy",
     "lst_last_error", "lst_status_string", "lst_get_stats", "lst_get_profile", "lst_serve_replay",
-    "lst_run_event_static",
+    "lst_run_event_static", "lst_set_tuning",
 ]
 
 _lib = None
@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH):
             "lst_get_profile": (i32, [P, P, u32, C.POINTER(u32)]),
             "lst_serve_replay": (i32, [P, P, P, P, u32, P, P, P, P]),
             "lst_run_event_static": (i32, [P, P, P, u32, C.POINTER(u32), P]),
+            "lst_set_tuning": (i32, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -148,11 +149,11 @@ class Session:
     """One context: geometry + connection map resident on the device."""
 
     def __init__(self, modules: np.ndarray, *, device: int = 0, keep_objects: bool = False, use_graph: int = 0,
-                 block_size: int = 0, blocks_per_sm: int = 0, profile: bool = False):
+                 block_size: int = 0, blocks_per_sm: int = 0, profile: bool = False, ls_list_cap: int = 0):
         L = load_library()
         self._mods = np.ascontiguousarray(modules)
         assert self._mods.dtype.itemsize == 48
-        cfg = lst_config(device, int(keep_objects), use_graph, block_size, blocks_per_sm, int(profile))
+        cfg = lst_config(device, int(keep_objects), use_graph, block_size, blocks_per_sm, int(profile), ls_list_cap)
         h = C.c_void_p()
         s = L.lst_load_geometry(self._mods.ctypes.data, len(self._mods), C.byref(cfg), C.byref(h))
         if s != LST_OK:
@@ -220,6 +221,10 @@ class Session:
         st = lst_stats()
         _check(self.ctx, load_library().lst_get_stats(self.ctx, C.byref(st)))
         return {f: getattr(st, f) for f, _ in lst_stats._fields_}
+
+    def set_tuning(self, block_size: int = 0, blocks_per_sm: int = 0, ls_list_cap: int = 0):
+        cfg = lst_config(0, 0, 0, block_size, blocks_per_sm, 0, ls_list_cap)
+        _check(self.ctx, load_library().lst_set_tuning(self.ctx, C.byref(cfg)))
 
     def profile(self) -> dict:
         """Per-kernel {name: (launches, ms)} of the last run (profile mode)."""

@@ -108,6 +108,7 @@ struct Launch {
   uint32_t grid;   // persistent grid (blocks)
   uint32_t block;  // threads per block
   uint32_t scan_grid;
+  uint32_t ls_list_cap;  // LS: neighbour MDs staged per warp (0: per-MD join everywhere)
 };
 
 }  // namespace lst

@@ -467,12 +467,18 @@ struct Pipeline {
     stream = nullptr;
   }
 
+  void set_tuning(const lst_config& cfg, int n_sm) {
+    const uint32_t bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
+    L.block = cfg.block_size ? cfg.block_size : 256;
+    L.ls_list_cap = cfg.ls_list_cap == 0 ? 512u : (cfg.ls_list_cap == 1 ? 0u : std::min<uint32_t>(cfg.ls_list_cap, 512u));
+    L.grid = (uint32_t)n_sm * bps;
+    graph_valid = false;
+  }
+
   void init(Geometry* g, const lst_config& cfg, int n_sm) {
     geo = g;
     C = method_constants();
-    const uint32_t bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
-    L.block = cfg.block_size ? cfg.block_size : 256;
-    L.grid = (uint32_t)n_sm * bps;
+    set_tuning(cfg, n_sm);
     uint32_t sg = ((2u * (uint32_t)n_sm) + 31u) / 32u * 32u;
     L.scan_grid = std::min<uint32_t>(sg, 1024u);
     CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
@@ -1089,6 +1095,11 @@ lst_status lst_load_geometry(const lst_module_desc* mods, uint32_t n_mods, const
   }
   if (cfg) c->cfg = *cfg;
   c->device = c->cfg.device;
+  if ((c->cfg.block_size && (c->cfg.block_size < 64 || c->cfg.block_size > 512 || c->cfg.block_size % 32)) ||
+      c->cfg.blocks_per_sm > 32) {
+    delete c;
+    return LST_ERR_INVALID_ARG;
+  }
   const lst_status s = guarded(c, [&]() -> lst_status {
     CK(cudaSetDevice(c->device));
     CK(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device));
@@ -1133,6 +1144,7 @@ lst_status lst_run_batch_device(lst_ctx* c, const lst_batch_dev* b, void* stream
   return guarded(c, [&]() -> lst_status {
     if (!c->geo.have_map) return fail(c, LST_ERR_NO_MAP, "lst_build_connection_map has not run");
     Pipeline& P = c->main;
+    if (P.pending) return fail(c, LST_ERR_INVALID_ARG, "a batch is still in flight (call lst_batch_finish)");
     Hdr h{};
     h.x = b->x; h.y = b->y; h.z = b->z; h.det = b->det; h.hit_off = b->hit_off;
     h.pls = (const PlsIn*)b->pls; h.pls_off = b->pls_off;
@@ -1153,8 +1165,9 @@ lst_status lst_batch_finish(lst_ctx* c, uint32_t timeout_ms, uint32_t* n_tc_per_
   return guarded(c, [&]() -> lst_status {
     Pipeline& P = c->main;
     if (!P.pending) return fail(c, LST_ERR_INVALID_ARG, "no batch in flight");
-    P.pending = false;
+    // on a timeout the batch stays in flight: a later call can wait for it again
     if (!P.wait(timeout_ms)) return fail(c, LST_ERR_TIMEOUT, "device did not finish within the time limit");
+    P.pending = false;
     const Hdr& h = *P.h_hdr_out;
     if (h.err & ERR_BAD_INPUT)
       return fail(c, LST_ERR_BAD_INPUT, "bad input: module id out of range, non-finite value or invalid pLS");
@@ -1226,6 +1239,21 @@ void lst_destroy(lst_ctx* c) {
 const char* lst_last_error(lst_ctx* c) {
   if (!c) return "null context";
   return c->err.c_str();
+}
+
+lst_status lst_set_tuning(lst_ctx* c, const lst_config* cfg) {
+  if (!c || !cfg) return LST_ERR_INVALID_ARG;
+  const uint32_t bs = cfg->block_size;
+  if (bs && (bs < 64 || bs > 512 || bs % 32)) return fail(c, LST_ERR_INVALID_ARG, "block_size must be 64..512, a multiple of 32");
+  if (cfg->blocks_per_sm > 32) return fail(c, LST_ERR_INVALID_ARG, "blocks_per_sm must be at most 32");
+  return guarded(c, [&]() -> lst_status {
+    if (c->main.pending) return fail(c, LST_ERR_INVALID_ARG, "a batch is still in flight");
+    c->cfg.block_size = cfg->block_size;
+    c->cfg.blocks_per_sm = cfg->blocks_per_sm;
+    c->cfg.ls_list_cap = cfg->ls_list_cap;
+    c->main.set_tuning(c->cfg, c->n_sm);
+    return LST_OK;
+  });
 }
 
 lst_status lst_get_profile(lst_ctx* c, lst_profile_entry* buf, uint32_t cap, uint32_t* n_out) {

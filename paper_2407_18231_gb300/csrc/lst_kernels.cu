@@ -511,14 +511,14 @@ constexpr uint32_t LS_LIST_CAP = 512;  // flattened neighbour MDs per warp in sh
 // 32-wide chunks for every MD a of A: no per-MD neighbour lookups, no per-chunk search.  The
 // count pass keeps each row's passing chunks as records (t0, ballot) for the fill pass.
 template <bool FILL>
-__global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B) {
+__global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B, uint32_t list_cap) {
   extern __shared__ uint32_t ls_smem[];
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t nu = H->n_ev * G.nm;
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t* list = ls_smem + (threadIdx.x >> 5) * LS_LIST_CAP;
+  uint32_t* list = ls_smem + (threadIdx.x >> 5) * list_cap;
   WarpAlloc wa;
   WARP_LOOP(u, nu) {
     const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
@@ -538,11 +538,11 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B)
       const uint32_t incl = warp_incl_scan(c);
       const uint32_t o = len + incl - c;
       for (uint32_t k = 0; k < c; k++)
-        if (o + k < LS_LIST_CAP) list[o + k] = b + k;
+        if (o + k < list_cap) list[o + k] = b + k;
       len += __shfl_sync(FULL, incl, 31);
     }
     __syncwarp();
-    if (len > LS_LIST_CAP) {
+    if (len > list_cap) {
       for (uint32_t a = a0; a < a1; a++) ls_md_join<FILL>(C, G, B, a, ev, A, wa);
       continue;
     }
@@ -1380,11 +1380,12 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.md_cnt, B.md_off, &H->n_ev, G.nm, T_MD, B.cap_md, mk);
   k_md<true><<<g, bs, 0, s>>>(C, G, B);
   mk(8);
-  const size_t ls_smem = (bs / 32) * LS_LIST_CAP * sizeof(uint32_t);
-  k_ls<false><<<g, bs, ls_smem, s>>>(C, G, B);
+  const uint32_t lcap = L.ls_list_cap;
+  const size_t ls_smem = (bs / 32) * lcap * sizeof(uint32_t);
+  k_ls<false><<<g, bs, ls_smem, s>>>(C, G, B, lcap);
   mk(9);
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
-  k_ls<true><<<g, bs, ls_smem, s>>>(C, G, B);
+  k_ls<true><<<g, bs, ls_smem, s>>>(C, G, B, lcap);
   mk(10);
   k_t3<false><<<g, bs, 0, s>>>(C, G, B);
   mk(11);
