@@ -71,14 +71,14 @@ struct BufView {
   float4 *md_lo4, *md_up4, *md_cst;
   // LS
   uint32_t *ls_cnt, *ls_off, *ls_in, *ls_out;
-  // T3
-  uint32_t *t3_cnt, *t3_off, *t3_a, *t3_b, *t3_c;
-  // T5
-  uint32_t *t5_cnt, *t5_off, *t5_m0, *t5_m1, *t5_m2, *t5_m3, *t5_m4;
+  // T3: per LS count/offset of the T3s built on it, per MD offset of those starting there
+  uint32_t *t3_lcnt, *t3_loff, *t3_off, *t3_a, *t3_b, *t3_c;
+  // T5: per T3 count/offset of the T5s built on it, per MD offset
+  uint32_t *t5_tcnt, *t5_toff, *t5_off, *t5_m0, *t5_m1, *t5_m2, *t5_m3, *t5_m4;
   float *t5_score, *t5_kfull;
   // pLS
   uint32_t *pls_ev, *pls_ncand, *pls_cand;
-  uint2 *pls_t3rng, *pls_t5rng;  // per candidate module: (first, count) of T3s / T5s starting there
+  uint32_t *pls_mdpass, *pls_nmdpass;  // MDs passing the first-anchor test (64 per pLS; NONE: more)
   float4 *pls_h0, *pls_h1;  // (x0, y0, z0, R), (cx, cy, cot, q)
   float *pls_pt;
   // pT3 / pT5

@@ -400,9 +400,9 @@ struct Pipeline {
   DevBuf sen_cnt, sen_off, hit_tmp, hit_ev, hit_idx, hit4;
   DevBuf md_cnt, md_off, md_unit, md_lo_idx, md_up_idx, md_lo4, md_up4, md_cst;
   DevBuf ls_cnt, ls_off, ls_in, ls_out;
-  DevBuf t3_cnt, t3_off, t3_a, t3_b, t3_c;
-  DevBuf t5_cnt, t5_off, t5_m[5], t5_score, t5_kfull;
-  DevBuf pls_ev, pls_ncand, pls_cand, pls_h0, pls_h1, pls_pt, pls_t3rng, pls_t5rng;
+  DevBuf t3_lcnt, t3_loff, t3_off, t3_a, t3_b, t3_c;
+  DevBuf t5_tcnt, t5_toff, t5_off, t5_m[5], t5_score, t5_kfull;
+  DevBuf pls_ev, pls_ncand, pls_cand, pls_h0, pls_h1, pls_pt, pls_mdpass, pls_nmdpass;
   DevBuf pt3_cnt, pt3_off, pt3_pls, pt3_obj, pt3_score;
   DevBuf pt5_cnt, pt5_off, pt5_pls, pt5_obj, pt5_score;
   DevBuf c5_cnt, c5_off, c5_list, c3_cnt, c3_off, c3_list, ct_cnt, ct_off, ct_list;
@@ -434,9 +434,9 @@ struct Pipeline {
   std::vector<DevBuf*> all_buffers() {
     std::vector<DevBuf*> v = {&hdr, &in_x, &in_y, &in_z, &in_det, &in_hoff, &in_pls, &in_poff, &sen_cnt, &sen_off,
                               &hit_tmp, &hit_ev, &hit_idx, &hit4, &md_cnt, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
-                              &md_lo4, &md_up4, &md_cst, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_cnt, &t3_off, &t3_a,
-                              &t3_b, &t3_c, &t5_cnt, &t5_off, &t5_score, &t5_kfull, &pls_ev, &pls_ncand, &pls_cand,
-                              &pls_h0, &pls_h1, &pls_pt, &pls_t3rng, &pls_t5rng, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
+                              &md_lo4, &md_up4, &md_cst, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off,
+                              &t3_a, &t3_b, &t3_c, &t5_tcnt, &t5_toff, &t5_off, &t5_score, &t5_kfull, &pls_ev,
+                              &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
                               &pt5_cnt, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
                               &c3_cnt, &c3_off, &c3_list, &ct_cnt, &ct_off, &ct_list, &alive5, &alive3, &alivet,
                               &plstc, &used5, &used3, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
@@ -534,12 +534,14 @@ struct Pipeline {
     need<uint32_t>(ls_off, c.md + 1);
     need<uint32_t>(ls_in, c.ls);
     need<uint32_t>(ls_out, c.ls);
-    need<uint32_t>(t3_cnt, c.md);
+    need<uint32_t>(t3_lcnt, c.ls);
+    need<uint32_t>(t3_loff, c.ls + 1);
     need<uint32_t>(t3_off, c.md + 1);
     need<uint32_t>(t3_a, c.t3);
     need<uint32_t>(t3_b, c.t3);
     need<uint32_t>(t3_c, c.t3);
-    need<uint32_t>(t5_cnt, c.md);
+    need<uint32_t>(t5_tcnt, c.t3);
+    need<uint32_t>(t5_toff, c.t3 + 1);
     need<uint32_t>(t5_off, c.md + 1);
     for (auto& b : t5_m) need<uint32_t>(b, c.t5);
     need<float>(t5_score, c.t5);
@@ -547,8 +549,8 @@ struct Pipeline {
     need<uint32_t>(pls_ev, c.pls);
     need<uint32_t>(pls_ncand, c.pls);
     need<uint32_t>(pls_cand, (size_t)c.pls * MAX_CAND);
-    need<uint2>(pls_t3rng, (size_t)c.pls * MAX_CAND);
-    need<uint2>(pls_t5rng, (size_t)c.pls * MAX_CAND);
+    need<uint32_t>(pls_mdpass, (size_t)c.pls * 64);
+    need<uint32_t>(pls_nmdpass, c.pls);
     need<float4>(pls_h0, c.pls);
     need<float4>(pls_h1, c.pls);
     need<float>(pls_pt, c.pls);
@@ -657,13 +659,14 @@ struct Pipeline {
     v.md_up_idx = P32(md_up_idx); v.md_lo4 = (float4*)md_lo4.p; v.md_up4 = (float4*)md_up4.p;
     v.md_cst = (float4*)md_cst.p;
     v.ls_cnt = P32(ls_cnt); v.ls_off = P32(ls_off); v.ls_in = P32(ls_in); v.ls_out = P32(ls_out);
-    v.t3_cnt = P32(t3_cnt); v.t3_off = P32(t3_off); v.t3_a = P32(t3_a); v.t3_b = P32(t3_b); v.t3_c = P32(t3_c);
-    v.t5_cnt = P32(t5_cnt); v.t5_off = P32(t5_off);
+    v.t3_lcnt = P32(t3_lcnt); v.t3_loff = P32(t3_loff); v.t3_off = P32(t3_off);
+    v.t3_a = P32(t3_a); v.t3_b = P32(t3_b); v.t3_c = P32(t3_c);
+    v.t5_tcnt = P32(t5_tcnt); v.t5_toff = P32(t5_toff); v.t5_off = P32(t5_off);
     v.t5_m0 = P32(t5_m[0]); v.t5_m1 = P32(t5_m[1]); v.t5_m2 = P32(t5_m[2]); v.t5_m3 = P32(t5_m[3]);
     v.t5_m4 = P32(t5_m[4]);
     v.t5_score = (float*)t5_score.p; v.t5_kfull = (float*)t5_kfull.p;
     v.pls_ev = P32(pls_ev); v.pls_ncand = P32(pls_ncand); v.pls_cand = P32(pls_cand);
-    v.pls_t3rng = (uint2*)pls_t3rng.p; v.pls_t5rng = (uint2*)pls_t5rng.p;
+    v.pls_mdpass = P32(pls_mdpass); v.pls_nmdpass = P32(pls_nmdpass);
     v.pls_h0 = (float4*)pls_h0.p; v.pls_h1 = (float4*)pls_h1.p; v.pls_pt = (float*)pls_pt.p;
     v.pt3_cnt = P32(pt3_cnt); v.pt3_off = P32(pt3_off); v.pt3_pls = P32(pt3_pls); v.pt3_obj = P32(pt3_obj);
     v.pt3_score = (float*)pt3_score.p;

@@ -639,80 +639,102 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
 }
 
 // ------------------------------------------------------------------ T3
-// Unit = MD a; candidates = LS (a -> b) x LS (b -> c).
+// Unit = LS l (a -> b), one thread each; candidates = the LSs leaving b (a handful).
+// T3s come out ordered by (LS l, LS l2), i.e. by (a, b, c).
 template <bool FILL>
 __global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  const uint32_t n = H->tot[T_MD];
-  WarpAlloc wa;
-  WARP_LOOP(a, n) {
-    const PointTol pa = md_point(B, a);
-    const uint32_t l0 = B.ls_off[a], nl = B.ls_off[a + 1] - l0;
-    const uint32_t base = FILL ? B.t3_off[a] : 0u;
-    const uint32_t n_out = FILL ? B.t3_off[a + 1] - base : 0u;
-    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[2], &B.mask_off[a]};
-    const uint32_t cnt = warp_join<FILL, NoPayload>(
-        nl, base, n_out, js, wa,
-        [&](uint32_t i, uint32_t& b, uint32_t& c) {
-          const uint32_t mb = B.ls_out[l0 + i];
-          b = B.ls_off[mb];
-          c = B.ls_off[mb + 1] - b;
-        },
-        [&](uint32_t i, uint32_t j) {
-          const uint32_t mb = B.ls_out[l0 + i], mc = B.ls_out[j];
-          return t3_select(C, pa, md_point(B, mb), md_upper(B, mb), md_point(B, mc));
-        },
-        [&](uint32_t, uint32_t, NoPayload&) {},
-        [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
-          B.t3_a[pos] = a;
-          B.t3_b[pos] = B.ls_out[l0 + i];
-          B.t3_c[pos] = B.ls_out[j];
-        });
-    if (!FILL && lane_id() == 0) B.t3_cnt[a] = cnt;
+  const uint32_t n = H->tot[T_LS];
+  THREAD_LOOP(l, n) {
+    uint32_t k = 0;
+    if (FILL) {
+      k = B.t3_loff[l];
+      if (B.t3_loff[l + 1] == k) continue;
+    }
+    const uint32_t a = B.ls_in[l], b = B.ls_out[l];
+    const uint32_t c0 = B.ls_off[b], c1 = B.ls_off[b + 1];
+    if (c0 == c1) {
+      if (!FILL) B.t3_lcnt[l] = 0;
+      continue;
+    }
+    const PointTol pa = md_point(B, a), pb = md_point(B, b), pbu = md_upper(B, b);
+    uint32_t cnt = 0;
+    for (uint32_t l2 = c0; l2 < c1; l2++) {
+      const uint32_t c = B.ls_out[l2];
+      if (t3_select(C, pa, pb, pbu, md_point(B, c))) {
+        if (FILL) {
+          B.t3_a[k] = a;
+          B.t3_b[k] = b;
+          B.t3_c[k] = c;
+          k++;
+        } else {
+          cnt++;
+        }
+      }
+    }
+    if (!FILL) B.t3_lcnt[l] = cnt;
   }
 }
 
+// T3s starting at MD a = T3s of the LSs leaving a: t3_off[a] = t3_loff[ls_off[a]].
+__global__ void k_t3_md_off(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(a, H->tot[T_MD] + 1) B.t3_off[a] = B.t3_loff[B.ls_off[a]];
+}
+
 // ------------------------------------------------------------------ T5
-// Unit = MD a; candidates = T3 (a, b, c) x T3 (c, d, e).
+// Unit = T3 t (a, b, c), one thread each; candidates = the T3s starting at c.  T5s come out
+// ordered by (T3 t, T3 t2), i.e. by (a, b, c, d, e), and t5_toff[t] gives the T5s built on t.
 template <bool FILL>
 __global__ void __launch_bounds__(512) k_t5(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  const uint32_t n = H->tot[T_MD];
-  WarpAlloc wa;
-  WARP_LOOP(a, n) {
-    const PointTol pa = md_point(B, a);
-    const uint32_t s0 = B.t3_off[a], ns = B.t3_off[a + 1] - s0;
-    const uint32_t base = FILL ? B.t5_off[a] : 0u;
-    const uint32_t n_out = FILL ? B.t5_off[a + 1] - base : 0u;
-    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[3], &B.mask_off[a]};
-    const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        ns, base, n_out, js, wa,
-        [&](uint32_t i, uint32_t& b, uint32_t& c) {
-          const uint32_t mc = B.t3_c[s0 + i];
-          b = B.t3_off[mc];
-          c = B.t3_off[mc + 1] - b;
-        },
-        [&](uint32_t i, uint32_t j) {
-          const uint32_t mb = B.t3_b[s0 + i], mc = B.t3_c[s0 + i], md = B.t3_b[j], me = B.t3_c[j];
-          return t5_accept(C, pa, md_point(B, mb), md_point(B, mc), md_point(B, md), md_point(B, me));
-        },
-        [&](uint32_t i, uint32_t j, ScorePayload& pl) {
-          const uint32_t mb = B.t3_b[s0 + i], mc = B.t3_c[s0 + i], md = B.t3_b[j], me = B.t3_c[j];
-          t5_select(C, pa, md_point(B, mb), md_point(B, mc), md_point(B, md), md_point(B, me), pl.score, pl.kfull);
-        },
-        [&](uint32_t pos, uint32_t i, uint32_t j, const ScorePayload& pl) {
-          B.t5_m0[pos] = a;
-          B.t5_m1[pos] = B.t3_b[s0 + i];
-          B.t5_m2[pos] = B.t3_c[s0 + i];
-          B.t5_m3[pos] = B.t3_b[j];
-          B.t5_m4[pos] = B.t3_c[j];
-          B.t5_score[pos] = pl.score;
-          B.t5_kfull[pos] = pl.kfull;
-        });
-    if (!FILL && lane_id() == 0) B.t5_cnt[a] = cnt;
+  const uint32_t n = H->tot[T_T3];
+  THREAD_LOOP(t, n) {
+    uint32_t k = 0;
+    if (FILL) {
+      k = B.t5_toff[t];
+      if (B.t5_toff[t + 1] == k) continue;
+    }
+    const uint32_t c = B.t3_c[t];
+    const uint32_t s0 = B.t3_off[c], s1 = B.t3_off[c + 1];
+    if (s0 == s1) {
+      if (!FILL) B.t5_tcnt[t] = 0;
+      continue;
+    }
+    const uint32_t a = B.t3_a[t], b = B.t3_b[t];
+    const PointTol pa = md_point(B, a), pb = md_point(B, b), pc = md_point(B, c);
+    uint32_t cnt = 0;
+    for (uint32_t t2 = s0; t2 < s1; t2++) {
+      const uint32_t d = B.t3_b[t2], e = B.t3_c[t2];
+      const PointTol pd = md_point(B, d), pe = md_point(B, e);
+      if (!FILL) {
+        cnt += t5_accept(C, pa, pb, pc, pd, pe) ? 1u : 0u;
+      } else {
+        float score, kfull;
+        if (t5_select(C, pa, pb, pc, pd, pe, score, kfull)) {
+          B.t5_m0[k] = a;
+          B.t5_m1[k] = b;
+          B.t5_m2[k] = c;
+          B.t5_m3[k] = d;
+          B.t5_m4[k] = e;
+          B.t5_score[k] = score;
+          B.t5_kfull[k] = kfull;
+          k++;
+        }
+      }
+    }
+    if (!FILL) B.t5_tcnt[t] = cnt;
   }
+}
+
+// T5s starting at MD a: t5_off[a] = t5_toff[t3_off[a]].
+__global__ void k_t5_md_off(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(a, H->tot[T_MD] + 1) B.t5_off[a] = B.t5_toff[B.t3_off[a]];
 }
 
 // ------------------------------------------------------------------ pLS module lookup
@@ -886,15 +908,7 @@ __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
       list[k] = v;
     }
     B.pls_ncand[p] = nc;
-    const uint32_t ubase = B.pls_ev[p] * G.nm;
-    for (uint32_t i = 0; i < nc; i++) {
-      B.pls_cand[(size_t)p * MAX_CAND + i] = list[i];
-      // T3s and T5s are sorted by first MD, so those starting on a module are one range
-      const uint32_t mb = B.md_off[ubase + list[i]], me = B.md_off[ubase + list[i] + 1];
-      const uint32_t t3b = B.t3_off[mb], t5b = B.t5_off[mb];
-      B.pls_t3rng[(size_t)p * MAX_CAND + i] = make_uint2(t3b, B.t3_off[me] - t3b);
-      B.pls_t5rng[(size_t)p * MAX_CAND + i] = make_uint2(t5b, B.t5_off[me] - t5b);
-    }
+    for (uint32_t i = 0; i < nc; i++) B.pls_cand[(size_t)p * MAX_CAND + i] = list[i];
   }
 }
 
@@ -908,45 +922,109 @@ __device__ __forceinline__ PlsHelix load_helix(const BufView& B, uint32_t p) {
 }
 
 // ------------------------------------------------------------------ pT3 / pT5
-// Unit = pLS p; candidates = T3s (T5s) whose first MD sits on one of p's candidate modules.
+constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, kept per pLS
+
+// pT3 (Sec. 1: pLS + T3).  Unit = pLS p.  Phase 1 tests p against every MD on its
+// candidate modules (the first anchor of any T3 it could join) and keeps the passing MDs in
+// order; phase 2 walks the T3s starting at those MDs and tests their other two anchors.  The
+// set equals "T3s whose first MD is on a candidate module, all three anchors inside the
+// windows" and comes out in T3 order.  More than PLS_MD_CAP passing MDs: the pLS falls back
+// to walking every T3 of its candidate modules.
 template <bool FILL>
 __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
   WarpAlloc wa;
   WARP_LOOP(p, n) {
     const PlsHelix h = load_helix(B, p);
+    const uint32_t ubase = B.pls_ev[p] * G.nm;
+    const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
+    const uint32_t nc = B.pls_ncand[p];
+    uint32_t* mlist = B.pls_mdpass + (size_t)p * PLS_MD_CAP;
+    uint32_t npass;
+    if (!FILL) {
+      npass = 0;
+      for (uint32_t g0 = 0; g0 < nc; g0 += 32) {
+        uint32_t b = 0, c = 0;
+        if (g0 + lane < nc) {
+          const uint32_t u = ubase + cand[g0 + lane];
+          b = B.md_off[u];
+          c = B.md_off[u + 1] - b;
+        }
+        const uint32_t incl = warp_incl_scan(c);
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+          const uint32_t cc0 = t0 + lane;
+          const uint32_t cc = cc0 < total ? cc0 : total - 1;
+          const uint32_t o = owner_lane(incl, cc);
+          const uint32_t bo = __shfl_sync(FULL, b, o);
+          const uint32_t co = __shfl_sync(FULL, c, o);
+          const uint32_t io = __shfl_sync(FULL, incl, o);
+          const uint32_t m = bo + (cc - (io - co));
+          const bool pass = cc0 < total && pls_anchor_accept(C, h, md_point(B, m));
+          const uint32_t bal = __ballot_sync(FULL, pass);
+          if (pass && npass + __popc(bal & lt) < PLS_MD_CAP) mlist[npass + __popc(bal & lt)] = m;
+          npass += __popc(bal);
+        }
+      }
+      if (npass > PLS_MD_CAP) npass = NONE;
+      if (lane == 0) B.pls_nmdpass[p] = npass;
+      __syncwarp();
+    } else {
+      npass = B.pls_nmdpass[p];
+    }
     const uint32_t base = FILL ? B.pt3_off[p] : 0u;
     const uint32_t n_out = FILL ? B.pt3_off[p + 1] - base : 0u;
     const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[4], &B.mask_off[p]};
-    const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        B.pls_ncand[p], base, n_out, js, wa,
-        [&](uint32_t i, uint32_t& b, uint32_t& c) {
-          const uint2 r = B.pls_t3rng[(size_t)p * MAX_CAND + i];
-          b = r.x;
-          c = r.y;
-        },
-        [&](uint32_t, uint32_t t) {
-          return pls_anchor_accept(C, h, md_point(B, B.t3_a[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) &&
-                 pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
-        },
-        [&](uint32_t, uint32_t t, ScorePayload& pl) {
-          float score = 0.0f;
-          pls_anchor(C, h, md_point(B, B.t3_a[t]), score);
-          pls_anchor(C, h, md_point(B, B.t3_b[t]), score);
-          pls_anchor(C, h, md_point(B, B.t3_c[t]), score);
-          pl.score = score;
-        },
-        [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
-          B.pt3_pls[pos] = p;
-          B.pt3_obj[pos] = t;
-          B.pt3_score[pos] = pl.score;
-        });
-    if (!FILL && lane_id() == 0) B.pt3_cnt[p] = cnt;
+    auto score3 = [&](uint32_t, uint32_t t, ScorePayload& pl) {
+      float score = 0.0f;
+      pls_anchor(C, h, md_point(B, B.t3_a[t]), score);
+      pls_anchor(C, h, md_point(B, B.t3_b[t]), score);
+      pls_anchor(C, h, md_point(B, B.t3_c[t]), score);
+      pl.score = score;
+    };
+    auto emit3 = [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
+      B.pt3_pls[pos] = p;
+      B.pt3_obj[pos] = t;
+      B.pt3_score[pos] = pl.score;
+    };
+    uint32_t cnt;
+    if (npass != NONE) {
+      cnt = warp_join<FILL, ScorePayload>(
+          npass, base, n_out, js, wa,
+          [&](uint32_t i, uint32_t& b, uint32_t& c) {
+            const uint32_t m = mlist[i];
+            b = B.t3_off[m];
+            c = B.t3_off[m + 1] - b;
+          },
+          [&](uint32_t, uint32_t t) {
+            return pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
+          },
+          score3, emit3);
+    } else {
+      cnt = warp_join<FILL, ScorePayload>(
+          nc, base, n_out, js, wa,
+          [&](uint32_t i, uint32_t& b, uint32_t& c) {
+            const uint32_t u = ubase + cand[i];
+            b = B.t3_off[B.md_off[u]];
+            c = B.t3_off[B.md_off[u + 1]] - b;
+          },
+          [&](uint32_t, uint32_t t) {
+            return pls_anchor_accept(C, h, md_point(B, B.t3_a[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) &&
+                   pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
+          },
+          score3, emit3);
+    }
+    if (!FILL && lane == 0) B.pt3_cnt[p] = cnt;
   }
 }
 
+// pT5 (Sec. 1: pLS + T5).  A pT5 tests the same windows on anchors a, b, c as the pT3 of the
+// T5's first T3 (a, b, c), so its candidates are exactly the T5s built on the pT3s of p
+// (t5_toff per T3); the other two anchors and the curvature decide.  Unit = pLS p.
 template <bool FILL>
 __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
@@ -954,29 +1032,27 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
   const uint32_t n = H->n_pls;
   WarpAlloc wa;
   WARP_LOOP(p, n) {
+    const uint32_t x0 = B.pt3_off[p], nx = B.pt3_off[p + 1] - x0;
+    if (nx == 0) {
+      if (!FILL && lane_id() == 0) B.pt5_cnt[p] = 0;
+      continue;
+    }
     const PlsHelix h = load_helix(B, p);
     const uint32_t base = FILL ? B.pt5_off[p] : 0u;
     const uint32_t n_out = FILL ? B.pt5_off[p + 1] - base : 0u;
     const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[5], &B.mask_off[p]};
     const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        B.pls_ncand[p], base, n_out, js, wa,
+        nx, base, n_out, js, wa,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
-          const uint2 r = B.pls_t5rng[(size_t)p * MAX_CAND + i];
-          b = r.x;
-          c = r.y;
+          const uint32_t t = B.pt3_obj[x0 + i];
+          b = B.t5_toff[t];
+          c = B.t5_toff[t + 1] - b;
         },
         [&](uint32_t, uint32_t t) {
-          const PointTol P0 = md_point(B, B.t5_m0[t]);
-          if (!pls_anchor_accept(C, h, P0)) return false;
-          const PointTol P2 = md_point(B, B.t5_m2[t]);
-          if (!pls_anchor_accept(C, h, P2)) return false;
-          const PointTol P4 = md_point(B, B.t5_m4[t]);
-          if (!pls_anchor_accept(C, h, P4)) return false;
-          if (!pls_anchor_accept(C, h, md_point(B, B.t5_m1[t]))) return false;
           if (!pls_anchor_accept(C, h, md_point(B, B.t5_m3[t]))) return false;
-          const float kf = B.t5_kfull[t];
-          const Circle3 fu = circle3(P0, P2, P4);
-          return fabsf(fabsf(kf) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
+          if (!pls_anchor_accept(C, h, md_point(B, B.t5_m4[t]))) return false;
+          const Circle3 fu = circle3(md_point(B, B.t5_m0[t]), md_point(B, B.t5_m2[t]), md_point(B, B.t5_m4[t]));
+          return fabsf(fabsf(B.t5_kfull[t]) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
         },
         [&](uint32_t, uint32_t t, ScorePayload& pl) {
           float score = 0.0f;
@@ -1326,7 +1402,8 @@ const char* const kKernelNames[] = {
     "zero_sensor_counts", "hits_count", "scan_reduce", "scan_top", "scan_apply", "hits_scatter", "hits_sort",
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "zero_md_lists", "md_lists_count", "md_lists_fill",
-    "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write"};
+    "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
+    "t3_md_offsets", "t5_md_offsets"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Marker {
@@ -1387,16 +1464,20 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
   k_ls<true><<<g, bs, ls_smem, s>>>(C, G, B, lcap);
   mk(10);
-  k_t3<false><<<g, bs, 0, s>>>(C, G, B);
+  k_t3<false><<<g, 256, 0, s>>>(C, G, B);
   mk(11);
-  scan(B, L, s, B.t3_cnt, B.t3_off, &H->tot[T_MD], 1, T_T3, B.cap_t3, mk);
-  k_t3<true><<<g, bs, 0, s>>>(C, G, B);
+  scan(B, L, s, B.t3_lcnt, B.t3_loff, &H->tot[T_LS], 1, T_T3, B.cap_t3, mk);
+  k_t3<true><<<g, 256, 0, s>>>(C, G, B);
   mk(12);
-  k_t5<false><<<g, bs, 0, s>>>(C, G, B);
+  k_t3_md_off<<<g, 256, 0, s>>>(B);
+  mk(32);
+  k_t5<false><<<g, 256, 0, s>>>(C, G, B);
   mk(13);
-  scan(B, L, s, B.t5_cnt, B.t5_off, &H->tot[T_MD], 1, T_T5, B.cap_t5, mk);
-  k_t5<true><<<g, bs, 0, s>>>(C, G, B);
+  scan(B, L, s, B.t5_tcnt, B.t5_toff, &H->tot[T_T3], 1, T_T5, B.cap_t5, mk);
+  k_t5<true><<<g, 256, 0, s>>>(C, G, B);
   mk(14);
+  k_t5_md_off<<<g, 256, 0, s>>>(B);
+  mk(33);
   k_pls_prep<<<g, 128, 0, s>>>(C, G, B);
   mk(15);
   k_pt3<false><<<g, bs, 0, s>>>(C, G, B);

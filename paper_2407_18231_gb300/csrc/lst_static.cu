@@ -84,12 +84,14 @@ size_t carve(char* base, BufView& B) {
   B.ls_off = c.take<uint32_t>(MAX_MD + 1);
   B.ls_in = c.take<uint32_t>(MAX_LS);
   B.ls_out = c.take<uint32_t>(MAX_LS);
-  B.t3_cnt = c.take<uint32_t>(MAX_MD);
+  B.t3_lcnt = c.take<uint32_t>(MAX_LS);
+  B.t3_loff = c.take<uint32_t>(MAX_LS + 1);
   B.t3_off = c.take<uint32_t>(MAX_MD + 1);
   B.t3_a = c.take<uint32_t>(MAX_T3);
   B.t3_b = c.take<uint32_t>(MAX_T3);
   B.t3_c = c.take<uint32_t>(MAX_T3);
-  B.t5_cnt = c.take<uint32_t>(MAX_MD);
+  B.t5_tcnt = c.take<uint32_t>(MAX_T3);
+  B.t5_toff = c.take<uint32_t>(MAX_T3 + 1);
   B.t5_off = c.take<uint32_t>(MAX_MD + 1);
   B.t5_m0 = c.take<uint32_t>(MAX_T5);
   B.t5_m1 = c.take<uint32_t>(MAX_T5);
@@ -101,8 +103,8 @@ size_t carve(char* base, BufView& B) {
   B.pls_ev = c.take<uint32_t>(MAX_PLS);
   B.pls_ncand = c.take<uint32_t>(MAX_PLS);
   B.pls_cand = c.take<uint32_t>((size_t)MAX_PLS * MAX_CAND);
-  B.pls_t3rng = c.take<uint2>((size_t)MAX_PLS * MAX_CAND);
-  B.pls_t5rng = c.take<uint2>((size_t)MAX_PLS * MAX_CAND);
+  B.pls_mdpass = c.take<uint32_t>((size_t)MAX_PLS * 64);
+  B.pls_nmdpass = c.take<uint32_t>(MAX_PLS);
   B.pls_h0 = c.take<float4>(MAX_PLS);
   B.pls_h1 = c.take<float4>(MAX_PLS);
   B.pls_pt = c.take<float>(MAX_PLS);
