@@ -185,6 +185,31 @@ __device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, u
   return count;
 }
 
+// Does any (outer i, inner j) candidate satisfy test(i, j)?  Same flattened walk as
+// warp_join, 32 candidates per step, stopping at the first step with a hit.
+template <typename OuterFn, typename TestFn>
+__device__ __forceinline__ bool warp_any(uint32_t n_outer, OuterFn outer, TestFn test) {
+  const uint32_t lane = lane_id();
+  for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
+    uint32_t b = 0, c = 0;
+    if (g0 + lane < n_outer) outer(g0 + lane, b, c);
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t bo = __shfl_sync(FULL, b, o);
+      const uint32_t co = __shfl_sync(FULL, c, o);
+      const uint32_t io = __shfl_sync(FULL, incl, o);
+      const uint32_t j = bo + (cc - (io - co));
+      const bool hit = cand < total && test(g0 + o, j);
+      if (__any_sync(FULL, hit)) return true;
+    }
+  }
+  return false;
+}
+
 __device__ __forceinline__ uint32_t find_slot(const uint32_t* off, uint32_t n, uint32_t x) {
   // largest e in [0, n) with off[e] <= x (off non-decreasing, off[0] = 0)
   uint32_t lo = 0, hi = n;
@@ -1136,31 +1161,39 @@ __global__ void k_csr_fill(BufView B) {
   }
 }
 
-// pT5 stage: dies iff a better pT5 shares its pLS or >= 3 MDs.
+// pT5 stage: dies iff a better pT5 shares its pLS or >= 3 MDs.  One warp per pT5: the
+// lanes test 32 neighbours at a time (the pLS's other pT5s, then the pT5s on three of its
+// MDs -- sharing >= 3 of 5 MDs means sharing one of any three of them).
 __global__ void k_kill_pt5(BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_PT5];
-  THREAD_LOOP(x, n) {
+  WARP_LOOP(x, n) {
     const uint32_t p = B.pt5_pls[x];
     const float sx = B.pt5_score[x];
-    bool dead = false;
-    for (uint32_t y = B.pt5_off[p]; y < B.pt5_off[p + 1] && !dead; y++)
-      if (y != x && better(B.pt5_score[y], y, sx, x)) dead = true;
     uint32_t mx[5];
     t5_mds(B, B.pt5_obj[x], mx);
-    // a pT5 sharing >= 3 of x's 5 MDs shares one of any 3 of them: scan 3 lists, not 5
-    for (int k = 0; k < 5 && !dead; k += 2) {
-      const uint32_t m = mx[k];
-      for (uint32_t j = B.c5_off[m]; j < B.c5_off[m + 1] && !dead; j++) {
-        const uint32_t y = B.c5_list[j];
-        if (y == x) continue;
-        uint32_t my[5];
-        t5_mds(B, B.pt5_obj[y], my);
-        if (shared_mds(mx, my) >= 3 && better(B.pt5_score[y], y, sx, x)) dead = true;
-      }
-    }
-    B.alive5[x] = dead ? 0u : 1u;
+    const bool dead = warp_any(
+        4u,
+        [&](uint32_t i, uint32_t& b, uint32_t& c) {
+          if (i == 0) {
+            b = B.pt5_off[p];
+            c = B.pt5_off[p + 1] - b;
+          } else {
+            const uint32_t m = mx[2 * (i - 1)];
+            b = B.c5_off[m];
+            c = B.c5_off[m + 1] - b;
+          }
+        },
+        [&](uint32_t i, uint32_t j) {
+          const uint32_t y = i == 0 ? j : B.c5_list[j];
+          if (y == x || !better(B.pt5_score[y], y, sx, x)) return false;
+          if (i == 0) return true;
+          uint32_t my[5];
+          t5_mds(B, B.pt5_obj[y], my);
+          return shared_mds(mx, my) >= 3;
+        });
+    if (lane_id() == 0) B.alive5[x] = dead ? 0u : 1u;
   }
 }
 
@@ -1234,55 +1267,66 @@ __global__ void k_used3(BufView B) {
   }
 }
 
-// T5 across stages: shares >= 3 MDs with a surviving pT5 or pT3.
+// T5 across stages: shares >= 3 MDs with a surviving pT5 or pT3 (one of any three of its
+// MDs is then shared).  One warp per T5.
 __global__ void k_cross_t5(BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  THREAD_LOOP(x, H->tot[T_T5]) {
-    bool dead = false;
+  WARP_LOOP(x, H->tot[T_T5]) {
     uint32_t mx[5];
     t5_mds(B, x, mx);
-    // >= 3 shared with a 5-MD or 3-MD object: one of any 3 of x's MDs is shared
-    for (int k = 0; k < 5 && !dead; k += 2) {
-      const uint32_t m = mx[k];
-      for (uint32_t j = B.c5_off[m]; j < B.c5_off[m + 1] && !dead; j++) {
-        const uint32_t z = B.c5_list[j];
-        if (!B.alive5[z]) continue;
-        uint32_t mz[5];
-        t5_mds(B, B.pt5_obj[z], mz);
-        if (shared_mds(mx, mz) >= 3) dead = true;
-      }
-      for (uint32_t j = B.c3_off[m]; j < B.c3_off[m + 1] && !dead; j++) {
-        const uint32_t z = B.c3_list[j];
-        if (!B.alive3[z]) continue;
-        uint32_t mz[3];
-        t3_mds(B, B.pt3_obj[z], mz);
-        if (shared_mds(mx, mz) >= 3) dead = true;
-      }
-    }
-    B.crosst[x] = dead ? 1u : 0u;
+    const bool dead = warp_any(
+        6u,
+        [&](uint32_t i, uint32_t& b, uint32_t& c) {
+          const uint32_t m = mx[2 * (i % 3)];
+          const uint32_t* off = i < 3 ? B.c5_off : B.c3_off;
+          b = off[m];
+          c = off[m + 1] - b;
+        },
+        [&](uint32_t i, uint32_t j) {
+          if (i < 3) {
+            const uint32_t z = B.c5_list[j];
+            if (!B.alive5[z]) return false;
+            uint32_t mz[5];
+            t5_mds(B, B.pt5_obj[z], mz);
+            return shared_mds(mx, mz) >= 3;
+          }
+          const uint32_t z = B.c3_list[j];
+          if (!B.alive3[z]) return false;
+          uint32_t mz[3];
+          t3_mds(B, B.pt3_obj[z], mz);
+          return shared_mds(mx, mz) >= 3;
+        });
+    if (lane_id() == 0) B.crosst[x] = dead ? 1u : 0u;
   }
 }
 
+// T5 stage among those left: dies iff a better one shares >= 3 MDs.  One warp per T5.
 __global__ void k_kill_t5(BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  THREAD_LOOP(x, H->tot[T_T5]) {
+  WARP_LOOP(x, H->tot[T_T5]) {
     bool dead = B.crosst[x] != 0;
-    const float sx = B.t5_score[x];
-    uint32_t mx[5];
-    t5_mds(B, x, mx);
-    for (int k = 0; k < 5 && !dead; k += 2) {  // >= 3 of 5 shared: three lists suffice
-      const uint32_t m = mx[k];
-      for (uint32_t j = B.ct_off[m]; j < B.ct_off[m + 1] && !dead; j++) {
-        const uint32_t y = B.ct_list[j];
-        if (y == x || B.crosst[y]) continue;
-        uint32_t my[5];
-        t5_mds(B, y, my);
-        if (shared_mds(mx, my) >= 3 && better(B.t5_score[y], y, sx, x)) dead = true;
-      }
+    if (!dead) {
+      const float sx = B.t5_score[x];
+      uint32_t mx[5];
+      t5_mds(B, x, mx);
+      dead = warp_any(
+          3u,
+          [&](uint32_t i, uint32_t& b, uint32_t& c) {
+            const uint32_t m = mx[2 * i];
+            b = B.ct_off[m];
+            c = B.ct_off[m + 1] - b;
+          },
+          [&](uint32_t, uint32_t j) {
+            const uint32_t y = B.ct_list[j];
+            if (y == x || B.crosst[y] || !better(B.t5_score[y], y, sx, x)) return false;
+            uint32_t my[5];
+            t5_mds(B, y, my);
+            return shared_mds(mx, my) >= 3;
+          });
     }
-    B.alivet[x] = dead ? 0u : 1u;
+    if (lane_id() == 0) B.alivet[x] = dead ? 0u : 1u;
   }
 }
 
