@@ -488,16 +488,30 @@ __device__ __forceinline__ PointTol md_upper(const BufView& B, uint32_t m) { ret
 // ------------------------------------------------------------------ Line Segments
 // The LS selection of ls_select for anchors (pa, pau) and MD j, loading the rest of MD j
 // only when the cheap tests pass.
-__device__ __forceinline__ bool ls_test(const MethodConst& C, const GeoView& G, const BufView& B, const PointTol& pa,
+// Split in two so that a warp can queue the candidates passing the cheap head and run the
+// tail only on full warps: ls_test = ls_head && ls_tail.
+__device__ __forceinline__ bool ls_head_pt(const MethodConst& C, const PointTol& pa, const PointTol& pb) {
+  return pair_rz(C, pa, pb) && pair_bend(C, pa, pb, pb.t.w);
+}
+
+__device__ __forceinline__ bool ls_head(const MethodConst& C, const BufView& B, const PointTol& pa, uint32_t j) {
+  return ls_head_pt(C, pa, md_point(B, j));
+}
+
+__device__ __forceinline__ bool ls_tail(const MethodConst& C, const GeoView& G, const BufView& B, const PointTol& pa,
                                         const PointTol& pau, float rnext, bool a_barrel, uint32_t ubase, uint32_t j) {
   const PointTol pb = md_point(B, j);
-  if (!(pair_rz(C, pa, pb) && pair_bend(C, pa, pb, pb.t.w))) return false;
   if (a_barrel && G.subdet[B.md_unit[j] - ubase] == 1 && !exit_ok(pa, pb, rnext, G.zb_half)) return false;
   const PointTol pbu = md_upper(B, j);
   const float cx = pb.p.x - pa.p.x;
   const float cy = pb.p.y - pa.p.y;
   const float clen = sqrtf(cx * cx + cy * cy);
   return md_dir(C, pa, pau, cx, cy, clen) && md_dir(C, pb, pbu, cx, cy, clen);
+}
+
+__device__ __forceinline__ bool ls_test(const MethodConst& C, const GeoView& G, const BufView& B, const PointTol& pa,
+                                        const PointTol& pau, float rnext, bool a_barrel, uint32_t ubase, uint32_t j) {
+  return ls_head(C, B, pa, j) && ls_tail(C, G, B, pa, pau, rnext, a_barrel, ubase, j);
 }
 
 // Per-MD LS join (candidates = MDs of every module in the connection map of A), used for
@@ -530,6 +544,10 @@ __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& 
 }
 
 constexpr uint32_t LS_LIST_CAP = 512;  // flattened neighbour MDs per warp in shared memory
+constexpr uint32_t LS_UNROLL = 2;      // candidate chunks whose loads are issued together
+constexpr uint32_t LS_RING = 128;      // ring of queued list positions (> 31 + 32 * LS_UNROLL)
+// per warp after the list: the ring and one pass bit per list position
+constexpr uint32_t LS_EXTRA_WORDS = LS_RING + LS_LIST_CAP / 32;
 
 // Unit = (event, module A).  The warp writes the indices of all MDs on the modules connected
 // to A into a shared-memory list once (module order, then MD order), then walks the list in
@@ -543,11 +561,14 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
   const uint32_t nu = H->n_ev * G.nm;
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t* list = ls_smem + (threadIdx.x >> 5) * list_cap;
+  uint32_t* list = ls_smem + (threadIdx.x >> 5) * (list_cap + LS_EXTRA_WORDS);
+  uint32_t* queue = list + list_cap;
+  uint32_t* pbits = queue + LS_RING;
   WarpAlloc wa;
   WARP_LOOP(u, nu) {
     const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
     if (a0 == a1) continue;
+    if (FILL && B.ls_off[a0] == B.ls_off[a1]) continue;  // no LS starts on this module
     const uint32_t ev = u / G.nm, A = u - ev * G.nm;
     const uint32_t ubase = ev * G.nm;
     const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
@@ -604,26 +625,49 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           }
         }
       } else {
-        uint32_t count = 0, nrec = 0, rt = 0, rb = 0;
-        bool spill = false;
-        for (uint32_t t0 = 0; t0 < len; t0 += 32) {
-          const bool pass = t0 + lane < len && ls_test(C, G, B, pa, pau, rnext, a_barrel, ubase, list[t0 + lane]);
-          const uint32_t bal = __ballot_sync(FULL, pass);
-          if (bal) {
-            if (nrec < 32) {
-              if (lane == nrec) {
-                rt = t0;
-                rb = bal;
-              }
-              nrec++;
-            } else {
-              spill = true;
-            }
+        // head on every candidate; positions passing it are queued and the tail runs on 32
+        // at a time; final passes set their bit in pbits (word k = chunk k's ballot)
+        const uint32_t nwords = (len + 31) >> 5;
+        if (lane < nwords) pbits[lane] = 0;
+        uint32_t qh = 0, qt = 0;  // ring head and tail (free-running)
+        __syncwarp();
+        for (uint32_t t0 = 0; t0 < len; t0 += 32 * LS_UNROLL) {
+          // the loads of LS_UNROLL chunks are in flight together: one L2 round trip for all
+          PointTol pb[LS_UNROLL];
+#pragma unroll
+          for (uint32_t k = 0; k < LS_UNROLL; k++) {
+            const uint32_t t = t0 + 32 * k + lane;
+            const uint32_t j = t < len ? list[t] : a;  // a: any valid MD for idle lanes
+            pb[k] = PointTol{__ldg(&B.md_lo4[j]), __ldg(&B.md_cst[j])};
           }
-          count += __popc(bal);
+#pragma unroll
+          for (uint32_t k = 0; k < LS_UNROLL; k++) {
+            const uint32_t t = t0 + 32 * k + lane;
+            const bool h = t < len && ls_head_pt(C, pa, pb[k]);
+            const uint32_t hb = __ballot_sync(FULL, h);
+            if (h) queue[(qt + __popc(hb & lt)) & (LS_RING - 1)] = t;
+            qt += __popc(hb);
+          }
+          __syncwarp();
+          while (qt - qh >= 32) {
+            const uint32_t q = queue[(qh + lane) & (LS_RING - 1)];
+            if (ls_tail(C, G, B, pa, pau, rnext, a_barrel, ubase, list[q])) atomicOr(&pbits[q >> 5], 1u << (q & 31));
+            qh += 32;
+          }
         }
+        if (lane < qt - qh) {
+          const uint32_t q = queue[(qh + lane) & (LS_RING - 1)];
+          if (ls_tail(C, G, B, pa, pau, rnext, a_barrel, ubase, list[q])) atomicOr(&pbits[q >> 5], 1u << (q & 31));
+        }
+        __syncwarp();
+        // records: the non-zero words, in chunk order
+        const uint32_t word = lane < nwords ? pbits[lane] : 0u;
+        const uint32_t nzb = __ballot_sync(FULL, word != 0u);
+        const uint32_t nrec = __popc(nzb);
+        const uint32_t count = __reduce_add_sync(FULL, __popc(word));
+        const uint32_t rk = __popc(nzb & lt);  // this lane's record index when word != 0
         uint32_t mbase = NONE;
-        if (count > 0 && !spill) {
+        if (count > 0) {
           const uint32_t need = 1 + 2 * nrec;
           uint32_t mb = NONE;
           if (lane == 0) {
@@ -647,9 +691,9 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           wa.end = __shfl_sync(FULL, wa.end, 0);
           if (mbase != NONE) {
             if (lane == 0) B.mask[mbase] = nrec;
-            if (lane < nrec) {
-              B.mask[mbase + 1 + 2 * lane] = rt;
-              B.mask[mbase + 2 + 2 * lane] = rb;
+            if (word != 0u) {
+              B.mask[mbase + 1 + 2 * rk] = lane << 5;
+              B.mask[mbase + 2 + 2 * rk] = word;
             }
           }
         }
@@ -657,6 +701,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           B.mask_off[a] = mbase;
           B.ls_cnt[a] = count;
         }
+        __syncwarp();  // pbits and the queue are reused by the next MD
       }
     }
     __syncwarp();  // the list is rewritten by the next unit
@@ -1079,11 +1124,10 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
           const Circle3 fu = circle3(md_point(B, B.t5_m0[t]), md_point(B, B.t5_m2[t]), md_point(B, B.t5_m4[t]));
           return fabsf(fabsf(B.t5_kfull[t]) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
         },
-        [&](uint32_t, uint32_t t, ScorePayload& pl) {
-          float score = 0.0f;
-          pls_anchor(C, h, md_point(B, B.t5_m0[t]), score);
-          pls_anchor(C, h, md_point(B, B.t5_m1[t]), score);
-          pls_anchor(C, h, md_point(B, B.t5_m2[t]), score);
+        [&](uint32_t i, uint32_t t, ScorePayload& pl) {
+          // anchors m0, m1, m2 are the parent pT3's a, b, c, summed in the same order: its
+          // score is this sum after three terms, bit for bit
+          float score = B.pt3_score[x0 + i];
           pls_anchor(C, h, md_point(B, B.t5_m3[t]), score);
           pls_anchor(C, h, md_point(B, B.t5_m4[t]), score);
           pl.score = score;
@@ -1502,7 +1546,7 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   k_md<true><<<g, bs, 0, s>>>(C, G, B);
   mk(8);
   const uint32_t lcap = L.ls_list_cap;
-  const size_t ls_smem = (bs / 32) * lcap * sizeof(uint32_t);
+  const size_t ls_smem = lcap ? (bs / 32) * (lcap + LS_EXTRA_WORDS) * sizeof(uint32_t) : 0;
   k_ls<false><<<g, bs, ls_smem, s>>>(C, G, B, lcap);
   mk(9);
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
