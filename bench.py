@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--served-rate", type=float, default=0.0, help="offered Hz (0: 0.8 x batched rate)")
     ap.add_argument("--cpu-sample", type=int, default=8, help="events for the CPU-oracle baseline (0 = skip)")
     ap.add_argument("--tune", type=int, default=1, help="autotune the launch configuration first (1) or not (0)")
+    ap.add_argument("--config", default="", help="fixed launch configuration block_size,blocks_per_sm,ls_list_cap "
+                                                 "(skips the autotuner)")
     return ap.parse_args()
 
 
@@ -224,6 +226,25 @@ def algorithmic_bytes(kernel, st, n_units):
     return table.get(kernel)
 
 
+# FP32 operations (add, sub, mul, div, sqrt, compare; abs is free) of the LS cuts, counted
+# from their expressions: the r-z pointing test on every connection-map candidate pair, the
+# bending test and the chord-direction tests of both MDs on every LS that comes out.  A
+# lower bound on the cut arithmetic any implementation of the selection performs.
+LS_OPS_RZ = 21
+LS_OPS_REST = 20 + 38
+
+
+def algorithmic_ops(kernel, st):
+    if kernel == "ls_count" and st.get("ls_candidates"):
+        return LS_OPS_RZ * st["ls_candidates"] + LS_OPS_REST * st["n_ls"]
+    return None
+
+
+def alu_peak(n_sm, sm_mhz):
+    """FP32 ops/s: every SM issues 128 FP32 lanes per clock (4 partitions x 32)."""
+    return n_sm * 128 * sm_mhz * 1e6
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -264,7 +285,10 @@ def main():
     dev_batches = [to_device(b) for b in batches]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     tuning = {}
-    if args.tune:
+    if args.config:
+        bs, bps, cap = (int(v) for v in args.config.split(","))
+        tuning = {"block_size": bs, "blocks_per_sm": bps, "ls_list_cap": cap}
+    elif args.tune:
         from paper_2407_18231_gb300 import autotune
         space = {"block_size": [128, 256], "blocks_per_sm": [2, 4, 8], "ls_list_cap": [128, 512]}
         tuning = autotune.tune(geom.modules, events[:8], device=local, space=space, reps=2)["best"]
@@ -372,15 +396,30 @@ def main():
     per_launch_ms = tot_ms / nl
     n_units = B * geom.n_modules
     algo = algorithmic_bytes(kname, pst, n_units)
+    ops = algorithmic_ops(kname, pst)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     roof = None
+    share = tot_ms / sum(v[1] for v in acc.values())
+    hbm = None
     if algo is not None:
         achieved = algo / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": recorded_traffic(kname), "peak_source": peak_src,
-                "algorithmic_bytes": algo, "ms_per_launch": per_launch_ms,
-                "kernel_share": tot_ms / sum(v[1] for v in acc.values())}
+        hbm = {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+               "peak_source": peak_src, "algorithmic_bytes": algo}
+    if ops is not None:
+        # the cut chain is FP32 arithmetic on an L2-resident working set: the ALU roof binds
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clk.summary().get("sm_max_mhz") or 2070.0
+        peak = alu_peak(n_sm, mhz) / 1e12
+        achieved = ops / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(kname),
+                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz",
+                "algorithmic_ops": ops, "ls_candidates": pst["ls_candidates"], "ms_per_launch": per_launch_ms,
+                "kernel_share": share, "hbm": hbm}
+    elif hbm is not None:
+        roof = {"bound": "hbm", "kernel": kname, "traffic": recorded_traffic(kname), "ms_per_launch": per_launch_ms,
+                "kernel_share": share, **hbm}
     kernel_times = {k: round(v[1] / reps, 4) for k, v in sorted(acc.items(), key=lambda kv: -kv[1][1])}
 
     # ---- CPU oracle on a bounded sample of the same events

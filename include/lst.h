@@ -210,6 +210,7 @@ typedef struct lst_stats {
   uint32_t reruns;        /* re-runs after an object list outgrew its storage */
   uint32_t kernels;       /* kernels launched per run */
   uint64_t device_bytes;  /* device memory held by the context */
+  uint64_t ls_candidates; /* MD pairs of connected modules the LS selection tested */
 } lst_stats;
 lst_status lst_get_stats(lst_ctx *ctx, lst_stats *out);
 

@@ -36,6 +36,7 @@ struct Hdr {
   uint32_t err;
   uint32_t pad2[3];
   uint32_t mask_used[8];  // join scratch words taken per stage (MD, LS, T3, T5, pT3, pT5)
+  unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)
 };
 
 // Geometry tables (device pointers) and per-geometry scalars.

@@ -1032,6 +1032,7 @@ void collect(lst_ctx* c, Pipeline& P, lst_result_id* outs, uint32_t* n_tc_per_ev
   c->stats.n_pt3 = h.tot[T_PT3];
   c->stats.n_pt5 = h.tot[T_PT5];
   c->stats.n_tc = h.tot[T_TC];
+  c->stats.ls_candidates = h.ls_cand;
   c->stats.kernels = (uint32_t)P.kernels;
   c->stats.device_bytes = P.dev_bytes + c->geo.dev_bytes;
 }

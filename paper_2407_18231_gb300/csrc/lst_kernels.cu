@@ -565,6 +565,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
   uint32_t* queue = list + list_cap;
   uint32_t* pbits = queue + LS_RING;
   WarpAlloc wa;
+  unsigned long long n_cand = 0;  // count pass: candidate pairs this warp tested
   WARP_LOOP(u, nu) {
     const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
     if (a0 == a1) continue;
@@ -588,6 +589,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
       len += __shfl_sync(FULL, incl, 31);
     }
     __syncwarp();
+    if (!FILL) n_cand += (unsigned long long)len * (a1 - a0);
     if (len > list_cap) {
       for (uint32_t a = a0; a < a1; a++) ls_md_join<FILL>(C, G, B, a, ev, A, wa);
       continue;
@@ -706,6 +708,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
     }
     __syncwarp();  // the list is rewritten by the next unit
   }
+  if (!FILL && lane == 0 && n_cand) atomicAdd(&B.hdr->ls_cand, n_cand);
 }
 
 // ------------------------------------------------------------------ T3

@@ -116,6 +116,11 @@ def test_bench_workload_sampled_parity(sess_full, ora_full):
     ids = sess_full.run_batch(evs)
     for i in (0, 7, 15):
         compare(sess_full, ids[i], oracle.run(ora_full, evs[i]), evs[i], f"bench event {i}")
+    # the candidate tally behind the LS roofline: every LS is a tested pair, and no MD is
+    # tested against more MDs than the batch holds
+    st = sess_full.stats()
+    assert st["n_ls"] <= st["ls_candidates"] <= st["n_md"] * st["n_md"]
+    assert st["ls_candidates"] > 20 * st["n_ls"]  # the cuts reject almost every pair
 
 
 def test_batched_barrel_workload(sess_barrel, ora_barrel):
