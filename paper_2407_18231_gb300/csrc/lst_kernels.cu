@@ -448,37 +448,129 @@ __global__ void k_hits_sort(GeoView G, BufView B) {
 }
 
 // ------------------------------------------------------------------ Mini Doublets
-// Unit = (event, module); candidates = lower-sensor hits x upper-sensor hits (Sec. 1).
+// Candidates of unit (event, module) = lower-sensor hits x upper-sensor hits (Sec. 1).
+__device__ __forceinline__ bool md_test(const MethodConst& C, const float4& cst, const float4& lo, const float4& up) {
+  const PointTol a{lo, cst}, b{up, cst};
+  return pair_rz(C, a, b) && pair_bend(C, a, b, cst.w);
+}
+
+// One unit per warp with join records; used for groups holding a unit with very many
+// candidate pairs.
+template <bool FILL>
+__device__ __forceinline__ void md_unit_join(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t u,
+                                             WarpAlloc& wa) {
+  const uint32_t lo_b = B.sen_off[2 * u], up_b = B.sen_off[2 * u + 1], up_e = B.sen_off[2 * u + 2];
+  const uint32_t n_lo = up_b - lo_b, n_up = up_e - up_b;
+  const float4 cst = G.modc[u % G.nm];
+  const uint32_t base = FILL ? B.md_off[u] : 0u;
+  const uint32_t n_out = FILL ? B.md_off[u + 1] - base : 0u;
+  const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[0], &B.mask_off[u]};
+  const uint32_t cnt = warp_join<FILL, NoPayload>(
+      n_lo, base, n_out, js, wa, [&](uint32_t, uint32_t& b, uint32_t& c) { b = up_b; c = n_up; },
+      [&](uint32_t i, uint32_t j) { return md_test(C, cst, B.hit4[lo_b + i], B.hit4[j]); },
+      [&](uint32_t, uint32_t, NoPayload&) {},
+      [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
+        B.md_unit[pos] = u;
+        B.md_lo4[pos] = B.hit4[lo_b + i];
+        B.md_up4[pos] = B.hit4[j];
+        B.md_cst[pos] = cst;
+        B.md_lo_idx[pos] = B.hit_idx[lo_b + i];
+        B.md_up_idx[pos] = B.hit_idx[j];
+      });
+  if (!FILL && lane_id() == 0) B.md_cnt[u] = cnt;
+}
+
+constexpr uint32_t MD_BIG = 1u << 20;  // candidate pairs above which a unit takes the per-unit join
+
+// A module sensor holds a few hits, so a unit has ~10 candidate pairs: one warp takes 32
+// units and walks their concatenated pairs 32 at a time, lower-major inside a unit (the
+// canonical MD order within the unit; every unit writes at its own offset).  A unit's
+// pairs in a chunk are a contiguous lane range, so its passes are popc(ballot & range);
+// the fill pass re-tests (the MD test is a few dozen operations) and ranks each pass by
+// the unit's passes in earlier chunks plus those of lower lanes in this chunk.
 template <bool FILL>
 __global__ void __launch_bounds__(512) k_md(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t nu = H->n_ev * G.nm;
+  const uint32_t ng = (nu + 31) >> 5;
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  // slot s = 32 grp + lane owns unit s P mod nu (P prime, not a divisor of nu: a
+  // permutation), so a group mixes modules and events and the busy inner-layer modules
+  // spread over all warps instead of piling up in a few
+  const uint32_t P = (nu % 1000003u) ? 1000003u : 999983u;
   WarpAlloc wa;
-  WARP_LOOP(u, nu) {
-    const uint32_t lo_b = B.sen_off[2 * u], up_b = B.sen_off[2 * u + 1], up_e = B.sen_off[2 * u + 2];
-    const uint32_t n_lo = up_b - lo_b, n_up = up_e - up_b;
-    const uint32_t m = u % G.nm;
-    const float4 cst = G.modc[m];
-    const uint32_t base = FILL ? B.md_off[u] : 0u;
-    const uint32_t n_out = FILL ? B.md_off[u + 1] - base : 0u;
-    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[0], &B.mask_off[u]};
-    const uint32_t cnt = warp_join<FILL, NoPayload>(
-        n_lo, base, n_out, js, wa, [&](uint32_t, uint32_t& b, uint32_t& c) { b = up_b; c = n_up; },
-        [&](uint32_t i, uint32_t j) {
-          const PointTol a{B.hit4[lo_b + i], cst}, b{B.hit4[j], cst};
-          return pair_rz(C, a, b) && pair_bend(C, a, b, cst.w);
-        },
-        [&](uint32_t, uint32_t, NoPayload&) {},
-        [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
-          B.md_unit[pos] = u;
-          B.md_lo4[pos] = B.hit4[lo_b + i];
-          B.md_up4[pos] = B.hit4[j];
+  WARP_LOOP(grp, ng) {
+    const uint32_t slot = grp * 32 + lane;
+    const bool valid = slot < nu;
+    const uint32_t u = valid ? (uint32_t)(((unsigned long long)slot * P) % nu) : 0u;
+    uint32_t lo_b = 0, n_lo = 0, n_up = 0, mod = 0;
+    if (valid) {
+      lo_b = B.sen_off[2 * u];
+      const uint32_t up_b = B.sen_off[2 * u + 1], up_e = B.sen_off[2 * u + 2];
+      n_lo = up_b - lo_b;
+      n_up = up_e - up_b;
+      mod = u % G.nm;
+    }
+    const float rcp = n_up ? 1.0f / (float)n_up : 0.0f;
+    const unsigned long long c64 = (unsigned long long)n_lo * n_up;
+    if (__any_sync(FULL, c64 >= MD_BIG)) {
+      for (uint32_t k = 0; k < 32; k++) {
+        const uint32_t uk = __shfl_sync(FULL, u, k);
+        if (grp * 32 + k < nu) md_unit_join<FILL>(C, G, B, uk, wa);
+      }
+      continue;
+    }
+    const uint32_t c = (uint32_t)c64;
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t start = incl - c;  // this lane's unit: pairs [start, incl)
+    uint32_t run = 0;                 // passes of this lane's unit so far
+    const uint32_t obase = FILL && valid ? B.md_off[u] : 0u;
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t so = __shfl_sync(FULL, start, o);
+      const uint32_t lbo = __shfl_sync(FULL, lo_b, o);
+      const uint32_t nlo = __shfl_sync(FULL, n_lo, o);
+      const uint32_t nup = __shfl_sync(FULL, n_up, o);
+      const float rcpo = __shfl_sync(FULL, rcp, o);
+      const uint32_t mo = __shfl_sync(FULL, mod, o);
+      // q = i nup + j: q < 2^20, so the rounded quotient is off by at most one
+      const uint32_t q = cc - so;
+      uint32_t i = (uint32_t)((float)q * rcpo);
+      if (i * nup > q) i--;
+      else if ((i + 1) * nup <= q) i++;
+      const uint32_t j = q - i * nup;
+      const uint32_t ih = lbo + i, jh = lbo + nlo + j;
+      const uint32_t uo = __shfl_sync(FULL, u, o);
+      const float4 cst = G.modc[mo];
+      const float4 hl = B.hit4[ih], hu = B.hit4[jh];
+      const bool pass = cand < total && md_test(C, cst, hl, hu);
+      const uint32_t bal = __ballot_sync(FULL, pass);
+      // this lane's unit's lanes in the chunk: [lo, hi)
+      const uint32_t lo = start > t0 ? min(start - t0, 32u) : 0u;
+      const uint32_t hi = incl > t0 ? min(incl - t0, 32u) : 0u;
+      const uint32_t mask = hi > lo ? ((hi == 32u ? FULL : (1u << hi) - 1u) & ~((1u << lo) - 1u)) : 0u;
+      if (FILL) {
+        const uint32_t lo_o = __shfl_sync(FULL, lo, o);
+        const uint32_t run_o = __shfl_sync(FULL, run, o);
+        const uint32_t base_o = __shfl_sync(FULL, obase, o);
+        if (pass) {
+          const uint32_t pos = base_o + run_o + __popc(bal & lt & ~((1u << lo_o) - 1u));
+          B.md_unit[pos] = uo;
+          B.md_lo4[pos] = hl;
+          B.md_up4[pos] = hu;
           B.md_cst[pos] = cst;
-          B.md_lo_idx[pos] = B.hit_idx[lo_b + i];
-          B.md_up_idx[pos] = B.hit_idx[j];
-        });
-    if (!FILL && lane_id() == 0) B.md_cnt[u] = cnt;
+          B.md_lo_idx[pos] = B.hit_idx[ih];
+          B.md_up_idx[pos] = B.hit_idx[jh];
+        }
+      }
+      run += __popc(bal & mask);
+    }
+    if (!FILL && valid) B.md_cnt[u] = run;
   }
 }
 
