@@ -76,6 +76,19 @@ __device__ __forceinline__ bool md_dir(const MethodConst& C, const PointTol& lo,
   return crs <= tol;
 }
 
+// The MD half of md_dir, for an MD whose direction terms were stored by md_direction:
+// the same operations in the same order, so the same decision bit for bit.
+__device__ __forceinline__ float4 md_direction(const float4& lo, const float4& up, const float4& cst) {
+  const float dx = up.x - lo.x;
+  const float dy = up.y - lo.y;
+  return make_float4(dx, dy, sqrtf(dx * dx + dy * dy), cst.y + cst.y);
+}
+__device__ __forceinline__ bool md_dir_pre(const MethodConst& C, const float4& d, float cx, float cy, float clen) {
+  const float crs = fabsf(d.x * cy - d.y * cx);
+  const float tol = clen * (d.z * clen * C.HINV + C.EDIR + d.w);
+  return crs <= tol;
+}
+
 // Barrel-to-disk LS: the anchors' r-z line must leave the barrel before the next layer.
 __device__ __forceinline__ bool exit_ok(const PointTol& a, const PointTol& b, float rnext, float zb_half) {
   const float Zb = b.p.z > 0.0f ? zb_half : -zb_half;

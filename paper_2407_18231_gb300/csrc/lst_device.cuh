@@ -37,6 +37,7 @@ struct Hdr {
   uint32_t pad2[3];
   uint32_t mask_used[8];  // join scratch words taken per stage (MD, LS, T3, T5, pT3, pT5)
   unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)
+  uint32_t work[8];            // work counters of the dynamically scheduled kernels
 };
 
 // Geometry tables (device pointers) and per-geometry scalars.
@@ -70,6 +71,7 @@ struct BufView {
   // MD
   uint32_t *md_cnt, *md_off, *md_unit, *md_lo_idx, *md_up_idx;
   float4 *md_lo4, *md_up4, *md_cst;
+  float4 *md_dir4;  // upper - lower hit: dx, dy, transverse length, rho + rho
   // LS
   uint32_t *ls_cnt, *ls_off, *ls_in, *ls_out;
   // T3: per LS count/offset of the T3s built on it, per MD offset of those starting there

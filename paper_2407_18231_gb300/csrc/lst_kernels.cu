@@ -223,6 +223,36 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t* off, uint32_t n, u
 #define WARP_LOOP(unit, n)                                                                         \
   for (uint32_t unit = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; unit < (n);                   \
        unit += (gridDim.x * blockDim.x) >> 5)
+// Dynamic scheduling for joins whose units differ widely in cost: warps take batches of G
+// units from a counter in the header (zeroed with every launch) and request the next batch
+// before working on the current one, so the atomic's latency overlaps the work.  When the
+// units are few (at most 4 batches per warp: one event) a warp's first batch is fixed
+// instead (warp w takes [w G, w G + G), the counter hands out the rest), which spares the
+// burst of atomics at launch that would dominate so short a kernel.  `continue` moves to
+// the next unit.
+struct WarpQueue {
+  uint32_t* ctr;
+  uint32_t g, base, cur;
+  __device__ __forceinline__ WarpQueue(uint32_t* c, uint32_t grain, uint32_t n) : ctr(c), g(grain) {
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    if (n <= 4u * nw * grain) {
+      base = nw * grain;
+      cur = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * grain;
+    } else {
+      base = 0;
+      cur = grab();
+    }
+  }
+  __device__ __forceinline__ uint32_t grab() {
+    uint32_t v = 0;
+    if (lane_id() == 0) v = atomicAdd(ctr, g);
+    return base + __shfl_sync(0xFFFFFFFFu, v, 0);
+  }
+};
+#define DYN_LOOP(k, ctr, n, grain)                                                                       \
+  for (WarpQueue wq_(ctr, grain, n); wq_.cur < (n);)                                                   \
+    for (uint32_t e_ = min(wq_.cur + (grain), (uint32_t)(n)), nxt_ = wq_.grab(), k = wq_.cur;            \
+         k < e_ || (wq_.cur = nxt_, false); k++)
 #define THREAD_LOOP(i, n) \
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
@@ -474,6 +504,7 @@ __device__ __forceinline__ void md_unit_join(const MethodConst& C, const GeoView
         B.md_lo4[pos] = B.hit4[lo_b + i];
         B.md_up4[pos] = B.hit4[j];
         B.md_cst[pos] = cst;
+        B.md_dir4[pos] = md_direction(B.hit4[lo_b + i], B.hit4[j], cst);
         B.md_lo_idx[pos] = B.hit_idx[lo_b + i];
         B.md_up_idx[pos] = B.hit_idx[j];
       });
@@ -564,6 +595,7 @@ __global__ void __launch_bounds__(512) k_md(MethodConst C, GeoView G, BufView B)
           B.md_lo4[pos] = hl;
           B.md_up4[pos] = hu;
           B.md_cst[pos] = cst;
+          B.md_dir4[pos] = md_direction(hl, hu, cst);
           B.md_lo_idx[pos] = B.hit_idx[ih];
           B.md_up_idx[pos] = B.hit_idx[jh];
         }
@@ -578,7 +610,7 @@ __device__ __forceinline__ PointTol md_point(const BufView& B, uint32_t m) { ret
 __device__ __forceinline__ PointTol md_upper(const BufView& B, uint32_t m) { return PointTol{B.md_up4[m], B.md_cst[m]}; }
 
 // ------------------------------------------------------------------ Line Segments
-// The LS selection of ls_select for anchors (pa, pau) and MD j, loading the rest of MD j
+// The LS selection of ls_select for anchor pa and MD j, loading the rest of MD j
 // only when the cheap tests pass.
 // Split in two so that a warp can queue the candidates passing the cheap head and run the
 // tail only on full warps: ls_test = ls_head && ls_tail.
@@ -590,20 +622,28 @@ __device__ __forceinline__ bool ls_head(const MethodConst& C, const BufView& B, 
   return ls_head_pt(C, pa, md_point(B, j));
 }
 
-__device__ __forceinline__ bool ls_tail(const MethodConst& C, const GeoView& G, const BufView& B, const PointTol& pa,
-                                        const PointTol& pau, float rnext, bool a_barrel, uint32_t ubase, uint32_t j) {
+// The rest of ls_select after the head: the barrel exit when the pair goes from a barrel
+// module to a disk (`exit`), then both MD directions against the chord, from the
+// directions stored per MD (da: the anchor's).
+__device__ __forceinline__ bool ls_tail_k(const MethodConst& C, const GeoView& G, const BufView& B, const PointTol& pa,
+                                          const float4& da, float rnext, bool exit, uint32_t j) {
   const PointTol pb = md_point(B, j);
-  if (a_barrel && G.subdet[B.md_unit[j] - ubase] == 1 && !exit_ok(pa, pb, rnext, G.zb_half)) return false;
-  const PointTol pbu = md_upper(B, j);
+  if (exit && !exit_ok(pa, pb, rnext, G.zb_half)) return false;
+  const float4 db = B.md_dir4[j];
   const float cx = pb.p.x - pa.p.x;
   const float cy = pb.p.y - pa.p.y;
   const float clen = sqrtf(cx * cx + cy * cy);
-  return md_dir(C, pa, pau, cx, cy, clen) && md_dir(C, pb, pbu, cx, cy, clen);
+  return md_dir_pre(C, da, cx, cy, clen) && md_dir_pre(C, db, cx, cy, clen);
+}
+
+__device__ __forceinline__ bool ls_tail(const MethodConst& C, const GeoView& G, const BufView& B, const PointTol& pa,
+                                        const float4& da, float rnext, bool a_barrel, uint32_t ubase, uint32_t j) {
+  return ls_tail_k(C, G, B, pa, da, rnext, a_barrel && G.subdet[B.md_unit[j] - ubase] == 1, j);
 }
 
 __device__ __forceinline__ bool ls_test(const MethodConst& C, const GeoView& G, const BufView& B, const PointTol& pa,
-                                        const PointTol& pau, float rnext, bool a_barrel, uint32_t ubase, uint32_t j) {
-  return ls_head(C, B, pa, j) && ls_tail(C, G, B, pa, pau, rnext, a_barrel, ubase, j);
+                                        const float4& da, float rnext, bool a_barrel, uint32_t ubase, uint32_t j) {
+  return ls_head(C, B, pa, j) && ls_tail(C, G, B, pa, da, rnext, a_barrel, ubase, j);
 }
 
 // Per-MD LS join (candidates = MDs of every module in the connection map of A), used for
@@ -611,7 +651,8 @@ __device__ __forceinline__ bool ls_test(const MethodConst& C, const GeoView& G, 
 template <bool FILL>
 __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t a,
                                            uint32_t ev, uint32_t A, WarpAlloc& wa) {
-  const PointTol pa = md_point(B, a), pau = md_upper(B, a);
+  const PointTol pa = md_point(B, a);
+  const float4 da = B.md_dir4[a];
   const float rnext = G.rnext[A];
   const bool a_barrel = G.subdet[A] == 0;
   const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
@@ -626,7 +667,7 @@ __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& 
         b = B.md_off[u];
         c = B.md_off[u + 1] - b;
       },
-      [&](uint32_t, uint32_t j) { return ls_test(C, G, B, pa, pau, rnext, a_barrel, ubase, j); },
+      [&](uint32_t, uint32_t j) { return ls_test(C, G, B, pa, da, rnext, a_barrel, ubase, j); },
       [&](uint32_t, uint32_t, NoPayload&) {},
       [&](uint32_t pos, uint32_t, uint32_t j, const NoPayload&) {
         B.ls_in[pos] = a;
@@ -658,18 +699,29 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
   uint32_t* pbits = queue + LS_RING;
   WarpAlloc wa;
   unsigned long long n_cand = 0;  // count pass: candidate pairs this warp tested
-  WARP_LOOP(u, nu) {
+  const uint32_t n_ev = H->n_ev;
+  auto unit = [&](const uint32_t u) {
     const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
-    if (a0 == a1) continue;
-    if (FILL && B.ls_off[a0] == B.ls_off[a1]) continue;  // no LS starts on this module
+    if (a0 == a1) return;
+    if (FILL && B.ls_off[a0] == B.ls_off[a1]) return;  // no LS starts on this module
     const uint32_t ev = u / G.nm, A = u - ev * G.nm;
     const uint32_t ubase = ev * G.nm;
     const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
-    // flattened neighbour list
-    uint32_t len = 0;
+    // flattened neighbour list; disk modules have the highest ids, so the disk entries are
+    // normally a suffix [t_disk, len) of the list (checked: otherwise each candidate's
+    // module is looked up)
+    uint32_t len = 0, t_disk = NONE;
+    bool suffix = true;
     for (uint32_t g0 = 0; g0 < nb; g0 += 32) {
       uint32_t b = 0, c = 0;
-      if (g0 + lane < nb) {
+      bool disk = false;
+      if (!FILL && g0 + lane < nb) {
+        const uint32_t Bm = G.conn[nb0 + g0 + lane];
+        const uint32_t uu = ubase + Bm;
+        b = B.md_off[uu];
+        c = B.md_off[uu + 1] - b;
+        disk = G.subdet[Bm] == 1;
+      } else if (FILL && g0 + lane < nb) {
         const uint32_t uu = ubase + G.conn[nb0 + g0 + lane];
         b = B.md_off[uu];
         c = B.md_off[uu + 1] - b;
@@ -678,18 +730,30 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
       const uint32_t o = len + incl - c;
       for (uint32_t k = 0; k < c; k++)
         if (o + k < list_cap) list[o + k] = b + k;
+      if (!FILL) {
+        const uint32_t dm = __ballot_sync(FULL, disk && c > 0), bm = __ballot_sync(FULL, !disk && c > 0);
+        if (t_disk != NONE) {
+          if (bm) suffix = false;
+        } else if (dm) {
+          const uint32_t fd = __ffs(dm) - 1;
+          if (fd < 31 && (bm >> (fd + 1))) suffix = false;
+          t_disk = __shfl_sync(FULL, o, fd);
+        }
+      }
       len += __shfl_sync(FULL, incl, 31);
     }
+    if (t_disk == NONE) t_disk = len;
     __syncwarp();
     if (!FILL) n_cand += (unsigned long long)len * (a1 - a0);
     if (len > list_cap) {
       for (uint32_t a = a0; a < a1; a++) ls_md_join<FILL>(C, G, B, a, ev, A, wa);
-      continue;
+      return;
     }
     const float rnext = G.rnext[A];
     const bool a_barrel = G.subdet[A] == 0;
     for (uint32_t a = a0; a < a1; a++) {
-      const PointTol pa = md_point(B, a), pau = md_upper(B, a);
+      const PointTol pa = md_point(B, a);
+      const float4 da = B.md_dir4[a];
       if (FILL) {
         const uint32_t base = B.ls_off[a], n_out = B.ls_off[a + 1] - base;
         if (n_out == 0) continue;
@@ -708,7 +772,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           }
         } else {
           for (uint32_t t0 = 0; t0 < len; t0 += 32) {
-            const bool pass = t0 + lane < len && ls_test(C, G, B, pa, pau, rnext, a_barrel, ubase, list[t0 + lane]);
+            const bool pass = t0 + lane < len && ls_test(C, G, B, pa, da, rnext, a_barrel, ubase, list[t0 + lane]);
             const uint32_t bal = __ballot_sync(FULL, pass);
             if (pass) {
               const uint32_t pos = base + count + __popc(bal & lt);
@@ -745,13 +809,17 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           __syncwarp();
           while (qt - qh >= 32) {
             const uint32_t q = queue[(qh + lane) & (LS_RING - 1)];
-            if (ls_tail(C, G, B, pa, pau, rnext, a_barrel, ubase, list[q])) atomicOr(&pbits[q >> 5], 1u << (q & 31));
+            const uint32_t j = list[q];
+            const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
+            if (ls_tail_k(C, G, B, pa, da, rnext, exit, j)) atomicOr(&pbits[q >> 5], 1u << (q & 31));
             qh += 32;
           }
         }
         if (lane < qt - qh) {
           const uint32_t q = queue[(qh + lane) & (LS_RING - 1)];
-          if (ls_tail(C, G, B, pa, pau, rnext, a_barrel, ubase, list[q])) atomicOr(&pbits[q >> 5], 1u << (q & 31));
+          const uint32_t j = list[q];
+          const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
+          if (ls_tail_k(C, G, B, pa, da, rnext, exit, j)) atomicOr(&pbits[q >> 5], 1u << (q & 31));
         }
         __syncwarp();
         // records: the non-zero words, in chunk order
@@ -799,6 +867,15 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
       }
     }
     __syncwarp();  // the list is rewritten by the next unit
+  
+  };
+  if (FILL) {
+    // the fill pass replays records: cheap per unit, the static split balances it
+    WARP_LOOP(u, nu) unit(u);
+  } else {
+    // module-major order (unit k = module k / n_ev of event k % n_ev) taken dynamically:
+    // module ids start with the innermost, busiest layers, so expensive units go first
+    DYN_LOOP(k, &B.hdr->work[0], nu, 2) unit((k % n_ev) * G.nm + k / n_ev);
   }
   if (!FILL && lane == 0 && n_cand) atomicAdd(&B.hdr->ls_cand, n_cand);
 }
@@ -903,13 +980,6 @@ __global__ void k_t5_md_off(BufView B) {
 }
 
 // ------------------------------------------------------------------ pLS module lookup
-__device__ __forceinline__ void add_cand(uint32_t* list, uint32_t& n, uint32_t id) {
-  if (id == NONE) return;
-  for (uint32_t i = 0; i < n; i++)
-    if (list[i] == id) return;
-  list[n++] = id;
-}
-
 __device__ __forceinline__ bool in_sector(const GeoView& G, uint32_t id, float px, float py) {
   const float4 e = G.mod_e[id];
   const float c0 = e.x * py - e.y * px;
@@ -941,19 +1011,6 @@ __device__ int find_sector(const GeoView& G, uint32_t row, float px, float py) {
   return -1;
 }
 
-__device__ void add_row_cands(const GeoView& G, int s, int row, float px, float py, uint32_t* list, uint32_t& n) {
-  if (row < 0 || (uint32_t)row >= G.surf_nrows[s]) return;
-  const uint32_t r = G.surf_row_base[s] + (uint32_t)row;
-  if (G.row_nphi[r] == 0) return;
-  const int k = find_sector(G, r, px, py);
-  if (k < 0) return;
-  const int nphi = (int)G.row_nphi[r];
-  for (int d = -1; d <= 1; d++) {
-    const int kk = ((k + d) % nphi + nphi) % nphi;
-    add_cand(list, n, G.row_mods[G.row_mod_base[r] + kk]);
-  }
-}
-
 __device__ __forceinline__ uint32_t row0_module(const GeoView& G, int s) {
   if (G.surf_nrows[s] == 0) return NONE;
   const uint32_t r = G.surf_row_base[s];
@@ -961,15 +1018,91 @@ __device__ __forceinline__ uint32_t row0_module(const GeoView& G, int s) {
   return G.row_mods[G.row_mod_base[r]];
 }
 
-// Unit = pLS: helix parameters, then the modules of barrel layers 1-2 and disks 1-2 its
-// helix crosses first, each with its +-1 neighbours (Sec. 1: pLSs join T3s and T5s).
+// The point where the helix of h first meets surface `which` (0, 1: barrel layers 1, 2;
+// 2, 3: the first two disks on its pz side) and the row index of that point on the
+// surface; false when it does not meet the surface within the rows (+- 2 rows of margin).
+__device__ __forceinline__ bool pls_surface_point(const MethodConst& C, const GeoView& G, const PlsHelix& h,
+                                                  int which, int& sf, float& Px, float& Py, int& irow) {
+  if (which < 2) {
+    sf = which;
+    if (G.surf_nrows[sf] == 0) return false;
+    const float rl = G.mod_g[G.surf_first[sf]].x;
+    const float d2 = h.cx * h.cx + h.cy * h.cy;
+    const float d = sqrtf(d2);
+    const float a = (rl * rl - h.R * h.R + d2) / (2.0f * d);
+    const float h2 = rl * rl - a * a;
+    if (!(h2 >= 0.0f)) return false;
+    const float hh = sqrtf(h2);
+    const float ex = h.cx / d, ey = h.cy / d;
+    const float P1x = a * ex - hh * ey, P1y = a * ey + hh * ex;
+    const float P2x = a * ex + hh * ey, P2y = a * ey - hh * ex;
+    const float wx = h.x0 - h.cx, wy = h.y0 - h.cy;
+    const float cr1 = wx * (P1y - h.cy) - wy * (P1x - h.cx);
+    const float cr2 = wx * (P2y - h.cy) - wy * (P2x - h.cx);
+    const bool f1 = -h.q * cr1 > 0.0f;
+    const bool f2 = -h.q * cr2 > 0.0f;
+    const float dt1 = wx * (P1x - h.cx) + wy * (P1y - h.cy);
+    const float dt2 = wx * (P2x - h.cx) + wy * (P2y - h.cy);
+    if (f1 && f2) {
+      if (dt1 >= dt2) { Px = P1x; Py = P1y; } else { Px = P2x; Py = P2y; }
+    } else if (f1) {
+      Px = P1x; Py = P1y;
+    } else if (f2) {
+      Px = P2x; Py = P2y;
+    } else {
+      return false;
+    }
+    const float dxc = Px - h.x0, dyc = Py - h.y0;
+    const float chord = sqrtf(dxc * dxc + dyc * dyc);
+    const float sarc = arc_length(chord, h.R);
+    const float zP = h.z0 + sarc * h.cot;
+    const uint32_t m0 = row0_module(G, sf);
+    if (m0 == NONE) return false;
+    const float4 g0 = G.mod_g[m0];
+    const float zlen = g0.w - g0.z;
+    const float zhi = g0.z + (float)G.surf_nrows[sf] * zlen;
+    if (!(zP > g0.z - 2.0f * zlen && zP < zhi + 2.0f * zlen)) return false;
+    irow = (int)floorf((zP - g0.z) / zlen);
+    return true;
+  }
+  if (h.cot == 0.0f) return false;
+  sf = (h.cot > 0.0f ? 11 : 6) + (which - 2);
+  const uint32_t m0 = row0_module(G, sf);
+  if (m0 == NONE) return false;
+  const float4 g0 = G.mod_g[m0];
+  const float zd = g0.x;
+  const float sarc = (zd - h.z0) / h.cot;
+  if (!(sarc > 0.0f)) return false;
+  const float alpha = sarc / h.R;
+  if (!(alpha < C.PI)) return false;
+  float sa, ca;
+  sin_cos_series(alpha, sa, ca);
+  const float sn = -h.q * sa;
+  const float wx = h.x0 - h.cx, wy = h.y0 - h.cy;
+  Px = h.cx + (wx * ca - wy * sn);
+  Py = h.cy + (wx * sn + wy * ca);
+  const float rP = sqrtf(Px * Px + Py * Py);
+  const float rlen = g0.w - g0.z;
+  const float rhi = g0.z + (float)G.surf_nrows[sf] * rlen;
+  if (!(rP > g0.z - 2.0f * rlen && rP < rhi + 2.0f * rlen)) return false;
+  irow = (int)floorf((rP - g0.z) / rlen);
+  return true;
+}
+
+// Unit = pLS, one warp: helix parameters, then the modules of barrel layers 1-2 and disks
+// 1-2 its helix crosses first, each with its +-1 neighbours in phi and in row (Sec. 1:
+// pLSs join T3s and T5s).  Lane 3 w + d (w < 4, d < 3) looks up row (crossing row + d - 1)
+// of surface w; the <= 36 ids are sorted by a 64-wide bitonic network in registers and the
+// repeats dropped, which gives the ascending set of distinct ids.
 __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
   Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
-  THREAD_LOOP(p, n) {
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  WARP_LOOP(p, n) {
     const PlsIn s = H->pls[p];
-    B.pls_ev[p] = find_slot(H->pls_off, H->n_ev, p);
+    if (lane == 0) B.pls_ev[p] = find_slot(H->pls_off, H->n_ev, p);
     bool bad = !(isfinite(s.px) && isfinite(s.py) && isfinite(s.pz) && isfinite(s.x0) && isfinite(s.y0) &&
                  isfinite(s.z0)) ||
                (s.charge != 1 && s.charge != -1);
@@ -977,8 +1110,10 @@ __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
     h.pt = sqrtf(s.px * s.px + s.py * s.py);
     if (!(h.pt > 0.0f)) bad = true;
     if (bad) {
-      atomicOr(&H->err, ERR_BAD_INPUT);
-      B.pls_ncand[p] = 0;
+      if (lane == 0) {
+        atomicOr(&H->err, ERR_BAD_INPUT);
+        B.pls_ncand[p] = 0;
+      }
       continue;
     }
     h.R = h.pt / C.KB;
@@ -990,90 +1125,64 @@ __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
     h.cx = s.x0 + qR * uy;
     h.cy = s.y0 - qR * ux;
     h.cot = s.pz / h.pt;
-    B.pls_h0[p] = make_float4(h.x0, h.y0, h.z0, h.R);
-    B.pls_h1[p] = make_float4(h.cx, h.cy, h.cot, h.q);
-    B.pls_pt[p] = h.pt;
-    uint32_t list[MAX_CAND];
-    uint32_t nc = 0;
-    for (int sf = 0; sf < 2; sf++) {
-      if (G.surf_nrows[sf] == 0) continue;
-      const float rl = G.mod_g[G.surf_first[sf]].x;
-      const float d2 = h.cx * h.cx + h.cy * h.cy;
-      const float d = sqrtf(d2);
-      const float a = (rl * rl - h.R * h.R + d2) / (2.0f * d);
-      const float h2 = rl * rl - a * a;
-      if (!(h2 >= 0.0f)) continue;
-      const float hh = sqrtf(h2);
-      const float ex = h.cx / d, ey = h.cy / d;
-      const float P1x = a * ex - hh * ey, P1y = a * ey + hh * ex;
-      const float P2x = a * ex + hh * ey, P2y = a * ey - hh * ex;
-      const float wx = h.x0 - h.cx, wy = h.y0 - h.cy;
-      const float cr1 = wx * (P1y - h.cy) - wy * (P1x - h.cx);
-      const float cr2 = wx * (P2y - h.cy) - wy * (P2x - h.cx);
-      const bool f1 = -h.q * cr1 > 0.0f;
-      const bool f2 = -h.q * cr2 > 0.0f;
-      const float dt1 = wx * (P1x - h.cx) + wy * (P1y - h.cy);
-      const float dt2 = wx * (P2x - h.cx) + wy * (P2y - h.cy);
+    if (lane == 0) {
+      B.pls_h0[p] = make_float4(h.x0, h.y0, h.z0, h.R);
+      B.pls_h1[p] = make_float4(h.cx, h.cy, h.cot, h.q);
+      B.pls_pt[p] = h.pt;
+    }
+    uint32_t v[3] = {NONE, NONE, NONE};
+    if (lane < 12) {
+      int sf, irow;
       float Px, Py;
-      if (f1 && f2) {
-        if (dt1 >= dt2) { Px = P1x; Py = P1y; } else { Px = P2x; Py = P2y; }
-      } else if (f1) {
-        Px = P1x; Py = P1y;
-      } else if (f2) {
-        Px = P2x; Py = P2y;
-      } else {
-        continue;
-      }
-      const float dxc = Px - h.x0, dyc = Py - h.y0;
-      const float chord = sqrtf(dxc * dxc + dyc * dyc);
-      const float sarc = arc_length(chord, h.R);
-      const float zP = h.z0 + sarc * h.cot;
-      const uint32_t m0 = row0_module(G, sf);
-      if (m0 == NONE) continue;
-      const float4 g0 = G.mod_g[m0];
-      const float zlen = g0.w - g0.z;
-      const float zhi = g0.z + (float)G.surf_nrows[sf] * zlen;
-      if (!(zP > g0.z - 2.0f * zlen && zP < zhi + 2.0f * zlen)) continue;
-      const int iz = (int)floorf((zP - g0.z) / zlen);
-      for (int dz = -1; dz <= 1; dz++) add_row_cands(G, sf, iz + dz, Px, Py, list, nc);
-    }
-    if (h.cot != 0.0f) {
-      const int side0 = h.cot > 0.0f ? 11 : 6;
-      for (int di = 0; di < 2; di++) {
-        const int sf = side0 + di;
-        const uint32_t m0 = row0_module(G, sf);
-        if (m0 == NONE) continue;
-        const float4 g0 = G.mod_g[m0];
-        const float zd = g0.x;
-        const float sarc = (zd - h.z0) / h.cot;
-        if (!(sarc > 0.0f)) continue;
-        const float alpha = sarc / h.R;
-        if (!(alpha < C.PI)) continue;
-        float sa, ca;
-        sin_cos_series(alpha, sa, ca);
-        const float sn = -h.q * sa;
-        const float wx = h.x0 - h.cx, wy = h.y0 - h.cy;
-        const float Px = h.cx + (wx * ca - wy * sn);
-        const float Py = h.cy + (wx * sn + wy * ca);
-        const float rP = sqrtf(Px * Px + Py * Py);
-        const float rlen = g0.w - g0.z;
-        const float rhi = g0.z + (float)G.surf_nrows[sf] * rlen;
-        if (!(rP > g0.z - 2.0f * rlen && rP < rhi + 2.0f * rlen)) continue;
-        const int ir = (int)floorf((rP - g0.z) / rlen);
-        for (int dr = -1; dr <= 1; dr++) add_row_cands(G, sf, ir + dr, Px, Py, list, nc);
+      if (pls_surface_point(C, G, h, (int)(lane / 3), sf, Px, Py, irow)) {
+        const int row = irow + (int)(lane % 3) - 1;
+        if (row >= 0 && (uint32_t)row < G.surf_nrows[sf]) {
+          const uint32_t r = G.surf_row_base[sf] + (uint32_t)row;
+          if (G.row_nphi[r] != 0) {
+            const int k = find_sector(G, r, Px, Py);
+            if (k >= 0) {
+              const int nphi = (int)G.row_nphi[r];
+#pragma unroll
+              for (int d = -1; d <= 1; d++) v[d + 1] = G.row_mods[G.row_mod_base[r] + ((k + d) % nphi + nphi) % nphi];
+            }
+          }
+        }
       }
     }
-    for (uint32_t i = 1; i < nc; i++) {  // ascending module id
-      const uint32_t v = list[i];
-      uint32_t k = i;
-      while (k > 0 && list[k - 1] > v) {
-        list[k] = list[k - 1];
-        k--;
+    // 36 values of lanes 0..11 into 64 slots: slot i in lane i (a) or lane i - 32 (b)
+    const uint32_t t1 = __shfl_sync(FULL, v[1], (lane - 12) & 31);
+    const uint32_t t2 = __shfl_sync(FULL, v[2], (lane - 24) & 31);
+    const uint32_t t3 = __shfl_sync(FULL, v[2], (lane + 8) & 31);
+    uint32_t a = lane < 12 ? v[0] : (lane < 24 ? t1 : t2);
+    uint32_t b = lane < 4 ? t3 : NONE;
+#pragma unroll
+    for (uint32_t k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        if (j == 32) {  // partners lane, lane + 32 in the same lane; k == 64: ascending
+          const uint32_t lo = min(a, b), hi = max(a, b);
+          a = lo;
+          b = hi;
+        } else {
+          const uint32_t pa = __shfl_xor_sync(FULL, a, j), pb = __shfl_xor_sync(FULL, b, j);
+          const bool lower = (lane & j) == 0;
+          const bool asc_a = (lane & k) == 0, asc_b = ((lane + 32) & k) == 0;
+          a = (lower == asc_a) ? min(a, pa) : max(a, pa);
+          b = (lower == asc_b) ? min(b, pb) : max(b, pb);
+        }
       }
-      list[k] = v;
     }
-    B.pls_ncand[p] = nc;
-    for (uint32_t i = 0; i < nc; i++) B.pls_cand[(size_t)p * MAX_CAND + i] = list[i];
+    const uint32_t prev_a = __shfl_up_sync(FULL, a, 1);
+    const uint32_t prev_b0 = __shfl_up_sync(FULL, b, 1);
+    const uint32_t last_a = __shfl_sync(FULL, a, 31);
+    const uint32_t prev_b = lane == 0 ? last_a : prev_b0;
+    const bool keep_a = a != NONE && (lane == 0 || a != prev_a);
+    const bool keep_b = b != NONE && b != prev_b;
+    const uint32_t ba = __ballot_sync(FULL, keep_a), bb = __ballot_sync(FULL, keep_b);
+    uint32_t* out = B.pls_cand + (size_t)p * MAX_CAND;
+    if (keep_a) out[__popc(ba & lt)] = a;
+    if (keep_b) out[__popc(ba) + __popc(bb & lt)] = b;
+    if (lane == 0) B.pls_ncand[p] = __popc(ba) + __popc(bb);
   }
 }
 
@@ -1103,7 +1212,7 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
   WarpAlloc wa;
-  WARP_LOOP(p, n) {
+  DYN_LOOP(p, &B.hdr->work[FILL ? 2 : 1], n, 2) {
     const PlsHelix h = load_helix(B, p);
     const uint32_t ubase = B.pls_ev[p] * G.nm;
     const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
@@ -1196,7 +1305,7 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
   if (H->err) return;
   const uint32_t n = H->n_pls;
   WarpAlloc wa;
-  WARP_LOOP(p, n) {
+  DYN_LOOP(p, &B.hdr->work[FILL ? 4 : 3], n, 2) {
     const uint32_t x0 = B.pt3_off[p], nx = B.pt3_off[p + 1] - x0;
     if (nx == 0) {
       if (!FILL && lane_id() == 0) B.pt5_cnt[p] = 0;

@@ -80,6 +80,7 @@ size_t carve(char* base, BufView& B) {
   B.md_lo4 = c.take<float4>(MAX_MD);
   B.md_up4 = c.take<float4>(MAX_MD);
   B.md_cst = c.take<float4>(MAX_MD);
+  B.md_dir4 = c.take<float4>(MAX_MD);
   B.ls_cnt = c.take<uint32_t>(MAX_MD);
   B.ls_off = c.take<uint32_t>(MAX_MD + 1);
   B.ls_in = c.take<uint32_t>(MAX_LS);
