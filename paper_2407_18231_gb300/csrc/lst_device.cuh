@@ -37,8 +37,12 @@ struct Hdr {
   uint32_t pad2[3];
   uint32_t mask_used[8];  // join scratch words taken per stage (MD, LS, T3, T5, pT3, pT5)
   unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)
-  uint32_t work[8];            // work counters of the dynamically scheduled kernels
+  uint32_t work[16];           // work counters of the dynamically scheduled kernels (W_*)
 };
+
+// Work counters in Hdr::work, one per dynamically scheduled kernel and pass.
+enum WorkCounter : int { W_LS = 0, W_PT3_COUNT, W_PT3_FILL, W_PT5_COUNT, W_PT5_FILL, N_WORK };
+static_assert(N_WORK <= 16, "Hdr::work too small");
 
 // Geometry tables (device pointers) and per-geometry scalars.
 struct GeoView {

@@ -232,27 +232,29 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t* off, uint32_t n, u
 // the next unit.
 struct WarpQueue {
   uint32_t* ctr;
-  uint32_t g, base, cur;
-  __device__ __forceinline__ WarpQueue(uint32_t* c, uint32_t grain, uint32_t n) : ctr(c), g(grain) {
+  uint32_t g, base, cur, pend;
+  __device__ __forceinline__ WarpQueue(uint32_t* c, uint32_t grain, uint32_t n) : ctr(c), g(grain), pend(0) {
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     if (n <= 4u * nw * grain) {
       base = nw * grain;
       cur = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * grain;
     } else {
       base = 0;
-      cur = grab();
+      issue();
+      cur = collect();
     }
   }
-  __device__ __forceinline__ uint32_t grab() {
-    uint32_t v = 0;
-    if (lane_id() == 0) v = atomicAdd(ctr, g);
-    return base + __shfl_sync(0xFFFFFFFFu, v, 0);
+  // lane 0 starts the atomic; its result is only read by collect(), after the batch's work
+  __device__ __forceinline__ uint32_t issue() {
+    if (lane_id() == 0) pend = atomicAdd(ctr, g);
+    return cur;
   }
+  __device__ __forceinline__ uint32_t collect() { return base + __shfl_sync(0xFFFFFFFFu, pend, 0); }
 };
 #define DYN_LOOP(k, ctr, n, grain)                                                                       \
   for (WarpQueue wq_(ctr, grain, n); wq_.cur < (n);)                                                   \
-    for (uint32_t e_ = min(wq_.cur + (grain), (uint32_t)(n)), nxt_ = wq_.grab(), k = wq_.cur;            \
-         k < e_ || (wq_.cur = nxt_, false); k++)
+    for (uint32_t e_ = min(wq_.cur + (grain), (uint32_t)(n)), k = wq_.issue(); k < e_ || (wq_.cur = wq_.collect(), false); \
+         k++)
 #define THREAD_LOOP(i, n) \
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
@@ -875,7 +877,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
   } else {
     // module-major order (unit k = module k / n_ev of event k % n_ev) taken dynamically:
     // module ids start with the innermost, busiest layers, so expensive units go first
-    DYN_LOOP(k, &B.hdr->work[0], nu, 2) unit((k % n_ev) * G.nm + k / n_ev);
+    DYN_LOOP(k, &B.hdr->work[W_LS], nu, 2) unit((k % n_ev) * G.nm + k / n_ev);
   }
   if (!FILL && lane == 0 && n_cand) atomicAdd(&B.hdr->ls_cand, n_cand);
 }
@@ -1212,7 +1214,7 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
   WarpAlloc wa;
-  DYN_LOOP(p, &B.hdr->work[FILL ? 2 : 1], n, 2) {
+  DYN_LOOP(p, &B.hdr->work[FILL ? W_PT3_FILL : W_PT3_COUNT], n, 2) {
     const PlsHelix h = load_helix(B, p);
     const uint32_t ubase = B.pls_ev[p] * G.nm;
     const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
@@ -1305,7 +1307,7 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
   if (H->err) return;
   const uint32_t n = H->n_pls;
   WarpAlloc wa;
-  DYN_LOOP(p, &B.hdr->work[FILL ? 4 : 3], n, 2) {
+  DYN_LOOP(p, &B.hdr->work[FILL ? W_PT5_FILL : W_PT5_COUNT], n, 2) {
     const uint32_t x0 = B.pt3_off[p], nx = B.pt3_off[p + 1] - x0;
     if (nx == 0) {
       if (!FILL && lane_id() == 0) B.pt5_cnt[p] = 0;
