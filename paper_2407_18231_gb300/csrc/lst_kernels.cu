@@ -661,9 +661,13 @@ __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& 
   const uint32_t base = FILL ? B.ls_off[a] : 0u;
   const uint32_t ubase = ev * G.nm;
   const uint32_t n_out = FILL ? B.ls_off[a + 1] - base : 0u;
-  const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[1], &B.mask_off[a]};
+  // partner-list records come from the list path only: rows joined here keep none (no
+  // scratch to take from), and the fill pass re-tests them
+  (void)wa;
+  WarpAlloc none;
+  const JoinScratch js{B.mask, 0u, &B.hdr->work[N_WORK], &B.mask_off[a]};
   const uint32_t cnt = warp_join<FILL, NoPayload>(
-      nb, base, n_out, js, wa,
+      nb, base, n_out, js, none,
       [&](uint32_t i, uint32_t& b, uint32_t& c) {
         const uint32_t u = ubase + G.conn[nb0 + i];
         b = B.md_off[u];
@@ -705,7 +709,24 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
   auto unit = [&](const uint32_t u) {
     const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
     if (a0 == a1) return;
-    if (FILL && B.ls_off[a0] == B.ls_off[a1]) return;  // no LS starts on this module
+    if (FILL) {
+      if (B.ls_off[a0] == B.ls_off[a1]) return;  // no LS starts on this module
+      // every row with LS has its partner list: copy, no neighbour list needed
+      bool retest = false;
+      for (uint32_t a = a0 + lane; a < a1; a += 32)
+        retest |= B.ls_off[a + 1] != B.ls_off[a] && B.mask_off[a] == NONE;
+      if (!__any_sync(FULL, retest)) {
+        for (uint32_t a = a0; a < a1; a++) {
+          const uint32_t base = B.ls_off[a], n_out = B.ls_off[a + 1] - base;
+          const uint32_t mbase = B.mask_off[a];
+          for (uint32_t i = lane; i < n_out; i += 32) {
+            B.ls_in[base + i] = a;
+            B.ls_out[base + i] = B.mask[mbase + 1 + i];
+          }
+        }
+        return;
+      }
+    }
     const uint32_t ev = u / G.nm, A = u - ev * G.nm;
     const uint32_t ubase = ev * G.nm;
     const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
@@ -762,15 +783,9 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
         const uint32_t mbase = B.mask_off[a];
         uint32_t count = 0;
         if (mbase != NONE) {
-          const uint32_t nrec = B.mask[mbase];
-          for (uint32_t r = 0; r < nrec; r++) {
-            const uint32_t t0 = B.mask[mbase + 1 + 2 * r], bal = B.mask[mbase + 2 + 2 * r];
-            if ((bal >> lane) & 1u) {
-              const uint32_t pos = base + count + __popc(bal & lt);
-              B.ls_in[pos] = a;
-              B.ls_out[pos] = list[t0 + lane];
-            }
-            count += __popc(bal);
+          for (uint32_t i = lane; i < n_out; i += 32) {
+            B.ls_in[base + i] = a;
+            B.ls_out[base + i] = B.mask[mbase + 1 + i];
           }
         } else {
           for (uint32_t t0 = 0; t0 < len; t0 += 32) {
@@ -824,15 +839,14 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           if (ls_tail_k(C, G, B, pa, da, rnext, exit, j)) atomicOr(&pbits[q >> 5], 1u << (q & 31));
         }
         __syncwarp();
-        // records: the non-zero words, in chunk order
+        // record: [count, partner MDs in list order] -- the fill pass only copies it
         const uint32_t word = lane < nwords ? pbits[lane] : 0u;
-        const uint32_t nzb = __ballot_sync(FULL, word != 0u);
-        const uint32_t nrec = __popc(nzb);
-        const uint32_t count = __reduce_add_sync(FULL, __popc(word));
-        const uint32_t rk = __popc(nzb & lt);  // this lane's record index when word != 0
+        const uint32_t wcnt = __popc(word);
+        const uint32_t wincl = warp_incl_scan(wcnt);
+        const uint32_t count = __shfl_sync(FULL, wincl, 31);
         uint32_t mbase = NONE;
         if (count > 0) {
-          const uint32_t need = 1 + 2 * nrec;
+          const uint32_t need = 1 + count;
           uint32_t mb = NONE;
           if (lane == 0) {
             if (wa.end - wa.cur < need) {
@@ -854,11 +868,9 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           wa.cur = __shfl_sync(FULL, wa.cur, 0);
           wa.end = __shfl_sync(FULL, wa.end, 0);
           if (mbase != NONE) {
-            if (lane == 0) B.mask[mbase] = nrec;
-            if (word != 0u) {
-              B.mask[mbase + 1 + 2 * rk] = lane << 5;
-              B.mask[mbase + 2 + 2 * rk] = word;
-            }
+            if (lane == 0) B.mask[mbase] = count;
+            uint32_t pos = mbase + 1 + wincl - wcnt;
+            for (uint32_t w = word; w; w &= w - 1u) B.mask[pos++] = list[(lane << 5) + __ffs(w) - 1];
           }
         }
         if (lane == 0) {
