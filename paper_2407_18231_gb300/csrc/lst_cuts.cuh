@@ -268,6 +268,17 @@ namespace lst {
 // so a residual beyond the window at s = 1.6 chord can never pass: that case is rejected
 // before the arc-length series is evaluated.  Exact: the bound only removes candidates
 // the full test rejects too.
+// The pre-rejection of pls_anchor_accept alone: false only where pls_anchor_accept is false.
+__device__ __forceinline__ bool pls_anchor_maybe(const MethodConst& C, const PlsHelix& h, const PointTol& X) {
+  const float ddx = X.p.x - h.x0, ddy = X.p.y - h.y0;
+  const float chord = sqrtf(ddx * ddx + ddy * ddy);
+  const float ex = X.p.x - h.cx, ey = X.p.y - h.cy;
+  const float dphi = sqrtf(ex * ex + ey * ey) - h.R;
+  const float smax = 1.6f * chord;
+  const float wmax = (C.W0 + 0.003f * smax + 0.015f * smax * smax / h.R + X.t.y) * 1.001f;
+  return !(fabsf(dphi) > wmax);
+}
+
 __device__ __forceinline__ bool pls_anchor_accept(const MethodConst& C, const PlsHelix& h, const PointTol& X) {
   const float ddx = X.p.x - h.x0, ddy = X.p.y - h.y0;
   const float chord = sqrtf(ddx * ddx + ddy * ddy);

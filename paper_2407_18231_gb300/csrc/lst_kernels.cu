@@ -1211,6 +1211,7 @@ __device__ __forceinline__ PlsHelix load_helix(const BufView& B, uint32_t p) {
 
 // ------------------------------------------------------------------ pT3 / pT5
 constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, kept per pLS
+constexpr uint32_t PT3_RING = 64;    // queued pre-rejection survivors per warp (> 31 + 32)
 
 // pT3 (Sec. 1: pLS + T3).  Unit = pLS p.  Phase 1 tests p against every MD on its
 // candidate modules (the first anchor of any T3 it could join) and keeps the passing MDs in
@@ -1225,6 +1226,7 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
   const uint32_t n = H->n_pls;
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
+  __shared__ uint32_t pt3_ring[512 / 32][PT3_RING];
   WarpAlloc wa;
   DYN_LOOP(p, &B.hdr->work[FILL ? W_PT3_FILL : W_PT3_COUNT], n, 2) {
     const PlsHelix h = load_helix(B, p);
@@ -1234,7 +1236,19 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
     uint32_t* mlist = B.pls_mdpass + (size_t)p * PLS_MD_CAP;
     uint32_t npass;
     if (!FILL) {
+      // the pre-rejection runs on every MD; survivors are queued in MD order and the full
+      // window test runs on 32 of them at a time, so passes are appended in MD order
+      uint32_t* ring = pt3_ring[threadIdx.x >> 5];
+      uint32_t qh = 0, qt = 0;
       npass = 0;
+      auto accept_queued = [&](uint32_t nq) {
+        const uint32_t m = lane < nq ? ring[(qh + lane) & (PT3_RING - 1)] : 0u;
+        const bool pass = lane < nq && pls_anchor_accept(C, h, md_point(B, m));
+        const uint32_t bal = __ballot_sync(FULL, pass);
+        if (pass && npass + __popc(bal & lt) < PLS_MD_CAP) mlist[npass + __popc(bal & lt)] = m;
+        npass += __popc(bal);
+        qh += nq;
+      };
       for (uint32_t g0 = 0; g0 < nc; g0 += 32) {
         uint32_t b = 0, c = 0;
         if (g0 + lane < nc) {
@@ -1252,12 +1266,19 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
           const uint32_t co = __shfl_sync(FULL, c, o);
           const uint32_t io = __shfl_sync(FULL, incl, o);
           const uint32_t m = bo + (cc - (io - co));
-          const bool pass = cc0 < total && pls_anchor_accept(C, h, md_point(B, m));
-          const uint32_t bal = __ballot_sync(FULL, pass);
-          if (pass && npass + __popc(bal & lt) < PLS_MD_CAP) mlist[npass + __popc(bal & lt)] = m;
-          npass += __popc(bal);
+          const bool maybe = cc0 < total && pls_anchor_maybe(C, h, md_point(B, m));
+          const uint32_t mb = __ballot_sync(FULL, maybe);
+          if (maybe) ring[(qt + __popc(mb & lt)) & (PT3_RING - 1)] = m;
+          qt += __popc(mb);
+          __syncwarp();
+          if (qt - qh >= 32) {
+            accept_queued(32);
+            __syncwarp();
+          }
         }
       }
+      if (qt != qh) accept_queued(qt - qh);
+      __syncwarp();
       if (npass > PLS_MD_CAP) npass = NONE;
       if (lane == 0) B.pls_nmdpass[p] = npass;
       __syncwarp();
