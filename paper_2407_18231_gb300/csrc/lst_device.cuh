@@ -111,6 +111,14 @@ typedef void (*MarkFn)(void* arg, int kernel_name);
 extern const char* const kKernelNames[];
 extern const int kNumKernelNames;
 
+// A second stream for work that depends only on the inputs (the pLS preparation): forked
+// from the main stream at the start of the chain and joined before the first kernel that
+// needs its results, so it overlaps the hit, MD and LS stages.  Null: one stream.
+struct SideBranch {
+  cudaStream_t s;
+  cudaEvent_t fork, join;
+};
+
 struct Launch {
   uint32_t grid;   // persistent grid (blocks)
   uint32_t block;  // threads per block

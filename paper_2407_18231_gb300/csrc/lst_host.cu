@@ -22,7 +22,7 @@
 
 namespace lst {
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
-                     MarkFn mark, void* arg);
+                     MarkFn mark, void* arg, const SideBranch* side = nullptr);
 }
 
 using namespace lst;
@@ -390,6 +390,7 @@ struct Pipeline {
   MethodConst C;
   Launch L;
   cudaStream_t stream = nullptr;
+  SideBranch side{nullptr, nullptr, nullptr};  // second stream of the chain (not in profile mode)
   cudaEvent_t done = nullptr;
   Caps cap;
   uint64_t dev_bytes = 0;
@@ -465,6 +466,10 @@ struct Pipeline {
     if (stream) cudaStreamDestroy(stream);
     done = nullptr;
     stream = nullptr;
+    if (side.fork) cudaEventDestroy(side.fork);
+    if (side.join) cudaEventDestroy(side.join);
+    if (side.s) cudaStreamDestroy(side.s);
+    side = SideBranch{nullptr, nullptr, nullptr};
   }
 
   void set_tuning(const lst_config& cfg, int n_sm) {
@@ -483,6 +488,9 @@ struct Pipeline {
     L.scan_grid = std::min<uint32_t>(sg, 1024u);
     CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming));
     profile = cfg.profile != 0;
     if (profile) {
       CK(cudaEventCreate(&prof_start));
@@ -721,7 +729,7 @@ struct Pipeline {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
         cudaMemcpyAsync(hdr.p, h_hdr, sizeof(Hdr), cudaMemcpyHostToDevice, stream);
-        kernels = enqueue_pipeline(C, G, B, L, stream, nullptr, nullptr);
+        kernels = enqueue_pipeline(C, G, B, L, stream, nullptr, nullptr, &side);
         cudaMemcpyAsync(h_hdr_out, hdr.p, sizeof(Hdr), cudaMemcpyDeviceToHost, stream);
         CK(cudaStreamEndCapture(stream, &g));
         cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
@@ -732,7 +740,7 @@ struct Pipeline {
       CK(cudaGraphLaunch(graph, st));
     } else {
       CK(cudaMemcpyAsync(hdr.p, h_hdr, sizeof(Hdr), cudaMemcpyHostToDevice, st));
-      kernels = enqueue_pipeline(C, G, B, L, st, nullptr, nullptr);
+      kernels = enqueue_pipeline(C, G, B, L, st, nullptr, nullptr, &side);
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(h_hdr_out, hdr.p, sizeof(Hdr), cudaMemcpyDeviceToHost, st));
     }

@@ -294,35 +294,34 @@ __global__ void k_scan_reduce(const uint32_t* __restrict__ in, const uint32_t* n
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_top(uint32_t* part, const uint32_t* nptr, uint32_t mul, uint32_t* out, Hdr* H, int tot_idx,
-                           uint32_t cap) {
-  if (H->err) return;
-  __shared__ uint32_t sm[33];
-  const uint32_t np = blockDim.x;  // one partial per thread (grid of the other passes)
-  const uint32_t v = part[threadIdx.x];
-  uint32_t tot;
-  const uint32_t ex = block_excl_scan(v, sm, tot);
-  part[threadIdx.x] = ex;
-  (void)np;
-  if (threadIdx.x == 0) {
-    const uint32_t n = (*nptr) * mul;
+// Sum of the block partials before this block; the last block also publishes the total
+// (out[n], hdr->tot[tot_idx], the overflow bit when it exceeds cap).
+__device__ __forceinline__ uint32_t scan_carry(const uint32_t* part, uint32_t* sm, uint32_t n, uint32_t* out, Hdr* H,
+                                               int tot_idx, uint32_t cap) {
+  uint32_t v = 0;
+  for (uint32_t i = threadIdx.x; i < blockIdx.x; i += blockDim.x) v += part[i];
+  uint32_t carry;
+  block_excl_scan(v, sm, carry);
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const uint32_t tot = carry + part[blockIdx.x];
     out[n] = tot;
     if (tot_idx >= 0) {
       H->tot[tot_idx] = tot;
       if (tot > cap) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + tot_idx));
     }
   }
+  return carry;
 }
 
-__global__ void k_scan_apply(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul, const Hdr* H,
-                             const uint32_t* part, uint32_t* __restrict__ out) {
+__global__ void k_scan_apply(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul, Hdr* H,
+                             const uint32_t* part, uint32_t* __restrict__ out, int tot_idx, uint32_t cap) {
   if (H->err) return;
   __shared__ uint32_t sm[33];
   const uint32_t n = (*nptr) * mul;
   const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const uint32_t lo = blockIdx.x * chunk;
   const uint32_t hi = min(n, lo + chunk);
-  uint32_t carry = part[blockIdx.x];
+  uint32_t carry = scan_carry(part, sm, n, out, H, tot_idx, cap);
   const uint32_t tile = blockDim.x * 4;
   for (uint32_t t = lo; t < hi; t += tile) {
     const uint32_t i0 = t + threadIdx.x * 4;
@@ -371,23 +370,7 @@ __global__ void k_scan_reduce_multi(ScanJobs J, const Hdr* H, uint32_t* part) {
   if (threadIdx.x == 0) part[blockIdx.y * 1024 + blockIdx.x] = tot;
 }
 
-__global__ void k_scan_top_multi(ScanJobs J, uint32_t* part, Hdr* H) {
-  if (H->err) return;
-  __shared__ uint32_t sm[33];
-  const ScanJob& q = J.j[blockIdx.x];
-  uint32_t* pp = part + blockIdx.x * 1024;
-  const uint32_t v = pp[threadIdx.x];
-  uint32_t tot;
-  const uint32_t ex = block_excl_scan(v, sm, tot);
-  pp[threadIdx.x] = ex;
-  if (threadIdx.x == 0) {
-    q.out[*q.nptr] = tot;
-    H->tot[q.tot] = tot;
-    if (tot > q.cap) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + q.tot));
-  }
-}
-
-__global__ void k_scan_apply_multi(ScanJobs J, const Hdr* H, const uint32_t* part) {
+__global__ void k_scan_apply_multi(ScanJobs J, Hdr* H, const uint32_t* part) {
   if (H->err) return;
   __shared__ uint32_t sm[33];
   const ScanJob& q = J.j[blockIdx.y];
@@ -395,7 +378,7 @@ __global__ void k_scan_apply_multi(ScanJobs J, const Hdr* H, const uint32_t* par
   const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const uint32_t lo = blockIdx.x * chunk;
   const uint32_t hi = min(n, lo + chunk);
-  uint32_t carry = part[blockIdx.y * 1024 + blockIdx.x];
+  uint32_t carry = scan_carry(part + blockIdx.y * 1024, sm, n, q.out, H, q.tot, q.cap);
   const uint32_t tile = blockDim.x * 4;
   for (uint32_t t = lo; t < hi; t += tile) {
     const uint32_t i0 = t + threadIdx.x * 4;
@@ -1726,7 +1709,7 @@ __global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
 // ------------------------------------------------------------------ host-side enqueue
 // Kernel names in launch order (profile mode records one CUDA event after each).
 const char* const kKernelNames[] = {
-    "zero_sensor_counts", "hits_count", "scan_reduce", "scan_top", "scan_apply", "hits_scatter", "hits_sort",
+    "zero_sensor_counts", "hits_count", "scan_reduce", "(unused)", "scan_apply", "hits_scatter", "hits_sort",
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "zero_md_lists", "md_lists_count", "md_lists_fill",
     "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
@@ -1747,17 +1730,13 @@ static void scan(const BufView& B, const Launch& L, cudaStream_t s, const uint32
                  const uint32_t* nptr, uint32_t mul, int tot, uint32_t cap, Marker& mk) {
   k_scan_reduce<<<L.scan_grid, 512, 0, s>>>(in, nptr, mul, B.hdr, B.scan_part);
   mk(2);
-  k_scan_top<<<1, L.scan_grid, 0, s>>>(B.scan_part, nptr, mul, out, B.hdr, tot, cap);
-  mk(3);
-  k_scan_apply<<<L.scan_grid, 512, 0, s>>>(in, nptr, mul, B.hdr, B.scan_part, out);
+  k_scan_apply<<<L.scan_grid, 512, 0, s>>>(in, nptr, mul, B.hdr, B.scan_part, out, tot, cap);
   mk(4);
 }
 
 static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const ScanJobs& J, int n, Marker& mk) {
   k_scan_reduce_multi<<<dim3(L.scan_grid, n), 512, 0, s>>>(J, B.hdr, B.scan_part);
   mk(2);
-  k_scan_top_multi<<<n, L.scan_grid, 0, s>>>(J, B.scan_part, B.hdr);
-  mk(3);
   k_scan_apply_multi<<<dim3(L.scan_grid, n), 512, 0, s>>>(J, B.hdr, B.scan_part);
   mk(4);
 }
@@ -1765,11 +1744,18 @@ static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const 
 // Enqueues the whole chain on stream s; returns the number of kernels launched.  mark (may
 // be null) is called after every launch with the index of its name in kKernelNames.
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
-                     MarkFn mark, void* arg) {
+                     MarkFn mark, void* arg, const SideBranch* side) {
   Marker mk{mark, arg, 0};
   Hdr* H = B.hdr;
   const uint32_t g = L.grid, bs = L.block;
   const uint32_t two_nm = 2 * G.nm;
+  if (side) {  // the pLS preparation needs only the inputs: run it beside the OT chain
+    cudaEventRecord(side->fork, s);
+    cudaStreamWaitEvent(side->s, side->fork, 0);
+    k_pls_prep<<<g, 128, 0, side->s>>>(C, G, B);
+    mk(15);
+    cudaEventRecord(side->join, side->s);
+  }
   k_zero<<<g, 256, 0, s>>>(B.sen_cnt, &H->n_ev, two_nm, 1);
   mk(0);
   k_hits_count<<<g, 256, 0, s>>>(G, B);
@@ -1805,8 +1791,12 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   mk(14);
   k_t5_md_off<<<g, 256, 0, s>>>(B);
   mk(33);
-  k_pls_prep<<<g, 128, 0, s>>>(C, G, B);
-  mk(15);
+  if (side) {
+    cudaStreamWaitEvent(s, side->join, 0);
+  } else {
+    k_pls_prep<<<g, 128, 0, s>>>(C, G, B);
+    mk(15);
+  }
   k_pt3<false><<<g, bs, 0, s>>>(C, G, B);
   mk(16);
   scan(B, L, s, B.pt3_cnt, B.pt3_off, &H->n_pls, 1, T_PT3, B.cap_pt3, mk);

@@ -18,7 +18,7 @@
 
 namespace lst {
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
-                     MarkFn mark, void* arg);
+                     MarkFn mark, void* arg, const SideBranch* side = nullptr);
 bool ctx_views(lst_ctx* c, GeoView* g, MethodConst* m, Launch* l, int* device, bool* have_map);
 void ctx_set_error(lst_ctx* c, const std::string& msg);
 }  // namespace lst
