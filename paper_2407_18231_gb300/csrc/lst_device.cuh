@@ -74,7 +74,8 @@ struct BufView {
   float4 *hit4;
   // MD
   uint32_t *md_cnt, *md_off, *md_unit, *md_lo_idx, *md_up_idx;
-  float4 *md_lo4, *md_up4, *md_cst;
+  float4 *md_pt;  // per MD, one 32-byte sector: [2m] lower hit (x, y, z, r), [2m + 1] module tolerances
+  float4 *md_up4;
   float4 *md_dir4;  // upper - lower hit: dx, dy, transverse length, rho + rho
   // LS
   uint32_t *ls_cnt, *ls_off, *ls_in, *ls_out;

@@ -399,7 +399,7 @@ struct Pipeline {
   // buffers
   DevBuf hdr, in_x, in_y, in_z, in_det, in_hoff, in_pls, in_poff;
   DevBuf sen_cnt, sen_off, hit_tmp, hit_ev, hit_idx, hit4;
-  DevBuf md_cnt, md_off, md_unit, md_lo_idx, md_up_idx, md_lo4, md_up4, md_cst, md_dir4;
+  DevBuf md_cnt, md_off, md_unit, md_lo_idx, md_up_idx, md_pt, md_up4, md_dir4;
   DevBuf ls_cnt, ls_off, ls_in, ls_out;
   DevBuf t3_lcnt, t3_loff, t3_off, t3_a, t3_b, t3_c;
   DevBuf t5_tcnt, t5_toff, t5_off, t5_m[5], t5_score, t5_kfull;
@@ -435,7 +435,7 @@ struct Pipeline {
   std::vector<DevBuf*> all_buffers() {
     std::vector<DevBuf*> v = {&hdr, &in_x, &in_y, &in_z, &in_det, &in_hoff, &in_pls, &in_poff, &sen_cnt, &sen_off,
                               &hit_tmp, &hit_ev, &hit_idx, &hit4, &md_cnt, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
-                              &md_lo4, &md_up4, &md_cst, &md_dir4, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off,
+                              &md_pt, &md_up4, &md_dir4, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off,
                               &t3_a, &t3_b, &t3_c, &t5_tcnt, &t5_toff, &t5_off, &t5_score, &t5_kfull, &pls_ev,
                               &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
                               &pt5_cnt, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
@@ -535,10 +535,9 @@ struct Pipeline {
     need<uint32_t>(md_unit, c.md);
     need<uint32_t>(md_lo_idx, c.md);
     need<uint32_t>(md_up_idx, c.md);
-    need<float4>(md_lo4, c.md);
+    need<float4>(md_pt, 2 * c.md);
     need<float4>(md_up4, c.md);
     need<float4>(md_dir4, c.md);
-    need<float4>(md_cst, c.md);
     need<uint32_t>(ls_cnt, c.md);
     need<uint32_t>(ls_off, c.md + 1);
     need<uint32_t>(ls_in, c.ls);
@@ -665,9 +664,8 @@ struct Pipeline {
     v.sen_cnt = P32(sen_cnt); v.sen_off = P32(sen_off); v.hit_tmp = P32(hit_tmp); v.hit_ev = P32(hit_ev);
     v.hit_idx = P32(hit_idx); v.hit4 = (float4*)hit4.p;
     v.md_cnt = P32(md_cnt); v.md_off = P32(md_off); v.md_unit = P32(md_unit); v.md_lo_idx = P32(md_lo_idx);
-    v.md_up_idx = P32(md_up_idx); v.md_lo4 = (float4*)md_lo4.p; v.md_up4 = (float4*)md_up4.p;
+    v.md_up_idx = P32(md_up_idx); v.md_pt = (float4*)md_pt.p; v.md_up4 = (float4*)md_up4.p;
     v.md_dir4 = (float4*)md_dir4.p;
-    v.md_cst = (float4*)md_cst.p;
     v.ls_cnt = P32(ls_cnt); v.ls_off = P32(ls_off); v.ls_in = P32(ls_in); v.ls_out = P32(ls_out);
     v.t3_lcnt = P32(t3_lcnt); v.t3_loff = P32(t3_loff); v.t3_off = P32(t3_off);
     v.t3_a = P32(t3_a); v.t3_b = P32(t3_b); v.t3_c = P32(t3_c);

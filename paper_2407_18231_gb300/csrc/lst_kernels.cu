@@ -486,9 +486,9 @@ __device__ __forceinline__ void md_unit_join(const MethodConst& C, const GeoView
       [&](uint32_t, uint32_t, NoPayload&) {},
       [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
         B.md_unit[pos] = u;
-        B.md_lo4[pos] = B.hit4[lo_b + i];
+        B.md_pt[2 * pos] = B.hit4[lo_b + i];
         B.md_up4[pos] = B.hit4[j];
-        B.md_cst[pos] = cst;
+        B.md_pt[2 * pos + 1] = cst;
         B.md_dir4[pos] = md_direction(B.hit4[lo_b + i], B.hit4[j], cst);
         B.md_lo_idx[pos] = B.hit_idx[lo_b + i];
         B.md_up_idx[pos] = B.hit_idx[j];
@@ -577,9 +577,9 @@ __global__ void __launch_bounds__(512) k_md(MethodConst C, GeoView G, BufView B)
         if (pass) {
           const uint32_t pos = base_o + run_o + __popc(bal & lt & ~((1u << lo_o) - 1u));
           B.md_unit[pos] = uo;
-          B.md_lo4[pos] = hl;
+          B.md_pt[2 * pos] = hl;
           B.md_up4[pos] = hu;
-          B.md_cst[pos] = cst;
+          B.md_pt[2 * pos + 1] = cst;
           B.md_dir4[pos] = md_direction(hl, hu, cst);
           B.md_lo_idx[pos] = B.hit_idx[ih];
           B.md_up_idx[pos] = B.hit_idx[jh];
@@ -591,8 +591,12 @@ __global__ void __launch_bounds__(512) k_md(MethodConst C, GeoView G, BufView B)
   }
 }
 
-__device__ __forceinline__ PointTol md_point(const BufView& B, uint32_t m) { return PointTol{B.md_lo4[m], B.md_cst[m]}; }
-__device__ __forceinline__ PointTol md_upper(const BufView& B, uint32_t m) { return PointTol{B.md_up4[m], B.md_cst[m]}; }
+__device__ __forceinline__ PointTol md_point(const BufView& B, uint32_t m) {
+  return PointTol{B.md_pt[2 * (size_t)m], B.md_pt[2 * (size_t)m + 1]};
+}
+__device__ __forceinline__ PointTol md_upper(const BufView& B, uint32_t m) {
+  return PointTol{B.md_up4[m], B.md_pt[2 * (size_t)m + 1]};
+}
 
 // ------------------------------------------------------------------ Line Segments
 // The LS selection of ls_select for anchor pa and MD j, loading the rest of MD j
@@ -796,7 +800,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           for (uint32_t k = 0; k < LS_UNROLL; k++) {
             const uint32_t t = t0 + 32 * k + lane;
             const uint32_t j = t < len ? list[t] : a;  // a: any valid MD for idle lanes
-            pb[k] = PointTol{__ldg(&B.md_lo4[j]), __ldg(&B.md_cst[j])};
+            pb[k] = PointTol{__ldg(&B.md_pt[2 * (size_t)j]), __ldg(&B.md_pt[2 * (size_t)j + 1])};
           }
 #pragma unroll
           for (uint32_t k = 0; k < LS_UNROLL; k++) {

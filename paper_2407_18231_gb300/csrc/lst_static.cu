@@ -77,9 +77,8 @@ size_t carve(char* base, BufView& B) {
   B.md_unit = c.take<uint32_t>(MAX_MD);
   B.md_lo_idx = c.take<uint32_t>(MAX_MD);
   B.md_up_idx = c.take<uint32_t>(MAX_MD);
-  B.md_lo4 = c.take<float4>(MAX_MD);
+  B.md_pt = c.take<float4>(2 * MAX_MD);
   B.md_up4 = c.take<float4>(MAX_MD);
-  B.md_cst = c.take<float4>(MAX_MD);
   B.md_dir4 = c.take<float4>(MAX_MD);
   B.ls_cnt = c.take<uint32_t>(MAX_MD);
   B.ls_off = c.take<uint32_t>(MAX_MD + 1);
