@@ -901,8 +901,17 @@ __global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B)
       if (!FILL) B.t3_lcnt[l] = 0;
       continue;
     }
+    if (FILL && c1 - c0 <= 32) {  // the count pass's pass bits: no test
+      for (uint32_t bits = B.t3_mask[l]; bits; bits &= bits - 1u) {
+        B.t3_a[k] = a;
+        B.t3_b[k] = b;
+        B.t3_c[k] = B.ls_out[c0 + __ffs(bits) - 1];
+        k++;
+      }
+      continue;
+    }
     const PointTol pa = md_point(B, a), pb = md_point(B, b), pbu = md_upper(B, b);
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, bits = 0;
     for (uint32_t l2 = c0; l2 < c1; l2++) {
       const uint32_t c = B.ls_out[l2];
       if (t3_select(C, pa, pb, pbu, md_point(B, c))) {
@@ -913,10 +922,14 @@ __global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B)
           k++;
         } else {
           cnt++;
+          if (l2 - c0 < 32) bits |= 1u << (l2 - c0);
         }
       }
     }
-    if (!FILL) B.t3_lcnt[l] = cnt;
+    if (!FILL) {
+      B.t3_lcnt[l] = cnt;
+      B.t3_mask[l] = bits;
+    }
   }
 }
 
@@ -949,12 +962,17 @@ __global__ void __launch_bounds__(512) k_t5(MethodConst C, GeoView G, BufView B)
     }
     const uint32_t a = B.t3_a[t], b = B.t3_b[t];
     const PointTol pa = md_point(B, a), pb = md_point(B, b), pc = md_point(B, c);
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, bits = 0;
+    // fill pass: with at most 32 candidates, only those the count pass accepted
+    const uint32_t todo = FILL && s1 - s0 <= 32 ? B.t5_mask[t] : FULL;
     for (uint32_t t2 = s0; t2 < s1; t2++) {
+      if (FILL && t2 - s0 < 32 && !((todo >> (t2 - s0)) & 1u)) continue;
       const uint32_t d = B.t3_b[t2], e = B.t3_c[t2];
       const PointTol pd = md_point(B, d), pe = md_point(B, e);
       if (!FILL) {
-        cnt += t5_accept(C, pa, pb, pc, pd, pe) ? 1u : 0u;
+        const bool ok = t5_accept(C, pa, pb, pc, pd, pe);
+        cnt += ok ? 1u : 0u;
+        if (ok && t2 - s0 < 32) bits |= 1u << (t2 - s0);
       } else {
         float score, kfull;
         if (t5_select(C, pa, pb, pc, pd, pe, score, kfull)) {
@@ -969,7 +987,10 @@ __global__ void __launch_bounds__(512) k_t5(MethodConst C, GeoView G, BufView B)
         }
       }
     }
-    if (!FILL) B.t5_tcnt[t] = cnt;
+    if (!FILL) {
+      B.t5_tcnt[t] = cnt;
+      B.t5_mask[t] = bits;
+    }
   }
 }
 

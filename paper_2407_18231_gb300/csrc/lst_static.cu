@@ -85,12 +85,14 @@ size_t carve(char* base, BufView& B) {
   B.ls_in = c.take<uint32_t>(MAX_LS);
   B.ls_out = c.take<uint32_t>(MAX_LS);
   B.t3_lcnt = c.take<uint32_t>(MAX_LS);
+  B.t3_mask = c.take<uint32_t>(MAX_LS);
   B.t3_loff = c.take<uint32_t>(MAX_LS + 1);
   B.t3_off = c.take<uint32_t>(MAX_MD + 1);
   B.t3_a = c.take<uint32_t>(MAX_T3);
   B.t3_b = c.take<uint32_t>(MAX_T3);
   B.t3_c = c.take<uint32_t>(MAX_T3);
   B.t5_tcnt = c.take<uint32_t>(MAX_T3);
+  B.t5_mask = c.take<uint32_t>(MAX_T3);
   B.t5_toff = c.take<uint32_t>(MAX_T3 + 1);
   B.t5_off = c.take<uint32_t>(MAX_MD + 1);
   B.t5_m0 = c.take<uint32_t>(MAX_T5);
