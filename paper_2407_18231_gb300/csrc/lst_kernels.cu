@@ -670,10 +670,9 @@ __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& 
 }
 
 constexpr uint32_t LS_LIST_CAP = 512;  // flattened neighbour MDs per warp in shared memory
-constexpr uint32_t LS_UNROLL = 2;      // candidate chunks whose loads are issued together
-constexpr uint32_t LS_RING = 128;      // ring of queued list positions (> 31 + 32 * LS_UNROLL)
-// per warp after the list: the ring and one pass bit per list position
-constexpr uint32_t LS_EXTRA_WORDS = LS_RING + LS_LIST_CAP / 32;
+constexpr uint32_t LS_RING = 128;      // ring of queued list positions (> 31 + 2 * 32)
+// per warp after the list: the ring and one pass bit per list position for each of two MDs
+constexpr uint32_t LS_EXTRA_WORDS = LS_RING + 2 * LS_LIST_CAP / 32;
 
 // Unit = (event, module A).  The warp writes the indices of all MDs on the modules connected
 // to A into a shared-memory list once (module order, then MD order), then walks the list in
@@ -690,6 +689,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
   uint32_t* list = ls_smem + (threadIdx.x >> 5) * (list_cap + LS_EXTRA_WORDS);
   uint32_t* queue = list + list_cap;
   uint32_t* pbits = queue + LS_RING;
+  uint32_t* pbits2 = pbits + LS_LIST_CAP / 32;
   WarpAlloc wa;
   unsigned long long n_cand = 0;  // count pass: candidate pairs this warp tested
   const uint32_t n_ev = H->n_ev;
@@ -761,20 +761,20 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
     }
     const float rnext = G.rnext[A];
     const bool a_barrel = G.subdet[A] == 0;
-    for (uint32_t a = a0; a < a1; a++) {
-      const PointTol pa = md_point(B, a);
-      const float4 da = B.md_dir4[a];
-      if (FILL) {
+    if (FILL) {
+      for (uint32_t a = a0; a < a1; a++) {
         const uint32_t base = B.ls_off[a], n_out = B.ls_off[a + 1] - base;
         if (n_out == 0) continue;
         const uint32_t mbase = B.mask_off[a];
-        uint32_t count = 0;
         if (mbase != NONE) {
           for (uint32_t i = lane; i < n_out; i += 32) {
             B.ls_in[base + i] = a;
             B.ls_out[base + i] = B.mask[mbase + 1 + i];
           }
         } else {
+          const PointTol pa = md_point(B, a);
+          const float4 da = B.md_dir4[a];
+          uint32_t count = 0;
           for (uint32_t t0 = 0; t0 < len; t0 += 32) {
             const bool pass = t0 + lane < len && ls_test(C, G, B, pa, da, rnext, a_barrel, ubase, list[t0 + lane]);
             const uint32_t bal = __ballot_sync(FULL, pass);
@@ -786,48 +786,15 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
             count += __popc(bal);
           }
         }
-      } else {
-        // head on every candidate; positions passing it are queued and the tail runs on 32
-        // at a time; final passes set their bit in pbits (word k = chunk k's ballot)
-        const uint32_t nwords = (len + 31) >> 5;
-        if (lane < nwords) pbits[lane] = 0;
-        uint32_t qh = 0, qt = 0;  // ring head and tail (free-running)
-        __syncwarp();
-        for (uint32_t t0 = 0; t0 < len; t0 += 32 * LS_UNROLL) {
-          // the loads of LS_UNROLL chunks are in flight together: one L2 round trip for all
-          PointTol pb[LS_UNROLL];
-#pragma unroll
-          for (uint32_t k = 0; k < LS_UNROLL; k++) {
-            const uint32_t t = t0 + 32 * k + lane;
-            const uint32_t j = t < len ? list[t] : a;  // a: any valid MD for idle lanes
-            pb[k] = PointTol{__ldg(&B.md_pt[2 * (size_t)j]), __ldg(&B.md_pt[2 * (size_t)j + 1])};
-          }
-#pragma unroll
-          for (uint32_t k = 0; k < LS_UNROLL; k++) {
-            const uint32_t t = t0 + 32 * k + lane;
-            const bool h = t < len && ls_head_pt(C, pa, pb[k]);
-            const uint32_t hb = __ballot_sync(FULL, h);
-            if (h) queue[(qt + __popc(hb & lt)) & (LS_RING - 1)] = t;
-            qt += __popc(hb);
-          }
-          __syncwarp();
-          while (qt - qh >= 32) {
-            const uint32_t q = queue[(qh + lane) & (LS_RING - 1)];
-            const uint32_t j = list[q];
-            const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
-            if (ls_tail_k(C, G, B, pa, da, rnext, exit, j)) atomicOr(&pbits[q >> 5], 1u << (q & 31));
-            qh += 32;
-          }
-        }
-        if (lane < qt - qh) {
-          const uint32_t q = queue[(qh + lane) & (LS_RING - 1)];
-          const uint32_t j = list[q];
-          const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
-          if (ls_tail_k(C, G, B, pa, da, rnext, exit, j)) atomicOr(&pbits[q >> 5], 1u << (q & 31));
-        }
-        __syncwarp();
-        // record: [count, partner MDs in list order] -- the fill pass only copies it
-        const uint32_t word = lane < nwords ? pbits[lane] : 0u;
+      }
+    } else {
+      // Two MDs of A per walk over the list: each candidate loaded is tested against both
+      // anchors (their own pass bits, pbits and pbits2); the head's survivors are queued
+      // as list position | anchor << 15 and the tail runs on 32 of them at a time.
+      const uint32_t nwords = (len + 31) >> 5;
+      // record of MD a: [count, partner MDs in list order] -- the fill pass only copies it
+      auto record = [&](uint32_t a, const uint32_t* bits) {
+        const uint32_t word = lane < nwords ? bits[lane] : 0u;
         const uint32_t wcnt = __popc(word);
         const uint32_t wincl = warp_incl_scan(wcnt);
         const uint32_t count = __shfl_sync(FULL, wincl, 31);
@@ -864,7 +831,50 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           B.mask_off[a] = mbase;
           B.ls_cnt[a] = count;
         }
-        __syncwarp();  // pbits and the queue are reused by the next MD
+      };
+      for (uint32_t a = a0; a < a1; a += 2) {
+        const bool two = a + 1 < a1;
+        const uint32_t a2 = two ? a + 1 : a;
+        const PointTol pa0 = md_point(B, a), pa1 = md_point(B, a2);
+        const float4 da0 = B.md_dir4[a], da1 = B.md_dir4[a2];
+        if (lane < nwords) {
+          pbits[lane] = 0;
+          pbits2[lane] = 0;
+        }
+        uint32_t qh = 0, qt = 0;  // ring head and tail (free-running)
+        auto tail = [&](uint32_t e) {
+          const bool second = e >> 15;
+          const uint32_t q = e & 0x7FFFu;
+          const uint32_t j = list[q];
+          const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
+          const PointTol& pa = second ? pa1 : pa0;
+          if (ls_tail_k(C, G, B, pa, second ? da1 : da0, rnext, exit, j))
+            atomicOr(&(second ? pbits2 : pbits)[q >> 5], 1u << (q & 31));
+        };
+        __syncwarp();
+        for (uint32_t t0 = 0; t0 < len; t0 += 32) {
+          const uint32_t t = t0 + lane;
+          const uint32_t j = t < len ? list[t] : a;  // a: any valid MD for idle lanes
+          const PointTol pb{__ldg(&B.md_pt[2 * (size_t)j]), __ldg(&B.md_pt[2 * (size_t)j + 1])};
+          const bool h0 = t < len && ls_head_pt(C, pa0, pb);
+          const uint32_t hb0 = __ballot_sync(FULL, h0);
+          if (h0) queue[(qt + __popc(hb0 & lt)) & (LS_RING - 1)] = t;
+          qt += __popc(hb0);
+          const bool h1 = two && t < len && ls_head_pt(C, pa1, pb);
+          const uint32_t hb1 = __ballot_sync(FULL, h1);
+          if (h1) queue[(qt + __popc(hb1 & lt)) & (LS_RING - 1)] = t | 0x8000u;
+          qt += __popc(hb1);
+          __syncwarp();
+          while (qt - qh >= 32) {
+            tail(queue[(qh + lane) & (LS_RING - 1)]);
+            qh += 32;
+          }
+        }
+        if (lane < qt - qh) tail(queue[(qh + lane) & (LS_RING - 1)]);
+        __syncwarp();
+        record(a, pbits);
+        if (two) record(a + 1, pbits2);
+        __syncwarp();  // pbits and the queue are reused by the next pair
       }
     }
     __syncwarp();  // the list is rewritten by the next unit
