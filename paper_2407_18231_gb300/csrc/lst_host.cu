@@ -23,6 +23,7 @@
 namespace lst {
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
                      MarkFn mark, void* arg, const SideBranch* side = nullptr);
+cudaError_t configure_kernels();
 }
 
 using namespace lst;
@@ -486,6 +487,7 @@ struct Pipeline {
     set_tuning(cfg, n_sm);
     uint32_t sg = ((2u * (uint32_t)n_sm) + 31u) / 32u * 32u;
     L.scan_grid = std::min<uint32_t>(sg, 1024u);
+    CK(configure_kernels());
     CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));

@@ -1776,6 +1776,15 @@ static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const 
   mk(4);
 }
 
+// Lets the LS kernels take the shared memory of the largest block (512 threads) on the
+// current device; called once per pipeline, outside any stream capture.
+cudaError_t configure_kernels() {
+  const int bytes = (int)((512 / 32) * (LS_LIST_CAP + LS_EXTRA_WORDS) * sizeof(uint32_t));
+  cudaError_t e = cudaFuncSetAttribute(k_ls<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ls<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
 // Enqueues the whole chain on stream s; returns the number of kernels launched.  mark (may
 // be null) is called after every launch with the index of its name in kKernelNames.
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
