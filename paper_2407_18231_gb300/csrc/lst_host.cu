@@ -476,7 +476,8 @@ struct Pipeline {
   void set_tuning(const lst_config& cfg, int n_sm) {
     const uint32_t bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
     L.block = cfg.block_size ? cfg.block_size : 256;
-    L.ls_list_cap = cfg.ls_list_cap == 0 ? 512u : (cfg.ls_list_cap == 1 ? 0u : std::min<uint32_t>(cfg.ls_list_cap, 512u));
+    // a multiple of 4: the LS kernel's per-warp shared-memory slices hold float4s
+    L.ls_list_cap = cfg.ls_list_cap == 0 ? 512u : (cfg.ls_list_cap == 1 ? 0u : std::min<uint32_t>(cfg.ls_list_cap, 512u) & ~3u);
     L.grid = (uint32_t)n_sm * bps;
     graph_valid = false;
   }

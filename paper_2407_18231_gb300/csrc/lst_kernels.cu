@@ -670,9 +670,11 @@ __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& 
 }
 
 constexpr uint32_t LS_LIST_CAP = 512;  // flattened neighbour MDs per warp in shared memory
-constexpr uint32_t LS_RING = 128;      // ring of queued list positions (> 31 + 2 * 32)
-// per warp after the list: the ring and one pass bit per list position for each of two MDs
-constexpr uint32_t LS_EXTRA_WORDS = LS_RING + 2 * LS_LIST_CAP / 32;
+constexpr uint32_t LS_ANCHORS = 8;     // MDs of a module tested per walk over its list
+constexpr uint32_t LS_RING = 64;       // ring of queued (list position, anchor) entries (> 31 + 32)
+// per warp after the list: the ring, one pass bit per list position for each anchor, and
+// the anchors (lower hit, tolerances, direction terms: three float4 each)
+constexpr uint32_t LS_EXTRA_WORDS = LS_RING + LS_ANCHORS * LS_LIST_CAP / 32 + LS_ANCHORS * 12;
 
 // Unit = (event, module A).  The warp writes the indices of all MDs on the modules connected
 // to A into a shared-memory list once (module order, then MD order), then walks the list in
@@ -689,7 +691,7 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
   uint32_t* list = ls_smem + (threadIdx.x >> 5) * (list_cap + LS_EXTRA_WORDS);
   uint32_t* queue = list + list_cap;
   uint32_t* pbits = queue + LS_RING;
-  uint32_t* pbits2 = pbits + LS_LIST_CAP / 32;
+  float4* anc = reinterpret_cast<float4*>(pbits + LS_ANCHORS * LS_LIST_CAP / 32);
   WarpAlloc wa;
   unsigned long long n_cand = 0;  // count pass: candidate pairs this warp tested
   const uint32_t n_ev = H->n_ev;
@@ -755,6 +757,14 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
     if (t_disk == NONE) t_disk = len;
     __syncwarp();
     if (!FILL) n_cand += (unsigned long long)len * (a1 - a0);
+    if (len == 0) {  // no neighbour MDs: no LS (and no shared memory touched)
+      if (!FILL)
+        for (uint32_t a = a0 + lane; a < a1; a += 32) {
+          B.ls_cnt[a] = 0;
+          B.mask_off[a] = NONE;
+        }
+      return;
+    }
     if (len > list_cap) {
       for (uint32_t a = a0; a < a1; a++) ls_md_join<FILL>(C, G, B, a, ev, A, wa);
       return;
@@ -788,9 +798,10 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
         }
       }
     } else {
-      // Two MDs of A per walk over the list: each candidate loaded is tested against both
-      // anchors (their own pass bits, pbits and pbits2); the head's survivors are queued
-      // as list position | anchor << 15 and the tail runs on 32 of them at a time.
+      // Up to LS_ANCHORS MDs of A per walk over the list: their points are staged in shared
+      // memory (read as broadcasts) and each candidate loaded is tested against all of
+      // them, each anchor with its own pass bits; the head's survivors are queued as
+      // list position | anchor << 9 and the tail runs on 32 of them at a time.
       const uint32_t nwords = (len + 31) >> 5;
       // record of MD a: [count, partner MDs in list order] -- the fill pass only copies it
       auto record = [&](uint32_t a, const uint32_t* bits) {
@@ -832,49 +843,46 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
           B.ls_cnt[a] = count;
         }
       };
-      for (uint32_t a = a0; a < a1; a += 2) {
-        const bool two = a + 1 < a1;
-        const uint32_t a2 = two ? a + 1 : a;
-        const PointTol pa0 = md_point(B, a), pa1 = md_point(B, a2);
-        const float4 da0 = B.md_dir4[a], da1 = B.md_dir4[a2];
-        if (lane < nwords) {
-          pbits[lane] = 0;
-          pbits2[lane] = 0;
+      for (uint32_t ag = a0; ag < a1; ag += LS_ANCHORS) {
+        const uint32_t na = min(LS_ANCHORS, a1 - ag);
+        if (lane < na) {
+          anc[3 * lane] = B.md_pt[2 * (size_t)(ag + lane)];
+          anc[3 * lane + 1] = B.md_pt[2 * (size_t)(ag + lane) + 1];
+          anc[3 * lane + 2] = B.md_dir4[ag + lane];
         }
+        for (uint32_t i = lane; i < na * (LS_LIST_CAP / 32); i += 32) pbits[i] = 0;
         uint32_t qh = 0, qt = 0;  // ring head and tail (free-running)
         auto tail = [&](uint32_t e) {
-          const bool second = e >> 15;
-          const uint32_t q = e & 0x7FFFu;
+          const uint32_t k = e >> 9, q = e & 511u;
           const uint32_t j = list[q];
           const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
-          const PointTol& pa = second ? pa1 : pa0;
-          if (ls_tail_k(C, G, B, pa, second ? da1 : da0, rnext, exit, j))
-            atomicOr(&(second ? pbits2 : pbits)[q >> 5], 1u << (q & 31));
+          const PointTol pa{anc[3 * k], anc[3 * k + 1]};
+          if (ls_tail_k(C, G, B, pa, anc[3 * k + 2], rnext, exit, j))
+            atomicOr(&pbits[k * (LS_LIST_CAP / 32) + (q >> 5)], 1u << (q & 31));
         };
         __syncwarp();
         for (uint32_t t0 = 0; t0 < len; t0 += 32) {
           const uint32_t t = t0 + lane;
-          const uint32_t j = t < len ? list[t] : a;  // a: any valid MD for idle lanes
+          const uint32_t j = t < len ? list[t] : a0;  // a0: any valid MD for idle lanes
           const PointTol pb{__ldg(&B.md_pt[2 * (size_t)j]), __ldg(&B.md_pt[2 * (size_t)j + 1])};
-          const bool h0 = t < len && ls_head_pt(C, pa0, pb);
-          const uint32_t hb0 = __ballot_sync(FULL, h0);
-          if (h0) queue[(qt + __popc(hb0 & lt)) & (LS_RING - 1)] = t;
-          qt += __popc(hb0);
-          const bool h1 = two && t < len && ls_head_pt(C, pa1, pb);
-          const uint32_t hb1 = __ballot_sync(FULL, h1);
-          if (h1) queue[(qt + __popc(hb1 & lt)) & (LS_RING - 1)] = t | 0x8000u;
-          qt += __popc(hb1);
-          __syncwarp();
-          while (qt - qh >= 32) {
-            tail(queue[(qh + lane) & (LS_RING - 1)]);
-            qh += 32;
+          for (uint32_t k = 0; k < na; k++) {
+            const PointTol pa{anc[3 * k], anc[3 * k + 1]};
+            const bool h = t < len && ls_head_pt(C, pa, pb);
+            const uint32_t hb = __ballot_sync(FULL, h);
+            if (h) queue[(qt + __popc(hb & lt)) & (LS_RING - 1)] = t | (k << 9);
+            qt += __popc(hb);
+            if (qt - qh >= 32) {
+              __syncwarp();
+              tail(queue[(qh + lane) & (LS_RING - 1)]);
+              qh += 32;
+            }
           }
         }
+        __syncwarp();
         if (lane < qt - qh) tail(queue[(qh + lane) & (LS_RING - 1)]);
         __syncwarp();
-        record(a, pbits);
-        if (two) record(a + 1, pbits2);
-        __syncwarp();  // pbits and the queue are reused by the next pair
+        for (uint32_t k = 0; k < na; k++) record(ag + k, pbits + k * (LS_LIST_CAP / 32));
+        __syncwarp();  // anchors, pbits and the queue are reused by the next group
       }
     }
     __syncwarp();  // the list is rewritten by the next unit
