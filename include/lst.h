@@ -99,7 +99,7 @@ typedef struct lst_batch_dev {
 typedef struct lst_config {
   int32_t device;        /* CUDA device ordinal (default 0) */
   uint32_t keep_objects; /* 1: every result also keeps all intermediate objects (tests) */
-  uint32_t use_graph;    /* lst_run_batch: 0 default (graph on), 1 force on, 2 force off */
+  uint32_t use_graph;    /* lst_run_event / lst_run_batch: 0 default (graph on), 1 force on, 2 force off */
   uint32_t block_size;   /* threads per block of the stage kernels (0 = tuned default) */
   uint32_t blocks_per_sm;/* resident blocks per SM of the persistent grids (0 = default) */
   uint32_t profile;      /* 1: run kernels eagerly with a CUDA event after each (per-kernel times) */
@@ -159,8 +159,9 @@ lst_status lst_load_geometry(const lst_module_desc *mods, uint32_t n_mods, const
  * pass the LS selection.  Errors: INVALID_ARG, OOM, CUDA. */
 lst_status lst_build_connection_map(lst_ctx *ctx);
 
-/* Runs the whole chain on one event with plain stream-ordered launches (the per-event
- * path).  ev: host arrays.  *out receives a result id (free with lst_release_result).
+/* Runs the whole chain on one event (the per-event path): the same persistent kernels as a
+ * batch, replayed from the context's CUDA graph (plain stream-ordered launches when
+ * use_graph = 2).  ev: host arrays.  *out receives a result id (free with lst_release_result).
  * Errors: INVALID_ARG, BAD_INPUT (checked on the device), NO_MAP, OOM, CUDA, TIMEOUT. */
 lst_status lst_run_event(lst_ctx *ctx, const lst_event *ev, lst_result_id *out);
 

@@ -1145,7 +1145,7 @@ lst_status lst_build_connection_map(lst_ctx* c) {
 
 lst_status lst_run_event(lst_ctx* c, const lst_event* ev, lst_result_id* out) {
   if (!c || !ev || !out) return LST_ERR_INVALID_ARG;
-  return guarded(c, [&]() { return run_host_batch(c, ev, 1, out, false); });
+  return guarded(c, [&]() { return run_host_batch(c, ev, 1, out, c->cfg.use_graph != 2); });
 }
 
 lst_status lst_run_batch(lst_ctx* c, const lst_event* evs, uint32_t n, lst_result_id* outs) {

@@ -208,6 +208,19 @@ def test_launch_configuration_invariance(built, full_geom):
         assert tc == ref, (bs, bps)
 
 
+def test_graph_and_eager_launches_agree(built, full_geom, ora_full):
+    # the per-event path replays the context's graph; use_graph = 2 launches stream-ordered
+    ev = S.make_event("pu200", 11, n_tracks=1200, with_pls=True)
+    out = []
+    for g in (0, 2):
+        s = lst.Session(full_geom.modules, keep_objects=True, use_graph=g)
+        rid = s.run_event(ev)
+        compare(s, rid, oracle.run(ora_full, ev), ev, f"use_graph={g}")
+        out.append(s.candidates(rid).tobytes())
+        s.close()
+    assert out[0] == out[1]
+
+
 def test_repeat_runs_identical(sess_full):
     ev = S.make_event("pu200", 10, with_pls=True)
     a = sess_full.candidates(sess_full.run_event(ev)).tobytes()
