@@ -41,7 +41,7 @@ struct Hdr {
 };
 
 // Work counters in Hdr::work, one per dynamically scheduled kernel and pass.
-enum WorkCounter : int { W_LS = 0, W_PT3_COUNT, W_PT3_FILL, W_PT5_COUNT, W_PT5_FILL, N_WORK };
+enum WorkCounter : int { W_LS = 0, W_PT3_COUNT, W_PT3_FILL, W_PT5_COUNT, W_PT5_FILL, W_PT3_FIRST, N_WORK };
 static_assert(N_WORK <= 16, "Hdr::work too small");
 
 // Geometry tables (device pointers) and per-geometry scalars.
@@ -114,12 +114,12 @@ typedef void (*MarkFn)(void* arg, int kernel_name);
 extern const char* const kKernelNames[];
 extern const int kNumKernelNames;
 
-// A second stream for work that depends only on the inputs (the pLS preparation): forked
-// from the main stream at the start of the chain and joined before the first kernel that
-// needs its results, so it overlaps the hit, MD and LS stages.  Null: one stream.
+// A second stream for the pLS side of the chain: the pLS preparation (needs only the inputs)
+// forked at the start, then pT3 phase 1 once the MDs exist; joined before the pT3 count, so
+// it overlaps the hit, MD, LS, T3 and T5 stages.  Null: one stream.
 struct SideBranch {
   cudaStream_t s;
-  cudaEvent_t fork, join;
+  cudaEvent_t fork, mds, join;  // chain start; MDs written; side work done
 };
 
 struct Launch {

@@ -391,7 +391,7 @@ struct Pipeline {
   MethodConst C;
   Launch L;
   cudaStream_t stream = nullptr;
-  SideBranch side{nullptr, nullptr, nullptr};  // second stream of the chain (not in profile mode)
+  SideBranch side{nullptr, nullptr, nullptr, nullptr};  // second stream of the chain (not in profile mode)
   cudaEvent_t done = nullptr;
   Caps cap;
   uint64_t dev_bytes = 0;
@@ -468,9 +468,10 @@ struct Pipeline {
     done = nullptr;
     stream = nullptr;
     if (side.fork) cudaEventDestroy(side.fork);
+    if (side.mds) cudaEventDestroy(side.mds);
     if (side.join) cudaEventDestroy(side.join);
     if (side.s) cudaStreamDestroy(side.s);
-    side = SideBranch{nullptr, nullptr, nullptr};
+    side = SideBranch{nullptr, nullptr, nullptr, nullptr};
   }
 
   void set_tuning(const lst_config& cfg, int n_sm) {
@@ -493,6 +494,7 @@ struct Pipeline {
     CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&side.mds, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming));
     profile = cfg.profile != 0;
     if (profile) {

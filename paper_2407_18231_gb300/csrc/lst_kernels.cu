@@ -1239,29 +1239,26 @@ __device__ __forceinline__ PlsHelix load_helix(const BufView& B, uint32_t p) {
 constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, kept per pLS
 constexpr uint32_t PT3_RING = 64;    // queued pre-rejection survivors per warp (> 31 + 32)
 
-// pT3 (Sec. 1: pLS + T3).  Unit = pLS p.  Phase 1 tests p against every MD on its
-// candidate modules (the first anchor of any T3 it could join) and keeps the passing MDs in
-// order; phase 2 walks the T3s starting at those MDs and tests their other two anchors.  The
-// set equals "T3s whose first MD is on a candidate module, all three anchors inside the
-// windows" and comes out in T3 order.  More than PLS_MD_CAP passing MDs: the pLS falls back
-// to walking every T3 of its candidate modules.
-template <bool FILL>
-__global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B) {
+// pT3 phase 1 (Sec. 1: pLS + T3), on its own so that it can run beside the LS, T3 and T5
+// stages (it needs only the MDs and the pLS preparation).  Unit = pLS p, one warp: the
+// first-anchor window on every MD of p's candidate modules; a cheap pre-rejection runs on
+// every MD, survivors are queued in MD order and the full window test runs on 32 of them
+// at a time, so the passing MDs (at most PLS_MD_CAP kept, else NONE) come out in MD order.
+__global__ void __launch_bounds__(512) k_pt3_first_anchor(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
   __shared__ uint32_t pt3_ring[512 / 32][PT3_RING];
-  WarpAlloc wa;
-  DYN_LOOP(p, &B.hdr->work[FILL ? W_PT3_FILL : W_PT3_COUNT], n, 2) {
+  DYN_LOOP(p, &B.hdr->work[W_PT3_FIRST], n, 2) {
     const PlsHelix h = load_helix(B, p);
     const uint32_t ubase = B.pls_ev[p] * G.nm;
     const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
     const uint32_t nc = B.pls_ncand[p];
     uint32_t* mlist = B.pls_mdpass + (size_t)p * PLS_MD_CAP;
     uint32_t npass;
-    if (!FILL) {
+    {
       // the pre-rejection runs on every MD; survivors are queued in MD order and the full
       // window test runs on 32 of them at a time, so passes are appended in MD order
       uint32_t* ring = pt3_ring[threadIdx.x >> 5];
@@ -1308,9 +1305,30 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
       if (npass > PLS_MD_CAP) npass = NONE;
       if (lane == 0) B.pls_nmdpass[p] = npass;
       __syncwarp();
-    } else {
-      npass = B.pls_nmdpass[p];
     }
+  }
+}
+
+// pT3 (Sec. 1: pLS + T3).  Unit = pLS p.  Phase 1 tests p against every MD on its
+// candidate modules (the first anchor of any T3 it could join) and keeps the passing MDs in
+// order; phase 2 walks the T3s starting at those MDs and tests their other two anchors.  The
+// set equals "T3s whose first MD is on a candidate module, all three anchors inside the
+// windows" and comes out in T3 order.  More than PLS_MD_CAP passing MDs: the pLS falls back
+// to walking every T3 of its candidate modules.
+template <bool FILL>
+__global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->n_pls;
+  const uint32_t lane = lane_id();
+  WarpAlloc wa;
+  DYN_LOOP(p, &B.hdr->work[FILL ? W_PT3_FILL : W_PT3_COUNT], n, 2) {
+    const PlsHelix h = load_helix(B, p);
+    const uint32_t ubase = B.pls_ev[p] * G.nm;
+    const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
+    const uint32_t nc = B.pls_ncand[p];
+    uint32_t* mlist = B.pls_mdpass + (size_t)p * PLS_MD_CAP;
+    const uint32_t npass = B.pls_nmdpass[p];  // from k_pt3_first_anchor
     const uint32_t base = FILL ? B.pt3_off[p] : 0u;
     const uint32_t n_out = FILL ? B.pt3_off[p + 1] - base : 0u;
     const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[4], &B.mask_off[p]};
@@ -1756,7 +1774,7 @@ const char* const kKernelNames[] = {
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "zero_md_lists", "md_lists_count", "md_lists_fill",
     "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
-    "t3_md_offsets", "t5_md_offsets"};
+    "t3_md_offsets", "t5_md_offsets", "pt3_first_anchor"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Marker {
@@ -1806,7 +1824,6 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     cudaStreamWaitEvent(side->s, side->fork, 0);
     k_pls_prep<<<g, 128, 0, side->s>>>(C, G, B);
     mk(15);
-    cudaEventRecord(side->join, side->s);
   }
   k_zero<<<g, 256, 0, s>>>(B.sen_cnt, &H->n_ev, two_nm, 1);
   mk(0);
@@ -1822,6 +1839,13 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.md_cnt, B.md_off, &H->n_ev, G.nm, T_MD, B.cap_md, mk);
   k_md<true><<<g, bs, 0, s>>>(C, G, B);
   mk(8);
+  if (side) {  // pT3 phase 1 needs the MDs and the pLS preparation only
+    cudaEventRecord(side->mds, s);
+    cudaStreamWaitEvent(side->s, side->mds, 0);
+    k_pt3_first_anchor<<<g, bs, 0, side->s>>>(C, G, B);
+    mk(34);
+    cudaEventRecord(side->join, side->s);
+  }
   const uint32_t lcap = L.ls_list_cap;
   const size_t ls_smem = lcap ? (bs / 32) * (lcap + LS_EXTRA_WORDS) * sizeof(uint32_t) : 0;
   k_ls<false><<<g, bs, ls_smem, s>>>(C, G, B, lcap);
@@ -1848,6 +1872,8 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   } else {
     k_pls_prep<<<g, 128, 0, s>>>(C, G, B);
     mk(15);
+    k_pt3_first_anchor<<<g, bs, 0, s>>>(C, G, B);
+    mk(34);
   }
   k_pt3<false><<<g, bs, 0, s>>>(C, G, B);
   mk(16);
