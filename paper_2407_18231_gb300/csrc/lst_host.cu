@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <condition_variable>
@@ -367,10 +368,85 @@ struct Geometry {
   }
 };
 
+// ------------------------------------------------------------------ host copy workers
+// A fixed set of helper threads for the host-side copies of a batch (packing the inputs
+// into pinned staging, unpacking the candidates): run(n, fn) calls fn(0..n-1) on the helpers
+// and the caller and returns when all calls are done.  One per pipeline, so batch slots
+// served concurrently never share it.
+class Workers {
+ public:
+  explicit Workers(unsigned n_helpers) {
+    for (unsigned i = 0; i < n_helpers; i++) th_.emplace_back([this] { loop(); });
+  }
+  ~Workers() {
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  void run(uint32_t n, const std::function<void(uint32_t)>& fn) {
+    if (n == 0) return;
+    uint64_t g;
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      fn_ = &fn;
+      n_ = n;
+      next_ = 0;
+      left_ = n;
+      g = ++gen_;
+    }
+    cv_.notify_all();
+    work(g, &fn);
+    std::unique_lock<std::mutex> lk(m_);
+    done_cv_.wait(lk, [this] { return left_ == 0; });
+  }
+
+ private:
+  // tasks are claimed under the lock and only for the job of generation g, so a helper
+  // that wakes after its job has ended never runs a later job's task with a stale fn
+  bool claim(uint64_t g, uint32_t& i) {
+    std::lock_guard<std::mutex> lk(m_);
+    if (gen_ != g || next_ >= n_) return false;
+    i = next_++;
+    return true;
+  }
+  void work(uint64_t g, const std::function<void(uint32_t)>* fn) {
+    uint32_t i;
+    while (claim(g, i)) {
+      (*fn)(i);
+      std::lock_guard<std::mutex> lk(m_);
+      if (--left_ == 0) done_cv_.notify_all();
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void(uint32_t)>* fn;
+      {
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+        fn = fn_;
+      }
+      work(seen, fn);
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex m_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(uint32_t)>* fn_ = nullptr;
+  uint32_t n_ = 0, next_ = 0, left_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
 // ------------------------------------------------------------------ results
 struct Result {
-  std::shared_ptr<const std::vector<lst_tc>> tc_buf;  // the batch's candidates
-  size_t tc_off = 0, tc_n = 0;                        // this event's slice
+  std::shared_ptr<const lst_tc[]> tc_buf;  // the batch's candidates
+  size_t tc_off = 0, tc_n = 0;             // this event's slice
   bool has_objects = false;
   std::vector<lst_md_rec> md;
   std::vector<lst_ls_rec> ls;
@@ -414,9 +490,18 @@ struct Pipeline {
   // host staging (pinned)
   Hdr* h_hdr = nullptr;        // header to upload
   Hdr* h_hdr_out = nullptr;    // header read back
-  std::vector<char> stage_dummy;
   void* h_stage = nullptr;
   size_t h_stage_bytes = 0;
+  lst_tc* h_tc = nullptr;  // pinned landing area of the candidates
+  size_t h_tc_cap = 0;
+  std::unique_ptr<Workers> workers;  // host copy helpers (created on first use)
+  Workers& copiers() {
+    if (!workers) {
+      const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+      workers.reset(new Workers(std::min(hw, 16u) - 1));
+    }
+    return *workers;
+  }
   // graph
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
@@ -455,6 +540,10 @@ struct Pipeline {
     dev_bytes = 0;
     if (h_hdr) cudaFreeHost(h_hdr);
     if (h_hdr_out) cudaFreeHost(h_hdr_out);
+    workers.reset();
+    if (h_tc) cudaFreeHost(h_tc);
+    h_tc = nullptr;
+    h_tc_cap = 0;
     if (h_stage) cudaFreeHost(h_stage);
     h_hdr = h_hdr_out = nullptr;
     h_stage = nullptr;
@@ -863,12 +952,11 @@ void pack_host_events(Pipeline& P, const lst_event* evs, uint32_t n) {
     }
   };
   const uint64_t total_bytes = nh * 16 + np * sizeof(PlsIn);
-  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const uint32_t nt = (uint32_t)std::min<uint64_t>({(uint64_t)n, (uint64_t)std::min(hw, 8u), total_bytes / (2u << 20) + 1});
+  const uint32_t nt = (uint32_t)std::min<uint64_t>({(uint64_t)n, 16u, total_bytes / (1u << 20) + 1});
   if (nt <= 1) {
     copy_range(0, n);
   } else {
-    // split events into nt ranges of about equal bytes
+    // split events into nt ranges of about equal bytes, copied by the pipeline's helpers
     std::vector<uint32_t> cut(nt + 1, n);
     cut[0] = 0;
     uint64_t acc = 0;
@@ -877,11 +965,7 @@ void pack_host_events(Pipeline& P, const lst_event* evs, uint32_t n) {
       acc += (uint64_t)evs[i].n_hits * 16 + (uint64_t)evs[i].n_pls * sizeof(PlsIn);
       if (acc * nt >= total_bytes * k) cut[k++] = i + 1;
     }
-    std::vector<std::thread> th;
-    for (uint32_t t = 1; t < nt; t++)
-      if (cut[t] < cut[t + 1]) th.emplace_back(copy_range, cut[t], cut[t + 1]);
-    copy_range(cut[0], cut[1]);
-    for (auto& t : th) t.join();
+    P.copiers().run(nt, [&](uint32_t t) { copy_range(cut[t], cut[t + 1]); });
   }
   cudaStream_t st = P.stream;
   if (nh) {
@@ -954,10 +1038,17 @@ void collect(lst_ctx* c, Pipeline& P, lst_result_id* outs, uint32_t* n_tc_per_ev
   const uint32_t ne = P.n_ev;
   std::vector<uint32_t> evoff(ne + 1);
   CK(cudaMemcpyAsync(evoff.data(), P.tc_ev_off.p, (ne + 1) * 4, cudaMemcpyDeviceToHost, P.stream));
-  auto tcs_ptr = std::make_shared<std::vector<lst_tc>>(outs ? h.tot[T_TC] : 0);
-  std::vector<lst_tc>& tcs = *tcs_ptr;
-  if (!tcs.empty())
-    CK(cudaMemcpyAsync(tcs.data(), P.tc.p, tcs.size() * sizeof(lst_tc), cudaMemcpyDeviceToHost, P.stream));
+  // candidates: device -> pinned landing area (fast), then copied by the helpers into one
+  // buffer shared by the batch's results
+  const size_t n_tc = outs ? h.tot[T_TC] : 0;
+  if (n_tc > P.h_tc_cap) {
+    if (P.h_tc) cudaFreeHost(P.h_tc);
+    P.h_tc = nullptr;
+    P.h_tc_cap = 0;
+    CK(cudaMallocHost((void**)&P.h_tc, n_tc * 3 / 2 * sizeof(lst_tc)));
+    P.h_tc_cap = n_tc * 3 / 2;
+  }
+  if (n_tc) CK(cudaMemcpyAsync(P.h_tc, P.tc.p, n_tc * sizeof(lst_tc), cudaMemcpyDeviceToHost, P.stream));
   const bool keep = c->cfg.keep_objects != 0 && outs;
   std::vector<uint32_t> md_off, md_unit, md_lo, md_up, ls_in, ls_out, t3a, t3b, t3c, t5m[5], t3_off, t5_off, pt3p,
       pt3o, pt5p, pt5o, a5, a3, at, ptc, pncand, pcand, pt3_off, pt5_off, poff;
@@ -999,6 +1090,15 @@ void collect(lst_ctx* c, Pipeline& P, lst_result_id* outs, uint32_t* n_tc_per_ev
     get(poff, P.in_poff, ne + 1);
   }
   CK(cudaStreamSynchronize(P.stream));
+  std::shared_ptr<lst_tc[]> tcs_ptr(new lst_tc[n_tc ? n_tc : 1]);
+  if (n_tc) {
+    const uint32_t parts = (uint32_t)std::min<size_t>(16, n_tc / 4096 + 1);
+    const size_t per = (n_tc + parts - 1) / parts;
+    P.copiers().run(parts, [&](uint32_t t) {
+      const size_t b = t * per, e = std::min(n_tc, b + per);
+      if (b < e) memcpy(tcs_ptr.get() + b, P.h_tc + b, (e - b) * sizeof(lst_tc));
+    });
+  }
   const uint32_t nm = c->geo.nm;
   for (uint32_t e = 0; e < ne; e++) {
     if (n_tc_per_event) n_tc_per_event[e] = evoff[e + 1] - evoff[e];
@@ -1212,7 +1312,7 @@ lst_status lst_get_candidates(lst_ctx* c, lst_result_id id, lst_tc* buf, uint32_
   *n_out = (uint32_t)r.tc_n;
   if (!buf) return LST_OK;
   if (cap < r.tc_n) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "candidate buffer too small");
-  if (r.tc_n) memcpy(buf, r.tc_buf->data() + r.tc_off, r.tc_n * sizeof(lst_tc));
+  if (r.tc_n) memcpy(buf, r.tc_buf.get() + r.tc_off, r.tc_n * sizeof(lst_tc));
   return LST_OK;
 }
 
