@@ -79,7 +79,7 @@ class lst_stats(C.Structure):
 
 class lst_serve_config(C.Structure):
     _fields_ = [("n_slots", C.c_uint32), ("max_batch", C.c_uint32), ("memory_budget", C.c_uint64),
-                ("reserved", C.c_uint32 * 8)]
+                ("share_device", C.c_uint32), ("reserved", C.c_uint32 * 7)]
 
 
 EXPORTS = [
@@ -236,7 +236,8 @@ class Session:
         _check(self.ctx, L.lst_get_profile(self.ctx, buf, n.value, C.byref(n)))
         return {buf[i].name.decode(): (buf[i].launches, buf[i].ms) for i in range(n.value)}
 
-    def serve_replay(self, events, arrival_s, *, n_slots=4, max_batch=16, memory_budget=0, keep_results=False):
+    def serve_replay(self, events, arrival_s, *, n_slots=4, max_batch=16, memory_budget=0, keep_results=False,
+                     share_device=False):
         n = len(events)
         keep = []
         arr = (lst_event * n)(*[_event_struct(ev, keep) for ev in events])
@@ -245,7 +246,7 @@ class Session:
         ntc = np.zeros(n, np.uint32)
         ids = (C.c_uint64 * n)() if keep_results else None
         wall = C.c_double()
-        cfg = lst_serve_config(n_slots, max_batch, memory_budget)
+        cfg = lst_serve_config(n_slots, max_batch, memory_budget, int(share_device))
         _check(self.ctx, load_library().lst_serve_replay(self.ctx, C.byref(cfg), arr, arrival.ctypes.data, n,
                                                          lat.ctypes.data, ntc.ctypes.data, ids, C.byref(wall)))
         return lat, ntc, (list(ids) if keep_results else None), wall.value

@@ -1459,6 +1459,8 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
     }
     // Shared state: arrived events not yet taken, and the first error of any worker.
     std::mutex qm;
+    std::mutex device_turn;  // held from launch to completion unless the slots share the device
+    const bool share = cfg->share_device != 0;
     std::condition_variable qcv;
     std::deque<uint32_t> queue;
     bool closed = false;
@@ -1514,8 +1516,12 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
           if (budget && held_by_others(k) + P.dev_bytes > budget && take.size() == 1)
             return set_error(LST_ERR_BUDGET, "one event alone exceeds the memory budget");
           for (int attempt = 0;; attempt++) {
-            P.launch(true);
-            if (!P.wait(0)) return set_error(LST_ERR_TIMEOUT, "device did not finish");
+            {
+              std::unique_lock<std::mutex> turn(device_turn, std::defer_lock);
+              if (!share) turn.lock();
+              P.launch(true);
+              if (!P.wait(0)) return set_error(LST_ERR_TIMEOUT, "device did not finish");
+            }
             const Hdr& h = *P.h_hdr_out;
             if (h.err & ERR_BAD_INPUT) return set_error(LST_ERR_BAD_INPUT, "bad input in a served event");
             if (!P.grow_after_overflow(h)) {

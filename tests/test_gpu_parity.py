@@ -255,8 +255,10 @@ def test_serving_results_equal_alone(built, full_geom):
     s = lst.Session(full_geom.modules)
     alone = [s.candidates(s.run_event(e)).tobytes() for e in evs]
     arrival = np.cumsum(np.full(len(evs), 2e-4))
-    lat, ntc, ids, wall = s.serve_replay(evs, arrival, n_slots=3, max_batch=4, keep_results=True)
-    for i in range(len(evs)):
-        assert s.candidates(ids[i]).tobytes() == alone[i], i
-        assert lat[i] > 0
+    for share in (False, True):  # one batch on the device at a time, or all slots at once
+        lat, ntc, ids, wall = s.serve_replay(evs, arrival, n_slots=3, max_batch=4, keep_results=True,
+                                             share_device=share)
+        for i in range(len(evs)):
+            assert s.candidates(ids[i]).tobytes() == alone[i], (share, i)
+            assert lat[i] > 0
     s.close()
