@@ -186,6 +186,14 @@ lst_status lst_batch_finish(lst_ctx *ctx, uint32_t timeout_ms, uint32_t *n_tc_pe
  * only *n_out is set (size query).  Errors: NOT_FOUND, BUFFER_TOO_SMALL, INVALID_ARG. */
 lst_status lst_get_candidates(lst_ctx *ctx, lst_result_id id, lst_tc *buf, uint32_t cap, uint32_t *n_out);
 
+/* The candidates of n results in one call (no paper counterpart: a batch convenience).
+ * ids: host array of n result ids.  counts: host array of n, receives each result's number
+ * of candidates.  buf (host, cap records) receives them back to back in ids' order; with
+ * buf == NULL only counts and *n_total are set (size query).  Errors: INVALID_ARG,
+ * NOT_FOUND (an unknown id; nothing is copied), BUFFER_TOO_SMALL (cap < *n_total). */
+lst_status lst_get_candidates_batch(lst_ctx *ctx, const lst_result_id *ids, uint32_t n, lst_tc *buf, uint64_t cap,
+                                    uint32_t *counts, uint64_t *n_total);
+
 /* Copies one kind of intermediate object (LST_OBJ_*) of a result kept with keep_objects = 1.
  * buf == NULL is a size query.  Errors: NOT_FOUND, INVALID_ARG (kind, or objects not kept),
  * BUFFER_TOO_SMALL. */

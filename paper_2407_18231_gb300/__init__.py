@@ -86,7 +86,7 @@ EXPORTS = [
     "lst_load_geometry", "lst_build_connection_map", "lst_run_event", "lst_run_batch", "lst_run_batch_device",
     "lst_batch_finish", "lst_get_candidates", "lst_get_objects", "lst_release_result", "lst_destroy",
     "lst_last_error", "lst_status_string", "lst_get_stats", "lst_get_profile", "lst_serve_replay",
-    "lst_run_event_static", "lst_set_tuning",
+    "lst_run_event_static", "lst_set_tuning", "lst_get_candidates_batch",
 ]
 
 _lib = None
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
             "lst_serve_replay": (i32, [P, P, P, P, u32, P, P, P, P]),
             "lst_run_event_static": (i32, [P, P, P, u32, C.POINTER(u32), P]),
             "lst_set_tuning": (i32, [P, P]),
+            "lst_get_candidates_batch": (i32, [P, P, u32, P, C.c_uint64, P, C.POINTER(C.c_uint64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -206,6 +207,19 @@ class Session:
         out = np.zeros(n.value, TC_DTYPE)
         _check(self.ctx, L.lst_get_candidates(self.ctx, rid, out.ctypes.data, n.value, C.byref(n)))
         return out
+
+    def candidates_batch(self, rids) -> tuple[np.ndarray, np.ndarray]:
+        """All candidates of several results in one call: (records back to back, counts)."""
+        L = load_library()
+        n = len(rids)
+        ids = (C.c_uint64 * n)(*rids)
+        counts = np.zeros(n, np.uint32)
+        total = C.c_uint64()
+        _check(self.ctx, L.lst_get_candidates_batch(self.ctx, ids, n, None, 0, counts.ctypes.data, C.byref(total)))
+        out = np.empty(total.value, TC_DTYPE)
+        _check(self.ctx, L.lst_get_candidates_batch(self.ctx, ids, n, out.ctypes.data, total.value,
+                                                    counts.ctypes.data, C.byref(total)))
+        return out, counts
 
     def objects(self, rid: int, kind: int) -> np.ndarray:
         L = load_library()

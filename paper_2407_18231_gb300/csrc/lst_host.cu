@@ -1316,6 +1316,30 @@ lst_status lst_get_candidates(lst_ctx* c, lst_result_id id, lst_tc* buf, uint32_
   return LST_OK;
 }
 
+lst_status lst_get_candidates_batch(lst_ctx* c, const lst_result_id* ids, uint32_t n, lst_tc* buf, uint64_t cap,
+                                    uint32_t* counts, uint64_t* n_total) {
+  if (!c || !n_total || (n && (!ids || !counts))) return LST_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<const Result*> rs(n);
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    auto it = c->results.find(ids[i]);
+    if (it == c->results.end()) return fail(c, LST_ERR_NOT_FOUND, "unknown result id");
+    rs[i] = &it->second;
+    counts[i] = (uint32_t)rs[i]->tc_n;
+    total += rs[i]->tc_n;
+  }
+  *n_total = total;
+  if (!buf) return LST_OK;
+  if (cap < total) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "candidate buffer too small");
+  uint64_t o = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    if (rs[i]->tc_n) memcpy(buf + o, rs[i]->tc_buf.get() + rs[i]->tc_off, rs[i]->tc_n * sizeof(lst_tc));
+    o += rs[i]->tc_n;
+  }
+  return LST_OK;
+}
+
 lst_status lst_get_objects(lst_ctx* c, lst_result_id id, int32_t kind, void* buf, uint32_t cap, uint32_t* n_out) {
   if (!c || !n_out) return LST_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);

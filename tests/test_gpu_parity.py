@@ -221,6 +221,21 @@ def test_graph_and_eager_launches_agree(built, full_geom, ora_full):
     assert out[0] == out[1]
 
 
+def test_candidates_batch_matches_per_result(built, full_geom):
+    evs = [S.make_event("pu200", 20 + i, n_tracks=400 * (i + 1), with_pls=True) for i in range(5)]
+    s = lst.Session(full_geom.modules)
+    ids = s.run_batch(evs)
+    tcs, counts = s.candidates_batch(ids)
+    per = [s.candidates(i) for i in ids]
+    assert list(counts) == [len(p) for p in per]
+    assert tcs.tobytes() == b"".join(p.tobytes() for p in per)
+    s.release(ids[2])
+    with pytest.raises(lst.LstError) as e:
+        s.candidates_batch(ids)
+    assert e.value.status == -9  # NOT_FOUND
+    s.close()
+
+
 def test_repeat_runs_identical(sess_full):
     ev = S.make_event("pu200", 10, with_pls=True)
     a = sess_full.candidates(sess_full.run_event(ev)).tobytes()
