@@ -1009,6 +1009,7 @@ struct lst_ctx {
   std::string err;
   lst_stats stats{};
   uint32_t reruns = 0;
+  std::unique_ptr<Workers> getters;  // copies for lst_get_candidates_batch (used under mu only)
 };
 
 namespace {
@@ -1332,10 +1333,19 @@ lst_status lst_get_candidates_batch(lst_ctx* c, const lst_result_id* ids, uint32
   *n_total = total;
   if (!buf) return LST_OK;
   if (cap < total) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "candidate buffer too small");
-  uint64_t o = 0;
-  for (uint32_t i = 0; i < n; i++) {
-    if (rs[i]->tc_n) memcpy(buf + o, rs[i]->tc_buf.get() + rs[i]->tc_off, rs[i]->tc_n * sizeof(lst_tc));
-    o += rs[i]->tc_n;
+  std::vector<uint64_t> at(n + 1, 0);
+  for (uint32_t i = 0; i < n; i++) at[i + 1] = at[i] + rs[i]->tc_n;
+  auto copy = [&](uint32_t i) {
+    if (rs[i]->tc_n) memcpy(buf + at[i], rs[i]->tc_buf.get() + rs[i]->tc_off, rs[i]->tc_n * sizeof(lst_tc));
+  };
+  if (total * sizeof(lst_tc) < (1u << 20) || n < 2) {
+    for (uint32_t i = 0; i < n; i++) copy(i);
+  } else {  // large: one result per task on the context's helper threads
+    if (!c->getters) {
+      const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+      c->getters.reset(new Workers(std::min(hw, 16u) - 1));
+    }
+    c->getters->run(n, copy);
   }
   return LST_OK;
 }
