@@ -242,7 +242,7 @@ lst_status lst_get_profile(lst_ctx *ctx, lst_profile_entry *buf, uint32_t cap, u
  * GPU, a latency-critical loop that cannot take cudaMalloc's implicit synchronisation, a
  * plug-in in a process that forbids device allocations after start-up).  The paper has no
  * counterpart; this is a deployment convenience.
- * All intermediate lists live in one file-scope device array of 6 MiB that every GPU which
+ * All intermediate lists live in one file-scope device array of 8 MiB that every GPU which
  * loads the library holds until the process exits.  Limits per call: 8192 hits, 512 pLS,
  * 16384 modules in the context, 8192 MDs, 32768 LS, 32768 T3, 16384 T5, 16384 pT3,
  * 16384 pT5; anything larger returns LST_ERR_BUDGET with the list named in lst_last_error.

@@ -82,9 +82,11 @@ struct BufView {
   // T3: per LS count/offset of the T3s built on it, per MD offset of those starting there
   uint32_t *t3_lcnt, *t3_loff, *t3_off, *t3_a, *t3_b, *t3_c;
   uint32_t *t3_mask;  // per LS: pass bits of its first 32 candidates (count pass -> fill pass)
+  uint4 *t3_md4;      // per T3: (a, b, c, 0), one load for duplicate removal
   // T5: per T3 count/offset of the T5s built on it, per MD offset
   uint32_t *t5_tcnt, *t5_toff, *t5_off, *t5_m0, *t5_m1, *t5_m2, *t5_m3, *t5_m4;
   uint32_t *t5_mask;  // per T3: pass bits of its first 32 candidates
+  uint4 *t5_md8;      // per T5: (m0, m1, m2, m3), (m4, 0, 0, 0), two loads for duplicate removal
   float *t5_score, *t5_kfull;
   // pLS
   uint32_t *pls_ev, *pls_ncand, *pls_cand;

@@ -478,8 +478,8 @@ struct Pipeline {
   DevBuf sen_cnt, sen_off, hit_tmp, hit_ev, hit_idx, hit4;
   DevBuf md_cnt, md_off, md_unit, md_lo_idx, md_up_idx, md_pt, md_up4, md_dir4;
   DevBuf ls_cnt, ls_off, ls_in, ls_out;
-  DevBuf t3_lcnt, t3_loff, t3_off, t3_a, t3_b, t3_c, t3_mask;
-  DevBuf t5_tcnt, t5_toff, t5_off, t5_m[5], t5_score, t5_kfull, t5_mask;
+  DevBuf t3_lcnt, t3_loff, t3_off, t3_a, t3_b, t3_c, t3_mask, t3_md4;
+  DevBuf t5_tcnt, t5_toff, t5_off, t5_m[5], t5_score, t5_kfull, t5_mask, t5_md8;
   DevBuf pls_ev, pls_ncand, pls_cand, pls_h0, pls_h1, pls_pt, pls_mdpass, pls_nmdpass;
   DevBuf pt3_cnt, pt3_off, pt3_pls, pt3_obj, pt3_score;
   DevBuf pt5_cnt, pt5_off, pt5_pls, pt5_obj, pt5_score;
@@ -521,7 +521,7 @@ struct Pipeline {
   std::vector<DevBuf*> all_buffers() {
     std::vector<DevBuf*> v = {&hdr, &in_x, &in_y, &in_z, &in_det, &in_hoff, &in_pls, &in_poff, &sen_cnt, &sen_off,
                               &hit_tmp, &hit_ev, &hit_idx, &hit4, &md_cnt, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
-                              &md_pt, &md_up4, &md_dir4, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off, &t3_mask, &t5_mask,
+                              &md_pt, &md_up4, &md_dir4, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off, &t3_mask, &t5_mask, &t3_md4, &t5_md8,
                               &t3_a, &t3_b, &t3_c, &t5_tcnt, &t5_toff, &t5_off, &t5_score, &t5_kfull, &pls_ev,
                               &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
                               &pt5_cnt, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
@@ -641,6 +641,7 @@ struct Pipeline {
     need<uint32_t>(t3_loff, c.ls + 1);
     need<uint32_t>(t3_off, c.md + 1);
     need<uint32_t>(t3_a, c.t3);
+    need<uint4>(t3_md4, c.t3);
     need<uint32_t>(t3_b, c.t3);
     need<uint32_t>(t3_c, c.t3);
     need<uint32_t>(t5_tcnt, c.t3);
@@ -649,6 +650,7 @@ struct Pipeline {
     need<uint32_t>(t5_off, c.md + 1);
     for (auto& b : t5_m) need<uint32_t>(b, c.t5);
     need<float>(t5_score, c.t5);
+    need<uint4>(t5_md8, 2 * (size_t)c.t5);
     need<float>(t5_kfull, c.t5);
     need<uint32_t>(pls_ev, c.pls);
     need<uint32_t>(pls_ncand, c.pls);
@@ -764,9 +766,10 @@ struct Pipeline {
     v.md_dir4 = (float4*)md_dir4.p;
     v.ls_cnt = P32(ls_cnt); v.ls_off = P32(ls_off); v.ls_in = P32(ls_in); v.ls_out = P32(ls_out);
     v.t3_lcnt = P32(t3_lcnt); v.t3_loff = P32(t3_loff); v.t3_off = P32(t3_off); v.t3_mask = P32(t3_mask);
-    v.t3_a = P32(t3_a); v.t3_b = P32(t3_b); v.t3_c = P32(t3_c);
+    v.t3_a = P32(t3_a); v.t3_b = P32(t3_b); v.t3_c = P32(t3_c); v.t3_md4 = (uint4*)t3_md4.p;
     v.t5_tcnt = P32(t5_tcnt); v.t5_toff = P32(t5_toff); v.t5_off = P32(t5_off); v.t5_mask = P32(t5_mask);
     v.t5_m0 = P32(t5_m[0]); v.t5_m1 = P32(t5_m[1]); v.t5_m2 = P32(t5_m[2]); v.t5_m3 = P32(t5_m[3]);
+    v.t5_md8 = (uint4*)t5_md8.p;
     v.t5_m4 = P32(t5_m[4]);
     v.t5_score = (float*)t5_score.p; v.t5_kfull = (float*)t5_kfull.p;
     v.pls_ev = P32(pls_ev); v.pls_ncand = P32(pls_ncand); v.pls_cand = P32(pls_cand);

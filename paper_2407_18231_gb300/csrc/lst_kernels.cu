@@ -921,9 +921,11 @@ __global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B)
     }
     if (FILL && c1 - c0 <= 32) {  // the count pass's pass bits: no test
       for (uint32_t bits = B.t3_mask[l]; bits; bits &= bits - 1u) {
+        const uint32_t c = B.ls_out[c0 + __ffs(bits) - 1];
         B.t3_a[k] = a;
         B.t3_b[k] = b;
-        B.t3_c[k] = B.ls_out[c0 + __ffs(bits) - 1];
+        B.t3_c[k] = c;
+        B.t3_md4[k] = make_uint4(a, b, c, 0u);
         k++;
       }
       continue;
@@ -937,6 +939,7 @@ __global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B)
           B.t3_a[k] = a;
           B.t3_b[k] = b;
           B.t3_c[k] = c;
+          B.t3_md4[k] = make_uint4(a, b, c, 0u);
           k++;
         } else {
           cnt++;
@@ -999,6 +1002,8 @@ __global__ void __launch_bounds__(512) k_t5(MethodConst C, GeoView G, BufView B)
           B.t5_m2[k] = c;
           B.t5_m3[k] = d;
           B.t5_m4[k] = e;
+          B.t5_md8[2 * (size_t)k] = make_uint4(a, b, c, d);
+          B.t5_md8[2 * (size_t)k + 1] = make_uint4(e, 0u, 0u, 0u);
           B.t5_score[k] = score;
           B.t5_kfull[k] = kfull;
           k++;
@@ -1235,6 +1240,16 @@ __device__ __forceinline__ PlsHelix load_helix(const BufView& B, uint32_t p) {
   return h;
 }
 
+// MD tuples of a T5 and a T3, from their array-of-structs copies.
+__device__ __forceinline__ void t5_mds(const BufView& B, uint32_t t, uint32_t m[5]) {
+  const uint4 p = B.t5_md8[2 * (size_t)t];
+  m[0] = p.x; m[1] = p.y; m[2] = p.z; m[3] = p.w; m[4] = B.t5_md8[2 * (size_t)t + 1].x;
+}
+__device__ __forceinline__ void t3_mds(const BufView& B, uint32_t t, uint32_t m[3]) {
+  const uint4 p = B.t3_md4[t];
+  m[0] = p.x; m[1] = p.y; m[2] = p.z;
+}
+
 // ------------------------------------------------------------------ pT3 / pT5
 constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, kept per pLS
 constexpr uint32_t PT3_RING = 64;    // queued pre-rejection survivors per warp (> 31 + 32)
@@ -1402,17 +1417,20 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
           c = B.t5_toff[t + 1] - b;
         },
         [&](uint32_t, uint32_t t) {
-          if (!pls_anchor_accept(C, h, md_point(B, B.t5_m3[t]))) return false;
-          if (!pls_anchor_accept(C, h, md_point(B, B.t5_m4[t]))) return false;
-          const Circle3 fu = circle3(md_point(B, B.t5_m0[t]), md_point(B, B.t5_m2[t]), md_point(B, B.t5_m4[t]));
+          uint32_t m[5];
+          t5_mds(B, t, m);
+          if (!pls_anchor_accept(C, h, md_point(B, m[3]))) return false;
+          if (!pls_anchor_accept(C, h, md_point(B, m[4]))) return false;
+          const Circle3 fu = circle3(md_point(B, m[0]), md_point(B, m[2]), md_point(B, m[4]));
           return fabsf(fabsf(B.t5_kfull[t]) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
         },
         [&](uint32_t i, uint32_t t, ScorePayload& pl) {
           // anchors m0, m1, m2 are the parent pT3's a, b, c, summed in the same order: its
           // score is this sum after three terms, bit for bit
           float score = B.pt3_score[x0 + i];
-          pls_anchor(C, h, md_point(B, B.t5_m3[t]), score);
-          pls_anchor(C, h, md_point(B, B.t5_m4[t]), score);
+          const uint4 m0123 = B.t5_md8[2 * (size_t)t];
+          pls_anchor(C, h, md_point(B, m0123.w), score);
+          pls_anchor(C, h, md_point(B, B.t5_md8[2 * (size_t)t + 1].x), score);
           pl.score = score;
         },
         [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
@@ -1425,12 +1443,6 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
 }
 
 // ------------------------------------------------------------------ duplicate removal
-__device__ __forceinline__ void t5_mds(const BufView& B, uint32_t t, uint32_t m[5]) {
-  m[0] = B.t5_m0[t]; m[1] = B.t5_m1[t]; m[2] = B.t5_m2[t]; m[3] = B.t5_m3[t]; m[4] = B.t5_m4[t];
-}
-__device__ __forceinline__ void t3_mds(const BufView& B, uint32_t t, uint32_t m[3]) {
-  m[0] = B.t3_a[t]; m[1] = B.t3_b[t]; m[2] = B.t3_c[t];
-}
 template <int NA, int NB>
 __device__ __forceinline__ int shared_mds(const uint32_t (&a)[NA], const uint32_t (&b)[NB]) {
   int c = 0;

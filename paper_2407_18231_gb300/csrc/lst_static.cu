@@ -38,7 +38,7 @@ constexpr uint32_t MAX_T5 = 16384;
 constexpr uint32_t MAX_PT3 = 16384;
 constexpr uint32_t MAX_PT5 = 16384;
 constexpr uint32_t MASK_WORDS = 65536;  // join ballots; a fuller event just re-tests in its fill passes
-constexpr size_t SCRATCH_BYTES = size_t(6) << 20;  // every GPU that loads the library holds this until exit
+constexpr size_t SCRATCH_BYTES = size_t(8) << 20;  // every GPU that loads the library holds this until exit
 
 // The scratch.  In host code `g_scratch` is only a stand-in symbol: its device address
 // comes from cudaGetSymbolAddress, once per device.
@@ -91,6 +91,7 @@ size_t carve(char* base, BufView& B) {
   B.t3_a = c.take<uint32_t>(MAX_T3);
   B.t3_b = c.take<uint32_t>(MAX_T3);
   B.t3_c = c.take<uint32_t>(MAX_T3);
+  B.t3_md4 = c.take<uint4>(MAX_T3);
   B.t5_tcnt = c.take<uint32_t>(MAX_T3);
   B.t5_mask = c.take<uint32_t>(MAX_T3);
   B.t5_toff = c.take<uint32_t>(MAX_T3 + 1);
@@ -102,6 +103,7 @@ size_t carve(char* base, BufView& B) {
   B.t5_m4 = c.take<uint32_t>(MAX_T5);
   B.t5_score = c.take<float>(MAX_T5);
   B.t5_kfull = c.take<float>(MAX_T5);
+  B.t5_md8 = c.take<uint4>(2 * MAX_T5);
   B.pls_ev = c.take<uint32_t>(MAX_PLS);
   B.pls_ncand = c.take<uint32_t>(MAX_PLS);
   B.pls_cand = c.take<uint32_t>((size_t)MAX_PLS * MAX_CAND);
