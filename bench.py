@@ -290,8 +290,8 @@ def main():
         tuning = {"block_size": bs, "blocks_per_sm": bps, "ls_list_cap": cap}
     elif args.tune:
         from paper_2407_18231_gb300 import autotune
-        space = {"block_size": [128, 256], "blocks_per_sm": [2, 4, 8], "ls_list_cap": [128, 512]}
-        tuning = autotune.tune(geom.modules, events[:8], device=local, space=space, reps=2)["best"]
+        space = {"block_size": [128, 256], "blocks_per_sm": [4, 8, 12], "ls_list_cap": [128, 512]}
+        tuning = autotune.tune(geom.modules, events[:B], device=local, space=space, reps=5)["best"]
     sess = lst.Session(geom.modules, device=local, **tuning)
     # the library runs on this stream, so events recorded on it bracket its kernels
     stream = torch.cuda.Stream(dev)
