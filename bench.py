@@ -8,7 +8,7 @@ T5, pLS lookup, pT3, pT5, duplicate removal, track candidates.  A step is one ba
 --batch events through the whole chain.
 
   value     events/s, batched + CUDA graph, inputs resident in HBM (lst_run_batch_device)
-  e2e       events/s through lst_run_batch with host buffers (copies inside the timed region)
+  e2e       events/s through lst_submit_batch / lst_collect_batch with host buffers (copies inside the timed region)
   per_event events/s and p50/p99 latency of the plain per-event launch (lst_run_event)
   served    p50/p99 latency and events/s of the continuous-batching loop (lst_serve_replay)
   roofline  the kernel with the largest device time, algorithmic bytes / CUDA-event time
@@ -333,26 +333,32 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    # ---- end to end: host buffers through lst_run_batch (H2D + D2H inside the timed region)
+    # ---- end to end: host buffers through the asynchronous batch API (lst_submit_batch /
+    # lst_collect_batch): one batch in flight while the next is packed and uploaded; every
+    # step's H2D copy and the read-back of its candidates fall inside the timed region
     sess_h = lst.Session(geom.modules, device=local, **tuning)
-    for k in range(max(args.warmup, P)):  # every batch once: buffers sized, graph captured
-        for i in sess_h.run_batch(batches[k % P]):
+    for k in range(max(args.warmup, P) + 1):  # both slots: buffers sized, graphs captured
+        t_w = sess_h.submit_batch(batches[k % P])
+        for i in sess_h.collect_batch(sess_h.submit_batch(batches[(k + 1) % P])) + sess_h.collect_batch(t_w):
             sess_h.release(i)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     e2e_steps = max(3, min(args.steps, 10))
     d2h = 0
+    t0 = time.perf_counter()
+    ticket = sess_h.submit_batch(batches[0])
     for k in range(e2e_steps):
-        ids = sess_h.run_batch(batches[k % P])
+        nxt = sess_h.submit_batch(batches[(k + 1) % P]) if k + 1 < e2e_steps else None
+        ids = sess_h.collect_batch(ticket)
         tcs, _ = sess_h.candidates_batch(ids)
         d2h += len(tcs) * 76 + (B + 1) * 4 + 256
         for i in ids:
             sess_h.release(i)
+        ticket = nxt
     e2e_s = time.perf_counter() - t0
     e2e = {"value": e2e_steps * B / e2e_s, "unit": "events/s",
            "h2d_bytes_per_step": int(np.mean([sum(e.n_hits * 16 + e.n_pls * 80 for e in b) + 2 * (B + 1) * 4
                                               for b in batches])),
-           "d2h_bytes_per_step": int(d2h / e2e_steps)}
+           "d2h_bytes_per_step": int(d2h / e2e_steps), "api": "lst_submit_batch / lst_collect_batch, one batch in flight"}
 
     # ---- per-event launch: latency of single events
     per_event = None

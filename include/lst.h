@@ -182,6 +182,23 @@ lst_status lst_run_batch_device(lst_ctx *ctx, const lst_batch_dev *batch, void *
 lst_status lst_batch_finish(lst_ctx *ctx, uint32_t timeout_ms, uint32_t *n_tc_per_event,
                             lst_result_id *outs);
 
+/* Asynchronous batches (no paper counterpart: a pipelining convenience).  The context has
+ * two batch slots.  lst_submit_batch packs n host events into a free slot, uploads them on
+ * the slot's stream and queues the chain behind the other slot's batch (the device runs one
+ * batch at a time; the upload overlaps the other batch's work), then returns at once with
+ * a ticket; the caller's arrays may be reused as soon as it returns.  A caller that keeps
+ * one batch in flight while it submits the next overlaps its host work with the device.
+ * Errors: INVALID_ARG (null, n == 0, both slots in flight), NO_MAP, OOM, CUDA. */
+lst_status lst_submit_batch(lst_ctx *ctx, const lst_event *evs, uint32_t n, uint64_t *ticket);
+
+/* Waits (bounded by timeout_ms, 0 = no bound) for a submitted batch, re-runs it with larger
+ * buffers if an object list outgrew its storage, frees its slot and stores its results like
+ * lst_run_batch.  n_tc_per_event, outs: host arrays of the batch's n events (either may be
+ * NULL).  Errors: NOT_FOUND (unknown or collected ticket), TIMEOUT (the batch stays in
+ * flight), BAD_INPUT, OOM, CUDA. */
+lst_status lst_collect_batch(lst_ctx *ctx, uint64_t ticket, uint32_t timeout_ms, uint32_t *n_tc_per_event,
+                             lst_result_id *outs);
+
 /* Copies the track candidates of a result into buf (host, cap records).  With buf == NULL
  * only *n_out is set (size query).  Errors: NOT_FOUND, BUFFER_TOO_SMALL, INVALID_ARG. */
 lst_status lst_get_candidates(lst_ctx *ctx, lst_result_id id, lst_tc *buf, uint32_t cap, uint32_t *n_out);

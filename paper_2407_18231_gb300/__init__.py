@@ -86,7 +86,7 @@ EXPORTS = [
     "lst_load_geometry", "lst_build_connection_map", "lst_run_event", "lst_run_batch", "lst_run_batch_device",
     "lst_batch_finish", "lst_get_candidates", "lst_get_objects", "lst_release_result", "lst_destroy",
     "lst_last_error", "lst_status_string", "lst_get_stats", "lst_get_profile", "lst_serve_replay",
-    "lst_run_event_static", "lst_set_tuning", "lst_get_candidates_batch",
+    "lst_run_event_static", "lst_set_tuning", "lst_get_candidates_batch", "lst_submit_batch", "lst_collect_batch",
 ]
 
 _lib = None
@@ -122,6 +122,8 @@ def load_library(path: str = LIB_PATH):
             "lst_run_event_static": (i32, [P, P, P, u32, C.POINTER(u32), P]),
             "lst_set_tuning": (i32, [P, P]),
             "lst_get_candidates_batch": (i32, [P, P, u32, P, C.c_uint64, P, C.POINTER(C.c_uint64)]),
+            "lst_submit_batch": (i32, [P, P, u32, C.POINTER(C.c_uint64)]),
+            "lst_collect_batch": (i32, [P, C.c_uint64, u32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -154,6 +156,7 @@ class Session:
                  block_size: int = 0, blocks_per_sm: int = 0, profile: bool = False, ls_list_cap: int = 0):
         L = load_library()
         self._mods = np.ascontiguousarray(modules)
+        self._tickets = {}
         assert self._mods.dtype.itemsize == 48
         cfg = lst_config(device, int(keep_objects), use_graph, block_size, blocks_per_sm, int(profile), ls_list_cap)
         h = C.c_void_p()
@@ -187,6 +190,23 @@ class Session:
         arr = (lst_event * len(events))(*[_event_struct(ev, keep) for ev in events])
         ids = (C.c_uint64 * len(events))()
         _check(self.ctx, load_library().lst_run_batch(self.ctx, arr, len(events), ids))
+        return list(ids)
+
+    def submit_batch(self, events) -> int:
+        """Start a batch on one of the two slots; returns a ticket for collect_batch."""
+        keep = []
+        arr = (lst_event * len(events))(*[_event_struct(ev, keep) for ev in events])
+        t = C.c_uint64()
+        _check(self.ctx, load_library().lst_submit_batch(self.ctx, arr, len(events), C.byref(t)))
+        self._tickets[t.value] = len(events)
+        return t.value
+
+    def collect_batch(self, ticket: int, timeout_ms: int = 0):
+        """Wait for a submitted batch; returns its result ids (one per event)."""
+        n = self._tickets.get(ticket, 1)
+        ids = (C.c_uint64 * n)()
+        _check(self.ctx, load_library().lst_collect_batch(self.ctx, ticket, timeout_ms, None, ids))
+        self._tickets.pop(ticket, None)
         return list(ids)
 
     def run_batch_device(self, batch: lst_batch_dev, stream=None):

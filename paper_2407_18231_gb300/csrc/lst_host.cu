@@ -803,12 +803,15 @@ struct Pipeline {
 
   // Enqueue header upload, the kernels and the header read-back (eagerly or as one graph)
   // on stream `on` (null: the pipeline's own stream).
-  void launch(bool use_graph, cudaStream_t on = nullptr) {
+  // after (may be null): an event the chain must wait for (another slot's batch) -- the
+  // inputs already uploaded on this stream are not held back by it
+  void launch(bool use_graph, cudaStream_t on = nullptr, cudaEvent_t after = nullptr) {
     *h_hdr = dev_inputs;
     const GeoView G = geo->view();
     const BufView B = view();
     cudaStream_t st = on ? on : stream;
     cur_stream = st;
+    if (after) CK(cudaStreamWaitEvent(st, after, 0));
     if (profile) {
       prof_name.clear();
       CK(cudaMemcpyAsync(hdr.p, h_hdr, sizeof(Hdr), cudaMemcpyHostToDevice, st));
@@ -1013,6 +1016,14 @@ struct lst_ctx {
   lst_stats stats{};
   uint32_t reruns = 0;
   std::unique_ptr<Workers> getters;  // copies for lst_get_candidates_batch (used under mu only)
+  // lst_submit_batch / lst_collect_batch: two slots, each with its own pipeline
+  struct AsyncSlot {
+    std::unique_ptr<Pipeline> P;
+    uint64_t ticket = 0;  // 0: free
+    uint32_t n_ev = 0;
+  };
+  AsyncSlot slots[2];
+  uint64_t next_ticket = 1;
 };
 
 namespace {
@@ -1291,6 +1302,63 @@ lst_status lst_batch_finish(lst_ctx* c, uint32_t timeout_ms, uint32_t* n_tc_per_
     // on a timeout the batch stays in flight: a later call can wait for it again
     if (!P.wait(timeout_ms)) return fail(c, LST_ERR_TIMEOUT, "device did not finish within the time limit");
     P.pending = false;
+    const Hdr& h = *P.h_hdr_out;
+    if (h.err & ERR_BAD_INPUT)
+      return fail(c, LST_ERR_BAD_INPUT, "bad input: module id out of range, non-finite value or invalid pLS");
+    if (P.grow_after_overflow(h)) {
+      c->reruns++;
+      c->stats.reruns++;
+      const lst_status s = run_packed(c, P, c->cfg.use_graph != 2, timeout_ms);
+      if (s != LST_OK) return s;
+    } else {
+      P.learn(h);
+    }
+    if (n_tc_per_event || outs) collect(c, P, outs, n_tc_per_event);
+    return LST_OK;
+  });
+}
+
+lst_status lst_submit_batch(lst_ctx* c, const lst_event* evs, uint32_t n, uint64_t* ticket) {
+  if (!c || !evs || !ticket || n == 0) return LST_ERR_INVALID_ARG;
+  return guarded(c, [&]() -> lst_status {
+    if (!c->geo.have_map) return fail(c, LST_ERR_NO_MAP, "lst_build_connection_map has not run");
+    int k = -1;
+    for (int i = 0; i < 2 && k < 0; i++)
+      if (c->slots[i].ticket == 0) k = i;
+    if (k < 0) return fail(c, LST_ERR_INVALID_ARG, "both batch slots are in flight (collect one first)");
+    lst_ctx::AsyncSlot& S = c->slots[k];
+    lst_ctx::AsyncSlot& other = c->slots[1 - k];
+    if (!S.P) {
+      S.P.reset(new Pipeline());
+      S.P->init(&c->geo, c->cfg, c->n_sm);
+    }
+    Pipeline& P = *S.P;
+    pack_host_events(P, evs, n);  // inputs uploaded on P's stream now
+    P.ensure_caps(P.estimate(n, P.n_hits, P.n_pls));
+    // the device runs one batch at a time (a batch's working set fills most of the L2):
+    // this chain starts when the other slot's finishes
+    P.launch(c->cfg.use_graph != 2, nullptr, other.ticket ? other.P->done : nullptr);
+    P.pending = true;
+    S.ticket = c->next_ticket++;
+    S.n_ev = n;
+    *ticket = S.ticket;
+    return LST_OK;
+  });
+}
+
+lst_status lst_collect_batch(lst_ctx* c, uint64_t ticket, uint32_t timeout_ms, uint32_t* n_tc_per_event,
+                             lst_result_id* outs) {
+  if (!c || ticket == 0) return LST_ERR_INVALID_ARG;
+  return guarded(c, [&]() -> lst_status {
+    lst_ctx::AsyncSlot* S = nullptr;
+    for (auto& s : c->slots)
+      if (s.ticket == ticket) S = &s;
+    if (!S) return fail(c, LST_ERR_NOT_FOUND, "unknown or already collected batch ticket");
+    Pipeline& P = *S->P;
+    // on a timeout the batch stays in flight: a later call can wait for it again
+    if (!P.wait(timeout_ms)) return fail(c, LST_ERR_TIMEOUT, "device did not finish within the time limit");
+    P.pending = false;
+    S->ticket = 0;
     const Hdr& h = *P.h_hdr_out;
     if (h.err & ERR_BAD_INPUT)
       return fail(c, LST_ERR_BAD_INPUT, "bad input: module id out of range, non-finite value or invalid pLS");

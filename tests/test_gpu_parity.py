@@ -236,6 +236,33 @@ def test_candidates_batch_matches_per_result(built, full_geom):
     s.close()
 
 
+def test_async_batches_match_run_batch(built, full_geom):
+    groups = [[S.make_event("pu200", 40 + 4 * g + i, n_tracks=600 + 200 * i, with_pls=True) for i in range(4)]
+              for g in range(3)]
+    s = lst.Session(full_geom.modules)
+    ref = []
+    for evs in groups:
+        ids = s.run_batch(evs)
+        ref.append([s.candidates(i).tobytes() for i in ids])
+        for i in ids:
+            s.release(i)
+    ta = s.submit_batch(groups[0])
+    tb = s.submit_batch(groups[1])
+    with pytest.raises(lst.LstError) as e:
+        s.submit_batch(groups[2])  # both slots in flight
+    assert e.value.status == -1
+    ids_b = s.collect_batch(tb)  # out of order: b waits for a on the device
+    ids_a = s.collect_batch(ta)
+    assert [s.candidates(i).tobytes() for i in ids_a] == ref[0]
+    assert [s.candidates(i).tobytes() for i in ids_b] == ref[1]
+    with pytest.raises(lst.LstError) as e:
+        s.collect_batch(ta)  # already collected
+    assert e.value.status == -9
+    ids_c = s.collect_batch(s.submit_batch(groups[2]))
+    assert [s.candidates(i).tobytes() for i in ids_c] == ref[2]
+    s.close()
+
+
 def test_repeat_runs_identical(sess_full):
     ev = S.make_event("pu200", 10, with_pls=True)
     a = sess_full.candidates(sess_full.run_event(ev)).tobytes()
