@@ -363,6 +363,8 @@ def main():
     # ---- per-event launch: latency of single events
     per_event = None
     if args.per_event:
+        for i in sess_h.run_batch(batches[0]):  # size the main pipeline for any single event
+            sess_h.release(i)
         lat = []
         for e in events[: args.per_event]:
             t0 = time.perf_counter()

@@ -284,8 +284,9 @@ typedef struct lst_serve_config {
   uint32_t n_slots;          /* concurrent batch slots (streams), >= 1 */
   uint32_t max_batch;        /* events per slot launch, >= 1 */
   uint64_t memory_budget;    /* bytes of device memory all slots may hold, 0 = unbounded */
-  uint32_t share_device;     /* 0: one slot's batch on the device at a time while the others
-                                pack and collect (a batch's working set fills most of the L2);
+  uint32_t share_device;     /* 0: the slots' batches run on the device one after another
+                                (each queued behind the previous launch; a batch's working
+                                set fills most of the L2) while the others pack and collect;
                                 1: the slots' batches run on the device concurrently */
   uint32_t reserved[7];
 } lst_serve_config;

@@ -1564,7 +1564,14 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
     }
     // Shared state: arrived events not yet taken, and the first error of any worker.
     std::mutex qm;
-    std::mutex device_turn;  // held from launch to completion unless the slots share the device
+    // unless the slots share the device, each batch's chain is queued behind the batch
+    // launched before it (an event wait on the device: no host round trip between batches)
+    std::mutex chain_m;
+    cudaEvent_t last_done = nullptr;  // completion event of the last batch launched
+    // batches launched and not yet finished (under qm): a slot takes events only when a
+    // full batch is waiting or at most one batch is in flight, so under load the batches
+    // grow to max_batch instead of launching a few events each while the device is busy
+    uint32_t in_flight = 0;
     const bool share = cfg->share_device != 0;
     std::condition_variable qcv;
     std::deque<uint32_t> queue;
@@ -1595,7 +1602,10 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
           batch.clear();
           {
             std::unique_lock<std::mutex> lk(qm);
-            qcv.wait(lk, [&] { return !queue.empty() || closed || status != LST_OK; });
+            qcv.wait(lk, [&] {
+              return (!queue.empty() && (queue.size() >= cfg->max_batch || in_flight <= 1 || closed)) ||
+                     (queue.empty() && closed) || status != LST_OK;
+            });
             if (status != LST_OK || (queue.empty() && closed)) return;
             uint64_t nh = 0, np = 0;
             while (!queue.empty() && take.size() < cfg->max_batch) {
@@ -1614,6 +1624,10 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
               queue.pop_front();
             }
           }
+          {
+            std::lock_guard<std::mutex> lk(qm);
+            in_flight++;
+          }
           for (uint32_t i : take) batch.push_back(evs[i]);
           pack_host_events(P, batch.data(), (uint32_t)batch.size());
           P.ensure_caps(P.estimate((uint32_t)batch.size(), P.n_hits, P.n_pls));
@@ -1621,12 +1635,14 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
           if (budget && held_by_others(k) + P.dev_bytes > budget && take.size() == 1)
             return set_error(LST_ERR_BUDGET, "one event alone exceeds the memory budget");
           for (int attempt = 0;; attempt++) {
-            {
-              std::unique_lock<std::mutex> turn(device_turn, std::defer_lock);
-              if (!share) turn.lock();
+            if (share) {
               P.launch(true);
-              if (!P.wait(0)) return set_error(LST_ERR_TIMEOUT, "device did not finish");
+            } else {
+              std::lock_guard<std::mutex> lk(chain_m);
+              P.launch(true, nullptr, last_done);
+              last_done = P.done;
             }
+            if (!P.wait(0)) return set_error(LST_ERR_TIMEOUT, "device did not finish");
             const Hdr& h = *P.h_hdr_out;
             if (h.err & ERR_BAD_INPUT) return set_error(LST_ERR_BAD_INPUT, "bad input in a served event");
             if (!P.grow_after_overflow(h)) {
@@ -1640,6 +1656,11 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
             std::lock_guard<std::mutex> lk(c->mu);
             c->reruns++;
           }
+          {
+            std::lock_guard<std::mutex> lk(qm);
+            in_flight--;
+          }
+          qcv.notify_all();
           tcn.assign(take.size(), 0);
           ids.assign(take.size(), 0);
           collect(c, P, outs ? ids.data() : nullptr, tcn.data());
