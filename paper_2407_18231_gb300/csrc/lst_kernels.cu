@@ -1134,72 +1134,80 @@ __device__ __forceinline__ bool pls_surface_point(const MethodConst& C, const Ge
   return true;
 }
 
-// Unit = pLS, one warp: helix parameters, then the modules of barrel layers 1-2 and disks
-// 1-2 its helix crosses first, each with its +-1 neighbours in phi and in row (Sec. 1:
-// pLSs join T3s and T5s).  Lane 3 w + d (w < 4, d < 3) looks up row (crossing row + d - 1)
-// of surface w; the <= 36 ids are sorted by a 64-wide bitonic network in registers and the
-// repeats dropped, which gives the ascending set of distinct ids.
+// pLS preparation (Sec. 1: pLSs join T3s and T5s) in two launches.  k_pls_prep: one thread
+// per (pLS p, r < 12), r = 3 w + d: the helix of p, the point where it first meets surface w
+// (barrel layers 1, 2; the first two disks on its pz side) and the modules of sector k - 1,
+// k, k + 1 (k the sector of that point) in row (crossing row + d - 1), written to slots
+// 3 r .. 3 r + 2 of p's 36 (NONE where there is none); thread r = 0 also stores the helix.
+// k_pls_sort: one warp per pLS sorts the 36 slots and drops repeats, which leaves the
+// ascending set of distinct candidate module ids.
 __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
   Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
-  const uint32_t lane = lane_id();
-  const uint32_t lt = (1u << lane) - 1u;
-  WARP_LOOP(p, n) {
+  THREAD_LOOP(item, 12u * n) {
+    const uint32_t p = item / 12u, r = item - 12u * p;
+    uint32_t* slot = B.pls_cand + (size_t)p * MAX_CAND + 3u * r;
     const PlsIn s = H->pls[p];
-    if (lane == 0) B.pls_ev[p] = find_slot(H->pls_off, H->n_ev, p);
+    if (r == 0) B.pls_ev[p] = find_slot(H->pls_off, H->n_ev, p);
     bool bad = !(isfinite(s.px) && isfinite(s.py) && isfinite(s.pz) && isfinite(s.x0) && isfinite(s.y0) &&
                  isfinite(s.z0)) ||
                (s.charge != 1 && s.charge != -1);
     PlsHelix h;
     h.pt = sqrtf(s.px * s.px + s.py * s.py);
     if (!(h.pt > 0.0f)) bad = true;
-    if (bad) {
-      if (lane == 0) {
-        atomicOr(&H->err, ERR_BAD_INPUT);
-        B.pls_ncand[p] = 0;
-      }
-      continue;
-    }
-    h.R = h.pt / C.KB;
-    const float ux = s.px / h.pt;
-    const float uy = s.py / h.pt;
-    h.q = (float)s.charge;
-    const float qR = h.q * h.R;
-    h.x0 = s.x0; h.y0 = s.y0; h.z0 = s.z0;
-    h.cx = s.x0 + qR * uy;
-    h.cy = s.y0 - qR * ux;
-    h.cot = s.pz / h.pt;
-    if (lane == 0) {
-      B.pls_h0[p] = make_float4(h.x0, h.y0, h.z0, h.R);
-      B.pls_h1[p] = make_float4(h.cx, h.cy, h.cot, h.q);
-      B.pls_pt[p] = h.pt;
-    }
     uint32_t v[3] = {NONE, NONE, NONE};
-    if (lane < 12) {
+    if (bad) {
+      if (r == 0) atomicOr(&H->err, ERR_BAD_INPUT);
+    } else {
+      h.R = h.pt / C.KB;
+      const float ux = s.px / h.pt;
+      const float uy = s.py / h.pt;
+      h.q = (float)s.charge;
+      const float qR = h.q * h.R;
+      h.x0 = s.x0; h.y0 = s.y0; h.z0 = s.z0;
+      h.cx = s.x0 + qR * uy;
+      h.cy = s.y0 - qR * ux;
+      h.cot = s.pz / h.pt;
+      if (r == 0) {
+        B.pls_h0[p] = make_float4(h.x0, h.y0, h.z0, h.R);
+        B.pls_h1[p] = make_float4(h.cx, h.cy, h.cot, h.q);
+        B.pls_pt[p] = h.pt;
+      }
       int sf, irow;
       float Px, Py;
-      if (pls_surface_point(C, G, h, (int)(lane / 3), sf, Px, Py, irow)) {
-        const int row = irow + (int)(lane % 3) - 1;
+      if (pls_surface_point(C, G, h, (int)(r / 3), sf, Px, Py, irow)) {
+        const int row = irow + (int)(r % 3) - 1;
         if (row >= 0 && (uint32_t)row < G.surf_nrows[sf]) {
-          const uint32_t r = G.surf_row_base[sf] + (uint32_t)row;
-          if (G.row_nphi[r] != 0) {
-            const int k = find_sector(G, r, Px, Py);
+          const uint32_t rr = G.surf_row_base[sf] + (uint32_t)row;
+          if (G.row_nphi[rr] != 0) {
+            const int k = find_sector(G, rr, Px, Py);
             if (k >= 0) {
-              const int nphi = (int)G.row_nphi[r];
+              const int nphi = (int)G.row_nphi[rr];
 #pragma unroll
-              for (int d = -1; d <= 1; d++) v[d + 1] = G.row_mods[G.row_mod_base[r] + ((k + d) % nphi + nphi) % nphi];
+              for (int d = -1; d <= 1; d++) v[d + 1] = G.row_mods[G.row_mod_base[rr] + ((k + d) % nphi + nphi) % nphi];
             }
           }
         }
       }
     }
-    // 36 values of lanes 0..11 into 64 slots: slot i in lane i (a) or lane i - 32 (b)
-    const uint32_t t1 = __shfl_sync(FULL, v[1], (lane - 12) & 31);
-    const uint32_t t2 = __shfl_sync(FULL, v[2], (lane - 24) & 31);
-    const uint32_t t3 = __shfl_sync(FULL, v[2], (lane + 8) & 31);
-    uint32_t a = lane < 12 ? v[0] : (lane < 24 ? t1 : t2);
-    uint32_t b = lane < 4 ? t3 : NONE;
+    slot[0] = v[0];
+    slot[1] = v[1];
+    slot[2] = v[2];
+  }
+}
+
+__global__ void k_pls_sort(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->n_pls;
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  WARP_LOOP(p, n) {
+    uint32_t* slots = B.pls_cand + (size_t)p * MAX_CAND;
+    // 36 slots in 64: slot i in lane i (a) or lane i - 32 (b)
+    uint32_t a = slots[lane];
+    uint32_t b = lane < MAX_CAND - 32 ? slots[32 + lane] : NONE;
 #pragma unroll
     for (uint32_t k = 2; k <= 64; k <<= 1) {
 #pragma unroll
@@ -1224,9 +1232,9 @@ __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
     const bool keep_a = a != NONE && (lane == 0 || a != prev_a);
     const bool keep_b = b != NONE && b != prev_b;
     const uint32_t ba = __ballot_sync(FULL, keep_a), bb = __ballot_sync(FULL, keep_b);
-    uint32_t* out = B.pls_cand + (size_t)p * MAX_CAND;
-    if (keep_a) out[__popc(ba & lt)] = a;
-    if (keep_b) out[__popc(ba) + __popc(bb & lt)] = b;
+    // every lane has read its slots (the shuffles above): the sorted ids go in place
+    if (keep_a) slots[__popc(ba & lt)] = a;
+    if (keep_b) slots[__popc(ba) + __popc(bb & lt)] = b;
     if (lane == 0) B.pls_ncand[p] = __popc(ba) + __popc(bb);
   }
 }
@@ -1786,7 +1794,7 @@ const char* const kKernelNames[] = {
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "zero_md_lists", "md_lists_count", "md_lists_fill",
     "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
-    "t3_md_offsets", "t5_md_offsets", "pt3_first_anchor"};
+    "t3_md_offsets", "t5_md_offsets", "pt3_first_anchor", "pls_sort"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Marker {
@@ -1834,8 +1842,10 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   if (side) {  // the pLS preparation needs only the inputs: run it beside the OT chain
     cudaEventRecord(side->fork, s);
     cudaStreamWaitEvent(side->s, side->fork, 0);
-    k_pls_prep<<<g, 128, 0, side->s>>>(C, G, B);
+    k_pls_prep<<<g, 256, 0, side->s>>>(C, G, B);
     mk(15);
+    k_pls_sort<<<g, 128, 0, side->s>>>(B);
+    mk(35);
   }
   k_zero<<<g, 256, 0, s>>>(B.sen_cnt, &H->n_ev, two_nm, 1);
   mk(0);
@@ -1882,8 +1892,10 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   if (side) {
     cudaStreamWaitEvent(s, side->join, 0);
   } else {
-    k_pls_prep<<<g, 128, 0, s>>>(C, G, B);
+    k_pls_prep<<<g, 256, 0, s>>>(C, G, B);
     mk(15);
+    k_pls_sort<<<g, 128, 0, s>>>(B);
+    mk(35);
     k_pt3_first_anchor<<<g, bs, 0, s>>>(C, G, B);
     mk(34);
   }
