@@ -268,15 +268,24 @@ namespace lst {
 // so a residual beyond the window at s = 1.6 chord can never pass: that case is rejected
 // before the arc-length series is evaluated.  Exact: the bound only removes candidates
 // the full test rejects too.
-// The pre-rejection of pls_anchor_accept alone: false only where pls_anchor_accept is false.
-__device__ __forceinline__ bool pls_anchor_maybe(const MethodConst& C, const PlsHelix& h, const PointTol& X) {
+// A cheap filter ahead of pls_anchor_accept: its first test (the r-phi residual against the
+// window at s = 1.6 chord) with the square roots by rsqrtf (at most 2 ulp off) and the
+// division by h.R as a product with inv_r = 1 / h.R; the window is widened by 1e-3 cm plus
+// 2e-6 of the lengths involved, more than those errors and the roundings can move either
+// side, so it keeps every anchor that test keeps.  Its survivors still go through
+// pls_anchor_accept, which alone decides.
+__device__ __forceinline__ bool pls_anchor_maybe_fast(const MethodConst& C, const PlsHelix& h, float inv_r,
+                                                      const PointTol& X) {
   const float ddx = X.p.x - h.x0, ddy = X.p.y - h.y0;
-  const float chord = sqrtf(ddx * ddx + ddy * ddy);
+  const float c2 = ddx * ddx + ddy * ddy;
+  const float chord = c2 > 0.0f ? c2 * rsqrtf(c2) : 0.0f;
   const float ex = X.p.x - h.cx, ey = X.p.y - h.cy;
-  const float dphi = sqrtf(ex * ex + ey * ey) - h.R;
+  const float e2 = ex * ex + ey * ey;
+  const float dist = e2 > 0.0f ? e2 * rsqrtf(e2) : 0.0f;
+  const float dphi = dist - h.R;
   const float smax = 1.6f * chord;
-  const float wmax = (C.W0 + 0.003f * smax + 0.015f * smax * smax / h.R + X.t.y) * 1.001f;
-  return !(fabsf(dphi) > wmax);
+  const float wmax = (C.W0 + 0.003f * smax + 0.015f * smax * smax * inv_r + X.t.y) * 1.001f;
+  return !(fabsf(dphi) > wmax + 1.0e-3f + 2.0e-6f * (dist + h.R + chord));
 }
 
 __device__ __forceinline__ bool pls_anchor_accept(const MethodConst& C, const PlsHelix& h, const PointTol& X) {

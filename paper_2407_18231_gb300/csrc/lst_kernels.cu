@@ -1276,6 +1276,7 @@ __global__ void __launch_bounds__(512) k_pt3_first_anchor(MethodConst C, GeoView
   __shared__ uint32_t pt3_ring[512 / 32][PT3_RING];
   DYN_LOOP(p, &B.hdr->work[W_PT3_FIRST], n, 2) {
     const PlsHelix h = load_helix(B, p);
+    const float inv_r = 1.0f / h.R;
     const uint32_t ubase = B.pls_ev[p] * G.nm;
     const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
     const uint32_t nc = B.pls_ncand[p];
@@ -1312,7 +1313,7 @@ __global__ void __launch_bounds__(512) k_pt3_first_anchor(MethodConst C, GeoView
           const uint32_t co = __shfl_sync(FULL, c, o);
           const uint32_t io = __shfl_sync(FULL, incl, o);
           const uint32_t m = bo + (cc - (io - co));
-          const bool maybe = cc0 < total && pls_anchor_maybe(C, h, md_point(B, m));
+          const bool maybe = cc0 < total && pls_anchor_maybe_fast(C, h, inv_r, md_point(B, m));
           const uint32_t mb = __ballot_sync(FULL, maybe);
           if (maybe) ring[(qt + __popc(mb & lt)) & (PT3_RING - 1)] = m;
           qt += __popc(mb);
