@@ -71,9 +71,12 @@ struct BufView {
   uint32_t cap_ev, cap_hits, cap_md, cap_ls, cap_t3, cap_t5, cap_pls, cap_pt3, cap_pt5, cap_tc;
   // hits
   uint32_t *sen_cnt, *sen_off, *hit_tmp, *hit_ev, *hit_idx;
+  uint32_t *hit_sen;  // per sorted hit: its sensor bucket (event * 2 modules + sensor)
   float4 *hit4;
   // MD
-  uint32_t *md_cnt, *md_off, *md_unit, *md_lo_idx, *md_up_idx;
+  uint32_t *md_hcnt, *md_hoff;  // per sorted hit: MDs with it as the lower hit, their offset
+  uint32_t *md_hmask;          // per sorted lower hit: pass bits of its first 32 candidates
+  uint32_t *md_off, *md_unit, *md_lo_idx, *md_up_idx;
   float4 *md_pt;  // per MD, one 32-byte sector: [2m] lower hit (x, y, z, r), [2m + 1] module tolerances
   float4 *md_up4;
   float4 *md_dir4;  // upper - lower hit: dx, dy, transverse length, rho + rho

@@ -459,6 +459,7 @@ __global__ void k_hits_sort(GeoView G, BufView B) {
     const float x = H->x[h], y = H->y[h], z = H->z[h];
     B.hit4[lo + rank] = make_float4(x, y, z, sqrtf(x * x + y * y));
     B.hit_idx[lo + rank] = h - H->hit_off[e];
+    B.hit_sen[lo + rank] = bkt;
   }
 }
 
@@ -469,125 +470,178 @@ __device__ __forceinline__ bool md_test(const MethodConst& C, const float4& cst,
   return pair_rz(C, a, b) && pair_bend(C, a, b, cst.w);
 }
 
-// One unit per warp with join records; used for groups holding a unit with very many
-// candidate pairs.
-template <bool FILL>
-__device__ __forceinline__ void md_unit_join(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t u,
-                                             WarpAlloc& wa) {
-  const uint32_t lo_b = B.sen_off[2 * u], up_b = B.sen_off[2 * u + 1], up_e = B.sen_off[2 * u + 2];
-  const uint32_t n_lo = up_b - lo_b, n_up = up_e - up_b;
-  const float4 cst = G.modc[u % G.nm];
-  const uint32_t base = FILL ? B.md_off[u] : 0u;
-  const uint32_t n_out = FILL ? B.md_off[u + 1] - base : 0u;
-  const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[0], &B.mask_off[u]};
-  const uint32_t cnt = warp_join<FILL, NoPayload>(
-      n_lo, base, n_out, js, wa, [&](uint32_t, uint32_t& b, uint32_t& c) { b = up_b; c = n_up; },
-      [&](uint32_t i, uint32_t j) { return md_test(C, cst, B.hit4[lo_b + i], B.hit4[j]); },
-      [&](uint32_t, uint32_t, NoPayload&) {},
-      [&](uint32_t pos, uint32_t i, uint32_t j, const NoPayload&) {
-        B.md_unit[pos] = u;
-        B.md_pt[2 * pos] = B.hit4[lo_b + i];
-        B.md_up4[pos] = B.hit4[j];
-        B.md_pt[2 * pos + 1] = cst;
-        B.md_dir4[pos] = md_direction(B.hit4[lo_b + i], B.hit4[j], cst);
-        B.md_lo_idx[pos] = B.hit_idx[lo_b + i];
-        B.md_up_idx[pos] = B.hit_idx[j];
-      });
-  if (!FILL && lane_id() == 0) B.md_cnt[u] = cnt;
+__device__ __forceinline__ void md_emit(const BufView& B, uint32_t pos, uint32_t u, uint32_t ih, uint32_t jh,
+                                        const float4& hl, const float4& hu, const float4& cst) {
+  B.md_unit[pos] = u;
+  B.md_pt[2 * (size_t)pos] = hl;
+  B.md_up4[pos] = hu;
+  B.md_pt[2 * (size_t)pos + 1] = cst;
+  B.md_dir4[pos] = md_direction(hl, hu, cst);
+  B.md_lo_idx[pos] = B.hit_idx[ih];
+  B.md_up_idx[pos] = B.hit_idx[jh];
 }
 
-constexpr uint32_t MD_BIG = 1u << 20;  // candidate pairs above which a unit takes the per-unit join
+constexpr uint32_t MD_BIG = 1u << 26;  // candidates of one lower hit above which it is walked alone
 
-// A module sensor holds a few hits, so a unit has ~10 candidate pairs: one warp takes 32
-// units and walks their concatenated pairs 32 at a time, lower-major inside a unit (the
-// canonical MD order within the unit; every unit writes at its own offset).  A unit's
-// pairs in a chunk are a contiguous lane range, so its passes are popc(ballot & range);
-// the fill pass re-tests (the MD test is a few dozen operations) and ranks each pass by
-// the unit's passes in earlier chunks plus those of lower lanes in this chunk.
-template <bool FILL>
-__global__ void __launch_bounds__(512) k_md(MethodConst C, GeoView G, BufView B) {
+// Items are the positions of the sorted hit array: a lower-sensor hit pairs with every
+// upper-sensor hit of its unit (event, module) (Sec. 1); an upper-sensor hit has none.  The
+// count pass writes each item's passes, and their scan over hit positions orders the MDs
+// unit-major and lower-hit-major within a unit (the canonical order).
+//
+// Count pass: a warp takes 32 items -- slot s owns item s P mod n (P prime, not a divisor of
+// n: a permutation), so the lower hits of the busy inner-layer modules spread over all
+// warps -- and walks their concatenated candidates 32 at a time.  An item's candidates in a
+// chunk are a contiguous lane range, so its passes are popc(ballot & range), and the pass
+// bits of its first 32 candidates are kept for the fill pass.
+__global__ void __launch_bounds__(512) k_md_count(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  const uint32_t nu = H->n_ev * G.nm;
-  const uint32_t ng = (nu + 31) >> 5;
+  const uint32_t n = H->n_hits;
+  const uint32_t ng = (n + 31) >> 5;
   const uint32_t lane = lane_id();
-  const uint32_t lt = (1u << lane) - 1u;
-  // slot s = 32 grp + lane owns unit s P mod nu (P prime, not a divisor of nu: a
-  // permutation), so a group mixes modules and events and the busy inner-layer modules
-  // spread over all warps instead of piling up in a few
-  const uint32_t P = (nu % 1000003u) ? 1000003u : 999983u;
-  WarpAlloc wa;
+  const uint32_t P = (n % 1000003u) ? 1000003u : 999983u;
   WARP_LOOP(grp, ng) {
     const uint32_t slot = grp * 32 + lane;
-    const bool valid = slot < nu;
-    const uint32_t u = valid ? (uint32_t)(((unsigned long long)slot * P) % nu) : 0u;
-    uint32_t lo_b = 0, n_lo = 0, n_up = 0, mod = 0;
+    const bool valid = slot < n;
+    const uint32_t p = valid ? (uint32_t)(((unsigned long long)slot * P) % n) : 0u;
+    uint32_t up_b = 0, c = 0, mod = 0;
     if (valid) {
-      lo_b = B.sen_off[2 * u];
-      const uint32_t up_b = B.sen_off[2 * u + 1], up_e = B.sen_off[2 * u + 2];
-      n_lo = up_b - lo_b;
-      n_up = up_e - up_b;
-      mod = u % G.nm;
-    }
-    const float rcp = n_up ? 1.0f / (float)n_up : 0.0f;
-    const unsigned long long c64 = (unsigned long long)n_lo * n_up;
-    if (__any_sync(FULL, c64 >= MD_BIG)) {
-      for (uint32_t k = 0; k < 32; k++) {
-        const uint32_t uk = __shfl_sync(FULL, u, k);
-        if (grp * 32 + k < nu) md_unit_join<FILL>(C, G, B, uk, wa);
+      const uint32_t sen = B.hit_sen[p];
+      if (!(sen & 1u)) {
+        up_b = B.sen_off[sen + 1];
+        c = B.sen_off[sen + 2] - up_b;
+        mod = (sen >> 1) % G.nm;
       }
+    }
+    if (__any_sync(FULL, c >= MD_BIG)) {  // one item at a time: the chunk sums stay in range
+      for (uint32_t k = 0; k < 32; k++) {
+        const uint32_t ck = __shfl_sync(FULL, c, k);
+        const uint32_t pk = __shfl_sync(FULL, p, k), ubk = __shfl_sync(FULL, up_b, k);
+        const uint32_t modk = __shfl_sync(FULL, mod, k);
+        if (ck == 0) continue;
+        const float4 cst = G.modc[modk];
+        const float4 hl = B.hit4[pk];
+        uint32_t run = 0;
+        for (uint32_t t0 = 0; t0 < ck; t0 += 32) {
+          const uint32_t j = t0 + lane;
+          const float4 hu = B.hit4[ubk + (j < ck ? j : 0u)];
+          const bool pass = j < ck && md_test(C, cst, hl, hu);
+          const uint32_t bal = __ballot_sync(FULL, pass);
+          if (t0 == 0 && lane == 0) B.md_hmask[pk] = bal;
+          run += __popc(bal);
+        }
+        if (lane == 0) B.md_hcnt[pk] = run;
+      }
+      if (valid && c == 0) B.md_hcnt[p] = 0u;
       continue;
     }
-    const uint32_t c = (uint32_t)c64;
     const uint32_t incl = warp_incl_scan(c);
     const uint32_t total = __shfl_sync(FULL, incl, 31);
-    const uint32_t start = incl - c;  // this lane's unit: pairs [start, incl)
-    uint32_t run = 0;                 // passes of this lane's unit so far
-    const uint32_t obase = FILL && valid ? B.md_off[u] : 0u;
+    const uint32_t start = incl - c;  // this lane's item: candidates [start, incl)
+    uint32_t run = 0;                 // passes of this lane's item so far
+    uint32_t bits = 0;                // pass bits of its first 32 candidates
     for (uint32_t t0 = 0; t0 < total; t0 += 32) {
       const uint32_t cand = t0 + lane;
       const uint32_t cc = cand < total ? cand : total - 1;
       const uint32_t o = owner_lane(incl, cc);
       const uint32_t so = __shfl_sync(FULL, start, o);
-      const uint32_t lbo = __shfl_sync(FULL, lo_b, o);
-      const uint32_t nlo = __shfl_sync(FULL, n_lo, o);
-      const uint32_t nup = __shfl_sync(FULL, n_up, o);
-      const float rcpo = __shfl_sync(FULL, rcp, o);
+      const uint32_t po = __shfl_sync(FULL, p, o);
+      const uint32_t ubo = __shfl_sync(FULL, up_b, o);
       const uint32_t mo = __shfl_sync(FULL, mod, o);
-      // q = i nup + j: q < 2^20, so the rounded quotient is off by at most one
-      const uint32_t q = cc - so;
-      uint32_t i = (uint32_t)((float)q * rcpo);
-      if (i * nup > q) i--;
-      else if ((i + 1) * nup <= q) i++;
-      const uint32_t j = q - i * nup;
-      const uint32_t ih = lbo + i, jh = lbo + nlo + j;
-      const uint32_t uo = __shfl_sync(FULL, u, o);
       const float4 cst = G.modc[mo];
-      const float4 hl = B.hit4[ih], hu = B.hit4[jh];
+      const float4 hl = B.hit4[po], hu = B.hit4[ubo + (cc - so)];
       const bool pass = cand < total && md_test(C, cst, hl, hu);
       const uint32_t bal = __ballot_sync(FULL, pass);
-      // this lane's unit's lanes in the chunk: [lo, hi)
+      // this lane's item's lanes in the chunk: [lo, hi), its candidates t0 + lo - start on
       const uint32_t lo = start > t0 ? min(start - t0, 32u) : 0u;
       const uint32_t hi = incl > t0 ? min(incl - t0, 32u) : 0u;
-      const uint32_t mask = hi > lo ? ((hi == 32u ? FULL : (1u << hi) - 1u) & ~((1u << lo) - 1u)) : 0u;
-      if (FILL) {
-        const uint32_t lo_o = __shfl_sync(FULL, lo, o);
-        const uint32_t run_o = __shfl_sync(FULL, run, o);
-        const uint32_t base_o = __shfl_sync(FULL, obase, o);
-        if (pass) {
-          const uint32_t pos = base_o + run_o + __popc(bal & lt & ~((1u << lo_o) - 1u));
-          B.md_unit[pos] = uo;
-          B.md_pt[2 * pos] = hl;
-          B.md_up4[pos] = hu;
-          B.md_pt[2 * pos + 1] = cst;
-          B.md_dir4[pos] = md_direction(hl, hu, cst);
-          B.md_lo_idx[pos] = B.hit_idx[ih];
-          B.md_up_idx[pos] = B.hit_idx[jh];
-        }
+      if (hi > lo) {
+        const uint32_t mine = (bal & (hi == 32u ? FULL : (1u << hi) - 1u)) >> lo;
+        run += __popc(mine);
+        const uint32_t first = t0 + lo - start;
+        if (first < 32u) bits |= mine << first;
       }
-      run += __popc(bal & mask);
     }
-    if (!FILL && valid) B.md_cnt[u] = run;
+    if (valid) {
+      B.md_hcnt[p] = run;
+      if (c) B.md_hmask[p] = bits;
+    }
+  }
+}
+
+// Fill pass in the natural item order, so that a warp's MDs are consecutive and its stores
+// coalesce: a warp takes 32 consecutive items and walks their concatenated passes 32 at a
+// time; a pass is the (k+1)-th set bit of its item's stored bits.  An item with more than 32
+// candidates (stored bits incomplete) re-tests its candidates instead.  Also writes the
+// per-unit MD offsets (the item offset of the unit's first hit).
+__global__ void __launch_bounds__(512) k_md_fill(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->n_hits;
+  {
+    const uint32_t nu = H->n_ev * G.nm;
+    THREAD_LOOP(u, nu + 1) B.md_off[u] = B.md_hoff[B.sen_off[2 * u]];
+  }
+  const uint32_t ng = (n + 31) >> 5;
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  WARP_LOOP(grp, ng) {
+    const uint32_t p = grp * 32 + lane;
+    uint32_t base = 0, np = 0, up_b = 0, c = 0, u = 0, mod = 0, bits = 0;
+    if (p < n) {
+      base = B.md_hoff[p];
+      np = B.md_hoff[p + 1] - base;
+      if (np) {  // a lower hit
+        const uint32_t sen = B.hit_sen[p];
+        up_b = B.sen_off[sen + 1];
+        c = B.sen_off[sen + 2] - up_b;
+        u = sen >> 1;
+        mod = u % G.nm;
+        bits = B.md_hmask[p];
+      }
+    }
+    const bool small = c <= 32u;
+    const uint32_t ns = small ? np : 0u;
+    const uint32_t incl = warp_incl_scan(ns);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t k = cc - (__shfl_sync(FULL, incl, o) - __shfl_sync(FULL, ns, o));
+      uint32_t m = __shfl_sync(FULL, bits, o);
+      const uint32_t po = grp * 32 + o;
+      const uint32_t ubo = __shfl_sync(FULL, up_b, o);
+      const uint32_t uo = __shfl_sync(FULL, u, o);
+      const uint32_t mo = __shfl_sync(FULL, mod, o);
+      const uint32_t bo = __shfl_sync(FULL, base, o);
+      if (cand < total) {
+        for (uint32_t i = 0; i < k; i++) m &= m - 1u;
+        const uint32_t jh = ubo + (uint32_t)(__ffs(m) - 1);
+        const float4 cst = G.modc[mo];
+        md_emit(B, bo + k, uo, po, jh, B.hit4[po], B.hit4[jh], cst);
+      }
+    }
+    // items with more than 32 candidates: re-test, one item at a time
+    for (uint32_t big = __ballot_sync(FULL, np && !small); big; big &= big - 1u) {
+      const uint32_t k = __ffs(big) - 1;
+      const uint32_t ck = __shfl_sync(FULL, c, k), ubk = __shfl_sync(FULL, up_b, k);
+      const uint32_t uk = __shfl_sync(FULL, u, k), modk = __shfl_sync(FULL, mod, k);
+      const uint32_t bk = __shfl_sync(FULL, base, k);
+      const uint32_t pk = grp * 32 + k;
+      const float4 cst = G.modc[modk];
+      const float4 hl = B.hit4[pk];
+      uint32_t run = 0;
+      for (uint32_t t0 = 0; t0 < ck; t0 += 32) {
+        const uint32_t j = t0 + lane;
+        const uint32_t jh = ubk + (j < ck ? j : 0u);
+        const float4 hu = B.hit4[jh];
+        const bool pass = j < ck && md_test(C, cst, hl, hu);
+        const uint32_t bal = __ballot_sync(FULL, pass);
+        if (pass) md_emit(B, bk + run + __popc(bal & lt), uk, pk, jh, hl, hu, cst);
+        run += __popc(bal);
+      }
+    }
   }
 }
 
@@ -1857,10 +1911,10 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   mk(5);
   k_hits_sort<<<g, 256, 0, s>>>(G, B);
   mk(6);
-  k_md<false><<<g, bs, 0, s>>>(C, G, B);
+  k_md_count<<<g, bs, 0, s>>>(C, G, B);
   mk(7);
-  scan(B, L, s, B.md_cnt, B.md_off, &H->n_ev, G.nm, T_MD, B.cap_md, mk);
-  k_md<true><<<g, bs, 0, s>>>(C, G, B);
+  scan(B, L, s, B.md_hcnt, B.md_hoff, &H->n_hits, 1, T_MD, B.cap_md, mk);
+  k_md_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(8);
   if (side) {  // pT3 phase 1 needs the MDs and the pLS preparation only
     cudaEventRecord(side->mds, s);

@@ -72,7 +72,10 @@ size_t carve(char* base, BufView& B) {
   B.hit_ev = c.take<uint32_t>(MAX_HITS);
   B.hit_idx = c.take<uint32_t>(MAX_HITS);
   B.hit4 = c.take<float4>(MAX_HITS);
-  B.md_cnt = c.take<uint32_t>(MAX_MODULES);
+  B.hit_sen = c.take<uint32_t>(MAX_HITS);
+  B.md_hcnt = c.take<uint32_t>(MAX_HITS);
+  B.md_hoff = c.take<uint32_t>(MAX_HITS + 1);
+  B.md_hmask = c.take<uint32_t>(MAX_HITS);
   B.md_off = c.take<uint32_t>(MAX_MODULES + 1);
   B.md_unit = c.take<uint32_t>(MAX_MD);
   B.md_lo_idx = c.take<uint32_t>(MAX_MD);
