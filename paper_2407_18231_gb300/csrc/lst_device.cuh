@@ -41,7 +41,7 @@ struct Hdr {
 };
 
 // Work counters in Hdr::work, one per dynamically scheduled kernel and pass.
-enum WorkCounter : int { W_LS = 0, W_PT3_COUNT, W_PT3_FILL, W_PT5_COUNT, W_PT5_FILL, W_PT3_FIRST, N_WORK };
+enum WorkCounter : int { W_LS = 0, W_PT3_COUNT, W_PT3_FILL, W_PT5_COUNT, W_PT5_FILL, W_PT3_FIRST, W_MD, N_WORK };
 static_assert(N_WORK <= 16, "Hdr::work too small");
 
 // Geometry tables (device pointers) and per-geometry scalars.

@@ -499,11 +499,9 @@ __global__ void __launch_bounds__(512) k_md_count(MethodConst C, GeoView G, BufV
   const uint32_t n = H->n_hits;
   const uint32_t ng = (n + 31) >> 5;
   const uint32_t lane = lane_id();
-  const uint32_t P = (n % 1000003u) ? 1000003u : 999983u;
-  WARP_LOOP(grp, ng) {
-    const uint32_t slot = grp * 32 + lane;
-    const bool valid = slot < n;
-    const uint32_t p = valid ? (uint32_t)(((unsigned long long)slot * P) % n) : 0u;
+  DYN_LOOP(grp, &B.hdr->work[W_MD], ng, 2) {
+    const uint32_t p = grp * 32 + lane;
+    const bool valid = p < n;
     uint32_t up_b = 0, c = 0, mod = 0;
     if (valid) {
       const uint32_t sen = B.hit_sen[p];
