@@ -210,6 +210,42 @@ __device__ __forceinline__ bool warp_any(uint32_t n_outer, OuterFn outer, TestFn
   return false;
 }
 
+// warp_any for groups of S lanes (S a power of two, n_outer <= S): each group answers for
+// its own object, so a warp has 32 / S objects' loads in flight.  A group with active ==
+// false has no candidates.  Uniform across the warp: every lane must call it.
+template <uint32_t S, typename OuterFn, typename TestFn>
+__device__ __forceinline__ bool group_any(bool active, uint32_t n_outer, OuterFn outer, TestFn test) {
+  static_assert(S >= 2 && S <= 32 && (S & (S - 1)) == 0, "group size");
+  const uint32_t r = lane_id() & (S - 1);
+  const uint32_t gmask = S == 32 ? FULL : ((1u << (S & 31u)) - 1u) << (lane_id() & ~(S - 1));
+  uint32_t b = 0, c = 0;
+  if (active && r < n_outer) outer(r, b, c);
+  uint32_t incl = c;
+#pragma unroll
+  for (uint32_t o = 1; o < S; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, incl, o, S);
+    if (r >= o) incl += t;
+  }
+  const uint32_t total = __shfl_sync(FULL, incl, S - 1, S);
+  bool found = false;
+  for (uint32_t t0 = 0; __any_sync(FULL, t0 < total && !found); t0 += S) {
+    const uint32_t cand = t0 + r;
+    const uint32_t cc = cand < total ? cand : (total ? total - 1 : 0u);
+    uint32_t o = 0;
+#pragma unroll
+    for (uint32_t st = S / 2; st >= 1; st >>= 1) {
+      const uint32_t v = __shfl_sync(FULL, incl, o + st - 1, S);
+      if (v <= cc) o += st;
+    }
+    const uint32_t bo = __shfl_sync(FULL, b, o, S);
+    const uint32_t co = __shfl_sync(FULL, c, o, S);
+    const uint32_t io = __shfl_sync(FULL, incl, o, S);
+    const bool hit = !found && cand < total && test(o, bo + (cc - (io - co)));
+    if (__ballot_sync(FULL, hit) & gmask) found = true;
+  }
+  return found;
+}
+
 __device__ __forceinline__ uint32_t find_slot(const uint32_t* off, uint32_t n, uint32_t x) {
   // largest e in [0, n) with off[e] <= x (off non-decreasing, off[0] = 0)
   uint32_t lo = 0, hi = n;
@@ -257,6 +293,15 @@ struct WarpQueue {
          k++)
 #define THREAD_LOOP(i, n) \
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+// One object per group of S lanes; the loop is uniform across the warp (act: this group has
+// an object in this round).
+#define GROUP_LOOP(x, act, n, S)                                                                          \
+  for (uint32_t x##0_ = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / (S)); x##0_ < (n);          \
+       x##0_ += ((gridDim.x * blockDim.x) >> 5) * (32 / (S)))                                             \
+    for (uint32_t x = x##0_ + (lane_id() / (S)), act = x < (n), once_ = 1; once_; once_ = 0)
+// Lanes per object in the duplicate-removal walks (measured: the T5 cross-stage walk gains
+// from several objects per warp, the same-stage walks, with longer lists, do not).
+constexpr uint32_t CROSS_T5_GROUP = 16, KILL_T5_GROUP = 32, KILL_PT5_GROUP = 32;
 
 // ------------------------------------------------------------------ scans
 // Exclusive scan of n = (*nptr) * mul u32 values into out[0..n], out[n] = total; the total
@@ -1568,13 +1613,16 @@ __global__ void k_kill_pt5(BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_PT5];
-  WARP_LOOP(x, n) {
-    const uint32_t p = B.pt5_pls[x];
-    const float sx = B.pt5_score[x];
-    uint32_t mx[5];
-    t5_mds(B, B.pt5_obj[x], mx);
-    const bool dead = warp_any(
-        4u,
+  GROUP_LOOP(x, act, n, KILL_PT5_GROUP) {
+    uint32_t p = 0, mx[5] = {0, 0, 0, 0, 0};
+    float sx = 0.0f;
+    if (act) {
+      p = B.pt5_pls[x];
+      sx = B.pt5_score[x];
+      t5_mds(B, B.pt5_obj[x], mx);
+    }
+    const bool dead = group_any<KILL_PT5_GROUP>(
+        act, 4u,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           if (i == 0) {
             b = B.pt5_off[p];
@@ -1593,7 +1641,7 @@ __global__ void k_kill_pt5(BufView B) {
           t5_mds(B, B.pt5_obj[y], my);
           return shared_mds(mx, my) >= 3;
         });
-    if (lane_id() == 0) B.alive5[x] = dead ? 0u : 1u;
+    if (act && (lane_id() & (KILL_PT5_GROUP - 1)) == 0) B.alive5[x] = dead ? 0u : 1u;
   }
 }
 
@@ -1672,11 +1720,11 @@ __global__ void k_used3(BufView B) {
 __global__ void k_cross_t5(BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  WARP_LOOP(x, H->tot[T_T5]) {
-    uint32_t mx[5];
-    t5_mds(B, x, mx);
-    const bool dead = warp_any(
-        6u,
+  GROUP_LOOP(x, act, H->tot[T_T5], CROSS_T5_GROUP) {
+    uint32_t mx[5] = {0, 0, 0, 0, 0};
+    if (act) t5_mds(B, x, mx);
+    const bool dead = group_any<CROSS_T5_GROUP>(
+        act, 6u,
         [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t m = mx[2 * (i % 3)];
           const uint32_t* off = i < 3 ? B.c5_off : B.c3_off;
@@ -1697,7 +1745,7 @@ __global__ void k_cross_t5(BufView B) {
           t3_mds(B, B.pt3_obj[z], mz);
           return shared_mds(mx, mz) >= 3;
         });
-    if (lane_id() == 0) B.crosst[x] = dead ? 1u : 0u;
+    if (act && (lane_id() & (CROSS_T5_GROUP - 1)) == 0) B.crosst[x] = dead ? 1u : 0u;
   }
 }
 
@@ -1705,14 +1753,17 @@ __global__ void k_cross_t5(BufView B) {
 __global__ void k_kill_t5(BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  WARP_LOOP(x, H->tot[T_T5]) {
-    bool dead = B.crosst[x] != 0;
-    if (!dead) {
-      const float sx = B.t5_score[x];
-      uint32_t mx[5];
-      t5_mds(B, x, mx);
-      dead = warp_any(
-          3u,
+  GROUP_LOOP(x, act, H->tot[T_T5], KILL_T5_GROUP) {
+    bool dead = act && B.crosst[x] != 0;
+    {
+      float sx = 0.0f;
+      uint32_t mx[5] = {0, 0, 0, 0, 0};
+      if (act && !dead) {
+        sx = B.t5_score[x];
+        t5_mds(B, x, mx);
+      }
+      dead = group_any<KILL_T5_GROUP>(
+          act && !dead, 3u,
           [&](uint32_t i, uint32_t& b, uint32_t& c) {
             const uint32_t m = mx[2 * i];
             b = B.ct_off[m];
@@ -1724,9 +1775,9 @@ __global__ void k_kill_t5(BufView B) {
             uint32_t my[5];
             t5_mds(B, y, my);
             return shared_mds(mx, my) >= 3;
-          });
+          }) || dead;
     }
-    if (lane_id() == 0) B.alivet[x] = dead ? 0u : 1u;
+    if (act && (lane_id() & (KILL_T5_GROUP - 1)) == 0) B.alivet[x] = dead ? 0u : 1u;
   }
 }
 
