@@ -766,6 +766,49 @@ __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& 
   if (!FILL && lane_id() == 0) B.ls_cnt[a] = cnt;
 }
 
+// LS fill pass, flat over anchor MDs in their order, so that a warp's LSs are consecutive
+// and its stores coalesce: a warp takes 32 consecutive anchors and walks their
+// concatenated partner lists (stored by the count pass) 32 LSs at a time.  An anchor whose
+// list the count pass could not store (arena full, or a neighbour list beyond the shared
+// memory) is joined again on its own.
+__global__ void __launch_bounds__(512) k_ls_fill(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_MD];
+  const uint32_t lane = lane_id();
+  WarpAlloc wa;
+  WARP_LOOP(grp, (n + 31) >> 5) {
+    const uint32_t a = grp * 32 + lane;
+    uint32_t base = 0, cnt = 0, mb = NONE;
+    if (a < n) {
+      base = B.ls_off[a];
+      cnt = B.ls_off[a + 1] - base;
+      if (cnt) mb = B.mask_off[a];
+    }
+    const uint32_t ns = mb != NONE ? cnt : 0u;
+    const uint32_t incl = warp_incl_scan(ns);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t k = cc - (__shfl_sync(FULL, incl, o) - __shfl_sync(FULL, ns, o));
+      const uint32_t bo = __shfl_sync(FULL, base, o);
+      const uint32_t mo = __shfl_sync(FULL, mb, o);
+      if (cand < total) {
+        B.ls_in[bo + k] = grp * 32 + o;
+        B.ls_out[bo + k] = B.mask[mo + 1 + k];
+      }
+    }
+    for (uint32_t re = __ballot_sync(FULL, cnt && mb == NONE); re; re &= re - 1u) {
+      const uint32_t ak = grp * 32 + __ffs(re) - 1;
+      const uint32_t u = B.md_unit[ak];
+      const uint32_t ev = u / G.nm;
+      ls_md_join<true>(C, G, B, ak, ev, u - ev * G.nm, wa);
+    }
+  }
+}
+
 constexpr uint32_t LS_LIST_CAP = 512;  // flattened neighbour MDs per warp in shared memory
 constexpr uint32_t LS_ANCHORS = 8;     // MDs of a module tested per walk over its list
 constexpr uint32_t LS_RING = 64;       // ring of queued (list position, anchor) entries (> 31 + 32)
@@ -1977,7 +2020,7 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   k_ls<false><<<g, bs, ls_smem, s>>>(C, G, B, lcap);
   mk(9);
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
-  k_ls<true><<<g, bs, ls_smem, s>>>(C, G, B, lcap);
+  k_ls_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(10);
   k_t3<false><<<g, 256, 0, s>>>(C, G, B);
   mk(11);
