@@ -210,6 +210,111 @@ __device__ __forceinline__ bool warp_any(uint32_t n_outer, OuterFn outer, TestFn
   return false;
 }
 
+// Count pass of a join whose fill pass only copies: the passing candidates' inner indices
+// and scores (score(i, j, payload), the fill pass's arithmetic) are staged in candidate
+// order in this warp's `stage` (2 LIST_CAP words of dynamic shared memory), then stored as
+// [j, score bits] pairs in `mask` through the warp's bump allocator.  More than LIST_CAP
+// passes, or a full scratch, store NONE: the fill pass then re-runs the join for that unit.
+constexpr uint32_t LIST_CAP = 256;
+template <typename OuterFn, typename TestFn, typename ScoreFn>
+__device__ __forceinline__ uint32_t warp_count_list(uint32_t n_outer, uint32_t* stage, const JoinScratch& js,
+                                                    WarpAlloc& wa, OuterFn outer, TestFn test, ScoreFn score) {
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t count = 0;
+  for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
+    uint32_t b = 0, c = 0;
+    if (g0 + lane < n_outer) outer(g0 + lane, b, c);
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t bo = __shfl_sync(FULL, b, o);
+      const uint32_t co = __shfl_sync(FULL, c, o);
+      const uint32_t io = __shfl_sync(FULL, incl, o);
+      const uint32_t j = bo + (cc - (io - co));
+      const bool pass = cand < total && test(g0 + o, j);
+      const uint32_t bal = __ballot_sync(FULL, pass);
+      const uint32_t r = count + __popc(bal & lt);
+      if (pass && r < LIST_CAP) {
+        ScorePayload pl;
+        score(g0 + o, j, pl);
+        stage[2 * r] = j;
+        stage[2 * r + 1] = __float_as_uint(pl.score);
+      }
+      count += __popc(bal);
+    }
+  }
+  __syncwarp();
+  uint32_t mbase = NONE;
+  if (count > 0 && count <= LIST_CAP) {
+    const uint32_t need = 2 * count;
+    uint32_t mb = NONE;
+    if (lane == 0) {
+      if (wa.end - wa.cur < need || wa.cur == NONE) {
+        const uint32_t b0 = atomicAdd(js.used, 1024u);
+        if (b0 < js.cap && 1024u <= js.cap - b0) {
+          wa.cur = b0;
+          wa.end = b0 + 1024u;
+        } else {
+          wa.cur = wa.end = 0;
+        }
+      }
+      if (wa.end - wa.cur >= need) {
+        mb = wa.cur;
+        wa.cur += need;
+      }
+    }
+    mbase = __shfl_sync(FULL, mb, 0);
+    wa.cur = __shfl_sync(FULL, wa.cur, 0);
+    wa.end = __shfl_sync(FULL, wa.end, 0);
+    if (mbase != NONE)
+      for (uint32_t i = lane; i < need; i += 32) js.mask[mbase + i] = stage[i];
+  }
+  __syncwarp();  // the stage is reused by the next unit
+  if (lane == 0) *js.unit_base = mbase;
+  return count;
+}
+
+// Fill pass of such a join, flat over the units in order so that a warp's outputs are
+// consecutive and its stores coalesce: a warp takes 32 consecutive units and walks their
+// concatenated stored lists; a unit without one (NONE) calls retest(unit).
+template <typename RetestFn>
+__device__ __forceinline__ void list_fill(uint32_t n, const uint32_t* off, const uint32_t* mask,
+                                          const uint32_t* mask_off, uint32_t* out_unit, uint32_t* out_obj,
+                                          float* out_score, RetestFn retest) {
+  const uint32_t lane = lane_id();
+  const uint32_t ng = (n + 31) >> 5;
+  for (uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; grp < ng; grp += (gridDim.x * blockDim.x) >> 5) {
+    const uint32_t p = grp * 32 + lane;
+    uint32_t base = 0, cnt = 0, mb = NONE;
+    if (p < n) {
+      base = off[p];
+      cnt = off[p + 1] - base;
+      if (cnt) mb = mask_off[p];
+    }
+    const uint32_t ns = mb != NONE ? cnt : 0u;
+    const uint32_t incl = warp_incl_scan(ns);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t k = cc - (__shfl_sync(FULL, incl, o) - __shfl_sync(FULL, ns, o));
+      const uint32_t bo = __shfl_sync(FULL, base, o);
+      const uint32_t mo = __shfl_sync(FULL, mb, o);
+      if (cand < total) {
+        out_unit[bo + k] = grp * 32 + o;
+        out_obj[bo + k] = mask[mo + 2 * k];
+        out_score[bo + k] = __uint_as_float(mask[mo + 2 * k + 1]);
+      }
+    }
+    for (uint32_t re = __ballot_sync(FULL, cnt && mb == NONE); re; re &= re - 1u) retest(grp * 32 + __ffs(re) - 1);
+  }
+}
+
 // warp_any for groups of S lanes (S a power of two, n_outer <= S): each group answers for
 // its own object, so a warp has 32 / S objects' loads in flight.  A group with active ==
 // false has no candidates.  Uniform across the warp: every lane must call it.
@@ -816,12 +921,11 @@ constexpr uint32_t LS_RING = 64;       // ring of queued (list position, anchor)
 // the anchors (lower hit, tolerances, direction terms: three float4 each)
 constexpr uint32_t LS_EXTRA_WORDS = LS_RING + LS_ANCHORS * LS_LIST_CAP / 32 + LS_ANCHORS * 12;
 
-// Unit = (event, module A).  The warp writes the indices of all MDs on the modules connected
-// to A into a shared-memory list once (module order, then MD order), then walks the list in
-// 32-wide chunks for every MD a of A: no per-MD neighbour lookups, no per-chunk search.  The
-// count pass keeps each row's passing chunks as records (t0, ballot) for the fill pass.
-template <bool FILL>
-__global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B, uint32_t list_cap) {
+// LS count pass.  Unit = (event, module A).  The warp writes the indices of all MDs on the
+// modules connected to A into a shared-memory list once (module order, then MD order), then
+// walks the list for the MDs a of A: no per-MD neighbour lookups, no per-chunk search.  It
+// stores each anchor's partner list (for k_ls_fill to copy) and its count.
+__global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufView B, uint32_t list_cap) {
   extern __shared__ uint32_t ls_smem[];
   const Hdr* H = B.hdr;
   if (H->err) return;
@@ -838,24 +942,6 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
   auto unit = [&](const uint32_t u) {
     const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
     if (a0 == a1) return;
-    if (FILL) {
-      if (B.ls_off[a0] == B.ls_off[a1]) return;  // no LS starts on this module
-      // every row with LS has its partner list: copy, no neighbour list needed
-      bool retest = false;
-      for (uint32_t a = a0 + lane; a < a1; a += 32)
-        retest |= B.ls_off[a + 1] != B.ls_off[a] && B.mask_off[a] == NONE;
-      if (!__any_sync(FULL, retest)) {
-        for (uint32_t a = a0; a < a1; a++) {
-          const uint32_t base = B.ls_off[a], n_out = B.ls_off[a + 1] - base;
-          const uint32_t mbase = B.mask_off[a];
-          for (uint32_t i = lane; i < n_out; i += 32) {
-            B.ls_in[base + i] = a;
-            B.ls_out[base + i] = B.mask[mbase + 1 + i];
-          }
-        }
-        return;
-      }
-    }
     const uint32_t ev = u / G.nm, A = u - ev * G.nm;
     const uint32_t ubase = ev * G.nm;
     const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
@@ -867,77 +953,44 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
     for (uint32_t g0 = 0; g0 < nb; g0 += 32) {
       uint32_t b = 0, c = 0;
       bool disk = false;
-      if (!FILL && g0 + lane < nb) {
+      if (g0 + lane < nb) {
         const uint32_t Bm = G.conn[nb0 + g0 + lane];
         const uint32_t uu = ubase + Bm;
         b = B.md_off[uu];
         c = B.md_off[uu + 1] - b;
         disk = G.subdet[Bm] == 1;
-      } else if (FILL && g0 + lane < nb) {
-        const uint32_t uu = ubase + G.conn[nb0 + g0 + lane];
-        b = B.md_off[uu];
-        c = B.md_off[uu + 1] - b;
       }
       const uint32_t incl = warp_incl_scan(c);
       const uint32_t o = len + incl - c;
       for (uint32_t k = 0; k < c; k++)
         if (o + k < list_cap) list[o + k] = b + k;
-      if (!FILL) {
-        const uint32_t dm = __ballot_sync(FULL, disk && c > 0), bm = __ballot_sync(FULL, !disk && c > 0);
-        if (t_disk != NONE) {
-          if (bm) suffix = false;
-        } else if (dm) {
-          const uint32_t fd = __ffs(dm) - 1;
-          if (fd < 31 && (bm >> (fd + 1))) suffix = false;
-          t_disk = __shfl_sync(FULL, o, fd);
-        }
+      const uint32_t dm = __ballot_sync(FULL, disk && c > 0), bm = __ballot_sync(FULL, !disk && c > 0);
+      if (t_disk != NONE) {
+        if (bm) suffix = false;
+      } else if (dm) {
+        const uint32_t fd = __ffs(dm) - 1;
+        if (fd < 31 && (bm >> (fd + 1))) suffix = false;
+        t_disk = __shfl_sync(FULL, o, fd);
       }
       len += __shfl_sync(FULL, incl, 31);
     }
     if (t_disk == NONE) t_disk = len;
     __syncwarp();
-    if (!FILL) n_cand += (unsigned long long)len * (a1 - a0);
+    n_cand += (unsigned long long)len * (a1 - a0);
     if (len == 0) {  // no neighbour MDs: no LS (and no shared memory touched)
-      if (!FILL)
-        for (uint32_t a = a0 + lane; a < a1; a += 32) {
-          B.ls_cnt[a] = 0;
-          B.mask_off[a] = NONE;
-        }
+      for (uint32_t a = a0 + lane; a < a1; a += 32) {
+        B.ls_cnt[a] = 0;
+        B.mask_off[a] = NONE;
+      }
       return;
     }
     if (len > list_cap) {
-      for (uint32_t a = a0; a < a1; a++) ls_md_join<FILL>(C, G, B, a, ev, A, wa);
+      for (uint32_t a = a0; a < a1; a++) ls_md_join<false>(C, G, B, a, ev, A, wa);
       return;
     }
     const float rnext = G.rnext[A];
     const bool a_barrel = G.subdet[A] == 0;
-    if (FILL) {
-      for (uint32_t a = a0; a < a1; a++) {
-        const uint32_t base = B.ls_off[a], n_out = B.ls_off[a + 1] - base;
-        if (n_out == 0) continue;
-        const uint32_t mbase = B.mask_off[a];
-        if (mbase != NONE) {
-          for (uint32_t i = lane; i < n_out; i += 32) {
-            B.ls_in[base + i] = a;
-            B.ls_out[base + i] = B.mask[mbase + 1 + i];
-          }
-        } else {
-          const PointTol pa = md_point(B, a);
-          const float4 da = B.md_dir4[a];
-          uint32_t count = 0;
-          for (uint32_t t0 = 0; t0 < len; t0 += 32) {
-            const bool pass = t0 + lane < len && ls_test(C, G, B, pa, da, rnext, a_barrel, ubase, list[t0 + lane]);
-            const uint32_t bal = __ballot_sync(FULL, pass);
-            if (pass) {
-              const uint32_t pos = base + count + __popc(bal & lt);
-              B.ls_in[pos] = a;
-              B.ls_out[pos] = list[t0 + lane];
-            }
-            count += __popc(bal);
-          }
-        }
-      }
-    } else {
+    {
       // Up to LS_ANCHORS MDs of A per walk over the list: their points are staged in shared
       // memory (read as broadcasts) and each candidate loaded is tested against all of
       // them, each anchor with its own pass bits; the head's survivors are queued as
@@ -1026,17 +1079,11 @@ __global__ void __launch_bounds__(512) k_ls(MethodConst C, GeoView G, BufView B,
       }
     }
     __syncwarp();  // the list is rewritten by the next unit
-  
   };
-  if (FILL) {
-    // the fill pass replays records: cheap per unit, the static split balances it
-    WARP_LOOP(u, nu) unit(u);
-  } else {
-    // module-major order (unit k = module k / n_ev of event k % n_ev) taken dynamically:
-    // module ids start with the innermost, busiest layers, so expensive units go first
-    DYN_LOOP(k, &B.hdr->work[W_LS], nu, 2) unit((k % n_ev) * G.nm + k / n_ev);
-  }
-  if (!FILL && lane == 0 && n_cand) atomicAdd(&B.hdr->ls_cand, n_cand);
+  // module-major order (unit k = module k / n_ev of event k % n_ev) taken dynamically:
+  // module ids start with the innermost, busiest layers, so expensive units go first
+  DYN_LOOP(k, &B.hdr->work[W_LS], nu, 2) unit((k % n_ev) * G.nm + k / n_ev);
+  if (lane == 0 && n_cand) atomicAdd(&B.hdr->ls_cand, n_cand);
 }
 
 // ------------------------------------------------------------------ T3
@@ -1479,14 +1526,12 @@ __global__ void __launch_bounds__(512) k_pt3_first_anchor(MethodConst C, GeoView
 // set equals "T3s whose first MD is on a candidate module, all three anchors inside the
 // windows" and comes out in T3 order.  More than PLS_MD_CAP passing MDs: the pLS falls back
 // to walking every T3 of its candidate modules.
+// The count pass keeps each pLS's (T3, score) list; the fill pass copies it (list_fill)
+// and re-runs the join only for a pLS without one.
 template <bool FILL>
-__global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B) {
-  const Hdr* H = B.hdr;
-  if (H->err) return;
-  const uint32_t n = H->n_pls;
-  const uint32_t lane = lane_id();
-  WarpAlloc wa;
-  DYN_LOOP(p, &B.hdr->work[FILL ? W_PT3_FILL : W_PT3_COUNT], n, 2) {
+__device__ __forceinline__ void pt3_unit(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t p,
+                                         WarpAlloc& wa, uint32_t* stage) {
+  {
     const PlsHelix h = load_helix(B, p);
     const uint32_t ubase = B.pls_ev[p] * G.nm;
     const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
@@ -1495,7 +1540,8 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
     const uint32_t npass = B.pls_nmdpass[p];  // from k_pt3_first_anchor
     const uint32_t base = FILL ? B.pt3_off[p] : 0u;
     const uint32_t n_out = FILL ? B.pt3_off[p + 1] - base : 0u;
-    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[4], &B.mask_off[p]};
+    uint32_t no_list = NONE;  // the fill pass runs only for a pLS without a stored list
+    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[4], FILL ? &no_list : &B.mask_off[p]};
     auto score3 = [&](uint32_t, uint32_t t, ScorePayload& pl) {
       float score = 0.0f;
       pls_anchor(C, h, md_point(B, B.t3_a[t]), score);
@@ -1508,10 +1554,14 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
       B.pt3_obj[pos] = t;
       B.pt3_score[pos] = pl.score;
     };
+    auto join = [&](uint32_t n_outer, auto outer, auto test) {
+      if (FILL) return warp_join<true, ScorePayload>(n_outer, base, n_out, js, wa, outer, test, score3, emit3);
+      return warp_count_list(n_outer, stage, js, wa, outer, test, score3);
+    };
     uint32_t cnt;
     if (npass != NONE) {
-      cnt = warp_join<FILL, ScorePayload>(
-          npass, base, n_out, js, wa,
+      cnt = join(
+          npass,
           [&](uint32_t i, uint32_t& b, uint32_t& c) {
             const uint32_t m = mlist[i];
             b = B.t3_off[m];
@@ -1519,11 +1569,10 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
           },
           [&](uint32_t, uint32_t t) {
             return pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
-          },
-          score3, emit3);
+          });
     } else {
-      cnt = warp_join<FILL, ScorePayload>(
-          nc, base, n_out, js, wa,
+      cnt = join(
+          nc,
           [&](uint32_t i, uint32_t& b, uint32_t& c) {
             const uint32_t u = ubase + cand[i];
             b = B.t3_off[B.md_off[u]];
@@ -1532,48 +1581,61 @@ __global__ void __launch_bounds__(512) k_pt3(MethodConst C, GeoView G, BufView B
           [&](uint32_t, uint32_t t) {
             return pls_anchor_accept(C, h, md_point(B, B.t3_a[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) &&
                    pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
-          },
-          score3, emit3);
+          });
     }
-    if (!FILL && lane == 0) B.pt3_cnt[p] = cnt;
+    if (!FILL && lane_id() == 0) B.pt3_cnt[p] = cnt;
   }
+}
+
+__global__ void __launch_bounds__(512) k_pt3_count(MethodConst C, GeoView G, BufView B) {
+  extern __shared__ uint32_t stage[];
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  WarpAlloc wa;
+  DYN_LOOP(p, &B.hdr->work[W_PT3_COUNT], H->n_pls, 2) pt3_unit<false>(C, G, B, p, wa, stage + (threadIdx.x >> 5) * 2 * LIST_CAP);
+}
+
+__global__ void __launch_bounds__(512) k_pt3_fill(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  WarpAlloc wa;
+  list_fill(H->n_pls, B.pt3_off, B.mask, B.mask_off, B.pt3_pls, B.pt3_obj, B.pt3_score,
+            [&](uint32_t p) { pt3_unit<true>(C, G, B, p, wa, nullptr); });
 }
 
 // pT5 (Sec. 1: pLS + T5).  A pT5 tests the same windows on anchors a, b, c as the pT3 of the
 // T5's first T3 (a, b, c), so its candidates are exactly the T5s built on the pT3s of p
 // (t5_toff per T3); the other two anchors and the curvature decide.  Unit = pLS p.
+// The count pass keeps each pLS's (T5, score) list; the fill pass copies it (list_fill)
+// and re-runs the join only for a pLS without one.
 template <bool FILL>
-__global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B) {
-  const Hdr* H = B.hdr;
-  if (H->err) return;
-  const uint32_t n = H->n_pls;
-  WarpAlloc wa;
-  DYN_LOOP(p, &B.hdr->work[FILL ? W_PT5_FILL : W_PT5_COUNT], n, 2) {
+__device__ __forceinline__ void pt5_unit(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t p,
+                                         WarpAlloc& wa, uint32_t* stage) {
+  {
     const uint32_t x0 = B.pt3_off[p], nx = B.pt3_off[p + 1] - x0;
     if (nx == 0) {
       if (!FILL && lane_id() == 0) B.pt5_cnt[p] = 0;
-      continue;
+      return;
     }
     const PlsHelix h = load_helix(B, p);
     const uint32_t base = FILL ? B.pt5_off[p] : 0u;
     const uint32_t n_out = FILL ? B.pt5_off[p + 1] - base : 0u;
-    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[5], &B.mask_off[p]};
-    const uint32_t cnt = warp_join<FILL, ScorePayload>(
-        nx, base, n_out, js, wa,
-        [&](uint32_t i, uint32_t& b, uint32_t& c) {
+    uint32_t no_list = NONE;  // the fill pass runs only for a pLS without a stored list
+    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[5], FILL ? &no_list : &B.mask_off[p]};
+    auto outer = [&](uint32_t i, uint32_t& b, uint32_t& c) {
           const uint32_t t = B.pt3_obj[x0 + i];
           b = B.t5_toff[t];
           c = B.t5_toff[t + 1] - b;
-        },
-        [&](uint32_t, uint32_t t) {
+        };
+    auto test = [&](uint32_t, uint32_t t) {
           uint32_t m[5];
           t5_mds(B, t, m);
           if (!pls_anchor_accept(C, h, md_point(B, m[3]))) return false;
           if (!pls_anchor_accept(C, h, md_point(B, m[4]))) return false;
           const Circle3 fu = circle3(md_point(B, m[0]), md_point(B, m[2]), md_point(B, m[4]));
           return fabsf(fabsf(B.t5_kfull[t]) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
-        },
-        [&](uint32_t i, uint32_t t, ScorePayload& pl) {
+        };
+    auto score5 = [&](uint32_t i, uint32_t t, ScorePayload& pl) {
           // anchors m0, m1, m2 are the parent pT3's a, b, c, summed in the same order: its
           // score is this sum after three terms, bit for bit
           float score = B.pt3_score[x0 + i];
@@ -1581,14 +1643,32 @@ __global__ void __launch_bounds__(512) k_pt5(MethodConst C, GeoView G, BufView B
           pls_anchor(C, h, md_point(B, m0123.w), score);
           pls_anchor(C, h, md_point(B, B.t5_md8[2 * (size_t)t + 1].x), score);
           pl.score = score;
-        },
-        [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
+        };
+    auto emit5 = [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
           B.pt5_pls[pos] = p;
           B.pt5_obj[pos] = t;
           B.pt5_score[pos] = pl.score;
-        });
+        };
+    const uint32_t cnt = FILL ? warp_join<true, ScorePayload>(nx, base, n_out, js, wa, outer, test, score5, emit5)
+                              : warp_count_list(nx, stage, js, wa, outer, test, score5);
     if (!FILL && lane_id() == 0) B.pt5_cnt[p] = cnt;
   }
+}
+
+__global__ void __launch_bounds__(512) k_pt5_count(MethodConst C, GeoView G, BufView B) {
+  extern __shared__ uint32_t stage[];
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  WarpAlloc wa;
+  DYN_LOOP(p, &B.hdr->work[W_PT5_COUNT], H->n_pls, 2) pt5_unit<false>(C, G, B, p, wa, stage + (threadIdx.x >> 5) * 2 * LIST_CAP);
+}
+
+__global__ void __launch_bounds__(512) k_pt5_fill(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  WarpAlloc wa;
+  list_fill(H->n_pls, B.pt5_off, B.mask, B.mask_off, B.pt5_pls, B.pt5_obj, B.pt5_score,
+            [&](uint32_t p) { pt5_unit<true>(C, G, B, p, wa, nullptr); });
 }
 
 // ------------------------------------------------------------------ duplicate removal
@@ -1969,12 +2049,14 @@ static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const 
   mk(4);
 }
 
-// Lets the LS kernels take the shared memory of the largest block (512 threads) on the
-// current device; called once per pipeline, outside any stream capture.
+// Lets the LS, pT3 and pT5 count kernels take the shared memory of the largest block (512
+// threads) on the current device; called once per pipeline, outside any stream capture.
 cudaError_t configure_kernels() {
   const int bytes = (int)((512 / 32) * (LS_LIST_CAP + LS_EXTRA_WORDS) * sizeof(uint32_t));
-  cudaError_t e = cudaFuncSetAttribute(k_ls<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ls<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_ls_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const int lbytes = (int)((512 / 32) * 2 * LIST_CAP * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pt3_count, cudaFuncAttributeMaxDynamicSharedMemorySize, lbytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pt5_count, cudaFuncAttributeMaxDynamicSharedMemorySize, lbytes);
   return e;
 }
 
@@ -2016,8 +2098,9 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     cudaEventRecord(side->join, side->s);
   }
   const uint32_t lcap = L.ls_list_cap;
+  const size_t list_smem = (bs / 32) * 2 * LIST_CAP * sizeof(uint32_t);
   const size_t ls_smem = lcap ? (bs / 32) * (lcap + LS_EXTRA_WORDS) * sizeof(uint32_t) : 0;
-  k_ls<false><<<g, bs, ls_smem, s>>>(C, G, B, lcap);
+  k_ls_count<<<g, bs, ls_smem, s>>>(C, G, B, lcap);
   mk(9);
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
   k_ls_fill<<<g, bs, 0, s>>>(C, G, B);
@@ -2046,15 +2129,15 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     k_pt3_first_anchor<<<g, bs, 0, s>>>(C, G, B);
     mk(34);
   }
-  k_pt3<false><<<g, bs, 0, s>>>(C, G, B);
+  k_pt3_count<<<g, bs, list_smem, s>>>(C, G, B);
   mk(16);
   scan(B, L, s, B.pt3_cnt, B.pt3_off, &H->n_pls, 1, T_PT3, B.cap_pt3, mk);
-  k_pt3<true><<<g, bs, 0, s>>>(C, G, B);
+  k_pt3_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(17);
-  k_pt5<false><<<g, bs, 0, s>>>(C, G, B);
+  k_pt5_count<<<g, bs, list_smem, s>>>(C, G, B);
   mk(18);
   scan(B, L, s, B.pt5_cnt, B.pt5_off, &H->n_pls, 1, T_PT5, B.cap_pt5, mk);
-  k_pt5<true><<<g, bs, 0, s>>>(C, G, B);
+  k_pt5_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(19);
   k_zero3<<<g, 256, 0, s>>>(B.c5_cnt, B.c3_cnt, B.ct_cnt, H);
   mk(20);
