@@ -41,7 +41,7 @@ struct Hdr {
 };
 
 // Work counters in Hdr::work, one per dynamically scheduled kernel and pass.
-enum WorkCounter : int { W_LS = 0, W_PT3_COUNT, W_PT3_FILL, W_PT5_COUNT, W_PT5_FILL, W_PT3_FIRST, W_MD, N_WORK };
+enum WorkCounter : int { W_LS = 0, W_PT3_COUNT, W_PT5_COUNT, W_PT3_FIRST, W_MD, N_WORK };
 static_assert(N_WORK <= 16, "Hdr::work too small");
 
 // Geometry tables (device pointers) and per-geometry scalars.
@@ -99,7 +99,8 @@ struct BufView {
   // pT3 / pT5
   uint32_t *pt3_cnt, *pt3_off, *pt3_pls, *pt3_obj;
   float *pt3_score;
-  uint32_t *pt5_cnt, *pt5_off, *pt5_pls, *pt5_obj;
+  uint32_t *pt5_xcnt, *pt5_xoff, *pt5_xmask;  // per pT3: pT5s on it, their offset, pass bits
+  uint32_t *pt5_off, *pt5_pls, *pt5_obj;
   float *pt5_score;
   // duplicate removal: MD -> object lists and flags (u32 so they can be scanned)
   uint32_t *c5_cnt, *c5_off, *c5_list, *c3_cnt, *c3_off, *c3_list, *ct_cnt, *ct_off, *ct_list;

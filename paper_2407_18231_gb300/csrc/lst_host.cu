@@ -482,7 +482,7 @@ struct Pipeline {
   DevBuf t5_tcnt, t5_toff, t5_off, t5_m[5], t5_score, t5_kfull, t5_mask, t5_md8;
   DevBuf pls_ev, pls_ncand, pls_cand, pls_h0, pls_h1, pls_pt, pls_mdpass, pls_nmdpass;
   DevBuf pt3_cnt, pt3_off, pt3_pls, pt3_obj, pt3_score;
-  DevBuf pt5_cnt, pt5_off, pt5_pls, pt5_obj, pt5_score;
+  DevBuf pt5_xcnt, pt5_xoff, pt5_xmask, pt5_off, pt5_pls, pt5_obj, pt5_score;
   DevBuf c5_cnt, c5_off, c5_list, c3_cnt, c3_off, c3_list, ct_cnt, ct_off, ct_list;
   DevBuf alive5, alive3, alivet, plstc, used5, used3, cross3, crosst, sa5, sa3, sat, sap;
   DevBuf tc_ev_off, tc, scan_part, mask, mask_off;
@@ -524,7 +524,7 @@ struct Pipeline {
                               &md_pt, &md_up4, &md_dir4, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off, &t3_mask, &t5_mask, &t3_md4, &t5_md8,
                               &t3_a, &t3_b, &t3_c, &t5_tcnt, &t5_toff, &t5_off, &t5_score, &t5_kfull, &pls_ev,
                               &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
-                              &pt5_cnt, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
+                              &pt5_xcnt, &pt5_xoff, &pt5_xmask, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
                               &c3_cnt, &c3_off, &c3_list, &ct_cnt, &ct_off, &ct_list, &alive5, &alive3, &alivet,
                               &plstc, &used5, &used3, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
                               &scan_part, &mask, &mask_off};
@@ -668,7 +668,9 @@ struct Pipeline {
     need<uint32_t>(pt3_pls, c.pt3);
     need<uint32_t>(pt3_obj, c.pt3);
     need<float>(pt3_score, c.pt3);
-    need<uint32_t>(pt5_cnt, c.pls);
+    need<uint32_t>(pt5_xcnt, c.pt3);
+    need<uint32_t>(pt5_xoff, c.pt3 + 1);
+    need<uint32_t>(pt5_xmask, c.pt3);
     need<uint32_t>(pt5_off, c.pls + 1);
     need<uint32_t>(pt5_pls, c.pt5);
     need<uint32_t>(pt5_obj, c.pt5);
@@ -780,7 +782,7 @@ struct Pipeline {
     v.pls_h0 = (float4*)pls_h0.p; v.pls_h1 = (float4*)pls_h1.p; v.pls_pt = (float*)pls_pt.p;
     v.pt3_cnt = P32(pt3_cnt); v.pt3_off = P32(pt3_off); v.pt3_pls = P32(pt3_pls); v.pt3_obj = P32(pt3_obj);
     v.pt3_score = (float*)pt3_score.p;
-    v.pt5_cnt = P32(pt5_cnt); v.pt5_off = P32(pt5_off); v.pt5_pls = P32(pt5_pls); v.pt5_obj = P32(pt5_obj);
+    v.pt5_xcnt = P32(pt5_xcnt); v.pt5_xoff = P32(pt5_xoff); v.pt5_xmask = P32(pt5_xmask); v.pt5_off = P32(pt5_off); v.pt5_pls = P32(pt5_pls); v.pt5_obj = P32(pt5_obj);
     v.pt5_score = (float*)pt5_score.p;
     v.c5_cnt = P32(c5_cnt); v.c5_off = P32(c5_off); v.c5_list = P32(c5_list);
     v.c3_cnt = P32(c3_cnt); v.c3_off = P32(c3_off); v.c3_list = P32(c3_list);

@@ -1605,70 +1605,143 @@ __global__ void __launch_bounds__(512) k_pt3_fill(MethodConst C, GeoView G, BufV
 
 // pT5 (Sec. 1: pLS + T5).  A pT5 tests the same windows on anchors a, b, c as the pT3 of the
 // T5's first T3 (a, b, c), so its candidates are exactly the T5s built on the pT3s of p
-// (t5_toff per T3); the other two anchors and the curvature decide.  Unit = pLS p.
-// The count pass keeps each pLS's (T5, score) list; the fill pass copies it (list_fill)
-// and re-runs the join only for a pLS without one.
-template <bool FILL>
-__device__ __forceinline__ void pt5_unit(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t p,
-                                         WarpAlloc& wa, uint32_t* stage) {
-  {
-    const uint32_t x0 = B.pt3_off[p], nx = B.pt3_off[p + 1] - x0;
-    if (nx == 0) {
-      if (!FILL && lane_id() == 0) B.pt5_cnt[p] = 0;
-      return;
+// (t5_toff per T3); the other two anchors and the curvature decide.  Items are the pT3s x
+// = (pLS p, T3 t), with the T5s built on t as candidates: p's pT5s are its pT3s' passes in
+// pT3 order, so per-item counts scanned over the pT3s give every pT5's position, and a pLS
+// with many pT3s is spread over many warps.
+__device__ __forceinline__ bool pt5_test(const MethodConst& C, const BufView& B, const PlsHelix& h, uint32_t t) {
+  uint32_t m[5];
+  t5_mds(B, t, m);
+  if (!pls_anchor_accept(C, h, md_point(B, m[3]))) return false;
+  if (!pls_anchor_accept(C, h, md_point(B, m[4]))) return false;
+  const Circle3 fu = circle3(md_point(B, m[0]), md_point(B, m[2]), md_point(B, m[4]));
+  return fabsf(fabsf(B.t5_kfull[t]) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
+}
+
+// Anchors m0, m1, m2 are the parent pT3's a, b, c, summed in the same order: its score is
+// this sum after three terms, bit for bit.
+__device__ __forceinline__ float pt5_score(const MethodConst& C, const BufView& B, const PlsHelix& h, uint32_t x,
+                                           uint32_t t) {
+  float score = B.pt3_score[x];
+  pls_anchor(C, h, md_point(B, B.t5_md8[2 * (size_t)t].w), score);
+  pls_anchor(C, h, md_point(B, B.t5_md8[2 * (size_t)t + 1].x), score);
+  return score;
+}
+
+// Count pass: a warp takes 32 consecutive pT3s and walks their concatenated candidates 32
+// at a time (as the MD count pass does), keeping each item's count and the pass bits of its
+// first 32 candidates.
+__global__ void __launch_bounds__(512) k_pt5_count(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_PT3];
+  const uint32_t lane = lane_id();
+  DYN_LOOP(grp, &B.hdr->work[W_PT5_COUNT], (n + 31) >> 5, 2) {
+    const uint32_t x = grp * 32 + lane;
+    const bool valid = x < n;
+    uint32_t b = 0, c = 0, p = 0;
+    if (valid) {
+      p = B.pt3_pls[x];
+      const uint32_t t = B.pt3_obj[x];
+      b = B.t5_toff[t];
+      c = B.t5_toff[t + 1] - b;
     }
-    const PlsHelix h = load_helix(B, p);
-    const uint32_t base = FILL ? B.pt5_off[p] : 0u;
-    const uint32_t n_out = FILL ? B.pt5_off[p + 1] - base : 0u;
-    uint32_t no_list = NONE;  // the fill pass runs only for a pLS without a stored list
-    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[5], FILL ? &no_list : &B.mask_off[p]};
-    auto outer = [&](uint32_t i, uint32_t& b, uint32_t& c) {
-          const uint32_t t = B.pt3_obj[x0 + i];
-          b = B.t5_toff[t];
-          c = B.t5_toff[t + 1] - b;
-        };
-    auto test = [&](uint32_t, uint32_t t) {
-          uint32_t m[5];
-          t5_mds(B, t, m);
-          if (!pls_anchor_accept(C, h, md_point(B, m[3]))) return false;
-          if (!pls_anchor_accept(C, h, md_point(B, m[4]))) return false;
-          const Circle3 fu = circle3(md_point(B, m[0]), md_point(B, m[2]), md_point(B, m[4]));
-          return fabsf(fabsf(B.t5_kfull[t]) - 1.0f / h.R) <= C.KPT5 / h.R + fu.tol;
-        };
-    auto score5 = [&](uint32_t i, uint32_t t, ScorePayload& pl) {
-          // anchors m0, m1, m2 are the parent pT3's a, b, c, summed in the same order: its
-          // score is this sum after three terms, bit for bit
-          float score = B.pt3_score[x0 + i];
-          const uint4 m0123 = B.t5_md8[2 * (size_t)t];
-          pls_anchor(C, h, md_point(B, m0123.w), score);
-          pls_anchor(C, h, md_point(B, B.t5_md8[2 * (size_t)t + 1].x), score);
-          pl.score = score;
-        };
-    auto emit5 = [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
-          B.pt5_pls[pos] = p;
-          B.pt5_obj[pos] = t;
-          B.pt5_score[pos] = pl.score;
-        };
-    const uint32_t cnt = FILL ? warp_join<true, ScorePayload>(nx, base, n_out, js, wa, outer, test, score5, emit5)
-                              : warp_count_list(nx, stage, js, wa, outer, test, score5);
-    if (!FILL && lane_id() == 0) B.pt5_cnt[p] = cnt;
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t start = incl - c;  // this lane's item: candidates [start, incl)
+    uint32_t run = 0, bits = 0;
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t so = __shfl_sync(FULL, start, o);
+      const uint32_t bo = __shfl_sync(FULL, b, o);
+      const uint32_t po = __shfl_sync(FULL, p, o);
+      const bool pass = cand < total && pt5_test(C, B, load_helix(B, po), bo + (cc - so));
+      const uint32_t bal = __ballot_sync(FULL, pass);
+      const uint32_t lo = start > t0 ? min(start - t0, 32u) : 0u;
+      const uint32_t hi = incl > t0 ? min(incl - t0, 32u) : 0u;
+      if (hi > lo) {
+        const uint32_t mine = (bal & (hi == 32u ? FULL : (1u << hi) - 1u)) >> lo;
+        run += __popc(mine);
+        const uint32_t first = t0 + lo - start;
+        if (first < 32u) bits |= mine << first;
+      }
+    }
+    if (valid) {
+      B.pt5_xcnt[x] = run;
+      B.pt5_xmask[x] = bits;
+    }
   }
 }
 
-__global__ void __launch_bounds__(512) k_pt5_count(MethodConst C, GeoView G, BufView B) {
-  extern __shared__ uint32_t stage[];
-  const Hdr* H = B.hdr;
-  if (H->err) return;
-  WarpAlloc wa;
-  DYN_LOOP(p, &B.hdr->work[W_PT5_COUNT], H->n_pls, 2) pt5_unit<false>(C, G, B, p, wa, stage + (threadIdx.x >> 5) * 2 * LIST_CAP);
-}
-
+// Fill pass in pT3 order (coalesced stores): passes of items with at most 32 candidates
+// come from the stored bits, the others are tested again; also writes the per-pLS offsets.
 __global__ void __launch_bounds__(512) k_pt5_fill(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  WarpAlloc wa;
-  list_fill(H->n_pls, B.pt5_off, B.mask, B.mask_off, B.pt5_pls, B.pt5_obj, B.pt5_score,
-            [&](uint32_t p) { pt5_unit<true>(C, G, B, p, wa, nullptr); });
+  const uint32_t n = H->tot[T_PT3];
+  THREAD_LOOP(q, H->n_pls + 1) B.pt5_off[q] = B.pt5_xoff[B.pt3_off[q]];
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  WARP_LOOP(grp, (n + 31) >> 5) {
+    const uint32_t x = grp * 32 + lane;
+    uint32_t base = 0, np = 0, b = 0, c = 0, p = 0, bits = 0;
+    if (x < n) {
+      base = B.pt5_xoff[x];
+      np = B.pt5_xoff[x + 1] - base;
+      if (np) {
+        p = B.pt3_pls[x];
+        const uint32_t t = B.pt3_obj[x];
+        b = B.t5_toff[t];
+        c = B.t5_toff[t + 1] - b;
+        bits = B.pt5_xmask[x];
+      }
+    }
+    const bool small = c <= 32u;
+    const uint32_t ns = small ? np : 0u;
+    const uint32_t incl = warp_incl_scan(ns);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t k = cc - (__shfl_sync(FULL, incl, o) - __shfl_sync(FULL, ns, o));
+      uint32_t m = __shfl_sync(FULL, bits, o);
+      const uint32_t bo = __shfl_sync(FULL, b, o);
+      const uint32_t po = __shfl_sync(FULL, p, o);
+      const uint32_t baseo = __shfl_sync(FULL, base, o);
+      if (cand < total) {
+        for (uint32_t i = 0; i < k; i++) m &= m - 1u;
+        const uint32_t t = bo + (uint32_t)(__ffs(m) - 1);
+        const uint32_t xo = grp * 32 + o;
+        B.pt5_pls[baseo + k] = po;
+        B.pt5_obj[baseo + k] = t;
+        B.pt5_score[baseo + k] = pt5_score(C, B, load_helix(B, po), xo, t);
+      }
+    }
+    // items with more than 32 candidates: test again, one item at a time
+    for (uint32_t big = __ballot_sync(FULL, np && !small); big; big &= big - 1u) {
+      const uint32_t kk = __ffs(big) - 1;
+      const uint32_t ck = __shfl_sync(FULL, c, kk), bk = __shfl_sync(FULL, b, kk);
+      const uint32_t pk = __shfl_sync(FULL, p, kk), basek = __shfl_sync(FULL, base, kk);
+      const uint32_t xk = grp * 32 + kk;
+      const PlsHelix h = load_helix(B, pk);
+      uint32_t run = 0;
+      for (uint32_t t0 = 0; t0 < ck; t0 += 32) {
+        const uint32_t t = bk + t0 + lane;
+        const bool pass = t0 + lane < ck && pt5_test(C, B, h, t);
+        const uint32_t bal = __ballot_sync(FULL, pass);
+        if (pass) {
+          const uint32_t pos = basek + run + __popc(bal & lt);
+          B.pt5_pls[pos] = pk;
+          B.pt5_obj[pos] = t;
+          B.pt5_score[pos] = pt5_score(C, B, h, xk, t);
+        }
+        run += __popc(bal);
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------------ duplicate removal
@@ -2049,14 +2122,13 @@ static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const 
   mk(4);
 }
 
-// Lets the LS, pT3 and pT5 count kernels take the shared memory of the largest block (512
+// Lets the LS and pT3 count kernels take the shared memory of the largest block (512
 // threads) on the current device; called once per pipeline, outside any stream capture.
 cudaError_t configure_kernels() {
   const int bytes = (int)((512 / 32) * (LS_LIST_CAP + LS_EXTRA_WORDS) * sizeof(uint32_t));
   cudaError_t e = cudaFuncSetAttribute(k_ls_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   const int lbytes = (int)((512 / 32) * 2 * LIST_CAP * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pt3_count, cudaFuncAttributeMaxDynamicSharedMemorySize, lbytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pt5_count, cudaFuncAttributeMaxDynamicSharedMemorySize, lbytes);
   return e;
 }
 
@@ -2134,9 +2206,9 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.pt3_cnt, B.pt3_off, &H->n_pls, 1, T_PT3, B.cap_pt3, mk);
   k_pt3_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(17);
-  k_pt5_count<<<g, bs, list_smem, s>>>(C, G, B);
+  k_pt5_count<<<g, bs, 0, s>>>(C, G, B);
   mk(18);
-  scan(B, L, s, B.pt5_cnt, B.pt5_off, &H->n_pls, 1, T_PT5, B.cap_pt5, mk);
+  scan(B, L, s, B.pt5_xcnt, B.pt5_xoff, &H->tot[T_PT3], 1, T_PT5, B.cap_pt5, mk);
   k_pt5_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(19);
   k_zero3<<<g, 256, 0, s>>>(B.c5_cnt, B.c3_cnt, B.ct_cnt, H);

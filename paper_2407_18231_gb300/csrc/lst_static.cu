@@ -120,7 +120,9 @@ size_t carve(char* base, BufView& B) {
   B.pt3_pls = c.take<uint32_t>(MAX_PT3);
   B.pt3_obj = c.take<uint32_t>(MAX_PT3);
   B.pt3_score = c.take<float>(MAX_PT3);
-  B.pt5_cnt = c.take<uint32_t>(MAX_PLS);
+  B.pt5_xcnt = c.take<uint32_t>(MAX_PT3);
+  B.pt5_xoff = c.take<uint32_t>(MAX_PT3 + 1);
+  B.pt5_xmask = c.take<uint32_t>(MAX_PT3);
   B.pt5_off = c.take<uint32_t>(MAX_PLS + 1);
   B.pt5_pls = c.take<uint32_t>(MAX_PT5);
   B.pt5_obj = c.take<uint32_t>(MAX_PT5);
