@@ -9,10 +9,13 @@ namespace lst {
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr int NSURF = 16;
 constexpr int MAX_CAND = 36;
+constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, kept per pLS
+// pT3 items of one pLS: its kept MDs, or (more passing MDs) its candidate modules
+constexpr uint32_t PLS_ITEMS = PLS_MD_CAP > (uint32_t)MAX_CAND ? PLS_MD_CAP : (uint32_t)MAX_CAND;
 
 // Totals written by the scans into the batch header.
 enum Total : int {
-  T_HITS = 0, T_MD, T_LS, T_T3, T_T5, T_PT3, T_PT5, T_C5, T_C3, T_CT, T_A5, T_A3, T_AT, T_AP, T_TC, N_TOTALS
+  T_HITS = 0, T_MD, T_LS, T_T3, T_T5, T_PT3, T_PT5, T_C5, T_C3, T_CT, T_A5, T_A3, T_AT, T_AP, T_TC, T_PT3I, N_TOTALS
 };
 constexpr uint32_t ERR_BAD_INPUT = 1u;
 constexpr uint32_t ERR_OVERFLOW_SHIFT = 8;  // bit (8 + Total) = that list outgrew its storage
@@ -97,7 +100,10 @@ struct BufView {
   float4 *pls_h0, *pls_h1;  // (x0, y0, z0, R), (cx, cy, cot, q)
   float *pls_pt;
   // pT3 / pT5
-  uint32_t *pt3_cnt, *pt3_off, *pt3_pls, *pt3_obj;
+  uint32_t *pt3_icnt, *pt3_ioff;  // per pLS: pT3 items (phase-2 MDs, or candidate modules), offsets
+  uint32_t *pt3_item_p;          // per item: its pLS
+  uint32_t *pt3_xcnt, *pt3_xoff, *pt3_xmask;  // per item: pT3s, their offset, pass bits
+  uint32_t *pt3_off, *pt3_pls, *pt3_obj;
   float *pt3_score;
   uint32_t *pt5_xcnt, *pt5_xoff, *pt5_xmask;  // per pT3: pT5s on it, their offset, pass bits
   uint32_t *pt5_off, *pt5_pls, *pt5_obj;
@@ -111,6 +117,7 @@ struct BufView {
   void *tc;  // lst_tc records
   // scan scratch
   uint32_t *scan_part;
+  uint32_t *scan_part2;  // block partials of the side stream's scan
   // join scratch: chunk ballots of the count passes, and each unit's slice of them
   uint32_t *mask, *mask_off;
   uint32_t cap_mask;

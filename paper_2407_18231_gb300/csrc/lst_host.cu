@@ -481,11 +481,11 @@ struct Pipeline {
   DevBuf t3_lcnt, t3_loff, t3_off, t3_a, t3_b, t3_c, t3_mask, t3_md4;
   DevBuf t5_tcnt, t5_toff, t5_off, t5_m[5], t5_score, t5_kfull, t5_mask, t5_md8;
   DevBuf pls_ev, pls_ncand, pls_cand, pls_h0, pls_h1, pls_pt, pls_mdpass, pls_nmdpass;
-  DevBuf pt3_cnt, pt3_off, pt3_pls, pt3_obj, pt3_score;
+  DevBuf pt3_icnt, pt3_ioff, pt3_item_p, pt3_xcnt, pt3_xoff, pt3_xmask, pt3_off, pt3_pls, pt3_obj, pt3_score;
   DevBuf pt5_xcnt, pt5_xoff, pt5_xmask, pt5_off, pt5_pls, pt5_obj, pt5_score;
   DevBuf c5_cnt, c5_off, c5_list, c3_cnt, c3_off, c3_list, ct_cnt, ct_off, ct_list;
   DevBuf alive5, alive3, alivet, plstc, used5, used3, cross3, crosst, sa5, sa3, sat, sap;
-  DevBuf tc_ev_off, tc, scan_part, mask, mask_off;
+  DevBuf tc_ev_off, tc, scan_part, scan_part2, mask, mask_off;
   uint32_t cap_mask = 0;
   // host staging (pinned)
   Hdr* h_hdr = nullptr;        // header to upload
@@ -523,11 +523,11 @@ struct Pipeline {
                               &hit_tmp, &hit_ev, &hit_idx, &hit_sen, &hit4, &md_hcnt, &md_hoff, &md_hmask, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
                               &md_pt, &md_up4, &md_dir4, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off, &t3_mask, &t5_mask, &t3_md4, &t5_md8,
                               &t3_a, &t3_b, &t3_c, &t5_tcnt, &t5_toff, &t5_off, &t5_score, &t5_kfull, &pls_ev,
-                              &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_cnt, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
+                              &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_icnt, &pt3_ioff, &pt3_item_p, &pt3_xcnt, &pt3_xoff, &pt3_xmask, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
                               &pt5_xcnt, &pt5_xoff, &pt5_xmask, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
                               &c3_cnt, &c3_off, &c3_list, &ct_cnt, &ct_off, &ct_list, &alive5, &alive3, &alivet,
                               &plstc, &used5, &used3, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
-                              &scan_part, &mask, &mask_off};
+                              &scan_part, &scan_part2, &mask, &mask_off};
     for (auto& b : t5_m) v.push_back(&b);
     return v;
   }
@@ -595,6 +595,7 @@ struct Pipeline {
     CK(cudaMallocHost((void**)&h_hdr_out, sizeof(Hdr)));
     hdr.ensure(sizeof(Hdr), dev_bytes);
     scan_part.ensure(4 * 1024 * sizeof(uint32_t), dev_bytes);  // up to four scans per launch
+    scan_part2.ensure(1024 * sizeof(uint32_t), dev_bytes);
   }
 
   template <typename T>
@@ -658,12 +659,17 @@ struct Pipeline {
     need<uint32_t>(pls_ev, c.pls);
     need<uint32_t>(pls_ncand, c.pls);
     need<uint32_t>(pls_cand, (size_t)c.pls * MAX_CAND);
-    need<uint32_t>(pls_mdpass, (size_t)c.pls * 64);
+    need<uint32_t>(pls_mdpass, (size_t)c.pls * PLS_MD_CAP);
     need<uint32_t>(pls_nmdpass, c.pls);
     need<float4>(pls_h0, c.pls);
     need<float4>(pls_h1, c.pls);
     need<float>(pls_pt, c.pls);
-    need<uint32_t>(pt3_cnt, c.pls);
+    need<uint32_t>(pt3_icnt, c.pls);
+    need<uint32_t>(pt3_ioff, c.pls + 1);
+    need<uint32_t>(pt3_item_p, (size_t)c.pls * PLS_ITEMS);
+    need<uint32_t>(pt3_xcnt, (size_t)c.pls * PLS_ITEMS);
+    need<uint32_t>(pt3_xoff, (size_t)c.pls * PLS_ITEMS + 1);
+    need<uint32_t>(pt3_xmask, (size_t)c.pls * PLS_ITEMS);
     need<uint32_t>(pt3_off, c.pls + 1);
     need<uint32_t>(pt3_pls, c.pt3);
     need<uint32_t>(pt3_obj, c.pt3);
@@ -780,7 +786,8 @@ struct Pipeline {
     v.pls_ev = P32(pls_ev); v.pls_ncand = P32(pls_ncand); v.pls_cand = P32(pls_cand);
     v.pls_mdpass = P32(pls_mdpass); v.pls_nmdpass = P32(pls_nmdpass);
     v.pls_h0 = (float4*)pls_h0.p; v.pls_h1 = (float4*)pls_h1.p; v.pls_pt = (float*)pls_pt.p;
-    v.pt3_cnt = P32(pt3_cnt); v.pt3_off = P32(pt3_off); v.pt3_pls = P32(pt3_pls); v.pt3_obj = P32(pt3_obj);
+    v.pt3_icnt = P32(pt3_icnt); v.pt3_ioff = P32(pt3_ioff); v.pt3_item_p = P32(pt3_item_p);
+    v.pt3_xcnt = P32(pt3_xcnt); v.pt3_xoff = P32(pt3_xoff); v.pt3_xmask = P32(pt3_xmask); v.pt3_off = P32(pt3_off); v.pt3_pls = P32(pt3_pls); v.pt3_obj = P32(pt3_obj);
     v.pt3_score = (float*)pt3_score.p;
     v.pt5_xcnt = P32(pt5_xcnt); v.pt5_xoff = P32(pt5_xoff); v.pt5_xmask = P32(pt5_xmask); v.pt5_off = P32(pt5_off); v.pt5_pls = P32(pt5_pls); v.pt5_obj = P32(pt5_obj);
     v.pt5_score = (float*)pt5_score.p;
@@ -790,7 +797,7 @@ struct Pipeline {
     v.alive5 = P32(alive5); v.alive3 = P32(alive3); v.alivet = P32(alivet); v.plstc = P32(plstc);
     v.used5 = P32(used5); v.used3 = P32(used3); v.cross3 = P32(cross3); v.crosst = P32(crosst);
     v.sa5 = P32(sa5); v.sa3 = P32(sa3); v.sat = P32(sat); v.sap = P32(sap);
-    v.tc_ev_off = P32(tc_ev_off); v.tc = tc.p; v.scan_part = P32(scan_part);
+    v.tc_ev_off = P32(tc_ev_off); v.tc = tc.p; v.scan_part = P32(scan_part); v.scan_part2 = P32(scan_part2);
     v.mask = P32(mask); v.mask_off = P32(mask_off); v.cap_mask = cap_mask;
 #undef P32
     return v;

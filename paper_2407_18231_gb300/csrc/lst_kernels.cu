@@ -210,111 +210,6 @@ __device__ __forceinline__ bool warp_any(uint32_t n_outer, OuterFn outer, TestFn
   return false;
 }
 
-// Count pass of a join whose fill pass only copies: the passing candidates' inner indices
-// and scores (score(i, j, payload), the fill pass's arithmetic) are staged in candidate
-// order in this warp's `stage` (2 LIST_CAP words of dynamic shared memory), then stored as
-// [j, score bits] pairs in `mask` through the warp's bump allocator.  More than LIST_CAP
-// passes, or a full scratch, store NONE: the fill pass then re-runs the join for that unit.
-constexpr uint32_t LIST_CAP = 256;
-template <typename OuterFn, typename TestFn, typename ScoreFn>
-__device__ __forceinline__ uint32_t warp_count_list(uint32_t n_outer, uint32_t* stage, const JoinScratch& js,
-                                                    WarpAlloc& wa, OuterFn outer, TestFn test, ScoreFn score) {
-  const uint32_t lane = lane_id();
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t count = 0;
-  for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
-    uint32_t b = 0, c = 0;
-    if (g0 + lane < n_outer) outer(g0 + lane, b, c);
-    const uint32_t incl = warp_incl_scan(c);
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
-    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-      const uint32_t cand = t0 + lane;
-      const uint32_t cc = cand < total ? cand : total - 1;
-      const uint32_t o = owner_lane(incl, cc);
-      const uint32_t bo = __shfl_sync(FULL, b, o);
-      const uint32_t co = __shfl_sync(FULL, c, o);
-      const uint32_t io = __shfl_sync(FULL, incl, o);
-      const uint32_t j = bo + (cc - (io - co));
-      const bool pass = cand < total && test(g0 + o, j);
-      const uint32_t bal = __ballot_sync(FULL, pass);
-      const uint32_t r = count + __popc(bal & lt);
-      if (pass && r < LIST_CAP) {
-        ScorePayload pl;
-        score(g0 + o, j, pl);
-        stage[2 * r] = j;
-        stage[2 * r + 1] = __float_as_uint(pl.score);
-      }
-      count += __popc(bal);
-    }
-  }
-  __syncwarp();
-  uint32_t mbase = NONE;
-  if (count > 0 && count <= LIST_CAP) {
-    const uint32_t need = 2 * count;
-    uint32_t mb = NONE;
-    if (lane == 0) {
-      if (wa.end - wa.cur < need || wa.cur == NONE) {
-        const uint32_t b0 = atomicAdd(js.used, 1024u);
-        if (b0 < js.cap && 1024u <= js.cap - b0) {
-          wa.cur = b0;
-          wa.end = b0 + 1024u;
-        } else {
-          wa.cur = wa.end = 0;
-        }
-      }
-      if (wa.end - wa.cur >= need) {
-        mb = wa.cur;
-        wa.cur += need;
-      }
-    }
-    mbase = __shfl_sync(FULL, mb, 0);
-    wa.cur = __shfl_sync(FULL, wa.cur, 0);
-    wa.end = __shfl_sync(FULL, wa.end, 0);
-    if (mbase != NONE)
-      for (uint32_t i = lane; i < need; i += 32) js.mask[mbase + i] = stage[i];
-  }
-  __syncwarp();  // the stage is reused by the next unit
-  if (lane == 0) *js.unit_base = mbase;
-  return count;
-}
-
-// Fill pass of such a join, flat over the units in order so that a warp's outputs are
-// consecutive and its stores coalesce: a warp takes 32 consecutive units and walks their
-// concatenated stored lists; a unit without one (NONE) calls retest(unit).
-template <typename RetestFn>
-__device__ __forceinline__ void list_fill(uint32_t n, const uint32_t* off, const uint32_t* mask,
-                                          const uint32_t* mask_off, uint32_t* out_unit, uint32_t* out_obj,
-                                          float* out_score, RetestFn retest) {
-  const uint32_t lane = lane_id();
-  const uint32_t ng = (n + 31) >> 5;
-  for (uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; grp < ng; grp += (gridDim.x * blockDim.x) >> 5) {
-    const uint32_t p = grp * 32 + lane;
-    uint32_t base = 0, cnt = 0, mb = NONE;
-    if (p < n) {
-      base = off[p];
-      cnt = off[p + 1] - base;
-      if (cnt) mb = mask_off[p];
-    }
-    const uint32_t ns = mb != NONE ? cnt : 0u;
-    const uint32_t incl = warp_incl_scan(ns);
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
-    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-      const uint32_t cand = t0 + lane;
-      const uint32_t cc = cand < total ? cand : total - 1;
-      const uint32_t o = owner_lane(incl, cc);
-      const uint32_t k = cc - (__shfl_sync(FULL, incl, o) - __shfl_sync(FULL, ns, o));
-      const uint32_t bo = __shfl_sync(FULL, base, o);
-      const uint32_t mo = __shfl_sync(FULL, mb, o);
-      if (cand < total) {
-        out_unit[bo + k] = grp * 32 + o;
-        out_obj[bo + k] = mask[mo + 2 * k];
-        out_score[bo + k] = __uint_as_float(mask[mo + 2 * k + 1]);
-      }
-    }
-    for (uint32_t re = __ballot_sync(FULL, cnt && mb == NONE); re; re &= re - 1u) retest(grp * 32 + __ffs(re) - 1);
-  }
-}
-
 // warp_any for groups of S lanes (S a power of two, n_outer <= S): each group answers for
 // its own object, so a warp has 32 / S objects' loads in flight.  A group with active ==
 // false has no candidates.  Uniform across the warp: every lane must call it.
@@ -1446,7 +1341,6 @@ __device__ __forceinline__ void t3_mds(const BufView& B, uint32_t t, uint32_t m[
 }
 
 // ------------------------------------------------------------------ pT3 / pT5
-constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, kept per pLS
 constexpr uint32_t PT3_RING = 64;    // queued pre-rejection survivors per warp (> 31 + 32)
 
 // pT3 phase 1 (Sec. 1: pLS + T3), on its own so that it can run beside the LS, T3 and T5
@@ -1514,93 +1408,173 @@ __global__ void __launch_bounds__(512) k_pt3_first_anchor(MethodConst C, GeoView
       if (qt != qh) accept_queued(qt - qh);
       __syncwarp();
       if (npass > PLS_MD_CAP) npass = NONE;
-      if (lane == 0) B.pls_nmdpass[p] = npass;
+      if (lane == 0) {
+        B.pls_nmdpass[p] = npass;
+        B.pt3_icnt[p] = npass != NONE ? npass : nc;  // pT3 items of p
+      }
       __syncwarp();
     }
   }
 }
 
-// pT3 (Sec. 1: pLS + T3).  Unit = pLS p.  Phase 1 tests p against every MD on its
-// candidate modules (the first anchor of any T3 it could join) and keeps the passing MDs in
-// order; phase 2 walks the T3s starting at those MDs and tests their other two anchors.  The
+// pT3 (Sec. 1: pLS + T3).  Phase 1 (k_pt3_first_anchor) tests pLS p against every MD on
+// its candidate modules (the first anchor of any T3 it could join) and keeps the passing
+// MDs in order; phase 2 tests the other two anchors of the T3s starting at those MDs.  The
 // set equals "T3s whose first MD is on a candidate module, all three anchors inside the
 // windows" and comes out in T3 order.  More than PLS_MD_CAP passing MDs: the pLS falls back
-// to walking every T3 of its candidate modules.
-// The count pass keeps each pLS's (T3, score) list; the fill pass copies it (list_fill)
-// and re-runs the join only for a pLS without one.
-template <bool FILL>
-__device__ __forceinline__ void pt3_unit(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t p,
-                                         WarpAlloc& wa, uint32_t* stage) {
-  {
-    const PlsHelix h = load_helix(B, p);
-    const uint32_t ubase = B.pls_ev[p] * G.nm;
-    const uint32_t* cand = B.pls_cand + (size_t)p * MAX_CAND;
-    const uint32_t nc = B.pls_ncand[p];
-    uint32_t* mlist = B.pls_mdpass + (size_t)p * PLS_MD_CAP;
-    const uint32_t npass = B.pls_nmdpass[p];  // from k_pt3_first_anchor
-    const uint32_t base = FILL ? B.pt3_off[p] : 0u;
-    const uint32_t n_out = FILL ? B.pt3_off[p + 1] - base : 0u;
-    uint32_t no_list = NONE;  // the fill pass runs only for a pLS without a stored list
-    const JoinScratch js{B.mask, B.cap_mask, &B.hdr->mask_used[4], FILL ? &no_list : &B.mask_off[p]};
-    auto score3 = [&](uint32_t, uint32_t t, ScorePayload& pl) {
-      float score = 0.0f;
-      pls_anchor(C, h, md_point(B, B.t3_a[t]), score);
-      pls_anchor(C, h, md_point(B, B.t3_b[t]), score);
-      pls_anchor(C, h, md_point(B, B.t3_c[t]), score);
-      pl.score = score;
-    };
-    auto emit3 = [&](uint32_t pos, uint32_t, uint32_t t, const ScorePayload& pl) {
-      B.pt3_pls[pos] = p;
-      B.pt3_obj[pos] = t;
-      B.pt3_score[pos] = pl.score;
-    };
-    auto join = [&](uint32_t n_outer, auto outer, auto test) {
-      if (FILL) return warp_join<true, ScorePayload>(n_outer, base, n_out, js, wa, outer, test, score3, emit3);
-      return warp_count_list(n_outer, stage, js, wa, outer, test, score3);
-    };
-    uint32_t cnt;
-    if (npass != NONE) {
-      cnt = join(
-          npass,
-          [&](uint32_t i, uint32_t& b, uint32_t& c) {
-            const uint32_t m = mlist[i];
-            b = B.t3_off[m];
-            c = B.t3_off[m + 1] - b;
-          },
-          [&](uint32_t, uint32_t t) {
-            return pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
-          });
-    } else {
-      cnt = join(
-          nc,
-          [&](uint32_t i, uint32_t& b, uint32_t& c) {
-            const uint32_t u = ubase + cand[i];
-            b = B.t3_off[B.md_off[u]];
-            c = B.t3_off[B.md_off[u + 1]] - b;
-          },
-          [&](uint32_t, uint32_t t) {
-            return pls_anchor_accept(C, h, md_point(B, B.t3_a[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) &&
-                   pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
-          });
-    }
-    if (!FILL && lane_id() == 0) B.pt3_cnt[p] = cnt;
+// to all T3s of its candidate modules, all three anchors tested.  Phase 2 runs over items:
+// item k of p is its k-th passing MD (or k-th candidate module in the fallback), with the
+// T3s starting there (there) as candidates, so p's pT3s are its items' passes in item order.
+
+// The item -> pLS table, from the items' offsets (scan of pt3_icnt).  One warp per pLS.
+__global__ void k_pt3_items(BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t lane = lane_id();
+  WARP_LOOP(p, H->n_pls) {
+    const uint32_t b = B.pt3_ioff[p], c = B.pt3_ioff[p + 1] - b;
+    for (uint32_t i = lane; i < c; i += 32) B.pt3_item_p[b + i] = p;
   }
 }
 
-__global__ void __launch_bounds__(512) k_pt3_count(MethodConst C, GeoView G, BufView B) {
-  extern __shared__ uint32_t stage[];
-  const Hdr* H = B.hdr;
-  if (H->err) return;
-  WarpAlloc wa;
-  DYN_LOOP(p, &B.hdr->work[W_PT3_COUNT], H->n_pls, 2) pt3_unit<false>(C, G, B, p, wa, stage + (threadIdx.x >> 5) * 2 * LIST_CAP);
+// Item x: its pLS p, whether all three anchors are tested, and its T3 range [b, b + c).
+__device__ __forceinline__ void pt3_item(const GeoView& G, const BufView& B, uint32_t x, uint32_t& p, bool& full,
+                                         uint32_t& b, uint32_t& c) {
+  p = B.pt3_item_p[x];
+  const uint32_t k = x - B.pt3_ioff[p];
+  full = B.pls_nmdpass[p] == NONE;
+  if (!full) {
+    const uint32_t m = B.pls_mdpass[(size_t)p * PLS_MD_CAP + k];
+    b = B.t3_off[m];
+    c = B.t3_off[m + 1] - b;
+  } else {
+    const uint32_t u = B.pls_ev[p] * G.nm + B.pls_cand[(size_t)p * MAX_CAND + k];
+    b = B.t3_off[B.md_off[u]];
+    c = B.t3_off[B.md_off[u + 1]] - b;
+  }
 }
 
+__device__ __forceinline__ bool pt3_test(const MethodConst& C, const BufView& B, const PlsHelix& h, bool full,
+                                         uint32_t t) {
+  if (full && !pls_anchor_accept(C, h, md_point(B, B.t3_a[t]))) return false;
+  return pls_anchor_accept(C, h, md_point(B, B.t3_b[t])) && pls_anchor_accept(C, h, md_point(B, B.t3_c[t]));
+}
+
+__device__ __forceinline__ float pt3_score(const MethodConst& C, const BufView& B, const PlsHelix& h, uint32_t t) {
+  float score = 0.0f;
+  pls_anchor(C, h, md_point(B, B.t3_a[t]), score);
+  pls_anchor(C, h, md_point(B, B.t3_b[t]), score);
+  pls_anchor(C, h, md_point(B, B.t3_c[t]), score);
+  return score;
+}
+
+// Count pass: a warp takes 32 consecutive items and walks their concatenated candidates 32
+// at a time, keeping each item's count and the pass bits of its first 32 candidates.
+__global__ void __launch_bounds__(512) k_pt3_count(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_PT3I];
+  const uint32_t lane = lane_id();
+  DYN_LOOP(grp, &B.hdr->work[W_PT3_COUNT], (n + 31) >> 5, 2) {
+    const uint32_t x = grp * 32 + lane;
+    const bool valid = x < n;
+    uint32_t b = 0, c = 0, p = 0;
+    bool full = false;
+    if (valid) pt3_item(G, B, x, p, full, b, c);
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t start = incl - c;  // this lane's item: candidates [start, incl)
+    uint32_t run = 0, bits = 0;
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t so = __shfl_sync(FULL, start, o);
+      const uint32_t bo = __shfl_sync(FULL, b, o);
+      const uint32_t po = __shfl_sync(FULL, p, o);
+      const bool fo = __shfl_sync(FULL, (uint32_t)full, o) != 0u;
+      const bool pass = cand < total && pt3_test(C, B, load_helix(B, po), fo, bo + (cc - so));
+      const uint32_t bal = __ballot_sync(FULL, pass);
+      const uint32_t lo = start > t0 ? min(start - t0, 32u) : 0u;
+      const uint32_t hi = incl > t0 ? min(incl - t0, 32u) : 0u;
+      if (hi > lo) {
+        const uint32_t mine = (bal & (hi == 32u ? FULL : (1u << hi) - 1u)) >> lo;
+        run += __popc(mine);
+        const uint32_t first = t0 + lo - start;
+        if (first < 32u) bits |= mine << first;
+      }
+    }
+    if (valid) {
+      B.pt3_xcnt[x] = run;
+      B.pt3_xmask[x] = bits;
+    }
+  }
+}
+
+// Fill pass in item order (coalesced stores): passes of items with at most 32 candidates
+// come from the stored bits, the others are tested again; also writes the per-pLS offsets.
 __global__ void __launch_bounds__(512) k_pt3_fill(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
-  WarpAlloc wa;
-  list_fill(H->n_pls, B.pt3_off, B.mask, B.mask_off, B.pt3_pls, B.pt3_obj, B.pt3_score,
-            [&](uint32_t p) { pt3_unit<true>(C, G, B, p, wa, nullptr); });
+  const uint32_t n = H->tot[T_PT3I];
+  THREAD_LOOP(q, H->n_pls + 1) B.pt3_off[q] = B.pt3_xoff[B.pt3_ioff[q]];
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  WARP_LOOP(grp, (n + 31) >> 5) {
+    const uint32_t x = grp * 32 + lane;
+    uint32_t base = 0, np = 0, b = 0, c = 0, p = 0, bits = 0;
+    bool full = false;
+    if (x < n) {
+      base = B.pt3_xoff[x];
+      np = B.pt3_xoff[x + 1] - base;
+      if (np) {
+        pt3_item(G, B, x, p, full, b, c);
+        bits = B.pt3_xmask[x];
+      }
+    }
+    const bool small = c <= 32u;
+    const uint32_t ns = small ? np : 0u;
+    const uint32_t incl = warp_incl_scan(ns);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t k = cc - (__shfl_sync(FULL, incl, o) - __shfl_sync(FULL, ns, o));
+      uint32_t m = __shfl_sync(FULL, bits, o);
+      const uint32_t bo = __shfl_sync(FULL, b, o);
+      const uint32_t po = __shfl_sync(FULL, p, o);
+      const uint32_t baseo = __shfl_sync(FULL, base, o);
+      if (cand < total) {
+        for (uint32_t i = 0; i < k; i++) m &= m - 1u;
+        const uint32_t t = bo + (uint32_t)(__ffs(m) - 1);
+        B.pt3_pls[baseo + k] = po;
+        B.pt3_obj[baseo + k] = t;
+        B.pt3_score[baseo + k] = pt3_score(C, B, load_helix(B, po), t);
+      }
+    }
+    // items with more than 32 candidates: test again, one item at a time
+    for (uint32_t big = __ballot_sync(FULL, np && !small); big; big &= big - 1u) {
+      const uint32_t kk = __ffs(big) - 1;
+      const uint32_t ck = __shfl_sync(FULL, c, kk), bk = __shfl_sync(FULL, b, kk);
+      const uint32_t pk = __shfl_sync(FULL, p, kk), basek = __shfl_sync(FULL, base, kk);
+      const bool fk = __shfl_sync(FULL, (uint32_t)full, kk) != 0u;
+      const PlsHelix h = load_helix(B, pk);
+      uint32_t run = 0;
+      for (uint32_t t0 = 0; t0 < ck; t0 += 32) {
+        const uint32_t t = bk + t0 + lane;
+        const bool pass = t0 + lane < ck && pt3_test(C, B, h, fk, t);
+        const uint32_t bal = __ballot_sync(FULL, pass);
+        if (pass) {
+          const uint32_t pos = basek + run + __popc(bal & lt);
+          B.pt3_pls[pos] = pk;
+          B.pt3_obj[pos] = t;
+          B.pt3_score[pos] = pt3_score(C, B, h, t);
+        }
+        run += __popc(bal);
+      }
+    }
+  }
 }
 
 // pT5 (Sec. 1: pLS + T5).  A pT5 tests the same windows on anchors a, b, c as the pT3 of the
@@ -2094,7 +2068,7 @@ const char* const kKernelNames[] = {
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "zero_md_lists", "md_lists_count", "md_lists_fill",
     "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
-    "t3_md_offsets", "t5_md_offsets", "pt3_first_anchor", "pls_sort"};
+    "t3_md_offsets", "t5_md_offsets", "pt3_first_anchor", "pls_sort", "pt3_items"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Marker {
@@ -2115,6 +2089,18 @@ static void scan(const BufView& B, const Launch& L, cudaStream_t s, const uint32
   mk(4);
 }
 
+// pT3 item offsets and item -> pLS table.  May run on the side stream beside the main
+// chain's scans, so its scan keeps its partials in a buffer of its own.
+static void pt3_items(const BufView& B, const Launch& L, cudaStream_t s, Marker& mk) {
+  k_scan_reduce<<<L.scan_grid, 512, 0, s>>>(B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2);
+  mk(2);
+  k_scan_apply<<<L.scan_grid, 512, 0, s>>>(B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2, B.pt3_ioff, T_PT3I,
+                                           0xFFFFFFFFu);
+  mk(4);
+  k_pt3_items<<<L.grid, 256, 0, s>>>(B);
+  mk(36);
+}
+
 static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const ScanJobs& J, int n, Marker& mk) {
   k_scan_reduce_multi<<<dim3(L.scan_grid, n), 512, 0, s>>>(J, B.hdr, B.scan_part);
   mk(2);
@@ -2122,14 +2108,11 @@ static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const 
   mk(4);
 }
 
-// Lets the LS and pT3 count kernels take the shared memory of the largest block (512
-// threads) on the current device; called once per pipeline, outside any stream capture.
+// Lets the LS count kernel take the shared memory of the largest block (512 threads) on the
+// current device; called once per pipeline, outside any stream capture.
 cudaError_t configure_kernels() {
   const int bytes = (int)((512 / 32) * (LS_LIST_CAP + LS_EXTRA_WORDS) * sizeof(uint32_t));
-  cudaError_t e = cudaFuncSetAttribute(k_ls_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  const int lbytes = (int)((512 / 32) * 2 * LIST_CAP * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pt3_count, cudaFuncAttributeMaxDynamicSharedMemorySize, lbytes);
-  return e;
+  return cudaFuncSetAttribute(k_ls_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // Enqueues the whole chain on stream s; returns the number of kernels launched.  mark (may
@@ -2167,10 +2150,10 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     cudaStreamWaitEvent(side->s, side->mds, 0);
     k_pt3_first_anchor<<<g, bs, 0, side->s>>>(C, G, B);
     mk(34);
+    pt3_items(B, L, side->s, mk);
     cudaEventRecord(side->join, side->s);
   }
   const uint32_t lcap = L.ls_list_cap;
-  const size_t list_smem = (bs / 32) * 2 * LIST_CAP * sizeof(uint32_t);
   const size_t ls_smem = lcap ? (bs / 32) * (lcap + LS_EXTRA_WORDS) * sizeof(uint32_t) : 0;
   k_ls_count<<<g, bs, ls_smem, s>>>(C, G, B, lcap);
   mk(9);
@@ -2200,10 +2183,11 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     mk(35);
     k_pt3_first_anchor<<<g, bs, 0, s>>>(C, G, B);
     mk(34);
+    pt3_items(B, L, s, mk);
   }
-  k_pt3_count<<<g, bs, list_smem, s>>>(C, G, B);
+  k_pt3_count<<<g, bs, 0, s>>>(C, G, B);
   mk(16);
-  scan(B, L, s, B.pt3_cnt, B.pt3_off, &H->n_pls, 1, T_PT3, B.cap_pt3, mk);
+  scan(B, L, s, B.pt3_xcnt, B.pt3_xoff, &H->tot[T_PT3I], 1, T_PT3, B.cap_pt3, mk);
   k_pt3_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(17);
   k_pt5_count<<<g, bs, 0, s>>>(C, G, B);

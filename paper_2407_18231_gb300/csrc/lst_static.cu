@@ -110,12 +110,17 @@ size_t carve(char* base, BufView& B) {
   B.pls_ev = c.take<uint32_t>(MAX_PLS);
   B.pls_ncand = c.take<uint32_t>(MAX_PLS);
   B.pls_cand = c.take<uint32_t>((size_t)MAX_PLS * MAX_CAND);
-  B.pls_mdpass = c.take<uint32_t>((size_t)MAX_PLS * 64);
+  B.pls_mdpass = c.take<uint32_t>((size_t)MAX_PLS * PLS_MD_CAP);
   B.pls_nmdpass = c.take<uint32_t>(MAX_PLS);
   B.pls_h0 = c.take<float4>(MAX_PLS);
   B.pls_h1 = c.take<float4>(MAX_PLS);
   B.pls_pt = c.take<float>(MAX_PLS);
-  B.pt3_cnt = c.take<uint32_t>(MAX_PLS);
+  B.pt3_icnt = c.take<uint32_t>(MAX_PLS);
+  B.pt3_ioff = c.take<uint32_t>(MAX_PLS + 1);
+  B.pt3_item_p = c.take<uint32_t>((size_t)MAX_PLS * PLS_ITEMS);
+  B.pt3_xcnt = c.take<uint32_t>((size_t)MAX_PLS * PLS_ITEMS);
+  B.pt3_xoff = c.take<uint32_t>((size_t)MAX_PLS * PLS_ITEMS + 1);
+  B.pt3_xmask = c.take<uint32_t>((size_t)MAX_PLS * PLS_ITEMS);
   B.pt3_off = c.take<uint32_t>(MAX_PLS + 1);
   B.pt3_pls = c.take<uint32_t>(MAX_PT3);
   B.pt3_obj = c.take<uint32_t>(MAX_PT3);
@@ -150,6 +155,7 @@ size_t carve(char* base, BufView& B) {
   B.sap = c.take<uint32_t>(MAX_PLS + 1);
   B.tc_ev_off = c.take<uint32_t>(2);
   B.scan_part = c.take<uint32_t>(4 * 1024);  // partials of up to four scans per launch
+  B.scan_part2 = c.take<uint32_t>(1024);
   B.mask_off = c.take<uint32_t>(MAX_MODULES);  // >= MAX_MD and MAX_PLS
   B.cap_mask = MASK_WORDS;
   B.mask = c.take<uint32_t>(MASK_WORDS);
@@ -162,7 +168,7 @@ __global__ void k_static_header(Hdr* H, Hdr v) {
 
 const char* list_name(int t) {
   static const char* n[N_TOTALS] = {"hits", "MD", "LS", "T3", "T5", "pT3", "pT5", "MD-pT5 list", "MD-pT3 list",
-                                    "MD-T5 list", "pT5 flags", "pT3 flags", "T5 flags", "pLS flags", "TC"};
+                                    "MD-T5 list", "pT5 flags", "pT3 flags", "T5 flags", "pLS flags", "TC", "pT3 items"};
   return (t >= 0 && t < N_TOTALS) ? n[t] : "?";
 }
 
