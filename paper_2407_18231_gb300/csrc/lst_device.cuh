@@ -38,7 +38,7 @@ struct Hdr {
   uint32_t tot[N_TOTALS];
   uint32_t err;
   uint32_t pad2[3];
-  uint32_t mask_used[8];  // join scratch words taken per stage (MD, LS, T3, T5, pT3, pT5)
+  uint32_t mask_used[8];  // scratch-arena words requested ([1]: LS partner lists; others unused)
   unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)
   uint32_t work[16];           // work counters of the dynamically scheduled kernels (W_*)
 };
@@ -119,6 +119,8 @@ struct BufView {
   uint32_t *scan_part;
   uint32_t *scan_part2;  // block partials of the side stream's scan
   // join scratch: chunk ballots of the count passes, and each unit's slice of them
+  // scratch arena: the LS count pass's partner lists [count, partner MDs] (mask_off: per
+  // anchor MD its list's offset, or NONE when the fill pass must join it again)
   uint32_t *mask, *mask_off;
   uint32_t cap_mask;
 };

@@ -704,9 +704,9 @@ struct Pipeline {
     need<uint32_t>(sap, c.pls + 1);
     need<uint32_t>(tc_ev_off, c.ev + 1);
     need<lst_tc>(tc, c.tc);
-    need<uint32_t>(mask_off, std::max<size_t>(std::max<size_t>(c.ev * nm, c.md), c.pls));
-    // join scratch: about two ballot words per hit suffice for PU200-like events; runs that
-    // need more fall back to re-testing and the next run gets the learned size
+    need<uint32_t>(mask_off, c.md);
+    // LS partner lists: about two words per hit suffice for PU200-like events; runs that
+    // need more fall back to joining again and the next run gets the learned size
     const uint32_t want = std::max<uint32_t>(cap_mask, (uint32_t)std::min<uint64_t>(4000000000ull, 4ull * c.hits + 65536));
     need<uint32_t>(mask, want);
     cap_mask = want;

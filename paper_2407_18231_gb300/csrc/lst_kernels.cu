@@ -44,72 +44,21 @@ __device__ __forceinline__ uint32_t owner_lane(uint32_t incl, uint32_t cand) {
   return o;
 }
 
-struct NoPayload {};
-struct ScorePayload {
-  float score, kfull;
-};
-
-// Scratch of the joins.  The count pass keeps, for each 32-candidate chunk that holds a
-// passing candidate, its position (outer group start, candidate offset) and its ballot word
-// in lane registers, then writes them as one record list [n, (g0, t0, ballot) x n] into
-// `mask` through a per-warp bump allocator (one global atomic per 1024+ words).  The fill
-// pass decodes only those chunks.  A unit whose passes span more than 32 chunks, or that
-// finds the scratch full, stores NONE and its fill pass re-runs the tests instead, so the
-// output never depends on the scratch size.
-struct JoinScratch {
-  uint32_t* mask;
-  uint32_t cap;
-  uint32_t* used;
-  uint32_t* unit_base;  // this unit's record list (or NONE)
-};
-
+// Per-warp bump allocator over a scratch arena (one global atomic per 1024+ words).
 struct WarpAlloc {
   uint32_t cur = 0, end = 0;  // warp-uniform
 };
 
-// Walks all (outer i, inner j) candidates of one unit; outer(i, begin, count) gives the
-// inner index range of outer item i.  Count pass (FILL = false): test(i, j) decides and the
-// number of passes is returned.  Fill pass: n_out passing candidates are emitted at
-// base + rank in candidate order, with score(i, j, payload) computing what emit needs.
-template <bool FILL, typename P, typename OuterFn, typename TestFn, typename ScoreFn, typename EmitFn>
-__device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, uint32_t n_out, const JoinScratch& js,
-                                              WarpAlloc& wa, OuterFn outer, TestFn test, ScoreFn score, EmitFn emit) {
+// Walks all (outer i, inner j) candidates of one unit 32 at a time; outer(i, begin, count)
+// gives the inner index range of outer item i and test(i, j) decides.  Count pass (FILL =
+// false): returns the number of passes.  Fill pass: emit(pos, i, j) for each pass, pos =
+// base + rank in candidate order.
+template <bool FILL, typename OuterFn, typename TestFn, typename EmitFn>
+__device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, OuterFn outer, TestFn test,
+                                              EmitFn emit) {
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  if (FILL) {
-    if (n_out == 0) return 0;
-    const uint32_t mbase = *js.unit_base;
-    if (mbase != NONE) {
-      const uint32_t nrec = js.mask[mbase];
-      uint32_t count = 0;
-      for (uint32_t r = 0; r < nrec; r++) {
-        const uint32_t g0 = js.mask[mbase + 1 + 3 * r];
-        const uint32_t t0 = js.mask[mbase + 2 + 3 * r];
-        const uint32_t bal = js.mask[mbase + 3 + 3 * r];
-        uint32_t b = 0, c = 0;
-        if (g0 + lane < n_outer) outer(g0 + lane, b, c);
-        const uint32_t incl = warp_incl_scan(c);
-        const uint32_t total = __shfl_sync(FULL, incl, 31);
-        const uint32_t cand = t0 + lane;
-        const uint32_t cc = cand < total ? cand : total - 1;
-        const uint32_t o = owner_lane(incl, cc);
-        const uint32_t bo = __shfl_sync(FULL, b, o);
-        const uint32_t co = __shfl_sync(FULL, c, o);
-        const uint32_t io = __shfl_sync(FULL, incl, o);
-        const uint32_t j = bo + (cc - (io - co));
-        if ((bal >> lane) & 1u) {
-          P pl;
-          score(g0 + o, j, pl);
-          emit(base + count + __popc(bal & lt), g0 + o, j, pl);
-        }
-        count += __popc(bal);
-      }
-      return count;
-    }
-  }
-  // full walk: the count pass, or a fill pass without records
-  uint32_t count = 0, nrec = 0, rg = 0, rt = 0, rb = 0;
-  bool spill = false;
+  uint32_t count = 0;
   for (uint32_t g0 = 0; g0 < n_outer; g0 += 32) {
     uint32_t b = 0, c = 0;
     if (g0 + lane < n_outer) outer(g0 + lane, b, c);
@@ -125,62 +74,9 @@ __device__ __forceinline__ uint32_t warp_join(uint32_t n_outer, uint32_t base, u
       const uint32_t j = bo + (cc - (io - co));
       const bool pass = cand < total && test(g0 + o, j);
       const uint32_t bal = __ballot_sync(FULL, pass);
-      if (bal) {
-        if (!FILL) {
-          if (nrec < 32) {
-            if (lane == nrec) {
-              rg = g0;
-              rt = t0;
-              rb = bal;
-            }
-            nrec++;
-          } else {
-            spill = true;
-          }
-        }
-        if (FILL && pass) {
-          P pl;
-          score(g0 + o, j, pl);
-          emit(base + count + __popc(bal & lt), g0 + o, j, pl);
-        }
-      }
+      if (FILL && pass) emit(base + count + __popc(bal & lt), g0 + o, j);
       count += __popc(bal);
     }
-  }
-  if (!FILL) {
-    uint32_t mbase = NONE;
-    if (count > 0 && !spill) {
-      const uint32_t need = 1 + 3 * nrec;
-      uint32_t mb = NONE;
-      if (lane == 0) {
-        if (wa.end - wa.cur < need || wa.cur == NONE) {
-          const uint32_t grab = need > 1024u ? need : 1024u;
-          const uint32_t b0 = atomicAdd(js.used, grab);
-          if (b0 < js.cap && grab <= js.cap - b0) {
-            wa.cur = b0;
-            wa.end = b0 + grab;
-          } else {
-            wa.cur = wa.end = 0;
-          }
-        }
-        if (wa.end - wa.cur >= need) {
-          mb = wa.cur;
-          wa.cur += need;
-        }
-      }
-      mbase = __shfl_sync(FULL, mb, 0);
-      wa.cur = __shfl_sync(FULL, wa.cur, 0);
-      wa.end = __shfl_sync(FULL, wa.end, 0);
-      if (mbase != NONE) {
-        if (lane == 0) js.mask[mbase] = nrec;
-        if (lane < nrec) {
-          js.mask[mbase + 1 + 3 * lane] = rg;
-          js.mask[mbase + 2 + 3 * lane] = rt;
-          js.mask[mbase + 3 + 3 * lane] = rb;
-        }
-      }
-    }
-    if (lane == 0) *js.unit_base = mbase;
   }
   return count;
 }
@@ -732,11 +628,12 @@ __device__ __forceinline__ bool ls_test(const MethodConst& C, const GeoView& G, 
   return ls_head(C, B, pa, j) && ls_tail(C, G, B, pa, da, rnext, a_barrel, ubase, j);
 }
 
-// Per-MD LS join (candidates = MDs of every module in the connection map of A), used for
-// modules whose flattened neighbour list does not fit the shared-memory list.
+// Per-MD LS join (candidates = MDs of every module in the connection map of A): the count
+// pass uses it for modules whose flattened neighbour list does not fit the shared-memory
+// list, the fill pass for anchors without a stored partner list.
 template <bool FILL>
 __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& G, const BufView& B, uint32_t a,
-                                           uint32_t ev, uint32_t A, WarpAlloc& wa) {
+                                           uint32_t ev, uint32_t A) {
   const PointTol pa = md_point(B, a);
   const float4 da = B.md_dir4[a];
   const float rnext = G.rnext[A];
@@ -744,26 +641,23 @@ __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& 
   const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
   const uint32_t base = FILL ? B.ls_off[a] : 0u;
   const uint32_t ubase = ev * G.nm;
-  const uint32_t n_out = FILL ? B.ls_off[a + 1] - base : 0u;
-  // partner-list records come from the list path only: rows joined here keep none (no
-  // scratch to take from), and the fill pass re-tests them
-  (void)wa;
-  WarpAlloc none;
-  const JoinScratch js{B.mask, 0u, &B.hdr->work[N_WORK], &B.mask_off[a]};
-  const uint32_t cnt = warp_join<FILL, NoPayload>(
-      nb, base, n_out, js, none,
+  const uint32_t cnt = warp_join<FILL>(
+      nb, base,
       [&](uint32_t i, uint32_t& b, uint32_t& c) {
         const uint32_t u = ubase + G.conn[nb0 + i];
         b = B.md_off[u];
         c = B.md_off[u + 1] - b;
       },
       [&](uint32_t, uint32_t j) { return ls_test(C, G, B, pa, da, rnext, a_barrel, ubase, j); },
-      [&](uint32_t, uint32_t, NoPayload&) {},
-      [&](uint32_t pos, uint32_t, uint32_t j, const NoPayload&) {
+      [&](uint32_t pos, uint32_t, uint32_t j) {
         B.ls_in[pos] = a;
         B.ls_out[pos] = j;
       });
-  if (!FILL && lane_id() == 0) B.ls_cnt[a] = cnt;
+  // no partner list is stored for an anchor joined here: the fill pass joins it again
+  if (!FILL && lane_id() == 0) {
+    B.ls_cnt[a] = cnt;
+    B.mask_off[a] = NONE;
+  }
 }
 
 // LS fill pass, flat over anchor MDs in their order, so that a warp's LSs are consecutive
@@ -776,7 +670,6 @@ __global__ void __launch_bounds__(512) k_ls_fill(MethodConst C, GeoView G, BufVi
   if (H->err) return;
   const uint32_t n = H->tot[T_MD];
   const uint32_t lane = lane_id();
-  WarpAlloc wa;
   WARP_LOOP(grp, (n + 31) >> 5) {
     const uint32_t a = grp * 32 + lane;
     uint32_t base = 0, cnt = 0, mb = NONE;
@@ -804,7 +697,7 @@ __global__ void __launch_bounds__(512) k_ls_fill(MethodConst C, GeoView G, BufVi
       const uint32_t ak = grp * 32 + __ffs(re) - 1;
       const uint32_t u = B.md_unit[ak];
       const uint32_t ev = u / G.nm;
-      ls_md_join<true>(C, G, B, ak, ev, u - ev * G.nm, wa);
+      ls_md_join<true>(C, G, B, ak, ev, u - ev * G.nm);
     }
   }
 }
@@ -880,7 +773,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
       return;
     }
     if (len > list_cap) {
-      for (uint32_t a = a0; a < a1; a++) ls_md_join<false>(C, G, B, a, ev, A, wa);
+      for (uint32_t a = a0; a < a1; a++) ls_md_join<false>(C, G, B, a, ev, A);
       return;
     }
     const float rnext = G.rnext[A];
@@ -982,56 +875,58 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
 }
 
 // ------------------------------------------------------------------ T3
-// Unit = LS l (a -> b), one thread each; candidates = the LSs leaving b (a handful).
-// T3s come out ordered by (LS l, LS l2), i.e. by (a, b, c).
-template <bool FILL>
-__global__ void __launch_bounds__(512) k_t3(MethodConst C, GeoView G, BufView B) {
+// Item = LS l (a -> b), one thread each; candidates = the LSs leaving b (a handful, so a
+// thread per LS loads a's and b's records once for all of them).  T3s come out ordered by
+// (LS l, LS l2), i.e. by (a, b, c).  The count pass keeps each LS's count and the pass bits
+// of its first 32 candidates.
+__global__ void __launch_bounds__(512) k_t3_count(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_LS];
   THREAD_LOOP(l, n) {
-    uint32_t k = 0;
-    if (FILL) {
-      k = B.t3_loff[l];
-      if (B.t3_loff[l + 1] == k) continue;
-    }
     const uint32_t a = B.ls_in[l], b = B.ls_out[l];
     const uint32_t c0 = B.ls_off[b], c1 = B.ls_off[b + 1];
-    if (c0 == c1) {
-      if (!FILL) B.t3_lcnt[l] = 0;
-      continue;
-    }
-    if (FILL && c1 - c0 <= 32) {  // the count pass's pass bits: no test
-      for (uint32_t bits = B.t3_mask[l]; bits; bits &= bits - 1u) {
-        const uint32_t c = B.ls_out[c0 + __ffs(bits) - 1];
-        B.t3_a[k] = a;
-        B.t3_b[k] = b;
-        B.t3_c[k] = c;
-        B.t3_md4[k] = make_uint4(a, b, c, 0u);
-        k++;
-      }
-      continue;
-    }
-    const PointTol pa = md_point(B, a), pb = md_point(B, b), pbu = md_upper(B, b);
     uint32_t cnt = 0, bits = 0;
-    for (uint32_t l2 = c0; l2 < c1; l2++) {
-      const uint32_t c = B.ls_out[l2];
-      if (t3_select(C, pa, pb, pbu, md_point(B, c))) {
-        if (FILL) {
-          B.t3_a[k] = a;
-          B.t3_b[k] = b;
-          B.t3_c[k] = c;
-          B.t3_md4[k] = make_uint4(a, b, c, 0u);
-          k++;
-        } else {
+    if (c0 != c1) {
+      const PointTol pa = md_point(B, a), pb = md_point(B, b), pbu = md_upper(B, b);
+      for (uint32_t l2 = c0; l2 < c1; l2++) {
+        if (t3_select(C, pa, pb, pbu, md_point(B, B.ls_out[l2]))) {
           cnt++;
           if (l2 - c0 < 32) bits |= 1u << (l2 - c0);
         }
       }
     }
-    if (!FILL) {
-      B.t3_lcnt[l] = cnt;
-      B.t3_mask[l] = bits;
+    B.t3_lcnt[l] = cnt;
+    B.t3_mask[l] = bits;
+  }
+}
+
+// Fill pass, one thread per LS: with at most 32 candidates the count pass's pass bits say
+// which candidates pass (no test), otherwise they are tested again.
+__global__ void __launch_bounds__(512) k_t3_fill(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_LS];
+  THREAD_LOOP(l, n) {
+    uint32_t k = B.t3_loff[l];
+    if (B.t3_loff[l + 1] == k) continue;
+    const uint32_t a = B.ls_in[l], b = B.ls_out[l];
+    const uint32_t c0 = B.ls_off[b], c1 = B.ls_off[b + 1];
+    auto emit = [&](uint32_t c) {
+      B.t3_a[k] = a;
+      B.t3_b[k] = b;
+      B.t3_c[k] = c;
+      B.t3_md4[k] = make_uint4(a, b, c, 0u);
+      k++;
+    };
+    if (c1 - c0 <= 32) {
+      for (uint32_t bits = B.t3_mask[l]; bits; bits &= bits - 1u) emit(B.ls_out[c0 + __ffs(bits) - 1]);
+      continue;
+    }
+    const PointTol pa = md_point(B, a), pb = md_point(B, b), pbu = md_upper(B, b);
+    for (uint32_t l2 = c0; l2 < c1; l2++) {
+      const uint32_t c = B.ls_out[l2];
+      if (t3_select(C, pa, pb, pbu, md_point(B, c))) emit(c);
     }
   }
 }
@@ -1044,57 +939,135 @@ __global__ void k_t3_md_off(BufView B) {
 }
 
 // ------------------------------------------------------------------ T5
-// Unit = T3 t (a, b, c), one thread each; candidates = the T3s starting at c.  T5s come out
-// ordered by (T3 t, T3 t2), i.e. by (a, b, c, d, e), and t5_toff[t] gives the T5s built on t.
-template <bool FILL>
-__global__ void __launch_bounds__(512) k_t5(MethodConst C, GeoView G, BufView B) {
+// Item = T3 t (a, b, c); candidates = the T3s starting at c.  T5s come out ordered by (T3 t,
+// T3 t2), i.e. by (a, b, c, d, e), and t5_toff[t] gives the T5s built on t.  Both passes
+// take 32 consecutive T3s per warp and walk their concatenated candidates (count) or
+// passes (fill) 32 at a time, so the lanes stay busy whatever the candidate counts.
+__global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_T3];
-  THREAD_LOOP(t, n) {
-    uint32_t k = 0;
-    if (FILL) {
-      k = B.t5_toff[t];
-      if (B.t5_toff[t + 1] == k) continue;
+  const uint32_t lane = lane_id();
+  WARP_LOOP(grp, (n + 31) >> 5) {
+    const uint32_t t = grp * 32 + lane;
+    const bool valid = t < n;
+    uint32_t s0 = 0, c = 0;
+    if (valid) {
+      const uint32_t m = B.t3_c[t];
+      s0 = B.t3_off[m];
+      c = B.t3_off[m + 1] - s0;
     }
-    const uint32_t c = B.t3_c[t];
-    const uint32_t s0 = B.t3_off[c], s1 = B.t3_off[c + 1];
-    if (s0 == s1) {
-      if (!FILL) B.t5_tcnt[t] = 0;
-      continue;
-    }
-    const uint32_t a = B.t3_a[t], b = B.t3_b[t];
-    const PointTol pa = md_point(B, a), pb = md_point(B, b), pc = md_point(B, c);
-    uint32_t cnt = 0, bits = 0;
-    // fill pass: with at most 32 candidates, only those the count pass accepted
-    const uint32_t todo = FILL && s1 - s0 <= 32 ? B.t5_mask[t] : FULL;
-    for (uint32_t t2 = s0; t2 < s1; t2++) {
-      if (FILL && t2 - s0 < 32 && !((todo >> (t2 - s0)) & 1u)) continue;
-      const uint32_t d = B.t3_b[t2], e = B.t3_c[t2];
-      const PointTol pd = md_point(B, d), pe = md_point(B, e);
-      if (!FILL) {
-        const bool ok = t5_accept(C, pa, pb, pc, pd, pe);
-        cnt += ok ? 1u : 0u;
-        if (ok && t2 - s0 < 32) bits |= 1u << (t2 - s0);
-      } else {
-        float score, kfull;
-        if (t5_select(C, pa, pb, pc, pd, pe, score, kfull)) {
-          B.t5_m0[k] = a;
-          B.t5_m1[k] = b;
-          B.t5_m2[k] = c;
-          B.t5_m3[k] = d;
-          B.t5_m4[k] = e;
-          B.t5_md8[2 * (size_t)k] = make_uint4(a, b, c, d);
-          B.t5_md8[2 * (size_t)k + 1] = make_uint4(e, 0u, 0u, 0u);
-          B.t5_score[k] = score;
-          B.t5_kfull[k] = kfull;
-          k++;
-        }
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t start = incl - c;  // this lane's T3: candidates [start, incl)
+    uint32_t run = 0, bits = 0;
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t t2 = __shfl_sync(FULL, s0, o) + (cc - __shfl_sync(FULL, start, o));
+      bool pass = false;
+      if (cand < total) {
+        const uint4 abc = B.t3_md4[grp * 32 + o];
+        pass = t5_accept(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, B.t3_b[t2]),
+                         md_point(B, B.t3_c[t2]));
+      }
+      const uint32_t bal = __ballot_sync(FULL, pass);
+      const uint32_t lo = start > t0 ? min(start - t0, 32u) : 0u;
+      const uint32_t hi = incl > t0 ? min(incl - t0, 32u) : 0u;
+      if (hi > lo) {
+        const uint32_t mine = (bal & (hi == 32u ? FULL : (1u << hi) - 1u)) >> lo;
+        run += __popc(mine);
+        const uint32_t first = t0 + lo - start;
+        if (first < 32u) bits |= mine << first;
       }
     }
-    if (!FILL) {
-      B.t5_tcnt[t] = cnt;
+    if (valid) {
+      B.t5_tcnt[t] = run;
       B.t5_mask[t] = bits;
+    }
+  }
+}
+
+__device__ __forceinline__ void t5_emit(const MethodConst& C, const BufView& B, uint32_t k, uint32_t a, uint32_t b,
+                                        uint32_t c, uint32_t d, uint32_t e, float score, float kfull) {
+  B.t5_m0[k] = a;
+  B.t5_m1[k] = b;
+  B.t5_m2[k] = c;
+  B.t5_m3[k] = d;
+  B.t5_m4[k] = e;
+  B.t5_md8[2 * (size_t)k] = make_uint4(a, b, c, d);
+  B.t5_md8[2 * (size_t)k + 1] = make_uint4(e, 0u, 0u, 0u);
+  B.t5_score[k] = score;
+  B.t5_kfull[k] = kfull;
+}
+
+// Fill pass: passes of T3s with at most 32 candidates come from the stored bits (the score
+// and curvature of each are computed once), the others are tested again.
+__global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufView B) {
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_T3];
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  WARP_LOOP(grp, (n + 31) >> 5) {
+    const uint32_t t = grp * 32 + lane;
+    uint32_t base = 0, np = 0, s0 = 0, c = 0, bits = 0;
+    if (t < n) {
+      base = B.t5_toff[t];
+      np = B.t5_toff[t + 1] - base;
+      if (np) {
+        const uint32_t m = B.t3_c[t];
+        s0 = B.t3_off[m];
+        c = B.t3_off[m + 1] - s0;
+        bits = B.t5_mask[t];
+      }
+    }
+    const bool small = c <= 32u;
+    const uint32_t ns = small ? np : 0u;
+    const uint32_t incl = warp_incl_scan(ns);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t k = cc - (__shfl_sync(FULL, incl, o) - __shfl_sync(FULL, ns, o));
+      uint32_t m = __shfl_sync(FULL, bits, o);
+      const uint32_t s0o = __shfl_sync(FULL, s0, o);
+      const uint32_t baseo = __shfl_sync(FULL, base, o);
+      if (cand < total) {
+        for (uint32_t i = 0; i < k; i++) m &= m - 1u;
+        const uint32_t t2 = s0o + (uint32_t)(__ffs(m) - 1);
+        const uint4 abc = B.t3_md4[grp * 32 + o];
+        const uint32_t d = B.t3_b[t2], e = B.t3_c[t2];
+        float score, kfull;
+        t5_select(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, d), md_point(B, e),
+                  score, kfull);
+        t5_emit(C, B, baseo + k, abc.x, abc.y, abc.z, d, e, score, kfull);
+      }
+    }
+    // T3s with more than 32 candidates: test again, one T3 at a time
+    for (uint32_t big = __ballot_sync(FULL, np && !small); big; big &= big - 1u) {
+      const uint32_t kk = __ffs(big) - 1;
+      const uint32_t ck = __shfl_sync(FULL, c, kk), sk = __shfl_sync(FULL, s0, kk);
+      const uint32_t basek = __shfl_sync(FULL, base, kk);
+      const uint4 abc = B.t3_md4[grp * 32 + kk];
+      const PointTol pa = md_point(B, abc.x), pb = md_point(B, abc.y), pc = md_point(B, abc.z);
+      uint32_t run = 0;
+      for (uint32_t t0 = 0; t0 < ck; t0 += 32) {
+        const uint32_t t2 = sk + t0 + lane;
+        float score = 0.0f, kfull = 0.0f;
+        uint32_t d = 0, e = 0;
+        bool pass = false;
+        if (t0 + lane < ck) {
+          d = B.t3_b[t2];
+          e = B.t3_c[t2];
+          pass = t5_select(C, pa, pb, pc, md_point(B, d), md_point(B, e), score, kfull);
+        }
+        const uint32_t bal = __ballot_sync(FULL, pass);
+        if (pass) t5_emit(C, B, basek + run + __popc(bal & lt), abc.x, abc.y, abc.z, d, e, score, kfull);
+        run += __popc(bal);
+      }
     }
   }
 }
@@ -2160,17 +2133,17 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
   k_ls_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(10);
-  k_t3<false><<<g, 256, 0, s>>>(C, G, B);
+  k_t3_count<<<g, 256, 0, s>>>(C, G, B);
   mk(11);
   scan(B, L, s, B.t3_lcnt, B.t3_loff, &H->tot[T_LS], 1, T_T3, B.cap_t3, mk);
-  k_t3<true><<<g, 256, 0, s>>>(C, G, B);
+  k_t3_fill<<<g, 256, 0, s>>>(C, G, B);
   mk(12);
   k_t3_md_off<<<g, 256, 0, s>>>(B);
   mk(32);
-  k_t5<false><<<g, 256, 0, s>>>(C, G, B);
+  k_t5_count<<<g, bs, 0, s>>>(C, G, B);
   mk(13);
   scan(B, L, s, B.t5_tcnt, B.t5_toff, &H->tot[T_T3], 1, T_T5, B.cap_t5, mk);
-  k_t5<true><<<g, 256, 0, s>>>(C, G, B);
+  k_t5_fill<<<g, bs, 0, s>>>(C, G, B);
   mk(14);
   k_t5_md_off<<<g, 256, 0, s>>>(B);
   mk(33);

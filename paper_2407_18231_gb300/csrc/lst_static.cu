@@ -156,7 +156,7 @@ size_t carve(char* base, BufView& B) {
   B.tc_ev_off = c.take<uint32_t>(2);
   B.scan_part = c.take<uint32_t>(4 * 1024);  // partials of up to four scans per launch
   B.scan_part2 = c.take<uint32_t>(1024);
-  B.mask_off = c.take<uint32_t>(MAX_MODULES);  // >= MAX_MD and MAX_PLS
+  B.mask_off = c.take<uint32_t>(MAX_MD);
   B.cap_mask = MASK_WORDS;
   B.mask = c.take<uint32_t>(MASK_WORDS);
   return c.off;
