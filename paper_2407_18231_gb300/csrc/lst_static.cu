@@ -37,7 +37,7 @@ constexpr uint32_t MAX_T3 = 32768;
 constexpr uint32_t MAX_T5 = 16384;
 constexpr uint32_t MAX_PT3 = 16384;
 constexpr uint32_t MAX_PT5 = 16384;
-constexpr uint32_t MASK_WORDS = 65536;  // join ballots; a fuller event just re-tests in its fill passes
+constexpr uint32_t MASK_WORDS = 65536;  // LS partner lists; a fuller event joins again in the fill pass
 constexpr size_t SCRATCH_BYTES = size_t(8) << 20;  // every GPU that loads the library holds this until exit
 
 // The scratch.  In host code `g_scratch` is only a stand-in symbol: its device address
