@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=32, help="events per step")
     ap.add_argument("--pool", type=int, default=4, help="distinct resident batches rotated over")
     ap.add_argument("--per-event", type=int, default=48, help="events for the per-event leg (0 = skip)")
-    ap.add_argument("--served", type=int, default=256, help="events for the served leg (0 = skip)")
+    ap.add_argument("--served", type=int, default=2048, help="events for the served leg (0 = skip)")
     ap.add_argument("--served-rate", type=float, default=0.0, help="offered Hz (0: 0.8 x batched rate)")
     ap.add_argument("--cpu-sample", type=int, default=8, help="events for the CPU-oracle baseline (0 = skip)")
     ap.add_argument("--tune", type=int, default=1, help="autotune the launch configuration first (1) or not (0)")
