@@ -14,6 +14,8 @@
 // replays any batch that fits the buffers.
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "../../include/lst.h"
 #include "lst_device.cuh"
 
@@ -22,6 +24,13 @@ namespace lst {
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Programmatic dependent launch: every kernel of the chain is launched so that it may be
+// scheduled as soon as its predecessor's blocks have all exited (no explicit trigger: an
+// early one let waiting blocks take the slots of the persistent grids and was slower), and
+// waits here, before any access to what the predecessor wrote, until that grid's writes
+// are visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   const uint32_t lane = lane_id();
@@ -222,6 +231,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sm, ui
 
 __global__ void k_scan_reduce(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul, const Hdr* H,
                               uint32_t* part) {
+  pdl_wait();
   if (H->err) return;
   __shared__ uint32_t sm[33];
   const uint32_t n = (*nptr) * mul;
@@ -256,6 +266,7 @@ __device__ __forceinline__ uint32_t scan_carry(const uint32_t* part, uint32_t* s
 
 __global__ void k_scan_apply(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul, Hdr* H,
                              const uint32_t* part, uint32_t* __restrict__ out, int tot_idx, uint32_t cap) {
+  pdl_wait();
   if (H->err) return;
   __shared__ uint32_t sm[33];
   const uint32_t n = (*nptr) * mul;
@@ -297,6 +308,7 @@ struct ScanJobs {
 };
 
 __global__ void k_scan_reduce_multi(ScanJobs J, const Hdr* H, uint32_t* part) {
+  pdl_wait();
   if (H->err) return;
   __shared__ uint32_t sm[33];
   const ScanJob& q = J.j[blockIdx.y];
@@ -312,6 +324,7 @@ __global__ void k_scan_reduce_multi(ScanJobs J, const Hdr* H, uint32_t* part) {
 }
 
 __global__ void k_scan_apply_multi(ScanJobs J, Hdr* H, const uint32_t* part) {
+  pdl_wait();
   if (H->err) return;
   __shared__ uint32_t sm[33];
   const ScanJob& q = J.j[blockIdx.y];
@@ -342,11 +355,13 @@ __global__ void k_scan_apply_multi(ScanJobs J, Hdr* H, const uint32_t* part) {
 }
 
 __global__ void k_zero(uint32_t* p, const uint32_t* nptr, uint32_t mul, uint32_t add) {
+  pdl_wait();
   const uint32_t n = (*nptr) * mul + add;
   THREAD_LOOP(i, n) p[i] = 0u;
 }
 
 __global__ void k_zero3(uint32_t* a, uint32_t* b, uint32_t* c, const Hdr* H) {
+  pdl_wait();
   if (H->err) return;
   const uint32_t n = H->tot[T_MD] + 1;
   THREAD_LOOP(i, n) {
@@ -359,6 +374,7 @@ __global__ void k_zero3(uint32_t* a, uint32_t* b, uint32_t* c, const Hdr* H) {
 // ------------------------------------------------------------------ hit binning
 // Count hits per (event, sensor); validate module ids and coordinates.
 __global__ void k_hits_count(GeoView G, BufView B) {
+  pdl_wait();
   Hdr* H = B.hdr;
   const uint32_t n = H->n_hits, ne = H->n_ev, two_nm = 2u * G.nm;
   THREAD_LOOP(h, n) {
@@ -375,6 +391,7 @@ __global__ void k_hits_count(GeoView G, BufView B) {
 }
 
 __global__ void k_hits_scatter(GeoView G, BufView B) {
+  pdl_wait();
   Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_hits, two_nm = 2u * G.nm;
@@ -387,6 +404,7 @@ __global__ void k_hits_scatter(GeoView G, BufView B) {
 
 // Stable order inside each sensor bucket: rank by input index.
 __global__ void k_hits_sort(GeoView G, BufView B) {
+  pdl_wait();
   Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_hits, two_nm = 2u * G.nm;
@@ -435,6 +453,7 @@ constexpr uint32_t MD_BIG = 1u << 26;  // candidates of one lower hit above whic
 // chunk are a contiguous lane range, so its passes are popc(ballot & range), and the pass
 // bits of its first 32 candidates are kept for the fill pass.
 __global__ void __launch_bounds__(512) k_md_count(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_hits;
@@ -514,6 +533,7 @@ __global__ void __launch_bounds__(512) k_md_count(MethodConst C, GeoView G, BufV
 // candidates (stored bits incomplete) re-tests its candidates instead.  Also writes the
 // per-unit MD offsets (the item offset of the unit's first hit).
 __global__ void __launch_bounds__(512) k_md_fill(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_hits;
@@ -666,6 +686,7 @@ __device__ __forceinline__ void ls_md_join(const MethodConst& C, const GeoView& 
 // list the count pass could not store (arena full, or a neighbour list beyond the shared
 // memory) is joined again on its own.
 __global__ void __launch_bounds__(512) k_ls_fill(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_MD];
@@ -714,6 +735,7 @@ constexpr uint32_t LS_EXTRA_WORDS = LS_RING + LS_ANCHORS * LS_LIST_CAP / 32 + LS
 // walks the list for the MDs a of A: no per-MD neighbour lookups, no per-chunk search.  It
 // stores each anchor's partner list (for k_ls_fill to copy) and its count.
 __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufView B, uint32_t list_cap) {
+  pdl_wait();
   extern __shared__ uint32_t ls_smem[];
   const Hdr* H = B.hdr;
   if (H->err) return;
@@ -880,6 +902,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
 // (LS l, LS l2), i.e. by (a, b, c).  The count pass keeps each LS's count and the pass bits
 // of its first 32 candidates.
 __global__ void __launch_bounds__(512) k_t3_count(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_LS];
@@ -904,6 +927,7 @@ __global__ void __launch_bounds__(512) k_t3_count(MethodConst C, GeoView G, BufV
 // Fill pass, one thread per LS: with at most 32 candidates the count pass's pass bits say
 // which candidates pass (no test), otherwise they are tested again.
 __global__ void __launch_bounds__(512) k_t3_fill(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_LS];
@@ -933,6 +957,7 @@ __global__ void __launch_bounds__(512) k_t3_fill(MethodConst C, GeoView G, BufVi
 
 // T3s starting at MD a = T3s of the LSs leaving a: t3_off[a] = t3_loff[ls_off[a]].
 __global__ void k_t3_md_off(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   THREAD_LOOP(a, H->tot[T_MD] + 1) B.t3_off[a] = B.t3_loff[B.ls_off[a]];
@@ -944,6 +969,7 @@ __global__ void k_t3_md_off(BufView B) {
 // take 32 consecutive T3s per warp and walk their concatenated candidates (count) or
 // passes (fill) 32 at a time, so the lanes stay busy whatever the candidate counts.
 __global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_T3];
@@ -1005,6 +1031,7 @@ __device__ __forceinline__ void t5_emit(const MethodConst& C, const BufView& B, 
 // Fill pass: passes of T3s with at most 32 candidates come from the stored bits (the score
 // and curvature of each are computed once), the others are tested again.
 __global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_T3];
@@ -1074,6 +1101,7 @@ __global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufVi
 
 // T5s starting at MD a: t5_off[a] = t5_toff[t3_off[a]].
 __global__ void k_t5_md_off(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   THREAD_LOOP(a, H->tot[T_MD] + 1) B.t5_off[a] = B.t5_toff[B.t3_off[a]];
@@ -1197,6 +1225,7 @@ __device__ __forceinline__ bool pls_surface_point(const MethodConst& C, const Ge
 // k_pls_sort: one warp per pLS sorts the 36 slots and drops repeats, which leaves the
 // ascending set of distinct candidate module ids.
 __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
@@ -1253,6 +1282,7 @@ __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
 }
 
 __global__ void k_pls_sort(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
@@ -1322,6 +1352,7 @@ constexpr uint32_t PT3_RING = 64;    // queued pre-rejection survivors per warp 
 // every MD, survivors are queued in MD order and the full window test runs on 32 of them
 // at a time, so the passing MDs (at most PLS_MD_CAP kept, else NONE) come out in MD order.
 __global__ void __launch_bounds__(512) k_pt3_first_anchor(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->n_pls;
@@ -1401,6 +1432,7 @@ __global__ void __launch_bounds__(512) k_pt3_first_anchor(MethodConst C, GeoView
 
 // The item -> pLS table, from the items' offsets (scan of pt3_icnt).  One warp per pLS.
 __global__ void k_pt3_items(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t lane = lane_id();
@@ -1444,6 +1476,7 @@ __device__ __forceinline__ float pt3_score(const MethodConst& C, const BufView& 
 // Count pass: a warp takes 32 consecutive items and walks their concatenated candidates 32
 // at a time, keeping each item's count and the pass bits of its first 32 candidates.
 __global__ void __launch_bounds__(512) k_pt3_count(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_PT3I];
@@ -1487,6 +1520,7 @@ __global__ void __launch_bounds__(512) k_pt3_count(MethodConst C, GeoView G, Buf
 // Fill pass in item order (coalesced stores): passes of items with at most 32 candidates
 // come from the stored bits, the others are tested again; also writes the per-pLS offsets.
 __global__ void __launch_bounds__(512) k_pt3_fill(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_PT3I];
@@ -1579,6 +1613,7 @@ __device__ __forceinline__ float pt5_score(const MethodConst& C, const BufView& 
 // at a time (as the MD count pass does), keeping each item's count and the pass bits of its
 // first 32 candidates.
 __global__ void __launch_bounds__(512) k_pt5_count(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_PT3];
@@ -1625,6 +1660,7 @@ __global__ void __launch_bounds__(512) k_pt5_count(MethodConst C, GeoView G, Buf
 // Fill pass in pT3 order (coalesced stores): passes of items with at most 32 candidates
 // come from the stored bits, the others are tested again; also writes the per-pLS offsets.
 __global__ void __launch_bounds__(512) k_pt5_fill(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_PT3];
@@ -1707,6 +1743,7 @@ __device__ __forceinline__ bool better(float sy, uint32_t y, float sx, uint32_t 
 
 // MD -> object lists for pT5 (5 MDs each), pT3 (3) and T5 (5).
 __global__ void k_csr_count(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n5 = H->tot[T_PT5], n3 = H->tot[T_PT3], nt = H->tot[T_T5];
@@ -1728,6 +1765,7 @@ __global__ void k_csr_count(BufView B) {
 }
 
 __global__ void k_csr_fill(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n5 = H->tot[T_PT5], n3 = H->tot[T_PT3], nt = H->tot[T_T5];
@@ -1753,6 +1791,7 @@ __global__ void k_csr_fill(BufView B) {
 // lanes test 32 neighbours at a time (the pLS's other pT5s, then the pT5s on three of its
 // MDs -- sharing >= 3 of 5 MDs means sharing one of any three of them).
 __global__ void k_kill_pt5(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_PT5];
@@ -1789,6 +1828,7 @@ __global__ void k_kill_pt5(BufView B) {
 }
 
 __global__ void k_used5(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   THREAD_LOOP(p, H->n_pls) {
@@ -1800,6 +1840,7 @@ __global__ void k_used5(BufView B) {
 
 // pT3 across stages: its pLS is used by a surviving pT5, or it shares >= 2 MDs with one.
 __global__ void k_cross_pt3(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   THREAD_LOOP(x, H->tot[T_PT3]) {
@@ -1823,6 +1864,7 @@ __global__ void k_cross_pt3(BufView B) {
 
 // pT3 stage among those left: dies iff a better one shares its pLS or >= 2 MDs.
 __global__ void k_kill_pt3(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   THREAD_LOOP(x, H->tot[T_PT3]) {
@@ -1848,6 +1890,7 @@ __global__ void k_kill_pt3(BufView B) {
 }
 
 __global__ void k_used3(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   THREAD_LOOP(p, H->n_pls) {
@@ -1861,6 +1904,7 @@ __global__ void k_used3(BufView B) {
 // T5 across stages: shares >= 3 MDs with a surviving pT5 or pT3 (one of any three of its
 // MDs is then shared).  One warp per T5.
 __global__ void k_cross_t5(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   GROUP_LOOP(x, act, H->tot[T_T5], CROSS_T5_GROUP) {
@@ -1894,6 +1938,7 @@ __global__ void k_cross_t5(BufView B) {
 
 // T5 stage among those left: dies iff a better one shares >= 3 MDs.  One warp per T5.
 __global__ void k_kill_t5(BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   GROUP_LOOP(x, act, H->tot[T_T5], KILL_T5_GROUP) {
@@ -1945,6 +1990,7 @@ __device__ __forceinline__ EvCounts ev_counts(const GeoView& G, const BufView& B
 }
 
 __global__ void k_tc_offsets(GeoView G, BufView B) {
+  pdl_wait();
   Hdr* H = B.hdr;
   if (H->err) return;
   __shared__ uint32_t sm[33];
@@ -1991,6 +2037,7 @@ __device__ __forceinline__ void write_tc(lst_tc* tc, uint8_t type, uint32_t obj,
 
 // Survivors -> track candidates: per event pT5s, pT3s, T5s, then unused pLSs (Sec. 1 list).
 __global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n5 = H->tot[T_PT5], n3 = H->tot[T_PT3], nt = H->tot[T_T5], np = H->n_pls;
@@ -2054,30 +2101,47 @@ struct Marker {
   }
 };
 
+// Launches kernel k on stream s allowing programmatic dependent launch: k may be scheduled
+// while the previous kernel on s drains, and waits for it in pdl_wait().
+template <typename... KArgs, typename... Args>
+static void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 static void scan(const BufView& B, const Launch& L, cudaStream_t s, const uint32_t* in, uint32_t* out,
                  const uint32_t* nptr, uint32_t mul, int tot, uint32_t cap, Marker& mk) {
-  k_scan_reduce<<<L.scan_grid, 512, 0, s>>>(in, nptr, mul, B.hdr, B.scan_part);
+  launch(k_scan_reduce, L.scan_grid, 512, 0, s, in, nptr, mul, B.hdr, B.scan_part);
   mk(2);
-  k_scan_apply<<<L.scan_grid, 512, 0, s>>>(in, nptr, mul, B.hdr, B.scan_part, out, tot, cap);
+  launch(k_scan_apply, L.scan_grid, 512, 0, s, in, nptr, mul, B.hdr, B.scan_part, out, tot, cap);
   mk(4);
 }
 
 // pT3 item offsets and item -> pLS table.  May run on the side stream beside the main
 // chain's scans, so its scan keeps its partials in a buffer of its own.
 static void pt3_items(const BufView& B, const Launch& L, cudaStream_t s, Marker& mk) {
-  k_scan_reduce<<<L.scan_grid, 512, 0, s>>>(B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2);
+  launch(k_scan_reduce, L.scan_grid, 512, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2);
   mk(2);
-  k_scan_apply<<<L.scan_grid, 512, 0, s>>>(B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2, B.pt3_ioff, T_PT3I,
+  launch(k_scan_apply, L.scan_grid, 512, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2, B.pt3_ioff, T_PT3I,
                                            0xFFFFFFFFu);
   mk(4);
-  k_pt3_items<<<L.grid, 256, 0, s>>>(B);
+  launch(k_pt3_items, L.grid, 256, 0, s, B);
   mk(36);
 }
 
 static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const ScanJobs& J, int n, Marker& mk) {
-  k_scan_reduce_multi<<<dim3(L.scan_grid, n), 512, 0, s>>>(J, B.hdr, B.scan_part);
+  launch(k_scan_reduce_multi, dim3(L.scan_grid, n), 512, 0, s, J, B.hdr, B.scan_part);
   mk(2);
-  k_scan_apply_multi<<<dim3(L.scan_grid, n), 512, 0, s>>>(J, B.hdr, B.scan_part);
+  launch(k_scan_apply_multi, dim3(L.scan_grid, n), 512, 0, s, J, B.hdr, B.scan_part);
   mk(4);
 }
 
@@ -2099,78 +2163,78 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   if (side) {  // the pLS preparation needs only the inputs: run it beside the OT chain
     cudaEventRecord(side->fork, s);
     cudaStreamWaitEvent(side->s, side->fork, 0);
-    k_pls_prep<<<g, 256, 0, side->s>>>(C, G, B);
+    launch(k_pls_prep, g, 256, 0, side->s, C, G, B);
     mk(15);
-    k_pls_sort<<<g, 128, 0, side->s>>>(B);
+    launch(k_pls_sort, g, 128, 0, side->s, B);
     mk(35);
   }
-  k_zero<<<g, 256, 0, s>>>(B.sen_cnt, &H->n_ev, two_nm, 1);
+  launch(k_zero, g, 256, 0, s, B.sen_cnt, &H->n_ev, two_nm, 1);
   mk(0);
-  k_hits_count<<<g, 256, 0, s>>>(G, B);
+  launch(k_hits_count, g, 256, 0, s, G, B);
   mk(1);
   scan(B, L, s, B.sen_cnt, B.sen_off, &H->n_ev, two_nm, T_HITS, 0xFFFFFFFFu, mk);
-  k_hits_scatter<<<g, 256, 0, s>>>(G, B);
+  launch(k_hits_scatter, g, 256, 0, s, G, B);
   mk(5);
-  k_hits_sort<<<g, 256, 0, s>>>(G, B);
+  launch(k_hits_sort, g, 256, 0, s, G, B);
   mk(6);
-  k_md_count<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_md_count, g, bs, 0, s, C, G, B);
   mk(7);
   scan(B, L, s, B.md_hcnt, B.md_hoff, &H->n_hits, 1, T_MD, B.cap_md, mk);
-  k_md_fill<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_md_fill, g, bs, 0, s, C, G, B);
   mk(8);
   if (side) {  // pT3 phase 1 needs the MDs and the pLS preparation only
     cudaEventRecord(side->mds, s);
     cudaStreamWaitEvent(side->s, side->mds, 0);
-    k_pt3_first_anchor<<<g, bs, 0, side->s>>>(C, G, B);
+    launch(k_pt3_first_anchor, g, bs, 0, side->s, C, G, B);
     mk(34);
     pt3_items(B, L, side->s, mk);
     cudaEventRecord(side->join, side->s);
   }
   const uint32_t lcap = L.ls_list_cap;
   const size_t ls_smem = lcap ? (bs / 32) * (lcap + LS_EXTRA_WORDS) * sizeof(uint32_t) : 0;
-  k_ls_count<<<g, bs, ls_smem, s>>>(C, G, B, lcap);
+  launch(k_ls_count, g, bs, ls_smem, s, C, G, B, lcap);
   mk(9);
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);
-  k_ls_fill<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_ls_fill, g, bs, 0, s, C, G, B);
   mk(10);
-  k_t3_count<<<g, 256, 0, s>>>(C, G, B);
+  launch(k_t3_count, g, 256, 0, s, C, G, B);
   mk(11);
   scan(B, L, s, B.t3_lcnt, B.t3_loff, &H->tot[T_LS], 1, T_T3, B.cap_t3, mk);
-  k_t3_fill<<<g, 256, 0, s>>>(C, G, B);
+  launch(k_t3_fill, g, 256, 0, s, C, G, B);
   mk(12);
-  k_t3_md_off<<<g, 256, 0, s>>>(B);
+  launch(k_t3_md_off, g, 256, 0, s, B);
   mk(32);
-  k_t5_count<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_t5_count, g, bs, 0, s, C, G, B);
   mk(13);
   scan(B, L, s, B.t5_tcnt, B.t5_toff, &H->tot[T_T3], 1, T_T5, B.cap_t5, mk);
-  k_t5_fill<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_t5_fill, g, bs, 0, s, C, G, B);
   mk(14);
-  k_t5_md_off<<<g, 256, 0, s>>>(B);
+  launch(k_t5_md_off, g, 256, 0, s, B);
   mk(33);
   if (side) {
     cudaStreamWaitEvent(s, side->join, 0);
   } else {
-    k_pls_prep<<<g, 256, 0, s>>>(C, G, B);
+    launch(k_pls_prep, g, 256, 0, s, C, G, B);
     mk(15);
-    k_pls_sort<<<g, 128, 0, s>>>(B);
+    launch(k_pls_sort, g, 128, 0, s, B);
     mk(35);
-    k_pt3_first_anchor<<<g, bs, 0, s>>>(C, G, B);
+    launch(k_pt3_first_anchor, g, bs, 0, s, C, G, B);
     mk(34);
     pt3_items(B, L, s, mk);
   }
-  k_pt3_count<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_pt3_count, g, bs, 0, s, C, G, B);
   mk(16);
   scan(B, L, s, B.pt3_xcnt, B.pt3_xoff, &H->tot[T_PT3I], 1, T_PT3, B.cap_pt3, mk);
-  k_pt3_fill<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_pt3_fill, g, bs, 0, s, C, G, B);
   mk(17);
-  k_pt5_count<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_pt5_count, g, bs, 0, s, C, G, B);
   mk(18);
   scan(B, L, s, B.pt5_xcnt, B.pt5_xoff, &H->tot[T_PT3], 1, T_PT5, B.cap_pt5, mk);
-  k_pt5_fill<<<g, bs, 0, s>>>(C, G, B);
+  launch(k_pt5_fill, g, bs, 0, s, C, G, B);
   mk(19);
-  k_zero3<<<g, 256, 0, s>>>(B.c5_cnt, B.c3_cnt, B.ct_cnt, H);
+  launch(k_zero3, g, 256, 0, s, B.c5_cnt, B.c3_cnt, B.ct_cnt, H);
   mk(20);
-  k_csr_count<<<g, 256, 0, s>>>(B);
+  launch(k_csr_count, g, 256, 0, s, B);
   mk(21);
   {
     ScanJobs J{};
@@ -2179,21 +2243,21 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     J.j[2] = {B.ct_cnt, B.ct_off, &H->tot[T_MD], T_CT, 5u * B.cap_t5};
     scan_multi(B, L, s, J, 3, mk);
   }
-  k_csr_fill<<<g, 256, 0, s>>>(B);
+  launch(k_csr_fill, g, 256, 0, s, B);
   mk(22);
-  k_kill_pt5<<<g, 256, 0, s>>>(B);
+  launch(k_kill_pt5, g, 256, 0, s, B);
   mk(23);
-  k_used5<<<g, 256, 0, s>>>(B);
+  launch(k_used5, g, 256, 0, s, B);
   mk(24);
-  k_cross_pt3<<<g, 256, 0, s>>>(B);
+  launch(k_cross_pt3, g, 256, 0, s, B);
   mk(25);
-  k_kill_pt3<<<g, 256, 0, s>>>(B);
+  launch(k_kill_pt3, g, 256, 0, s, B);
   mk(26);
-  k_used3<<<g, 256, 0, s>>>(B);
+  launch(k_used3, g, 256, 0, s, B);
   mk(27);
-  k_cross_t5<<<g, 256, 0, s>>>(B);
+  launch(k_cross_t5, g, 256, 0, s, B);
   mk(28);
-  k_kill_t5<<<g, 256, 0, s>>>(B);
+  launch(k_kill_t5, g, 256, 0, s, B);
   mk(29);
   {
     ScanJobs J{};
@@ -2203,9 +2267,9 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     J.j[3] = {B.plstc, B.sap, &H->n_pls, T_AP, 0xFFFFFFFFu};
     scan_multi(B, L, s, J, 4, mk);
   }
-  k_tc_offsets<<<1, 1024, 0, s>>>(G, B);
+  launch(k_tc_offsets, 1, 1024, 0, s, G, B);
   mk(30);
-  k_tc_write<<<g, 256, 0, s>>>(C, G, B);
+  launch(k_tc_write, g, 256, 0, s, C, G, B);
   mk(31);
   return mk.nk;
 }
