@@ -208,6 +208,43 @@ def test_launch_configuration_invariance(built, full_geom):
         assert tc == ref, (bs, bps)
 
 
+def test_ls_without_stored_partner_lists(built, full_geom, ora_full):
+    # ls_list_cap 1 (no shared-memory list) sends every module to the per-MD LS join, which
+    # stores no partner lists, so the fill pass joins every anchor again; 4 mixes both paths
+    ev = S.make_event("pu200", 13, n_tracks=1500, with_pls=True)
+    ora = oracle.run(ora_full, ev)
+    for cap in (1, 4):
+        s = lst.Session(full_geom.modules, keep_objects=True, ls_list_cap=cap)
+        compare(s, s.run_event(ev), ora, ev, f"ls_list_cap {cap}")
+        s.close()
+
+
+def test_pls_with_many_first_anchor_mds(built, full_geom, ora_full):
+    # one exact 5 GeV track plus 11 extra hits on each sensor of its first-layer module,
+    # within 20 um of its crossing: 144 MDs there all pass the pLS's first-anchor window
+    # (more than the 64 kept per pLS), so pT3 phase 2 takes the fallback over every T3 of
+    # the candidate modules, with more than 32 candidates per item
+    rng = np.random.default_rng(5)
+    t = E.random_tracks(rng, 1, pt_lo=5.0, pt_hi=5.0001, eta_max=0.3)
+    ev = E.event_from_tracks(full_geom, t, 3, exact=True, with_pls=True, fake_pls_frac=0.0, shuffle=False)
+    _, _, mod, sen, x, y, z = E.track_crossings(full_geom, t)
+    r = np.hypot(x, y)
+    xs, ys, zs, ds = [ev.x], [ev.y], [ev.z], [ev.det]
+    for i in np.argsort(r)[:2]:
+        phi = np.arctan2(y[i], x[i]) + rng.normal(0, 0.002 / r[i], 11)
+        xs.append((r[i] * np.cos(phi)).astype(np.float32))
+        ys.append((r[i] * np.sin(phi)).astype(np.float32))
+        zs.append((z[i] + rng.normal(0, 0.002, 11)).astype(np.float32))
+        ds.append(np.full(11, 2 * mod[i] + sen[i], np.uint32))
+    ev = E.Event(np.concatenate(xs), np.concatenate(ys), np.concatenate(zs), np.concatenate(ds),
+                 np.concatenate([ev.sim, np.full(22, -1, np.int32)]), ev.tracks, ev.pls)
+    ora = oracle.run(ora_full, ev)
+    assert (ora["md"][:, 0] == mod[np.argmin(r)]).sum() >= 144 and len(ora["pt3"]) > 64
+    s = lst.Session(full_geom.modules, keep_objects=True)
+    compare(s, s.run_event(ev), ora, ev, "dense first layer")
+    s.close()
+
+
 def test_graph_and_eager_launches_agree(built, full_geom, ora_full):
     # the per-event path replays the context's graph; use_graph = 2 launches stream-ordered
     ev = S.make_event("pu200", 11, n_tracks=1200, with_pls=True)
