@@ -1,17 +1,19 @@
 // Stage kernels of the LST chain on sm_103a (arXiv:2407.18231, Sec. 1).
 //
-// Design: every object-producing stage is a "join" over a work unit (a module, an MD or a
-// pLS) whose candidates are the concatenation of a few contiguous index ranges.  One warp
-// owns a unit: it scans the range lengths with shuffles, walks the flattened candidates 32
-// at a time (each lane finds its range by a shuffle binary search), tests them, and
-// compacts the passing ones with ballot + popc into the unit's slice of the output.  A
-// count pass sizes every unit, a device-wide scan turns sizes into offsets, and a fill
-// pass re-runs the tests and writes.  Output order is therefore fixed by the inputs (unit
-// order, then candidate order) and never by scheduling, no list is truncated, and every
-// object list ends up sorted by its first MD -- which makes "all T3s starting on module M"
-// a single contiguous range for the pLS joins.  All grids are persistent (a multiple of the
-// SM count) and read their sizes from the device-side batch header, so one CUDA graph
-// replays any batch that fits the buffers.
+// Design: every object-producing stage is a join over small work units (a lower hit, an
+// anchor MD, an LS, a T3, a (pLS, MD) item, a pT3) whose candidates are a few contiguous
+// index ranges.  A warp takes a unit, or 32 consecutive units, scans their range lengths
+// with shuffles, walks the concatenated candidates 32 at a time (each lane finds its unit
+// by a shuffle binary search), tests them and counts the passes with ballot + popc.  A
+// count pass sizes every unit (keeping pass bits or partner lists where they fit), a
+// device-wide scan turns sizes into offsets, and a fill pass writes each unit's slice of
+// the output from what the count pass kept, testing again only where nothing was kept.
+// Output order is therefore fixed by the inputs (unit order, then candidate order) and
+// never by scheduling, no list is truncated, and every object list ends up sorted by its
+// first MD -- which makes "all T3s starting on module M" a single contiguous range for
+// the pLS joins.  All grids are persistent (a multiple of the SM count) and read their
+// sizes from the device-side batch header, so one CUDA graph replays any batch that fits
+// the buffers.
 #include <cuda_runtime.h>
 
 #include <utility>
