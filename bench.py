@@ -180,9 +180,13 @@ def aggregate(elapsed_ms: float, events_per_rank: int):
 
 # ---------------------------------------------------------------- roofline
 def kernel_hash():
+    """Hash of the kernel sources' code: comments and blank lines do not count."""
     h = hashlib.sha1()
     for p in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        src = open(os.path.join(ROOT, p)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(l.rstrip() for l in src.splitlines() if l.strip()).encode())
     return h.hexdigest()[:12]
 
 
