@@ -257,6 +257,7 @@ def main():
     ws, rank, local = dist_env()
     import torch
     import paper_2407_18231_gb300 as lst
+    from paper_2407_18231_gb300 import validation as V
     import lst_synth as S
     if ws > 1:
         import torch.distributed as dist
@@ -364,6 +365,26 @@ def main():
                                               for b in batches])),
            "d2h_bytes_per_step": int(d2h / e2e_steps), "api": "lst_submit_batch / lst_collect_batch, one batch in flight"}
 
+    # ---- physics: track-level metrics (Sec. 3) of the first batch's candidates, not timed
+    phys_ids = sess_h.run_batch(batches[0])
+    tcs, counts = sess_h.candidates_batch(phys_ids)
+    for i in phys_ids:
+        sess_h.release(i)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    c_all, c_ot = [], []
+    for k, e in enumerate(batches[0]):
+        tc = tcs[offs[k]:offs[k + 1]]
+        sel = (e.tracks["pt"] >= 0.9) & (np.abs(e.tracks["eta"]) < 2.4)
+        c_all.append(V.event_counts(tc, e.sim, e.pls_sim, len(e.tracks), sel))
+        c_ot.append(V.event_counts(tc[tc["type"] != lst.TC_PLS], e.sim, e.pls_sim, len(e.tracks), sel))
+    r_all, r_ot = V.rates(c_all), V.rates(c_ot)
+    physics = {"events": B, "selection": "simulated tracks with pT >= 0.9 GeV and |eta| < 2.4",
+               "match": "more than 75 % of a candidate's hits from one simulated track (Sec. 3)",
+               "efficiency": r_all["efficiency"], "fake_rate": r_all["fake_rate"],
+               "duplicate_rate": r_all["duplicate_rate"],
+               "without_pls_only": {"efficiency": r_ot["efficiency"], "fake_rate": r_ot["fake_rate"],
+                                    "duplicate_rate": r_ot["duplicate_rate"]}}
+
     # ---- per-event launch: latency of single events
     per_event = None
     if args.per_event:
@@ -456,7 +477,7 @@ def main():
                    "tuning": tuning or "defaults",
                    "l2": "256 MB buffer written between timed steps; inputs rotate over "
                          f"{P} resident batches"},
-        "e2e": e2e, "per_event": per_event, "served": served,
+        "e2e": e2e, "per_event": per_event, "served": served, "physics": physics,
         "objects_per_step": {k: stats[k] for k in ("n_md", "n_ls", "n_t3", "n_t5", "n_pt3", "n_pt5", "n_tc")},
         "roofline": roof, "kernel_ms_per_step": kernel_times, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": kernels_per_step * args.steps,

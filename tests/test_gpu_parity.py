@@ -245,6 +245,28 @@ def test_pls_with_many_first_anchor_mds(built, full_geom, ora_full):
     s.close()
 
 
+def test_track_metrics_from_batched_candidates(built, full_geom, ora_full):
+    # the Sec. 3 metrics of a batch's candidates (split per event by the batch counts) equal
+    # those of the oracle's candidates
+    from paper_2407_18231_gb300 import validation as V
+    evs = [S.make_event("pu200", 20 + i, n_tracks=1200, with_pls=True) for i in range(3)]
+    s = lst.Session(full_geom.modules)
+    ids = s.run_batch(evs)
+    tcs, counts = s.candidates_batch(ids)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    for k, ev in enumerate(evs):
+        r = oracle.run(ora_full, ev)
+        tc_o = np.zeros(len(r["tc_type"]), lst.TC_DTYPE)
+        tc_o["ot"] = r["tc_ot"]
+        tc_o["pix"] = r["tc_pix"]
+        got = V.event_counts(tcs[offs[k]:offs[k + 1]], ev.sim, ev.pls_sim, len(ev.tracks))
+        exp = V.event_counts(tc_o, ev.sim, ev.pls_sim, len(ev.tracks))
+        assert {a: b for a, b in got.items() if a != "matched_per_sim"} == \
+            {a: b for a, b in exp.items() if a != "matched_per_sim"}
+        assert np.array_equal(got["matched_per_sim"], exp["matched_per_sim"])
+    s.close()
+
+
 def test_graph_and_eager_launches_agree(built, full_geom, ora_full):
     # the per-event path replays the context's graph; use_graph = 2 launches stream-ordered
     ev = S.make_event("pu200", 11, n_tracks=1200, with_pls=True)
