@@ -370,7 +370,7 @@ def main():
     tcs, counts = sess_h.candidates_batch(phys_ids)
     for i in phys_ids:
         sess_h.release(i)
-    offs = np.concatenate([[0], np.cumsum(counts)])
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     c_all, c_ot = [], []
     for k, e in enumerate(batches[0]):
         tc = tcs[offs[k]:offs[k + 1]]

@@ -253,7 +253,7 @@ def test_track_metrics_from_batched_candidates(built, full_geom, ora_full):
     s = lst.Session(full_geom.modules)
     ids = s.run_batch(evs)
     tcs, counts = s.candidates_batch(ids)
-    offs = np.concatenate([[0], np.cumsum(counts)])
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     for k, ev in enumerate(evs):
         r = oracle.run(ora_full, ev)
         tc_o = np.zeros(len(r["tc_type"]), lst.TC_DTYPE)
