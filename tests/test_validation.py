@@ -79,3 +79,27 @@ def test_oracle_candidates_resolution_event(barrel_geom, ora_barrel):
     assert rates["efficiency"] >= 0.9
     assert rates["fake_rate"] <= 0.05
     assert rates["duplicate_rate"] <= 0.1
+
+
+def test_displaced_track_efficiency_ends_where_t5s_end(barrel_geom, ora_barrel):
+    # Sec. 3: T5-based candidates accept displaced tracks, with an endpoint where fewer
+    # than five surfaces remain.  Tracks produced inside the first layer are found; tracks
+    # produced beyond the second layer (four layers left) are not.
+    G = E.G  # the synthetic geometry's constants
+    rng = np.random.default_rng(3)
+    n = 400
+    t = E.random_tracks(rng, n, pt_mode="uniform", pt_lo=2.0, pt_hi=10.0, eta_max=0.5)
+    rv = rng.uniform(0, 60, n)
+    ang = t["phi0"] + rng.normal(0, 0.05, n)
+    t["vx"], t["vy"], t["vz"] = rv * np.cos(ang), rv * np.sin(ang), rng.normal(0, 5, n)
+    ev = E.event_from_tracks(barrel_geom, t, 3, exact=False)
+    r = oracle.run(ora_barrel, ev)
+    tc = np.zeros(len(r["tc_type"]), TC_DTYPE)
+    tc["ot"] = r["tc_ot"]
+    tc["pix"] = r["tc_pix"]
+    c = V.event_counts(tc, ev.sim, ev.pls_sim, n_sim=n)
+    r1 = G.BARREL_R[0]
+    r2 = G.BARREL_R[1] + G.BARREL_GAP[1]
+    eff = V.efficiency_by(rv, c["matched_per_sim"], np.array([0.0, r1 - 1.0, r2 + 1.0, 60.0]))
+    assert eff[0] >= 0.85
+    assert eff[2] <= 0.05
