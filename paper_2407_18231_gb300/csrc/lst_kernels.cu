@@ -362,17 +362,6 @@ __global__ void k_zero(uint32_t* p, const uint32_t* nptr, uint32_t mul, uint32_t
   THREAD_LOOP(i, n) p[i] = 0u;
 }
 
-__global__ void k_zero3(uint32_t* a, uint32_t* b, uint32_t* c, const Hdr* H) {
-  pdl_wait();
-  if (H->err) return;
-  const uint32_t n = H->tot[T_MD] + 1;
-  THREAD_LOOP(i, n) {
-    a[i] = 0u;
-    b[i] = 0u;
-    c[i] = 0u;
-  }
-}
-
 // ------------------------------------------------------------------ hit binning
 // Count hits per (event, sensor); validate module ids and coordinates.
 __global__ void k_hits_count(GeoView G, BufView B) {
@@ -927,11 +916,13 @@ __global__ void __launch_bounds__(512) k_t3_count(MethodConst C, GeoView G, BufV
 }
 
 // Fill pass, one thread per LS: with at most 32 candidates the count pass's pass bits say
-// which candidates pass (no test), otherwise they are tested again.
+// which candidates pass (no test), otherwise they are tested again.  Also writes the T3s
+// starting at each MD a (those of the LSs leaving a): t3_off[a] = t3_loff[ls_off[a]].
 __global__ void __launch_bounds__(512) k_t3_fill(MethodConst C, GeoView G, BufView B) {
   pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
+  THREAD_LOOP(a, H->tot[T_MD] + 1) B.t3_off[a] = B.t3_loff[B.ls_off[a]];
   const uint32_t n = H->tot[T_LS];
   THREAD_LOOP(l, n) {
     uint32_t k = B.t3_loff[l];
@@ -955,14 +946,6 @@ __global__ void __launch_bounds__(512) k_t3_fill(MethodConst C, GeoView G, BufVi
       if (t3_select(C, pa, pb, pbu, md_point(B, c))) emit(c);
     }
   }
-}
-
-// T3s starting at MD a = T3s of the LSs leaving a: t3_off[a] = t3_loff[ls_off[a]].
-__global__ void k_t3_md_off(BufView B) {
-  pdl_wait();
-  const Hdr* H = B.hdr;
-  if (H->err) return;
-  THREAD_LOOP(a, H->tot[T_MD] + 1) B.t3_off[a] = B.t3_loff[B.ls_off[a]];
 }
 
 // ------------------------------------------------------------------ T5
@@ -1031,11 +1014,19 @@ __device__ __forceinline__ void t5_emit(const MethodConst& C, const BufView& B, 
 }
 
 // Fill pass: passes of T3s with at most 32 candidates come from the stored bits (the score
-// and curvature of each are computed once), the others are tested again.
+// and curvature of each are computed once), the others are tested again.  Also writes the
+// T5s starting at each MD a, t5_off[a] = t5_toff[t3_off[a]], and zeroes the per-MD counts
+// of the duplicate-removal lists (untouched until then).
 __global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufView B) {
   pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
+  THREAD_LOOP(a, H->tot[T_MD] + 1) {
+    B.t5_off[a] = B.t5_toff[B.t3_off[a]];
+    B.c5_cnt[a] = 0u;
+    B.c3_cnt[a] = 0u;
+    B.ct_cnt[a] = 0u;
+  }
   const uint32_t n = H->tot[T_T3];
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
@@ -1099,14 +1090,6 @@ __global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufVi
       }
     }
   }
-}
-
-// T5s starting at MD a: t5_off[a] = t5_toff[t3_off[a]].
-__global__ void k_t5_md_off(BufView B) {
-  pdl_wait();
-  const Hdr* H = B.hdr;
-  if (H->err) return;
-  THREAD_LOOP(a, H->tot[T_MD] + 1) B.t5_off[a] = B.t5_toff[B.t3_off[a]];
 }
 
 // ------------------------------------------------------------------ pLS module lookup
@@ -2088,9 +2071,9 @@ __global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
 const char* const kKernelNames[] = {
     "zero_sensor_counts", "hits_count", "scan_reduce", "(unused)", "scan_apply", "hits_scatter", "hits_sort",
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
-    "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "zero_md_lists", "md_lists_count", "md_lists_fill",
+    "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "(unused)", "md_lists_count", "md_lists_fill",
     "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
-    "t3_md_offsets", "t5_md_offsets", "pt3_first_anchor", "pls_sort", "pt3_items"};
+    "(unused)", "(unused)", "pt3_first_anchor", "pls_sort", "pt3_items"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Marker {
@@ -2204,15 +2187,11 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.t3_lcnt, B.t3_loff, &H->tot[T_LS], 1, T_T3, B.cap_t3, mk);
   launch(k_t3_fill, g, 256, 0, s, C, G, B);
   mk(12);
-  launch(k_t3_md_off, g, 256, 0, s, B);
-  mk(32);
   launch(k_t5_count, g, bs, 0, s, C, G, B);
   mk(13);
   scan(B, L, s, B.t5_tcnt, B.t5_toff, &H->tot[T_T3], 1, T_T5, B.cap_t5, mk);
   launch(k_t5_fill, g, bs, 0, s, C, G, B);
   mk(14);
-  launch(k_t5_md_off, g, 256, 0, s, B);
-  mk(33);
   if (side) {
     cudaStreamWaitEvent(s, side->join, 0);
   } else {
@@ -2234,8 +2213,6 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.pt5_xcnt, B.pt5_xoff, &H->tot[T_PT3], 1, T_PT5, B.cap_pt5, mk);
   launch(k_pt5_fill, g, bs, 0, s, C, G, B);
   mk(19);
-  launch(k_zero3, g, 256, 0, s, B.c5_cnt, B.c3_cnt, B.ct_cnt, H);
-  mk(20);
   launch(k_csr_count, g, 256, 0, s, B);
   mk(21);
   {
