@@ -110,7 +110,7 @@ struct BufView {
   float *pt5_score;
   // duplicate removal: MD -> object lists and flags (u32 so they can be scanned)
   uint32_t *c5_cnt, *c5_off, *c5_list, *c3_cnt, *c3_off, *c3_list, *ct_cnt, *ct_off, *ct_list;
-  uint32_t *alive5, *alive3, *alivet, *plstc, *used5, *used3, *cross3, *crosst;
+  uint32_t *alive5, *alive3, *alivet, *plstc, *cross3, *crosst;
   uint32_t *sa5, *sa3, *sat, *sap;  // exclusive scans of the alive flags
   // track candidates
   uint32_t *tc_ev_off;

@@ -484,7 +484,7 @@ struct Pipeline {
   DevBuf pt3_icnt, pt3_ioff, pt3_item_p, pt3_xcnt, pt3_xoff, pt3_xmask, pt3_off, pt3_pls, pt3_obj, pt3_score;
   DevBuf pt5_xcnt, pt5_xoff, pt5_xmask, pt5_off, pt5_pls, pt5_obj, pt5_score;
   DevBuf c5_cnt, c5_off, c5_list, c3_cnt, c3_off, c3_list, ct_cnt, ct_off, ct_list;
-  DevBuf alive5, alive3, alivet, plstc, used5, used3, cross3, crosst, sa5, sa3, sat, sap;
+  DevBuf alive5, alive3, alivet, plstc, cross3, crosst, sa5, sa3, sat, sap;
   DevBuf tc_ev_off, tc, scan_part, scan_part2, mask, mask_off;
   uint32_t cap_mask = 0;
   // host staging (pinned)
@@ -526,7 +526,7 @@ struct Pipeline {
                               &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_icnt, &pt3_ioff, &pt3_item_p, &pt3_xcnt, &pt3_xoff, &pt3_xmask, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
                               &pt5_xcnt, &pt5_xoff, &pt5_xmask, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
                               &c3_cnt, &c3_off, &c3_list, &ct_cnt, &ct_off, &ct_list, &alive5, &alive3, &alivet,
-                              &plstc, &used5, &used3, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
+                              &plstc, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
                               &scan_part, &scan_part2, &mask, &mask_off};
     for (auto& b : t5_m) v.push_back(&b);
     return v;
@@ -694,8 +694,6 @@ struct Pipeline {
     need<uint32_t>(alive3, c.pt3);
     need<uint32_t>(alivet, c.t5);
     need<uint32_t>(plstc, c.pls);
-    need<uint32_t>(used5, c.pls);
-    need<uint32_t>(used3, c.pls);
     need<uint32_t>(cross3, c.pt3);
     need<uint32_t>(crosst, c.t5);
     need<uint32_t>(sa5, c.pt5 + 1);
@@ -795,7 +793,7 @@ struct Pipeline {
     v.c3_cnt = P32(c3_cnt); v.c3_off = P32(c3_off); v.c3_list = P32(c3_list);
     v.ct_cnt = P32(ct_cnt); v.ct_off = P32(ct_off); v.ct_list = P32(ct_list);
     v.alive5 = P32(alive5); v.alive3 = P32(alive3); v.alivet = P32(alivet); v.plstc = P32(plstc);
-    v.used5 = P32(used5); v.used3 = P32(used3); v.cross3 = P32(cross3); v.crosst = P32(crosst);
+    v.cross3 = P32(cross3); v.crosst = P32(crosst);
     v.sa5 = P32(sa5); v.sa3 = P32(sa3); v.sat = P32(sat); v.sap = P32(sap);
     v.tc_ev_off = P32(tc_ev_off); v.tc = tc.p; v.scan_part = P32(scan_part); v.scan_part2 = P32(scan_part2);
     v.mask = P32(mask); v.mask_off = P32(mask_off); v.cap_mask = cap_mask;

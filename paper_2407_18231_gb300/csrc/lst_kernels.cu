@@ -1812,15 +1812,11 @@ __global__ void k_kill_pt5(BufView B) {
   }
 }
 
-__global__ void k_used5(BufView B) {
-  pdl_wait();
-  const Hdr* H = B.hdr;
-  if (H->err) return;
-  THREAD_LOOP(p, H->n_pls) {
-    uint32_t u = 0;
-    for (uint32_t y = B.pt5_off[p]; y < B.pt5_off[p + 1]; y++) u |= B.alive5[y];
-    B.used5[p] = u;
-  }
+// Is pLS p used by a surviving pT5?
+__device__ __forceinline__ bool pls_used5(const BufView& B, uint32_t p) {
+  for (uint32_t y = B.pt5_off[p]; y < B.pt5_off[p + 1]; y++)
+    if (B.alive5[y]) return true;
+  return false;
 }
 
 // pT3 across stages: its pLS is used by a surviving pT5, or it shares >= 2 MDs with one.
@@ -1829,7 +1825,7 @@ __global__ void k_cross_pt3(BufView B) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   THREAD_LOOP(x, H->tot[T_PT3]) {
-    bool dead = B.used5[B.pt3_pls[x]] != 0;
+    bool dead = pls_used5(B, B.pt3_pls[x]);
     uint32_t mx[3];
     t3_mds(B, B.pt3_obj[x], mx);
     // sharing >= 2 of x's 3 MDs means sharing one of any 2 of them
@@ -1874,24 +1870,18 @@ __global__ void k_kill_pt3(BufView B) {
   }
 }
 
-__global__ void k_used3(BufView B) {
-  pdl_wait();
-  const Hdr* H = B.hdr;
-  if (H->err) return;
-  THREAD_LOOP(p, H->n_pls) {
-    uint32_t u = 0;
-    for (uint32_t y = B.pt3_off[p]; y < B.pt3_off[p + 1]; y++) u |= B.alive3[y];
-    B.used3[p] = u;
-    B.plstc[p] = (u | B.used5[p]) ? 0u : 1u;
-  }
-}
-
 // T5 across stages: shares >= 3 MDs with a surviving pT5 or pT3 (one of any three of its
-// MDs is then shared).  One warp per T5.
+// MDs is then shared).  A group of lanes per T5.  Also flags the pLSs that become track
+// candidates themselves: those used by no surviving pT5 or pT3.
 __global__ void k_cross_t5(BufView B) {
   pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
+  THREAD_LOOP(p, H->n_pls) {
+    bool used = pls_used5(B, p);
+    for (uint32_t y = B.pt3_off[p]; y < B.pt3_off[p + 1] && !used; y++) used = B.alive3[y] != 0;
+    B.plstc[p] = used ? 0u : 1u;
+  }
   GROUP_LOOP(x, act, H->tot[T_T5], CROSS_T5_GROUP) {
     uint32_t mx[5] = {0, 0, 0, 0, 0};
     if (act) t5_mds(B, x, mx);
@@ -2072,7 +2062,7 @@ const char* const kKernelNames[] = {
     "zero_sensor_counts", "hits_count", "scan_reduce", "(unused)", "scan_apply", "hits_scatter", "hits_sort",
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "(unused)", "md_lists_count", "md_lists_fill",
-    "kill_pt5", "used_pt5", "cross_pt3", "kill_pt3", "used_pt3", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
+    "kill_pt5", "(unused)", "cross_pt3", "kill_pt3", "(unused)", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
     "(unused)", "(unused)", "pt3_first_anchor", "pls_sort", "pt3_items"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
@@ -2226,14 +2216,10 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   mk(22);
   launch(k_kill_pt5, g, 256, 0, s, B);
   mk(23);
-  launch(k_used5, g, 256, 0, s, B);
-  mk(24);
   launch(k_cross_pt3, g, 256, 0, s, B);
   mk(25);
   launch(k_kill_pt3, g, 256, 0, s, B);
   mk(26);
-  launch(k_used3, g, 256, 0, s, B);
-  mk(27);
   launch(k_cross_t5, g, 256, 0, s, B);
   mk(28);
   launch(k_kill_t5, g, 256, 0, s, B);

@@ -145,8 +145,6 @@ size_t carve(char* base, BufView& B) {
   B.alive3 = c.take<uint32_t>(MAX_PT3);
   B.alivet = c.take<uint32_t>(MAX_T5);
   B.plstc = c.take<uint32_t>(MAX_PLS);
-  B.used5 = c.take<uint32_t>(MAX_PLS);
-  B.used3 = c.take<uint32_t>(MAX_PLS);
   B.cross3 = c.take<uint32_t>(MAX_PT3);
   B.crosst = c.take<uint32_t>(MAX_T5);
   B.sa5 = c.take<uint32_t>(MAX_PT5 + 1);
