@@ -83,6 +83,7 @@ struct BufView {
   float4 *md_pt;  // per MD, one 32-byte sector: [2m] lower hit (x, y, z, r), [2m + 1] module tolerances
   float4 *md_up4;
   float4 *md_dir4;  // upper - lower hit: dx, dy, transverse length, rho + rho
+  float4 *md_box;   // per unit: its MDs' lower-hit box, (x0, x1, y0, y1), (z0, z1, -, -)
   // LS
   uint32_t *ls_cnt, *ls_off, *ls_in, *ls_out;
   // T3: per LS count/offset of the T3s built on it, per MD offset of those starting there

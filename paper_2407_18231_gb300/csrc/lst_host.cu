@@ -476,7 +476,7 @@ struct Pipeline {
   // buffers
   DevBuf hdr, in_x, in_y, in_z, in_det, in_hoff, in_pls, in_poff;
   DevBuf sen_cnt, sen_off, hit_tmp, hit_ev, hit_idx, hit_sen, hit4;
-  DevBuf md_hcnt, md_hoff, md_hmask, md_off, md_unit, md_lo_idx, md_up_idx, md_pt, md_up4, md_dir4;
+  DevBuf md_hcnt, md_hoff, md_hmask, md_box, md_off, md_unit, md_lo_idx, md_up_idx, md_pt, md_up4, md_dir4;
   DevBuf ls_cnt, ls_off, ls_in, ls_out;
   DevBuf t3_lcnt, t3_loff, t3_off, t3_a, t3_b, t3_c, t3_mask, t3_md4;
   DevBuf t5_tcnt, t5_toff, t5_off, t5_m[5], t5_score, t5_kfull, t5_mask, t5_md8;
@@ -520,7 +520,7 @@ struct Pipeline {
 
   std::vector<DevBuf*> all_buffers() {
     std::vector<DevBuf*> v = {&hdr, &in_x, &in_y, &in_z, &in_det, &in_hoff, &in_pls, &in_poff, &sen_cnt, &sen_off,
-                              &hit_tmp, &hit_ev, &hit_idx, &hit_sen, &hit4, &md_hcnt, &md_hoff, &md_hmask, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
+                              &hit_tmp, &hit_ev, &hit_idx, &hit_sen, &hit4, &md_hcnt, &md_hoff, &md_hmask, &md_box, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
                               &md_pt, &md_up4, &md_dir4, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off, &t3_mask, &t5_mask, &t3_md4, &t5_md8,
                               &t3_a, &t3_b, &t3_c, &t5_tcnt, &t5_toff, &t5_off, &t5_score, &t5_kfull, &pls_ev,
                               &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_icnt, &pt3_ioff, &pt3_item_p, &pt3_xcnt, &pt3_xoff, &pt3_xmask, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
@@ -630,6 +630,7 @@ struct Pipeline {
     need<uint32_t>(md_hoff, c.hits + 1);
     need<uint32_t>(md_hmask, c.hits);
     need<uint32_t>(md_off, c.ev * nm + 1);
+    need<float4>(md_box, 2 * (size_t)c.ev * nm);
     need<uint32_t>(md_unit, c.md);
     need<uint32_t>(md_lo_idx, c.md);
     need<uint32_t>(md_up_idx, c.md);
@@ -770,7 +771,7 @@ struct Pipeline {
 #define P32(x) (uint32_t*)x.p
     v.sen_cnt = P32(sen_cnt); v.sen_off = P32(sen_off); v.hit_tmp = P32(hit_tmp); v.hit_ev = P32(hit_ev);
     v.hit_idx = P32(hit_idx); v.hit4 = (float4*)hit4.p;
-    v.md_hcnt = P32(md_hcnt); v.md_hoff = P32(md_hoff); v.md_hmask = P32(md_hmask); v.hit_sen = P32(hit_sen); v.md_off = P32(md_off); v.md_unit = P32(md_unit); v.md_lo_idx = P32(md_lo_idx);
+    v.md_hcnt = P32(md_hcnt); v.md_hoff = P32(md_hoff); v.md_hmask = P32(md_hmask); v.md_box = (float4*)md_box.p; v.hit_sen = P32(hit_sen); v.md_off = P32(md_off); v.md_unit = P32(md_unit); v.md_lo_idx = P32(md_lo_idx);
     v.md_up_idx = P32(md_up_idx); v.md_pt = (float4*)md_pt.p; v.md_up4 = (float4*)md_up4.p;
     v.md_dir4 = (float4*)md_dir4.p;
     v.ls_cnt = P32(ls_cnt); v.ls_off = P32(ls_off); v.ls_in = P32(ls_in); v.ls_out = P32(ls_out);

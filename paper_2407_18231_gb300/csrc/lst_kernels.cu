@@ -1331,6 +1331,59 @@ __device__ __forceinline__ void t3_mds(const BufView& B, uint32_t t, uint32_t m[
 // ------------------------------------------------------------------ pT3 / pT5
 constexpr uint32_t PT3_RING = 64;    // queued pre-rejection survivors per warp (> 31 + 32)
 
+// Per unit (event, module): the bounding box of its MDs' lower hits, (x0, x1, y0, y1) and
+// (z0, z1, -, -), for pT3 phase 1's module-level pruning.  An empty unit's box is unused.
+__global__ void k_md_box(GeoView G, BufView B) {
+  pdl_wait();
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  THREAD_LOOP(u, H->n_ev * G.nm) {
+    float x0 = 3.0e38f, x1 = -3.0e38f, y0 = 3.0e38f, y1 = -3.0e38f, z0 = 3.0e38f, z1 = -3.0e38f;
+    for (uint32_t m = B.md_off[u]; m < B.md_off[u + 1]; m++) {
+      const float4 p = B.md_pt[2 * (size_t)m];
+      x0 = fminf(x0, p.x);
+      x1 = fmaxf(x1, p.x);
+      y0 = fminf(y0, p.y);
+      y1 = fmaxf(y1, p.y);
+      z0 = fminf(z0, p.z);
+      z1 = fmaxf(z1, p.z);
+    }
+    B.md_box[2 * (size_t)u] = make_float4(x0, x1, y0, y1);
+    B.md_box[2 * (size_t)u + 1] = make_float4(z0, z1, 0.0f, 0.0f);
+  }
+}
+
+// Can an MD whose lower hit lies in box (bxy: x0, x1, y0, y1; bz: z0, z1) on a module with
+// tolerances t pass pls_anchor_accept for helix h?  Both of its windows are bounded over
+// the box: the arc length s from the reference point lies in [chord_min, 1.6 chord_max]
+// (s >= chord, and s <= 1.6 chord up to half a turn), so the r-phi window is at most its
+// value at 1.6 chord_max and the r-z window at most its value at that s; the r-phi
+// residual is at least the distance between the circle and the box, and the r-z residual
+// at least the distance between the box's z range and z0 + s cot over that s range.  A
+// false answer is certain: the margins (1 % plus 2e-2 cm plus 4e-6 of the lengths
+// involved) exceed the float rounding of both sides.
+__device__ __forceinline__ bool pls_module_maybe(const MethodConst& C, const PlsHelix& h, const float4& bxy,
+                                                 const float4& bz, const float4& t) {
+  // distances from the reference point (chord) and from the circle's centre to the box
+  const float px = fmaxf(fmaxf(bxy.x - h.x0, h.x0 - bxy.y), 0.0f), py = fmaxf(fmaxf(bxy.z - h.y0, h.y0 - bxy.w), 0.0f);
+  const float ch_lo = sqrtf(px * px + py * py);
+  const float fx = fmaxf(fabsf(bxy.x - h.x0), fabsf(bxy.y - h.x0)), fy = fmaxf(fabsf(bxy.z - h.y0), fabsf(bxy.w - h.y0));
+  const float ch_hi = sqrtf(fx * fx + fy * fy);
+  const float qx = fmaxf(fmaxf(bxy.x - h.cx, h.cx - bxy.y), 0.0f), qy = fmaxf(fmaxf(bxy.z - h.cy, h.cy - bxy.w), 0.0f);
+  const float d_lo = sqrtf(qx * qx + qy * qy);
+  const float gx = fmaxf(fabsf(bxy.x - h.cx), fabsf(bxy.y - h.cx)), gy = fmaxf(fabsf(bxy.z - h.cy), fabsf(bxy.w - h.cy));
+  const float d_hi = sqrtf(gx * gx + gy * gy);
+  const float slack = 0.02f + 4.0e-6f * (h.R + d_hi + ch_hi);
+  const float s_lo = ch_lo, s_hi = 1.6f * ch_hi;
+  const float wphi = C.W0 + 0.003f * s_hi + 0.015f * s_hi * s_hi / h.R + t.y;
+  const float rphi = fmaxf(fmaxf(d_lo - h.R, h.R - d_hi), 0.0f);
+  if (rphi > wphi * 1.01f + slack) return false;
+  const float zp0 = h.z0 + fminf(s_lo * h.cot, s_hi * h.cot), zp1 = h.z0 + fmaxf(s_lo * h.cot, s_hi * h.cot);
+  const float rz = fmaxf(fmaxf(bz.x - zp1, zp0 - bz.y), 0.0f);
+  const float wz = 0.05f + 0.002f * s_hi + t.x + t.y * fabsf(h.cot);
+  return !(rz > wz * 1.01f + slack + 4.0e-6f * (fabsf(h.z0) + fabsf(bz.x) + fabsf(bz.y) + s_hi * fabsf(h.cot)));
+}
+
 // pT3 phase 1 (Sec. 1: pLS + T3), on its own so that it can run beside the LS, T3 and T5
 // stages (it needs only the MDs and the pLS preparation).  Unit = pLS p, one warp: the
 // first-anchor window on every MD of p's candidate modules; a cheap pre-rejection runs on
@@ -1369,9 +1422,11 @@ __global__ void __launch_bounds__(512) k_pt3_first_anchor(MethodConst C, GeoView
       for (uint32_t g0 = 0; g0 < nc; g0 += 32) {
         uint32_t b = 0, c = 0;
         if (g0 + lane < nc) {
-          const uint32_t u = ubase + cand[g0 + lane];
+          const uint32_t mod = cand[g0 + lane], u = ubase + mod;
           b = B.md_off[u];
           c = B.md_off[u + 1] - b;
+          // a module none of whose MDs can pass the window holds no first anchor
+          if (c && !pls_module_maybe(C, h, B.md_box[2 * (size_t)u], B.md_box[2 * (size_t)u + 1], G.modc[mod])) c = 0;
         }
         const uint32_t incl = warp_incl_scan(c);
         const uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -2063,7 +2118,7 @@ const char* const kKernelNames[] = {
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "(unused)", "md_lists_count", "md_lists_fill",
     "kill_pt5", "(unused)", "cross_pt3", "kill_pt3", "(unused)", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
-    "(unused)", "(unused)", "pt3_first_anchor", "pls_sort", "pt3_items"};
+    "(unused)", "(unused)", "pt3_first_anchor", "pls_sort", "pt3_items", "md_boxes"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Marker {
@@ -2160,6 +2215,8 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   if (side) {  // pT3 phase 1 needs the MDs and the pLS preparation only
     cudaEventRecord(side->mds, s);
     cudaStreamWaitEvent(side->s, side->mds, 0);
+    launch(k_md_box, g, 256, 0, side->s, G, B);
+    mk(37);
     launch(k_pt3_first_anchor, g, bs, 0, side->s, C, G, B);
     mk(34);
     pt3_items(B, L, side->s, mk);
@@ -2189,6 +2246,8 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     mk(15);
     launch(k_pls_sort, g, 128, 0, s, B);
     mk(35);
+    launch(k_md_box, g, 256, 0, s, G, B);
+    mk(37);
     launch(k_pt3_first_anchor, g, bs, 0, s, C, G, B);
     mk(34);
     pt3_items(B, L, s, mk);

@@ -77,6 +77,7 @@ size_t carve(char* base, BufView& B) {
   B.md_hoff = c.take<uint32_t>(MAX_HITS + 1);
   B.md_hmask = c.take<uint32_t>(MAX_HITS);
   B.md_off = c.take<uint32_t>(MAX_MODULES + 1);
+  B.md_box = c.take<float4>(2 * (size_t)MAX_MODULES);
   B.md_unit = c.take<uint32_t>(MAX_MD);
   B.md_lo_idx = c.take<uint32_t>(MAX_MD);
   B.md_up_idx = c.take<uint32_t>(MAX_MD);
