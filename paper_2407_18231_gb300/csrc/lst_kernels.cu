@@ -718,8 +718,9 @@ constexpr uint32_t LS_LIST_CAP = 512;  // flattened neighbour MDs per warp in sh
 constexpr uint32_t LS_ANCHORS = 8;     // MDs of a module tested per walk over its list
 constexpr uint32_t LS_RING = 64;       // ring of queued (list position, anchor) entries (> 31 + 32)
 // per warp after the list: the ring, one pass bit per list position for each anchor, and
-// the anchors (lower hit, tolerances, direction terms: three float4 each)
-constexpr uint32_t LS_EXTRA_WORDS = LS_RING + LS_ANCHORS * LS_LIST_CAP / 32 + LS_ANCHORS * 12;
+// the anchors (lower hit and direction terms: two float4 each; the tolerances are the
+// module's, the same for every anchor)
+constexpr uint32_t LS_EXTRA_WORDS = LS_RING + LS_ANCHORS * LS_LIST_CAP / 32 + LS_ANCHORS * 8;
 
 // LS count pass.  Unit = (event, module A).  The warp writes the indices of all MDs on the
 // modules connected to A into a shared-memory list once (module order, then MD order), then
@@ -791,6 +792,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
     }
     const float rnext = G.rnext[A];
     const bool a_barrel = G.subdet[A] == 0;
+    const float4 t_a = G.modc[A];  // every MD of A carries its module's tolerances
     {
       // Up to LS_ANCHORS MDs of A per walk over the list: their points are staged in shared
       // memory (read as broadcasts) and each candidate loaded is tested against all of
@@ -840,9 +842,8 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
       for (uint32_t ag = a0; ag < a1; ag += LS_ANCHORS) {
         const uint32_t na = min(LS_ANCHORS, a1 - ag);
         if (lane < na) {
-          anc[3 * lane] = B.md_pt[2 * (size_t)(ag + lane)];
-          anc[3 * lane + 1] = B.md_pt[2 * (size_t)(ag + lane) + 1];
-          anc[3 * lane + 2] = B.md_dir4[ag + lane];
+          anc[2 * lane] = B.md_pt[2 * (size_t)(ag + lane)];
+          anc[2 * lane + 1] = B.md_dir4[ag + lane];
         }
         for (uint32_t i = lane; i < na * (LS_LIST_CAP / 32); i += 32) pbits[i] = 0;
         uint32_t qh = 0, qt = 0;  // ring head and tail (free-running)
@@ -850,8 +851,8 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
           const uint32_t k = e >> 9, q = e & 511u;
           const uint32_t j = list[q];
           const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
-          const PointTol pa{anc[3 * k], anc[3 * k + 1]};
-          if (ls_tail_k(C, G, B, pa, anc[3 * k + 2], rnext, exit, j))
+          const PointTol pa{anc[2 * k], t_a};
+          if (ls_tail_k(C, G, B, pa, anc[2 * k + 1], rnext, exit, j))
             atomicOr(&pbits[k * (LS_LIST_CAP / 32) + (q >> 5)], 1u << (q & 31));
         };
         __syncwarp();
@@ -860,7 +861,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
           const uint32_t j = t < len ? list[t] : a0;  // a0: any valid MD for idle lanes
           const PointTol pb{__ldg(&B.md_pt[2 * (size_t)j]), __ldg(&B.md_pt[2 * (size_t)j + 1])};
           for (uint32_t k = 0; k < na; k++) {
-            const PointTol pa{anc[3 * k], anc[3 * k + 1]};
+            const PointTol pa{anc[2 * k], t_a};
             const bool h = t < len && ls_head_pt(C, pa, pb);
             const uint32_t hb = __ballot_sync(FULL, h);
             if (h) queue[(qt + __popc(hb & lt)) & (LS_RING - 1)] = t | (k << 9);
