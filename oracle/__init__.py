@@ -66,8 +66,13 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(LIB_PATH)
+            # LST_ORACLE_LIB: a separately built copy of the oracle (the mutation test builds
+            # copies with one planted mistake each and runs the pins against them)
+            path = os.environ.get("LST_ORACLE_LIB")
+            if not path:
+                build()
+                path = LIB_PATH
+            L = C.CDLL(path)
             L.ora_geom_create.restype = C.c_void_p
             L.ora_geom_create.argtypes = [C.c_void_p, C.c_uint32]
             L.ora_geom_destroy.argtypes = [C.c_void_p]
@@ -84,6 +89,17 @@ def lib():
             L.ora_sincos.argtypes = [C.c_float, C.POINTER(C.c_float), C.POINTER(C.c_float)]
             L.ora_md_test.restype = C.c_int
             L.ora_md_test.argtypes = [C.c_void_p, C.c_uint32, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+            F3 = C.POINTER(C.c_float)
+            L.ora_ls_eval.restype = C.c_uint32
+            L.ora_ls_eval.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, F3, F3, F3, F3]
+            L.ora_t3_eval.restype = C.c_uint32
+            L.ora_t3_eval.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), F3, F3, F3, F3]
+            L.ora_t5_eval.restype = C.c_uint32
+            L.ora_t5_eval.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), F3, F3, F3]
+            L.ora_pls_eval.restype = C.c_uint32
+            L.ora_pls_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, F3, F3]
+            L.ora_pt5_eval.restype = C.c_uint32
+            L.ora_pt5_eval.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint32), F3]
             _lib = L
     return _lib
 
@@ -200,3 +216,48 @@ def md_test(geom: Geometry, module: int, a, b) -> bool:
     fa = (C.c_float * 3)(*a)
     fb = (C.c_float * 3)(*b)
     return bool(lib().ora_md_test(geom._h, module, fa, fb))
+
+
+# ---- predicate-level decisions (bit masks; see lst_oracle.h) ----
+LS_BEND, LS_RZ, LS_EXIT, LS_DIR_IN, LS_DIR_OUT = 1, 2, 4, 8, 16
+T3_RZ, T3_MIDDIR, T3_RADIUS = 1, 2, 4
+T5_INOUT, T5_BRFULL, T5_RADIUS, T5_RZ = 1, 2, 4, 8
+PLS_RPHI, PLS_RZ = 1, 2
+PT5_WINDOWS, PT5_CURV = 1, 2
+
+
+def _f3(v):
+    return (C.c_float * 3)(*[float(np.float32(x)) for x in v])
+
+
+def ls_eval(geom: Geometry, A: int, B: int, a, au, b, bu) -> int:
+    return int(lib().ora_ls_eval(geom._h, A, B, _f3(a), _f3(au), _f3(b), _f3(bu)))
+
+
+def t3_eval(geom: Geometry, mods, a, b, bu, c) -> int:
+    m = (C.c_uint32 * 3)(*map(int, mods))
+    return int(lib().ora_t3_eval(geom._h, m, _f3(a), _f3(b), _f3(bu), _f3(c)))
+
+
+def t5_eval(geom: Geometry, mods, pts):
+    """(mask, score, k_full) of five anchors (x, y, z) on modules ``mods``."""
+    m = (C.c_uint32 * 5)(*map(int, mods))
+    p = (C.c_float * 15)(*np.asarray(pts, np.float32).ravel().tolist())
+    sc, kf = C.c_float(), C.c_float()
+    mask = lib().ora_t5_eval(geom._h, m, p, C.byref(sc), C.byref(kf))
+    return int(mask), np.float32(sc.value), np.float32(kf.value)
+
+
+def pls_eval(geom: Geometry, pls, module: int, x):
+    """(mask, normalised squared residual) of one anchor against one pLS record."""
+    rec = np.ascontiguousarray(np.asarray(pls).reshape(1))
+    sc = C.c_float()
+    mask = lib().ora_pls_eval(geom._h, rec.ctypes.data, int(module), _f3(x), C.byref(sc))
+    return int(mask), np.float32(sc.value)
+
+
+def pt5_eval(geom: Geometry, pls, mods, pts) -> int:
+    rec = np.ascontiguousarray(np.asarray(pls).reshape(1))
+    m = (C.c_uint32 * 5)(*map(int, mods))
+    p = (C.c_float * 15)(*np.asarray(pts, np.float32).ravel().tolist())
+    return int(lib().ora_pt5_eval(geom._h, rec.ctypes.data, m, p))

@@ -448,12 +448,9 @@ static int mid_dir(const pt_t *a, const pt_t *b, const pt_t *bu, const pt_t *c) 
   return crs <= tol;
 }
 
-/* T3 (Sec. 1: two LSs sharing an MD): r-z straightness, the middle MD's direction, and
- * a circle radius R = |ab||bc||ca| / (2 |cross|) >= Rmin (1 - 5 %) with the cross product
- * reduced by the point tolerance.  Straight triples pass. */
-static int t3_pass(const pt_t *a, const pt_t *b, const pt_t *bu, const pt_t *c) {
-  if (!rz3(a, b, c)) return 0;
-  if (!mid_dir(a, b, bu, c)) return 0;
+/* Circle radius of a triple: R = |ab||bc||ca| / (2 |cross|) >= Rmin (1 - 5 %), with the
+ * cross product reduced by the point tolerance times the perimeter.  Straight triples pass. */
+static int t3_radius(const pt_t *a, const pt_t *b, const pt_t *c) {
   float k, tol, cross, prod, perim;
   curv3(a, b, c, &k, &tol, &cross, &prod, &perim);
   float dmax = max3f(a->delta, b->delta, c->delta);
@@ -461,10 +458,20 @@ static int t3_pass(const pt_t *a, const pt_t *b, const pt_t *bu, const pt_t *c) 
   return (slack <= 0.0f) || (prod >= C_K3 * slack);
 }
 
+/* T3 (Sec. 1: two LSs sharing an MD): r-z straightness, the middle MD's direction, and
+ * a circle radius R = |ab||bc||ca| / (2 |cross|) >= Rmin (1 - 5 %) with the cross product
+ * reduced by the point tolerance.  Straight triples pass. */
+static int t3_pass(const pt_t *a, const pt_t *b, const pt_t *bu, const pt_t *c) {
+  if (!rz3(a, b, c)) return 0;
+  if (!mid_dir(a, b, bu, c)) return 0;
+  return t3_radius(a, b, c);
+}
+
 /* T5 (Sec. 1: two T3s sharing an MD; circle-radius consistency): curvatures of the
  * inner (a,b,c), outer (c,d,e), bridge (b,c,d) and full (a,c,e) triples must agree,
- * the full circle must satisfy R >= Rmin (1 - 5 %), and a, c, e must be straight in r-z. */
-static int t5_pass(const pt_t *P[5], float *score, float *kfull_out) {
+ * the full circle must satisfy R >= Rmin (1 - 5 %), and a, c, e must be straight in r-z.
+ * Returns the four conditions as bits 0-3 (inner/outer, bridge/full, radius, r-z). */
+static unsigned t5_eval(const pt_t *P[5], float *score, float *kfull_out) {
   float kin, tin, kout, tout, kbr, tbr, kfu, tfu;
   curv3(P[0], P[1], P[2], &kin, &tin, NULL, NULL, NULL);
   curv3(P[2], P[3], P[4], &kout, &tout, NULL, NULL, NULL);
@@ -478,8 +485,10 @@ static int t5_pass(const pt_t *P[5], float *score, float *kfull_out) {
   int c4 = rz3(P[0], P[2], P[4]);
   *score = d1 + d2;
   *kfull_out = kfu;
-  return c1 && c2 && c3 && c4;
+  return (unsigned)c1 | (unsigned)c2 << 1 | (unsigned)c3 << 2 | (unsigned)c4 << 3;
 }
+
+static int t5_pass(const pt_t *P[5], float *score, float *kfull_out) { return t5_eval(P, score, kfull_out) == 15u; }
 
 /* ---------------- pLS helix and module lookup ---------------- */
 typedef struct { float x0, y0, z0, R, cx, cy, cot, q, pt; int valid; } pls_t;
@@ -639,8 +648,9 @@ static uint32_t pls_candidates(const ora_geom *g, const pls_t *p, uint32_t out[3
 /* pLS-to-anchor compatibility (reading of pT3/pT5, Sec. 1): each anchor must lie within
  * an r-phi window of the pLS circle and an r-z window of the pLS line, both growing with
  * the arc length s from the reference point (1 % pT, 1 mrad phi and direction spread).
- * Adds the normalised squared residuals to *score. */
-static int pls_anchor(const pls_t *p, const pt_t *X, float *score) {
+ * Adds the normalised squared residuals to *score; returns the r-phi (bit 0) and r-z
+ * (bit 1) window decisions. */
+static unsigned pls_anchor_eval(const pls_t *p, const pt_t *X, float *score) {
   float ddx = X->x - p->x0, ddy = X->y - p->y0;
   float chord = sqrtf(ddx * ddx + ddy * ddy);
   float s = arc_len(chord, p->R);
@@ -651,7 +661,17 @@ static int pls_anchor(const pls_t *p, const pt_t *X, float *score) {
   float wz = 0.05f + 0.002f * s + X->zeta + X->rho * fabsf(p->cot);
   float a = dphi / wphi, b = ez / wz;
   *score = *score + (a * a + b * b);
-  return (fabsf(dphi) <= wphi) && (fabsf(ez) <= wz);
+  return (unsigned)(fabsf(dphi) <= wphi) | (unsigned)(fabsf(ez) <= wz) << 1;
+}
+
+static int pls_anchor(const pls_t *p, const pt_t *X, float *score) { return pls_anchor_eval(p, X, score) == 3u; }
+
+/* pT5 (reading of Sec. 1): the T5's full-circle curvature must agree with the pLS's,
+ * ||k_full| - 1/R| <= 15 % / R plus the curvature tolerance of the T5's (a, c, e) triple. */
+static int pt5_curv(const pls_t *p, float kf, const pt_t *P0, const pt_t *P2, const pt_t *P4) {
+  float kk, tf;
+  curv3(P0, P2, P4, &kk, &tf, NULL, NULL, NULL);
+  return fabsf(fabsf(kf) - 1.0f / p->R) <= C_KPT5 / p->R + tf;
 }
 
 /* ---------------- the chain ---------------- */
@@ -872,12 +892,9 @@ int ora_run(const ora_geom *g, const ora_event *ev, int brute_ls, ora_result *ou
           int ok = 1;
           out->n_tests[6]++;
           for (int k = 0; k < 5; k++) ok &= pls_anchor(&pl[p], &hit[md_lo.p[t5.p[5 * t + k]]], &score);
-          float kf = t5k.p[t];
           const pt_t *P0 = &hit[md_lo.p[t5.p[5 * t]]], *P2 = &hit[md_lo.p[t5.p[5 * t + 2]]],
                      *P4 = &hit[md_lo.p[t5.p[5 * t + 4]]];
-          float kk, tf;
-          curv3(P0, P2, P4, &kk, &tf, NULL, NULL, NULL);
-          int c5 = fabsf(fabsf(kf) - 1.0f / pl[p].R) <= C_KPT5 / pl[p].R + tf;
+          int c5 = pt5_curv(&pl[p], t5k.p[t], P0, P2, P4);
           if (ok && c5 && (vu32_push(&pt5p, p) || vu32_push(&pt5o, t) || vf32_push(&pt5s, score))) goto done;
         }
       }
@@ -1124,4 +1141,80 @@ int ora_md_test(const ora_geom *g, uint32_t module, const float a[3], const floa
   pa.delta = pb.delta = g->delta[module];
   pa.T = pb.T = g->T[module];
   return pair_bend(&pa, &pb, g->T[module]) && pair_rz(&pa, &pb);
+}
+
+/* Predicate-level evaluation, so that tests can show which single condition a
+ * constructed configuration fails.  Points are (x, y, z); each takes the tolerances of
+ * the module given beside it.  Every function only calls the predicates the chain uses. */
+static void load_pt(const ora_geom *g, uint32_t module, const float v[3], pt_t *o) {
+  o->x = v[0]; o->y = v[1]; o->z = v[2];
+  o->r = sqrtf(o->x * o->x + o->y * o->y);
+  o->zeta = g->zeta[module]; o->rho = g->rho[module]; o->delta = g->delta[module]; o->T = g->T[module];
+}
+
+uint32_t ora_ls_eval(const ora_geom *g, uint32_t A, uint32_t B, const float a[3], const float au[3],
+                     const float b[3], const float bu[3]) {
+  if (A >= g->n || B >= g->n) return 0;
+  pt_t pa, pau, pb, pbu;
+  load_pt(g, A, a, &pa); load_pt(g, A, au, &pau); load_pt(g, B, b, &pb); load_pt(g, B, bu, &pbu);
+  int b2d = g->m[A].subdet == 0 && g->m[B].subdet == 1;
+  float cx = pb.x - pa.x;
+  float cy = pb.y - pa.y;
+  float clen = sqrtf(cx * cx + cy * cy);
+  uint32_t m = 0;
+  m |= (uint32_t)pair_bend(&pa, &pb, g->T[B]);
+  m |= (uint32_t)pair_rz(&pa, &pb) << 1;
+  m |= (uint32_t)(!b2d || exit_ok(&pa, &pb, g->rnext[A], g->zb_half)) << 2;
+  m |= (uint32_t)md_dir(&pa, &pau, cx, cy, clen) << 3;
+  m |= (uint32_t)md_dir(&pb, &pbu, cx, cy, clen) << 4;
+  return m;
+}
+
+uint32_t ora_t3_eval(const ora_geom *g, const uint32_t mod[3], const float a[3], const float b[3],
+                     const float bu[3], const float c[3]) {
+  for (int k = 0; k < 3; k++)
+    if (mod[k] >= g->n) return 0;
+  pt_t pa, pb, pbu, pc;
+  load_pt(g, mod[0], a, &pa); load_pt(g, mod[1], b, &pb); load_pt(g, mod[1], bu, &pbu); load_pt(g, mod[2], c, &pc);
+  return (uint32_t)rz3(&pa, &pb, &pc) | (uint32_t)mid_dir(&pa, &pb, &pbu, &pc) << 1 |
+         (uint32_t)t3_radius(&pa, &pb, &pc) << 2;
+}
+
+uint32_t ora_t5_eval(const ora_geom *g, const uint32_t mod[5], const float p[15], float *score, float *kfull) {
+  pt_t q[5];
+  const pt_t *P[5];
+  for (int k = 0; k < 5; k++) {
+    if (mod[k] >= g->n) return 0;
+    load_pt(g, mod[k], p + 3 * k, &q[k]);
+    P[k] = &q[k];
+  }
+  return t5_eval(P, score, kfull);
+}
+
+uint32_t ora_pls_eval(const ora_geom *g, const ora_pls *s, uint32_t module, const float x[3], float *score) {
+  if (module >= g->n) return 0;
+  pls_t p;
+  pt_t X;
+  pls_params(s, &p);
+  load_pt(g, module, x, &X);
+  *score = 0.0f;
+  return pls_anchor_eval(&p, &X, score);
+}
+
+/* bit 0: all five anchors inside the pLS windows; bit 1: the pT5 curvature agreement. */
+uint32_t ora_pt5_eval(const ora_geom *g, const ora_pls *s, const uint32_t mod[5], const float pts[15]) {
+  pt_t q[5];
+  const pt_t *P[5];
+  pls_t p;
+  pls_params(s, &p);
+  for (int k = 0; k < 5; k++) {
+    if (mod[k] >= g->n) return 0;
+    load_pt(g, mod[k], pts + 3 * k, &q[k]);
+    P[k] = &q[k];
+  }
+  float score = 0.0f, t5score, kf;
+  int ok = 1;
+  for (int k = 0; k < 5; k++) ok &= pls_anchor(&p, P[k], &score);
+  t5_eval(P, &t5score, &kf);
+  return (uint32_t)ok | (uint32_t)pt5_curv(&p, kf, P[0], P[2], P[4]) << 1;
 }

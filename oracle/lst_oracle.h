@@ -96,6 +96,18 @@ int ora_run_many(const ora_geom *g, const ora_event *evs, uint32_t n, int n_thre
 float ora_arc_len(float chord, float R);
 void ora_sincos(float a, float *s, float *c);
 int ora_md_test(const ora_geom *g, uint32_t module, const float a[3], const float b[3]);
+/* Predicate-level decisions as bit masks (tests only).  LS: bending, r-z pointing, barrel
+ * exit (1 unless barrel to disk), inner-MD direction, outer-MD direction.  T3: r-z
+ * straightness, middle-MD direction, radius.  T5: inner/outer curvature, bridge/full
+ * curvature, full radius, (a, c, e) r-z straightness (also returns score and k_full).
+ * pLS anchor: r-phi window, r-z window.  pT5: all five anchor windows, curvature. */
+uint32_t ora_ls_eval(const ora_geom *g, uint32_t A, uint32_t B, const float a[3], const float au[3],
+                     const float b[3], const float bu[3]);
+uint32_t ora_t3_eval(const ora_geom *g, const uint32_t mod[3], const float a[3], const float b[3],
+                     const float bu[3], const float c[3]);
+uint32_t ora_t5_eval(const ora_geom *g, const uint32_t mod[5], const float p[15], float *score, float *kfull);
+uint32_t ora_pls_eval(const ora_geom *g, const ora_pls *s, uint32_t module, const float x[3], float *score);
+uint32_t ora_pt5_eval(const ora_geom *g, const ora_pls *s, const uint32_t mod[5], const float pts[15]);
 
 #ifdef __cplusplus
 }

@@ -325,3 +325,75 @@ def test_efficiency_with_resolution(barrel_geom, ora_barrel):
         if n.max() > frac * len(h) and s[n.argmax()] >= 0:
             matched.add(int(s[n.argmax()]))
     assert len(matched) >= 0.9 * len(t)
+
+
+def test_dedup_definition_on_a_full_pu200_event(full_geom, ora_full):
+    """R15 stated as set operations on sparse MD-incidence matrices, on a full PU200-like
+    event with seeds (thousands of pT5s, pT3s and T5s, so that overlaps of exactly two MDs,
+    pT3s next to removed pT5s and the like all occur)."""
+    import scipy.sparse as sp
+    ev = S.make_event("pu200", 4, with_pls=True)
+    r = oracle.run(ora_full, ev)
+    nmd = len(r["md"])
+    t3, t5 = r["t3"], r["t5"]
+    P5, P3 = r["pt5"][:, 0].astype(np.int64), r["pt3"][:, 0].astype(np.int64)
+    m5, m3 = t5[r["pt5"][:, 1]], t3[r["pt3"][:, 1]]
+    s5, s3, st = r["pt5_score"], r["pt3_score"], r["t5_score"]
+
+    def inc(rows):
+        n, k = rows.shape
+        return sp.csr_matrix((np.ones(n * k), (np.repeat(np.arange(n), k), rows.ravel().astype(np.int64))),
+                             shape=(n, nmd))
+
+    def pairs(A, B, thr):
+        C = (A @ B.T).tocoo()
+        sel = C.data >= thr
+        return C.row[sel], C.col[sel]
+
+    def same_pls(p):
+        # the lists are sorted by pLS: pairs within each run of one pLS
+        out_x, out_y = [], []
+        starts = np.flatnonzero(np.r_[True, p[1:] != p[:-1]])
+        ends = np.r_[starts[1:], len(p)]
+        for a, b in zip(starts, ends):
+            g = np.arange(a, b)
+            gx, gy = np.meshgrid(g, g, indexing="ij")
+            out_x.append(gx.ravel()); out_y.append(gy.ravel())
+        return np.concatenate(out_x), np.concatenate(out_y)
+
+    def kill(x, y, s, n, excl=None):
+        keep = (x != y) if excl is None else (x != y) & ~excl[y]
+        x, y = x[keep], y[keep]
+        better = (s[y] < s[x]) | ((s[y] == s[x]) & (y < x))
+        dead = np.zeros(n, bool)
+        np.logical_or.at(dead, x, better)
+        return dead
+
+    M5, M3, MT = inc(m5), inc(m3), inc(t5)
+    assert len(P5) > 3000 and len(P3) > 3000 and len(t5) > 5000
+    x1, y1 = pairs(M5, M5, 3)
+    x2, y2 = same_pls(P5)
+    alive5 = ~kill(np.r_[x1, x2], np.r_[y1, y2], s5, len(P5))
+    used5 = np.zeros(ev.n_pls, bool)
+    used5[P5[alive5]] = True
+    x, z = pairs(M3, M5, 2)
+    cross3 = used5[P3].copy()
+    np.logical_or.at(cross3, x, alive5[z])
+    x1, y1 = pairs(M3, M3, 2)
+    x2, y2 = same_pls(P3)
+    alive3 = ~(cross3 | kill(np.r_[x1, x2], np.r_[y1, y2], s3, len(P3), excl=cross3))
+    used3 = np.zeros(ev.n_pls, bool)
+    used3[P3[alive3]] = True
+    crosst = np.zeros(len(t5), bool)
+    x, z = pairs(MT, M5, 3)
+    np.logical_or.at(crosst, x, alive5[z])
+    x, z = pairs(MT, M3, 3)
+    np.logical_or.at(crosst, x, alive3[z])
+    x1, y1 = pairs(MT, MT, 3)
+    alivet = ~(crosst | kill(x1, y1, st, len(t5), excl=crosst))
+    assert np.array_equal(alive5.astype(np.uint8), r["alive_pt5"])
+    assert np.array_equal(alive3.astype(np.uint8), r["alive_pt3"])
+    assert np.array_equal(alivet.astype(np.uint8), r["alive_t5"])
+    assert np.array_equal((~(used5 | used3)).astype(np.uint8), r["pls_tc"])
+    # the event exercises every branch
+    assert (~alive5).sum() > 100 and cross3.sum() > 100 and crosst.sum() > 100 and (~alive3 & ~cross3).sum() > 10
