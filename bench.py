@@ -7,12 +7,20 @@ pT / 1 mrad smear, 10 % fakes), so that every step of the chain runs: binning, M
 T5, pLS lookup, pT3, pT5, duplicate removal, track candidates.  A step is one batch of
 --batch events through the whole chain.
 
-  value     events/s, batched + CUDA graph, inputs resident in HBM (lst_run_batch_device)
-  e2e       events/s through lst_submit_batch / lst_collect_batch with host buffers (copies inside the timed region)
-  per_event events/s and p50/p99 latency of the plain per-event launch (lst_run_event)
-  served    p50/p99 latency and events/s of the continuous-batching loop (lst_serve_replay)
-  roofline  the kernel with the largest device time, algorithmic bytes / CUDA-event time
-  cpu_baseline  the CPU oracle on the host cores, on a bounded sample of the same events
+  value      events/s, batched + CUDA graph, inputs resident in HBM (lst_run_batch_device)
+  parity     after timing, sampled events of a timed batch against the CPU oracle, bit for bit
+  sustained  the same step repeated for --sustain seconds (clock evidence under load)
+  e2e        events/s through lst_submit_batch / lst_collect_batch with host buffers (copies inside the timed region)
+  per_event  events/s and p50/p99 latency of the plain per-event launch (lst_run_event)
+  served     p50/p99 latency and events/s of the continuous-batching loop (lst_serve_replay)
+  serving_sweep  the serving workload (U{2000..8000} tracks) at 1-20 kHz offered, 8 and 64 GB
+             budgets, slots' batches one after another or sharing the device
+  workloads  the tiny event (us/event), the 64-event barrel batch and the 16-event
+             high-occupancy batch with seeds (events/s, objects/s), each with a parity check
+  roofline   the kernel with the largest device time, algorithmic work / CUDA-event time;
+             the MD and LS stages' HBM fraction beside it
+  cpu_baseline  the CPU oracle on the host cores (1 thread, 2 threads pinned to 2 cores,
+             all cores) on the benchmark's own events
 
 --impl reference times the CPU oracle itself on the same workload and metric.
 Multi-GPU: one process per GPU (torchrun), each a replica on its own events (weak scaling).
@@ -49,7 +57,11 @@ def parse():
     ap.add_argument("--per-event", type=int, default=48, help="events for the per-event leg (0 = skip)")
     ap.add_argument("--served", type=int, default=2048, help="events for the served leg (0 = skip)")
     ap.add_argument("--served-rate", type=float, default=0.0, help="offered Hz (0: 0.8 x batched rate)")
-    ap.add_argument("--cpu-sample", type=int, default=8, help="events for the CPU-oracle baseline (0 = skip)")
+    ap.add_argument("--cpu-sample", type=int, default=1, help="CPU-oracle baseline (0 = skip)")
+    ap.add_argument("--sustain", type=float, default=2.0, help="seconds of the sustained run (0 = skip)")
+    ap.add_argument("--sweep", type=int, default=1, help="serving sweep over rates and budgets (0 = skip)")
+    ap.add_argument("--legs", type=int, default=1, help="tiny / barrel-batch / high-occupancy legs (0 = skip)")
+    ap.add_argument("--parity", type=int, default=3, help="events of a timed batch checked against the oracle")
     ap.add_argument("--tune", type=int, default=1, help="autotune the launch configuration first (1) or not (0)")
     ap.add_argument("--config", default="", help="fixed launch configuration block_size,blocks_per_sm,ls_list_cap "
                                                  "(skips the autotuner)")
@@ -125,42 +137,102 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(events, geom_modules):
+def _oracle_seconds(og, events, threads, cpus=None):
+    """Wall seconds of the oracle over `events` on `threads` host threads (optionally
+    pinned to the CPU set `cpus`: the calling thread's affinity, which the oracle's threads
+    inherit)."""
+    import oracle
+    old = os.sched_getaffinity(0) if cpus else None
+    try:
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        t0 = time.perf_counter()
+        oracle.run_many(og, events, n_threads=threads, convert=False)
+        return time.perf_counter() - t0
+    finally:
+        if old:
+            os.sched_setaffinity(0, old)
+
+
+def check_pending(pending):
+    """CPU leg: the oracle on every event whose GPU candidates were kept, field by field."""
+    import oracle
+    geoms, out = {}, {}
+    for label, k, tc, ev, modules in pending:
+        key = id(modules)
+        if key not in geoms:
+            geoms[key] = oracle.Geometry(modules)
+        r = out.setdefault(label, {"events": [], "identical": True,
+                                   "compared": "every track-candidate field, pT and score bit for bit"})
+        r["events"].append(k)
+        r["identical"] = r["identical"] and tc_parity(tc, oracle.run(geoms[key], ev))
+    return out
+
+
+def cpu_oracle_rates(events, geom_modules):
+    """The oracle as it stands on the host cores, on the benchmark's own events: one thread,
+    two threads pinned to two cores (the paper's CPU setup, Sec. 3), and every core (at
+    least two events per core so that no core idles).  A bounded sample: about 10 s."""
     import oracle
     og = oracle.Geometry(geom_modules)
-    cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    oracle.run_many(og, events, n_threads=cores, convert=False)
-    dt = time.perf_counter() - t0
-    return len(events) / dt, cores, dt
+    cpus = sorted(os.sched_getaffinity(0))
+    cores = len(cpus)
+    n1 = min(len(events), 6)
+    n2 = min(len(events), 8)
+    na = min(len(events), 2 * cores)
+    t1 = _oracle_seconds(og, events[:n1], 1)
+    t2 = _oracle_seconds(og, events[:n2], 2, set(cpus[:2]))
+    ta = _oracle_seconds(og, events[:na], cores)
+    return {"value": na / ta, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "rates": {"1_thread": n1 / t1, "2_threads_pinned_2_cores": n2 / t2, f"{cores}_threads": na / ta},
+            "sample": f"the benchmark's first PU200-like events with seeds: {n1} on 1 thread ({t1:.1f} s), "
+                      f"{n2} on 2 threads pinned to 2 cores ({t2:.1f} s), {na} on {cores} threads ({ta:.1f} s)"}
 
 
 def reference_arm(args):
+    """The CPU oracle as the reference arm: every step runs 2 x cores of the benchmark's
+    events on all host cores (threads over events)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import lst_synth as S
-    geom = S.geometry(False)
-    per_step = max(1, min(args.batch, 4))
-    evs = make_events(per_step * 2, 10_000)
     import oracle
+    geom = S.geometry(False)
+    cores = len(os.sched_getaffinity(0))
+    per_step = 2 * cores
+    evs = make_events(per_step, 0)
     og = oracle.Geometry(geom.modules)
-    cores = os.cpu_count() or 1
     for w in range(args.warmup):
-        oracle.run_many(og, evs[:per_step], n_threads=cores, convert=False)
+        oracle.run_many(og, evs, n_threads=cores, convert=False)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle.run_many(og, evs[(k % 2) * per_step:(k % 2 + 1) * per_step], n_threads=cores, convert=False)
+        oracle.run_many(og, evs, n_threads=cores, convert=False)
     dt = time.perf_counter() - t0
     rate = args.steps * per_step / dt
+    cpu = cpu_oracle_rates(evs, geom.modules)
     line = {"metric": METRIC, "value": rate, "unit": "events/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "events_per_step": per_step, "parallelism": "host threads over events"},
+            "config": {"workload": WORKLOAD, "events_per_step": per_step, "parallelism": f"{cores} host threads over events"},
             "cpu_baseline": {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} PU200-like events per step, all host cores"},
+                             "rates": cpu["rates"],
+                             "sample": f"{per_step} PU200-like events per step (the GPU benchmark's first events), "
+                                       f"all {cores} host cores; {cpu['sample']}"},
             "e2e": {"value": rate, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- parity
+def tc_parity(tc, ora):
+    """Track candidates of one event against the oracle's: every field, floats bit for bit."""
+    if len(tc) != len(ora["tc_type"]):
+        return False
+    checks = [np.array_equal(tc["type"], ora["tc_type"]), np.array_equal(tc["obj"], ora["tc_obj"]),
+              np.array_equal(tc["pls"], ora["tc_pls"]), np.array_equal(tc["ot"], ora["tc_ot"]),
+              np.array_equal(tc["pix"], ora["tc_pix"]),
+              tc["pt"].astype(np.float32).tobytes() == ora["tc_pt"].tobytes(),
+              tc["score"].astype(np.float32).tobytes() == ora["tc_score"].tobytes()]
+    return bool(all(checks))
 
 
 # ---------------------------------------------------------------- ranks
@@ -249,6 +321,171 @@ def alu_peak(n_sm, sm_mhz):
     return n_sm * 128 * sm_mhz * 1e6
 
 
+def to_device(evs, dev):
+    """One concatenated, device-resident copy of a batch's inputs (lst_batch_dev + owners)."""
+    import torch
+    import paper_2407_18231_gb300 as lst
+    cat = lambda k: torch.from_numpy(np.ascontiguousarray(np.concatenate([getattr(e, k) for e in evs]))).to(dev)  # noqa
+    x, y, z = cat("x"), cat("y"), cat("z")
+    det = torch.from_numpy(np.concatenate([e.det for e in evs]).view(np.int32)).to(dev)
+    pls_all = np.concatenate([e.pls for e in evs])
+    pls = torch.from_numpy(pls_all.view(np.uint8) if len(pls_all) else np.zeros(80, np.uint8)).to(dev)
+    hoff = torch.tensor(np.concatenate([[0], np.cumsum([e.n_hits for e in evs])]).astype(np.int32), device=dev)
+    poff = torch.tensor(np.concatenate([[0], np.cumsum([e.n_pls for e in evs])]).astype(np.int32), device=dev)
+    desc = lst.lst_batch_dev(len(evs), int(hoff[-1]), int(poff[-1]), max(e.n_hits for e in evs),
+                             x.data_ptr(), y.data_ptr(), z.data_ptr(), det.data_ptr(), hoff.data_ptr(),
+                             pls.data_ptr(), poff.data_ptr())
+    return desc, (x, y, z, det, pls, hoff, poff)
+
+
+OBJ_KEYS = ("n_md", "n_ls", "n_t3", "n_t5", "n_pt3", "n_pt5", "n_tc")
+
+
+def time_device_batches(sess, dev_batches, n_ev, stream, flush, steps, warmup):
+    """Warm-up, then `steps` device-resident batches timed with CUDA events on the
+    library's stream, L2 flushed between steps; returns (ms per step, stats of the run)."""
+    import torch
+    for k in range(max(warmup, len(dev_batches))):
+        sess.run_batch_device(dev_batches[k % len(dev_batches)][0], stream.cuda_stream)
+        sess.batch_finish(n_ev, timeout_ms=120000)
+    t_a = torch.cuda.Event(enable_timing=True)
+    t_b = torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.zero_()
+            t_a.record(stream)
+            sess.run_batch_device(dev_batches[k % len(dev_batches)][0], stream.cuda_stream)
+            t_b.record(stream)
+            sess.batch_finish(n_ev, timeout_ms=120000)
+            ms += t_a.elapsed_time(t_b)
+    return ms / steps, sess.stats()
+
+
+def sampled_candidates(sess, dev_batch, n_ev, events, picks, stream, label, modules, pending):
+    """One more run of a resident batch keeping its results: the picked events' candidates
+    are queued for the CPU leg, which checks them against the oracle."""
+    sess.run_batch_device(dev_batch, stream.cuda_stream)
+    _, ids = sess.batch_finish(n_ev, timeout_ms=120000, keep_results=True)
+    for k in picks:
+        pending.append((label, int(k), sess.candidates(ids[k]), events[k], modules))
+    for i in ids:
+        sess.release(i)
+
+
+def workload_legs(local, dev, flush, stream, pending):
+    """The other workloads: the tiny event per launch, the 64-event barrel batch (tuned) and
+    the 16-event high-occupancy batch with seeds; a sampled event of each is queued for the
+    CPU leg's oracle check."""
+    import lst_synth as S
+    import paper_2407_18231_gb300 as lst
+    from paper_2407_18231_gb300 import autotune
+    out = {}
+    # tiny: plain per-event launch, latency-bound
+    gb = S.geometry(True)
+    ev = S.make_event("tiny")
+    sess = lst.Session(gb.modules, device=local)
+    for _ in range(20):
+        sess.release(sess.run_event(ev))
+    lat = []
+    for _ in range(300):
+        t0 = time.perf_counter()
+        rid = sess.run_event(ev)
+        tc = sess.candidates(rid)
+        lat.append(time.perf_counter() - t0)
+        sess.release(rid)
+    lat = np.array(lat)
+    out["tiny"] = {"us_per_event_p50": float(np.median(lat) * 1e6), "us_per_event_p99": float(np.percentile(lat, 99) * 1e6),
+                   "events_per_s": float(1.0 / lat.mean()), "hits": ev.n_hits, "tcs": int(len(tc)),
+                   "api": "lst_run_event + lst_get_candidates (host buffers)"}
+    pending.append(("tiny", 0, tc, ev, gb.modules))
+    sess.close()
+    # 64-event barrel batch (U{500..6000} tracks like tiny), launch configuration tuned on it
+    evs = [S.make_event("batched", i) for i in range(64)]
+    best = autotune.tune(gb.modules, evs, device=local, reps=3,
+                         space={"block_size": [128, 256, 512], "blocks_per_sm": [4, 8], "ls_list_cap": [128, 512]})
+    sess = lst.Session(gb.modules, device=local, **best["best"])
+    db = [to_device(evs, dev)]
+    ms, st = time_device_batches(sess, db, 64, stream, flush, 10, 3)
+    objs = sum(st[k] for k in OBJ_KEYS)
+    sampled_candidates(sess, db[0][0], 64, evs, [7], stream, "barrel_batch64", gb.modules, pending)
+    out["barrel_batch64"] = {"events_per_s": 64 / (ms * 1e-3), "objects_per_s": objs / (ms * 1e-3),
+                             "ms_per_batch": ms, "objects_per_batch": {k: st[k] for k in OBJ_KEYS},
+                             "mean_hits_per_event": float(np.mean([e.n_hits for e in evs])),
+                             "tuning": best["best"]}
+    sess.close()
+    # 16-event high-occupancy batch with seeds
+    gf = S.geometry(False)
+    evs = [S.make_event("highocc", i) for i in range(16)]
+    sess = lst.Session(gf.modules, device=local)
+    db = [to_device(evs, dev)]
+    ms, st = time_device_batches(sess, db, 16, stream, flush, 10, 3)
+    objs = sum(st[k] for k in OBJ_KEYS)
+    sampled_candidates(sess, db[0][0], 16, evs, [3], stream, "highocc_batch16", gf.modules, pending)
+    out["highocc_batch16"] = {"events_per_s": 16 / (ms * 1e-3), "objects_per_s": objs / (ms * 1e-3),
+                              "ms_per_batch": ms, "objects_per_batch": {k: st[k] for k in OBJ_KEYS},
+                              "mean_hits_per_event": float(np.mean([e.n_hits for e in evs]))}
+    sess.close()
+    return out
+
+
+def serving_sweep(local, rates=(1e3, 5e3, 10e3, 20e3), budgets_gb=(8, 64), n_events=2200, warm=200):
+    """Serving workload (U{2000..8000} tracks, 20 % noise): Poisson arrivals at each offered
+    rate, under each device-memory budget, with the slots' batches queued one after another
+    on the device or sharing it.  Events cycle over a pool of 64 generated events."""
+    import lst_synth as S
+    import paper_2407_18231_gb300 as lst
+    g = S.geometry(False)
+    pool = [S.make_event("serving", i) for i in range(64)]
+    sess = lst.Session(g.modules, device=local)
+    for i in sess.run_batch(pool[:32]):
+        sess.release(i)
+    lat = []
+    for e in pool[:24]:
+        t0 = time.perf_counter()
+        rid = sess.run_event(e)
+        sess.candidates(rid)
+        lat.append(time.perf_counter() - t0)
+        sess.release(rid)
+    lat = np.array(lat[4:])
+    per_event = {"events_per_s": float(1.0 / lat.mean()), "p50_ms": float(np.median(lat) * 1e3),
+                 "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+    points = []
+    rng = np.random.default_rng(11)
+    evs = [pool[i % len(pool)] for i in range(n_events)]
+    for budget in budgets_gb:
+        for share in (False, True):
+            for rate in rates:
+                arrival = np.cumsum(rng.exponential(1.0 / rate, n_events))
+                lt, ntc, _, wall = sess.serve_replay(evs, arrival, n_slots=4, max_batch=32,
+                                                     memory_budget=int(budget) << 30, share_device=share)
+                st = sess.stats()
+                l = lt[warm:]
+                points.append({"offered_hz": rate, "budget_gb": budget, "share_device": int(share),
+                               "events_per_s": n_events / wall, "p50_ms": float(np.median(l) * 1e3),
+                               "p99_ms": float(np.percentile(l, 99) * 1e3), "batches": st["served_batches"],
+                               "max_batch": st["served_max_batch"],
+                               "peak_device_gb": st["served_peak_bytes"] / 2 ** 30})
+    sess.close()
+    return {"workload": "serving: U{2000..8000} tracks, 20 % noise, no seeds", "events_per_point": n_events,
+            "warmup_events": warm, "pool": "64 generated events, cycled", "slots": 4, "max_batch": 32,
+            "per_event": per_event, "points": points}
+
+
+# Algorithmic bytes of the MD and LS stages per unit (the minimum each must move): MD =
+# 20 B per hit read (x, y, z, r, index) + 32 B per MD written (two hit indices, anchor
+# point, direction) + 100 B per module of geometry; LS = 32 B per MD read once + 4 B per
+# connection-map entry of the batch + 16 B per LS written.
+def stage_hbm(st, n_ev, n_mod, map_edges, ms_md, ms_ls, peak):
+    md_bytes = 20 * st["n_hits"] + 32 * st["n_md"] + 100 * n_mod
+    ls_bytes = 32 * st["n_md"] + 4 * map_edges * n_ev + 16 * st["n_ls"]
+    out = {}
+    for name, b, ms in (("md", md_bytes, ms_md), ("ls", ls_bytes, ms_ls)):
+        gbs = b / (ms * 1e-3) / 1e9
+        out[name] = {"algorithmic_bytes": int(b), "ms": ms, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -273,21 +510,7 @@ def main():
     B, P = args.batch, args.pool
     events = make_events(B * P, 100_000 * rank)
     batches = [events[i * B:(i + 1) * B] for i in range(P)]
-
-    # device-resident inputs, one concatenated set per batch
-    def to_device(evs):
-        cat = lambda k: torch.from_numpy(np.ascontiguousarray(np.concatenate([getattr(e, k) for e in evs]))).to(dev)  # noqa
-        x, y, z = cat("x"), cat("y"), cat("z")
-        det = torch.from_numpy(np.concatenate([e.det for e in evs]).view(np.int32)).to(dev)
-        pls = torch.from_numpy(np.concatenate([e.pls for e in evs]).view(np.uint8)).to(dev)
-        hoff = torch.tensor(np.concatenate([[0], np.cumsum([e.n_hits for e in evs])]).astype(np.int32), device=dev)
-        poff = torch.tensor(np.concatenate([[0], np.cumsum([e.n_pls for e in evs])]).astype(np.int32), device=dev)
-        desc = lst.lst_batch_dev(len(evs), int(hoff[-1]), int(poff[-1]), max(e.n_hits for e in evs),
-                                 x.data_ptr(), y.data_ptr(), z.data_ptr(), det.data_ptr(), hoff.data_ptr(),
-                                 pls.data_ptr(), poff.data_ptr())
-        return desc, (x, y, z, det, pls, hoff, poff)
-
-    dev_batches = [to_device(b) for b in batches]
+    dev_batches = [to_device(b, dev) for b in batches]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     tuning = {}
     if args.config:
@@ -326,6 +549,22 @@ def main():
             sess.batch_finish(B, timeout_ms=120000)
             elapsed_ms += t_start.elapsed_time(t_end)
         torch.cuda.synchronize()
+        # sustained: the same step for --sustain seconds right after the timed steps, so
+        # that the clock samples cover the device under this load
+        sustained = None
+        if args.sustain > 0:
+            n_s, ms_s = 0, 0.0
+            t_wall = time.perf_counter()
+            while time.perf_counter() - t_wall < args.sustain:
+                flush.zero_()
+                t_start.record(stream)
+                sess.run_batch_device(dev_batches[n_s % P][0], stream.cuda_stream)
+                t_end.record(stream)
+                sess.batch_finish(B, timeout_ms=120000)
+                ms_s += t_start.elapsed_time(t_end)
+                n_s += 1
+            sustained = {"steps": n_s, "seconds": time.perf_counter() - t_wall, "ms_per_step": ms_s / n_s,
+                         "events_per_s": n_s * B / (ms_s * 1e-3)}
     if sess.stats()["reruns"] != reruns_before:
         raise RuntimeError("a timed step re-ran after a list overflow; warm-up did not size the buffers")
     if ws > 1:
@@ -337,6 +576,13 @@ def main():
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
+
+    # ---- what was timed, kept for the oracle check of the CPU leg: sampled events of a
+    # timed batch (the same resident inputs, graph and launch configuration)
+    pending = []
+    if args.parity:
+        picks = sorted(set(np.linspace(0, B - 1, args.parity).astype(int).tolist()))
+        sampled_candidates(sess, dev_batches[0][0], B, batches[0], picks, stream, "headline", geom.modules, pending)
 
     # ---- end to end: host buffers through the asynchronous batch API (lst_submit_batch /
     # lst_collect_batch): one batch in flight while the next is packed and uploaded; every
@@ -412,6 +658,7 @@ def main():
         served = {"offered_hz": rate, "events_per_s": args.served / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                   "p99_ms": float(np.percentile(lat, 99) * 1e3), "events": args.served, "slots": 4,
                   "max_batch": B}
+    sess_h.close()
 
     # ---- roofline of the dominant kernel (profile mode: CUDA events around every kernel)
     prof_sess = lst.Session(geom.modules, device=local, profile=True, **tuning)
@@ -427,6 +674,7 @@ def main():
             a[0] += n
             a[1] += ms
     pst = prof_sess.stats()
+    prof_sess.close()
     top = max(acc.items(), key=lambda kv: kv[1][1])
     kname, (nl, tot_ms) = top
     per_launch_ms = tot_ms / nl
@@ -442,6 +690,11 @@ def main():
         achieved = algo / (per_launch_ms * 1e-3) / 1e9
         hbm = {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                "peak_source": peak_src, "algorithmic_bytes": algo}
+    # the MD and LS stages against the HBM roof, with the minimal bytes of each stage
+    map_edges = int(pst["map_edges"])
+    per = lambda k: acc.get(k, [1, 0.0])[1] / reps  # noqa: E731
+    stages = stage_hbm(pst, B, geom.n_modules, map_edges, per("md_count") + per("md_fill"),
+                       per("ls_count") + per("ls_fill"), hbm_peak)
     if ops is not None:
         # the cut chain is FP32 arithmetic on an L2-resident working set: the ALU roof binds
         n_sm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -452,20 +705,30 @@ def main():
                 "frac": achieved / peak, "traffic": recorded_traffic(kname),
                 "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz",
                 "algorithmic_ops": ops, "ls_candidates": pst["ls_candidates"], "ms_per_launch": per_launch_ms,
-                "kernel_share": share, "hbm": hbm}
+                "kernel_share": share, "hbm": hbm, "md_ls_stages_hbm": stages}
     elif hbm is not None:
         roof = {"bound": "hbm", "kernel": kname, "traffic": recorded_traffic(kname), "ms_per_launch": per_launch_ms,
-                "kernel_share": share, **hbm}
+                "kernel_share": share, **hbm, "md_ls_stages_hbm": stages}
     kernel_times = {k: round(v[1] / reps, 4) for k, v in sorted(acc.items(), key=lambda kv: -kv[1][1])}
 
-    # ---- CPU oracle on a bounded sample of the same events
-    cpu = None
+    # ---- the other workloads and the serving sweep (not timed with the headline)
+    legs = workload_legs(local, dev, flush, stream, pending) if args.legs else None
+    sweep = serving_sweep(local) if args.sweep else None
+
+    # ---- CPU leg: the oracle on a bounded sample of the same events, and the oracle check
+    # of every GPU result kept above
+    cpu, parity = None, None
     if args.cpu_sample:
-        rate_cpu, cores, dt = cpu_oracle_rate(events[: args.cpu_sample], geom.modules)
-        cpu = {"value": rate_cpu, "unit": "events/s", "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_sample} of the benchmark's events, threads over events, {dt:.1f} s"}
+        cpu = cpu_oracle_rates(events, geom.modules)
+        checked = check_pending(pending)
+        parity = checked.pop("headline", None)
+        for label, r in checked.items():
+            if legs and label in legs:
+                legs[label]["parity"] = r
 
     clocks = clk.summary()
+    clocks["window"] = (f"{args.steps} timed steps + the sustained run ({sustained['seconds']:.1f} s)"
+                        if sustained else f"{args.steps} timed steps")
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
         "warmup": n_warm, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -477,8 +740,10 @@ def main():
                    "tuning": tuning or "defaults",
                    "l2": "256 MB buffer written between timed steps; inputs rotate over "
                          f"{P} resident batches"},
-        "e2e": e2e, "per_event": per_event, "served": served, "physics": physics,
-        "objects_per_step": {k: stats[k] for k in ("n_md", "n_ls", "n_t3", "n_t5", "n_pt3", "n_pt5", "n_tc")},
+        "parity": parity, "sustained": sustained,
+        "e2e": e2e, "per_event": per_event, "served": served, "serving_sweep": sweep, "workloads": legs,
+        "physics": physics,
+        "objects_per_step": {k: stats[k] for k in OBJ_KEYS},
         "roofline": roof, "kernel_ms_per_step": kernel_times, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": kernels_per_step * args.steps,
     }

@@ -237,6 +237,11 @@ typedef struct lst_stats {
   uint32_t kernels;       /* kernels launched per run */
   uint64_t device_bytes;  /* device memory held by the context */
   uint64_t ls_candidates; /* MD pairs of connected modules the LS selection tested */
+  /* the last lst_serve_replay on the context: batches launched, events in its largest
+   * batch, and the most device memory the context and its slots held at once */
+  uint32_t served_batches, served_max_batch;
+  uint64_t served_peak_bytes;
+  uint64_t map_edges;     /* module pairs in the connection map */
 } lst_stats;
 lst_status lst_get_stats(lst_ctx *ctx, lst_stats *out);
 
@@ -268,9 +273,10 @@ lst_status lst_get_profile(lst_ctx *ctx, lst_profile_entry *buf, uint32_t cap, u
  * *n_tc (host) receives their number (also when it exceeds tc_cap, with
  * LST_ERR_BUFFER_TOO_SMALL).  stream: cudaStream_t to run on (NULL = default stream); the
  * call waits for it.  The call performs no cudaMalloc/cudaFree and no allocating library
- * call.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current and should come before any stream
- * capture.  Every call shares the one array and resets what must start at zero, so calls
+ * call, its first call on a device included: lst_load_geometry, with the context's device
+ * current, looks up the array's device address (cudaGetSymbolAddress, which loads the
+ * library's code for that device and commits the array) and loads every kernel the chain
+ * launches.  Every call shares the one array and resets what must start at zero, so calls
  * whose work overlaps on the GPU (other streams, other threads) race and must not be
  * issued.  Errors: INVALID_ARG, NO_MAP, BUDGET, BAD_INPUT, BUFFER_TOO_SMALL, CUDA. */
 lst_status lst_run_event_static(lst_ctx *ctx, const lst_batch_dev *ev, lst_tc *tc_out, uint32_t tc_cap,
@@ -283,7 +289,13 @@ lst_status lst_run_event_static(lst_ctx *ctx, const lst_batch_dev *ev, lst_tc *t
 typedef struct lst_serve_config {
   uint32_t n_slots;          /* concurrent batch slots (streams), >= 1 */
   uint32_t max_batch;        /* events per slot launch, >= 1 */
-  uint64_t memory_budget;    /* bytes of device memory all slots may hold, 0 = unbounded */
+  uint64_t memory_budget;    /* bytes of device memory the context and all slots may hold,
+                                0 = unbounded.  What the context already holds (geometry,
+                                map, its own pipeline) stays; the rest is split evenly over
+                                the slots, and a slot admits waiting events into its next
+                                batch only while the buffers that batch needs (computed
+                                before anything is allocated) fit its share.  An event that
+                                alone needs more than a slot's share returns LST_ERR_BUDGET. */
   uint32_t share_device;     /* 0: the slots' batches run on the device one after another
                                 (each queued behind the previous launch; a batch's working
                                 set fills most of the L2) while the others pack and collect;
@@ -294,6 +306,8 @@ typedef struct lst_serve_config {
 /* Replays a stream of events: event i becomes visible at arrival_s[i] seconds after the
  * call starts (host clock).  latency_s[i] receives completion time - arrival time and
  * n_tc[i] the number of track candidates.  outs (may be NULL) receives result ids.
+ * lst_get_stats afterwards reports the batches launched, the largest batch and the peak
+ * device memory of the replay.
  * Errors: INVALID_ARG, NO_MAP, BUDGET (an event alone exceeds the budget), OOM, CUDA. */
 lst_status lst_serve_replay(lst_ctx *ctx, const lst_serve_config *cfg, const lst_event *evs,
                             const double *arrival_s, uint32_t n, double *latency_s, uint32_t *n_tc,

@@ -74,7 +74,11 @@ class lst_profile_entry(C.Structure):
 class lst_stats(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in ("n_events", "n_hits", "n_pls", "n_md", "n_ls", "n_t3", "n_t5", "n_pt3",
                                           "n_pt5", "n_tc", "reruns", "kernels")] + [("device_bytes", C.c_uint64),
-                                                                           ("ls_candidates", C.c_uint64)]
+                                                                           ("ls_candidates", C.c_uint64),
+                                                                           ("served_batches", C.c_uint32),
+                                                                           ("served_max_batch", C.c_uint32),
+                                                                           ("served_peak_bytes", C.c_uint64),
+                                                                           ("map_edges", C.c_uint64)]
 
 
 class lst_serve_config(C.Structure):

@@ -24,6 +24,7 @@
 namespace lst {
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
                      MarkFn mark, void* arg, const SideBranch* side = nullptr);
+cudaError_t static_scratch_prepare(int device);  // lst_static.cu
 cudaError_t configure_kernels();
 }
 
@@ -605,8 +606,8 @@ struct Pipeline {
     if (b.bytes != before) graph_valid = false;
   }
 
-  // Grow every buffer to the capacities in c (never shrinks).
-  void ensure_caps(const Caps& c_in) {
+  // Capacities c merged with the current ones (buffers never shrink).
+  Caps merged(const Caps& c_in) const {
     Caps c = c_in;
     c.ev = std::max(c.ev, cap.ev);
     c.hits = std::max(c.hits, cap.hits);
@@ -618,98 +619,136 @@ struct Pipeline {
     c.pt3 = std::max(c.pt3, cap.pt3);
     c.pt5 = std::max(c.pt5, cap.pt5);
     c.tc = std::max(c.tc, cap.tc);
+    return c;
+  }
+
+  // LS partner lists: about two words per hit suffice for PU200-like events; runs that
+  // need more fall back to joining again and the next run gets the learned size
+  uint32_t mask_words(const Caps& c) const {
+    return std::max<uint32_t>(cap_mask, (uint32_t)std::min<uint64_t>(4000000000ull, 4ull * c.hits + 65536));
+  }
+
+  // Every capacity-dependent buffer with the bytes capacities c need: f(buffer, bytes).
+  template <typename F>
+  void for_buffers(const Caps& c, F&& f) {
     const size_t nm = geo->nm;
-    need<uint32_t>(sen_cnt, c.ev * 2 * nm + 1);
-    need<uint32_t>(sen_off, c.ev * 2 * nm + 1);
-    need<uint32_t>(hit_tmp, c.hits);
-    need<uint32_t>(hit_ev, c.hits);
-    need<uint32_t>(hit_idx, c.hits);
-    need<uint32_t>(hit_sen, c.hits);
-    need<float4>(hit4, c.hits);
-    need<uint32_t>(md_hcnt, c.hits);
-    need<uint32_t>(md_hoff, c.hits + 1);
-    need<uint32_t>(md_hmask, c.hits);
-    need<uint32_t>(md_off, c.ev * nm + 1);
-    need<float4>(md_box, 2 * (size_t)c.ev * nm);
-    need<uint32_t>(md_unit, c.md);
-    need<uint32_t>(md_lo_idx, c.md);
-    need<uint32_t>(md_up_idx, c.md);
-    need<float4>(md_pt, 2 * c.md);
-    need<float4>(md_up4, c.md);
-    need<float4>(md_dir4, c.md);
-    need<uint32_t>(ls_cnt, c.md);
-    need<uint32_t>(ls_off, c.md + 1);
-    need<uint32_t>(ls_in, c.ls);
-    need<uint32_t>(ls_out, c.ls);
-    need<uint32_t>(t3_lcnt, c.ls);
-    need<uint32_t>(t3_mask, c.ls);
-    need<uint32_t>(t3_loff, c.ls + 1);
-    need<uint32_t>(t3_off, c.md + 1);
-    need<uint32_t>(t3_a, c.t3);
-    need<uint4>(t3_md4, c.t3);
-    need<uint32_t>(t3_b, c.t3);
-    need<uint32_t>(t3_c, c.t3);
-    need<uint32_t>(t5_tcnt, c.t3);
-    need<uint32_t>(t5_mask, c.t3);
-    need<uint32_t>(t5_toff, c.t3 + 1);
-    need<uint32_t>(t5_off, c.md + 1);
-    for (auto& b : t5_m) need<uint32_t>(b, c.t5);
-    need<float>(t5_score, c.t5);
-    need<uint4>(t5_md8, 2 * (size_t)c.t5);
-    need<float>(t5_kfull, c.t5);
-    need<uint32_t>(pls_ev, c.pls);
-    need<uint32_t>(pls_ncand, c.pls);
-    need<uint32_t>(pls_cand, (size_t)c.pls * MAX_CAND);
-    need<uint32_t>(pls_mdpass, (size_t)c.pls * PLS_MD_CAP);
-    need<uint32_t>(pls_nmdpass, c.pls);
-    need<float4>(pls_h0, c.pls);
-    need<float4>(pls_h1, c.pls);
-    need<float>(pls_pt, c.pls);
-    need<uint32_t>(pt3_icnt, c.pls);
-    need<uint32_t>(pt3_ioff, c.pls + 1);
-    need<uint32_t>(pt3_item_p, (size_t)c.pls * PLS_ITEMS);
-    need<uint32_t>(pt3_xcnt, (size_t)c.pls * PLS_ITEMS);
-    need<uint32_t>(pt3_xoff, (size_t)c.pls * PLS_ITEMS + 1);
-    need<uint32_t>(pt3_xmask, (size_t)c.pls * PLS_ITEMS);
-    need<uint32_t>(pt3_off, c.pls + 1);
-    need<uint32_t>(pt3_pls, c.pt3);
-    need<uint32_t>(pt3_obj, c.pt3);
-    need<float>(pt3_score, c.pt3);
-    need<uint32_t>(pt5_xcnt, c.pt3);
-    need<uint32_t>(pt5_xoff, c.pt3 + 1);
-    need<uint32_t>(pt5_xmask, c.pt3);
-    need<uint32_t>(pt5_off, c.pls + 1);
-    need<uint32_t>(pt5_pls, c.pt5);
-    need<uint32_t>(pt5_obj, c.pt5);
-    need<float>(pt5_score, c.pt5);
-    need<uint32_t>(c5_cnt, c.md + 1);
-    need<uint32_t>(c5_off, c.md + 1);
-    need<uint32_t>(c5_list, (size_t)5 * c.pt5);
-    need<uint32_t>(c3_cnt, c.md + 1);
-    need<uint32_t>(c3_off, c.md + 1);
-    need<uint32_t>(c3_list, (size_t)3 * c.pt3);
-    need<uint32_t>(ct_cnt, c.md + 1);
-    need<uint32_t>(ct_off, c.md + 1);
-    need<uint32_t>(ct_list, (size_t)5 * c.t5);
-    need<uint32_t>(alive5, c.pt5);
-    need<uint32_t>(alive3, c.pt3);
-    need<uint32_t>(alivet, c.t5);
-    need<uint32_t>(plstc, c.pls);
-    need<uint32_t>(cross3, c.pt3);
-    need<uint32_t>(crosst, c.t5);
-    need<uint32_t>(sa5, c.pt5 + 1);
-    need<uint32_t>(sa3, c.pt3 + 1);
-    need<uint32_t>(sat, c.t5 + 1);
-    need<uint32_t>(sap, c.pls + 1);
-    need<uint32_t>(tc_ev_off, c.ev + 1);
-    need<lst_tc>(tc, c.tc);
-    need<uint32_t>(mask_off, c.md);
-    // LS partner lists: about two words per hit suffice for PU200-like events; runs that
-    // need more fall back to joining again and the next run gets the learned size
-    const uint32_t want = std::max<uint32_t>(cap_mask, (uint32_t)std::min<uint64_t>(4000000000ull, 4ull * c.hits + 65536));
-    need<uint32_t>(mask, want);
-    cap_mask = want;
+    f(sen_cnt, std::max<size_t>(c.ev * 2 * nm + 1, 1) * sizeof(uint32_t));
+    f(sen_off, std::max<size_t>(c.ev * 2 * nm + 1, 1) * sizeof(uint32_t));
+    f(hit_tmp, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
+    f(hit_ev, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
+    f(hit_idx, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
+    f(hit_sen, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
+    f(hit4, std::max<size_t>(c.hits, 1) * sizeof(float4));
+    f(md_hcnt, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
+    f(md_hoff, std::max<size_t>(c.hits + 1, 1) * sizeof(uint32_t));
+    f(md_hmask, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
+    f(md_off, std::max<size_t>(c.ev * nm + 1, 1) * sizeof(uint32_t));
+    f(md_box, std::max<size_t>(2 * (size_t)c.ev * nm, 1) * sizeof(float4));
+    f(md_unit, std::max<size_t>(c.md, 1) * sizeof(uint32_t));
+    f(md_lo_idx, std::max<size_t>(c.md, 1) * sizeof(uint32_t));
+    f(md_up_idx, std::max<size_t>(c.md, 1) * sizeof(uint32_t));
+    f(md_pt, std::max<size_t>(2 * c.md, 1) * sizeof(float4));
+    f(md_up4, std::max<size_t>(c.md, 1) * sizeof(float4));
+    f(md_dir4, std::max<size_t>(c.md, 1) * sizeof(float4));
+    f(ls_cnt, std::max<size_t>(c.md, 1) * sizeof(uint32_t));
+    f(ls_off, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    f(ls_in, std::max<size_t>(c.ls, 1) * sizeof(uint32_t));
+    f(ls_out, std::max<size_t>(c.ls, 1) * sizeof(uint32_t));
+    f(t3_lcnt, std::max<size_t>(c.ls, 1) * sizeof(uint32_t));
+    f(t3_mask, std::max<size_t>(c.ls, 1) * sizeof(uint32_t));
+    f(t3_loff, std::max<size_t>(c.ls + 1, 1) * sizeof(uint32_t));
+    f(t3_off, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    f(t3_a, std::max<size_t>(c.t3, 1) * sizeof(uint32_t));
+    f(t3_md4, std::max<size_t>(c.t3, 1) * sizeof(uint4));
+    f(t3_b, std::max<size_t>(c.t3, 1) * sizeof(uint32_t));
+    f(t3_c, std::max<size_t>(c.t3, 1) * sizeof(uint32_t));
+    f(t5_tcnt, std::max<size_t>(c.t3, 1) * sizeof(uint32_t));
+    f(t5_mask, std::max<size_t>(c.t3, 1) * sizeof(uint32_t));
+    f(t5_toff, std::max<size_t>(c.t3 + 1, 1) * sizeof(uint32_t));
+    f(t5_off, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    for (auto& b : t5_m) f(b, std::max<size_t>(c.t5, 1) * sizeof(uint32_t));
+    f(t5_score, std::max<size_t>(c.t5, 1) * sizeof(float));
+    f(t5_md8, std::max<size_t>(2 * (size_t)c.t5, 1) * sizeof(uint4));
+    f(t5_kfull, std::max<size_t>(c.t5, 1) * sizeof(float));
+    f(pls_ev, std::max<size_t>(c.pls, 1) * sizeof(uint32_t));
+    f(pls_ncand, std::max<size_t>(c.pls, 1) * sizeof(uint32_t));
+    f(pls_cand, std::max<size_t>((size_t)c.pls * MAX_CAND, 1) * sizeof(uint32_t));
+    f(pls_mdpass, std::max<size_t>((size_t)c.pls * PLS_MD_CAP, 1) * sizeof(uint32_t));
+    f(pls_nmdpass, std::max<size_t>(c.pls, 1) * sizeof(uint32_t));
+    f(pls_h0, std::max<size_t>(c.pls, 1) * sizeof(float4));
+    f(pls_h1, std::max<size_t>(c.pls, 1) * sizeof(float4));
+    f(pls_pt, std::max<size_t>(c.pls, 1) * sizeof(float));
+    f(pt3_icnt, std::max<size_t>(c.pls, 1) * sizeof(uint32_t));
+    f(pt3_ioff, std::max<size_t>(c.pls + 1, 1) * sizeof(uint32_t));
+    f(pt3_item_p, std::max<size_t>((size_t)c.pls * PLS_ITEMS, 1) * sizeof(uint32_t));
+    f(pt3_xcnt, std::max<size_t>((size_t)c.pls * PLS_ITEMS, 1) * sizeof(uint32_t));
+    f(pt3_xoff, std::max<size_t>((size_t)c.pls * PLS_ITEMS + 1, 1) * sizeof(uint32_t));
+    f(pt3_xmask, std::max<size_t>((size_t)c.pls * PLS_ITEMS, 1) * sizeof(uint32_t));
+    f(pt3_off, std::max<size_t>(c.pls + 1, 1) * sizeof(uint32_t));
+    f(pt3_pls, std::max<size_t>(c.pt3, 1) * sizeof(uint32_t));
+    f(pt3_obj, std::max<size_t>(c.pt3, 1) * sizeof(uint32_t));
+    f(pt3_score, std::max<size_t>(c.pt3, 1) * sizeof(float));
+    f(pt5_xcnt, std::max<size_t>(c.pt3, 1) * sizeof(uint32_t));
+    f(pt5_xoff, std::max<size_t>(c.pt3 + 1, 1) * sizeof(uint32_t));
+    f(pt5_xmask, std::max<size_t>(c.pt3, 1) * sizeof(uint32_t));
+    f(pt5_off, std::max<size_t>(c.pls + 1, 1) * sizeof(uint32_t));
+    f(pt5_pls, std::max<size_t>(c.pt5, 1) * sizeof(uint32_t));
+    f(pt5_obj, std::max<size_t>(c.pt5, 1) * sizeof(uint32_t));
+    f(pt5_score, std::max<size_t>(c.pt5, 1) * sizeof(float));
+    f(c5_cnt, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    f(c5_off, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    f(c5_list, std::max<size_t>((size_t)5 * c.pt5, 1) * sizeof(uint32_t));
+    f(c3_cnt, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    f(c3_off, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    f(c3_list, std::max<size_t>((size_t)3 * c.pt3, 1) * sizeof(uint32_t));
+    f(ct_cnt, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    f(ct_off, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
+    f(ct_list, std::max<size_t>((size_t)5 * c.t5, 1) * sizeof(uint32_t));
+    f(alive5, std::max<size_t>(c.pt5, 1) * sizeof(uint32_t));
+    f(alive3, std::max<size_t>(c.pt3, 1) * sizeof(uint32_t));
+    f(alivet, std::max<size_t>(c.t5, 1) * sizeof(uint32_t));
+    f(plstc, std::max<size_t>(c.pls, 1) * sizeof(uint32_t));
+    f(cross3, std::max<size_t>(c.pt3, 1) * sizeof(uint32_t));
+    f(crosst, std::max<size_t>(c.t5, 1) * sizeof(uint32_t));
+    f(sa5, std::max<size_t>(c.pt5 + 1, 1) * sizeof(uint32_t));
+    f(sa3, std::max<size_t>(c.pt3 + 1, 1) * sizeof(uint32_t));
+    f(sat, std::max<size_t>(c.t5 + 1, 1) * sizeof(uint32_t));
+    f(sap, std::max<size_t>(c.pls + 1, 1) * sizeof(uint32_t));
+    f(tc_ev_off, std::max<size_t>(c.ev + 1, 1) * sizeof(uint32_t));
+    f(tc, std::max<size_t>(c.tc, 1) * sizeof(lst_tc));
+    f(mask_off, std::max<size_t>(c.md, 1) * sizeof(uint32_t));
+    f(mask, (size_t)mask_words(c) * sizeof(uint32_t));
+  }
+
+  // Grow every buffer to the capacities in c (never shrinks).
+  void ensure_caps(const Caps& c_in) {
+    const Caps c = merged(c_in);
+    const uint32_t words = mask_words(c);
+    for_buffers(c, [&](DevBuf& b, size_t bytes) {
+      const size_t before = b.bytes;
+      b.ensure(bytes, dev_bytes);
+      if (b.bytes != before) graph_valid = false;
+    });
+    cap_mask = words;
     cap = c;
+  }
+
+  // Device bytes the pipeline would hold after ensure_caps(c) and ensure_inputs(ne, nh, np),
+  // without allocating anything (serving admission under a memory budget).
+  uint64_t bytes_after(const Caps& c_in, uint32_t ne, uint32_t nh, uint32_t np) {
+    uint64_t t = dev_bytes;
+    auto add = [&](const DevBuf& b, size_t bytes) {
+      if (bytes > b.bytes) t += bytes - b.bytes;
+    };
+    for_buffers(merged(c_in), add);
+    add(in_x, std::max<size_t>(nh, 1) * 4);
+    add(in_y, std::max<size_t>(nh, 1) * 4);
+    add(in_z, std::max<size_t>(nh, 1) * 4);
+    add(in_det, std::max<size_t>(nh, 1) * 4);
+    add(in_hoff, (size_t)(ne + 1) * 4);
+    add(in_pls, std::max<size_t>(np, 1) * sizeof(PlsIn));
+    add(in_poff, (size_t)(ne + 1) * 4);
+    return t;
   }
 
   void learn_mask(const Hdr& h) {
@@ -1035,6 +1074,9 @@ struct lst_ctx {
   };
   AsyncSlot slots[2];
   uint64_t next_ticket = 1;
+  // last lst_serve_replay: batches launched, largest batch, peak device bytes
+  uint32_t served_batches = 0, served_max_batch = 0;
+  uint64_t served_peak_bytes = 0;
 };
 
 namespace {
@@ -1251,6 +1293,8 @@ lst_status lst_load_geometry(const lst_module_desc* mods, uint32_t n_mods, const
     c->geo.load(mods, n_mods);
     c->geo.upload_tables();
     c->main.init(&c->geo, c->cfg, c->n_sm);
+    // the allocation-free entry point's array and kernels, loaded now so that its calls allocate nothing
+    CK(static_scratch_prepare(c->device));
     return LST_OK;
   });
   if (s != LST_OK) {
@@ -1508,6 +1552,10 @@ lst_status lst_get_stats(lst_ctx* c, lst_stats* out) {
   *out = c->stats;
   out->reruns = c->reruns;
   out->device_bytes = c->main.dev_bytes + c->geo.dev_bytes;
+  out->served_batches = c->served_batches;
+  out->served_max_batch = c->served_max_batch;
+  out->served_peak_bytes = c->served_peak_bytes;
+  out->map_edges = c->geo.conn.size();
   return LST_OK;
 }
 
@@ -1539,16 +1587,21 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
       s.P->r_md = c->main.r_md; s.P->r_ls = c->main.r_ls; s.P->r_t3 = c->main.r_t3; s.P->r_t5 = c->main.r_t5;
       s.P->r_pt3 = c->main.r_pt3; s.P->r_pt5 = c->main.r_pt5;
     }
+    // Memory budget: the context's own buffers stay, the rest is split evenly over the
+    // slots; a slot admits events only while its buffers for the batch fit its share.
     const uint64_t budget = cfg->memory_budget;
-    std::vector<std::atomic<uint64_t>> slot_bytes(slots.size());
-    auto held_by_others = [&](size_t me) {
-      uint64_t t = c->geo.dev_bytes + c->main.dev_bytes;
-      for (size_t k = 0; k < slots.size(); k++)
-        if (k != me) t += slot_bytes[k].load();
-      return t;
+    const uint64_t base = c->geo.dev_bytes + c->main.dev_bytes;
+    if (budget && budget <= base) return fail(c, LST_ERR_BUDGET, "the memory budget is below the context's resident buffers");
+    const uint64_t slot_share = budget ? (budget - base) / slots.size() : ~0ull;
+    std::atomic<uint32_t> n_batches{0}, max_taken{0};
+    std::atomic<uint64_t> peak{0};
+    auto fits = [&](Pipeline& P, uint32_t ne, uint64_t nh, uint64_t np) {
+      if (!budget) return true;
+      if (nh > 0xF0000000ull || np > 0x0F000000ull) return false;
+      return P.bytes_after(P.estimate(ne, (uint32_t)nh, (uint32_t)np), ne, (uint32_t)nh, (uint32_t)np) <= slot_share;
     };
-    // Before the clock starts: size every slot for a full batch of typical events (from the
-    // first events of the stream) and capture its graph, unless that alone breaks the budget.
+    // Before the clock starts: size every slot for the largest batch of typical events (from
+    // the first events of the stream) that fits its share, up to max_batch, and capture its graph.
     {
       const uint32_t m = std::min<uint32_t>(n, 64);
       uint64_t sh = 0, sp = 0;
@@ -1556,16 +1609,15 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
         sh += evs[i].n_hits;
         sp += evs[i].n_pls;
       }
-      const uint32_t bh = (uint32_t)std::min<uint64_t>(0xF0000000ull, sh * 3 / 2 * cfg->max_batch / m + 1);
-      const uint32_t bp = (uint32_t)std::min<uint64_t>(0x0F000000ull, sp * 3 / 2 * cfg->max_batch / m + 1);
+      auto hits_for = [&](uint32_t b) { return std::min<uint64_t>(0xF0000000ull, sh * 3 / 2 * b / m + 1); };
+      auto pls_for = [&](uint32_t b) { return std::min<uint64_t>(0x0F000000ull, sp * 3 / 2 * b / m + 1); };
+      uint32_t b = cfg->max_batch;
+      while (b > 0 && !fits(*slots[0].P, b, hits_for(b), pls_for(b))) b = b > 8 ? b * 3 / 4 : b - 1;
       for (size_t k = 0; k < slots.size(); k++) {
         Pipeline& P = *slots[k].P;
-        const uint64_t before = P.dev_bytes;
-        P.ensure_caps(P.estimate(cfg->max_batch, bh, bp));
-        P.ensure_inputs(cfg->max_batch, bh, bp);
-        slot_bytes[k] = P.dev_bytes;
-        if (budget && held_by_others(k) + P.dev_bytes > budget && before == 0) {
-          // too large for the budget: keep the slot small, it grows per batch
+        if (b > 0) {
+          P.ensure_caps(P.estimate(b, (uint32_t)hits_for(b), (uint32_t)pls_for(b)));
+          P.ensure_inputs(b, (uint32_t)hits_for(b), (uint32_t)pls_for(b));
         }
         lst_event empty{};
         pack_host_events(P, &empty, 1);
@@ -1573,6 +1625,14 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
         if (!P.wait(0)) return fail(c, LST_ERR_TIMEOUT, "slot warm-up timed out");
       }
     }
+    auto note_bytes = [&] {
+      uint64_t t = base;
+      for (auto& sl : slots) t += sl.P->dev_bytes;
+      uint64_t p = peak.load();
+      while (t > p && !peak.compare_exchange_weak(p, t)) {
+      }
+    };
+    note_bytes();
     // Shared state: arrived events not yet taken, and the first error of any worker.
     std::mutex qm;
     // unless the slots share the device, each batch's chain is queued behind the batch
@@ -1621,13 +1681,12 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
             uint64_t nh = 0, np = 0;
             while (!queue.empty() && take.size() < cfg->max_batch) {
               const lst_event& e = evs[queue.front()];
-              if (budget && !take.empty()) {
-                const Caps est = P.estimate((uint32_t)take.size() + 1, (uint32_t)(nh + e.n_hits),
-                                            (uint32_t)(np + e.n_pls));
-                const uint64_t bytes = (uint64_t)est.hits * 48 + (uint64_t)est.md * 96 + (uint64_t)est.ls * 16 +
-                                       (uint64_t)est.t3 * 24 + (uint64_t)est.t5 * 80 + (uint64_t)est.pls * 220 +
-                                       (uint64_t)(est.pt3 + est.pt5) * 40 + (uint64_t)est.ev * c->geo.nm * 24;
-                if (held_by_others(k) + std::max<uint64_t>(bytes, P.dev_bytes) > budget) break;
+              if (!fits(P, (uint32_t)take.size() + 1, nh + e.n_hits, np + e.n_pls)) {
+                if (take.empty()) {
+                  lk.unlock();
+                  return set_error(LST_ERR_BUDGET, "one event alone needs more than a slot's share of the memory budget");
+                }
+                break;
               }
               take.push_back(queue.front());
               nh += e.n_hits;
@@ -1642,9 +1701,10 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
           for (uint32_t i : take) batch.push_back(evs[i]);
           pack_host_events(P, batch.data(), (uint32_t)batch.size());
           P.ensure_caps(P.estimate((uint32_t)batch.size(), P.n_hits, P.n_pls));
-          slot_bytes[k] = P.dev_bytes;
-          if (budget && held_by_others(k) + P.dev_bytes > budget && take.size() == 1)
-            return set_error(LST_ERR_BUDGET, "one event alone exceeds the memory budget");
+          note_bytes();
+          n_batches++;
+          for (uint32_t mt = max_taken.load(); take.size() > mt && !max_taken.compare_exchange_weak(mt, (uint32_t)take.size());) {
+          }
           for (int attempt = 0;; attempt++) {
             if (share) {
               P.launch(true);
@@ -1660,9 +1720,9 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
               P.learn(h);
               break;
             }
-            slot_bytes[k] = P.dev_bytes;
-            if (budget && held_by_others(k) + P.dev_bytes > budget)
-              return set_error(LST_ERR_BUDGET, "memory budget exceeded by a batch");
+            note_bytes();
+            if (budget && P.dev_bytes > slot_share)
+              return set_error(LST_ERR_BUDGET, "a batch outgrew its slot's share of the memory budget");
             if (attempt > 10) return set_error(LST_ERR_OOM, "object lists kept outgrowing their storage");
             std::lock_guard<std::mutex> lk(c->mu);
             c->reruns++;
@@ -1715,6 +1775,12 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
     qcv.notify_all();
     for (auto& t : th) t.join();
     if (wall_s) *wall_s = now_s() - t0;
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      c->served_batches = n_batches.load();
+      c->served_max_batch = max_taken.load();
+      c->served_peak_bytes = peak.load();
+    }
     if (status != LST_OK) return fail(c, status, err_msg);
     return LST_OK;
   });

@@ -2183,6 +2183,28 @@ cudaError_t configure_kernels() {
   return cudaFuncSetAttribute(k_ls_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// Loads every kernel of the chain on the current device (cudaFuncGetAttributes resolves
+// each function, which lazy module loading otherwise defers to its first launch), so that
+// later launches allocate nothing for code or module data.
+cudaError_t preload_kernels() {
+  const void* ks[] = {
+      (const void*)k_scan_reduce, (const void*)k_scan_apply, (const void*)k_scan_reduce_multi,
+      (const void*)k_scan_apply_multi, (const void*)k_zero, (const void*)k_hits_count, (const void*)k_hits_scatter,
+      (const void*)k_hits_sort, (const void*)k_md_count, (const void*)k_md_fill, (const void*)k_ls_fill,
+      (const void*)k_ls_count, (const void*)k_t3_count, (const void*)k_t3_fill, (const void*)k_t5_count,
+      (const void*)k_t5_fill, (const void*)k_pls_prep, (const void*)k_pls_sort, (const void*)k_md_box,
+      (const void*)k_pt3_first_anchor, (const void*)k_pt3_items, (const void*)k_pt3_count, (const void*)k_pt3_fill,
+      (const void*)k_pt5_count, (const void*)k_pt5_fill, (const void*)k_csr_count, (const void*)k_csr_fill,
+      (const void*)k_kill_pt5, (const void*)k_cross_pt3, (const void*)k_kill_pt3, (const void*)k_cross_t5,
+      (const void*)k_kill_t5, (const void*)k_tc_offsets, (const void*)k_tc_write};
+  for (const void* k : ks) {
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, k);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Enqueues the whole chain on stream s; returns the number of kernels launched.  mark (may
 // be null) is called after every launch with the index of its name in kKernelNames.
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,

@@ -21,6 +21,8 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
                      MarkFn mark, void* arg, const SideBranch* side = nullptr);
 bool ctx_views(lst_ctx* c, GeoView* g, MethodConst* m, Launch* l, int* device, bool* have_map);
 void ctx_set_error(lst_ctx* c, const std::string& msg);
+cudaError_t preload_kernels();
+cudaError_t static_scratch_prepare(int device);
 }  // namespace lst
 
 using namespace lst;
@@ -48,118 +50,134 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void* g_scratch_dev[MAX_DEVICES] = {};
 
-struct Carver {
-  char* base;
-  size_t off;
+// Sinks for carve_layout: Sizer only adds up the 256-byte aligned extents (usable in a
+// constant expression), Placer also points every list into the scratch.
+struct Sizer {
+  size_t off = 0;
   template <typename T>
-  T* take(size_t n) {
+  constexpr void take(T*&, size_t n) {
     off = (off + 255) & ~size_t(255);
-    T* p = reinterpret_cast<T*>(base + off);
     off += n * sizeof(T);
-    return p;
+  }
+};
+struct Placer {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  void take(T*& p, size_t n) {
+    off = (off + 255) & ~size_t(255);
+    p = reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T);
   }
 };
 
-// Lays every list of one event out in the scratch; returns the bytes used.
-size_t carve(char* base, BufView& B) {
-  Carver c{base, 0};
-  B.hdr = c.take<Hdr>(1);
+// Lays every list of one event out in the scratch (through sink c); returns the bytes used.
+template <typename Sink>
+constexpr size_t carve_layout(Sink& c, BufView& B) {
+  c.take(B.hdr, 1);
   B.cap_ev = 1; B.cap_hits = MAX_HITS; B.cap_md = MAX_MD; B.cap_ls = MAX_LS; B.cap_t3 = MAX_T3;
   B.cap_t5 = MAX_T5; B.cap_pls = MAX_PLS; B.cap_pt3 = MAX_PT3; B.cap_pt5 = MAX_PT5;
-  B.sen_cnt = c.take<uint32_t>(2 * MAX_MODULES + 1);
-  B.sen_off = c.take<uint32_t>(2 * MAX_MODULES + 1);
-  B.hit_tmp = c.take<uint32_t>(MAX_HITS);
-  B.hit_ev = c.take<uint32_t>(MAX_HITS);
-  B.hit_idx = c.take<uint32_t>(MAX_HITS);
-  B.hit4 = c.take<float4>(MAX_HITS);
-  B.hit_sen = c.take<uint32_t>(MAX_HITS);
-  B.md_hcnt = c.take<uint32_t>(MAX_HITS);
-  B.md_hoff = c.take<uint32_t>(MAX_HITS + 1);
-  B.md_hmask = c.take<uint32_t>(MAX_HITS);
-  B.md_off = c.take<uint32_t>(MAX_MODULES + 1);
-  B.md_box = c.take<float4>(2 * (size_t)MAX_MODULES);
-  B.md_unit = c.take<uint32_t>(MAX_MD);
-  B.md_lo_idx = c.take<uint32_t>(MAX_MD);
-  B.md_up_idx = c.take<uint32_t>(MAX_MD);
-  B.md_pt = c.take<float4>(2 * MAX_MD);
-  B.md_up4 = c.take<float4>(MAX_MD);
-  B.md_dir4 = c.take<float4>(MAX_MD);
-  B.ls_cnt = c.take<uint32_t>(MAX_MD);
-  B.ls_off = c.take<uint32_t>(MAX_MD + 1);
-  B.ls_in = c.take<uint32_t>(MAX_LS);
-  B.ls_out = c.take<uint32_t>(MAX_LS);
-  B.t3_lcnt = c.take<uint32_t>(MAX_LS);
-  B.t3_mask = c.take<uint32_t>(MAX_LS);
-  B.t3_loff = c.take<uint32_t>(MAX_LS + 1);
-  B.t3_off = c.take<uint32_t>(MAX_MD + 1);
-  B.t3_a = c.take<uint32_t>(MAX_T3);
-  B.t3_b = c.take<uint32_t>(MAX_T3);
-  B.t3_c = c.take<uint32_t>(MAX_T3);
-  B.t3_md4 = c.take<uint4>(MAX_T3);
-  B.t5_tcnt = c.take<uint32_t>(MAX_T3);
-  B.t5_mask = c.take<uint32_t>(MAX_T3);
-  B.t5_toff = c.take<uint32_t>(MAX_T3 + 1);
-  B.t5_off = c.take<uint32_t>(MAX_MD + 1);
-  B.t5_m0 = c.take<uint32_t>(MAX_T5);
-  B.t5_m1 = c.take<uint32_t>(MAX_T5);
-  B.t5_m2 = c.take<uint32_t>(MAX_T5);
-  B.t5_m3 = c.take<uint32_t>(MAX_T5);
-  B.t5_m4 = c.take<uint32_t>(MAX_T5);
-  B.t5_score = c.take<float>(MAX_T5);
-  B.t5_kfull = c.take<float>(MAX_T5);
-  B.t5_md8 = c.take<uint4>(2 * MAX_T5);
-  B.pls_ev = c.take<uint32_t>(MAX_PLS);
-  B.pls_ncand = c.take<uint32_t>(MAX_PLS);
-  B.pls_cand = c.take<uint32_t>((size_t)MAX_PLS * MAX_CAND);
-  B.pls_mdpass = c.take<uint32_t>((size_t)MAX_PLS * PLS_MD_CAP);
-  B.pls_nmdpass = c.take<uint32_t>(MAX_PLS);
-  B.pls_h0 = c.take<float4>(MAX_PLS);
-  B.pls_h1 = c.take<float4>(MAX_PLS);
-  B.pls_pt = c.take<float>(MAX_PLS);
-  B.pt3_icnt = c.take<uint32_t>(MAX_PLS);
-  B.pt3_ioff = c.take<uint32_t>(MAX_PLS + 1);
-  B.pt3_item_p = c.take<uint32_t>((size_t)MAX_PLS * PLS_ITEMS);
-  B.pt3_xcnt = c.take<uint32_t>((size_t)MAX_PLS * PLS_ITEMS);
-  B.pt3_xoff = c.take<uint32_t>((size_t)MAX_PLS * PLS_ITEMS + 1);
-  B.pt3_xmask = c.take<uint32_t>((size_t)MAX_PLS * PLS_ITEMS);
-  B.pt3_off = c.take<uint32_t>(MAX_PLS + 1);
-  B.pt3_pls = c.take<uint32_t>(MAX_PT3);
-  B.pt3_obj = c.take<uint32_t>(MAX_PT3);
-  B.pt3_score = c.take<float>(MAX_PT3);
-  B.pt5_xcnt = c.take<uint32_t>(MAX_PT3);
-  B.pt5_xoff = c.take<uint32_t>(MAX_PT3 + 1);
-  B.pt5_xmask = c.take<uint32_t>(MAX_PT3);
-  B.pt5_off = c.take<uint32_t>(MAX_PLS + 1);
-  B.pt5_pls = c.take<uint32_t>(MAX_PT5);
-  B.pt5_obj = c.take<uint32_t>(MAX_PT5);
-  B.pt5_score = c.take<float>(MAX_PT5);
-  B.c5_cnt = c.take<uint32_t>(MAX_MD + 1);
-  B.c5_off = c.take<uint32_t>(MAX_MD + 1);
-  B.c5_list = c.take<uint32_t>((size_t)5 * MAX_PT5);
-  B.c3_cnt = c.take<uint32_t>(MAX_MD + 1);
-  B.c3_off = c.take<uint32_t>(MAX_MD + 1);
-  B.c3_list = c.take<uint32_t>((size_t)3 * MAX_PT3);
-  B.ct_cnt = c.take<uint32_t>(MAX_MD + 1);
-  B.ct_off = c.take<uint32_t>(MAX_MD + 1);
-  B.ct_list = c.take<uint32_t>((size_t)5 * MAX_T5);
-  B.alive5 = c.take<uint32_t>(MAX_PT5);
-  B.alive3 = c.take<uint32_t>(MAX_PT3);
-  B.alivet = c.take<uint32_t>(MAX_T5);
-  B.plstc = c.take<uint32_t>(MAX_PLS);
-  B.cross3 = c.take<uint32_t>(MAX_PT3);
-  B.crosst = c.take<uint32_t>(MAX_T5);
-  B.sa5 = c.take<uint32_t>(MAX_PT5 + 1);
-  B.sa3 = c.take<uint32_t>(MAX_PT3 + 1);
-  B.sat = c.take<uint32_t>(MAX_T5 + 1);
-  B.sap = c.take<uint32_t>(MAX_PLS + 1);
-  B.tc_ev_off = c.take<uint32_t>(2);
-  B.scan_part = c.take<uint32_t>(4 * 1024);  // partials of up to four scans per launch
-  B.scan_part2 = c.take<uint32_t>(1024);
-  B.mask_off = c.take<uint32_t>(MAX_MD);
+  c.take(B.sen_cnt, 2 * MAX_MODULES + 1);
+  c.take(B.sen_off, 2 * MAX_MODULES + 1);
+  c.take(B.hit_tmp, MAX_HITS);
+  c.take(B.hit_ev, MAX_HITS);
+  c.take(B.hit_idx, MAX_HITS);
+  c.take(B.hit4, MAX_HITS);
+  c.take(B.hit_sen, MAX_HITS);
+  c.take(B.md_hcnt, MAX_HITS);
+  c.take(B.md_hoff, MAX_HITS + 1);
+  c.take(B.md_hmask, MAX_HITS);
+  c.take(B.md_off, MAX_MODULES + 1);
+  c.take(B.md_box, 2 * (size_t)MAX_MODULES);
+  c.take(B.md_unit, MAX_MD);
+  c.take(B.md_lo_idx, MAX_MD);
+  c.take(B.md_up_idx, MAX_MD);
+  c.take(B.md_pt, 2 * MAX_MD);
+  c.take(B.md_up4, MAX_MD);
+  c.take(B.md_dir4, MAX_MD);
+  c.take(B.ls_cnt, MAX_MD);
+  c.take(B.ls_off, MAX_MD + 1);
+  c.take(B.ls_in, MAX_LS);
+  c.take(B.ls_out, MAX_LS);
+  c.take(B.t3_lcnt, MAX_LS);
+  c.take(B.t3_mask, MAX_LS);
+  c.take(B.t3_loff, MAX_LS + 1);
+  c.take(B.t3_off, MAX_MD + 1);
+  c.take(B.t3_a, MAX_T3);
+  c.take(B.t3_b, MAX_T3);
+  c.take(B.t3_c, MAX_T3);
+  c.take(B.t3_md4, MAX_T3);
+  c.take(B.t5_tcnt, MAX_T3);
+  c.take(B.t5_mask, MAX_T3);
+  c.take(B.t5_toff, MAX_T3 + 1);
+  c.take(B.t5_off, MAX_MD + 1);
+  c.take(B.t5_m0, MAX_T5);
+  c.take(B.t5_m1, MAX_T5);
+  c.take(B.t5_m2, MAX_T5);
+  c.take(B.t5_m3, MAX_T5);
+  c.take(B.t5_m4, MAX_T5);
+  c.take(B.t5_score, MAX_T5);
+  c.take(B.t5_kfull, MAX_T5);
+  c.take(B.t5_md8, 2 * MAX_T5);
+  c.take(B.pls_ev, MAX_PLS);
+  c.take(B.pls_ncand, MAX_PLS);
+  c.take(B.pls_cand, (size_t)MAX_PLS * MAX_CAND);
+  c.take(B.pls_mdpass, (size_t)MAX_PLS * PLS_MD_CAP);
+  c.take(B.pls_nmdpass, MAX_PLS);
+  c.take(B.pls_h0, MAX_PLS);
+  c.take(B.pls_h1, MAX_PLS);
+  c.take(B.pls_pt, MAX_PLS);
+  c.take(B.pt3_icnt, MAX_PLS);
+  c.take(B.pt3_ioff, MAX_PLS + 1);
+  c.take(B.pt3_item_p, (size_t)MAX_PLS * PLS_ITEMS);
+  c.take(B.pt3_xcnt, (size_t)MAX_PLS * PLS_ITEMS);
+  c.take(B.pt3_xoff, (size_t)MAX_PLS * PLS_ITEMS + 1);
+  c.take(B.pt3_xmask, (size_t)MAX_PLS * PLS_ITEMS);
+  c.take(B.pt3_off, MAX_PLS + 1);
+  c.take(B.pt3_pls, MAX_PT3);
+  c.take(B.pt3_obj, MAX_PT3);
+  c.take(B.pt3_score, MAX_PT3);
+  c.take(B.pt5_xcnt, MAX_PT3);
+  c.take(B.pt5_xoff, MAX_PT3 + 1);
+  c.take(B.pt5_xmask, MAX_PT3);
+  c.take(B.pt5_off, MAX_PLS + 1);
+  c.take(B.pt5_pls, MAX_PT5);
+  c.take(B.pt5_obj, MAX_PT5);
+  c.take(B.pt5_score, MAX_PT5);
+  c.take(B.c5_cnt, MAX_MD + 1);
+  c.take(B.c5_off, MAX_MD + 1);
+  c.take(B.c5_list, (size_t)5 * MAX_PT5);
+  c.take(B.c3_cnt, MAX_MD + 1);
+  c.take(B.c3_off, MAX_MD + 1);
+  c.take(B.c3_list, (size_t)3 * MAX_PT3);
+  c.take(B.ct_cnt, MAX_MD + 1);
+  c.take(B.ct_off, MAX_MD + 1);
+  c.take(B.ct_list, (size_t)5 * MAX_T5);
+  c.take(B.alive5, MAX_PT5);
+  c.take(B.alive3, MAX_PT3);
+  c.take(B.alivet, MAX_T5);
+  c.take(B.plstc, MAX_PLS);
+  c.take(B.cross3, MAX_PT3);
+  c.take(B.crosst, MAX_T5);
+  c.take(B.sa5, MAX_PT5 + 1);
+  c.take(B.sa3, MAX_PT3 + 1);
+  c.take(B.sat, MAX_T5 + 1);
+  c.take(B.sap, MAX_PLS + 1);
+  c.take(B.tc_ev_off, 2);
+  c.take(B.scan_part, 4 * 1024);  // partials of up to four scans per launch
+  c.take(B.scan_part2, 1024);
+  c.take(B.mask_off, MAX_MD);
   B.cap_mask = MASK_WORDS;
-  B.mask = c.take<uint32_t>(MASK_WORDS);
+  c.take(B.mask, MASK_WORDS);
   return c.off;
 }
+
+constexpr size_t layout_bytes() {
+  Sizer z;
+  BufView B{};
+  return carve_layout(z, B);
+}
+static_assert(layout_bytes() <= SCRATCH_BYTES, "the static scratch layout is larger than the scratch array");
 
 __global__ void k_static_header(Hdr* H, Hdr v) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *H = v;
@@ -171,7 +189,38 @@ const char* list_name(int t) {
   return (t >= 0 && t < N_TOTALS) ? n[t] : "?";
 }
 
+// Device address of the scratch on `device`, looked up once (with that device current).
+cudaError_t scratch_address(int device, void** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_dev[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_dev[device] = p;
+  }
+  *out = g_scratch_dev[device];
+  return cudaSuccess;
+}
+
 }  // namespace
+
+namespace lst {
+// Context set-up for the allocation-free entry point, run by lst_load_geometry with the
+// context's device current: the scratch's device address (resolving it loads this file's
+// module, and with it the array, on that device) and every kernel the chain launches, so
+// that lst_run_event_static itself allocates nothing, not even on its first call.
+cudaError_t static_scratch_prepare(int device) {
+  if (device < 0 || device >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  void* p = nullptr;
+  cudaError_t e = scratch_address(device, &p);
+  if (e == cudaSuccess) {
+    cudaFuncAttributes a;
+    e = cudaFuncGetAttributes(&a, (const void*)k_static_header);
+  }
+  if (e == cudaSuccess) e = preload_kernels();
+  return e;
+}
+}  // namespace lst
 
 extern "C" lst_status lst_run_event_static(lst_ctx* ctx, const lst_batch_dev* ev, lst_tc* tc_out, uint32_t tc_cap,
                                            uint32_t* n_tc, void* stream) {
@@ -206,27 +255,15 @@ extern "C" lst_status lst_run_event_static(lst_ctx* ctx, const lst_batch_dev* ev
     return LST_ERR_CUDA;
   }
   void* base = nullptr;
-  {
-    // once per device, with that device current: the device address of the scratch
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_dev[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_scratch);
-      if (e != cudaSuccess) {
-        ctx_set_error(ctx, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        return LST_ERR_CUDA;
-      }
-      BufView probe;
-      if (carve((char*)p, probe) > SCRATCH_BYTES) {
-        ctx_set_error(ctx, "static scratch layout larger than the scratch array");
-        return LST_ERR_BUDGET;
-      }
-      g_scratch_dev[dev] = p;
-    }
-    base = g_scratch_dev[dev];
+  // prepared by lst_load_geometry; looked up here only if that set-up could not run
+  e = scratch_address(dev, &base);
+  if (e != cudaSuccess) {
+    ctx_set_error(ctx, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    return LST_ERR_CUDA;
   }
-  BufView B;
-  carve((char*)base, B);
+  BufView B{};
+  Placer place{(char*)base};
+  carve_layout(place, B);
   B.cap_tc = tc_cap;
   B.tc = tc_out;
   cudaStream_t s = (cudaStream_t)stream;
@@ -236,9 +273,13 @@ extern "C" lst_status lst_run_event_static(lst_ctx* ctx, const lst_batch_dev* ev
   h.n_ev = 1; h.n_hits = ev->n_hits; h.n_pls = ev->n_pls;
   // the header (and with it every total and the error word) starts from zero on each call
   k_static_header<<<1, 32, 0, s>>>(B.hdr, h);
-  enqueue_pipeline(C, G, B, L, s, nullptr, nullptr);
+  const int launched = enqueue_pipeline(C, G, B, L, s, nullptr, nullptr);
   Hdr out;
   e = cudaGetLastError();
+  if (e == cudaSuccess && launched <= 0) {
+    ctx_set_error(ctx, "lst_run_event_static: the chain was not enqueued");
+    return LST_ERR_CUDA;
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&out, B.hdr, sizeof(Hdr), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {

@@ -363,3 +363,44 @@ def test_serving_results_equal_alone(built, full_geom):
             assert s.candidates(ids[i]).tobytes() == alone[i], (share, i)
             assert lat[i] > 0
     s.close()
+
+
+def test_serving_under_a_memory_budget(built, full_geom):
+    """A budget that leaves each slot room for only a few events: batches stay below
+    max_batch, the peak device memory stays within the budget, results are unchanged."""
+    evs = [S.make_event("serving", i, n_tracks=1500 + 300 * i, with_pls=True) for i in range(16)]
+    s = lst.Session(full_geom.modules)
+    alone = [s.candidates(s.run_event(e)).tobytes() for e in evs]
+    arrival = np.zeros(len(evs))  # all waiting at once: unbounded, every batch would be full
+    lat, ntc, ids, wall = s.serve_replay(evs, arrival, n_slots=2, max_batch=8, keep_results=True)
+    st = s.stats()
+    assert st["served_max_batch"] == 8
+    base = st["device_bytes"]
+    per_slot_full = (st["served_peak_bytes"] - base) / 2
+    budget = int(base + 2 * 0.4 * per_slot_full)
+    for share in (False, True):
+        lat, ntc, ids, wall = s.serve_replay(evs, arrival, n_slots=2, max_batch=8, keep_results=True,
+                                             memory_budget=budget, share_device=share)
+        st = s.stats()
+        assert 1 <= st["served_max_batch"] < 8, st
+        assert st["served_batches"] > 2
+        assert st["served_peak_bytes"] <= budget, (st["served_peak_bytes"], budget)
+        for i in range(len(evs)):
+            assert s.candidates(ids[i]).tobytes() == alone[i], (share, i)
+    s.close()
+
+
+def test_serving_event_beyond_the_budget(built, full_geom):
+    """An event that alone needs more than a slot's share fails with LST_ERR_BUDGET; the
+    context keeps working."""
+    evs = [S.make_event("serving", 40 + i, n_tracks=3000, with_pls=True) for i in range(3)]
+    s = lst.Session(full_geom.modules)
+    ref = s.candidates(s.run_event(evs[0])).tobytes()
+    budget = int(s.stats()["device_bytes"] + (8 << 20))
+    with pytest.raises(lst.LstError) as e:
+        s.serve_replay(evs, np.zeros(3), n_slots=2, max_batch=4, memory_budget=budget)
+    assert e.value.status == -5
+    assert s.candidates(s.run_event(evs[0])).tobytes() == ref
+    lat, ntc, ids, wall = s.serve_replay(evs, np.zeros(3), n_slots=2, max_batch=4, keep_results=True)
+    assert s.candidates(ids[0]).tobytes() == ref
+    s.close()

@@ -31,6 +31,12 @@ def _device_event(torch, ev, dev):
     return desc, (x, y, z, det, pls, hoff, poff)
 
 
+def _free_device_bytes():
+    torch = pytest.importorskip("torch")
+    free, _ = torch.cuda.mem_get_info(0)
+    return free
+
+
 def test_static_entry_point_matches_run_event():
     torch = pytest.importorskip("torch")
     lst.build()
@@ -42,11 +48,15 @@ def test_static_entry_point_matches_run_event():
               S.make_event("pu200", 22, n_tracks=180, with_pls=True)]
     cap = 4096
     out = torch.zeros(cap * lst.TC_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-    for ev in events:
+    refs = [sess.candidates(sess.run_event(ev)) for ev in events]
+    descs = [_device_event(torch, ev, dev) for ev in events]
+    torch.cuda.synchronize()
+    # from here on only the allocation-free entry point runs: device memory must not move,
+    # its first call on this device included (the context prepared it at creation)
+    free0 = _free_device_bytes()
+    for ev, ref, (desc, keep) in zip(events, refs, descs):
         assert ev.n_hits <= 8192 and ev.n_pls <= 512
-        ref = sess.candidates(sess.run_event(ev))
         assert len(ref) > 10
-        desc, keep = _device_event(torch, ev, dev)
         for call in range(2):  # two calls in a row on the same shared scratch
             n = C.c_uint32(0)
             s = L.lst_run_event_static(sess.ctx, C.byref(desc), out.data_ptr(), cap, C.byref(n), None)
@@ -54,6 +64,34 @@ def test_static_entry_point_matches_run_event():
             assert n.value == len(ref)
             got = np.frombuffer(out[: n.value * lst.TC_DTYPE.itemsize].cpu().numpy().tobytes(), lst.TC_DTYPE)
             assert got.tobytes() == ref.tobytes(), f"call {call}"
+            assert _free_device_bytes() == free0, f"device memory changed on call {call}"
+    sess.close()
+
+
+def test_static_entry_point_matches_the_oracle():
+    """The allocation-free path against the CPU oracle directly, field by field."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    L = lst.load_library()
+    dev = torch.device("cuda:0")
+    geom = S.geometry(False)
+    sess = lst.Session(geom.modules)
+    ev = S.make_event("pu200", 25, n_tracks=220, with_pls=True)
+    ora = oracle.run(oracle.Geometry(geom.modules), ev)
+    desc, keep = _device_event(torch, ev, dev)
+    cap = 4096
+    out = torch.zeros(cap * lst.TC_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    n = C.c_uint32(0)
+    assert L.lst_run_event_static(sess.ctx, C.byref(desc), out.data_ptr(), cap, C.byref(n), None) == 0
+    tc = np.frombuffer(out[: n.value * lst.TC_DTYPE.itemsize].cpu().numpy().tobytes(), lst.TC_DTYPE)
+    assert len(tc) == len(ora["tc_type"]) > 10
+    assert np.array_equal(tc["type"], ora["tc_type"])
+    assert np.array_equal(tc["obj"], ora["tc_obj"])
+    assert np.array_equal(tc["pls"], ora["tc_pls"])
+    assert np.array_equal(tc["ot"], ora["tc_ot"])
+    assert np.array_equal(tc["pix"], ora["tc_pix"])
+    assert tc["pt"].tobytes() == ora["tc_pt"].tobytes()
+    assert tc["score"].tobytes() == ora["tc_score"].tobytes()
     sess.close()
 
 
