@@ -13,8 +13,8 @@ T5, pLS lookup, pT3, pT5, duplicate removal, track candidates.  A step is one ba
   e2e        events/s through lst_submit_batch / lst_collect_batch with host buffers (copies inside the timed region)
   per_event  events/s and p50/p99 latency of the plain per-event launch (lst_run_event)
   served     p50/p99 latency and events/s of the continuous-batching loop (lst_serve_replay)
-  serving_sweep  the serving workload (U{2000..8000} tracks) at 1-20 kHz offered, 8 and 64 GB
-             budgets, slots' batches one after another or sharing the device
+  serving_sweep  the serving workload (U{2000..8000} tracks) at 1-20 kHz offered, 1, 8 and
+             64 GB budgets, slots' batches one after another or sharing the device
   workloads  the tiny event (us/event), the 64-event barrel batch and the 16-event
              high-occupancy batch with seeds (events/s, objects/s), each with a parity check
   roofline   the kernel with the largest device time, algorithmic work / CUDA-event time;
@@ -429,7 +429,7 @@ def workload_legs(local, dev, flush, stream, pending):
     return out
 
 
-def serving_sweep(local, rates=(1e3, 5e3, 10e3, 20e3), budgets_gb=(8, 64), n_events=2200, warm=200):
+def serving_sweep(local, rates=(1e3, 5e3, 10e3, 20e3), budgets_gb=(1, 8, 64), n_events=2200, warm=200):
     """Serving workload (U{2000..8000} tracks, 20 % noise): Poisson arrivals at each offered
     rate, under each device-memory budget, with the slots' batches queued one after another
     on the device or sharing it.  Events cycle over a pool of 64 generated events."""
@@ -654,10 +654,12 @@ def main():
         rng = np.random.default_rng(7)
         arrival = np.cumsum(rng.exponential(1.0 / rate, args.served))
         evs = [events[i % len(events)] for i in range(args.served)]
-        lat, ntc, _, wall = sess_h.serve_replay(evs, arrival, n_slots=4, max_batch=B)
+        # the slots' batches share the device (measured faster than queueing them one after
+        # another at every offered rate of the serving sweep)
+        lat, ntc, _, wall = sess_h.serve_replay(evs, arrival, n_slots=4, max_batch=B, share_device=True)
         served = {"offered_hz": rate, "events_per_s": args.served / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                   "p99_ms": float(np.percentile(lat, 99) * 1e3), "events": args.served, "slots": 4,
-                  "max_batch": B}
+                  "max_batch": B, "share_device": 1}
     sess_h.close()
 
     # ---- roofline of the dominant kernel (profile mode: CUDA events around every kernel)

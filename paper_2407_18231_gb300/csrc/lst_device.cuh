@@ -38,7 +38,8 @@ struct Hdr {
   uint32_t tot[N_TOTALS];
   uint32_t err;
   uint32_t pad2[3];
-  uint32_t mask_used[8];  // scratch-arena words requested ([1]: LS partner lists; others unused)
+  uint32_t mask_used[8];  // LS partner-list arena: [1] words handed out in pieces (may pass the
+                          // arena's end), [2] words of the lists that found it exhausted
   unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)
   uint32_t work[16];           // work counters of the dynamically scheduled kernels (W_*)
 };

@@ -488,6 +488,7 @@ struct Pipeline {
   DevBuf alive5, alive3, alivet, plstc, cross3, crosst, sa5, sa3, sat, sap;
   DevBuf tc_ev_off, tc, scan_part, scan_part2, mask, mask_off;
   uint32_t cap_mask = 0;
+  uint64_t byte_cap = 0;  // 0: none; otherwise learn_mask keeps dev_bytes within it
   // host staging (pinned)
   Hdr* h_hdr = nullptr;        // header to upload
   Hdr* h_hdr_out = nullptr;    // header read back
@@ -751,13 +752,22 @@ struct Pipeline {
     return t;
   }
 
+  // Grows the LS partner-list arena to what the last run used (words handed out up to the
+  // arena's end plus the exact needs of the lists that found it exhausted), with 25 %
+  // headroom; under a byte cap (a serving slot's budget share) it grows only as far as the
+  // cap allows -- a smaller arena only means more anchors joined again by the fill pass.
   void learn_mask(const Hdr& h) {
-    uint32_t mx = 0;
-    for (int k = 0; k < 6; k++) mx = std::max(mx, h.mask_used[k]);
-    if (mx > cap_mask) {
-      const uint32_t want = (uint32_t)std::min<uint64_t>(4000000000ull, (uint64_t)mx * 5 / 4 + 65536);
-      need<uint32_t>(mask, want);
-      cap_mask = want;
+    const uint64_t used = std::min<uint64_t>(h.mask_used[1], cap_mask) + h.mask_used[2];
+    if (used <= cap_mask) return;
+    uint64_t want = std::min<uint64_t>(4000000000ull, used * 5 / 4 + 65536);
+    if (byte_cap) {
+      const uint64_t others = dev_bytes - mask.bytes;
+      const uint64_t room = byte_cap > others ? (byte_cap - others) / sizeof(uint32_t) : 0;
+      want = std::min(want, room);
+    }
+    if (want > cap_mask) {
+      need<uint32_t>(mask, (size_t)want);
+      cap_mask = (uint32_t)want;
     }
   }
 
@@ -856,6 +866,10 @@ struct Pipeline {
   // after (may be null): an event the chain must wait for (another slot's batch) -- the
   // inputs already uploaded on this stream are not held back by it
   void launch(bool use_graph, cudaStream_t on = nullptr, cudaEvent_t after = nullptr) {
+    // every kernel writes per-event and per-hit arrays: never launch before ensure_caps sized
+    // them for this batch
+    if (cap.ev < dev_inputs.n_ev || cap.hits < dev_inputs.n_hits || cap.pls < dev_inputs.n_pls || cap.ev == 0)
+      throw StatusError{LST_ERR_INVALID_ARG, "internal: pipeline launched before its buffers were sized"};
     *h_hdr = dev_inputs;
     const GeoView G = geo->view();
     const BufView B = view();
@@ -1615,16 +1629,18 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
       while (b > 0 && !fits(*slots[0].P, b, hits_for(b), pls_for(b))) b = b > 8 ? b * 3 / 4 : b - 1;
       for (size_t k = 0; k < slots.size(); k++) {
         Pipeline& P = *slots[k].P;
-        if (b > 0) {
-          P.ensure_caps(P.estimate(b, (uint32_t)hits_for(b), (uint32_t)pls_for(b)));
-          P.ensure_inputs(b, (uint32_t)hits_for(b), (uint32_t)pls_for(b));
-        }
+        // a slot with no room for even one typical event stays unsized (no buffers) until a
+        // batch is admitted into it, and is not warmed up: its graph is captured then
+        if (b == 0) continue;
+        P.ensure_caps(P.estimate(b, (uint32_t)hits_for(b), (uint32_t)pls_for(b)));
+        P.ensure_inputs(b, (uint32_t)hits_for(b), (uint32_t)pls_for(b));
         lst_event empty{};
         pack_host_events(P, &empty, 1);
         P.launch(true);
         if (!P.wait(0)) return fail(c, LST_ERR_TIMEOUT, "slot warm-up timed out");
       }
     }
+    for (auto& sl : slots) sl.P->byte_cap = budget ? slot_share : 0;
     auto note_bytes = [&] {
       uint64_t t = base;
       for (auto& sl : slots) t += sl.P->dev_bytes;
@@ -1683,8 +1699,15 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
               const lst_event& e = evs[queue.front()];
               if (!fits(P, (uint32_t)take.size() + 1, nh + e.n_hits, np + e.n_pls)) {
                 if (take.empty()) {
+                  const uint64_t need = P.bytes_after(P.estimate(1, e.n_hits, e.n_pls), 1, e.n_hits, e.n_pls);
                   lk.unlock();
-                  return set_error(LST_ERR_BUDGET, "one event alone needs more than a slot's share of the memory budget");
+                  char msg[256];
+                  snprintf(msg, sizeof msg,
+                           "one event alone (%u hits, %u seeds) needs %llu bytes in its slot, more than the slot's "
+                           "share of the memory budget (%llu bytes; the slot holds %llu)",
+                           e.n_hits, e.n_pls, (unsigned long long)need, (unsigned long long)slot_share,
+                           (unsigned long long)P.dev_bytes);
+                  return set_error(LST_ERR_BUDGET, msg);
                 }
                 break;
               }

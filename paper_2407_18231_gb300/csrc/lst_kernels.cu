@@ -58,6 +58,7 @@ __device__ __forceinline__ uint32_t owner_lane(uint32_t incl, uint32_t cand) {
 // Per-warp bump allocator over a scratch arena (one global atomic per 1024+ words).
 struct WarpAlloc {
   uint32_t cur = 0, end = 0;  // warp-uniform
+  bool full = false;          // a request found the arena exhausted: count needs, stop grabbing
 };
 
 // Walks all (outer i, inner j) candidates of one unit 32 at a time; outer(i, begin, count)
@@ -811,13 +812,21 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
           uint32_t mb = NONE;
           if (lane == 0) {
             if (wa.end - wa.cur < need) {
-              const uint32_t grab = need > 1024u ? need : 1024u;
-              const uint32_t b0 = atomicAdd(&B.hdr->mask_used[1], grab);
-              if (b0 < B.cap_mask && grab <= B.cap_mask - b0) {
-                wa.cur = b0;
-                wa.end = b0 + grab;
+              if (wa.full) {
+                // the arena is exhausted: record only what this list needs ([2]), so the
+                // host sizes the next arena from real demand, not from repeated requests
+                atomicAdd(&B.hdr->mask_used[2], need);
               } else {
-                wa.cur = wa.end = 0;
+                const uint32_t grab = need > 1024u ? need : 1024u;
+                const uint32_t b0 = atomicAdd(&B.hdr->mask_used[1], grab);
+                if (b0 < B.cap_mask && grab <= B.cap_mask - b0) {
+                  wa.cur = b0;
+                  wa.end = b0 + grab;
+                } else {
+                  wa.cur = wa.end = 0;
+                  wa.full = true;
+                  atomicAdd(&B.hdr->mask_used[2], need);
+                }
               }
             }
             if (wa.end - wa.cur >= need) {
@@ -828,6 +837,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
           mbase = __shfl_sync(FULL, mb, 0);
           wa.cur = __shfl_sync(FULL, wa.cur, 0);
           wa.end = __shfl_sync(FULL, wa.end, 0);
+          wa.full = __shfl_sync(FULL, (uint32_t)wa.full, 0) != 0;
           if (mbase != NONE) {
             if (lane == 0) B.mask[mbase] = count;
             uint32_t pos = mbase + 1 + wincl - wcnt;
