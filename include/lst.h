@@ -47,6 +47,12 @@ typedef int32_t lst_status;
  *   barrel: surf = lower-sensor radius, gap = radial sensor spacing, [emin, emax) = z extent
  *   endcap: surf = lower-sensor signed z, gap = |z| spacing, [emin, emax) = r extent
  *   (e0x, e0y) / (e1x, e1y): unit vectors of the lower / upper phi edge of the module.
+ *   tilt: barrel only, the tilt of the module in the r-z plane in radians (|tilt| < 1.5;
+ *   0 = flat, the sensors are the cylinders r = surf and surf + gap).  A tilted module's
+ *   lower sensor is the surface (r - surf) cos(tilt) + (z - zc) sin(tilt) = 0 through the
+ *   centre zc of its z bin [emin, emax), its upper sensor is one gap along that normal,
+ *   and its hits carry both a z and a radial tolerance (the PS coarse coordinate runs
+ *   along the tilted surface; Fig. 1's tilted inner-barrel modules).  Endcap: tilt = 0.
  * Rows (ieta = barrel z bin or endcap ring) must be uniform in length within a surface;
  * iphi < nphi numbers the sectors of a row. */
 typedef struct lst_module_desc {
@@ -60,7 +66,7 @@ typedef struct lst_module_desc {
   uint16_t pad;
   float surf, gap, emin, emax;
   float e0x, e0y, e1x, e1y;
-  uint32_t reserved;
+  float tilt;      /* barrel tilt in the r-z plane (rad), 0 = flat; endcap 0 */
 } lst_module_desc;
 
 /* Inner-tracker seed, the pLS of Sec. 1 (80 bytes): helix parameters at a reference point

@@ -15,7 +15,9 @@ Physics model (units cm, GeV, T):
     assigned to the module containing the crossing.  Resolution: 30 um along r-phi
     (a rotation about the beam line), barrel PS z smeared 0.5 mm, barrel 2S z replaced by
     the centre of its 2.5 cm strip, endcap r smeared 0.5 mm.  ``exact=True`` turns all
-    of that off (points on the helix up to float32 rounding).
+    of that off (points on the helix up to float32 rounding).  In the realistic geometry a
+    tilted PS module measures its coarse coordinate along its own surface (0.5 mm, which
+    moves both r and z), and a 2S endcap module gives r as the centre of a 5 cm strip.
   * Noise hits: a fraction of the track-hit count, each on a uniformly chosen module and
     sensor, uniform on the sensor area, with the same resolution model.
   * Pixel seeds (pLS): for every track with pT >= 0.8 GeV, four hits on pixel cylinders at
@@ -124,6 +126,38 @@ def plane_alpha(t, zp):
     return np.where(ok, alpha, np.nan)
 
 
+STRIP_2S_EC = 5.0  # radial strip length of a 2S endcap module (realistic geometry)
+
+
+def cone_alpha(t, r0, zc, tilt, offset):
+    """Turning angle in (0, pi] at which each track crosses, moving outward, the surface
+    (r - r0) cos(tilt) + (z - zc) sin(tilt) = offset (a tilted module's sensor plane in
+    r-z, a cone about the beam line); nan where it does not.  Bisection on the helix."""
+    ct, st = np.cos(tilt), np.sin(tilt)
+
+    def f(a):
+        x, y, z, _ = helix_point(t, a)
+        return (np.hypot(x, y) - r0) * ct + (z - zc) * st - offset
+
+    R = t["pt"] / G.PT_PER_CM
+    lo = np.full(len(t), 1e-9)
+    hi = cylinder_alpha(t, r0 + 12.0)
+    hi = np.where(np.isnan(hi), np.pi, hi)
+    flo, fhi = f(lo), f(hi)
+    ok = (flo < 0) & (fhi > 0)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        fm = f(mid)
+        up = fm > 0
+        hi = np.where(up, mid, hi)
+        lo = np.where(up, lo, mid)
+    a = 0.5 * (lo + hi)
+    x0, y0, _, _ = helix_point(t, a)
+    x1, y1, _, _ = helix_point(t, np.minimum(a + 1e-6, np.pi))
+    outward = np.hypot(x1, y1) >= np.hypot(x0, y0)
+    return np.where(ok & outward & (R > 0), a, np.nan)
+
+
 def _smear(rng, geom: G.Geometry, x, y, z, module, exact):
     """Apply the sensor resolution model to float64 points on their modules."""
     if exact or x.size == 0:
@@ -135,11 +169,18 @@ def _smear(rng, geom: G.Geometry, x, y, z, module, exact):
     c, s = np.cos(d), np.sin(d)
     x, y = x * c - y * s, x * s + y * c
     ps = m["stype"] == G.STYPE_PS
-    zs = z + rng.normal(0.0, SIGMA_Z_PS, size=z.shape)
+    tilt = m["tilt"].astype(np.float64)
+    # PS: the coarse coordinate along the module surface in the r-z plane, (-sin t, cos t)
+    ds = rng.normal(0.0, SIGMA_Z_PS, size=z.shape)
+    zs = z + np.cos(tilt) * ds
+    rs = r - np.sin(tilt) * ds
     zq = (np.floor(z / STRIP_2S) + 0.5) * STRIP_2S
     z = np.where(barrel, np.where(ps, zs, zq), z)
-    rnew = r + rng.normal(0.0, SIGMA_R_EC, size=r.shape)
-    scale = np.where(barrel, 1.0, rnew / r)
+    r_ec_ps = r + rng.normal(0.0, SIGMA_R_EC, size=r.shape)
+    emin = m["emin"].astype(np.float64)
+    r_ec_2s = emin + (np.floor((r - emin) / STRIP_2S_EC) + 0.5) * STRIP_2S_EC
+    rnew = np.where(barrel, np.where(ps, rs, r), np.where(ps, r_ec_ps, r_ec_2s))
+    scale = rnew / r
     return x * scale, y * scale, z
 
 
@@ -148,19 +189,63 @@ def track_crossings(geom: G.Geometry, t):
     out = []
     n = len(t)
     idx = np.arange(n)
+    zr_cache = {}
     for li in range(len(G.BARREL_R)):
+        tilted_rows = [iz for iz in range(G.BARREL_NZ) if geom.row_tilt[(li + 1, iz)] != 0.0]
         for sensor in (0, 1):
             rho = G.BARREL_R[li] + sensor * G.BARREL_GAP[li]
             a = cylinder_alpha(t, rho)
             ok = ~np.isnan(a)
-            if not np.any(ok):
-                continue
-            tt = t[ok]
-            x, y, z, _ = helix_point(tt, a[ok])
-            mod = geom.barrel_module(np.full(len(tt), li + 1), z, np.arctan2(y, x))
-            keep = mod >= 0
-            out.append((idx[ok][keep], a[ok][keep], mod[keep], np.full(keep.sum(), sensor),
-                        x[keep], y[keep], z[keep]))
+            if np.any(ok):
+                tt = t[ok]
+                x, y, z, _ = helix_point(tt, a[ok])
+                mod = geom.barrel_module(np.full(len(tt), li + 1), z, np.arctan2(y, x))
+                keep = mod >= 0
+                if tilted_rows:  # cylinder crossings count only on flat rows
+                    keep &= geom.modules["tilt"][np.maximum(mod, 0)] == 0.0
+                out.append((idx[ok][keep], a[ok][keep], mod[keep], np.full(keep.sum(), sensor),
+                            x[keep], y[keep], z[keep]))
+            # tilted rows: the crossing of each row's section (upper sensor one gap along
+            # the module normal), kept where it lies between the rays from the origin
+            # through the row's z-bin edges at the layer radius; every (track, row) pair
+            # that can meet is solved at once
+            if tilted_rows:
+                r0 = G.BARREL_R[li]
+                gap = G.BARREL_GAP[li]
+                pairs_t, pairs_row = [], []
+                for iz in tilted_rows:
+                    tilt = geom.row_tilt[(li + 1, iz)]
+                    z_lo = -G.BARREL_ZHALF + iz * G.BARREL_ZLEN
+                    span = G.BARREL_ZLEN * abs(np.tan(tilt))
+                    zr = zr_cache.get((li, round(span, 6)))
+                    if zr is None:
+                        a1 = cylinder_alpha(t, max(r0 - span, 1.0))
+                        a2 = cylinder_alpha(t, r0 + span + gap)
+                        _, _, z1, _ = helix_point(t, np.where(np.isnan(a1), 0.0, a1))
+                        _, _, z2, _ = helix_point(t, np.where(np.isnan(a2), np.pi, a2))
+                        zr = (~np.isnan(a1), np.minimum(z1, z2), np.maximum(z1, z2))
+                        zr_cache[(li, round(span, 6))] = zr
+                    cand = np.nonzero(zr[0] & (zr[2] > z_lo - 5.0) & (zr[1] < z_lo + G.BARREL_ZLEN + 5.0))[0]
+                    pairs_t.append(cand)
+                    pairs_row.append(np.full(len(cand), iz))
+                ti = np.concatenate(pairs_t)
+                rows_i = np.concatenate(pairs_row)
+                if len(ti):
+                    tilt = np.array([geom.row_tilt[(li + 1, iz)] for iz in rows_i])
+                    z_lo = -G.BARREL_ZHALF + rows_i * G.BARREL_ZLEN
+                    zc = z_lo + 0.5 * G.BARREL_ZLEN
+                    tt = t[ti]
+                    a = cone_alpha(tt, r0, zc, tilt, sensor * gap)
+                    ok = ~np.isnan(a)
+                    x, y, z, _ = helix_point(tt[ok], a[ok])
+                    tl, zlo, zcc = tilt[ok], z_lo[ok], zc[ok]
+                    rl = np.hypot(x, y) - sensor * gap * np.cos(tl)  # the lower-sensor point
+                    zl = z - sensor * gap * np.sin(tl)
+                    inside = (zl * r0 >= zlo * rl) & (zl * r0 < (zlo + G.BARREL_ZLEN) * rl)
+                    mod = geom.barrel_module(np.full(len(x), li + 1), zcc, np.arctan2(y, x))
+                    keep = inside & (mod >= 0)
+                    out.append((idx[ti][ok][keep], a[ok][keep], mod[keep], np.full(keep.sum(), sensor),
+                                x[keep], y[keep], z[keep]))
     if not geom.barrel_only:
         for side in (-1, 1):
             for di, zd in enumerate(G.DISK_Z):
@@ -201,6 +286,18 @@ def noise_points(rng, geom: G.Geometry, n):
     surf = m["surf"].astype(np.float64) + sensor * m["gap"] * np.where(barrel, 1.0, m["side"])
     r = np.where(barrel, surf, ext)
     z = np.where(barrel, ext, surf)
+    # tilted barrel modules: uniform along the row's section between the rays from the
+    # origin through the bin edges, the upper sensor one gap along the normal
+    tilt = m["tilt"].astype(np.float64)
+    r0 = m["surf"].astype(np.float64)
+    zlo, zhi = m["emin"].astype(np.float64), m["emax"].astype(np.float64)
+    zc = 0.5 * (zlo + zhi)
+    ct, st = np.cos(tilt), np.sin(tilt)
+    u_lo = (zlo - zc) / (ct + zlo / r0 * st)
+    u_hi = (zhi - zc) / (ct + zhi / r0 * st)
+    w = u_lo + rng.random(n) * (u_hi - u_lo)
+    r = np.where(tilt != 0.0, r0 - w * st + sensor * m["gap"] * ct, r)
+    z = np.where(tilt != 0.0, zc + w * ct + sensor * m["gap"] * st, z)
     return r * np.cos(phi), r * np.sin(phi), z, mod, sensor
 
 

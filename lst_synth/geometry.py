@@ -13,11 +13,24 @@ Geometry (cm):
     further out in |z|), 9 rings of 10 cm in r in [20, 110), ceil(2*pi*r_mid/10) phi sectors.
     All endcap modules are PS-like (radial coordinate measured to 0.5 mm).
 
+Two features of the Phase-2 layout in the paper's Fig. 1 that the plain geometry leaves
+out (Sec. 1) can be switched on: ``realistic=True`` tilts the inner-barrel rows and
+``endcap_2s=True`` makes the outer endcap rings 2S modules:
+  * tilted inner-barrel modules: in layers 1-3 the rows with |z centre| >= 45 cm are
+    tilted towards the interaction point by half the angle under which the row centre is
+    seen from it (tilt = atan(|z_c| / r) / 2, sign of z_c).  A tilted module's lower sensor
+    is the cone section through (r, z_c) whose normal in the r-z plane is
+    (cos tilt, sin tilt), over the same 10 cm z bin; the upper sensor sits one gap along
+    that normal;
+  * PS and 2S endcap rings: rings at r >= 60 cm are 2S modules (strips: r known only to
+    the centre of a 5 cm strip).
+
 The paper describes this structure qualitatively (Sec. 1, Fig. 1: every outer-tracker
 layer is two closely spaced sensors; the module is the unit of locality).  The radii,
 gaps and extents are the workload recipe's numbers.
 
-The record layout below is the C struct ``lst_module_desc`` (48 bytes).
+The record layout below is the C struct ``lst_module_desc`` (48 bytes); ``tilt`` is the
+barrel tilt angle in radians (0: the sensors are the cylinders r = surf, surf + gap).
 """
 from __future__ import annotations
 
@@ -41,6 +54,8 @@ RING_R0 = 20.0
 RING_DR = 10.0
 N_RING = 9
 PHI_PITCH = 10.0
+TILT_Z = 45.0      # realistic geometry: barrel rows 1-3 with |z centre| >= this are tilted
+RING_2S_R = 60.0   # realistic geometry: endcap rings starting at or beyond this radius are 2S
 
 SUBDET_BARREL = 0
 SUBDET_ENDCAP = 1
@@ -65,7 +80,7 @@ MODULE_DTYPE = np.dtype(
         ("e0y", np.float32),
         ("e1x", np.float32),
         ("e1y", np.float32),
-        ("reserved", np.uint32),
+        ("tilt", np.float32),
     ],
     align=False,
 )
@@ -90,8 +105,10 @@ class Geometry:
     ``barrel_only`` drops the endcap disks (the tiny and barrel-batch workloads).
     """
 
-    def __init__(self, barrel_only: bool = False):
+    def __init__(self, barrel_only: bool = False, realistic: bool = False, endcap_2s: bool = False):
         self.barrel_only = barrel_only
+        self.realistic = realistic
+        self.endcap_2s = endcap_2s
         rows = []
         self.barrel_base = []  # first module id of each barrel layer
         self.barrel_nphi = []
@@ -102,11 +119,15 @@ class Geometry:
             self.barrel_nphi.append(n)
             for iz in range(BARREL_NZ):
                 z0 = -BARREL_ZHALF + iz * BARREL_ZLEN
+                zc = z0 + 0.5 * BARREL_ZLEN
+                tilt = 0.0
+                if realistic and li < 3 and abs(zc) >= TILT_Z:
+                    tilt = math.copysign(0.5 * math.atan(abs(zc) / r), zc)
                 for k in range(n):
                     rows.append(
                         (SUBDET_BARREL, li + 1, 0, STYPE_PS if BARREL_PS[li] else STYPE_2S,
                          iz, k, n, 0, r, BARREL_GAP[li], z0, z0 + BARREL_ZLEN,
-                         e[k, 0], e[k, 1], e[k + 1, 0], e[k + 1, 1], 0)
+                         e[k, 0], e[k, 1], e[k + 1, 0], e[k + 1, 1], tilt)
                     )
         # endcap_base[(side, disk)][ring] -> first module id of that ring
         self.endcap_base = {}
@@ -121,15 +142,22 @@ class Geometry:
                         e = ring_edges[j]
                         bases.append(len(rows))
                         r0 = RING_R0 + RING_DR * j
+                        st = STYPE_2S if endcap_2s and r0 >= RING_2S_R else STYPE_PS
                         for k in range(n):
                             rows.append(
-                                (SUBDET_ENDCAP, di + 1, side, STYPE_PS, j, k, n, 0,
+                                (SUBDET_ENDCAP, di + 1, side, st, j, k, n, 0,
                                  side * zd, DISK_GAP, r0, r0 + RING_DR,
-                                 e[k, 0], e[k, 1], e[k + 1, 0], e[k + 1, 1], 0)
+                                 e[k, 0], e[k, 1], e[k + 1, 0], e[k + 1, 1], 0.0)
                             )
                     self.endcap_base[(side, di + 1)] = bases
         self.modules = np.array(rows, dtype=MODULE_DTYPE)
         self.n_modules = len(self.modules)
+        # (layer, z bin) -> tilt of that barrel row
+        self.row_tilt = {}
+        for li in range(len(BARREL_R)):
+            base = self.barrel_base[li]
+            for iz in range(BARREL_NZ):
+                self.row_tilt[(li + 1, iz)] = float(self.modules["tilt"][base + iz * self.barrel_nphi[li]])
 
     # ---- point -> module (used to decide which sensor a simulated particle fired) ----
     def barrel_module(self, layer: np.ndarray, z: np.ndarray, phi: np.ndarray):

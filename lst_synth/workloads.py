@@ -23,10 +23,13 @@ WORKLOAD_ID = {"tiny": 1, "pu200": 2, "batched": 3, "serving": 4, "highocc": 5}
 _GEOMS: dict = {}
 
 
-def geometry(barrel_only: bool) -> G.Geometry:
-    if barrel_only not in _GEOMS:
-        _GEOMS[barrel_only] = G.Geometry(barrel_only=barrel_only)
-    return _GEOMS[barrel_only]
+def geometry(barrel_only: bool, realistic: bool = False, endcap_2s: bool = False) -> G.Geometry:
+    """The detector of a workload; ``realistic`` tilts the inner-barrel rows and
+    ``endcap_2s`` makes the outer endcap rings 2S (features of the paper's Fig. 1)."""
+    key = (barrel_only, realistic, endcap_2s)
+    if key not in _GEOMS:
+        _GEOMS[key] = G.Geometry(barrel_only=barrel_only, realistic=realistic, endcap_2s=endcap_2s)
+    return _GEOMS[key]
 
 
 def seed_of(workload: str, i: int) -> int:
@@ -35,17 +38,19 @@ def seed_of(workload: str, i: int) -> int:
     return SEED_STRIDE * WORKLOAD_ID[workload] + i
 
 
-def make_event(workload: str, i: int = 0, *, n_tracks=None, with_pls=None, exact=False) -> E.Event:
-    """Event ``i`` of ``workload`` (``n_tracks``/``with_pls`` override the recipe)."""
+def make_event(workload: str, i: int = 0, *, n_tracks=None, with_pls=None, exact=False,
+               realistic=False) -> E.Event:
+    """Event ``i`` of ``workload`` (``n_tracks``/``with_pls`` override the recipe;
+    ``realistic`` simulates it in the geometry with tilted inner-barrel modules)."""
     seed = seed_of(workload, i)
     rng = np.random.default_rng(seed + 7)
     if workload in ("tiny", "batched"):
-        geom = geometry(True)
+        geom = geometry(True, realistic)
         n = n_tracks if n_tracks is not None else (10 if workload == "tiny" else int(rng.integers(500, 6001)))
         t = E.random_tracks(rng, n, pt_mode="uniform", pt_lo=1.0, pt_hi=10.0, eta_max=1.0)
         return E.event_from_tracks(geom, t, seed, noise_frac=0.0, exact=exact,
                                    with_pls=bool(with_pls))
-    geom = geometry(False)
+    geom = geometry(False, realistic)
     if workload == "pu200":
         n, noise, pls = 4000, 0.20, False
     elif workload == "serving":
@@ -63,5 +68,5 @@ def make_event(workload: str, i: int = 0, *, n_tracks=None, with_pls=None, exact
                                with_pls=pls)
 
 
-def workload_geometry(workload: str) -> G.Geometry:
-    return geometry(workload in ("tiny", "batched"))
+def workload_geometry(workload: str, realistic: bool = False) -> G.Geometry:
+    return geometry(workload in ("tiny", "batched"), realistic)

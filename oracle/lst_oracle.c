@@ -120,27 +120,48 @@ static int next_surfaces(int s, int out[3]) {
 
 /* Per-module constants (reading of the pT >= 0.8 GeV window, Sec. 1):
  *   T     = tan(asin(r_max / (2 Rmin))): largest angle between a prompt pT >= 0.8 GeV
- *           track's chord ending at radius r_max and the radial direction at its start;
+ *           track's chord ending at radius r_max and the radial direction at its start
+ *           (r_max: the module's largest radius, the upper sensor of a tilted module
+ *           included);
  *   zeta  = z tolerance of one hit (PS 3 x 0.5 mm, 2S half a 2.5 cm strip + 0.5 mm);
- *   rho   = radial tolerance of one hit (endcap 3 x 0.5 mm);
- *   delta = transverse point tolerance (3 x 30 um rounded up, plus rho). */
+ *   rho   = radial tolerance of one hit (endcap PS 3 x 0.5 mm, endcap 2S half a 5 cm
+ *           strip + 0.5 mm);
+ *   delta = transverse point tolerance (3 x 30 um rounded up, plus rho).
+ * A tilted barrel PS module (Fig. 1) measures its coarse coordinate along its surface,
+ * direction (-sin t, cos t) in r-z: 3 x 0.5 mm projects to zeta = 0.15 |cos t| and
+ * rho = 0.15 |sin t|; its lower sensor spans r in surf +- (half its z length) |tan t|. */
 static void module_consts(const ora_module *m, float *T, float *zeta, float *rho, float *delta) {
-  double rmax = (m->subdet == 0) ? (double)m->surf + (double)m->gap : (double)m->emax;
+  double rmax;
+  if (m->subdet == 0) {
+    double t = (double)m->tilt;
+    rmax = (double)m->surf + 0.5 * ((double)m->emax - (double)m->emin) * fabs(tan(t)) + (double)m->gap * cos(t);
+  } else {
+    rmax = (double)m->emax;
+  }
   double s = rmax / (2.0 * RMIN_D);
   *T = (float)(s < 1.0 ? s / sqrt(1.0 - s * s) : 1.0e30);
   if (m->subdet == 0) {
-    *zeta = m->stype == 0 ? 0.15f : 1.30f;
-    *rho = 0.0f;
+    if (m->tilt != 0.0f) {
+      *zeta = (float)(0.15 * fabs(cos((double)m->tilt)));
+      *rho = (float)(0.15 * fabs(sin((double)m->tilt)));
+    } else {
+      *zeta = m->stype == 0 ? 0.15f : 1.30f;
+      *rho = 0.0f;
+    }
   } else {
     *zeta = 0.0f;
-    *rho = 0.15f;
+    *rho = m->stype == 0 ? 0.15f : 2.55f;
   }
   *delta = 0.01f + *rho;
 }
 
 /* Anchor coordinate box of a module (lower sensor, with margins for resolution). */
 static void anchor_box(const ora_module *m, double *r0, double *r1, double *z0, double *z1) {
-  if (m->subdet == 0) {
+  if (m->subdet == 0 && m->tilt != 0.0f) {
+    double h = 0.5 * ((double)m->emax - (double)m->emin) * fabs(tan((double)m->tilt));
+    *r0 = m->surf - h - 0.5; *r1 = m->surf + h + 0.5;
+    *z0 = m->emin - 0.5; *z1 = m->emax + 0.5;
+  } else if (m->subdet == 0) {
     *r0 = m->surf - 0.01; *r1 = m->surf + 0.01;
     *z0 = m->emin - 0.5; *z1 = m->emax + 0.5;
   } else {
@@ -232,6 +253,7 @@ ora_geom *ora_geom_create(const ora_module *mods, uint32_t n) {
     int s = module_surface(m);
     if (s < 0 || m->nphi == 0 || m->iphi >= m->nphi) goto fail;
     if (!isfinite(m->surf) || !isfinite(m->gap) || !isfinite(m->emin) || !isfinite(m->emax)) goto fail;
+    if (!(fabsf(m->tilt) < 1.5f) || (m->subdet != 0 && m->tilt != 0.0f)) goto fail;
     g->surface[i] = s;
     module_consts(m, &g->T[i], &g->zeta[i], &g->rho[i], &g->delta[i]);
     if (m->ieta + 1u > g->n_rows[s]) g->n_rows[s] = m->ieta + 1u;

@@ -37,7 +37,7 @@ typedef struct {
   float emin, emax;/* barrel: z extent; endcap: r extent */
   float e0x, e0y;  /* lower phi edge (unit vector) */
   float e1x, e1y;  /* upper phi edge (unit vector) */
-  uint32_t reserved;
+  float tilt;      /* barrel: tilt of the module in the r-z plane (rad), 0 = flat; endcap: 0 */
 } ora_module;
 
 typedef struct {

@@ -154,21 +154,37 @@ struct Geometry {
       const lst_module_desc& d = mods[i];
       const int s = surface_of(d);
       if (s < 0 || d.nphi == 0 || d.iphi >= d.nphi || !std::isfinite(d.surf) || !std::isfinite(d.gap) ||
-          !std::isfinite(d.emin) || !std::isfinite(d.emax) || !(d.emax > d.emin))
+          !std::isfinite(d.emin) || !std::isfinite(d.emax) || !(d.emax > d.emin) || !(std::fabs(d.tilt) < 1.5f) ||
+          (d.subdet != 0 && d.tilt != 0.0f))
         throw StatusError{LST_ERR_BAD_INPUT, "module " + std::to_string(i) + " is malformed"};
       surface[i] = s;
       subdet[i] = d.subdet;
-      // bending slope at the module's largest radius, tolerances of its hits
-      const double rmax = d.subdet == 0 ? (double)d.surf + (double)d.gap : (double)d.emax;
+      // bending slope at the module's largest radius (the upper sensor of a tilted module
+      // included), tolerances of its hits: a tilted PS module's coarse coordinate runs
+      // along its surface, so 3 x 0.5 mm projects onto both z and r; an endcap 2S module
+      // gives r to half a 5 cm strip
+      double rmax;
+      if (d.subdet == 0) {
+        const double t = (double)d.tilt;
+        rmax = (double)d.surf + 0.5 * ((double)d.emax - (double)d.emin) * std::fabs(std::tan(t)) +
+               (double)d.gap * std::cos(t);
+      } else {
+        rmax = (double)d.emax;
+      }
       const double sq = rmax / (2.0 * RMIN_D);
       const float T = (float)(sq < 1.0 ? sq / std::sqrt(1.0 - sq * sq) : 1.0e30);
       float zeta, rho;
       if (d.subdet == 0) {
-        zeta = d.stype == 0 ? 0.15f : 1.30f;
-        rho = 0.0f;
+        if (d.tilt != 0.0f) {
+          zeta = (float)(0.15 * std::fabs(std::cos((double)d.tilt)));
+          rho = (float)(0.15 * std::fabs(std::sin((double)d.tilt)));
+        } else {
+          zeta = d.stype == 0 ? 0.15f : 1.30f;
+          rho = 0.0f;
+        }
       } else {
         zeta = 0.0f;
-        rho = 0.15f;
+        rho = d.stype == 0 ? 0.15f : 2.55f;
       }
       const float delta = 0.01f + rho;
       modc[i] = make_float4(zeta, rho, delta, T);
@@ -241,7 +257,11 @@ struct Geometry {
   Box box_of(uint32_t i) const {
     const lst_module_desc& d = mods[i];
     Box b;
-    if (d.subdet == 0) {
+    if (d.subdet == 0 && d.tilt != 0.0f) {  // a tilted section spans surf +- half its z length x |tan(tilt)|
+      const double h = 0.5 * ((double)d.emax - (double)d.emin) * std::fabs(std::tan((double)d.tilt));
+      b.r0 = d.surf - h - 0.5; b.r1 = d.surf + h + 0.5;
+      b.z0 = d.emin - 0.5; b.z1 = d.emax + 0.5;
+    } else if (d.subdet == 0) {
       b.r0 = d.surf - 0.01; b.r1 = d.surf + 0.01;
       b.z0 = d.emin - 0.5; b.z1 = d.emax + 0.5;
     } else {

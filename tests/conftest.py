@@ -34,3 +34,15 @@ def ora_barrel(barrel_geom):
 def ora_full(full_geom):
     import oracle
     return oracle.Geometry(full_geom.modules)
+
+
+@pytest.fixture(scope="session")
+def tilted_geom():
+    import lst_synth
+    return lst_synth.geometry(False, True)
+
+
+@pytest.fixture(scope="session")
+def ora_tilted(tilted_geom):
+    import oracle
+    return oracle.Geometry(tilted_geom.modules)

@@ -404,3 +404,30 @@ def test_serving_event_beyond_the_budget(built, full_geom):
     lat, ntc, ids, wall = s.serve_replay(evs, np.zeros(3), n_slots=2, max_batch=4, keep_results=True)
     assert s.candidates(ids[0]).tobytes() == ref
     s.close()
+
+
+# ---------------------------------------------------------------- tilted inner-barrel modules
+@pytest.fixture(scope="module")
+def sess_tilted(built, tilted_geom):
+    return lst.Session(tilted_geom.modules, keep_objects=True)
+
+
+def test_tilted_pu200_parity(sess_tilted, ora_tilted):
+    """A PU200-like event with seeds in the geometry with tilted inner-barrel modules."""
+    ev = S.make_event("pu200", 11, with_pls=True, realistic=True)
+    compare(sess_tilted, sess_tilted.run_event(ev), oracle.run(ora_tilted, ev), ev, "tilted pu200")
+
+
+def test_tilted_highocc_parity(sess_tilted, ora_tilted):
+    """The high-occupancy event (12000 tracks, 30 % noise, seeds) with tilted modules."""
+    ev = S.make_event("highocc", 1, realistic=True)
+    compare(sess_tilted, sess_tilted.run_event(ev), oracle.run(ora_tilted, ev), ev, "tilted highocc")
+
+
+def test_tilted_batch_parity(sess_tilted, ora_tilted):
+    """Tilted-geometry events of uneven size in one batch, each equal to the oracle."""
+    evs = [S.make_event("pu200", 12 + i, n_tracks=n, with_pls=True, realistic=True)
+           for i, n in enumerate((300, 2500, 900))]
+    ids = sess_tilted.run_batch(evs)
+    for i, (rid, ev) in enumerate(zip(ids, evs)):
+        compare(sess_tilted, rid, oracle.run(ora_tilted, ev), ev, f"tilted batch {i}")

@@ -80,9 +80,12 @@ def _brute(geom, og, ev):
         np.array([kfull[k] for k in idx], np.float32)
 
 
-@pytest.mark.parametrize("case", ["tiny", "barrel_res", "pu200_small"])
-def test_ls_t3_t5_equal_brute_force(case, barrel_geom, full_geom, ora_barrel, ora_full):
-    if case == "tiny":
+@pytest.mark.parametrize("case", ["tiny", "barrel_res", "pu200_small", "tilted_small"])
+def test_ls_t3_t5_equal_brute_force(case, barrel_geom, full_geom, ora_barrel, ora_full, tilted_geom, ora_tilted):
+    if case == "tilted_small":
+        geom, og = tilted_geom, ora_tilted
+        ev = S.make_event("pu200", 8, n_tracks=60, realistic=True)
+    elif case == "tiny":
         geom, og, ev = barrel_geom, ora_barrel, S.make_event("tiny")
     elif case == "barrel_res":
         geom, og = barrel_geom, ora_barrel

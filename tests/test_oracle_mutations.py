@@ -3,7 +3,8 @@
 Each mutation below is one plausible slip in the oracle's source (a dropped term, a
 flipped sign, a transposed operand, a wrong index or bound).  The test builds a copy of
 lst_oracle.c with that one change (on the CPU, in a temporary directory), runs the oracle
-pins (test_oracle_pins.py, test_oracle_cuts.py, test_oracle_enumeration.py) against the
+pins (test_oracle_pins.py, test_oracle_cuts.py, test_oracle_enumeration.py,
+test_oracle_tilted.py) against the
 copy in a child process, and requires at least one of them to fail.  A mutation that no
 pin catches would be a part of the oracle that nothing but the oracle itself vouches for.
 """
@@ -17,7 +18,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lst_oracle.c")
-PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_cuts.py", "tests/test_oracle_enumeration.py"]
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_cuts.py", "tests/test_oracle_enumeration.py",
+        "tests/test_oracle_tilted.py"]
 
 # Two widening terms are left out on purpose: the endcap part of the bending slack
 # (rho_a + rho_b) (|sin dphi| + 0.05) and the sensor gap in a barrel module's r_max.  No
@@ -27,7 +29,9 @@ PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_cuts.py", "tests/test_or
 # oracle-GPU identity fixes them.  Two more slips have no effect on any event tried
 # (full PU200-like and high-occupancy events): dropping the neighbour module's half width
 # from the connection map's phi window (the window's bending term is far wider than any
-# accepted pair needs) and letting removed pT5s remove pT3s (no pT3 overlapping a removed
+# accepted pair needs), dropping a tilted module's radial span from its connection-map box
+# (the map's r-z corner bound stays permissive for every pair tried) and letting removed
+# pT5s remove pT3s (no pT3 overlapping a removed
 # pT5 in two MDs survives the other rules), so they are not listed either.
 #
 # (name, exact source text, replacement)
@@ -113,6 +117,12 @@ MUTATIONS = [
     ("module constants: 2S z tolerance of a PS module", "*zeta = m->stype == 0 ? 0.15f : 1.30f;", "*zeta = 0.15f;"),
     ("hit radius includes z", "o->z = ev->z[h];\n  o->r = sqrtf(o->x * o->x + o->y * o->y);",
      "o->z = ev->z[h];\n  o->r = sqrtf(o->x * o->x + o->y * o->y + o->z * o->z);"),
+    # tilted barrel modules
+    ("tilted: bending slope without the section's radial span",
+     "rmax = (double)m->surf + 0.5 * ((double)m->emax - (double)m->emin) * fabs(tan(t)) + (double)m->gap * cos(t);",
+     "rmax = (double)m->surf + (double)m->gap * cos(t);"),
+    ("tilted: radial tolerance dropped", "*rho = (float)(0.15 * fabs(sin((double)m->tilt)));", "*rho = 0.0f;"),
+    ("tilted: z tolerance of a 2S strip", "*zeta = (float)(0.15 * fabs(cos((double)m->tilt)));", "*zeta = 1.30f;"),
     # duplicate removal and candidates
     ("dedup: pT5 overlap threshold 2", "if (count_shared(pls_md5 + 5 * x, 5, pls_md5 + 5 * y, 5) >= 3 && better",
      "if (count_shared(pls_md5 + 5 * x, 5, pls_md5 + 5 * y, 5) >= 2 && better"),
