@@ -15,8 +15,9 @@ T5, pLS lookup, pT3, pT5, duplicate removal, track candidates.  A step is one ba
   served     p50/p99 latency and events/s of the continuous-batching loop (lst_serve_replay)
   serving_sweep  the serving workload (U{2000..8000} tracks) at 1-20 kHz offered, 1, 8 and
              64 GB budgets, slots' batches one after another or sharing the device
-  workloads  the tiny event (us/event), the 64-event barrel batch and the 16-event
-             high-occupancy batch with seeds (events/s, objects/s), each with a parity check
+  workloads  the tiny event (us/event), the 64-event barrel batch, the 16-event
+             high-occupancy batch with seeds and the headline batch in the geometry with
+             tilted inner-barrel modules (events/s, objects/s), each with a parity check
   roofline   the kernel with the largest device time, algorithmic work / CUDA-event time;
              the MD and LS stages' HBM fraction beside it
   cpu_baseline  the CPU oracle on the host cores (1 thread, 2 threads pinned to 2 cores,
@@ -374,9 +375,10 @@ def sampled_candidates(sess, dev_batch, n_ev, events, picks, stream, label, modu
 
 
 def workload_legs(local, dev, flush, stream, pending):
-    """The other workloads: the tiny event per launch, the 64-event barrel batch (tuned) and
-    the 16-event high-occupancy batch with seeds; a sampled event of each is queued for the
-    CPU leg's oracle check."""
+    """The other workloads: the tiny event per launch, the 64-event barrel batch (tuned),
+    the 16-event high-occupancy batch with seeds and the PU200-like batch in the geometry
+    with tilted inner-barrel modules; a sampled event of each is queued for the CPU leg's
+    oracle check."""
     import lst_synth as S
     import paper_2407_18231_gb300 as lst
     from paper_2407_18231_gb300 import autotune
@@ -425,6 +427,19 @@ def workload_legs(local, dev, flush, stream, pending):
     out["highocc_batch16"] = {"events_per_s": 16 / (ms * 1e-3), "objects_per_s": objs / (ms * 1e-3),
                               "ms_per_batch": ms, "objects_per_batch": {k: st[k] for k in OBJ_KEYS},
                               "mean_hits_per_event": float(np.mean([e.n_hits for e in evs]))}
+    sess.close()
+    # the headline workload in the geometry with tilted inner-barrel modules
+    gt = S.geometry(False, True)
+    evs = [S.make_event("pu200", i, with_pls=True, realistic=True) for i in range(32)]
+    sess = lst.Session(gt.modules, device=local)
+    db = [to_device(evs, dev)]
+    ms, st = time_device_batches(sess, db, 32, stream, flush, 10, 3)
+    objs = sum(st[k] for k in OBJ_KEYS)
+    sampled_candidates(sess, db[0][0], 32, evs, [9], stream, "pu200_tilted_batch32", gt.modules, pending)
+    out["pu200_tilted_batch32"] = {"events_per_s": 32 / (ms * 1e-3), "objects_per_s": objs / (ms * 1e-3),
+                                   "ms_per_batch": ms, "objects_per_batch": {k: st[k] for k in OBJ_KEYS},
+                                   "mean_hits_per_event": float(np.mean([e.n_hits for e in evs])),
+                                   "geometry": "tilted inner-barrel rows (|z| >= 45 cm, layers 1-3)"}
     sess.close()
     return out
 
