@@ -20,6 +20,8 @@ T5, pLS lookup, pT3, pT5, duplicate removal, track candidates.  A step is one ba
              tilted inner-barrel modules (events/s, objects/s), each with a parity check
   roofline   the kernel with the largest device time, algorithmic work / CUDA-event time;
              the MD and LS stages' HBM fraction beside it
+  seeding    LST as a seeder (Sec. 2, Table 1): unlinked seeds handed on, quads only or
+             quads and triplets, and the simulated tracks LST's tracks plus those seeds cover
   cpu_baseline  the CPU oracle on the host cores (1 thread, 2 threads pinned to 2 cores,
              all cores) on the benchmark's own events
 
@@ -646,6 +648,33 @@ def main():
                "without_pls_only": {"efficiency": r_ot["efficiency"], "fake_rate": r_ot["fake_rate"],
                                     "duplicate_rate": r_ot["duplicate_rate"]}}
 
+    # ---- LST as a seeder (Sec. 2, Table 1): PU200-like events whose seeds are 20 %
+    # triplets; LST's tracks (pT5, pT3, T5) plus the seeds it leaves unlinked, quads only or
+    # quads and triplets, as the recovery iteration would receive them (not timed)
+    seed_evs = [S.make_event("pu200", 500 + i, with_pls=True, triplet_frac=0.2) for i in range(8)]
+    seed_ids = sess_h.run_batch(seed_evs)
+    cover = {"quads": [0, 0], "quads_triplets": [0, 0]}
+    n_seeds = {"quads": 0, "quads_triplets": 0}
+    for rid, e in zip(seed_ids, seed_evs):
+        tc = sess_h.candidates(rid)
+        sel = (e.tracks["pt"] >= 0.9) & (np.abs(e.tracks["eta"]) < 2.4)
+        tracks = V.match_candidates(tc[tc["type"] != lst.TC_PLS], e.sim, e.pls_sim)
+        for name, mode in (("quads", lst.SEEDS_QUADS), ("quads_triplets", lst.SEEDS_QUADS_TRIPLETS)):
+            sd = sess_h.seeds(rid, mode)
+            n_seeds[name] += len(sd)
+            rec = np.zeros(len(sd), lst.TC_DTYPE)
+            rec["ot"] = lst.NONE
+            rec["pix"] = sd["pix"]
+            found = set(tracks[tracks >= 0].tolist()) | set(V.match_candidates(rec, e.sim, e.pls_sim).tolist())
+            cover[name][0] += int(sel.sum())
+            cover[name][1] += int(sum(1 for k in np.nonzero(sel)[0] if int(k) in found))
+        sess_h.release(rid)
+    seeding = {"events": len(seed_evs), "triplet_fraction_of_seeds": 0.2,
+               "seeds_per_event": {k: v / len(seed_evs) for k, v in n_seeds.items()},
+               "tracks_covered": {k: v[1] / max(v[0], 1) for k, v in cover.items()},
+               "covered": "simulated tracks with pT >= 0.9 GeV and |eta| < 2.4 matched (75 % rule) by an LST "
+                          "pT5, pT3 or T5 or by a seed handed on"}
+
     # ---- per-event launch: latency of single events
     per_event = None
     if args.per_event:
@@ -759,7 +788,7 @@ def main():
                          f"{P} resident batches"},
         "parity": parity, "sustained": sustained,
         "e2e": e2e, "per_event": per_event, "served": served, "serving_sweep": sweep, "workloads": legs,
-        "physics": physics,
+        "physics": physics, "seeding": seeding,
         "objects_per_step": {k: stats[k] for k in OBJ_KEYS},
         "roofline": roof, "kernel_ms_per_step": kernel_times, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": kernels_per_step * args.steps,

@@ -70,13 +70,14 @@ typedef struct lst_module_desc {
 } lst_module_desc;
 
 /* Inner-tracker seed, the pLS of Sec. 1 (80 bytes): helix parameters at a reference point
- * and its four pixel hits.  Pixel hits get the ids 4 * pls_index + k in track candidates. */
+ * and its pixel hits, four (a quad) or three (a triplet, hits in the first three slots).
+ * Pixel hits get the ids 4 * pls_index + k (k < n_hits) in track candidates. */
 typedef struct lst_pls {
   float px, py, pz;  /* momentum at the reference point, GeV; px = py = 0 is rejected */
   float x0, y0, z0;  /* reference point, cm */
   float hx[4], hy[4], hz[4];
   int32_t charge;    /* +1 or -1 */
-  uint32_t reserved;
+  uint32_t n_hits;   /* 4 (quad; 0 is read as 4) or 3 (triplet); other values are rejected */
 } lst_pls;
 
 /* One event as host arrays (the library copies them during the call). */
@@ -118,12 +119,12 @@ typedef struct lst_config {
 typedef struct lst_tc {
   uint8_t type;        /* LST_TC_PT5 / PT3 / T5 / PLS */
   uint8_t n_ot;        /* outer-tracker hits used (10, 6 or 0) */
-  uint8_t n_pix;       /* pixel hits used (4 or 0) */
+  uint8_t n_pix;       /* pixel hits used (4, 3 or 0) */
   uint8_t pad;
   uint32_t obj;        /* index of the object in its own list (pT5, pT3, T5 or pLS) */
   uint32_t pls;        /* pLS index, or 0xFFFFFFFF */
   uint32_t ot[10];     /* input hit indices, 0xFFFFFFFF padded (MD lower, upper, ...) */
-  uint32_t pix[4];     /* 4 * pls + k, or 0xFFFFFFFF */
+  uint32_t pix[4];     /* 4 * pls + k for k < n_pix, 0xFFFFFFFF after */
   float pt;            /* GeV: the pLS pT, or for a T5 0.0113922 / |curvature| */
   float score;         /* selection score (lower is better) */
 } lst_tc;
@@ -222,6 +223,22 @@ lst_status lst_get_candidates_batch(lst_ctx *ctx, const lst_result_id *ids, uint
  * BUFFER_TOO_SMALL. */
 lst_status lst_get_objects(lst_ctx *ctx, lst_result_id id, int32_t kind, void *buf, uint32_t cap,
                            uint32_t *n_out);
+
+/* LST as a seeder (Sec. 2, Table 1: the recovery iteration seeded by "LST pLS quads" or
+ * by "LST pLS quads+triplets"): the seeds LST left unlinked -- not used by any surviving
+ * pT3 or pT5, the pLS track candidates -- handed on instead of being emitted as tracks.
+ * mode LST_SEEDS_QUADS keeps the four-hit seeds, LST_SEEDS_QUADS_TRIPLETS also the
+ * three-hit ones.  buf (host, cap records) receives them in seed order; buf == NULL is a
+ * size query.  Errors: NOT_FOUND, INVALID_ARG (mode), BUFFER_TOO_SMALL. */
+#define LST_SEEDS_QUADS 0
+#define LST_SEEDS_QUADS_TRIPLETS 1
+typedef struct lst_seed {
+  uint32_t pls;     /* seed index in the event's pLS list */
+  uint32_t n_pix;   /* 4 or 3 */
+  uint32_t pix[4];  /* 4 * pls + k for k < n_pix, 0xFFFFFFFF after */
+} lst_seed;
+lst_status lst_get_seeds(lst_ctx *ctx, lst_result_id id, int32_t mode, lst_seed *buf, uint32_t cap,
+                         uint32_t *n_out);
 
 /* Frees a result's host storage.  Errors: NOT_FOUND. */
 lst_status lst_release_result(lst_ctx *ctx, lst_result_id id);

@@ -47,7 +47,7 @@ PLS_DTYPE = np.dtype(
         ("px", np.float32), ("py", np.float32), ("pz", np.float32),
         ("x0", np.float32), ("y0", np.float32), ("z0", np.float32),
         ("hx", np.float32, (4,)), ("hy", np.float32, (4,)), ("hz", np.float32, (4,)),
-        ("charge", np.int32), ("reserved", np.uint32),
+        ("charge", np.int32), ("n_hits", np.uint32),
     ]
 )
 assert PLS_DTYPE.itemsize == 80
@@ -301,10 +301,13 @@ def noise_points(rng, geom: G.Geometry, n):
     return r * np.cos(phi), r * np.sin(phi), z, mod, sensor
 
 
-def make_pls(rng, t, track_ids, n_fake, exact=False):
+def make_pls(rng, t, track_ids, n_fake, exact=False, triplet_frac=0.0):
     """Pixel seeds for tracks ``t`` (already selected) plus ``n_fake`` random seeds.
 
-    ``exact`` keeps the hits on the helix and the parameters unsmeared."""
+    ``exact`` keeps the hits on the helix and the parameters unsmeared.  A fraction
+    ``triplet_frac`` of the seeds lose one of their four pixel hits (chosen at random):
+    triplets, whose three hits come first, whose fourth slot is zero, and whose reference
+    point and direction are those at their first remaining hit."""
     w = 0.0 if exact else 1.0
     n = len(t)
     alphas = np.stack([cylinder_alpha(t, r) for r in PIXEL_R], axis=1) if n else np.zeros((0, 4))
@@ -325,7 +328,8 @@ def make_pls(rng, t, track_ids, n_fake, exact=False):
             hy[:, k] = x * s + y * c
             hz[:, k] = z + w * rng.normal(0.0, SIGMA_PIX, size=n)
         q = t["q"].astype(np.float64)
-        phi1 = t["phi0"] - q * alphas[:, 0] + w * rng.normal(0.0, 0.001, size=n)
+        dphi = w * rng.normal(0.0, 0.001, size=n)
+        phi1 = t["phi0"] - q * alphas[:, 0] + dphi
         pt = t["pt"] * (1.0 + w * rng.normal(0.0, 0.01, size=n))
         pls["px"][:n] = pt * np.cos(phi1)
         pls["py"][:n] = pt * np.sin(phi1)
@@ -348,11 +352,25 @@ def make_pls(rng, t, track_ids, n_fake, exact=False):
             pls["hz"][f, k] = rng.uniform(-30, 30, n_fake)
         pls["x0"][f] = pls["hx"][f, 0]; pls["y0"][f] = pls["hy"][f, 0]; pls["z0"][f] = pls["hz"][f, 0]
         pls["charge"][f] = rng.choice(np.array([-1, 1], np.int32), n_fake)
+    pls["n_hits"] = 4
+    if triplet_frac > 0.0 and len(pls):
+        drop = rng.integers(0, 4, len(pls))
+        trip = np.nonzero(rng.random(len(pls)) < triplet_frac)[0]
+        for i in trip:
+            keep = [k for k in range(4) if k != drop[i]]
+            for key in ("hx", "hy", "hz"):
+                pls[key][i] = np.concatenate([pls[key][i][keep], [0.0]])
+            pls["n_hits"][i] = 3
+            pls["x0"][i], pls["y0"][i], pls["z0"][i] = pls["hx"][i][0], pls["hy"][i][0], pls["hz"][i][0]
+            if i < n and drop[i] == 0:  # the reference moves to the second pixel layer
+                ptr = float(np.hypot(pls["px"][i], pls["py"][i]))
+                ph = t["phi0"][i] - q[i] * alphas[i, 1] + dphi[i]
+                pls["px"][i], pls["py"][i] = ptr * np.cos(ph), ptr * np.sin(ph)
     return pls, sim
 
 
 def event_from_tracks(geom: G.Geometry, t, seed: int, *, noise_frac=0.0, exact=False,
-                      with_pls=False, fake_pls_frac=0.10, shuffle=True) -> Event:
+                      with_pls=False, fake_pls_frac=0.10, shuffle=True, triplet_frac=0.0) -> Event:
     """Simulate the hits (and optionally the pixel seeds) of the given tracks."""
     rng = np.random.default_rng(seed)
     trk, _alpha, mod, sensor, x, y, z = track_crossings(geom, t)
@@ -370,7 +388,7 @@ def event_from_tracks(geom: G.Geometry, t, seed: int, *, noise_frac=0.0, exact=F
     if with_pls:
         sel = np.nonzero(t["pt"] >= PLS_PT_MIN)[0]
         n_fake = int(round(fake_pls_frac * len(sel)))
-        ev.pls, ev.pls_sim = make_pls(rng, t[sel], sel, n_fake, exact=exact)
+        ev.pls, ev.pls_sim = make_pls(rng, t[sel], sel, n_fake, exact=exact, triplet_frac=triplet_frac)
     return ev
 
 

@@ -39,9 +39,10 @@ def seed_of(workload: str, i: int) -> int:
 
 
 def make_event(workload: str, i: int = 0, *, n_tracks=None, with_pls=None, exact=False,
-               realistic=False) -> E.Event:
+               realistic=False, triplet_frac=0.0) -> E.Event:
     """Event ``i`` of ``workload`` (``n_tracks``/``with_pls`` override the recipe;
-    ``realistic`` simulates it in the geometry with tilted inner-barrel modules)."""
+    ``realistic`` simulates it in the geometry with tilted inner-barrel modules;
+    ``triplet_frac`` of the pixel seeds are triplets, three hits instead of four)."""
     seed = seed_of(workload, i)
     rng = np.random.default_rng(seed + 7)
     if workload in ("tiny", "batched"):
@@ -49,7 +50,7 @@ def make_event(workload: str, i: int = 0, *, n_tracks=None, with_pls=None, exact
         n = n_tracks if n_tracks is not None else (10 if workload == "tiny" else int(rng.integers(500, 6001)))
         t = E.random_tracks(rng, n, pt_mode="uniform", pt_lo=1.0, pt_hi=10.0, eta_max=1.0)
         return E.event_from_tracks(geom, t, seed, noise_frac=0.0, exact=exact,
-                                   with_pls=bool(with_pls))
+                                   with_pls=bool(with_pls), triplet_frac=triplet_frac)
     geom = geometry(False, realistic)
     if workload == "pu200":
         n, noise, pls = 4000, 0.20, False
@@ -65,7 +66,7 @@ def make_event(workload: str, i: int = 0, *, n_tracks=None, with_pls=None, exact
         pls = with_pls
     t = E.random_tracks(rng, n, pt_mode="inv2", pt_lo=0.5, eta_max=2.4)
     return E.event_from_tracks(geom, t, seed, noise_frac=0.0 if exact else noise, exact=exact,
-                               with_pls=pls)
+                               with_pls=pls, triplet_frac=triplet_frac)
 
 
 def workload_geometry(workload: str, realistic: bool = False) -> G.Geometry:

@@ -759,6 +759,8 @@ int ora_run(const ora_geom *g, const ora_event *ev, int brute_ls, ora_result *ou
     if (ev->det[i] >= 2u * nm) goto done;
     if (!isfinite(ev->x[i]) || !isfinite(ev->y[i]) || !isfinite(ev->z[i])) goto done;
   }
+  for (uint32_t p = 0; p < ev->n_pls; p++)
+    if (ev->pls[p].n_hits != 0 && ev->pls[p].n_hits != 3 && ev->pls[p].n_hits != 4) goto done;
   /* ---- hit binning by module sensor (stable: input order kept) ---- */
   bin_off = (uint32_t *)calloc(2 * (size_t)nm + 1, sizeof(uint32_t));
   bin_list = (uint32_t *)malloc(((size_t)nh + 1) * sizeof(uint32_t));
@@ -1070,7 +1072,9 @@ int ora_run(const ora_geom *g, const ora_event *ev, int brute_ls, ora_result *ou
           out->tc_ot[10 * (size_t)w + 2 * k] = md_lo.p[mds[k]];
           out->tc_ot[10 * (size_t)w + 2 * k + 1] = md_up.p[mds[k]];
         }
-        for (int k = 0; k < 4; k++) out->tc_pix[4 * (size_t)w + k] = pls != UINT32_MAX ? 4 * pls + (uint32_t)k : UINT32_MAX;
+        /* the seed's pixel hits: four for a quad, the first three for a triplet */
+        uint32_t npix = pls == UINT32_MAX ? 0 : (ev->pls[pls].n_hits == 3 ? 3 : 4);
+        for (uint32_t k = 0; k < 4; k++) out->tc_pix[4 * (size_t)w + k] = k < npix ? 4 * pls + k : UINT32_MAX;
         out->tc_pt[w] = pt;
         out->tc_score[w] = score;
         w++;

@@ -43,9 +43,9 @@ typedef struct {
 typedef struct {
   float px, py, pz;   /* momentum at the reference point (GeV) */
   float x0, y0, z0;   /* reference point (cm) */
-  float hx[4], hy[4], hz[4]; /* pixel hits */
+  float hx[4], hy[4], hz[4]; /* pixel hits (a triplet: the first three) */
   int32_t charge;     /* +1 / -1 */
-  uint32_t reserved;
+  uint32_t n_hits;    /* pixel hits: 4 (quad; 0 is read as 4) or 3 (triplet) */
 } ora_pls;
 
 typedef struct {

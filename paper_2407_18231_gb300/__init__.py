@@ -33,6 +33,8 @@ TC_DTYPE = np.dtype([("type", np.uint8), ("n_ot", np.uint8), ("n_pix", np.uint8)
                      ("obj", np.uint32), ("pls", np.uint32), ("ot", np.uint32, (10,)), ("pix", np.uint32, (4,)),
                      ("pt", np.float32), ("score", np.float32)])
 assert TC_DTYPE.itemsize == 76
+SEEDS_QUADS, SEEDS_QUADS_TRIPLETS = 0, 1
+SEED_DTYPE = np.dtype([("pls", np.uint32), ("n_pix", np.uint32), ("pix", np.uint32, (4,))])
 OBJ_DTYPES = {
     OBJ_MD: np.dtype([("module", np.uint32), ("lo", np.uint32), ("up", np.uint32)]),
     OBJ_LS: np.dtype([("md", np.uint32, (2,))]),
@@ -91,6 +93,7 @@ EXPORTS = [
     "lst_batch_finish", "lst_get_candidates", "lst_get_objects", "lst_release_result", "lst_destroy",
     "lst_last_error", "lst_status_string", "lst_get_stats", "lst_get_profile", "lst_serve_replay",
     "lst_run_event_static", "lst_set_tuning", "lst_get_candidates_batch", "lst_submit_batch", "lst_collect_batch",
+    "lst_get_seeds",
 ]
 
 _lib = None
@@ -128,6 +131,7 @@ def load_library(path: str = LIB_PATH):
             "lst_get_candidates_batch": (i32, [P, P, u32, P, C.c_uint64, P, C.POINTER(C.c_uint64)]),
             "lst_submit_batch": (i32, [P, P, u32, C.POINTER(C.c_uint64)]),
             "lst_collect_batch": (i32, [P, C.c_uint64, u32, P, P]),
+            "lst_get_seeds": (i32, [P, C.c_uint64, i32, P, u32, C.POINTER(u32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,6 +234,15 @@ class Session:
         _check(self.ctx, L.lst_get_candidates(self.ctx, rid, None, 0, C.byref(n)))
         out = np.zeros(n.value, TC_DTYPE)
         _check(self.ctx, L.lst_get_candidates(self.ctx, rid, out.ctypes.data, n.value, C.byref(n)))
+        return out
+
+    def seeds(self, rid: int, mode: int = SEEDS_QUADS) -> np.ndarray:
+        """The seeds LST left unlinked (lst_get_seeds): quads, or quads and triplets."""
+        L = load_library()
+        n = C.c_uint32()
+        _check(self.ctx, L.lst_get_seeds(self.ctx, rid, mode, None, 0, C.byref(n)))
+        out = np.zeros(n.value, SEED_DTYPE)
+        _check(self.ctx, L.lst_get_seeds(self.ctx, rid, mode, out.ctypes.data, n.value, C.byref(n)))
         return out
 
     def candidates_batch(self, rids) -> tuple[np.ndarray, np.ndarray]:

@@ -25,7 +25,7 @@ struct PlsIn {
   float px, py, pz, x0, y0, z0;
   float hx[4], hy[4], hz[4];
   int32_t charge;
-  uint32_t reserved;
+  uint32_t n_hits;  // pixel hits: 4 (quad; 0 is read as 4) or 3 (triplet)
 };
 
 // Per-batch header in device memory: input pointers, sizes, totals, error word.

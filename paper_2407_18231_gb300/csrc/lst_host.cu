@@ -1477,6 +1477,30 @@ lst_status lst_get_candidates(lst_ctx* c, lst_result_id id, lst_tc* buf, uint32_
   return LST_OK;
 }
 
+// The pLS track candidates (seeds no surviving pT3 or pT5 uses) of a result, as seeds.
+lst_status lst_get_seeds(lst_ctx* c, lst_result_id id, int32_t mode, lst_seed* buf, uint32_t cap, uint32_t* n_out) {
+  if (!c || !n_out) return LST_ERR_INVALID_ARG;
+  if (mode != LST_SEEDS_QUADS && mode != LST_SEEDS_QUADS_TRIPLETS) return fail(c, LST_ERR_INVALID_ARG, "unknown seed mode");
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->results.find(id);
+  if (it == c->results.end()) return fail(c, LST_ERR_NOT_FOUND, "unknown result id");
+  const Result& r = it->second;
+  const lst_tc* tc = r.tc_buf.get() + r.tc_off;
+  uint32_t n = 0;
+  for (size_t i = 0; i < r.tc_n; i++) {
+    if (tc[i].type != LST_TC_PLS || (mode == LST_SEEDS_QUADS && tc[i].n_pix != 4)) continue;
+    if (buf) {
+      if (n >= cap) return fail(c, LST_ERR_BUFFER_TOO_SMALL, "seed buffer too small");
+      buf[n].pls = tc[i].pls;
+      buf[n].n_pix = tc[i].n_pix;
+      for (int k = 0; k < 4; k++) buf[n].pix[k] = tc[i].pix[k];
+    }
+    n++;
+  }
+  *n_out = n;
+  return LST_OK;
+}
+
 lst_status lst_get_candidates_batch(lst_ctx* c, const lst_result_id* ids, uint32_t n, lst_tc* buf, uint64_t cap,
                                     uint32_t* counts, uint64_t* n_total) {
   if (!c || !n_total || (n && (!ids || !counts))) return LST_ERR_INVALID_ARG;

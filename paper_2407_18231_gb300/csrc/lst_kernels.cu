@@ -1232,7 +1232,7 @@ __global__ void k_pls_prep(MethodConst C, GeoView G, BufView B) {
     if (r == 0) B.pls_ev[p] = find_slot(H->pls_off, H->n_ev, p);
     bool bad = !(isfinite(s.px) && isfinite(s.py) && isfinite(s.pz) && isfinite(s.x0) && isfinite(s.y0) &&
                  isfinite(s.z0)) ||
-               (s.charge != 1 && s.charge != -1);
+               (s.charge != 1 && s.charge != -1) || (s.n_hits != 0 && s.n_hits != 3 && s.n_hits != 4);
     PlsHelix h;
     h.pt = sqrtf(s.px * s.px + s.py * s.py);
     if (!(h.pt > 0.0f)) bad = true;
@@ -2056,12 +2056,13 @@ __global__ void k_tc_offsets(GeoView G, BufView B) {
   }
 }
 
+// npix: the seed's pixel hits (4 for a quad, 3 for a triplet, 0 without a seed).
 __device__ __forceinline__ void write_tc(lst_tc* tc, uint8_t type, uint32_t obj, uint32_t pls, const uint32_t* mds,
-                                         int nmd, const BufView& B, float pt, float score) {
+                                         int nmd, const BufView& B, float pt, float score, uint32_t npix) {
   lst_tc r;
   r.type = type;
   r.n_ot = (uint8_t)(2 * nmd);
-  r.n_pix = pls != NONE ? 4 : 0;
+  r.n_pix = (uint8_t)npix;
   r.pad = 0;
   r.obj = obj;
   r.pls = pls;
@@ -2070,11 +2071,14 @@ __device__ __forceinline__ void write_tc(lst_tc* tc, uint8_t type, uint32_t obj,
     r.ot[2 * k] = B.md_lo_idx[mds[k]];
     r.ot[2 * k + 1] = B.md_up_idx[mds[k]];
   }
-  for (int k = 0; k < 4; k++) r.pix[k] = pls != NONE ? 4 * pls + (uint32_t)k : NONE;
+  for (uint32_t k = 0; k < 4; k++) r.pix[k] = k < npix ? 4 * pls + k : NONE;
   r.pt = pt;
   r.score = score;
   *tc = r;
 }
+
+// Pixel hits of seed p (global index): a triplet has three, anything else four.
+__device__ __forceinline__ uint32_t seed_hits(const Hdr* H, uint32_t p) { return H->pls[p].n_hits == 3 ? 3u : 4u; }
 
 // Survivors -> track candidates: per event pT5s, pT3s, T5s, then unused pLSs (Sec. 1 list).
 __global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
@@ -2092,7 +2096,7 @@ __global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
       const uint32_t pos = B.tc_ev_off[e] + (B.sa5[x] - B.sa5[c.b5]);
       uint32_t m[5];
       t5_mds(B, B.pt5_obj[x], m);
-      write_tc(tc + pos, LST_TC_PT5, x - c.b5, p - c.bp, m, 5, B, B.pls_pt[p], B.pt5_score[x]);
+      write_tc(tc + pos, LST_TC_PT5, x - c.b5, p - c.bp, m, 5, B, B.pls_pt[p], B.pt5_score[x], seed_hits(H, p));
     } else if (i < n5 + n3) {
       const uint32_t x = i - n5;
       if (!B.alive3[x]) continue;
@@ -2101,7 +2105,7 @@ __global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
       const uint32_t pos = B.tc_ev_off[e] + c.n5 + (B.sa3[x] - B.sa3[c.b3]);
       uint32_t m[3];
       t3_mds(B, B.pt3_obj[x], m);
-      write_tc(tc + pos, LST_TC_PT3, x - c.b3, p - c.bp, m, 3, B, B.pls_pt[p], B.pt3_score[x]);
+      write_tc(tc + pos, LST_TC_PT3, x - c.b3, p - c.bp, m, 3, B, B.pls_pt[p], B.pt3_score[x], seed_hits(H, p));
     } else if (i < n5 + n3 + nt) {
       const uint32_t x = i - n5 - n3;
       if (!B.alivet[x]) continue;
@@ -2110,14 +2114,14 @@ __global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
       const uint32_t pos = B.tc_ev_off[e] + c.n5 + c.n3 + (B.sat[x] - B.sat[c.bt]);
       uint32_t m[5];
       t5_mds(B, x, m);
-      write_tc(tc + pos, LST_TC_T5, x - c.bt, NONE, m, 5, B, C.KB / fabsf(B.t5_kfull[x]), B.t5_score[x]);
+      write_tc(tc + pos, LST_TC_T5, x - c.bt, NONE, m, 5, B, C.KB / fabsf(B.t5_kfull[x]), B.t5_score[x], 0u);
     } else {
       const uint32_t p = i - n5 - n3 - nt;
       if (!B.plstc[p]) continue;
       const uint32_t e = B.pls_ev[p];
       const EvCounts c = ev_counts(G, B, H, e);
       const uint32_t pos = B.tc_ev_off[e] + c.n5 + c.n3 + c.nt + (B.sap[p] - B.sap[c.bp]);
-      write_tc(tc + pos, LST_TC_PLS, p - c.bp, p - c.bp, nullptr, 0, B, B.pls_pt[p], 0.0f);
+      write_tc(tc + pos, LST_TC_PLS, p - c.bp, p - c.bp, nullptr, 0, B, B.pls_pt[p], 0.0f, seed_hits(H, p));
     }
   }
 }

@@ -59,6 +59,7 @@ def compare(sess, rid, ora, ev, label=""):
     assert np.array_equal(_bits(tc["pt"]), _bits(ora["tc_pt"])), label
     assert np.array_equal(_bits(tc["score"]), _bits(ora["tc_score"])), label
     assert np.all(tc["n_ot"] == (tc["ot"] != lst.NONE).sum(1))
+    assert np.all(tc["n_pix"] == (tc["pix"] != lst.NONE).sum(1))
 
 
 @pytest.fixture(scope="module")
@@ -431,3 +432,35 @@ def test_tilted_batch_parity(sess_tilted, ora_tilted):
     ids = sess_tilted.run_batch(evs)
     for i, (rid, ev) in enumerate(zip(ids, evs)):
         compare(sess_tilted, rid, oracle.run(ora_tilted, ev), ev, f"tilted batch {i}")
+
+
+# ---------------------------------------------------------------- LST as a seeder
+def test_triplet_seeds_parity_and_seeder_output(sess_full, ora_full):
+    """Events whose pixel seeds are 20 % triplets: every list equals the oracle's, and
+    lst_get_seeds returns exactly the unlinked seeds (pLS candidates), quads only or quads
+    and triplets (Sec. 2, Table 1)."""
+    evs = [S.make_event("pu200", 30 + i, n_tracks=n, with_pls=True, triplet_frac=0.2)
+           for i, n in enumerate((4000, 1200))]
+    ids = sess_full.run_batch(evs)
+    for rid, ev in zip(ids, evs):
+        ora = oracle.run(ora_full, ev)
+        compare(sess_full, rid, ora, ev, "triplet seeds")
+        nh = np.where(ev.pls["n_hits"] == 3, 3, 4)
+        assert (nh == 3).sum() > 50
+        unlinked = np.nonzero(ora["pls_tc"])[0]
+        for mode, want in ((lst.SEEDS_QUADS, unlinked[nh[unlinked] == 4]), (lst.SEEDS_QUADS_TRIPLETS, unlinked)):
+            seeds = sess_full.seeds(rid, mode)
+            assert np.array_equal(seeds["pls"], want)
+            assert np.array_equal(seeds["n_pix"], nh[want])
+            for s_ in seeds:
+                assert list(s_["pix"][: s_["n_pix"]]) == [4 * s_["pls"] + k for k in range(s_["n_pix"])]
+
+
+def test_bad_seed_hit_count_is_rejected(sess_full):
+    ev = S.make_event("pu200", 33, n_tracks=300, with_pls=True)
+    ev.pls["n_hits"][5] = 2
+    with pytest.raises(lst.LstError) as e:
+        sess_full.run_event(ev)
+    assert e.value.status == -2
+    ev.pls["n_hits"][5] = 4
+    assert len(sess_full.candidates(sess_full.run_event(ev))) > 0

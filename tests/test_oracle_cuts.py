@@ -597,3 +597,38 @@ def test_pt3_sharing_two_mds_with_a_pt5_is_removed(barrel_geom, ora_barrel):
     assert not np.any(r["alive_pt3"][pt3_b])
     types = sorted(zip(r["tc_type"].tolist(), r["tc_pls"].tolist()))
     assert (0, 0) in types and (3, 1) in types and all(t != 1 for t, _ in types)
+
+
+def test_triplet_seeds_link_like_quads(barrel_geom, ora_barrel):
+    """A pixel triplet (one of the four pixel hits missing, Sec. 2: legacy and LST
+    triplets) carries the same helix at its first remaining hit: exact triplet seeds of
+    clean tracks form the same pT5 as the quad would, with the three pixel hits in the
+    candidate; with the first hit missing, the reference point moves to the second pixel
+    layer and the seed still links."""
+    from lst_synth import events as E
+    n = 0
+    for phi0 in np.linspace(0.3, 6.0, 12):
+        t = track(4.0, phi0, 0.2)
+        ev = E.event_from_tracks(barrel_geom, t, 5, exact=True, with_pls=True, fake_pls_frac=0.0, shuffle=False)
+        if len(doublets(ev)) != 6 or ev.n_pls != 1:
+            continue
+        quad = oracle.run(ora_barrel, ev)
+        assert list(quad["tc_type"]) == [0]
+        for drop in (0, 2):
+            pls, _ = E.make_pls(np.random.default_rng(0), t, np.array([0]), 0, exact=True)
+            keep = [k for k in range(4) if k != drop]
+            for key in ("hx", "hy", "hz"):
+                pls[key][0] = np.concatenate([pls[key][0][keep], [0.0]])
+            pls["n_hits"][0] = 3
+            if drop == 0:
+                a = E.cylinder_alpha(t, E.PIXEL_R[1])
+                x, y, z, ph = E.helix_point(t, a)
+                pls["x0"][0], pls["y0"][0], pls["z0"][0] = x[0], y[0], z[0]
+                ptr = float(np.hypot(pls["px"][0], pls["py"][0]))
+                pls["px"][0], pls["py"][0] = ptr * np.cos(ph[0]), ptr * np.sin(ph[0])
+            r = oracle.run(ora_barrel, edited(ev, {}, pls=pls))
+            assert list(r["tc_type"]) == [0]
+            assert list(r["tc_pix"][0]) == [0, 1, 2, 0xFFFFFFFF]
+            assert r["tc_pt"][0] == pytest.approx(4.0, rel=1e-5)
+            n += 1
+    assert n >= 10

@@ -133,6 +133,7 @@ MUTATIONS = [
     ("dedup: tie broken the wrong way", "return sy < sx || (sy == sx && y < x);", "return sy < sx || (sy == sx && y > x);"),
     ("tc: pLS used by a pT3 stays a candidate", "out->pls_tc[p] = !(used5[p] || used3[p]);", "out->pls_tc[p] = !used5[p];"),
     ("tc: T5 pT without the field constant", "pt = C_KB / fabsf(t5k.p[x]);", "pt = 1.0f / fabsf(t5k.p[x]);"),
+    ("tc: a triplet seed listed with four pixel hits", "(ev->pls[pls].n_hits == 3 ? 3 : 4)", "(4)"),
 ]
 
 
