@@ -100,6 +100,12 @@ def lib():
             L.ora_pls_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, F3, F3]
             L.ora_pt5_eval.restype = C.c_uint32
             L.ora_pt5_eval.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint32), F3]
+            L.ora_geom_set_t5_mlp.restype = C.c_int
+            L.ora_geom_set_t5_mlp.argtypes = [C.c_void_p, F3, C.c_uint32]
+            L.ora_t5_features.restype = C.c_uint32
+            L.ora_t5_features.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), F3, F3]
+            L.ora_t5_logit.restype = C.c_float
+            L.ora_t5_logit.argtypes = [F3, F3]
             _lib = L
     return _lib
 
@@ -246,6 +252,39 @@ def t5_eval(geom: Geometry, mods, pts):
     sc, kf = C.c_float(), C.c_float()
     mask = lib().ora_t5_eval(geom._h, m, p, C.byref(sc), C.byref(kf))
     return int(mask), np.float32(sc.value), np.float32(kf.value)
+
+
+T5_NF, T5_NH = 8, 16
+T5_NPARAM = T5_NH * T5_NF + T5_NH + T5_NH * T5_NH + T5_NH + T5_NH + 1
+
+
+def set_t5_mlp(geom: Geometry, weights) -> None:
+    """Learned T5 selection on ``geom`` (T5_NPARAM float32 weights), or None for the cuts."""
+    if weights is None:
+        lib().ora_geom_set_t5_mlp(geom._h, None, 0)
+        return
+    w = np.ascontiguousarray(np.asarray(weights, np.float32).ravel())
+    if lib().ora_geom_set_t5_mlp(geom._h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size) != 0:
+        raise ValueError("bad T5 network weights")
+
+
+def t5_features(geom: Geometry, mods, pts) -> np.ndarray:
+    """The T5_NF network inputs of five anchors (x, y, z) on modules ``mods``."""
+    m = (C.c_uint32 * 5)(*map(int, mods))
+    p = (C.c_float * 15)(*np.asarray(pts, np.float32).ravel().tolist())
+    f = (C.c_float * T5_NF)()
+    if not lib().ora_t5_features(geom._h, m, p, f):
+        raise ValueError("module id out of range")
+    return np.array(f[:], np.float32)
+
+
+def t5_logit(weights, f) -> np.float32:
+    """Network output z for inputs f (the candidate passes when z > 0)."""
+    w = np.ascontiguousarray(np.asarray(weights, np.float32).ravel())
+    x = np.ascontiguousarray(np.asarray(f, np.float32).ravel())
+    assert w.size == T5_NPARAM and x.size == T5_NF
+    return np.float32(lib().ora_t5_logit(w.ctypes.data_as(C.POINTER(C.c_float)),
+                                         x.ctypes.data_as(C.POINTER(C.c_float))))
 
 
 def pls_eval(geom: Geometry, pls, module: int, x):

@@ -91,6 +91,7 @@ struct ora_geom {
   uint32_t *surf_list[NSURF];   /* module ids of each surface, ascending */
   uint32_t surf_count[NSURF];
   uint32_t *row_off, *cols;     /* connection map (CSR) */
+  float *t5_mlp;                /* learned T5 selection (ORA_T5_NPARAM weights), NULL = cuts */
 };
 
 static int module_surface(const ora_module *m) {
@@ -230,7 +231,7 @@ void ora_geom_destroy(ora_geom *g) {
     free(g->surf_list[s]);
   }
   free(g->m); free(g->surface); free(g->T); free(g->zeta); free(g->rho); free(g->delta); free(g->rnext);
-  free(g->row_off); free(g->cols);
+  free(g->row_off); free(g->cols); free(g->t5_mlp);
   free(g);
 }
 
@@ -412,16 +413,21 @@ static int ls_pass(const pt_t *a, const pt_t *au, const pt_t *b, const pt_t *bu,
 /* r-z straightness of three hits p, q, s along the transverse chord: z is linear in arc
  * length, so (zq - zp) d_ps = (zs - zp) d_pq up to the arc/chord bound and the
  * resolution terms.  No beam-line constraint (displaced tracks). */
-static int rz3(const pt_t *p, const pt_t *q, const pt_t *s) {
+static void rz3_terms(const pt_t *p, const pt_t *q, const pt_t *s, float *lhs, float *tol) {
   float dxq = q->x - p->x, dyq = q->y - p->y;
   float dxs = s->x - p->x, dys = s->y - p->y;
   float dpq = sqrtf(dxq * dxq + dyq * dyq);
   float dps = sqrtf(dxs * dxs + dys * dys);
   float zqp = q->z - p->z;
   float zsp = s->z - p->z;
-  float lhs = fabsf(zqp * dps - zsp * dpq);
-  float tol = C_KARC * dps * dps * fabsf(zsp) * dpq + p->zeta * fabsf(dps - dpq) + q->zeta * dps + s->zeta * dpq +
-              (p->rho + s->rho) * fabsf(zqp) + (p->rho + q->rho) * fabsf(zsp);
+  *lhs = fabsf(zqp * dps - zsp * dpq);
+  *tol = C_KARC * dps * dps * fabsf(zsp) * dpq + p->zeta * fabsf(dps - dpq) + q->zeta * dps + s->zeta * dpq +
+         (p->rho + s->rho) * fabsf(zqp) + (p->rho + q->rho) * fabsf(zsp);
+}
+
+static int rz3(const pt_t *p, const pt_t *q, const pt_t *s) {
+  float lhs, tol;
+  rz3_terms(p, q, s, &lhs, &tol);
   return lhs <= tol;
 }
 
@@ -489,28 +495,106 @@ static int t3_pass(const pt_t *a, const pt_t *b, const pt_t *bu, const pt_t *c) 
   return t3_radius(a, b, c);
 }
 
+/* The four circles of a T5 (a..e): inner (a,b,c), outer (c,d,e), bridge (b,c,d) and full
+ * (a,c,e), their curvature differences d1 = |kin - kout|, d2 = |kbr - kfu| and the
+ * right-hand sides of the two agreement conditions,
+ * rhs = kappa (|k1| + |k2|) + tol1 + tol2 + kappa0. */
+typedef struct { float kin, tin, kout, tout, kbr, tbr, kfu, tfu, d1, d2, rhs1, rhs2; } t5_circles;
+
+static void t5_circles_of(const pt_t *P[5], t5_circles *c) {
+  curv3(P[0], P[1], P[2], &c->kin, &c->tin, NULL, NULL, NULL);
+  curv3(P[2], P[3], P[4], &c->kout, &c->tout, NULL, NULL, NULL);
+  curv3(P[1], P[2], P[3], &c->kbr, &c->tbr, NULL, NULL, NULL);
+  curv3(P[0], P[2], P[4], &c->kfu, &c->tfu, NULL, NULL, NULL);
+  c->d1 = fabsf(c->kin - c->kout);
+  c->d2 = fabsf(c->kbr - c->kfu);
+  c->rhs1 = C_KAPPA * (fabsf(c->kin) + fabsf(c->kout)) + c->tin + c->tout + C_KAPPA0;
+  c->rhs2 = C_KAPPA * (fabsf(c->kbr) + fabsf(c->kfu)) + c->tbr + c->tfu + C_KAPPA0;
+}
+
+/* x / (x + y) for non-negative x, y (0 when both are 0). */
+static float frac_of(float x, float y) {
+  float den = x + y;
+  return den > 0.0f ? x / den : 0.0f;
+}
+
+/* Inputs of the learned T5 selection (Sec. 1 cites machine-learning methods among the LST
+ * selections; this reading scores the curvature agreement with a small network instead of
+ * the two kappa conditions).  Every input but f5 is a ratio x / (x + y) of non-negative
+ * terms, so it lies in [0, 1):
+ *   f0 = d1 / (d1 + rhs1)                 inner/outer difference against its tolerance
+ *   f1 = d2 / (d2 + rhs2)                 bridge/full difference against its tolerance
+ *   f2 = d1 / (d1 + |kin| + |kout| + kappa0)   relative inner/outer difference
+ *   f3 = d2 / (d2 + |kbr| + |kfu| + kappa0)    relative bridge/full difference
+ *   f4 = e / (e + |kin| + |kout| + kappa0), e = tol_in + tol_out: relative curvature error
+ *   f5 = |kfu| / kmax                     full curvature against the pT threshold's
+ *   f6 = l / (l + t), the r-z straightness residual l and tolerance t of (a, c, e)
+ *   f7 = the same for (b, c, d), the triple across the shared MD c. */
+static void t5_features_of(const pt_t *P[5], const t5_circles *c, float f[ORA_T5_NF]) {
+  float l, t;
+  f[0] = frac_of(c->d1, c->rhs1);
+  f[1] = frac_of(c->d2, c->rhs2);
+  f[2] = frac_of(c->d1, fabsf(c->kin) + fabsf(c->kout) + C_KAPPA0);
+  f[3] = frac_of(c->d2, fabsf(c->kbr) + fabsf(c->kfu) + C_KAPPA0);
+  f[4] = frac_of(c->tin + c->tout, fabsf(c->kin) + fabsf(c->kout) + C_KAPPA0);
+  f[5] = fabsf(c->kfu) / C_KMAX;
+  rz3_terms(P[0], P[2], P[4], &l, &t);
+  f[6] = frac_of(l, t);
+  rz3_terms(P[1], P[2], P[3], &l, &t);
+  f[7] = frac_of(l, t);
+}
+
+/* The network: two hidden layers of ORA_T5_NH rectified units and a linear output,
+ *   h1[j] = max(0, b1[j] + sum_i w1[j][i] f[i]),  h2[k] = max(0, b2[k] + sum_j w2[k][j] h1[j]),
+ *   z = b3 + sum_k w3[k] h2[k],
+ * in binary32, every sum accumulated from the bias in index order.  Weights in that order:
+ * w1 (row j holds unit j's ORA_T5_NF inputs), b1, w2 (row k), b2, w3, b3.  The candidate
+ * passes when z > 0. */
+static float t5_mlp_logit(const float *w, const float f[ORA_T5_NF]) {
+  const float *w1 = w, *b1 = w1 + ORA_T5_NH * ORA_T5_NF, *w2 = b1 + ORA_T5_NH;
+  const float *b2 = w2 + ORA_T5_NH * ORA_T5_NH, *w3 = b2 + ORA_T5_NH, *b3 = w3 + ORA_T5_NH;
+  float h1[ORA_T5_NH], h2[ORA_T5_NH];
+  for (int j = 0; j < ORA_T5_NH; j++) {
+    float a = b1[j];
+    for (int i = 0; i < ORA_T5_NF; i++) a = a + w1[j * ORA_T5_NF + i] * f[i];
+    h1[j] = a > 0.0f ? a : 0.0f;
+  }
+  for (int k = 0; k < ORA_T5_NH; k++) {
+    float a = b2[k];
+    for (int j = 0; j < ORA_T5_NH; j++) a = a + w2[k * ORA_T5_NH + j] * h1[j];
+    h2[k] = a > 0.0f ? a : 0.0f;
+  }
+  float z = b3[0];
+  for (int k = 0; k < ORA_T5_NH; k++) z = z + w3[k] * h2[k];
+  return z;
+}
+
 /* T5 (Sec. 1: two T3s sharing an MD; circle-radius consistency): curvatures of the
  * inner (a,b,c), outer (c,d,e), bridge (b,c,d) and full (a,c,e) triples must agree,
  * the full circle must satisfy R >= Rmin (1 - 5 %), and a, c, e must be straight in r-z.
- * Returns the four conditions as bits 0-3 (inner/outer, bridge/full, radius, r-z). */
-static unsigned t5_eval(const pt_t *P[5], float *score, float *kfull_out) {
-  float kin, tin, kout, tout, kbr, tbr, kfu, tfu;
-  curv3(P[0], P[1], P[2], &kin, &tin, NULL, NULL, NULL);
-  curv3(P[2], P[3], P[4], &kout, &tout, NULL, NULL, NULL);
-  curv3(P[1], P[2], P[3], &kbr, &tbr, NULL, NULL, NULL);
-  curv3(P[0], P[2], P[4], &kfu, &tfu, NULL, NULL, NULL);
-  float d1 = fabsf(kin - kout);
-  float d2 = fabsf(kbr - kfu);
-  int c1 = d1 <= C_KAPPA * (fabsf(kin) + fabsf(kout)) + tin + tout + C_KAPPA0;
-  int c2 = d2 <= C_KAPPA * (fabsf(kbr) + fabsf(kfu)) + tbr + tfu + C_KAPPA0;
-  int c3 = fabsf(kfu) <= C_KMAX + tfu;
+ * Returns the four conditions as bits 0-3 (inner/outer, bridge/full, radius, r-z).  With a
+ * learned selection (mlp != NULL) the network's decision replaces both agreement
+ * conditions: bits 0 and 1 are each z > 0. */
+static unsigned t5_eval(const pt_t *P[5], const float *mlp, float *score, float *kfull_out) {
+  t5_circles c;
+  t5_circles_of(P, &c);
+  int c1 = c.d1 <= c.rhs1;
+  int c2 = c.d2 <= c.rhs2;
+  int c3 = fabsf(c.kfu) <= C_KMAX + c.tfu;
   int c4 = rz3(P[0], P[2], P[4]);
-  *score = d1 + d2;
-  *kfull_out = kfu;
+  if (mlp) {
+    float f[ORA_T5_NF];
+    t5_features_of(P, &c, f);
+    c1 = c2 = t5_mlp_logit(mlp, f) > 0.0f;
+  }
+  *score = c.d1 + c.d2;
+  *kfull_out = c.kfu;
   return (unsigned)c1 | (unsigned)c2 << 1 | (unsigned)c3 << 2 | (unsigned)c4 << 3;
 }
 
-static int t5_pass(const pt_t *P[5], float *score, float *kfull_out) { return t5_eval(P, score, kfull_out) == 15u; }
+static int t5_pass(const pt_t *P[5], const float *mlp, float *score, float *kfull_out) {
+  return t5_eval(P, mlp, score, kfull_out) == 15u;
+}
 
 /* ---------------- pLS helix and module lookup ---------------- */
 typedef struct { float x0, y0, z0, R, cx, cy, cot, q, pt; int valid; } pls_t;
@@ -871,7 +955,7 @@ int ora_run(const ora_geom *g, const ora_event *ev, int brute_ls, ora_result *ou
                             &hit[md_lo.p[e]]};
         float score, kf;
         out->n_tests[3]++;
-        if (t5_pass(P, &score, &kf)) {
+        if (t5_pass(P, g->t5_mlp, &score, &kf)) {
           if (vu32_push(&t5, a) || vu32_push(&t5, b) || vu32_push(&t5, c) || vu32_push(&t5, d) ||
               vu32_push(&t5, e) || vf32_push(&t5s, score) || vf32_push(&t5k, kf))
             goto done;
@@ -1214,7 +1298,40 @@ uint32_t ora_t5_eval(const ora_geom *g, const uint32_t mod[5], const float p[15]
     load_pt(g, mod[k], p + 3 * k, &q[k]);
     P[k] = &q[k];
   }
-  return t5_eval(P, score, kfull);
+  return t5_eval(P, g->t5_mlp, score, kfull);
+}
+
+uint32_t ora_t5_features(const ora_geom *g, const uint32_t mod[5], const float p[15], float f[ORA_T5_NF]) {
+  pt_t q[5];
+  const pt_t *P[5];
+  for (int k = 0; k < 5; k++) {
+    if (mod[k] >= g->n) return 0;
+    load_pt(g, mod[k], p + 3 * k, &q[k]);
+    P[k] = &q[k];
+  }
+  t5_circles c;
+  t5_circles_of(P, &c);
+  t5_features_of(P, &c, f);
+  return 1;
+}
+
+float ora_t5_logit(const float *w, const float f[ORA_T5_NF]) { return t5_mlp_logit(w, f); }
+
+int ora_geom_set_t5_mlp(ora_geom *g, const float *w, uint32_t n) {
+  if (!w) {
+    free(g->t5_mlp);
+    g->t5_mlp = NULL;
+    return 0;
+  }
+  if (n != ORA_T5_NPARAM) return -1;
+  for (uint32_t i = 0; i < n; i++)
+    if (!isfinite(w[i])) return -1;
+  float *c = (float *)malloc(n * sizeof(float));
+  if (!c) return -1;
+  memcpy(c, w, n * sizeof(float));
+  free(g->t5_mlp);
+  g->t5_mlp = c;
+  return 0;
 }
 
 uint32_t ora_pls_eval(const ora_geom *g, const ora_pls *s, uint32_t module, const float x[3], float *score) {
@@ -1241,6 +1358,6 @@ uint32_t ora_pt5_eval(const ora_geom *g, const ora_pls *s, const uint32_t mod[5]
   float score = 0.0f, t5score, kf;
   int ok = 1;
   for (int k = 0; k < 5; k++) ok &= pls_anchor(&p, P[k], &score);
-  t5_eval(P, &t5score, &kf);
+  t5_eval(P, NULL, &t5score, &kf);
   return (uint32_t)ok | (uint32_t)pt5_curv(&p, kf, P[0], P[2], P[4]) << 1;
 }

@@ -106,6 +106,19 @@ uint32_t ora_ls_eval(const ora_geom *g, uint32_t A, uint32_t B, const float a[3]
 uint32_t ora_t3_eval(const ora_geom *g, const uint32_t mod[3], const float a[3], const float b[3],
                      const float bu[3], const float c[3]);
 uint32_t ora_t5_eval(const ora_geom *g, const uint32_t mod[5], const float p[15], float *score, float *kfull);
+
+/* Learned T5 selection: ORA_T5_NF inputs per candidate, two hidden layers of ORA_T5_NH
+ * units, ORA_T5_NPARAM weights (w1, b1, w2, b2, w3, b3; see t5_mlp_logit).
+ * ora_geom_set_t5_mlp copies the weights into the geometry (w == NULL: back to the kappa
+ * cuts); returns 0, or -1 when n != ORA_T5_NPARAM or a weight is not finite.
+ * ora_t5_features fills f (returns 0 when a module id is out of range);
+ * ora_t5_logit evaluates the network on f. */
+#define ORA_T5_NF 8
+#define ORA_T5_NH 16
+#define ORA_T5_NPARAM (ORA_T5_NH * ORA_T5_NF + ORA_T5_NH + ORA_T5_NH * ORA_T5_NH + ORA_T5_NH + ORA_T5_NH + 1)
+int ora_geom_set_t5_mlp(ora_geom *g, const float *w, uint32_t n);
+uint32_t ora_t5_features(const ora_geom *g, const uint32_t mod[5], const float p[15], float f[ORA_T5_NF]);
+float ora_t5_logit(const float *w, const float f[ORA_T5_NF]);
 uint32_t ora_pls_eval(const ora_geom *g, const ora_pls *s, uint32_t module, const float x[3], float *score);
 uint32_t ora_pt5_eval(const ora_geom *g, const ora_pls *s, const uint32_t mod[5], const float pts[15]);
 

@@ -96,6 +96,21 @@ EXPORTS = [
     "lst_get_seeds",
 ]
 
+T5_MLP_PARAMS = 433  # LST_T5_MLP_PARAMS
+T5_MLP_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "t5_mlp_pu200.json")
+
+
+def load_t5_mlp(path: str = T5_MLP_PATH) -> np.ndarray:
+    """Weights of the learned T5 selection (LST_T5_MLP_PARAMS float32, lst.h order) from a
+    JSON file; the default is the network the package ships, trained on synthetic PU200-like
+    events."""
+    import json
+    with open(path) as f:
+        w = np.array(json.load(f)["weights"], np.float32)
+    if w.size != T5_MLP_PARAMS:
+        raise ValueError(f"{path}: {w.size} weights, expected {T5_MLP_PARAMS}")
+    return w
+
 _lib = None
 _lock = threading.Lock()
 

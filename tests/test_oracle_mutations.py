@@ -4,7 +4,7 @@ Each mutation below is one plausible slip in the oracle's source (a dropped term
 flipped sign, a transposed operand, a wrong index or bound).  The test builds a copy of
 lst_oracle.c with that one change (on the CPU, in a temporary directory), runs the oracle
 pins (test_oracle_pins.py, test_oracle_cuts.py, test_oracle_enumeration.py,
-test_oracle_tilted.py) against the
+test_oracle_tilted.py, test_oracle_t5_mlp.py) against the
 copy in a child process, and requires at least one of them to fail.  A mutation that no
 pin catches would be a part of the oracle that nothing but the oracle itself vouches for.
 """
@@ -19,7 +19,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lst_oracle.c")
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_cuts.py", "tests/test_oracle_enumeration.py",
-        "tests/test_oracle_tilted.py"]
+        "tests/test_oracle_tilted.py", "tests/test_oracle_t5_mlp.py"]
 
 # Two widening terms are left out on purpose: the endcap part of the bending slack
 # (rho_a + rho_b) (|sin dphi| + 0.05) and the sensor gap in a barrel module's r_max.  No
@@ -67,9 +67,9 @@ MUTATIONS = [
     ("exit: start from the outer anchor", "float rexit = a->r + (b->r - a->r) * t;", "float rexit = b->r + (b->r - a->r) * t;"),
     ("exit: one side only", "float Zb = b->z > 0.0f ? zb_half : -zb_half;", "float Zb = zb_half;"),
     # T3
-    ("rz3: operands transposed", "float lhs = fabsf(zqp * dps - zsp * dpq);", "float lhs = fabsf(zqp * dpq - zsp * dps);"),
+    ("rz3: operands transposed", "*lhs = fabsf(zqp * dps - zsp * dpq);", "*lhs = fabsf(zqp * dpq - zsp * dps);"),
     ("rz3: resolution terms dropped",
-     "p->zeta * fabsf(dps - dpq) + q->zeta * dps + s->zeta * dpq +\n              (p->rho + s->rho) * fabsf(zqp) + (p->rho + q->rho) * fabsf(zsp);",
+     "p->zeta * fabsf(dps - dpq) + q->zeta * dps + s->zeta * dpq +\n         (p->rho + s->rho) * fabsf(zqp) + (p->rho + q->rho) * fabsf(zsp);",
      "(p->rho + s->rho) * fabsf(zqp) + (p->rho + q->rho) * fabsf(zsp);"),
     ("mid_dir: arc difference as a sum", "(fabsf(dbc - dab) + 0.02f * clen)", "((dbc + dab) + 0.02f * clen)"),
     ("mid_dir: direction error dropped",
@@ -81,14 +81,14 @@ MUTATIONS = [
     # curvature and T5
     ("curv3: factor 2 dropped", "*k = 2.0f * cross / prod;", "*k = cross / prod;"),
     ("curv3: sagitta tolerance not squared", "*tol = 8.0f * dmax / (dsp * dsp);", "*tol = 8.0f * dmax / dsp;"),
-    ("t5: inner/outer difference as a sum", "float d1 = fabsf(kin - kout);", "float d1 = fabsf(kin + kout);"),
-    ("t5: bridge triple index", "curv3(P[1], P[2], P[3], &kbr, &tbr, NULL, NULL, NULL);",
-     "curv3(P[1], P[2], P[4], &kbr, &tbr, NULL, NULL, NULL);"),
-    ("t5: radius from the inner triple", "int c3 = fabsf(kfu) <= C_KMAX + tfu;", "int c3 = fabsf(kin) <= C_KMAX + tfu;"),
+    ("t5: inner/outer difference as a sum", "c->d1 = fabsf(c->kin - c->kout);", "c->d1 = fabsf(c->kin + c->kout);"),
+    ("t5: bridge triple index", "curv3(P[1], P[2], P[3], &c->kbr, &c->tbr, NULL, NULL, NULL);",
+     "curv3(P[1], P[2], P[4], &c->kbr, &c->tbr, NULL, NULL, NULL);"),
+    ("t5: radius from the inner triple", "int c3 = fabsf(c.kfu) <= C_KMAX + c.tfu;", "int c3 = fabsf(c.kin) <= C_KMAX + c.tfu;"),
     ("t5: r-z of the wrong triple", "int c4 = rz3(P[0], P[2], P[4]);", "int c4 = rz3(P[0], P[1], P[4]);"),
-    ("t5: relative slack dropped", "int c1 = d1 <= C_KAPPA * (fabsf(kin) + fabsf(kout)) + tin + tout + C_KAPPA0;",
-     "int c1 = d1 <= tin + tout + C_KAPPA0;"),
-    ("t5: score without the bridge term", "*score = d1 + d2;", "*score = d1;"),
+    ("t5: relative slack dropped", "c->rhs1 = C_KAPPA * (fabsf(c->kin) + fabsf(c->kout)) + c->tin + c->tout + C_KAPPA0;",
+     "c->rhs1 = c->tin + c->tout + C_KAPPA0;"),
+    ("t5: score without the bridge term", "*score = c.d1 + c.d2;", "*score = c.d1;"),
     # pLS helix, lookup, anchors
     ("pls: centre on the wrong side", "o->cx = s->x0 + qR * uy;", "o->cx = s->x0 - qR * uy;"),
     ("pls: cot from the radius", "o->cot = s->pz / o->pt;", "o->cot = s->pz / o->R;"),
@@ -134,6 +134,23 @@ MUTATIONS = [
     ("tc: pLS used by a pT3 stays a candidate", "out->pls_tc[p] = !(used5[p] || used3[p]);", "out->pls_tc[p] = !used5[p];"),
     ("tc: T5 pT without the field constant", "pt = C_KB / fabsf(t5k.p[x]);", "pt = 1.0f / fabsf(t5k.p[x]);"),
     ("tc: a triplet seed listed with four pixel hits", "(ev->pls[pls].n_hits == 3 ? 3 : 4)", "(4)"),
+    # learned T5 selection: its inputs, the network, where its decision goes
+    ("t5 net: f0 against the bridge/full tolerance", "f[0] = frac_of(c->d1, c->rhs1);", "f[0] = frac_of(c->d1, c->rhs2);"),
+    ("t5 net: f3 with the inner curvature", "f[3] = frac_of(c->d2, fabsf(c->kbr) + fabsf(c->kfu) + C_KAPPA0);",
+     "f[3] = frac_of(c->d2, fabsf(c->kin) + fabsf(c->kfu) + C_KAPPA0);"),
+    ("t5 net: f4 with the bridge error", "f[4] = frac_of(c->tin + c->tout,", "f[4] = frac_of(c->tbr + c->tout,"),
+    ("t5 net: f5 times k_max", "f[5] = fabsf(c->kfu) / C_KMAX;", "f[5] = fabsf(c->kfu) * C_KMAX;"),
+    ("t5 net: f6 on (a, b, e)", "rz3_terms(P[0], P[2], P[4], &l, &t);\n  f[6]", "rz3_terms(P[0], P[1], P[4], &l, &t);\n  f[6]"),
+    ("t5 net: f7 on (a, c, d)", "rz3_terms(P[1], P[2], P[3], &l, &t);", "rz3_terms(P[0], P[2], P[3], &l, &t);"),
+    ("t5 net: ratio inverted", "return den > 0.0f ? x / den : 0.0f;", "return den > 0.0f ? y / den : 0.0f;"),
+    ("t5 net: first layer not rectified", "h1[j] = a > 0.0f ? a : 0.0f;", "h1[j] = a;"),
+    ("t5 net: W1 transposed", "a = a + w1[j * ORA_T5_NF + i] * f[i];", "a = a + w1[i * ORA_T5_NH + j] * f[i];"),
+    ("t5 net: W2 transposed", "a = a + w2[k * ORA_T5_NH + j] * h1[j];", "a = a + w2[j * ORA_T5_NH + k] * h1[j];"),
+    ("t5 net: b2 read from b1", "float a = b2[k];", "float a = b1[k];"),
+    ("t5 net: output bias dropped", "float z = b3[0];", "float z = 0.0f;"),
+    ("t5 net: decision z >= 0", "c1 = c2 = t5_mlp_logit(mlp, f) > 0.0f;", "c1 = c2 = t5_mlp_logit(mlp, f) >= 0.0f;"),
+    ("t5 net: replaces the radius condition", "c1 = c2 = t5_mlp_logit(mlp, f) > 0.0f;",
+     "c1 = c3 = t5_mlp_logit(mlp, f) > 0.0f;"),
 ]
 
 
