@@ -161,10 +161,11 @@ def check_pending(pending):
     """CPU leg: the oracle on every event whose GPU candidates were kept, field by field."""
     import oracle
     geoms, out = {}, {}
-    for label, k, tc, ev, modules in pending:
-        key = id(modules)
+    for label, k, tc, ev, modules, t5_weights in pending:
+        key = (id(modules), None if t5_weights is None else id(t5_weights))
         if key not in geoms:
             geoms[key] = oracle.Geometry(modules)
+            oracle.set_t5_mlp(geoms[key], t5_weights)
         r = out.setdefault(label, {"events": [], "identical": True,
                                    "compared": "every track-candidate field, pT and score bit for bit"})
         r["events"].append(k)
@@ -365,22 +366,42 @@ def time_device_batches(sess, dev_batches, n_ev, stream, flush, steps, warmup):
     return ms / steps, sess.stats()
 
 
-def sampled_candidates(sess, dev_batch, n_ev, events, picks, stream, label, modules, pending):
+def sampled_candidates(sess, dev_batch, n_ev, events, picks, stream, label, modules, pending, t5_weights=None):
     """One more run of a resident batch keeping its results: the picked events' candidates
-    are queued for the CPU leg, which checks them against the oracle."""
+    are queued for the CPU leg, which checks them against the oracle (with the same T5
+    network when ``t5_weights`` is set); returns the track-level rates of the whole batch."""
     sess.run_batch_device(dev_batch, stream.cuda_stream)
     _, ids = sess.batch_finish(n_ev, timeout_ms=120000, keep_results=True)
     for k in picks:
-        pending.append((label, int(k), sess.candidates(ids[k]), events[k], modules))
+        pending.append((label, int(k), sess.candidates(ids[k]), events[k], modules, t5_weights))
+    tcs = [sess.candidates(i) for i in ids]
     for i in ids:
         sess.release(i)
+    return track_rates(tcs, events)
+
+
+def track_rates(tcs, events):
+    """Efficiency, fake and duplicate rates (Sec. 3 definitions) of the events' candidates,
+    with and without the pLS-only candidates."""
+    import paper_2407_18231_gb300 as lst
+    from paper_2407_18231_gb300 import validation as V
+    c_all, c_ot = [], []
+    for tc, e in zip(tcs, events):
+        sel = (e.tracks["pt"] >= 0.9) & (np.abs(e.tracks["eta"]) < 2.4)
+        c_all.append(V.event_counts(tc, e.sim, e.pls_sim, len(e.tracks), sel))
+        c_ot.append(V.event_counts(tc[tc["type"] != lst.TC_PLS], e.sim, e.pls_sim, len(e.tracks), sel))
+    a, o = V.rates(c_all), V.rates(c_ot)
+    return {"efficiency": a["efficiency"], "fake_rate": a["fake_rate"], "duplicate_rate": a["duplicate_rate"],
+            "without_pls_only": {"efficiency": o["efficiency"], "fake_rate": o["fake_rate"],
+                                 "duplicate_rate": o["duplicate_rate"]}}
 
 
 def workload_legs(local, dev, flush, stream, pending):
     """The other workloads: the tiny event per launch, the 64-event barrel batch (tuned),
-    the 16-event high-occupancy batch with seeds and the PU200-like batch in the geometry
-    with tilted inner-barrel modules; a sampled event of each is queued for the CPU leg's
-    oracle check."""
+    the 16-event high-occupancy batch with seeds (curvature cuts, then the learned T5
+    selection), the headline batch with the learned T5 selection, and the PU200-like batch
+    in the geometry with tilted inner-barrel modules; a sampled event of each is queued for
+    the CPU leg's oracle check."""
     import lst_synth as S
     import paper_2407_18231_gb300 as lst
     from paper_2407_18231_gb300 import autotune
@@ -402,7 +423,7 @@ def workload_legs(local, dev, flush, stream, pending):
     out["tiny"] = {"us_per_event_p50": float(np.median(lat) * 1e6), "us_per_event_p99": float(np.percentile(lat, 99) * 1e6),
                    "events_per_s": float(1.0 / lat.mean()), "hits": ev.n_hits, "tcs": int(len(tc)),
                    "api": "lst_run_event + lst_get_candidates (host buffers)"}
-    pending.append(("tiny", 0, tc, ev, gb.modules))
+    pending.append(("tiny", 0, tc, ev, gb.modules, None))
     sess.close()
     # 64-event barrel batch (U{500..6000} tracks like tiny), launch configuration tuned on it
     evs = [S.make_event("batched", i) for i in range(64)]
@@ -418,17 +439,33 @@ def workload_legs(local, dev, flush, stream, pending):
                              "mean_hits_per_event": float(np.mean([e.n_hits for e in evs])),
                              "tuning": best["best"]}
     sess.close()
-    # 16-event high-occupancy batch with seeds
+    # 16-event high-occupancy batch with seeds, with the curvature cuts and with the learned
+    # T5 selection (the shipped network), and the headline batch with the network
     gf = S.geometry(False)
+    w = lst.load_t5_mlp()
     evs = [S.make_event("highocc", i) for i in range(16)]
-    sess = lst.Session(gf.modules, device=local)
     db = [to_device(evs, dev)]
-    ms, st = time_device_batches(sess, db, 16, stream, flush, 10, 3)
+    for label, weights in (("highocc_batch16", None), ("highocc_batch16_learned_t5", w)):
+        sess = lst.Session(gf.modules, device=local)
+        sess.set_t5_selection(weights)
+        ms, st = time_device_batches(sess, db, 16, stream, flush, 10, 3)
+        objs = sum(st[k] for k in OBJ_KEYS)
+        phys = sampled_candidates(sess, db[0][0], 16, evs, [3], stream, label, gf.modules, pending, weights)
+        out[label] = {"events_per_s": 16 / (ms * 1e-3), "objects_per_s": objs / (ms * 1e-3),
+                      "ms_per_batch": ms, "objects_per_batch": {k: st[k] for k in OBJ_KEYS},
+                      "mean_hits_per_event": float(np.mean([e.n_hits for e in evs])), "physics": phys,
+                      "t5_selection": "curvature cuts" if weights is None else "learned (shipped network)"}
+        sess.close()
+    evs = make_events(32, 0)
+    db = [to_device(evs, dev)]
+    sess = lst.Session(gf.modules, device=local)
+    sess.set_t5_selection(w)
+    ms, st = time_device_batches(sess, db, 32, stream, flush, 10, 3)
     objs = sum(st[k] for k in OBJ_KEYS)
-    sampled_candidates(sess, db[0][0], 16, evs, [3], stream, "highocc_batch16", gf.modules, pending)
-    out["highocc_batch16"] = {"events_per_s": 16 / (ms * 1e-3), "objects_per_s": objs / (ms * 1e-3),
-                              "ms_per_batch": ms, "objects_per_batch": {k: st[k] for k in OBJ_KEYS},
-                              "mean_hits_per_event": float(np.mean([e.n_hits for e in evs]))}
+    phys = sampled_candidates(sess, db[0][0], 32, evs, [5], stream, "pu200_batch32_learned_t5", gf.modules, pending, w)
+    out["pu200_batch32_learned_t5"] = {"events_per_s": 32 / (ms * 1e-3), "objects_per_s": objs / (ms * 1e-3),
+                                       "ms_per_batch": ms, "objects_per_batch": {k: st[k] for k in OBJ_KEYS},
+                                       "physics": phys, "t5_selection": "learned (shipped network)"}
     sess.close()
     # the headline workload in the geometry with tilted inner-barrel modules
     gt = S.geometry(False, True)

@@ -273,6 +273,30 @@ lst_status lst_get_stats(lst_ctx *ctx, lst_stats *out);
  * re-captures its graph.  Errors: INVALID_ARG (out of range, or a batch in flight). */
 lst_status lst_set_tuning(lst_ctx *ctx, const lst_config *cfg);
 
+/* Learned T5 selection (Sec. 1: the LST selections include machine-learning methods).  A
+ * network of two hidden layers of LST_T5_MLP_HIDDEN rectified units scores each T5
+ * candidate and replaces the two curvature-agreement conditions (inner/outer and
+ * bridge/full); the full-circle radius and the (a, c, e) r-z condition stay.  With d1, d2
+ * the two curvature differences, rhs1, rhs2 the cut tolerances they are held against, k_*
+ * the signed curvatures of the inner, outer, bridge and full triples and tol_* their
+ * errors, the LST_T5_MLP_INPUTS inputs are (x / (x + y), 0 when both are 0, written x:y):
+ *   f0 = d1 : rhs1,  f1 = d2 : rhs2,
+ *   f2 = d1 : (|k_in| + |k_out| + 1e-4),  f3 = d2 : (|k_br| + |k_full| + 1e-4),
+ *   f4 = (tol_in + tol_out) : (|k_in| + |k_out| + 1e-4),  f5 = |k_full| / k_max,
+ *   f6, f7 = r-z residual : tolerance of (a, c, e) and of (b, c, d);
+ * then h1 = relu(b1 + W1 f), h2 = relu(b2 + W2 h1), z = b3 + w3 . h2 in binary32, every sum
+ * from the bias in index order, and the candidate passes when z > 0.  weights (host,
+ * LST_T5_MLP_PARAMS floats) in this order: W1 (16 rows of 8, row j = unit j), b1 (16),
+ * W2 (16 rows of 16), b2 (16), w3 (16), b3 (1); the call copies them.  weights == NULL
+ * returns to the curvature cuts (the default).  T5 scores, curvatures and everything after
+ * the T5 step keep their definitions.  Applies to every later run on the context (its
+ * graphs are captured again); the package ships weights trained on synthetic events.
+ * Errors: INVALID_ARG (n != LST_T5_MLP_PARAMS, a weight not finite, a batch in flight). */
+#define LST_T5_MLP_INPUTS 8
+#define LST_T5_MLP_HIDDEN 16
+#define LST_T5_MLP_PARAMS 433
+lst_status lst_set_t5_selection(lst_ctx *ctx, const float *weights, uint32_t n);
+
 /* Per-kernel device time of the last run in profile mode (CUDA events on the launching
  * stream, summed over the kernel's launches in that run).  buf == NULL is a size query. */
 typedef struct lst_profile_entry {

@@ -93,7 +93,7 @@ EXPORTS = [
     "lst_batch_finish", "lst_get_candidates", "lst_get_objects", "lst_release_result", "lst_destroy",
     "lst_last_error", "lst_status_string", "lst_get_stats", "lst_get_profile", "lst_serve_replay",
     "lst_run_event_static", "lst_set_tuning", "lst_get_candidates_batch", "lst_submit_batch", "lst_collect_batch",
-    "lst_get_seeds",
+    "lst_get_seeds", "lst_set_t5_selection",
 ]
 
 T5_MLP_PARAMS = 433  # LST_T5_MLP_PARAMS
@@ -147,6 +147,7 @@ def load_library(path: str = LIB_PATH):
             "lst_submit_batch": (i32, [P, P, u32, C.POINTER(C.c_uint64)]),
             "lst_collect_batch": (i32, [P, C.c_uint64, u32, P, P]),
             "lst_get_seeds": (i32, [P, C.c_uint64, i32, P, u32, C.POINTER(u32)]),
+            "lst_set_t5_selection": (i32, [P, P, u32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -292,6 +293,16 @@ class Session:
     def set_tuning(self, block_size: int = 0, blocks_per_sm: int = 0, ls_list_cap: int = 0):
         cfg = lst_config(0, 0, 0, block_size, blocks_per_sm, 0, ls_list_cap)
         _check(self.ctx, load_library().lst_set_tuning(self.ctx, C.byref(cfg)))
+
+    def set_t5_selection(self, weights=None):
+        """Learned T5 selection with these LST_T5_MLP_PARAMS weights (lst_set_t5_selection),
+        or the curvature cuts when ``weights`` is None."""
+        L = load_library()
+        if weights is None:
+            _check(self.ctx, L.lst_set_t5_selection(self.ctx, None, 0))
+            return
+        w = np.ascontiguousarray(np.asarray(weights, np.float32).ravel())
+        _check(self.ctx, L.lst_set_t5_selection(self.ctx, w.ctypes.data, w.size))
 
     def profile(self) -> dict:
         """Per-kernel {name: (launches, ms)} of the last run (profile mode)."""

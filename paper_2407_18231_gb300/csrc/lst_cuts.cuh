@@ -110,17 +110,24 @@ __device__ __forceinline__ bool ls_select(const MethodConst& C, const PointTol& 
   return md_dir(C, a, au, cx, cy, clen) && md_dir(C, b, bu, cx, cy, clen);
 }
 
-// r-z straightness of p, q, s along the transverse chord (z linear in arc length).
-__device__ __forceinline__ bool rz3(const MethodConst& C, const PointTol& p, const PointTol& q, const PointTol& s) {
+// r-z straightness of p, q, s along the transverse chord (z linear in arc length): the
+// residual lhs and its tolerance; the triple is straight when lhs <= tol.
+__device__ __forceinline__ void rz3_terms(const MethodConst& C, const PointTol& p, const PointTol& q,
+                                          const PointTol& s, float& lhs, float& tol) {
   const float dxq = q.p.x - p.p.x, dyq = q.p.y - p.p.y;
   const float dxs = s.p.x - p.p.x, dys = s.p.y - p.p.y;
   const float dpq = sqrtf(dxq * dxq + dyq * dyq);
   const float dps = sqrtf(dxs * dxs + dys * dys);
   const float zqp = q.p.z - p.p.z;
   const float zsp = s.p.z - p.p.z;
-  const float lhs = fabsf(zqp * dps - zsp * dpq);
-  const float tol = C.KARC * dps * dps * fabsf(zsp) * dpq + p.t.x * fabsf(dps - dpq) + q.t.x * dps + s.t.x * dpq +
-                    (p.t.y + s.t.y) * fabsf(zqp) + (p.t.y + q.t.y) * fabsf(zsp);
+  lhs = fabsf(zqp * dps - zsp * dpq);
+  tol = C.KARC * dps * dps * fabsf(zsp) * dpq + p.t.x * fabsf(dps - dpq) + q.t.x * dps + s.t.x * dpq +
+        (p.t.y + s.t.y) * fabsf(zqp) + (p.t.y + q.t.y) * fabsf(zsp);
+}
+
+__device__ __forceinline__ bool rz3(const MethodConst& C, const PointTol& p, const PointTol& q, const PointTol& s) {
+  float lhs, tol;
+  rz3_terms(C, p, q, s, lhs, tol);
   return lhs <= tol;
 }
 
@@ -212,6 +219,84 @@ __device__ __forceinline__ bool t5_accept(const MethodConst& C, const PointTol& 
   if (!(d2 <= C.KAPPA * (fabsf(br.k) + fabsf(fu.k)) + br.tol + fu.tol + C.KAPPA0)) return false;
   if (!(fabsf(fu.k) <= C.KMAX + fu.tol)) return false;
   return rz3(C, A, Cc, E);
+}
+
+// ---- learned T5 selection ----
+// The paper's selections include machine-learning methods (Sec. 1); here a small network
+// can take the place of the two curvature-agreement conditions of a T5 while the radius
+// and (a, c, e) r-z conditions stay.  Inputs (all but f5 are x / (x + y) of non-negative
+// terms, in [0, 1)):
+//   f0 = d1 / (d1 + rhs1)   f1 = d2 / (d2 + rhs2)   (differences against the cut tolerances)
+//   f2 = d1 / (d1 + |kin| + |kout| + kappa0)   f3 = d2 / (d2 + |kbr| + |kfu| + kappa0)
+//   f4 = (tol_in + tol_out) / ((tol_in + tol_out) + |kin| + |kout| + kappa0)
+//   f5 = |kfu| / kmax
+//   f6, f7 = residual / (residual + tolerance) of the r-z straightness of (a, c, e), (b, c, d)
+// Network: h1 = relu(b1 + W1 f), h2 = relu(b2 + W2 h1), z = b3 + w3 . h2, every sum taken
+// from the bias in index order; the candidate passes when z > 0.  The weights travel as a
+// kernel parameter, so every read is a uniform constant-bank operand.
+constexpr int T5_NF = 8, T5_NH = 16;
+constexpr int T5_W1 = 0, T5_B1 = T5_W1 + T5_NH * T5_NF, T5_W2 = T5_B1 + T5_NH, T5_B2 = T5_W2 + T5_NH * T5_NH,
+              T5_W3 = T5_B2 + T5_NH, T5_B3 = T5_W3 + T5_NH, T5_NPARAM = T5_B3 + 1;
+struct T5Mlp {
+  float w[T5_NPARAM];
+};
+
+__device__ __forceinline__ float frac_of(float x, float y) {
+  const float den = x + y;
+  return den > 0.0f ? x / den : 0.0f;
+}
+
+__device__ __forceinline__ float t5_mlp_logit(const T5Mlp& M, const float (&f)[T5_NF]) {
+  float h1[T5_NH];
+#pragma unroll
+  for (int j = 0; j < T5_NH; j++) {
+    float a = M.w[T5_B1 + j];
+#pragma unroll
+    for (int i = 0; i < T5_NF; i++) a = a + M.w[T5_W1 + j * T5_NF + i] * f[i];
+    h1[j] = a > 0.0f ? a : 0.0f;
+  }
+  float z = M.w[T5_B3];
+#pragma unroll
+  for (int k = 0; k < T5_NH; k++) {
+    float a = M.w[T5_B2 + k];
+#pragma unroll
+    for (int j = 0; j < T5_NH; j++) a = a + M.w[T5_W2 + k * T5_NH + j] * h1[j];
+    z = z + M.w[T5_W3 + k] * (a > 0.0f ? a : 0.0f);
+  }
+  return z;
+}
+
+// t5_select with the network in place of the two curvature-agreement conditions (the
+// score and curvature are the same); the network runs only when the radius and r-z
+// conditions pass.
+__device__ __forceinline__ bool t5_select_mlp(const MethodConst& C, const T5Mlp& M, const PointTol& A,
+                                              const PointTol& B, const PointTol& Cc, const PointTol& D,
+                                              const PointTol& E, float& score, float& kfull) {
+  const Circle3 in = circle3(A, B, Cc);
+  const Circle3 out = circle3(Cc, D, E);
+  const Circle3 br = circle3(B, Cc, D);
+  const Circle3 fu = circle3(A, Cc, E);
+  const float d1 = fabsf(in.k - out.k);
+  const float d2 = fabsf(br.k - fu.k);
+  score = d1 + d2;
+  kfull = fu.k;
+  if (!(fabsf(fu.k) <= C.KMAX + fu.tol)) return false;
+  float l, t;
+  rz3_terms(C, A, Cc, E, l, t);
+  if (!(l <= t)) return false;
+  float f[T5_NF];
+  const float rhs1 = C.KAPPA * (fabsf(in.k) + fabsf(out.k)) + in.tol + out.tol + C.KAPPA0;
+  const float rhs2 = C.KAPPA * (fabsf(br.k) + fabsf(fu.k)) + br.tol + fu.tol + C.KAPPA0;
+  f[0] = frac_of(d1, rhs1);
+  f[1] = frac_of(d2, rhs2);
+  f[2] = frac_of(d1, fabsf(in.k) + fabsf(out.k) + C.KAPPA0);
+  f[3] = frac_of(d2, fabsf(br.k) + fabsf(fu.k) + C.KAPPA0);
+  f[4] = frac_of(in.tol + out.tol, fabsf(in.k) + fabsf(out.k) + C.KAPPA0);
+  f[5] = fabsf(fu.k) / C.KMAX;
+  f[6] = frac_of(l, t);
+  rz3_terms(C, B, Cc, D, l, t);
+  f[7] = frac_of(l, t);
+  return t5_mlp_logit(M, f) > 0.0f;
 }
 
 // ---- pLS helix ----

@@ -144,6 +144,7 @@ struct Launch {
   uint32_t block;  // threads per block
   uint32_t scan_grid;
   uint32_t ls_list_cap;  // LS: neighbour MDs staged per warp (0: per-MD join everywhere)
+  const T5Mlp* t5_mlp = nullptr;  // learned T5 selection (host copy, passed by value), null: the cuts
 };
 
 }  // namespace lst

@@ -125,6 +125,11 @@ struct Geometry {
   std::vector<float> row_phi0;
   std::vector<uint32_t> conn_off, conn;
   bool have_map = false;
+  // learned T5 selection (passed to the T5 kernels by value); sel_version counts changes so
+  // that every pipeline re-captures its graph after one
+  bool has_t5_mlp = false;
+  T5Mlp t5_mlp{};
+  uint32_t sel_version = 0;
   // device copies
   DevBuf d_modc, d_rnext, d_subdet, d_mod_e, d_mod_g, d_row_nphi, d_row_base, d_row_mods, d_conn_off, d_conn,
       d_row_fast, d_row_phi0;
@@ -527,6 +532,7 @@ struct Pipeline {
   // graph
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
+  uint32_t graph_sel_version = 0;  // the geometry's selection the graph was captured with
   int kernels = 0;
   // profile mode: one event after every kernel of an eager run
   bool profile = false;
@@ -891,6 +897,11 @@ struct Pipeline {
     if (cap.ev < dev_inputs.n_ev || cap.hits < dev_inputs.n_hits || cap.pls < dev_inputs.n_pls || cap.ev == 0)
       throw StatusError{LST_ERR_INVALID_ARG, "internal: pipeline launched before its buffers were sized"};
     *h_hdr = dev_inputs;
+    L.t5_mlp = geo->has_t5_mlp ? &geo->t5_mlp : nullptr;
+    if (graph_sel_version != geo->sel_version) {
+      graph_valid = false;
+      graph_sel_version = geo->sel_version;
+    }
     const GeoView G = geo->view();
     const BufView B = view();
     cudaStream_t st = on ? on : stream;
@@ -1593,6 +1604,24 @@ lst_status lst_set_tuning(lst_ctx* c, const lst_config* cfg) {
   });
 }
 
+static_assert(LST_T5_MLP_PARAMS == T5_NPARAM && LST_T5_MLP_INPUTS == T5_NF && LST_T5_MLP_HIDDEN == T5_NH,
+              "lst.h and the device network disagree");
+
+lst_status lst_set_t5_selection(lst_ctx* c, const float* weights, uint32_t n) {
+  if (!c) return LST_ERR_INVALID_ARG;
+  if (weights && n != (uint32_t)T5_NPARAM)
+    return fail(c, LST_ERR_INVALID_ARG, "the T5 network takes " + std::to_string(T5_NPARAM) + " weights");
+  if (weights)
+    for (uint32_t i = 0; i < n; i++)
+      if (!std::isfinite(weights[i])) return fail(c, LST_ERR_INVALID_ARG, "T5 network weight " + std::to_string(i) + " is not finite");
+  if (c->main.pending || c->slots[0].ticket || c->slots[1].ticket)
+    return fail(c, LST_ERR_INVALID_ARG, "a batch is still in flight");
+  c->geo.has_t5_mlp = weights != nullptr;
+  if (weights) memcpy(c->geo.t5_mlp.w, weights, sizeof(c->geo.t5_mlp.w));
+  c->geo.sel_version++;
+  return LST_OK;
+}
+
 lst_status lst_get_profile(lst_ctx* c, lst_profile_entry* buf, uint32_t cap, uint32_t* n_out) {
   if (!c || !n_out) return LST_ERR_INVALID_ARG;
   return guarded(c, [&]() -> lst_status {
@@ -1860,6 +1889,7 @@ bool ctx_views(lst_ctx* c, GeoView* g, MethodConst* m, Launch* l, int* device, b
   *g = c->geo.view();
   *m = c->main.C;
   *l = c->main.L;
+  l->t5_mlp = c->geo.has_t5_mlp ? &c->geo.t5_mlp : nullptr;
   *device = c->device;
   *have_map = c->geo.have_map;
   return true;

@@ -964,8 +964,34 @@ __global__ void __launch_bounds__(512) k_t3_fill(MethodConst C, GeoView G, BufVi
 // T3 t2), i.e. by (a, b, c, d, e), and t5_toff[t] gives the T5s built on t.  Both passes
 // take 32 consecutive T3s per warp and walk their concatenated candidates (count) or
 // passes (fill) 32 at a time, so the lanes stay busy whatever the candidate counts.
-__global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufView B) {
-  pdl_wait();
+// The selection is a policy: the curvature cuts, or the learned selection in their place.
+struct T5Cuts {
+  __device__ __forceinline__ bool accept(const MethodConst& C, const PointTol& A, const PointTol& B,
+                                         const PointTol& Cc, const PointTol& D, const PointTol& E) const {
+    return t5_accept(C, A, B, Cc, D, E);
+  }
+  __device__ __forceinline__ bool select(const MethodConst& C, const PointTol& A, const PointTol& B,
+                                         const PointTol& Cc, const PointTol& D, const PointTol& E, float& score,
+                                         float& kfull) const {
+    return t5_select(C, A, B, Cc, D, E, score, kfull);
+  }
+};
+struct T5Net {
+  const T5Mlp& M;
+  __device__ __forceinline__ bool accept(const MethodConst& C, const PointTol& A, const PointTol& B,
+                                         const PointTol& Cc, const PointTol& D, const PointTol& E) const {
+    float score, kfull;
+    return t5_select_mlp(C, M, A, B, Cc, D, E, score, kfull);
+  }
+  __device__ __forceinline__ bool select(const MethodConst& C, const PointTol& A, const PointTol& B,
+                                         const PointTol& Cc, const PointTol& D, const PointTol& E, float& score,
+                                         float& kfull) const {
+    return t5_select_mlp(C, M, A, B, Cc, D, E, score, kfull);
+  }
+};
+
+template <class Sel>
+__device__ __forceinline__ void t5_count_body(const MethodConst& C, const BufView& B, const Sel& sel) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_T3];
@@ -991,8 +1017,8 @@ __global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufV
       bool pass = false;
       if (cand < total) {
         const uint4 abc = B.t3_md4[grp * 32 + o];
-        pass = t5_accept(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, B.t3_b[t2]),
-                         md_point(B, B.t3_c[t2]));
+        pass = sel.accept(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, B.t3_b[t2]),
+                          md_point(B, B.t3_c[t2]));
       }
       const uint32_t bal = __ballot_sync(FULL, pass);
       const uint32_t lo = start > t0 ? min(start - t0, 32u) : 0u;
@@ -1009,6 +1035,17 @@ __global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufV
       B.t5_mask[t] = bits;
     }
   }
+}
+
+__global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
+  t5_count_body(C, B, T5Cuts{});
+}
+
+__global__ void __launch_bounds__(512) k_t5_count_mlp(MethodConst C, GeoView G, BufView B,
+                                                      const __grid_constant__ T5Mlp M) {
+  pdl_wait();
+  t5_count_body(C, B, T5Net{M});
 }
 
 __device__ __forceinline__ void t5_emit(const MethodConst& C, const BufView& B, uint32_t k, uint32_t a, uint32_t b,
@@ -1028,8 +1065,8 @@ __device__ __forceinline__ void t5_emit(const MethodConst& C, const BufView& B, 
 // and curvature of each are computed once), the others are tested again.  Also writes the
 // T5s starting at each MD a, t5_off[a] = t5_toff[t3_off[a]], and zeroes the per-MD counts
 // of the duplicate-removal lists (untouched until then).
-__global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufView B) {
-  pdl_wait();
+template <class Sel>
+__device__ __forceinline__ void t5_fill_body(const MethodConst& C, const BufView& B, const Sel& sel) {
   const Hdr* H = B.hdr;
   if (H->err) return;
   THREAD_LOOP(a, H->tot[T_MD] + 1) {
@@ -1072,8 +1109,8 @@ __global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufVi
         const uint4 abc = B.t3_md4[grp * 32 + o];
         const uint32_t d = B.t3_b[t2], e = B.t3_c[t2];
         float score, kfull;
-        t5_select(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, d), md_point(B, e),
-                  score, kfull);
+        sel.select(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, d), md_point(B, e),
+                   score, kfull);
         t5_emit(C, B, baseo + k, abc.x, abc.y, abc.z, d, e, score, kfull);
       }
     }
@@ -1093,7 +1130,7 @@ __global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufVi
         if (t0 + lane < ck) {
           d = B.t3_b[t2];
           e = B.t3_c[t2];
-          pass = t5_select(C, pa, pb, pc, md_point(B, d), md_point(B, e), score, kfull);
+          pass = sel.select(C, pa, pb, pc, md_point(B, d), md_point(B, e), score, kfull);
         }
         const uint32_t bal = __ballot_sync(FULL, pass);
         if (pass) t5_emit(C, B, basek + run + __popc(bal & lt), abc.x, abc.y, abc.z, d, e, score, kfull);
@@ -1101,6 +1138,17 @@ __global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufVi
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
+  t5_fill_body(C, B, T5Cuts{});
+}
+
+__global__ void __launch_bounds__(512) k_t5_fill_mlp(MethodConst C, GeoView G, BufView B,
+                                                     const __grid_constant__ T5Mlp M) {
+  pdl_wait();
+  t5_fill_body(C, B, T5Net{M});
 }
 
 // ------------------------------------------------------------------ pLS module lookup
@@ -2206,7 +2254,7 @@ cudaError_t preload_kernels() {
       (const void*)k_scan_apply_multi, (const void*)k_zero, (const void*)k_hits_count, (const void*)k_hits_scatter,
       (const void*)k_hits_sort, (const void*)k_md_count, (const void*)k_md_fill, (const void*)k_ls_fill,
       (const void*)k_ls_count, (const void*)k_t3_count, (const void*)k_t3_fill, (const void*)k_t5_count,
-      (const void*)k_t5_fill, (const void*)k_pls_prep, (const void*)k_pls_sort, (const void*)k_md_box,
+      (const void*)k_t5_fill, (const void*)k_t5_count_mlp, (const void*)k_t5_fill_mlp, (const void*)k_pls_prep, (const void*)k_pls_sort, (const void*)k_md_box,
       (const void*)k_pt3_first_anchor, (const void*)k_pt3_items, (const void*)k_pt3_count, (const void*)k_pt3_fill,
       (const void*)k_pt5_count, (const void*)k_pt5_fill, (const void*)k_csr_count, (const void*)k_csr_fill,
       (const void*)k_kill_pt5, (const void*)k_cross_pt3, (const void*)k_kill_pt3, (const void*)k_cross_t5,
@@ -2271,10 +2319,16 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   scan(B, L, s, B.t3_lcnt, B.t3_loff, &H->tot[T_LS], 1, T_T3, B.cap_t3, mk);
   launch(k_t3_fill, g, 256, 0, s, C, G, B);
   mk(12);
-  launch(k_t5_count, g, bs, 0, s, C, G, B);
+  if (L.t5_mlp)
+    launch(k_t5_count_mlp, g, bs, 0, s, C, G, B, *L.t5_mlp);
+  else
+    launch(k_t5_count, g, bs, 0, s, C, G, B);
   mk(13);
   scan(B, L, s, B.t5_tcnt, B.t5_toff, &H->tot[T_T3], 1, T_T5, B.cap_t5, mk);
-  launch(k_t5_fill, g, bs, 0, s, C, G, B);
+  if (L.t5_mlp)
+    launch(k_t5_fill_mlp, g, bs, 0, s, C, G, B, *L.t5_mlp);
+  else
+    launch(k_t5_fill, g, bs, 0, s, C, G, B);
   mk(14);
   if (side) {
     cudaStreamWaitEvent(s, side->join, 0);

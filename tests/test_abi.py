@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "lst.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lst_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lst_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_boundary():
@@ -52,3 +52,15 @@ def test_record_sizes_match_header():
     assert C.sizeof(lst.lst_config) == 16 * 4
     assert lst.OBJ_DTYPES[lst.OBJ_PLS].itemsize == 38 * 4
     assert np.dtype(lst.OBJ_DTYPES[lst.OBJ_T5]).itemsize == 32
+
+
+def test_t5_network_sizes_agree():
+    """lst.h's network constants, the binding's, the oracle's and the shipped weights agree."""
+    import oracle
+    text = open(HEADER).read()
+    c = {k: int(v) for k, v in re.findall(r"#define (LST_T5_MLP_[A-Z]+) (\d+)", text)}
+    nf, nh = c["LST_T5_MLP_INPUTS"], c["LST_T5_MLP_HIDDEN"]
+    assert c["LST_T5_MLP_PARAMS"] == nh * nf + nh + nh * nh + nh + nh + 1
+    assert (nf, nh, c["LST_T5_MLP_PARAMS"]) == (oracle.T5_NF, oracle.T5_NH, oracle.T5_NPARAM)
+    assert lst.T5_MLP_PARAMS == c["LST_T5_MLP_PARAMS"] == lst.load_t5_mlp().size
+    assert lst.load_library().lst_set_t5_selection(None, None, 0) == -1  # null context, no CUDA call

@@ -117,3 +117,32 @@ def test_static_entry_point_rejects_oversize():
     got = np.frombuffer(out[: n.value * lst.TC_DTYPE.itemsize].cpu().numpy().tobytes(), lst.TC_DTYPE)
     assert got.tobytes() == ref.tobytes()
     sess.close()
+
+
+def test_static_entry_point_follows_the_t5_selection():
+    """With the learned T5 selection set on the context the allocation-free path runs it too
+    (oracle with the same weights), and after it is cleared, the cuts again."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    L = lst.load_library()
+    dev = torch.device("cuda:0")
+    geom = S.geometry(False)
+    sess = lst.Session(geom.modules)
+    w = lst.load_t5_mlp()
+    og = oracle.Geometry(geom.modules)
+    ev = S.make_event("pu200", 26, n_tracks=260, with_pls=True)
+    desc, keep = _device_event(torch, ev, dev)
+    cap = 4096
+    out = torch.zeros(cap * lst.TC_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    for weights in (w, None):
+        sess.set_t5_selection(weights)
+        oracle.set_t5_mlp(og, weights)
+        ora = oracle.run(og, ev)
+        n = C.c_uint32(0)
+        assert L.lst_run_event_static(sess.ctx, C.byref(desc), out.data_ptr(), cap, C.byref(n), None) == 0
+        tc = np.frombuffer(out[: n.value * lst.TC_DTYPE.itemsize].cpu().numpy().tobytes(), lst.TC_DTYPE)
+        assert len(tc) == len(ora["tc_type"]) > 10
+        assert np.array_equal(tc["type"], ora["tc_type"]) and np.array_equal(tc["obj"], ora["tc_obj"])
+        assert np.array_equal(tc["ot"], ora["tc_ot"]) and np.array_equal(tc["pix"], ora["tc_pix"])
+        assert tc["score"].tobytes() == ora["tc_score"].tobytes()
+    sess.close()
