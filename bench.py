@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--legs", type=int, default=1, help="tiny / barrel-batch / high-occupancy legs (0 = skip)")
     ap.add_argument("--parity", type=int, default=3, help="events of a timed batch checked against the oracle")
     ap.add_argument("--tune", type=int, default=1, help="autotune the launch configuration first (1) or not (0)")
+    ap.add_argument("--workload", default="pu200", choices=["pu200", "highocc"],
+                    help="events of the timed batches (profiling: highocc = 12000 tracks, 30 %% noise)")
+    ap.add_argument("--t5", default="cuts", choices=["cuts", "learned"],
+                    help="T5 selection of the timed and end-to-end sessions (learned: the shipped network)")
     ap.add_argument("--config", default="", help="fixed launch configuration block_size,blocks_per_sm,ls_list_cap "
                                                  "(skips the autotuner)")
     return ap.parse_args()
@@ -78,9 +82,9 @@ def dist_env():
     return ws, rank, local
 
 
-def make_events(n, first):
+def make_events(n, first, workload="pu200"):
     import lst_synth as S
-    return [S.make_event("pu200", first + i, with_pls=True) for i in range(n)]
+    return [S.make_event(workload, first + i, with_pls=True) for i in range(n)]
 
 
 # ---------------------------------------------------------------- clocks
@@ -562,8 +566,9 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
 
     B, P = args.batch, args.pool
-    events = make_events(B * P, 100_000 * rank)
+    events = make_events(B * P, 100_000 * rank, args.workload)
     batches = [events[i * B:(i + 1) * B] for i in range(P)]
+    t5_weights = lst.load_t5_mlp() if args.t5 == "learned" else None
     dev_batches = [to_device(b, dev) for b in batches]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     tuning = {}
@@ -575,6 +580,7 @@ def main():
         space = {"block_size": [128, 256], "blocks_per_sm": [4, 8, 12], "ls_list_cap": [128, 512]}
         tuning = autotune.tune(geom.modules, events[:B], device=local, space=space, reps=5)["best"]
     sess = lst.Session(geom.modules, device=local, **tuning)
+    sess.set_t5_selection(t5_weights)
     # the library runs on this stream, so events recorded on it bracket its kernels
     stream = torch.cuda.Stream(dev)
     assert stream.cuda_stream != 0
@@ -636,12 +642,14 @@ def main():
     pending = []
     if args.parity:
         picks = sorted(set(np.linspace(0, B - 1, args.parity).astype(int).tolist()))
-        sampled_candidates(sess, dev_batches[0][0], B, batches[0], picks, stream, "headline", geom.modules, pending)
+        sampled_candidates(sess, dev_batches[0][0], B, batches[0], picks, stream, "headline", geom.modules, pending,
+                           t5_weights)
 
     # ---- end to end: host buffers through the asynchronous batch API (lst_submit_batch /
     # lst_collect_batch): one batch in flight while the next is packed and uploaded; every
     # step's H2D copy and the read-back of its candidates fall inside the timed region
     sess_h = lst.Session(geom.modules, device=local, **tuning)
+    sess_h.set_t5_selection(t5_weights)
     for k in range(max(args.warmup, P) + 1):  # both slots: buffers sized, graphs captured
         t_w = sess_h.submit_batch(batches[k % P])
         for i in sess_h.collect_batch(sess_h.submit_batch(batches[(k + 1) % P])) + sess_h.collect_batch(t_w):
@@ -816,7 +824,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
         "warmup": n_warm, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events_per_step": B, "mean_hits_per_event": float(np.mean([e.n_hits for e in events])),
+        "config": {"workload": WORKLOAD if args.workload == "pu200" else "highocc_12000trk_30pct_noise_with_pixel_seeds",
+                   "t5_selection": "curvature cuts" if t5_weights is None else "learned (shipped network)",
+                   "events_per_step": B, "mean_hits_per_event": float(np.mean([e.n_hits for e in events])),
                    "mean_pls_per_event": float(np.mean([e.n_pls for e in events])),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "mode": "batched persistent kernels, CUDA graph replay",

@@ -233,45 +233,76 @@ __device__ __forceinline__ bool t5_accept(const MethodConst& C, const PointTol& 
 //   f6, f7 = residual / (residual + tolerance) of the r-z straightness of (a, c, e), (b, c, d)
 // Network: h1 = relu(b1 + W1 f), h2 = relu(b2 + W2 h1), z = b3 + w3 . h2, every sum taken
 // from the bias in index order; the candidate passes when z > 0.  The weights travel as a
-// kernel parameter, so every read is a uniform constant-bank operand.
+// kernel parameter (by value, so a captured graph carries them) and each block stages them
+// in shared memory, W2 transposed, where every read is a broadcast.
 constexpr int T5_NF = 8, T5_NH = 16;
 constexpr int T5_W1 = 0, T5_B1 = T5_W1 + T5_NH * T5_NF, T5_W2 = T5_B1 + T5_NH, T5_B2 = T5_W2 + T5_NH * T5_NH,
               T5_W3 = T5_B2 + T5_NH, T5_B3 = T5_W3 + T5_NH, T5_NPARAM = T5_B3 + 1;
+constexpr int T5_SMEM_FLOATS = (T5_NPARAM + 3) & ~3;  // staged copy, float4-aligned sections
 struct T5Mlp {
   float w[T5_NPARAM];
 };
+
+// Copies the weights into shared memory Ws (T5_SMEM_FLOATS, 16-byte aligned) with W2
+// transposed (Ws[T5_W2 + j * T5_NH + k] = W2[k][j]); the caller synchronises the block.
+__device__ __forceinline__ void t5_mlp_stage(const T5Mlp& M, float* Ws) {
+  for (int i = threadIdx.x; i < T5_NPARAM; i += blockDim.x) {
+    int d = i;
+    if (i >= T5_W2 && i < T5_B2) {
+      const int k = (i - T5_W2) / T5_NH, j = (i - T5_W2) % T5_NH;
+      d = T5_W2 + j * T5_NH + k;
+    }
+    Ws[d] = M.w[i];
+  }
+}
 
 __device__ __forceinline__ float frac_of(float x, float y) {
   const float den = x + y;
   return den > 0.0f ? x / den : 0.0f;
 }
 
-__device__ __forceinline__ float t5_mlp_logit(const T5Mlp& M, const float (&f)[T5_NF]) {
-  float h1[T5_NH];
+// The network on staged weights.  The loop runs over the first layer's units j; unit j's
+// output is added, as term j, into all second-layer sums at once, so each sum still runs
+// from its bias through j = 0, 1, ... in order, and the loop body stays short.
+__device__ __forceinline__ float t5_mlp_logit(const float* Ws, const float (&f)[T5_NF]) {
+  float a2[T5_NH];
 #pragma unroll
+  for (int k = 0; k < T5_NH; k++) a2[k] = Ws[T5_B2 + k];
+#pragma unroll 1
   for (int j = 0; j < T5_NH; j++) {
-    float a = M.w[T5_B1 + j];
+    const float4 wa = *reinterpret_cast<const float4*>(Ws + T5_W1 + j * T5_NF);
+    const float4 wb = *reinterpret_cast<const float4*>(Ws + T5_W1 + j * T5_NF + 4);
+    float a = Ws[T5_B1 + j];
+    a = a + wa.x * f[0];
+    a = a + wa.y * f[1];
+    a = a + wa.z * f[2];
+    a = a + wa.w * f[3];
+    a = a + wb.x * f[4];
+    a = a + wb.y * f[5];
+    a = a + wb.z * f[6];
+    a = a + wb.w * f[7];
+    const float h = a > 0.0f ? a : 0.0f;
+    const float4* w2 = reinterpret_cast<const float4*>(Ws + T5_W2 + j * T5_NH);
 #pragma unroll
-    for (int i = 0; i < T5_NF; i++) a = a + M.w[T5_W1 + j * T5_NF + i] * f[i];
-    h1[j] = a > 0.0f ? a : 0.0f;
+    for (int q = 0; q < T5_NH / 4; q++) {
+      const float4 v = w2[q];
+      a2[4 * q] = a2[4 * q] + v.x * h;
+      a2[4 * q + 1] = a2[4 * q + 1] + v.y * h;
+      a2[4 * q + 2] = a2[4 * q + 2] + v.z * h;
+      a2[4 * q + 3] = a2[4 * q + 3] + v.w * h;
+    }
   }
-  float z = M.w[T5_B3];
+  float z = Ws[T5_B3];
 #pragma unroll
-  for (int k = 0; k < T5_NH; k++) {
-    float a = M.w[T5_B2 + k];
-#pragma unroll
-    for (int j = 0; j < T5_NH; j++) a = a + M.w[T5_W2 + k * T5_NH + j] * h1[j];
-    z = z + M.w[T5_W3 + k] * (a > 0.0f ? a : 0.0f);
-  }
+  for (int k = 0; k < T5_NH; k++) z = z + Ws[T5_W3 + k] * (a2[k] > 0.0f ? a2[k] : 0.0f);
   return z;
 }
 
-// t5_select with the network in place of the two curvature-agreement conditions (the
-// score and curvature are the same); the network runs only when the radius and r-z
-// conditions pass.
-__device__ __forceinline__ bool t5_select_mlp(const MethodConst& C, const T5Mlp& M, const PointTol& A,
-                                              const PointTol& B, const PointTol& Cc, const PointTol& D,
-                                              const PointTol& E, float& score, float& kfull) {
+// The radius and (a, c, e) r-z conditions of a T5 candidate and, when both pass, the
+// network's inputs f; score and curvature as in t5_select.
+__device__ __forceinline__ bool t5_mlp_inputs(const MethodConst& C, const PointTol& A, const PointTol& B,
+                                              const PointTol& Cc, const PointTol& D, const PointTol& E,
+                                              float (&f)[T5_NF], float& score, float& kfull) {
   const Circle3 in = circle3(A, B, Cc);
   const Circle3 out = circle3(Cc, D, E);
   const Circle3 br = circle3(B, Cc, D);
@@ -284,7 +315,6 @@ __device__ __forceinline__ bool t5_select_mlp(const MethodConst& C, const T5Mlp&
   float l, t;
   rz3_terms(C, A, Cc, E, l, t);
   if (!(l <= t)) return false;
-  float f[T5_NF];
   const float rhs1 = C.KAPPA * (fabsf(in.k) + fabsf(out.k)) + in.tol + out.tol + C.KAPPA0;
   const float rhs2 = C.KAPPA * (fabsf(br.k) + fabsf(fu.k)) + br.tol + fu.tol + C.KAPPA0;
   f[0] = frac_of(d1, rhs1);
@@ -296,7 +326,29 @@ __device__ __forceinline__ bool t5_select_mlp(const MethodConst& C, const T5Mlp&
   f[6] = frac_of(l, t);
   rz3_terms(C, B, Cc, D, l, t);
   f[7] = frac_of(l, t);
-  return t5_mlp_logit(M, f) > 0.0f;
+  return true;
+}
+
+// t5_select with the network in place of the two curvature-agreement conditions (the
+// score and curvature are the same); the network runs only when the radius and r-z
+// conditions pass.
+__device__ __forceinline__ bool t5_select_mlp(const MethodConst& C, const float* Ws, const PointTol& A,
+                                              const PointTol& B, const PointTol& Cc, const PointTol& D,
+                                              const PointTol& E, float& score, float& kfull) {
+  float f[T5_NF];
+  if (!t5_mlp_inputs(C, A, B, Cc, D, E, f, score, kfull)) return false;
+  return t5_mlp_logit(Ws, f) > 0.0f;
+}
+
+// Score and full-circle curvature of a T5 whose decision is already known.
+__device__ __forceinline__ void t5_measure(const PointTol& A, const PointTol& B, const PointTol& Cc,
+                                           const PointTol& D, const PointTol& E, float& score, float& kfull) {
+  const Circle3 in = circle3(A, B, Cc);
+  const Circle3 out = circle3(Cc, D, E);
+  const Circle3 br = circle3(B, Cc, D);
+  const Circle3 fu = circle3(A, Cc, E);
+  score = fabsf(in.k - out.k) + fabsf(br.k - fu.k);
+  kfull = fu.k;
 }
 
 // ---- pLS helix ----

@@ -964,34 +964,37 @@ __global__ void __launch_bounds__(512) k_t3_fill(MethodConst C, GeoView G, BufVi
 // T3 t2), i.e. by (a, b, c, d, e), and t5_toff[t] gives the T5s built on t.  Both passes
 // take 32 consecutive T3s per warp and walk their concatenated candidates (count) or
 // passes (fill) 32 at a time, so the lanes stay busy whatever the candidate counts.
-// The selection is a policy: the curvature cuts, or the learned selection in their place.
+// The fill pass is a template over the selection (the curvature cuts, or the learned
+// selection in their place: select decides and measures, measure only measures); the count
+// pass with the learned selection is a kernel of its own, k_t5_count_mlp.
 struct T5Cuts {
-  __device__ __forceinline__ bool accept(const MethodConst& C, const PointTol& A, const PointTol& B,
-                                         const PointTol& Cc, const PointTol& D, const PointTol& E) const {
-    return t5_accept(C, A, B, Cc, D, E);
-  }
   __device__ __forceinline__ bool select(const MethodConst& C, const PointTol& A, const PointTol& B,
                                          const PointTol& Cc, const PointTol& D, const PointTol& E, float& score,
                                          float& kfull) const {
     return t5_select(C, A, B, Cc, D, E, score, kfull);
   }
+  __device__ __forceinline__ void measure(const MethodConst& C, const PointTol& A, const PointTol& B,
+                                          const PointTol& Cc, const PointTol& D, const PointTol& E, float& score,
+                                          float& kfull) const {
+    t5_select(C, A, B, Cc, D, E, score, kfull);
+  }
 };
 struct T5Net {
-  const T5Mlp& M;
-  __device__ __forceinline__ bool accept(const MethodConst& C, const PointTol& A, const PointTol& B,
-                                         const PointTol& Cc, const PointTol& D, const PointTol& E) const {
-    float score, kfull;
-    return t5_select_mlp(C, M, A, B, Cc, D, E, score, kfull);
-  }
+  const float* Ws;  // staged weights (t5_mlp_stage)
   __device__ __forceinline__ bool select(const MethodConst& C, const PointTol& A, const PointTol& B,
                                          const PointTol& Cc, const PointTol& D, const PointTol& E, float& score,
                                          float& kfull) const {
-    return t5_select_mlp(C, M, A, B, Cc, D, E, score, kfull);
+    return t5_select_mlp(C, Ws, A, B, Cc, D, E, score, kfull);
+  }
+  __device__ __forceinline__ void measure(const MethodConst& C, const PointTol& A, const PointTol& B,
+                                          const PointTol& Cc, const PointTol& D, const PointTol& E, float& score,
+                                          float& kfull) const {
+    t5_measure(A, B, Cc, D, E, score, kfull);
   }
 };
 
-template <class Sel>
-__device__ __forceinline__ void t5_count_body(const MethodConst& C, const BufView& B, const Sel& sel) {
+__global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufView B) {
+  pdl_wait();
   const Hdr* H = B.hdr;
   if (H->err) return;
   const uint32_t n = H->tot[T_T3];
@@ -1017,8 +1020,8 @@ __device__ __forceinline__ void t5_count_body(const MethodConst& C, const BufVie
       bool pass = false;
       if (cand < total) {
         const uint4 abc = B.t3_md4[grp * 32 + o];
-        pass = sel.accept(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, B.t3_b[t2]),
-                          md_point(B, B.t3_c[t2]));
+        pass = t5_accept(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, B.t3_b[t2]),
+                         md_point(B, B.t3_c[t2]));
       }
       const uint32_t bal = __ballot_sync(FULL, pass);
       const uint32_t lo = start > t0 ? min(start - t0, 32u) : 0u;
@@ -1037,15 +1040,104 @@ __device__ __forceinline__ void t5_count_body(const MethodConst& C, const BufVie
   }
 }
 
-__global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufView B) {
-  pdl_wait();
-  t5_count_body(C, B, T5Cuts{});
+
+// Count pass with the learned selection.  Only the candidates passing the radius and r-z
+// conditions (typically a third of a warp's lanes) need the network, so their inputs go into
+// a per-warp queue in shared memory (T5_QCAP entries: inputs, owner lane, position among the
+// owner's candidates) and the network runs 32 queued candidates at a time on full warps;
+// passes are tallied per owner in shared memory (count, bits of the first 32 candidates).
+// Dynamic shared memory: the staged weights, then one queue per warp.
+constexpr uint32_t T5_QCAP = 64;  // a chunk adds at most 32 to fewer than 32 waiting
+constexpr size_t T5_QWORDS = (T5_NF + 1) * T5_QCAP + 2 * 32;  // per warp: inputs, tags, run, bits
+size_t t5_count_mlp_smem(uint32_t block) {
+  return (T5_SMEM_FLOATS + (block / 32) * T5_QWORDS) * sizeof(uint32_t);
+}
+
+__device__ __forceinline__ void t5_net_drain(const float* Ws, float* qf, const uint32_t* qtag, uint32_t* srun,
+                                             uint32_t* sbits, uint32_t head, uint32_t m, uint32_t lane) {
+  if (lane < m) {
+    const uint32_t slot = (head + lane) & (T5_QCAP - 1);
+    float f[T5_NF];
+#pragma unroll
+    for (int i = 0; i < T5_NF; i++) f[i] = qf[i * T5_QCAP + slot];
+    if (t5_mlp_logit(Ws, f) > 0.0f) {
+      const uint32_t tag = qtag[slot], o = tag & 31u, k = tag >> 5;
+      atomicAdd(&srun[o], 1u);
+      if (k < 32u) atomicOr(&sbits[o], 1u << k);
+    }
+  }
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(512) k_t5_count_mlp(MethodConst C, GeoView G, BufView B,
                                                       const __grid_constant__ T5Mlp M) {
+  extern __shared__ __align__(16) uint32_t t5q[];
+  float* Ws = reinterpret_cast<float*>(t5q);
+  t5_mlp_stage(M, Ws);
+  __syncthreads();
   pdl_wait();
-  t5_count_body(C, B, T5Net{M});
+  const Hdr* H = B.hdr;
+  if (H->err) return;
+  const uint32_t n = H->tot[T_T3];
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t* wq = t5q + T5_SMEM_FLOATS + (threadIdx.x >> 5) * T5_QWORDS;
+  float* qf = reinterpret_cast<float*>(wq);
+  uint32_t* qtag = wq + T5_NF * T5_QCAP;
+  uint32_t* srun = qtag + T5_QCAP;
+  uint32_t* sbits = srun + 32;
+  WARP_LOOP(grp, (n + 31) >> 5) {
+    const uint32_t t = grp * 32 + lane;
+    const bool valid = t < n;
+    uint32_t s0 = 0, c = 0;
+    if (valid) {
+      const uint32_t m = B.t3_c[t];
+      s0 = B.t3_off[m];
+      c = B.t3_off[m + 1] - s0;
+    }
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t start = incl - c;
+    srun[lane] = 0u;
+    sbits[lane] = 0u;
+    __syncwarp();
+    uint32_t head = 0, queued = 0;  // warp-uniform
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t cand = t0 + lane;
+      const uint32_t cc = cand < total ? cand : total - 1;
+      const uint32_t o = owner_lane(incl, cc);
+      const uint32_t so = __shfl_sync(FULL, start, o);
+      const uint32_t t2 = __shfl_sync(FULL, s0, o) + (cc - so);
+      bool need = false;
+      float f[T5_NF];
+      if (cand < total) {
+        const uint4 abc = B.t3_md4[grp * 32 + o];
+        float score, kfull;
+        need = t5_mlp_inputs(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, B.t3_b[t2]),
+                             md_point(B, B.t3_c[t2]), f, score, kfull);
+      }
+      const uint32_t bal = __ballot_sync(FULL, need);
+      if (need) {
+        const uint32_t slot = (head + queued + __popc(bal & lt)) & (T5_QCAP - 1);
+#pragma unroll
+        for (int i = 0; i < T5_NF; i++) qf[i * T5_QCAP + slot] = f[i];
+        qtag[slot] = o | ((cand - so) << 5);
+      }
+      queued += __popc(bal);
+      __syncwarp();
+      if (queued >= 32u) {
+        t5_net_drain(Ws, qf, qtag, srun, sbits, head, 32u, lane);
+        head = (head + 32u) & (T5_QCAP - 1);
+        queued -= 32u;
+      }
+    }
+    if (queued) t5_net_drain(Ws, qf, qtag, srun, sbits, head, queued, lane);
+    if (valid) {
+      B.t5_tcnt[t] = srun[lane];
+      B.t5_mask[t] = sbits[lane];
+    }
+    __syncwarp();
+  }
 }
 
 __device__ __forceinline__ void t5_emit(const MethodConst& C, const BufView& B, uint32_t k, uint32_t a, uint32_t b,
@@ -1109,8 +1201,8 @@ __device__ __forceinline__ void t5_fill_body(const MethodConst& C, const BufView
         const uint4 abc = B.t3_md4[grp * 32 + o];
         const uint32_t d = B.t3_b[t2], e = B.t3_c[t2];
         float score, kfull;
-        sel.select(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, d), md_point(B, e),
-                   score, kfull);
+        sel.measure(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, d), md_point(B, e),
+                    score, kfull);
         t5_emit(C, B, baseo + k, abc.x, abc.y, abc.z, d, e, score, kfull);
       }
     }
@@ -1147,8 +1239,11 @@ __global__ void __launch_bounds__(512) k_t5_fill(MethodConst C, GeoView G, BufVi
 
 __global__ void __launch_bounds__(512) k_t5_fill_mlp(MethodConst C, GeoView G, BufView B,
                                                      const __grid_constant__ T5Mlp M) {
+  __shared__ __align__(16) float Ws[T5_SMEM_FLOATS];
+  t5_mlp_stage(M, Ws);
+  __syncthreads();
   pdl_wait();
-  t5_fill_body(C, B, T5Net{M});
+  t5_fill_body(C, B, T5Net{Ws});
 }
 
 // ------------------------------------------------------------------ pLS module lookup
@@ -2320,7 +2415,7 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   launch(k_t3_fill, g, 256, 0, s, C, G, B);
   mk(12);
   if (L.t5_mlp)
-    launch(k_t5_count_mlp, g, bs, 0, s, C, G, B, *L.t5_mlp);
+    launch(k_t5_count_mlp, g, bs, t5_count_mlp_smem(bs), s, C, G, B, *L.t5_mlp);
   else
     launch(k_t5_count, g, bs, 0, s, C, G, B);
   mk(13);
