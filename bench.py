@@ -432,7 +432,7 @@ def workload_legs(local, dev, flush, stream, pending):
     # 64-event barrel batch (U{500..6000} tracks like tiny), launch configuration tuned on it
     evs = [S.make_event("batched", i) for i in range(64)]
     best = autotune.tune(gb.modules, evs, device=local, reps=3,
-                         space={"block_size": [128, 256, 512], "blocks_per_sm": [4, 8], "ls_list_cap": [128, 512]})
+                         space={"block_size": [128, 256, 512], "blocks_per_sm": [4, 8], "ls_list_cap": [512, 1024]})
     sess = lst.Session(gb.modules, device=local, **best["best"])
     db = [to_device(evs, dev)]
     ms, st = time_device_batches(sess, db, 64, stream, flush, 10, 3)
@@ -577,7 +577,7 @@ def main():
         tuning = {"block_size": bs, "blocks_per_sm": bps, "ls_list_cap": cap}
     elif args.tune:
         from paper_2407_18231_gb300 import autotune
-        space = {"block_size": [128, 256], "blocks_per_sm": [4, 8, 12], "ls_list_cap": [128, 512]}
+        space = {"block_size": [128, 256], "blocks_per_sm": [4, 8, 12], "ls_list_cap": [512, 1024]}
         tuning = autotune.tune(geom.modules, events[:B], device=local, space=space, reps=5)["best"]
     sess = lst.Session(geom.modules, device=local, **tuning)
     sess.set_t5_selection(t5_weights)

@@ -9,6 +9,7 @@ namespace lst {
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr int NSURF = 16;
 constexpr int MAX_CAND = 36;
+constexpr uint32_t LS_LIST_MAX = 2048;  // longest neighbour list the LS count pass stages
 constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, kept per pLS
 // pT3 items of one pLS: its kept MDs, or (more passing MDs) its candidate modules
 constexpr uint32_t PLS_ITEMS = PLS_MD_CAP > (uint32_t)MAX_CAND ? PLS_MD_CAP : (uint32_t)MAX_CAND;
@@ -37,7 +38,8 @@ struct Hdr {
   uint32_t n_ev, n_hits, n_pls, pad;
   uint32_t tot[N_TOTALS];
   uint32_t err;
-  uint32_t pad2[3];
+  uint32_t ls_over;  // LS count pass: units whose neighbour list exceeded the launch's list cap
+  uint32_t pad2[2];
   uint32_t mask_used[8];  // LS partner-list arena: [1] words handed out in pieces (may pass the
                           // arena's end), [2] words of the lists that found it exhausted
   unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)

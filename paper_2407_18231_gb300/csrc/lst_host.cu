@@ -514,6 +514,7 @@ struct Pipeline {
   DevBuf tc_ev_off, tc, scan_part, scan_part2, mask, mask_off;
   uint32_t cap_mask = 0;
   uint64_t byte_cap = 0;  // 0: none; otherwise learn_mask keeps dev_bytes within it
+  bool auto_list_cap = true;  // the LS list cap is the library's choice (learn may raise it)
   // host staging (pinned)
   Hdr* h_hdr = nullptr;        // header to upload
   Hdr* h_hdr_out = nullptr;    // header read back
@@ -595,7 +596,9 @@ struct Pipeline {
     const uint32_t bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
     L.block = cfg.block_size ? cfg.block_size : 256;
     // a multiple of 4: the LS kernel's per-warp shared-memory slices hold float4s
-    L.ls_list_cap = cfg.ls_list_cap == 0 ? 512u : (cfg.ls_list_cap == 1 ? 0u : std::min<uint32_t>(cfg.ls_list_cap, 512u) & ~3u);
+    L.ls_list_cap = cfg.ls_list_cap == 0 ? 1024u
+                                         : (cfg.ls_list_cap == 1 ? 0u : std::min(cfg.ls_list_cap, LS_LIST_MAX) & ~3u);
+    auto_list_cap = cfg.ls_list_cap == 0;
     L.grid = (uint32_t)n_sm * bps;
     graph_valid = false;
   }
@@ -826,6 +829,13 @@ struct Pipeline {
   // Learn sizes from a finished run so that the next estimate is large enough.
   void learn(const Hdr& h) {
     learn_mask(h);
+    // a neighbour list longer than the LS pass's shared-memory list sent its module to the
+    // per-MD join: later runs get the longest list (when the cap is the library's choice;
+    // a 1024-entry list keeps more blocks resident, so it stays the start value)
+    if (h.ls_over && auto_list_cap && L.ls_list_cap && L.ls_list_cap < LS_LIST_MAX) {
+      L.ls_list_cap = LS_LIST_MAX;
+      graph_valid = false;
+    }
     if (h.n_hits) {
       r_md = std::max(r_md, (double)h.tot[T_MD] / h.n_hits);
       r_ls = std::max(r_ls, (double)h.tot[T_LS] / h.n_hits);

@@ -715,13 +715,19 @@ __global__ void __launch_bounds__(512) k_ls_fill(MethodConst C, GeoView G, BufVi
   }
 }
 
-constexpr uint32_t LS_LIST_CAP = 512;  // flattened neighbour MDs per warp in shared memory
+// Flattened neighbour MDs per warp in shared memory: the launch's list_cap, at most
+// LS_LIST_MAX = 64 x 32 (two pass-bit words per lane).  Every list of a PU200-like event fits
+// in 512; high-occupancy events reach about 1100, 1500 with tilted modules.
+static_assert(LS_LIST_MAX <= 64 * 32, "two pass-bit words per lane");
 constexpr uint32_t LS_ANCHORS = 8;     // MDs of a module tested per walk over its list
 constexpr uint32_t LS_RING = 64;       // ring of queued (list position, anchor) entries (> 31 + 32)
 // per warp after the list: the ring, one pass bit per list position for each anchor, and
 // the anchors (lower hit and direction terms: two float4 each; the tolerances are the
-// module's, the same for every anchor)
-constexpr uint32_t LS_EXTRA_WORDS = LS_RING + LS_ANCHORS * LS_LIST_CAP / 32 + LS_ANCHORS * 8;
+// module's, the same for every anchor); list_cap is a multiple of 4, so the anchors' float4s
+// stay 16-byte aligned
+__host__ __device__ constexpr uint32_t ls_warp_words(uint32_t list_cap) {
+  return list_cap + LS_RING + LS_ANCHORS * ((list_cap + 31) / 32) + LS_ANCHORS * 8;
+}
 
 // LS count pass.  Unit = (event, module A).  The warp writes the indices of all MDs on the
 // modules connected to A into a shared-memory list once (module order, then MD order), then
@@ -735,10 +741,11 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
   const uint32_t nu = H->n_ev * G.nm;
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t* list = ls_smem + (threadIdx.x >> 5) * (list_cap + LS_EXTRA_WORDS);
+  uint32_t* list = ls_smem + (threadIdx.x >> 5) * ls_warp_words(list_cap);
   uint32_t* queue = list + list_cap;
   uint32_t* pbits = queue + LS_RING;
-  float4* anc = reinterpret_cast<float4*>(pbits + LS_ANCHORS * LS_LIST_CAP / 32);
+  const uint32_t pw = (list_cap + 31) >> 5;  // pass-bit words per anchor
+  float4* anc = reinterpret_cast<float4*>(pbits + LS_ANCHORS * pw);
   WarpAlloc wa;
   unsigned long long n_cand = 0;  // count pass: candidate pairs this warp tested
   const uint32_t n_ev = H->n_ev;
@@ -787,7 +794,8 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
       }
       return;
     }
-    if (len > list_cap) {
+    if (len > list_cap) {  // counted, so that the host can give later runs a longer list
+      if (lane == 0) atomicAdd(&B.hdr->ls_over, 1u);
       for (uint32_t a = a0; a < a1; a++) ls_md_join<false>(C, G, B, a, ev, A);
       return;
     }
@@ -798,14 +806,23 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
       // Up to LS_ANCHORS MDs of A per walk over the list: their points are staged in shared
       // memory (read as broadcasts) and each candidate loaded is tested against all of
       // them, each anchor with its own pass bits; the head's survivors are queued as
-      // list position | anchor << 9 and the tail runs on 32 of them at a time.
+      // list position | anchor << 11 and the tail runs on 32 of them at a time.
       const uint32_t nwords = (len + 31) >> 5;
       // record of MD a: [count, partner MDs in list order] -- the fill pass only copies it
+      // (list positions below 1024 in words 0-31, one per lane; beyond, words 32-63)
       auto record = [&](uint32_t a, const uint32_t* bits) {
         const uint32_t word = lane < nwords ? bits[lane] : 0u;
         const uint32_t wcnt = __popc(word);
         const uint32_t wincl = warp_incl_scan(wcnt);
-        const uint32_t count = __shfl_sync(FULL, wincl, 31);
+        uint32_t count = __shfl_sync(FULL, wincl, 31);
+        const uint32_t n_lo = count;
+        uint32_t word2 = 0, wcnt2 = 0, wincl2 = 0;
+        if (nwords > 32) {  // warp-uniform
+          word2 = lane + 32 < nwords ? bits[lane + 32] : 0u;
+          wcnt2 = __popc(word2);
+          wincl2 = warp_incl_scan(wcnt2);
+          count += __shfl_sync(FULL, wincl2, 31);
+        }
         uint32_t mbase = NONE;
         if (count > 0) {
           const uint32_t need = 1 + count;
@@ -842,6 +859,8 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
             if (lane == 0) B.mask[mbase] = count;
             uint32_t pos = mbase + 1 + wincl - wcnt;
             for (uint32_t w = word; w; w &= w - 1u) B.mask[pos++] = list[(lane << 5) + __ffs(w) - 1];
+            pos = mbase + 1 + n_lo + wincl2 - wcnt2;
+            for (uint32_t w = word2; w; w &= w - 1u) B.mask[pos++] = list[((lane + 32) << 5) + __ffs(w) - 1];
           }
         }
         if (lane == 0) {
@@ -855,15 +874,16 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
           anc[2 * lane] = B.md_pt[2 * (size_t)(ag + lane)];
           anc[2 * lane + 1] = B.md_dir4[ag + lane];
         }
-        for (uint32_t i = lane; i < na * (LS_LIST_CAP / 32); i += 32) pbits[i] = 0;
+        for (uint32_t w = lane; w < nwords; w += 32)  // only the words the list covers are used
+          for (uint32_t k = 0; k < na; k++) pbits[k * pw + w] = 0;
         uint32_t qh = 0, qt = 0;  // ring head and tail (free-running)
         auto tail = [&](uint32_t e) {
-          const uint32_t k = e >> 9, q = e & 511u;
+          const uint32_t k = e >> 11, q = e & 2047u;
           const uint32_t j = list[q];
           const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
           const PointTol pa{anc[2 * k], t_a};
           if (ls_tail_k(C, G, B, pa, anc[2 * k + 1], rnext, exit, j))
-            atomicOr(&pbits[k * (LS_LIST_CAP / 32) + (q >> 5)], 1u << (q & 31));
+            atomicOr(&pbits[k * pw + (q >> 5)], 1u << (q & 31));
         };
         __syncwarp();
         for (uint32_t t0 = 0; t0 < len; t0 += 32) {
@@ -874,7 +894,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
             const PointTol pa{anc[2 * k], t_a};
             const bool h = t < len && ls_head_pt(C, pa, pb);
             const uint32_t hb = __ballot_sync(FULL, h);
-            if (h) queue[(qt + __popc(hb & lt)) & (LS_RING - 1)] = t | (k << 9);
+            if (h) queue[(qt + __popc(hb & lt)) & (LS_RING - 1)] = t | (k << 11);
             qt += __popc(hb);
             if (qt - qh >= 32) {
               __syncwarp();
@@ -886,7 +906,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
         __syncwarp();
         if (lane < qt - qh) tail(queue[(qh + lane) & (LS_RING - 1)]);
         __syncwarp();
-        for (uint32_t k = 0; k < na; k++) record(ag + k, pbits + k * (LS_LIST_CAP / 32));
+        for (uint32_t k = 0; k < na; k++) record(ag + k, pbits + k * pw);
         __syncwarp();  // anchors, pbits and the queue are reused by the next group
       }
     }
@@ -2336,7 +2356,7 @@ static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const 
 // Lets the LS count kernel take the shared memory of the largest block (512 threads) on the
 // current device; called once per pipeline, outside any stream capture.
 cudaError_t configure_kernels() {
-  const int bytes = (int)((512 / 32) * (LS_LIST_CAP + LS_EXTRA_WORDS) * sizeof(uint32_t));
+  const int bytes = (int)((512 / 32) * ls_warp_words(LS_LIST_MAX) * sizeof(uint32_t));
   return cudaFuncSetAttribute(k_ls_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -2403,7 +2423,7 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     cudaEventRecord(side->join, side->s);
   }
   const uint32_t lcap = L.ls_list_cap;
-  const size_t ls_smem = lcap ? (bs / 32) * (lcap + LS_EXTRA_WORDS) * sizeof(uint32_t) : 0;
+  const size_t ls_smem = lcap ? (bs / 32) * ls_warp_words(lcap) * sizeof(uint32_t) : 0;
   launch(k_ls_count, g, bs, ls_smem, s, C, G, B, lcap);
   mk(9);
   scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, mk);

@@ -220,6 +220,35 @@ def test_ls_without_stored_partner_lists(built, full_geom, ora_full):
         s.close()
 
 
+def test_long_neighbour_lists_at_every_list_cap(built, full_geom, ora_full):
+    # high occupancy (12000 tracks): 15123 of 75703 anchors have more than 512 neighbour MDs
+    # and 248 more than 1024, so a 512-entry list sends many modules to the per-MD join, a
+    # 1024-entry list a few and a 2048-entry list none; all equal the oracle
+    ev = S.make_event("highocc", 0)
+    ora = oracle.run(ora_full, ev)
+    for cap in (512, 1024, 2048):
+        s = lst.Session(full_geom.modules, keep_objects=True, ls_list_cap=cap)
+        compare(s, s.run_event(ev), ora, ev, f"highocc ls_list_cap {cap}")
+        s.close()
+    # the library's choice: the first run overflows a 1024-entry list, later runs use 2048
+    s = lst.Session(full_geom.modules, keep_objects=True)
+    for run in range(2):
+        compare(s, s.run_event(ev), ora, ev, f"highocc default list cap, run {run}")
+    s.close()
+
+
+def test_long_neighbour_lists_with_tilted_modules(built, tilted_geom, ora_tilted):
+    # with tilted inner-barrel modules an eighth of the high-occupancy pairs sit in lists of
+    # 1024-1500 MDs: the first run at the default cap joins those modules per MD, the
+    # second stages them (2048); both equal the oracle
+    ev = S.make_event("highocc", 1, realistic=True)
+    ora = oracle.run(ora_tilted, ev)
+    s = lst.Session(tilted_geom.modules, keep_objects=True)
+    for run in range(2):
+        compare(s, s.run_event(ev), ora, ev, f"tilted highocc, run {run}")
+    s.close()
+
+
 def test_pls_with_many_first_anchor_mds(built, full_geom, ora_full):
     # one exact 5 GeV track plus 11 extra hits on each sensor of its first-layer module,
     # within 20 um of its crossing: 144 MDs there all pass the pLS's first-anchor window

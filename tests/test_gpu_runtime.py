@@ -48,7 +48,8 @@ def test_tuning_space_gives_identical_results(full_geom):
     ev = S.make_event("pu200", 30, n_tracks=2500, with_pls=True)
     s = lst.Session(full_geom.modules, keep_objects=True)
     ref_tc = ref_ls = None
-    for bs, bps, cap in ((256, 4, 512), (128, 2, 1), (512, 8, 128), (64, 4, 32), (256, 1, 1)):
+    for bs, bps, cap in ((256, 4, 512), (128, 2, 1), (512, 8, 128), (64, 4, 32), (256, 1, 1), (512, 4, 1024),
+                         (256, 8, 1024)):
         s.set_tuning(bs, bps, cap)
         rid = s.run_event(ev)
         tc = s.candidates(rid).tobytes()
