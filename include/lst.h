@@ -111,8 +111,8 @@ typedef struct lst_config {
   uint32_t blocks_per_sm;/* resident blocks per SM of the persistent grids (0 = default) */
   uint32_t profile;      /* 1: run kernels eagerly with a CUDA event after each (per-kernel times) */
   uint32_t ls_list_cap;  /* LS work split: neighbour MDs staged per warp in shared memory, up to
-                            2048 (0 = the library's choice: 1024, raised to 2048 after a run
-                            with a longer neighbour list; 1 = no staging, one warp per MD) */
+                            2048 (0 = the library's choice: 512, raised after a run with a
+                            longer neighbour list to hold it; 1 = no staging, one warp per MD) */
   uint32_t reserved[9];
 } lst_config;
 

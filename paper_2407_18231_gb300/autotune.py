@@ -20,7 +20,7 @@ import numpy as np
 from . import Session, lst_config  # noqa: F401
 
 SPACE = {"block_size": [128, 256, 512], "blocks_per_sm": [2, 4, 8, 12], "ls_list_cap": [1, 128, 512, 1024]}
-DEFAULT = {"block_size": 256, "blocks_per_sm": 4, "ls_list_cap": 1024}
+DEFAULT = {"block_size": 256, "blocks_per_sm": 4, "ls_list_cap": 512}
 
 
 def _device_name(device: int) -> str:

@@ -38,7 +38,7 @@ struct Hdr {
   uint32_t n_ev, n_hits, n_pls, pad;
   uint32_t tot[N_TOTALS];
   uint32_t err;
-  uint32_t ls_over;  // LS count pass: units whose neighbour list exceeded the launch's list cap
+  uint32_t ls_maxlen;  // LS count pass: the longest neighbour list beyond the launch's list cap
   uint32_t pad2[2];
   uint32_t mask_used[8];  // LS partner-list arena: [1] words handed out in pieces (may pass the
                           // arena's end), [2] words of the lists that found it exhausted

@@ -596,7 +596,7 @@ struct Pipeline {
     const uint32_t bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
     L.block = cfg.block_size ? cfg.block_size : 256;
     // a multiple of 4: the LS kernel's per-warp shared-memory slices hold float4s
-    L.ls_list_cap = cfg.ls_list_cap == 0 ? 1024u
+    L.ls_list_cap = cfg.ls_list_cap == 0 ? 512u
                                          : (cfg.ls_list_cap == 1 ? 0u : std::min(cfg.ls_list_cap, LS_LIST_MAX) & ~3u);
     auto_list_cap = cfg.ls_list_cap == 0;
     L.grid = (uint32_t)n_sm * bps;
@@ -830,10 +830,10 @@ struct Pipeline {
   void learn(const Hdr& h) {
     learn_mask(h);
     // a neighbour list longer than the LS pass's shared-memory list sent its module to the
-    // per-MD join: later runs get the longest list (when the cap is the library's choice;
-    // a 1024-entry list keeps more blocks resident, so it stays the start value)
-    if (h.ls_over && auto_list_cap && L.ls_list_cap && L.ls_list_cap < LS_LIST_MAX) {
-      L.ls_list_cap = LS_LIST_MAX;
+    // per-MD join: later runs get a list that holds it, up to LS_LIST_MAX (when the cap is
+    // the library's choice; a shorter list keeps more blocks resident, so 512 stays the start)
+    if (h.ls_maxlen > L.ls_list_cap && auto_list_cap && L.ls_list_cap && L.ls_list_cap < LS_LIST_MAX) {
+      L.ls_list_cap = std::min(LS_LIST_MAX, (h.ls_maxlen + 127u) & ~127u);
       graph_valid = false;
     }
     if (h.n_hits) {

@@ -27,6 +27,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+
 // Programmatic dependent launch: every kernel of the chain is launched so that it may be
 // scheduled as soon as its predecessor's blocks have all exited (no explicit trigger: an
 // early one let waiting blocks take the slots of the persistent grids and was slower), and
@@ -794,8 +795,8 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
       }
       return;
     }
-    if (len > list_cap) {  // counted, so that the host can give later runs a longer list
-      if (lane == 0) atomicAdd(&B.hdr->ls_over, 1u);
+    if (len > list_cap) {  // recorded, so that the host can give later runs a longer list
+      if (lane == 0) atomicMax(&B.hdr->ls_maxlen, len);
       for (uint32_t a = a0; a < a1; a++) ls_md_join<false>(C, G, B, a, ev, A);
       return;
     }

@@ -230,7 +230,8 @@ def test_long_neighbour_lists_at_every_list_cap(built, full_geom, ora_full):
         s = lst.Session(full_geom.modules, keep_objects=True, ls_list_cap=cap)
         compare(s, s.run_event(ev), ora, ev, f"highocc ls_list_cap {cap}")
         s.close()
-    # the library's choice: the first run overflows a 1024-entry list, later runs use 2048
+    # the library's choice: the first run overflows the 512-entry start list, later runs
+    # use a list that holds the longest one (1152)
     s = lst.Session(full_geom.modules, keep_objects=True)
     for run in range(2):
         compare(s, s.run_event(ev), ora, ev, f"highocc default list cap, run {run}")
@@ -238,9 +239,9 @@ def test_long_neighbour_lists_at_every_list_cap(built, full_geom, ora_full):
 
 
 def test_long_neighbour_lists_with_tilted_modules(built, tilted_geom, ora_tilted):
-    # with tilted inner-barrel modules an eighth of the high-occupancy pairs sit in lists of
-    # 1024-1500 MDs: the first run at the default cap joins those modules per MD, the
-    # second stages them (2048); both equal the oracle
+    # with tilted inner-barrel modules half of the high-occupancy pairs sit in lists of
+    # 512-1520 MDs: the first run at the default cap joins those modules per MD, the second
+    # stages them (a 1536-entry list); both equal the oracle
     ev = S.make_event("highocc", 1, realistic=True)
     ora = oracle.run(ora_tilted, ev)
     s = lst.Session(tilted_geom.modules, keep_objects=True)
