@@ -721,6 +721,8 @@ __global__ void __launch_bounds__(512) k_ls_fill(MethodConst C, GeoView G, BufVi
 // in 512; high-occupancy events reach about 1100, 1500 with tilted modules.
 static_assert(LS_LIST_MAX <= 64 * 32, "two pass-bit words per lane");
 constexpr uint32_t LS_ANCHORS = 8;     // MDs of a module tested per walk over its list
+constexpr uint32_t LS_SPLIT = 4;       // units per module in batches of fewer than 8 events
+constexpr uint32_t LS_SPLIT_MIN_HITS = 16384;  // ... that hold at least this many hits
 constexpr uint32_t LS_RING = 64;       // ring of queued (list position, anchor) entries (> 31 + 32)
 // per warp after the list: the ring, one pass bit per list position for each anchor, and
 // the anchors (lower hit and direction terms: two float4 each; the tolerances are the
@@ -748,11 +750,21 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
   const uint32_t pw = (list_cap + 31) >> 5;  // pass-bit words per anchor
   float4* anc = reinterpret_cast<float4*>(pbits + LS_ANCHORS * pw);
   WarpAlloc wa;
+  // arena pieces a warp takes at least: small enough that every warp of the grid can hold
+  // one twice over (a single event's lists need far fewer words than 1024 per warp)
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t grab_min = max(32u, min(1024u, B.cap_mask / (2u * n_warps)));
   unsigned long long n_cand = 0;  // count pass: candidate pairs this warp tested
   const uint32_t n_ev = H->n_ev;
-  auto unit = [&](const uint32_t u) {
+  // A small but busy batch has few modules per warp, and its latency is that of the busiest
+  // module: there each module's anchor groups are split over LS_SPLIT units (group g in part
+  // g mod LS_SPLIT), each walking the module's list for its own groups only.  (A sparse
+  // batch would only multiply the work-counter atomics of its mostly empty modules.)
+  const uint32_t nsplit = (n_ev < 8 && H->n_hits >= LS_SPLIT_MIN_HITS) ? LS_SPLIT : 1u;
+  const uint32_t step = nsplit * LS_ANCHORS;
+  auto unit = [&](const uint32_t u, const uint32_t part) {
     const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
-    if (a0 == a1) return;
+    if (a0 + part * LS_ANCHORS >= a1) return;  // no anchor group in this part
     const uint32_t ev = u / G.nm, A = u - ev * G.nm;
     const uint32_t ubase = ev * G.nm;
     const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
@@ -787,17 +799,21 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
     }
     if (t_disk == NONE) t_disk = len;
     __syncwarp();
-    n_cand += (unsigned long long)len * (a1 - a0);
+    uint32_t n_mine = 0;  // anchors of this part
+    for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step) n_mine += min(LS_ANCHORS, a1 - ag);
+    n_cand += (unsigned long long)len * n_mine;
     if (len == 0) {  // no neighbour MDs: no LS (and no shared memory touched)
-      for (uint32_t a = a0 + lane; a < a1; a += 32) {
-        B.ls_cnt[a] = 0;
-        B.mask_off[a] = NONE;
-      }
+      for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step)
+        if (ag + lane < min(ag + LS_ANCHORS, a1)) {
+          B.ls_cnt[ag + lane] = 0;
+          B.mask_off[ag + lane] = NONE;
+        }
       return;
     }
     if (len > list_cap) {  // recorded, so that the host can give later runs a longer list
       if (lane == 0) atomicMax(&B.hdr->ls_maxlen, len);
-      for (uint32_t a = a0; a < a1; a++) ls_md_join<false>(C, G, B, a, ev, A);
+      for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step)
+        for (uint32_t a = ag; a < min(ag + LS_ANCHORS, a1); a++) ls_md_join<false>(C, G, B, a, ev, A);
       return;
     }
     const float rnext = G.rnext[A];
@@ -835,7 +851,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
                 // host sizes the next arena from real demand, not from repeated requests
                 atomicAdd(&B.hdr->mask_used[2], need);
               } else {
-                const uint32_t grab = need > 1024u ? need : 1024u;
+                const uint32_t grab = need > grab_min ? need : grab_min;
                 const uint32_t b0 = atomicAdd(&B.hdr->mask_used[1], grab);
                 if (b0 < B.cap_mask && grab <= B.cap_mask - b0) {
                   wa.cur = b0;
@@ -869,7 +885,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
           B.ls_cnt[a] = count;
         }
       };
-      for (uint32_t ag = a0; ag < a1; ag += LS_ANCHORS) {
+      for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step) {
         const uint32_t na = min(LS_ANCHORS, a1 - ag);
         if (lane < na) {
           anc[2 * lane] = B.md_pt[2 * (size_t)(ag + lane)];
@@ -913,9 +929,13 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
     }
     __syncwarp();  // the list is rewritten by the next unit
   };
-  // module-major order (unit k = module k / n_ev of event k % n_ev) taken dynamically:
-  // module ids start with the innermost, busiest layers, so expensive units go first
-  DYN_LOOP(k, &B.hdr->work[W_LS], nu, 2) unit((k % n_ev) * G.nm + k / n_ev);
+  // module-major order (unit k = part k % nsplit of module k' / n_ev of event k' % n_ev, k' =
+  // k / nsplit) taken dynamically: module ids start with the innermost, busiest layers, so
+  // expensive units go first; the parts of a module go to different warps (grain 1)
+  DYN_LOOP(k, &B.hdr->work[W_LS], nu * nsplit, nsplit > 1 ? 1u : 2u) {
+    const uint32_t k1 = k / nsplit;
+    unit((k1 % n_ev) * G.nm + k1 / n_ev, k - k1 * nsplit);
+  }
   if (lane == 0 && n_cand) atomicAdd(&B.hdr->ls_cand, n_cand);
 }
 
