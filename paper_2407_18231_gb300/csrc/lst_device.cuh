@@ -14,11 +14,15 @@ constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, k
 // pT3 items of one pLS: its kept MDs, or (more passing MDs) its candidate modules
 constexpr uint32_t PLS_ITEMS = PLS_MD_CAP > (uint32_t)MAX_CAND ? PLS_MD_CAP : (uint32_t)MAX_CAND;
 
+constexpr int N_SCAN_SLOTS = 16;          // scans of one run that can take the single-pass form
+constexpr uint32_t SCAN_MID_BLOCKS = 32;   // blocks of a single-pass scan
+
 // Totals written by the scans into the batch header.
 enum Total : int {
   T_HITS = 0, T_MD, T_LS, T_T3, T_T5, T_PT3, T_PT5, T_C5, T_C3, T_CT, T_A5, T_A3, T_AT, T_AP, T_TC, T_PT3I, N_TOTALS
 };
 constexpr uint32_t ERR_BAD_INPUT = 1u;
+constexpr uint32_t ERR_WAIT = 2u;  // a bounded device-side wait ran out (the run is discarded)
 constexpr uint32_t ERR_OVERFLOW_SHIFT = 8;  // bit (8 + Total) = that list outgrew its storage
 
 // pLS record as the device reads it (layout of lst_pls).
@@ -44,6 +48,10 @@ struct Hdr {
                           // arena's end), [2] words of the lists that found it exhausted
   unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)
   uint32_t work[16];           // work counters of the dynamically scheduled kernels (W_*)
+  // single-pass scans of mid-size arrays: per scan, the block tickets and the chunk totals
+  // each block publishes (bit 32 set once written)
+  uint32_t scan_ticket[N_SCAN_SLOTS];
+  unsigned long long scan_agg[N_SCAN_SLOTS][SCAN_MID_BLOCKS];
 };
 
 // Work counters in Hdr::work, one per dynamically scheduled kernel and pass.

@@ -1284,6 +1284,7 @@ lst_status run_packed(lst_ctx* c, Pipeline& P, bool use_graph, uint32_t timeout_
     const Hdr& h = *P.h_hdr_out;
     if (h.err & ERR_BAD_INPUT)
       return fail(c, LST_ERR_BAD_INPUT, "bad input: module id out of range, non-finite value or invalid pLS");
+    if (h.err & ERR_WAIT) return fail(c, LST_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (!P.grow_after_overflow(h)) {
       P.learn(h);
       return LST_OK;
@@ -1415,6 +1416,7 @@ lst_status lst_batch_finish(lst_ctx* c, uint32_t timeout_ms, uint32_t* n_tc_per_
     const Hdr& h = *P.h_hdr_out;
     if (h.err & ERR_BAD_INPUT)
       return fail(c, LST_ERR_BAD_INPUT, "bad input: module id out of range, non-finite value or invalid pLS");
+    if (h.err & ERR_WAIT) return fail(c, LST_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (P.grow_after_overflow(h)) {
       c->reruns++;
       c->stats.reruns++;
@@ -1472,6 +1474,7 @@ lst_status lst_collect_batch(lst_ctx* c, uint64_t ticket, uint32_t timeout_ms, u
     const Hdr& h = *P.h_hdr_out;
     if (h.err & ERR_BAD_INPUT)
       return fail(c, LST_ERR_BAD_INPUT, "bad input: module id out of range, non-finite value or invalid pLS");
+    if (h.err & ERR_WAIT) return fail(c, LST_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (P.grow_after_overflow(h)) {
       c->reruns++;
       c->stats.reruns++;
@@ -1822,6 +1825,7 @@ extern "C" lst_status lst_serve_replay(lst_ctx* c, const lst_serve_config* cfg, 
             if (!P.wait(0)) return set_error(LST_ERR_TIMEOUT, "device did not finish");
             const Hdr& h = *P.h_hdr_out;
             if (h.err & ERR_BAD_INPUT) return set_error(LST_ERR_BAD_INPUT, "bad input in a served event");
+            if (h.err & ERR_WAIT) return set_error(LST_ERR_TIMEOUT, "a bounded device-side wait ran out");
             if (!P.grow_after_overflow(h)) {
               P.learn(h);
               break;

@@ -346,6 +346,77 @@ __global__ void __launch_bounds__(1024) k_scan_small(const uint32_t* __restrict_
   scan_small_body(in, (*nptr) * mul, out, H, tot_idx, cap, sm);
 }
 
+// Mid-size arrays (capacity up to SCAN_MID_MAX, one event's lists): a single pass of
+// SCAN_MID_BLOCKS blocks of 1024 threads, each scanning one chunk of at most 8 elements per
+// thread.  A block takes a ticket when it starts (the chunk it scans, so chunks are handed
+// out in start order), publishes its chunk's total, and adds the totals of the chunks before
+// its own: it waits only for blocks that started before it, so every wait ends.  Each wait
+// is still bounded (SCAN_WAIT_LIMIT polls); a block whose wait runs out sets ERR_WAIT, and
+// the host reports the run as failed.
+constexpr uint32_t SCAN_MID_PER_THREAD = 8;
+constexpr uint32_t SCAN_MID_MAX = SCAN_MID_BLOCKS * 1024u * SCAN_MID_PER_THREAD;
+constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 22;
+static_assert(11 + 4 <= N_SCAN_SLOTS, "scan slots: eight single scans, then three and four arrays");
+__device__ __forceinline__ void scan_mid_body(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ out,
+                                              Hdr* H, int tot_idx, uint32_t cap, uint32_t slot, uint32_t* sm) {
+  if (threadIdx.x == 0) sm[33] = atomicAdd(&H->scan_ticket[slot], 1u);
+  __syncthreads();
+  const uint32_t b = sm[33];
+  const uint32_t chunk = (n + SCAN_MID_BLOCKS - 1) / SCAN_MID_BLOCKS;
+  const uint32_t lo = min(n, b * chunk), hi = min(n, lo + chunk);
+  const uint32_t i0 = lo + threadIdx.x * SCAN_MID_PER_THREAD;
+  uint32_t v[SCAN_MID_PER_THREAD];
+  uint32_t s = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < SCAN_MID_PER_THREAD; k++) {
+    v[k] = (i0 + k < hi) ? in[i0 + k] : 0u;
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t ex = block_excl_scan(s, sm, tot);
+  unsigned long long* agg = H->scan_agg[slot];
+  if (threadIdx.x == 0) atomicExch(&agg[b], (1ull << 32) | tot);
+  if (threadIdx.x < 32) {  // look-back: lane j adds chunk j's total, for every j < b
+    uint32_t x = 0;
+    if (threadIdx.x < b) {
+      unsigned long long w = 0;
+      for (uint32_t it = 0; it < SCAN_WAIT_LIMIT; it++) {
+        w = atomicAdd(&agg[threadIdx.x], 0ull);
+        if (w >> 32) break;
+      }
+      if (!(w >> 32)) atomicOr(&H->err, ERR_WAIT);
+      x = (uint32_t)w;
+    }
+    const uint32_t carry = __shfl_sync(FULL, warp_incl_scan(x), 31);
+    if (threadIdx.x == 0) sm[34] = carry;
+  }
+  __syncthreads();
+  const uint32_t carry = sm[34];
+  ex += carry;
+#pragma unroll
+  for (uint32_t k = 0; k < SCAN_MID_PER_THREAD; k++) {
+    if (i0 + k < hi) out[i0 + k] = ex;
+    ex += v[k];
+  }
+  if (b == SCAN_MID_BLOCKS - 1 && threadIdx.x == 0) {
+    const uint32_t total = carry + tot;
+    out[n] = total;
+    if (tot_idx >= 0) {
+      H->tot[tot_idx] = total;
+      if (total > cap) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + tot_idx));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_mid(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul,
+                                                   Hdr* H, uint32_t* __restrict__ out, int tot_idx, uint32_t cap,
+                                                   uint32_t slot) {
+  pdl_wait();
+  if (H->err) return;
+  __shared__ uint32_t sm[35];
+  scan_mid_body(in, (*nptr) * mul, out, H, tot_idx, cap, slot, sm);
+}
+
 // Up to four independent scans in one launch (blockIdx.y picks the array).
 struct ScanJob {
   const uint32_t* in;
@@ -365,6 +436,15 @@ __global__ void __launch_bounds__(1024) k_scan_small_multi(ScanJobs J, Hdr* H) {
   __shared__ uint32_t sm[33];
   const ScanJob& q = J.j[blockIdx.x];
   scan_small_body(q.in, *q.nptr, q.out, H, q.tot, q.cap, sm);
+}
+
+// The single-pass scan of several mid-size arrays (blockIdx.y picks the array and its slot).
+__global__ void __launch_bounds__(1024) k_scan_mid_multi(ScanJobs J, Hdr* H, uint32_t slot0) {
+  pdl_wait();
+  if (H->err) return;
+  __shared__ uint32_t sm[35];
+  const ScanJob& q = J.j[blockIdx.y];
+  scan_mid_body(q.in, *q.nptr, q.out, H, q.tot, q.cap, slot0 + blockIdx.y, sm);
 }
 
 __global__ void k_scan_reduce_multi(ScanJobs J, const Hdr* H, uint32_t* part) {
@@ -2373,7 +2453,7 @@ const char* const kKernelNames[] = {
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "(unused)", "md_lists_count", "md_lists_fill",
     "kill_pt5", "(unused)", "cross_pt3", "kill_pt3", "(unused)", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
-    "(unused)", "(unused)", "pt3_first_anchor", "pls_sort", "pt3_items", "md_boxes", "scan_small"};
+    "(unused)", "(unused)", "pt3_first_anchor", "pls_sort", "pt3_items", "md_boxes", "scan_small", "scan_mid"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Marker {
@@ -2405,11 +2485,17 @@ static void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
 
 // bound: the most elements the array can hold (its buffer's capacity), which picks the
 // one-block scan for small arrays when the pipeline is sized for them.
+// slot: this scan's own ticket counter and chunk totals in the header (single-pass form).
 static void scan(const BufView& B, const Launch& L, cudaStream_t s, const uint32_t* in, uint32_t* out,
-                 const uint32_t* nptr, uint32_t mul, int tot, uint32_t cap, uint64_t bound, Marker& mk) {
+                 const uint32_t* nptr, uint32_t mul, int tot, uint32_t cap, uint64_t bound, uint32_t slot, Marker& mk) {
   if (bound <= SCAN_SMALL_MAX) {
     launch(k_scan_small, 1, 1024, 0, s, in, nptr, mul, B.hdr, out, tot, cap);
     mk(38);
+    return;
+  }
+  if (bound <= SCAN_MID_MAX) {
+    launch(k_scan_mid, SCAN_MID_BLOCKS, 1024, 0, s, in, nptr, mul, B.hdr, out, tot, cap, slot);
+    mk(39);
     return;
   }
   launch(k_scan_reduce, L.scan_grid, 512, 0, s, in, nptr, mul, B.hdr, B.scan_part);
@@ -2424,6 +2510,10 @@ static void pt3_items(const BufView& B, const Launch& L, cudaStream_t s, Marker&
   if (B.cap_pls <= SCAN_SMALL_MAX) {
     launch(k_scan_small, 1, 1024, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.pt3_ioff, T_PT3I, 0xFFFFFFFFu);
     mk(38);
+  } else if (B.cap_pls <= SCAN_MID_MAX) {
+    launch(k_scan_mid, SCAN_MID_BLOCKS, 1024, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.pt3_ioff, T_PT3I,
+           0xFFFFFFFFu, 5u);
+    mk(39);
   } else {
     launch(k_scan_reduce, L.scan_grid, 512, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2);
     mk(2);
@@ -2436,10 +2526,15 @@ static void pt3_items(const BufView& B, const Launch& L, cudaStream_t s, Marker&
 }
 
 static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const ScanJobs& J, int n, uint64_t bound,
-                       Marker& mk) {
+                       uint32_t slot0, Marker& mk) {
   if (bound <= SCAN_SMALL_MAX) {
     launch(k_scan_small_multi, n, 1024, 0, s, J, B.hdr);
     mk(38);
+    return;
+  }
+  if (bound <= SCAN_MID_MAX) {
+    launch(k_scan_mid_multi, dim3(SCAN_MID_BLOCKS, n), 1024, 0, s, J, B.hdr, slot0);
+    mk(39);
     return;
   }
   launch(k_scan_reduce_multi, dim3(L.scan_grid, n), 512, 0, s, J, B.hdr, B.scan_part);
@@ -2461,7 +2556,8 @@ cudaError_t configure_kernels() {
 cudaError_t preload_kernels() {
   const void* ks[] = {
       (const void*)k_scan_reduce, (const void*)k_scan_apply, (const void*)k_scan_reduce_multi,
-      (const void*)k_scan_apply_multi, (const void*)k_scan_small, (const void*)k_scan_small_multi, (const void*)k_zero, (const void*)k_hits_count, (const void*)k_hits_scatter,
+      (const void*)k_scan_apply_multi, (const void*)k_scan_small, (const void*)k_scan_small_multi,
+      (const void*)k_scan_mid, (const void*)k_scan_mid_multi, (const void*)k_zero, (const void*)k_hits_count, (const void*)k_hits_scatter,
       (const void*)k_hits_sort, (const void*)k_md_count, (const void*)k_md_fill, (const void*)k_ls_fill,
       (const void*)k_ls_count, (const void*)k_t3_count, (const void*)k_t3_fill, (const void*)k_t5_count,
       (const void*)k_t5_fill, (const void*)k_t5_count_mlp, (const void*)k_t5_fill_mlp, (const void*)k_pls_prep, (const void*)k_pls_sort, (const void*)k_md_box,
@@ -2497,14 +2593,14 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   mk(0);
   launch(k_hits_count, g, 256, 0, s, G, B);
   mk(1);
-  scan(B, L, s, B.sen_cnt, B.sen_off, &H->n_ev, two_nm, T_HITS, 0xFFFFFFFFu, (uint64_t)B.cap_ev * two_nm, mk);
+  scan(B, L, s, B.sen_cnt, B.sen_off, &H->n_ev, two_nm, T_HITS, 0xFFFFFFFFu, (uint64_t)B.cap_ev * two_nm, 0u, mk);
   launch(k_hits_scatter, g, 256, 0, s, G, B);
   mk(5);
   launch(k_hits_sort, g, 256, 0, s, G, B);
   mk(6);
   launch(k_md_count, g, bs, 0, s, C, G, B);
   mk(7);
-  scan(B, L, s, B.md_hcnt, B.md_hoff, &H->n_hits, 1, T_MD, B.cap_md, B.cap_hits, mk);
+  scan(B, L, s, B.md_hcnt, B.md_hoff, &H->n_hits, 1, T_MD, B.cap_md, B.cap_hits, 1u, mk);
   launch(k_md_fill, g, bs, 0, s, C, G, B);
   mk(8);
   if (side) {  // pT3 phase 1 needs the MDs and the pLS preparation only
@@ -2521,12 +2617,12 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   const size_t ls_smem = lcap ? (bs / 32) * ls_warp_words(lcap) * sizeof(uint32_t) : 0;
   launch(k_ls_count, g, bs, ls_smem, s, C, G, B, lcap);
   mk(9);
-  scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, B.cap_md, mk);
+  scan(B, L, s, B.ls_cnt, B.ls_off, &H->tot[T_MD], 1, T_LS, B.cap_ls, B.cap_md, 2u, mk);
   launch(k_ls_fill, g, bs, 0, s, C, G, B);
   mk(10);
   launch(k_t3_count, g, 256, 0, s, C, G, B);
   mk(11);
-  scan(B, L, s, B.t3_lcnt, B.t3_loff, &H->tot[T_LS], 1, T_T3, B.cap_t3, B.cap_ls, mk);
+  scan(B, L, s, B.t3_lcnt, B.t3_loff, &H->tot[T_LS], 1, T_T3, B.cap_t3, B.cap_ls, 3u, mk);
   launch(k_t3_fill, g, 256, 0, s, C, G, B);
   mk(12);
   if (L.t5_mlp)
@@ -2534,7 +2630,7 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   else
     launch(k_t5_count, g, bs, 0, s, C, G, B);
   mk(13);
-  scan(B, L, s, B.t5_tcnt, B.t5_toff, &H->tot[T_T3], 1, T_T5, B.cap_t5, B.cap_t3, mk);
+  scan(B, L, s, B.t5_tcnt, B.t5_toff, &H->tot[T_T3], 1, T_T5, B.cap_t5, B.cap_t3, 4u, mk);
   if (L.t5_mlp)
     launch(k_t5_fill_mlp, g, bs, 0, s, C, G, B, *L.t5_mlp);
   else
@@ -2555,12 +2651,12 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
   }
   launch(k_pt3_count, g, bs, 0, s, C, G, B);
   mk(16);
-  scan(B, L, s, B.pt3_xcnt, B.pt3_xoff, &H->tot[T_PT3I], 1, T_PT3, B.cap_pt3, (uint64_t)B.cap_pls * PLS_ITEMS, mk);
+  scan(B, L, s, B.pt3_xcnt, B.pt3_xoff, &H->tot[T_PT3I], 1, T_PT3, B.cap_pt3, (uint64_t)B.cap_pls * PLS_ITEMS, 6u, mk);
   launch(k_pt3_fill, g, bs, 0, s, C, G, B);
   mk(17);
   launch(k_pt5_count, g, bs, 0, s, C, G, B);
   mk(18);
-  scan(B, L, s, B.pt5_xcnt, B.pt5_xoff, &H->tot[T_PT3], 1, T_PT5, B.cap_pt5, B.cap_pt3, mk);
+  scan(B, L, s, B.pt5_xcnt, B.pt5_xoff, &H->tot[T_PT3], 1, T_PT5, B.cap_pt5, B.cap_pt3, 7u, mk);
   launch(k_pt5_fill, g, bs, 0, s, C, G, B);
   mk(19);
   launch(k_csr_count, g, 256, 0, s, B);
@@ -2570,7 +2666,7 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     J.j[0] = {B.c5_cnt, B.c5_off, &H->tot[T_MD], T_C5, 5u * B.cap_pt5};
     J.j[1] = {B.c3_cnt, B.c3_off, &H->tot[T_MD], T_C3, 3u * B.cap_pt3};
     J.j[2] = {B.ct_cnt, B.ct_off, &H->tot[T_MD], T_CT, 5u * B.cap_t5};
-    scan_multi(B, L, s, J, 3, B.cap_md, mk);
+    scan_multi(B, L, s, J, 3, B.cap_md, 8u, mk);
   }
   launch(k_csr_fill, g, 256, 0, s, B);
   mk(22);
@@ -2590,7 +2686,8 @@ int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, c
     J.j[1] = {B.alive3, B.sa3, &H->tot[T_PT3], T_A3, 0xFFFFFFFFu};
     J.j[2] = {B.alivet, B.sat, &H->tot[T_T5], T_AT, 0xFFFFFFFFu};
     J.j[3] = {B.plstc, B.sap, &H->n_pls, T_AP, 0xFFFFFFFFu};
-    scan_multi(B, L, s, J, 4, std::max<uint64_t>(std::max(B.cap_pt5, B.cap_pt3), std::max(B.cap_t5, B.cap_pls)), mk);
+    scan_multi(B, L, s, J, 4, std::max<uint64_t>(std::max(B.cap_pt5, B.cap_pt3), std::max(B.cap_t5, B.cap_pls)), 11u,
+               mk);
   }
   launch(k_tc_offsets, 1, 1024, 0, s, G, B);
   mk(30);

@@ -290,6 +290,10 @@ extern "C" lst_status lst_run_event_static(lst_ctx* ctx, const lst_batch_dev* ev
     ctx_set_error(ctx, "bad input: module id out of range, non-finite value or invalid pLS");
     return LST_ERR_BAD_INPUT;
   }
+  if (out.err & ERR_WAIT) {
+    ctx_set_error(ctx, "a bounded device-side wait ran out");
+    return LST_ERR_TIMEOUT;
+  }
   const uint32_t ovf = out.err >> ERR_OVERFLOW_SHIFT;
   if (ovf & (1u << T_TC)) {
     *n_tc = out.tot[T_TC];
