@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <functional>
@@ -515,6 +516,10 @@ struct Pipeline {
   uint32_t cap_mask = 0;
   uint64_t byte_cap = 0;  // 0: none; otherwise learn_mask keeps dev_bytes within it
   bool auto_list_cap = true;  // the LS list cap is the library's choice (learn may raise it)
+  // test hook for the bounded device waits: the next stall_scan_runs launches start every
+  // single-pass scan's tickets past its last chunk, so its blocks wait for chunk totals that
+  // nothing publishes until their polls run out (LST_TEST_STALL_SCAN at context creation)
+  uint32_t stall_scan_runs = 0;
   // host staging (pinned)
   Hdr* h_hdr = nullptr;        // header to upload
   Hdr* h_hdr_out = nullptr;    // header read back
@@ -907,6 +912,10 @@ struct Pipeline {
     if (cap.ev < dev_inputs.n_ev || cap.hits < dev_inputs.n_hits || cap.pls < dev_inputs.n_pls || cap.ev == 0)
       throw StatusError{LST_ERR_INVALID_ARG, "internal: pipeline launched before its buffers were sized"};
     *h_hdr = dev_inputs;
+    if (stall_scan_runs) {
+      stall_scan_runs--;
+      for (uint32_t& t : h_hdr->scan_ticket) t = SCAN_MID_BLOCKS;
+    }
     L.t5_mlp = geo->has_t5_mlp ? &geo->t5_mlp : nullptr;
     if (graph_sel_version != geo->sel_version) {
       graph_valid = false;
@@ -1349,6 +1358,7 @@ lst_status lst_load_geometry(const lst_module_desc* mods, uint32_t n_mods, const
     c->geo.load(mods, n_mods);
     c->geo.upload_tables();
     c->main.init(&c->geo, c->cfg, c->n_sm);
+    if (const char* v = std::getenv("LST_TEST_STALL_SCAN")) c->main.stall_scan_runs = (uint32_t)std::atoi(v);
     // the allocation-free entry point's array and kernels, loaded now so that its calls allocate nothing
     CK(static_scratch_prepare(c->device));
     return LST_OK;

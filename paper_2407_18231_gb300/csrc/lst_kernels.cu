@@ -355,8 +355,9 @@ __global__ void __launch_bounds__(1024) k_scan_small(const uint32_t* __restrict_
 // the host reports the run as failed.
 constexpr uint32_t SCAN_MID_PER_THREAD = 8;
 constexpr uint32_t SCAN_MID_MAX = SCAN_MID_BLOCKS * 1024u * SCAN_MID_PER_THREAD;
-constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 22;
+constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 20;  // about a second of polls
 static_assert(11 + 4 <= N_SCAN_SLOTS, "scan slots: eight single scans, then three and four arrays");
+static_assert(SCAN_MID_BLOCKS == 32, "one look-back lane per chunk");
 __device__ __forceinline__ void scan_mid_body(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ out,
                                               Hdr* H, int tot_idx, uint32_t cap, uint32_t slot, uint32_t* sm) {
   if (threadIdx.x == 0) sm[33] = atomicAdd(&H->scan_ticket[slot], 1u);
@@ -375,10 +376,12 @@ __device__ __forceinline__ void scan_mid_body(const uint32_t* __restrict__ in, u
   uint32_t tot;
   uint32_t ex = block_excl_scan(s, sm, tot);
   unsigned long long* agg = H->scan_agg[slot];
-  if (threadIdx.x == 0) atomicExch(&agg[b], (1ull << 32) | tot);
+  // (a ticket past the last chunk -- only the test hook that stalls the scans makes one --
+  // scans and publishes nothing and waits for every chunk)
+  if (threadIdx.x == 0 && b < SCAN_MID_BLOCKS) atomicExch(&agg[b], (1ull << 32) | tot);
   if (threadIdx.x < 32) {  // look-back: lane j adds chunk j's total, for every j < b
     uint32_t x = 0;
-    if (threadIdx.x < b) {
+    if (threadIdx.x < b) {  // threadIdx.x < 32 = SCAN_MID_BLOCKS: within agg
       unsigned long long w = 0;
       for (uint32_t it = 0; it < SCAN_WAIT_LIMIT; it++) {
         w = atomicAdd(&agg[threadIdx.x], 0ull);

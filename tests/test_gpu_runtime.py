@@ -73,3 +73,22 @@ def test_autotuner_picks_a_configuration(full_geom, tmp_path):
     s = lst.Session(full_geom.modules, **res["best"])
     assert len(s.candidates(s.run_event(evs[0]))) > 0
     s.close()
+
+
+def test_bounded_scan_wait_reports_timeout(full_geom, monkeypatch):
+    """The single-pass scans wait for the chunk totals of blocks that started earlier, every
+    wait bounded.  The test hook makes the first run's scan blocks wait for totals that
+    nothing publishes: their polls run out (about a second), the run returns
+    LST_ERR_TIMEOUT, and the next run on the same context equals the oracle."""
+    import oracle
+    monkeypatch.setenv("LST_TEST_STALL_SCAN", "1")
+    s = lst.Session(full_geom.modules)
+    monkeypatch.delenv("LST_TEST_STALL_SCAN")
+    ev = S.make_event("pu200", 46, with_pls=True)  # one event: single-pass scans
+    with pytest.raises(lst.LstError) as e:
+        s.run_event(ev)
+    assert e.value.status == -7 and "wait ran out" in str(e.value)
+    tc = s.candidates(s.run_event(ev))
+    ora = oracle.run(oracle.Geometry(full_geom.modules), ev)
+    assert np.array_equal(tc["ot"], ora["tc_ot"]) and tc["score"].tobytes() == ora["tc_score"].tobytes()
+    s.close()
