@@ -499,17 +499,22 @@ def serving_sweep(local, rates=(1e3, 5e3, 10e3, 20e3), budgets_gb=(1, 8, 64), n_
     import paper_2407_18231_gb300 as lst
     g = S.geometry(False)
     pool = [S.make_event("serving", i) for i in range(64)]
-    sess = lst.Session(g.modules, device=local)
-    for i in sess.run_batch(pool[:32]):
-        sess.release(i)
+    # per-event baseline on a context that only runs single events (sized by one pass)
+    sess_e = lst.Session(g.modules, device=local)
+    for e in pool[:24]:
+        sess_e.release(sess_e.run_event(e))
     lat = []
     for e in pool[:24]:
         t0 = time.perf_counter()
-        rid = sess.run_event(e)
-        sess.candidates(rid)
+        rid = sess_e.run_event(e)
+        sess_e.candidates(rid)
         lat.append(time.perf_counter() - t0)
-        sess.release(rid)
+        sess_e.release(rid)
+    sess_e.close()
     lat = np.array(lat[4:])
+    sess = lst.Session(g.modules, device=local)
+    for i in sess.run_batch(pool[:32]):
+        sess.release(i)
     per_event = {"events_per_s": float(1.0 / lat.mean()), "p50_ms": float(np.median(lat) * 1e3),
                  "p99_ms": float(np.percentile(lat, 99) * 1e3)}
     points = []
@@ -729,15 +734,20 @@ def main():
     # ---- per-event launch: latency of single events
     per_event = None
     if args.per_event:
-        for i in sess_h.run_batch(batches[0]):  # size the main pipeline for any single event
-            sess_h.release(i)
+        # a context that only ever runs single events (as a per-event deployment would):
+        # every timed event once first, so that its buffers hold the largest of them
+        sess_e = lst.Session(geom.modules, device=local, **tuning)
+        sess_e.set_t5_selection(t5_weights)
+        for e in events[: args.per_event]:
+            sess_e.release(sess_e.run_event(e))
         lat = []
         for e in events[: args.per_event]:
             t0 = time.perf_counter()
-            rid = sess_h.run_event(e)
-            sess_h.candidates(rid)
+            rid = sess_e.run_event(e)
+            sess_e.candidates(rid)
             lat.append(time.perf_counter() - t0)
-            sess_h.release(rid)
+            sess_e.release(rid)
+        sess_e.close()
         lat = np.array(lat[2:])
         per_event = {"events_per_s": float(1.0 / lat.mean()), "p50_ms": float(np.percentile(lat, 50) * 1e3),
                      "p99_ms": float(np.percentile(lat, 99) * 1e3), "events": int(len(lat))}
