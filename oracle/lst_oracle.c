@@ -20,9 +20,9 @@
  * project's reading: the paper defers the selections to its references.  Each reading
  * is stated at the function that applies it.
  *
- * Object order ("canonical"): MDs by (module, lower-hit input index, upper-hit input
- * index); LS by (inner MD, outer MD); T3 by (MD a, b, c); T5 by (a..e); pT3/pT5 by
- * (pLS, T3/T5 index); TCs by type pT5, pT3, T5, pLS then index.
+ * Object order ("canonical"): hits of a sensor by (pseudo-angle, input index); MDs by
+ * (module, lower hit, upper hit) in that order; LS by (inner MD, outer MD); T3 by (MD a, b,
+ * c); T5 by (a..e); pT3/pT5 by (pLS, T3/T5 index); TCs by type pT5, pT3, T5, pLS then index.
  */
 #include "lst_oracle.h"
 
@@ -780,6 +780,23 @@ static int pt5_curv(const pls_t *p, float kf, const pt_t *P0, const pt_t *P2, co
   return fabsf(fabsf(kf) - 1.0f / p->R) <= C_KPT5 / p->R + tf;
 }
 
+/* Pseudo-angle of (x, y) in [0, 4): 0 along +x, 1 along +y, 2 along -x, 3 along -y,
+ * increasing with the azimuth inside each quadrant (y / (x + y) in the first), from
+ * divisions only, so that binary32 gives the same value everywhere.  The origin maps to 0.
+ * Hits of one sensor are ordered by it (reading of "objects sorted", R17: azimuth order
+ * inside a module). */
+static float pseudo_angle(float x, float y) {
+  if (y >= 0.0f) {
+    if (x >= 0.0f) {
+      float den = x + y;
+      return den > 0.0f ? y / den : 0.0f;
+    }
+    return 1.0f + (-x) / (y - x);
+  }
+  if (x < 0.0f) return 2.0f + (-y) / (-x - y);
+  return 3.0f + x / (x - y);
+}
+
 /* ---------------- the chain ---------------- */
 typedef struct {
   const ora_geom *g;
@@ -845,7 +862,8 @@ int ora_run(const ora_geom *g, const ora_event *ev, int brute_ls, ora_result *ou
   }
   for (uint32_t p = 0; p < ev->n_pls; p++)
     if (ev->pls[p].n_hits != 0 && ev->pls[p].n_hits != 3 && ev->pls[p].n_hits != 4) goto done;
-  /* ---- hit binning by module sensor (stable: input order kept) ---- */
+  /* ---- hit binning by module sensor, in azimuth order inside each sensor (pseudo-angle,
+   * ties by input index) ---- */
   bin_off = (uint32_t *)calloc(2 * (size_t)nm + 1, sizeof(uint32_t));
   bin_list = (uint32_t *)malloc(((size_t)nh + 1) * sizeof(uint32_t));
   hit = (pt_t *)malloc(((size_t)nh + 1) * sizeof(pt_t));
@@ -858,6 +876,22 @@ int ora_run(const ora_geom *g, const ora_event *ev, int brute_ls, ora_result *ou
     memcpy(cur, bin_off, (2 * (size_t)nm + 1) * sizeof(uint32_t));
     for (uint32_t i = 0; i < nh; i++) bin_list[cur[ev->det[i]]++] = i;
     free(cur);
+  }
+  {
+    float *psi = (float *)malloc(((size_t)nh + 1) * sizeof(float));
+    if (!psi) goto done;
+    for (uint32_t i = 0; i < nh; i++) psi[i] = pseudo_angle(ev->x[i], ev->y[i]);
+    for (uint32_t s = 0; s < 2 * nm; s++) /* insertion sort: sensors hold a few hits */
+      for (uint32_t i = bin_off[s] + 1; i < bin_off[s + 1]; i++) {
+        uint32_t h = bin_list[i], j = i;
+        while (j > bin_off[s] && (psi[bin_list[j - 1]] > psi[h] ||
+                                  (psi[bin_list[j - 1]] == psi[h] && bin_list[j - 1] > h))) {
+          bin_list[j] = bin_list[j - 1];
+          j--;
+        }
+        bin_list[j] = h;
+      }
+    free(psi);
   }
   for (uint32_t i = 0; i < nh; i++) get_pt(g, ev, i, ev->det[i] >> 1, &hit[i]);
 

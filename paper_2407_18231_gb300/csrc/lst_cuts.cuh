@@ -221,6 +221,22 @@ __device__ __forceinline__ bool t5_accept(const MethodConst& C, const PointTol& 
   return rz3(C, A, Cc, E);
 }
 
+// Pseudo-angle of (x, y) in [0, 4): 0 along +x, 1 along +y, 2 along -x, 3 along -y,
+// increasing with the azimuth inside each quadrant, from divisions only (the same binary32
+// value on every device); the origin maps to 0.  Hits of a sensor are ordered by it, and
+// |d psi / d phi| <= 1, so an azimuth window of half-width w is inside psi +- w.
+__host__ __device__ __forceinline__ float pseudo_angle(float x, float y) {
+  if (y >= 0.0f) {
+    if (x >= 0.0f) {
+      const float den = x + y;
+      return den > 0.0f ? y / den : 0.0f;
+    }
+    return 1.0f + (-x) / (y - x);
+  }
+  if (x < 0.0f) return 2.0f + (-y) / (-x - y);
+  return 3.0f + x / (x - y);
+}
+
 // ---- learned T5 selection ----
 // The paper's selections include machine-learning methods (Sec. 1); here a small network
 // can take the place of the two curvature-agreement conditions of a T5 while the radius

@@ -534,7 +534,7 @@ __global__ void k_hits_scatter(GeoView G, BufView B) {
   }
 }
 
-// Stable order inside each sensor bucket: rank by input index.
+// Order inside each sensor bucket: by pseudo-angle (azimuth), ties by input index.
 __global__ void k_hits_sort(GeoView G, BufView B) {
   pdl_wait();
   Hdr* H = B.hdr;
@@ -545,9 +545,14 @@ __global__ void k_hits_sort(GeoView G, BufView B) {
     const uint32_t e = B.hit_ev[h];
     const uint32_t bkt = e * two_nm + H->det[h];
     const uint32_t lo = B.sen_off[bkt], hi = B.sen_off[bkt + 1];
-    uint32_t rank = 0;
-    for (uint32_t q = lo; q < hi; q++) rank += B.hit_tmp[q] < h;
     const float x = H->x[h], y = H->y[h], z = H->z[h];
+    const float ph = pseudo_angle(x, y);
+    uint32_t rank = 0;
+    for (uint32_t q = lo; q < hi; q++) {
+      const uint32_t g = B.hit_tmp[q];
+      const float pg = pseudo_angle(H->x[g], H->y[g]);
+      rank += (pg < ph) || (pg == ph && g < h);
+    }
     B.hit4[lo + rank] = make_float4(x, y, z, sqrtf(x * x + y * y));
     B.hit_idx[lo + rank] = h - H->hit_off[e];
     B.hit_sen[lo + rank] = bkt;

@@ -134,6 +134,10 @@ MUTATIONS = [
     ("tc: pLS used by a pT3 stays a candidate", "out->pls_tc[p] = !(used5[p] || used3[p]);", "out->pls_tc[p] = !used5[p];"),
     ("tc: T5 pT without the field constant", "pt = C_KB / fabsf(t5k.p[x]);", "pt = 1.0f / fabsf(t5k.p[x]);"),
     ("tc: a triplet seed listed with four pixel hits", "(ev->pls[pls].n_hits == 3 ? 3 : 4)", "(4)"),
+    # azimuth order of the hits inside a sensor
+    ("hit order: second-quadrant pseudo-angle reversed", "return 1.0f + (-x) / (y - x);", "return 1.0f + y / (y - x);"),
+    ("hit order: input order kept", "while (j > bin_off[s] && (psi[bin_list[j - 1]] > psi[h] ||",
+     "while (j > bin_off[s] && 0 && (psi[bin_list[j - 1]] > psi[h] ||"),
     # learned T5 selection: its inputs, the network, where its decision goes
     ("t5 net: f0 against the bridge/full tolerance", "f[0] = frac_of(c->d1, c->rhs1);", "f[0] = frac_of(c->d1, c->rhs2);"),
     ("t5 net: f3 with the inner curvature", "f[3] = frac_of(c->d2, fabsf(c->kbr) + fabsf(c->kfu) + C_KAPPA0);",

@@ -78,7 +78,15 @@ def test_md_brute_force(workload, ora_barrel, ora_full):
                     found.add((int(ev.det[i] >> 1), i, j))
     got = [tuple(map(int, m)) for m in r["md"]]
     assert set(got) == found and len(got) == len(found)
-    assert got == sorted(got)  # canonical order: module, lower index, upper index
+    # canonical order: module, then the lower hit's azimuth, then the upper hit's (the
+    # hits' pseudo-angle order, checked here against float64 azimuths in [0, 2 pi))
+    phi = np.mod(np.arctan2(ev.y.astype(np.float64), ev.x.astype(np.float64)), 2 * np.pi)
+    for (m1, a1, b1), (m2, a2, b2) in zip(got, got[1:]):
+        assert m1 <= m2
+        if m1 == m2 and a1 != a2:
+            assert phi[a1] < phi[a2] + 1e-6, (m1, a1, a2)
+        elif m1 == m2:
+            assert phi[b1] < phi[b2] + 1e-6, (m1, b1, b2)
 
 
 @pytest.mark.parametrize("n_tracks", [400, 1500])
