@@ -66,6 +66,7 @@ struct GeoView {
   const float *rnext;   // next barrel layer radius (1e30 if none)
   const uint8_t *subdet;
   const uint32_t *conn_off, *conn;
+  const float* conn_dpsi;  // per map edge: pseudo-angle half-width of the LS bending window
   const float4 *mod_e;  // e0x, e0y, e1x, e1y
   const float4 *mod_g;  // surf, gap, emin, emax
   int32_t surf_first[NSURF];
@@ -85,6 +86,7 @@ struct BufView {
   uint32_t cap_ev, cap_hits, cap_md, cap_ls, cap_t3, cap_t5, cap_pls, cap_pt3, cap_pt5, cap_tc;
   // hits
   uint32_t *sen_cnt, *sen_off, *hit_tmp, *hit_ev, *hit_idx;
+  float *hit_psi;     // pseudo-angle of the hit at the same position of hit_tmp
   uint32_t *hit_sen;  // per sorted hit: its sensor bucket (event * 2 modules + sensor)
   float4 *hit4;
   // MD
@@ -94,6 +96,7 @@ struct BufView {
   float4 *md_pt;  // per MD, one 32-byte sector: [2m] lower hit (x, y, z, r), [2m + 1] module tolerances
   float4 *md_up4;
   float4 *md_dir4;  // upper - lower hit: dx, dy, transverse length, rho + rho
+  float *md_psi;    // pseudo-angle of the lower hit (a module's MDs are in its order)
   float4 *md_box;   // per unit: its MDs' lower-hit box, (x0, x1, y0, y1), (z0, z1, -, -)
   // LS
   uint32_t *ls_cnt, *ls_off, *ls_in, *ls_out;

@@ -125,6 +125,7 @@ struct Geometry {
   std::vector<uint8_t> row_fast;
   std::vector<float> row_phi0;
   std::vector<uint32_t> conn_off, conn;
+  std::vector<float> conn_dpsi;  // per map edge: pseudo-angle half-width of the LS bending window
   bool have_map = false;
   // learned T5 selection (passed to the T5 kernels by value); sel_version counts changes so
   // that every pipeline re-captures its graph after one
@@ -133,12 +134,12 @@ struct Geometry {
   uint32_t sel_version = 0;
   // device copies
   DevBuf d_modc, d_rnext, d_subdet, d_mod_e, d_mod_g, d_row_nphi, d_row_base, d_row_mods, d_conn_off, d_conn,
-      d_row_fast, d_row_phi0;
+      d_row_fast, d_row_phi0, d_conn_dpsi;
   uint64_t dev_bytes = 0;
 
   ~Geometry() {
     DevBuf* all[] = {&d_modc, &d_rnext, &d_subdet, &d_mod_e, &d_mod_g, &d_row_nphi, &d_row_base,
-                     &d_row_mods, &d_conn_off, &d_conn, &d_row_fast, &d_row_phi0};
+                     &d_row_mods, &d_conn_off, &d_conn, &d_row_fast, &d_row_phi0, &d_conn_dpsi};
     for (DevBuf* b : all) b->release();
   }
 
@@ -282,12 +283,24 @@ struct Geometry {
     return b;
   }
 
+  // Largest azimuth difference |d| = |phi_b - phi_a| of an anchor pair (a in A, b in B)
+  // that can pass the LS bending cut.  With U = r_a r_b sin(d), W = r_a (r_b cos(d) - r_a +
+  // rs) and E = (e0 + rs (|sin(d)| + 0.05)) r_a, the cut |U| <= W T_B + E, W > 0 gives
+  // cos(d) > 0 and |sin(d)| <= (1 - (r_a - rs) / r_b) T_B + e_max / r_b, e_max = e0 + 1.05 rs,
+  // which is largest at the smallest r_a of A's box and at an end of B's radius range; plus
+  // 3 mrad for the rounding of the binary32 test.
+  double bend_dphi(uint32_t A, uint32_t Bm, const Box& a, const Box& b) const {
+    const double rs = (double)modc[A].y + (double)modc[Bm].y;
+    const double emax = 0.03 + 1.05 * rs;
+    const double T = (double)modc[Bm].w;
+    auto bound = [&](double rb) { return (1.0 - (a.r0 - rs) / rb) * T + emax / rb; };
+    const double S = std::max(bound(b.r0), bound(b.r1));
+    return (S >= 1.0 ? 0.5 * M_PI : std::asin(S)) + 3.0e-3;
+  }
+
   // Can some anchor in A and some anchor in B pass the LS bending and r-z cuts?
   bool reachable(uint32_t A, uint32_t Bm, const Box& a, const Box& b) const {
-    const double rs = (double)modc[A].y + (double)modc[Bm].y;
-    // bending cut => |tan(phi_b - phi_a)| <= T_B + e_max / (r_a - rs)
-    const double emax = 0.03 + 1.05 * rs;
-    const double dphi = std::atan((double)modc[Bm].w + emax / (a.r0 - rs)) + 3.0e-3;
+    const double dphi = bend_dphi(A, Bm, a, b);
     double d = std::fmod(a.phic - b.phic, 2 * M_PI);
     if (d > M_PI) d -= 2 * M_PI;
     if (d < -M_PI) d += 2 * M_PI;
@@ -320,6 +333,7 @@ struct Geometry {
     for (uint32_t i = 0; i < nm; i++) by_surface[surface[i]].push_back(i);
     conn_off.assign(nm + 1, 0);
     conn.clear();
+    conn_dpsi.clear();
     for (uint32_t A = 0; A < nm; A++) {
       conn_off[A] = (uint32_t)conn.size();
       const int s = surface[A];
@@ -331,11 +345,16 @@ struct Geometry {
       } else if ((s < 11 && s < 10) || (s >= 11 && s < 15)) {
         next[k++] = s + 1;  // next disk on the same side
       }
-      const size_t start = conn.size();
+      std::vector<uint32_t> nbr;
       for (int t = 0; t < k; t++)
         for (uint32_t Bm : by_surface[next[t]])
-          if (reachable(A, Bm, boxes[A], boxes[Bm])) conn.push_back(Bm);
-      std::sort(conn.begin() + start, conn.end());
+          if (reachable(A, Bm, boxes[A], boxes[Bm])) nbr.push_back(Bm);
+      std::sort(nbr.begin(), nbr.end());
+      for (uint32_t Bm : nbr) {
+        conn.push_back(Bm);
+        // the azimuth bound as a pseudo-angle half-width (|d psi| <= |d phi|), rounded up
+        conn_dpsi.push_back((float)(bend_dphi(A, Bm, boxes[A], boxes[Bm]) * (1.0 + 1e-6) + 1e-4));
+      }
     }
     conn_off[nm] = (uint32_t)conn.size();
     have_map = true;
@@ -368,6 +387,7 @@ struct Geometry {
   void upload_map() {
     upload(d_conn_off, conn_off);
     upload(d_conn, conn);
+    upload(d_conn_dpsi, conn_dpsi);
   }
 
   GeoView view() const {
@@ -379,6 +399,7 @@ struct Geometry {
     v.subdet = (const uint8_t*)d_subdet.p;
     v.conn_off = (const uint32_t*)d_conn_off.p;
     v.conn = (const uint32_t*)d_conn.p;
+    v.conn_dpsi = (const float*)d_conn_dpsi.p;
     v.mod_e = (const float4*)d_mod_e.p;
     v.mod_g = (const float4*)d_mod_g.p;
     for (int s = 0; s < NSURF; s++) {
@@ -502,8 +523,8 @@ struct Pipeline {
   double r_md = 0.6, r_ls = 1.5, r_t3 = 1.0, r_t5 = 0.3, r_pt3 = 6.0, r_pt5 = 6.0;
   // buffers
   DevBuf hdr, in_x, in_y, in_z, in_det, in_hoff, in_pls, in_poff;
-  DevBuf sen_cnt, sen_off, hit_tmp, hit_ev, hit_idx, hit_sen, hit4;
-  DevBuf md_hcnt, md_hoff, md_hmask, md_box, md_off, md_unit, md_lo_idx, md_up_idx, md_pt, md_up4, md_dir4;
+  DevBuf sen_cnt, sen_off, hit_tmp, hit_psi, hit_ev, hit_idx, hit_sen, hit4;
+  DevBuf md_hcnt, md_hoff, md_hmask, md_box, md_off, md_unit, md_lo_idx, md_up_idx, md_pt, md_up4, md_dir4, md_psi;
   DevBuf ls_cnt, ls_off, ls_in, ls_out;
   DevBuf t3_lcnt, t3_loff, t3_off, t3_a, t3_b, t3_c, t3_mask, t3_md4;
   DevBuf t5_tcnt, t5_toff, t5_off, t5_m[5], t5_score, t5_kfull, t5_mask, t5_md8;
@@ -554,8 +575,8 @@ struct Pipeline {
 
   std::vector<DevBuf*> all_buffers() {
     std::vector<DevBuf*> v = {&hdr, &in_x, &in_y, &in_z, &in_det, &in_hoff, &in_pls, &in_poff, &sen_cnt, &sen_off,
-                              &hit_tmp, &hit_ev, &hit_idx, &hit_sen, &hit4, &md_hcnt, &md_hoff, &md_hmask, &md_box, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
-                              &md_pt, &md_up4, &md_dir4, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off, &t3_mask, &t5_mask, &t3_md4, &t5_md8,
+                              &hit_tmp, &hit_psi, &hit_ev, &hit_idx, &hit_sen, &hit4, &md_hcnt, &md_hoff, &md_hmask, &md_box, &md_off, &md_unit, &md_lo_idx, &md_up_idx,
+                              &md_pt, &md_up4, &md_dir4, &md_psi, &ls_cnt, &ls_off, &ls_in, &ls_out, &t3_lcnt, &t3_loff, &t3_off, &t3_mask, &t5_mask, &t3_md4, &t5_md8,
                               &t3_a, &t3_b, &t3_c, &t5_tcnt, &t5_toff, &t5_off, &t5_score, &t5_kfull, &pls_ev,
                               &pls_ncand, &pls_cand, &pls_h0, &pls_h1, &pls_pt, &pls_mdpass, &pls_nmdpass, &pt3_icnt, &pt3_ioff, &pt3_item_p, &pt3_xcnt, &pt3_xoff, &pt3_xmask, &pt3_off, &pt3_pls, &pt3_obj, &pt3_score,
                               &pt5_xcnt, &pt5_xoff, &pt5_xmask, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
@@ -670,6 +691,7 @@ struct Pipeline {
     f(sen_cnt, std::max<size_t>(c.ev * 2 * nm + 1, 1) * sizeof(uint32_t));
     f(sen_off, std::max<size_t>(c.ev * 2 * nm + 1, 1) * sizeof(uint32_t));
     f(hit_tmp, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
+    f(hit_psi, std::max<size_t>(c.hits, 1) * sizeof(float));
     f(hit_ev, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
     f(hit_idx, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
     f(hit_sen, std::max<size_t>(c.hits, 1) * sizeof(uint32_t));
@@ -685,6 +707,7 @@ struct Pipeline {
     f(md_pt, std::max<size_t>(2 * c.md, 1) * sizeof(float4));
     f(md_up4, std::max<size_t>(c.md, 1) * sizeof(float4));
     f(md_dir4, std::max<size_t>(c.md, 1) * sizeof(float4));
+    f(md_psi, std::max<size_t>(c.md, 1) * sizeof(float));
     f(ls_cnt, std::max<size_t>(c.md, 1) * sizeof(uint32_t));
     f(ls_off, std::max<size_t>(c.md + 1, 1) * sizeof(uint32_t));
     f(ls_in, std::max<size_t>(c.ls, 1) * sizeof(uint32_t));
@@ -859,11 +882,12 @@ struct Pipeline {
     v.cap_ev = cap.ev; v.cap_hits = cap.hits; v.cap_md = cap.md; v.cap_ls = cap.ls; v.cap_t3 = cap.t3;
     v.cap_t5 = cap.t5; v.cap_pls = cap.pls; v.cap_pt3 = cap.pt3; v.cap_pt5 = cap.pt5; v.cap_tc = cap.tc;
 #define P32(x) (uint32_t*)x.p
-    v.sen_cnt = P32(sen_cnt); v.sen_off = P32(sen_off); v.hit_tmp = P32(hit_tmp); v.hit_ev = P32(hit_ev);
+    v.sen_cnt = P32(sen_cnt); v.sen_off = P32(sen_off); v.hit_tmp = P32(hit_tmp); v.hit_psi = (float*)hit_psi.p; v.hit_ev = P32(hit_ev);
     v.hit_idx = P32(hit_idx); v.hit4 = (float4*)hit4.p;
     v.md_hcnt = P32(md_hcnt); v.md_hoff = P32(md_hoff); v.md_hmask = P32(md_hmask); v.md_box = (float4*)md_box.p; v.hit_sen = P32(hit_sen); v.md_off = P32(md_off); v.md_unit = P32(md_unit); v.md_lo_idx = P32(md_lo_idx);
     v.md_up_idx = P32(md_up_idx); v.md_pt = (float4*)md_pt.p; v.md_up4 = (float4*)md_up4.p;
     v.md_dir4 = (float4*)md_dir4.p;
+    v.md_psi = (float*)md_psi.p;
     v.ls_cnt = P32(ls_cnt); v.ls_off = P32(ls_off); v.ls_in = P32(ls_in); v.ls_out = P32(ls_out);
     v.t3_lcnt = P32(t3_lcnt); v.t3_loff = P32(t3_loff); v.t3_off = P32(t3_off); v.t3_mask = P32(t3_mask);
     v.t3_a = P32(t3_a); v.t3_b = P32(t3_b); v.t3_c = P32(t3_c); v.t3_md4 = (uint4*)t3_md4.p;

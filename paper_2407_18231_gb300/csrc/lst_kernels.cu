@@ -531,6 +531,7 @@ __global__ void k_hits_scatter(GeoView G, BufView B) {
     const uint32_t bkt = B.hit_ev[h] * two_nm + H->det[h];
     const uint32_t pos = B.sen_off[bkt] + atomicSub(&B.sen_cnt[bkt], 1u) - 1u;
     B.hit_tmp[pos] = h;
+    B.hit_psi[pos] = pseudo_angle(H->x[h], H->y[h]);
   }
 }
 
@@ -546,11 +547,11 @@ __global__ void k_hits_sort(GeoView G, BufView B) {
     const uint32_t bkt = e * two_nm + H->det[h];
     const uint32_t lo = B.sen_off[bkt], hi = B.sen_off[bkt + 1];
     const float x = H->x[h], y = H->y[h], z = H->z[h];
-    const float ph = pseudo_angle(x, y);
+    const float ph = B.hit_psi[p];
     uint32_t rank = 0;
     for (uint32_t q = lo; q < hi; q++) {
       const uint32_t g = B.hit_tmp[q];
-      const float pg = pseudo_angle(H->x[g], H->y[g]);
+      const float pg = B.hit_psi[q];
       rank += (pg < ph) || (pg == ph && g < h);
     }
     B.hit4[lo + rank] = make_float4(x, y, z, sqrtf(x * x + y * y));
@@ -573,6 +574,7 @@ __device__ __forceinline__ void md_emit(const BufView& B, uint32_t pos, uint32_t
   B.md_up4[pos] = hu;
   B.md_pt[2 * (size_t)pos + 1] = cst;
   B.md_dir4[pos] = md_direction(hl, hu, cst);
+  B.md_psi[pos] = pseudo_angle(hl.x, hl.y);
   B.md_lo_idx[pos] = B.hit_idx[ih];
   B.md_up_idx[pos] = B.hit_idx[jh];
 }
@@ -912,65 +914,91 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
     const uint32_t ev = u / G.nm, A = u - ev * G.nm;
     const uint32_t ubase = ev * G.nm;
     const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
-    // flattened neighbour list; disk modules have the highest ids, so the disk entries are
-    // normally a suffix [t_disk, len) of the list (checked: otherwise each candidate's
-    // module is looked up)
-    uint32_t len = 0, t_disk = NONE;
-    bool suffix = true;
-    for (uint32_t g0 = 0; g0 < nb; g0 += 32) {
-      uint32_t b = 0, c = 0;
-      bool disk = false;
-      if (g0 + lane < nb) {
-        const uint32_t Bm = G.conn[nb0 + g0 + lane];
-        const uint32_t uu = ubase + Bm;
-        b = B.md_off[uu];
-        c = B.md_off[uu + 1] - b;
-        disk = G.subdet[Bm] == 1;
-      }
-      const uint32_t incl = warp_incl_scan(c);
-      const uint32_t o = len + incl - c;
-      for (uint32_t k = 0; k < c; k++)
-        if (o + k < list_cap) list[o + k] = b + k;
-      const uint32_t dm = __ballot_sync(FULL, disk && c > 0), bm = __ballot_sync(FULL, !disk && c > 0);
-      if (t_disk != NONE) {
-        if (bm) suffix = false;
-      } else if (dm) {
-        const uint32_t fd = __ffs(dm) - 1;
-        if (fd < 31 && (bm >> (fd + 1))) suffix = false;
-        t_disk = __shfl_sync(FULL, o, fd);
-      }
-      len += __shfl_sync(FULL, incl, 31);
-    }
-    if (t_disk == NONE) t_disk = len;
-    __syncwarp();
-    uint32_t n_mine = 0;  // anchors of this part
-    for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step) n_mine += min(LS_ANCHORS, a1 - ag);
-    n_cand += (unsigned long long)len * n_mine;
-    if (len == 0) {  // no neighbour MDs: no LS (and no shared memory touched)
-      for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step)
-        if (ag + lane < min(ag + LS_ANCHORS, a1)) {
-          B.ls_cnt[ag + lane] = 0;
-          B.mask_off[ag + lane] = NONE;
-        }
-      return;
-    }
-    if (len > list_cap) {  // recorded, so that the host can give later runs a longer list
-      if (lane == 0) atomicMax(&B.hdr->ls_maxlen, len);
-      for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step)
-        for (uint32_t a = ag; a < min(ag + LS_ANCHORS, a1); a++) ls_md_join<false>(C, G, B, a, ev, A);
-      return;
-    }
     const float rnext = G.rnext[A];
     const bool a_barrel = G.subdet[A] == 0;
     const float4 t_a = G.modc[A];  // every MD of A carries its module's tolerances
-    {
+    for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step) {
+      const uint32_t na = min(LS_ANCHORS, a1 - ag);
+      // The group's anchors span [psi_lo, psi_hi] in pseudo-angle (a module's MDs are in
+      // azimuth order), and a candidate on module B can pass the bending cut with one of them
+      // only within the edge's half-width (|d psi| <= |d phi|): the list takes, from each
+      // connected module, the MDs inside that window (one or, across psi = 0, two runs of its
+      // sorted MDs), in module and MD order.
+      const float psi_lo = B.md_psi[ag], psi_hi = B.md_psi[ag + na - 1];
+      // flattened neighbour list; disk modules have the highest ids, so the disk entries are
+      // normally a suffix [t_disk, len) of the list (checked: otherwise each candidate's
+      // module is looked up)
+      uint32_t len = 0, t_disk = NONE;
+      bool suffix = true;
+      for (uint32_t g0 = 0; g0 < nb; g0 += 32) {
+        uint32_t s1 = 0, e1 = 0, s2 = 0, e2 = 0, c = 0;
+        bool disk = false;
+        if (g0 + lane < nb) {
+          const uint32_t Bm = G.conn[nb0 + g0 + lane];
+          const uint32_t uu = ubase + Bm;
+          const uint32_t b = B.md_off[uu], end = B.md_off[uu + 1];
+          disk = G.subdet[Bm] == 1;
+          const float w = G.conn_dpsi[nb0 + g0 + lane];
+          const float lo = psi_lo - w, hi = psi_hi + w;
+          if (hi - lo >= 4.0f) {  // the whole circle
+            s1 = b; e1 = end; s2 = e2 = end;
+          } else {
+            // window [lo, hi], or [lo + 4, 4) and [0, hi] below 0, or [lo, 4) and [0, hi - 4]
+            // above 4: count the sorted MDs below each edge
+            const float cut_lo = lo < 0.0f ? lo + 4.0f : lo;
+            const float cut_hi = hi >= 4.0f ? hi - 4.0f : hi;
+            uint32_t n_lo = 0, n_hi = 0;  // MDs with psi < cut_lo, with psi <= cut_hi
+            for (uint32_t i = b; i < end; i++) {
+              const float p = B.md_psi[i];
+              n_lo += p < cut_lo;
+              n_hi += p <= cut_hi;
+            }
+            if (lo < 0.0f || hi >= 4.0f) {  // two runs: [b, b + n_hi) and [b + n_lo, end)
+              s1 = b; e1 = b + n_hi;
+              s2 = max(b + n_lo, e1); e2 = end;
+            } else {
+              s1 = b + n_lo; e1 = max(b + n_hi, s1); s2 = e2 = end;
+            }
+          }
+          c = (e1 - s1) + (e2 - s2);
+        }
+        const uint32_t incl = warp_incl_scan(c);
+        const uint32_t o = len + incl - c;
+        uint32_t wpos = o;
+        for (uint32_t k = s1; k < e1; k++, wpos++)
+          if (wpos < list_cap) list[wpos] = k;
+        for (uint32_t k = s2; k < e2; k++, wpos++)
+          if (wpos < list_cap) list[wpos] = k;
+        const uint32_t dm = __ballot_sync(FULL, disk && c > 0), bm = __ballot_sync(FULL, !disk && c > 0);
+        if (t_disk != NONE) {
+          if (bm) suffix = false;
+        } else if (dm) {
+          const uint32_t fd = __ffs(dm) - 1;
+          if (fd < 31 && (bm >> (fd + 1))) suffix = false;
+          t_disk = __shfl_sync(FULL, o, fd);
+        }
+        len += __shfl_sync(FULL, incl, 31);
+      }
+      if (t_disk == NONE) t_disk = len;
+      __syncwarp();
+      n_cand += (unsigned long long)len * na;
+      if (len == 0) {  // no neighbour MD in the window: no LS
+        if (lane < na) {
+          B.ls_cnt[ag + lane] = 0;
+          B.mask_off[ag + lane] = NONE;
+        }
+        continue;
+      }
+      if (len > list_cap) {  // recorded, so that the host can give later runs a longer list
+        if (lane == 0) atomicMax(&B.hdr->ls_maxlen, len);
+        for (uint32_t a = ag; a < ag + na; a++) ls_md_join<false>(C, G, B, a, ev, A);
+        continue;
+      }
       // Up to LS_ANCHORS MDs of A per walk over the list: their points are staged in shared
       // memory (read as broadcasts) and each candidate loaded is tested against all of
       // them, each anchor with its own pass bits; the head's survivors are queued as
       // list position | anchor << 11 and the tail runs on 32 of them at a time.
       const uint32_t nwords = (len + 31) >> 5;
-      // record of MD a: [count, partner MDs in list order] -- the fill pass only copies it
-      // (list positions below 1024 in words 0-31, one per lane; beyond, words 32-63)
       auto record = [&](uint32_t a, const uint32_t* bits) {
         const uint32_t word = lane < nwords ? bits[lane] : 0u;
         const uint32_t wcnt = __popc(word);
@@ -1029,49 +1057,45 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
           B.ls_cnt[a] = count;
         }
       };
-      for (uint32_t ag = a0 + part * LS_ANCHORS; ag < a1; ag += step) {
-        const uint32_t na = min(LS_ANCHORS, a1 - ag);
-        if (lane < na) {
-          anc[2 * lane] = B.md_pt[2 * (size_t)(ag + lane)];
-          anc[2 * lane + 1] = B.md_dir4[ag + lane];
-        }
-        for (uint32_t w = lane; w < nwords; w += 32)  // only the words the list covers are used
-          for (uint32_t k = 0; k < na; k++) pbits[k * pw + w] = 0;
-        uint32_t qh = 0, qt = 0;  // ring head and tail (free-running)
-        auto tail = [&](uint32_t e) {
-          const uint32_t k = e >> 11, q = e & 2047u;
-          const uint32_t j = list[q];
-          const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
+      if (lane < na) {
+        anc[2 * lane] = B.md_pt[2 * (size_t)(ag + lane)];
+        anc[2 * lane + 1] = B.md_dir4[ag + lane];
+      }
+      for (uint32_t w = lane; w < nwords; w += 32)  // only the words the list covers are used
+        for (uint32_t k = 0; k < na; k++) pbits[k * pw + w] = 0;
+      uint32_t qh = 0, qt = 0;  // ring head and tail (free-running)
+      auto tail = [&](uint32_t e) {
+        const uint32_t k = e >> 11, q = e & 2047u;
+        const uint32_t j = list[q];
+        const bool exit = a_barrel && (suffix ? q >= t_disk : G.subdet[B.md_unit[j] - ubase] == 1);
+        const PointTol pa{anc[2 * k], t_a};
+        if (ls_tail_k(C, G, B, pa, anc[2 * k + 1], rnext, exit, j))
+          atomicOr(&pbits[k * pw + (q >> 5)], 1u << (q & 31));
+      };
+      __syncwarp();
+      for (uint32_t t0 = 0; t0 < len; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        const uint32_t j = t < len ? list[t] : a0;  // a0: any valid MD for idle lanes
+        const PointTol pb{__ldg(&B.md_pt[2 * (size_t)j]), __ldg(&B.md_pt[2 * (size_t)j + 1])};
+        for (uint32_t k = 0; k < na; k++) {
           const PointTol pa{anc[2 * k], t_a};
-          if (ls_tail_k(C, G, B, pa, anc[2 * k + 1], rnext, exit, j))
-            atomicOr(&pbits[k * pw + (q >> 5)], 1u << (q & 31));
-        };
-        __syncwarp();
-        for (uint32_t t0 = 0; t0 < len; t0 += 32) {
-          const uint32_t t = t0 + lane;
-          const uint32_t j = t < len ? list[t] : a0;  // a0: any valid MD for idle lanes
-          const PointTol pb{__ldg(&B.md_pt[2 * (size_t)j]), __ldg(&B.md_pt[2 * (size_t)j + 1])};
-          for (uint32_t k = 0; k < na; k++) {
-            const PointTol pa{anc[2 * k], t_a};
-            const bool h = t < len && ls_head_pt(C, pa, pb);
-            const uint32_t hb = __ballot_sync(FULL, h);
-            if (h) queue[(qt + __popc(hb & lt)) & (LS_RING - 1)] = t | (k << 11);
-            qt += __popc(hb);
-            if (qt - qh >= 32) {
-              __syncwarp();
-              tail(queue[(qh + lane) & (LS_RING - 1)]);
-              qh += 32;
-            }
+          const bool h = t < len && ls_head_pt(C, pa, pb);
+          const uint32_t hb = __ballot_sync(FULL, h);
+          if (h) queue[(qt + __popc(hb & lt)) & (LS_RING - 1)] = t | (k << 11);
+          qt += __popc(hb);
+          if (qt - qh >= 32) {
+            __syncwarp();
+            tail(queue[(qh + lane) & (LS_RING - 1)]);
+            qh += 32;
           }
         }
-        __syncwarp();
-        if (lane < qt - qh) tail(queue[(qh + lane) & (LS_RING - 1)]);
-        __syncwarp();
-        for (uint32_t k = 0; k < na; k++) record(ag + k, pbits + k * pw);
-        __syncwarp();  // anchors, pbits and the queue are reused by the next group
       }
+      __syncwarp();
+      if (lane < qt - qh) tail(queue[(qh + lane) & (LS_RING - 1)]);
+      __syncwarp();
+      for (uint32_t k = 0; k < na; k++) record(ag + k, pbits + k * pw);
+      __syncwarp();  // the list, anchors, pbits and the queue are reused by the next group
     }
-    __syncwarp();  // the list is rewritten by the next unit
   };
   // module-major order (unit k = part k % nsplit of module k' / n_ev of event k' % n_ev, k' =
   // k / nsplit) taken dynamically: module ids start with the innermost, busiest layers, so

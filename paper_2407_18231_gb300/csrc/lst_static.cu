@@ -80,6 +80,7 @@ constexpr size_t carve_layout(Sink& c, BufView& B) {
   c.take(B.sen_cnt, 2 * MAX_MODULES + 1);
   c.take(B.sen_off, 2 * MAX_MODULES + 1);
   c.take(B.hit_tmp, MAX_HITS);
+  c.take(B.hit_psi, MAX_HITS);
   c.take(B.hit_ev, MAX_HITS);
   c.take(B.hit_idx, MAX_HITS);
   c.take(B.hit4, MAX_HITS);
@@ -95,6 +96,7 @@ constexpr size_t carve_layout(Sink& c, BufView& B) {
   c.take(B.md_pt, 2 * MAX_MD);
   c.take(B.md_up4, MAX_MD);
   c.take(B.md_dir4, MAX_MD);
+  c.take(B.md_psi, MAX_MD);
   c.take(B.ls_cnt, MAX_MD);
   c.take(B.ls_off, MAX_MD + 1);
   c.take(B.ls_in, MAX_LS);
