@@ -541,6 +541,10 @@ struct Pipeline {
   // single-pass scan's tickets past its last chunk, so its blocks wait for chunk totals that
   // nothing publishes until their polls run out (LST_TEST_STALL_SCAN at context creation)
   uint32_t stall_scan_runs = 0;
+  // test hook for the LS partner-list arena: when set, the arena holds this many words and
+  // never grows, so that most anchors find it exhausted and are joined again by the fill
+  // pass (LST_TEST_MASK_WORDS at context creation)
+  uint32_t test_mask_words = 0;
   // host staging (pinned)
   Hdr* h_hdr = nullptr;        // header to upload
   Hdr* h_hdr_out = nullptr;    // header read back
@@ -681,6 +685,7 @@ struct Pipeline {
   // LS partner lists: about two words per hit suffice for PU200-like events; runs that
   // need more fall back to joining again and the next run gets the learned size
   uint32_t mask_words(const Caps& c) const {
+    if (test_mask_words) return test_mask_words;
     return std::max<uint32_t>(cap_mask, (uint32_t)std::min<uint64_t>(4000000000ull, 4ull * c.hits + 65536));
   }
 
@@ -815,7 +820,7 @@ struct Pipeline {
   // cap allows -- a smaller arena only means more anchors joined again by the fill pass.
   void learn_mask(const Hdr& h) {
     const uint64_t used = std::min<uint64_t>(h.mask_used[1], cap_mask) + h.mask_used[2];
-    if (used <= cap_mask) return;
+    if (used <= cap_mask || test_mask_words) return;
     uint64_t want = std::min<uint64_t>(4000000000ull, used * 5 / 4 + 65536);
     if (byte_cap) {
       const uint64_t others = dev_bytes - mask.bytes;
@@ -1383,6 +1388,7 @@ lst_status lst_load_geometry(const lst_module_desc* mods, uint32_t n_mods, const
     c->geo.upload_tables();
     c->main.init(&c->geo, c->cfg, c->n_sm);
     if (const char* v = std::getenv("LST_TEST_STALL_SCAN")) c->main.stall_scan_runs = (uint32_t)std::atoi(v);
+    if (const char* v = std::getenv("LST_TEST_MASK_WORDS")) c->main.test_mask_words = (uint32_t)std::atoi(v);
     // the allocation-free entry point's array and kernels, loaded now so that its calls allocate nothing
     CK(static_scratch_prepare(c->device));
     return LST_OK;

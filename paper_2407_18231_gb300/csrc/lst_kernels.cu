@@ -999,6 +999,40 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
       // them, each anchor with its own pass bits; the head's survivors are queued as
       // list position | anchor << 11 and the tail runs on 32 of them at a time.
       const uint32_t nwords = (len + 31) >> 5;
+      // `need` words of the scratch arena from this warp's piece (warp-uniform; NONE when the
+      // arena is exhausted: the anchors are then joined again by the fill pass)
+      auto alloc = [&](uint32_t need) {
+        uint32_t mb = NONE;
+        if (lane == 0) {
+          if (wa.end - wa.cur < need) {
+            if (wa.full) {
+              // the arena is exhausted: record only what this list needs ([2]), so the
+              // host sizes the next arena from real demand, not from repeated requests
+              atomicAdd(&B.hdr->mask_used[2], need);
+            } else {
+              const uint32_t grab = need > grab_min ? need : grab_min;
+              const uint32_t b0 = atomicAdd(&B.hdr->mask_used[1], grab);
+              if (b0 < B.cap_mask && grab <= B.cap_mask - b0) {
+                wa.cur = b0;
+                wa.end = b0 + grab;
+              } else {
+                wa.cur = wa.end = 0;
+                wa.full = true;
+                atomicAdd(&B.hdr->mask_used[2], need);
+              }
+            }
+          }
+          if (wa.end - wa.cur >= need) {
+            mb = wa.cur;
+            wa.cur += need;
+          }
+        }
+        wa.cur = __shfl_sync(FULL, wa.cur, 0);
+        wa.end = __shfl_sync(FULL, wa.end, 0);
+        wa.full = __shfl_sync(FULL, (uint32_t)wa.full, 0) != 0;
+        return __shfl_sync(FULL, mb, 0);
+      };
+      // One anchor's partner list: [count, list entries of its pass bits in list order].
       auto record = [&](uint32_t a, const uint32_t* bits) {
         const uint32_t word = lane < nwords ? bits[lane] : 0u;
         const uint32_t wcnt = __popc(word);
@@ -1014,36 +1048,7 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
         }
         uint32_t mbase = NONE;
         if (count > 0) {
-          const uint32_t need = 1 + count;
-          uint32_t mb = NONE;
-          if (lane == 0) {
-            if (wa.end - wa.cur < need) {
-              if (wa.full) {
-                // the arena is exhausted: record only what this list needs ([2]), so the
-                // host sizes the next arena from real demand, not from repeated requests
-                atomicAdd(&B.hdr->mask_used[2], need);
-              } else {
-                const uint32_t grab = need > grab_min ? need : grab_min;
-                const uint32_t b0 = atomicAdd(&B.hdr->mask_used[1], grab);
-                if (b0 < B.cap_mask && grab <= B.cap_mask - b0) {
-                  wa.cur = b0;
-                  wa.end = b0 + grab;
-                } else {
-                  wa.cur = wa.end = 0;
-                  wa.full = true;
-                  atomicAdd(&B.hdr->mask_used[2], need);
-                }
-              }
-            }
-            if (wa.end - wa.cur >= need) {
-              mb = wa.cur;
-              wa.cur += need;
-            }
-          }
-          mbase = __shfl_sync(FULL, mb, 0);
-          wa.cur = __shfl_sync(FULL, wa.cur, 0);
-          wa.end = __shfl_sync(FULL, wa.end, 0);
-          wa.full = __shfl_sync(FULL, (uint32_t)wa.full, 0) != 0;
+          mbase = alloc(1 + count);
           if (mbase != NONE) {
             if (lane == 0) B.mask[mbase] = count;
             uint32_t pos = mbase + 1 + wincl - wcnt;
@@ -1055,6 +1060,36 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
         if (lane == 0) {
           B.mask_off[a] = mbase;
           B.ls_cnt[a] = count;
+        }
+      };
+      // All na anchors' lists at once when their pass-bit words fit the warp (lane = anchor k
+      // x nwords + word w): one scan and one arena request for the group, the lists laid out
+      // one after another in anchor order, each as record() lays it out.
+      auto record_group = [&]() {
+        const uint32_t k = lane / nwords, w = lane - k * nwords;
+        const uint32_t first = k * nwords;  // the lane holding anchor k's first word
+        const uint32_t word = k < na ? pbits[k * pw + w] : 0u;
+        const uint32_t c = __popc(word);
+        const uint32_t incl = warp_incl_scan(c);
+        const uint32_t excl = incl - c;
+        const uint32_t fl = k < na ? first : 0u, ll = k < na ? first + nwords - 1 : 0u;  // <= 31
+        const uint32_t first_excl = __shfl_sync(FULL, excl, fl);
+        const uint32_t last_incl = __shfl_sync(FULL, incl, ll);
+        const uint32_t count = k < na ? last_incl - first_excl : 0u;
+        // anchors with partners, marked at their first lane: each takes one count word
+        const uint32_t heads = __ballot_sync(FULL, k < na && w == 0 && count > 0);
+        const uint32_t before = __popc(heads & ((1u << fl) - 1u));  // heads of anchors < k
+        const uint32_t total = __shfl_sync(FULL, incl, 31) + __popc(heads);
+        const uint32_t mbase = total ? alloc(total) : NONE;
+        if (mbase != NONE && count > 0) {
+          const uint32_t hk = mbase + first_excl + before;  // anchor k's count word
+          if (w == 0) B.mask[hk] = count;
+          uint32_t pos = hk + 1 + (excl - first_excl);
+          for (uint32_t b = word; b; b &= b - 1u) B.mask[pos++] = list[(w << 5) + __ffs(b) - 1];
+        }
+        if (k < na && w == 0) {
+          B.mask_off[ag + k] = count > 0 ? (mbase != NONE ? mbase + first_excl + before : NONE) : NONE;
+          B.ls_cnt[ag + k] = count;
         }
       };
       if (lane < na) {
@@ -1093,7 +1128,11 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
       __syncwarp();
       if (lane < qt - qh) tail(queue[(qh + lane) & (LS_RING - 1)]);
       __syncwarp();
-      for (uint32_t k = 0; k < na; k++) record(ag + k, pbits + k * pw);
+      if (na * nwords <= 32) {
+        record_group();
+      } else {
+        for (uint32_t k = 0; k < na; k++) record(ag + k, pbits + k * pw);
+      }
       __syncwarp();  // the list, anchors, pbits and the queue are reused by the next group
     }
   };

@@ -92,3 +92,24 @@ def test_bounded_scan_wait_reports_timeout(full_geom, monkeypatch):
     ora = oracle.run(oracle.Geometry(full_geom.modules), ev)
     assert np.array_equal(tc["ot"], ora["tc_ot"]) and tc["score"].tobytes() == ora["tc_score"].tobytes()
     s.close()
+
+
+def test_exhausted_partner_arena_rejoins_anchors(full_geom, ora_full, monkeypatch):
+    """The LS count pass stores each anchor group's partner lists in a scratch arena; an
+    anchor whose lists find it exhausted is joined again by the fill pass.  The test hook
+    holds the arena at 4096 words and never lets it grow, so nearly every anchor of these
+    runs takes that path: a single event, a batch, and the same batch again all equal the
+    oracle list by list."""
+    import oracle
+    from test_gpu_parity import compare
+    monkeypatch.setenv("LST_TEST_MASK_WORDS", "4096")
+    s = lst.Session(full_geom.modules, keep_objects=True)
+    monkeypatch.delenv("LST_TEST_MASK_WORDS")
+    evs = [S.make_event("pu200", 47 + i, n_tracks=2000 + 1000 * i, with_pls=True) for i in range(3)]
+    refs = [oracle.run(ora_full, ev) for ev in evs]
+    compare(s, s.run_event(evs[0]), refs[0], evs[0], "arena single event")
+    for rep in range(2):
+        for i, (ev, rid) in enumerate(zip(evs, s.run_batch(evs))):
+            compare(s, rid, refs[i], ev, f"arena batch {rep} event {i}")
+            s.release(rid)
+    s.close()
