@@ -869,6 +869,7 @@ static_assert(LS_LIST_MAX <= 64 * 32, "two pass-bit words per lane");
 constexpr uint32_t LS_ANCHORS = 8;     // MDs of a module tested per walk over its list
 constexpr uint32_t LS_SPLIT = 4;       // units per module in batches of fewer than 8 events
 constexpr uint32_t LS_SPLIT_MIN_HITS = 16384;  // ... that hold at least this many hits
+constexpr uint32_t LS_DENSE_HITS = 100000;      // hits per event above which units go one at a time
 constexpr uint32_t LS_RING = 64;       // ring of queued (list position, anchor) entries (> 31 + 32)
 // per warp after the list: the ring, one pass bit per list position for each anchor, and
 // the anchors (lower hit and direction terms: two float4 each; the tolerances are the
@@ -907,6 +908,8 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
   // g mod LS_SPLIT), each walking the module's list for its own groups only.  (A sparse
   // batch would only multiply the work-counter atomics of its mostly empty modules.)
   const uint32_t nsplit = (n_ev < 8 && H->n_hits >= LS_SPLIT_MIN_HITS) ? LS_SPLIT : 1u;
+  // events denser than LS_DENSE_HITS hits: units one at a time (their costs differ more)
+  const bool dense = H->n_hits >= (uint64_t)LS_DENSE_HITS * n_ev;
   const uint32_t step = nsplit * LS_ANCHORS;
   auto unit = [&](const uint32_t u, const uint32_t part) {
     const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
@@ -1138,8 +1141,9 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
   };
   // module-major order (unit k = part k % nsplit of module k' / n_ev of event k' % n_ev, k' =
   // k / nsplit) taken dynamically: module ids start with the innermost, busiest layers, so
-  // expensive units go first; the parts of a module go to different warps (grain 1)
-  DYN_LOOP(k, &B.hdr->work[W_LS], nu * nsplit, nsplit > 1 ? 1u : 2u) {
+  // expensive units go first; the parts of a module go to different warps (grain 1), and so
+  // do the units of dense events, whose busiest modules cost many times the rest
+  DYN_LOOP(k, &B.hdr->work[W_LS], nu * nsplit, (nsplit > 1 || dense) ? 1u : 2u) {
     const uint32_t k1 = k / nsplit;
     unit((k1 % n_ev) * G.nm + k1 / n_ev, k - k1 * nsplit);
   }
