@@ -56,6 +56,18 @@ __device__ __forceinline__ uint32_t owner_lane(uint32_t incl, uint32_t cand) {
   return o;
 }
 
+// Division by a divisor fixed for a launch, for n + d < 2^32: the multiply-high estimate by
+// m = ceil(2^32 / d) is floor(n / d) or one more, and one comparison corrects it.
+struct FastDiv {
+  uint32_t d, m;
+  __device__ explicit FastDiv(uint32_t d_) : d(d_), m(d_ > 1 ? (uint32_t)((0x100000000ull + d_ - 1) / d_) : 0u) {}
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    if (d <= 1) return n;
+    const uint32_t q = __umulhi(n, m);
+    return q * d > n ? q - 1 : q;
+  }
+};
+
 // Per-warp bump allocator over a scratch arena (one global atomic per 1024+ words).
 struct WarpAlloc {
   uint32_t cur = 0, end = 0;  // warp-uniform
@@ -911,11 +923,11 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
   // events denser than LS_DENSE_HITS hits: units one at a time (their costs differ more)
   const bool dense = H->n_hits >= (uint64_t)LS_DENSE_HITS * n_ev;
   const uint32_t step = nsplit * LS_ANCHORS;
-  auto unit = [&](const uint32_t u, const uint32_t part) {
-    const uint32_t a0 = B.md_off[u], a1 = B.md_off[u + 1];
-    if (a0 + part * LS_ANCHORS >= a1) return;  // no anchor group in this part
-    const uint32_t ev = u / G.nm, A = u - ev * G.nm;
+  const FastDiv by_ev(n_ev);
+  auto unit = [&](const uint32_t ev, const uint32_t A, const uint32_t part) {
     const uint32_t ubase = ev * G.nm;
+    const uint32_t a0 = B.md_off[ubase + A], a1 = B.md_off[ubase + A + 1];
+    if (a0 + part * LS_ANCHORS >= a1) return;  // no anchor group in this part
     const uint32_t nb0 = G.conn_off[A], nb = G.conn_off[A + 1] - nb0;
     const float rnext = G.rnext[A];
     const bool a_barrel = G.subdet[A] == 0;
@@ -1144,8 +1156,9 @@ __global__ void __launch_bounds__(512) k_ls_count(MethodConst C, GeoView G, BufV
   // expensive units go first; the parts of a module go to different warps (grain 1), and so
   // do the units of dense events, whose busiest modules cost many times the rest
   DYN_LOOP(k, &B.hdr->work[W_LS], nu * nsplit, (nsplit > 1 || dense) ? 1u : 2u) {
-    const uint32_t k1 = k / nsplit;
-    unit((k1 % n_ev) * G.nm + k1 / n_ev, k - k1 * nsplit);
+    const uint32_t k1 = nsplit > 1 ? k / LS_SPLIT : k;
+    const uint32_t A = by_ev.div(k1);
+    unit(k1 - A * n_ev, A, k - k1 * nsplit);
   }
   if (lane == 0 && n_cand) atomicAdd(&B.hdr->ls_cand, n_cand);
 }
