@@ -16,6 +16,7 @@ constexpr uint32_t PLS_ITEMS = PLS_MD_CAP > (uint32_t)MAX_CAND ? PLS_MD_CAP : (u
 
 constexpr int N_SCAN_SLOTS = 16;          // scans of one run that can take the single-pass form
 constexpr uint32_t SCAN_MID_BLOCKS = 32;   // blocks of a single-pass scan
+constexpr uint32_t SCAN_LARGE_CHUNK = 8192; // elements per block of a large single-pass scan
 
 // Totals written by the scans into the batch header.
 enum Total : int {
@@ -43,7 +44,8 @@ struct Hdr {
   uint32_t tot[N_TOTALS];
   uint32_t err;
   uint32_t ls_maxlen;  // LS count pass: the longest neighbour list beyond the launch's list cap
-  uint32_t pad2[2];
+  uint32_t scan_epoch;  // this run's number (1, 2, ...): tags the chunk states of the large scans
+  uint32_t pad2;
   uint32_t mask_used[8];  // LS partner-list arena: [1] words handed out in pieces (may pass the
                           // arena's end), [2] words of the lists that found it exhausted
   unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)
@@ -130,14 +132,15 @@ struct BufView {
   // track candidates
   uint32_t *tc_ev_off;
   void *tc;  // lst_tc records
-  // scan scratch
-  uint32_t *scan_part;
-  uint32_t *scan_part2;  // block partials of the side stream's scan
   // join scratch: chunk ballots of the count passes, and each unit's slice of them
   // scratch arena: the LS count pass's partner lists [count, partner MDs] (mask_off: per
   // anchor MD its list's offset, or NONE when the fill pass must join it again)
   uint32_t *mask, *mask_off;
   uint32_t cap_mask;
+  // single-pass scans of large arrays: scan_chunks chunk states per scan slot (null where no
+  // scan is large)
+  unsigned long long* scan_state;
+  uint32_t scan_chunks;
 };
 
 typedef void (*MarkFn)(void* arg, int kernel_name);
@@ -155,7 +158,6 @@ struct SideBranch {
 struct Launch {
   uint32_t grid;   // persistent grid (blocks)
   uint32_t block;  // threads per block
-  uint32_t scan_grid;
   uint32_t ls_list_cap;  // LS: neighbour MDs staged per warp (0: per-MD join everywhere)
   const T5Mlp* t5_mlp = nullptr;  // learned T5 selection (host copy, passed by value), null: the cuts
 };

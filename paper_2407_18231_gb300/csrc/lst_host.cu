@@ -533,7 +533,9 @@ struct Pipeline {
   DevBuf pt5_xcnt, pt5_xoff, pt5_xmask, pt5_off, pt5_pls, pt5_obj, pt5_score;
   DevBuf c5_cnt, c5_off, c5_list, c3_cnt, c3_off, c3_list, ct_cnt, ct_off, ct_list;
   DevBuf alive5, alive3, alivet, plstc, cross3, crosst, sa5, sa3, sat, sap;
-  DevBuf tc_ev_off, tc, scan_part, scan_part2, mask, mask_off;
+  DevBuf tc_ev_off, tc, mask, mask_off, scan_state;
+  uint32_t scan_chunks = 1;  // chunk states per scan slot of the large single-pass scans
+  uint32_t epoch = 0;        // runs launched (tags the chunk states; 30 bits)
   uint32_t cap_mask = 0;
   uint64_t byte_cap = 0;  // 0: none; otherwise learn_mask keeps dev_bytes within it
   bool auto_list_cap = true;  // the LS list cap is the library's choice (learn may raise it)
@@ -586,7 +588,7 @@ struct Pipeline {
                               &pt5_xcnt, &pt5_xoff, &pt5_xmask, &pt5_off, &pt5_pls, &pt5_obj, &pt5_score, &c5_cnt, &c5_off, &c5_list,
                               &c3_cnt, &c3_off, &c3_list, &ct_cnt, &ct_off, &ct_list, &alive5, &alive3, &alivet,
                               &plstc, &cross3, &crosst, &sa5, &sa3, &sat, &sap, &tc_ev_off, &tc,
-                              &scan_part, &scan_part2, &mask, &mask_off};
+                              &mask, &mask_off, &scan_state};
     for (auto& b : t5_m) v.push_back(&b);
     return v;
   }
@@ -637,8 +639,6 @@ struct Pipeline {
     geo = g;
     C = method_constants();
     set_tuning(cfg, n_sm);
-    uint32_t sg = ((2u * (uint32_t)n_sm) + 31u) / 32u * 32u;
-    L.scan_grid = std::min<uint32_t>(sg, 1024u);
     CK(configure_kernels());
     CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -655,8 +655,6 @@ struct Pipeline {
     CK(cudaMallocHost((void**)&h_hdr, sizeof(Hdr)));
     CK(cudaMallocHost((void**)&h_hdr_out, sizeof(Hdr)));
     hdr.ensure(sizeof(Hdr), dev_bytes);
-    scan_part.ensure(4 * 1024 * sizeof(uint32_t), dev_bytes);  // up to four scans per launch
-    scan_part2.ensure(1024 * sizeof(uint32_t), dev_bytes);
   }
 
   template <typename T>
@@ -781,17 +779,36 @@ struct Pipeline {
     f(tc, std::max<size_t>(c.tc, 1) * sizeof(lst_tc));
     f(mask_off, std::max<size_t>(c.md, 1) * sizeof(uint32_t));
     f(mask, (size_t)mask_words(c) * sizeof(uint32_t));
+    f(scan_state, (size_t)N_SCAN_SLOTS * scan_chunks_for(c) * sizeof(unsigned long long));
+  }
+
+  // Chunks of the largest array a scan of the chain may hold at capacities c (the bound each
+  // scan is launched with), hence the chunk states one scan slot needs.
+  uint32_t scan_chunks_for(const Caps& c) const {
+    const uint64_t b = std::max<uint64_t>(
+        {(uint64_t)c.ev * 2 * geo->nm, c.hits, c.md, c.ls, c.t3, c.t5, c.pt3, c.pt5, (uint64_t)c.pls * PLS_ITEMS});
+    return (uint32_t)std::max<uint64_t>(1, (b + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK);
+  }
+
+  // Clears the chunk states (a new array may hold anything, and after 2^30 - 1 runs the tags
+  // repeat), ordered before whatever is launched next on s.
+  void clear_scan_state(cudaStream_t s) {
+    CK(cudaMemsetAsync(scan_state.p, 0, scan_state.bytes, s));
+    CK(cudaStreamSynchronize(s));
   }
 
   // Grow every buffer to the capacities in c (never shrinks).
   void ensure_caps(const Caps& c_in) {
     const Caps c = merged(c_in);
     const uint32_t words = mask_words(c);
+    const void* state_before = scan_state.p;
     for_buffers(c, [&](DevBuf& b, size_t bytes) {
       const size_t before = b.bytes;
       b.ensure(bytes, dev_bytes);
       if (b.bytes != before) graph_valid = false;
     });
+    scan_chunks = scan_chunks_for(c);
+    if (scan_state.p != state_before) clear_scan_state(stream);
     cap_mask = words;
     cap = c;
   }
@@ -915,8 +932,9 @@ struct Pipeline {
     v.alive5 = P32(alive5); v.alive3 = P32(alive3); v.alivet = P32(alivet); v.plstc = P32(plstc);
     v.cross3 = P32(cross3); v.crosst = P32(crosst);
     v.sa5 = P32(sa5); v.sa3 = P32(sa3); v.sat = P32(sat); v.sap = P32(sap);
-    v.tc_ev_off = P32(tc_ev_off); v.tc = tc.p; v.scan_part = P32(scan_part); v.scan_part2 = P32(scan_part2);
+    v.tc_ev_off = P32(tc_ev_off); v.tc = tc.p;
     v.mask = P32(mask); v.mask_off = P32(mask_off); v.cap_mask = cap_mask;
+    v.scan_state = (unsigned long long*)scan_state.p; v.scan_chunks = scan_chunks;
 #undef P32
     return v;
   }
@@ -941,6 +959,11 @@ struct Pipeline {
     if (cap.ev < dev_inputs.n_ev || cap.hits < dev_inputs.n_hits || cap.pls < dev_inputs.n_pls || cap.ev == 0)
       throw StatusError{LST_ERR_INVALID_ARG, "internal: pipeline launched before its buffers were sized"};
     *h_hdr = dev_inputs;
+    if (epoch == 0x3FFFFFFFu) {  // the 30-bit run tags would repeat: start again from clear states
+      clear_scan_state(on ? on : stream);
+      epoch = 0;
+    }
+    h_hdr->scan_epoch = ++epoch;
     if (stall_scan_runs) {
       stall_scan_runs--;
       for (uint32_t& t : h_hdr->scan_ticket) t = SCAN_MID_BLOCKS;

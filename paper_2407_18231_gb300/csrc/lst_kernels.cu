@@ -245,72 +245,6 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sm, ui
   return r;
 }
 
-__global__ void k_scan_reduce(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul, const Hdr* H,
-                              uint32_t* part) {
-  pdl_wait();
-  if (H->err) return;
-  __shared__ uint32_t sm[33];
-  const uint32_t n = (*nptr) * mul;
-  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const uint32_t lo = blockIdx.x * chunk;
-  const uint32_t hi = min(n, lo + chunk);
-  uint32_t s = 0;
-  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += in[i];
-  uint32_t tot;
-  block_excl_scan(s, sm, tot);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-// Sum of the block partials before this block; the last block also publishes the total
-// (out[n], hdr->tot[tot_idx], the overflow bit when it exceeds cap).
-__device__ __forceinline__ uint32_t scan_carry(const uint32_t* part, uint32_t* sm, uint32_t n, uint32_t* out, Hdr* H,
-                                               int tot_idx, uint32_t cap) {
-  uint32_t v = 0;
-  for (uint32_t i = threadIdx.x; i < blockIdx.x; i += blockDim.x) v += part[i];
-  uint32_t carry;
-  block_excl_scan(v, sm, carry);
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-    const uint32_t tot = carry + part[blockIdx.x];
-    out[n] = tot;
-    if (tot_idx >= 0) {
-      H->tot[tot_idx] = tot;
-      if (tot > cap) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + tot_idx));
-    }
-  }
-  return carry;
-}
-
-__global__ void k_scan_apply(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul, Hdr* H,
-                             const uint32_t* part, uint32_t* __restrict__ out, int tot_idx, uint32_t cap) {
-  pdl_wait();
-  if (H->err) return;
-  __shared__ uint32_t sm[33];
-  const uint32_t n = (*nptr) * mul;
-  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const uint32_t lo = blockIdx.x * chunk;
-  const uint32_t hi = min(n, lo + chunk);
-  uint32_t carry = scan_carry(part, sm, n, out, H, tot_idx, cap);
-  const uint32_t tile = blockDim.x * 4;
-  for (uint32_t t = lo; t < hi; t += tile) {
-    const uint32_t i0 = t + threadIdx.x * 4;
-    uint32_t v[4];
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      v[k] = (i0 + k < hi) ? in[i0 + k] : 0u;
-      s += v[k];
-    }
-    uint32_t tot;
-    uint32_t ex = block_excl_scan(s, sm, tot) + carry;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      if (i0 + k < hi) out[i0 + k] = ex;
-      ex += v[k];
-    }
-    carry += tot;
-  }
-}
-
 // One block scans a whole array when the array's capacity is at most SCAN_SMALL_MAX (the
 // lists of a small event): tiles of 16 elements per thread with a running carry, the same
 // outputs as k_scan_reduce + k_scan_apply (out[0..n), out[n] = total, the header total and
@@ -432,6 +366,118 @@ __global__ void __launch_bounds__(1024) k_scan_mid(const uint32_t* __restrict__ 
   scan_mid_body(in, (*nptr) * mul, out, H, tot_idx, cap, slot, sm);
 }
 
+// Large arrays (capacity above SCAN_MID_MAX: the lists of a batch): a single pass with one
+// chunk of SCAN_LARGE_CHUNK elements (1024 threads x 8) per block.  A block takes a ticket
+// when it starts (its chunk, so chunks are handed out in start order), publishes its chunk's
+// total at once, then looks back over the chunks before its own, 32 at a time, adding their
+// totals until it meets one that has published its inclusive prefix, and publishes its own
+// (decoupled look-back).  A chunk state is [run number | flag | value]: states of earlier
+// runs read as not yet written, so the state array is never cleared between runs.  A block
+// waits only for blocks that started before it, and every wait is bounded
+// (SCAN_WAIT_LIMIT polls, then ERR_WAIT, the wait taken as an inclusive prefix of 0).
+constexpr unsigned long long ST_AGG = 1ull << 32, ST_INCL = 2ull << 32, ST_FLAGS = 3ull << 32;
+constexpr uint32_t SCAN_LARGE_PER_THREAD = SCAN_LARGE_CHUNK / 1024;
+static_assert(SCAN_LARGE_PER_THREAD == 8, "two 16-byte loads and stores per thread");
+__device__ __forceinline__ void scan_large_body(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ out,
+                                                Hdr* H, int tot_idx, uint32_t cap, uint32_t slot, const BufView& B,
+                                                uint32_t* sm) {
+  if (threadIdx.x == 0) sm[33] = atomicAdd(&H->scan_ticket[slot], 1u);
+  __syncthreads();
+  const uint32_t b = sm[33];
+  const uint32_t nch = max(1u, (n + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK);  // chunk 0 also when n = 0
+  if (b >= nch) return;  // (block-uniform) a block past the last chunk
+  if (b >= B.scan_chunks || B.scan_state == nullptr) {  // cannot happen: the states are sized from the capacities
+    if (threadIdx.x == 0) atomicOr(&H->err, ERR_WAIT);
+    return;
+  }
+  unsigned long long* st = B.scan_state + (size_t)slot * B.scan_chunks;
+  const unsigned long long tag = (unsigned long long)(H->scan_epoch & 0x3FFFFFFFu) << 34;
+  const uint32_t lo = b * SCAN_LARGE_CHUNK, hi = min(n, lo + SCAN_LARGE_CHUNK);
+  const uint32_t i0 = lo + threadIdx.x * SCAN_LARGE_PER_THREAD;
+  const bool vec = i0 + SCAN_LARGE_PER_THREAD <= hi &&
+                   ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+  uint32_t v[SCAN_LARGE_PER_THREAD];
+  if (vec) {
+    const uint4 a = *reinterpret_cast<const uint4*>(in + i0), c = *reinterpret_cast<const uint4*>(in + i0 + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
+  } else {
+#pragma unroll
+    for (uint32_t k = 0; k < SCAN_LARGE_PER_THREAD; k++) v[k] = (i0 + k < hi) ? in[i0 + k] : 0u;
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < SCAN_LARGE_PER_THREAD; k++) s += v[k];
+  uint32_t tot;
+  uint32_t ex = block_excl_scan(s, sm, tot);
+  if (threadIdx.x < 32) {
+    const uint32_t lane = threadIdx.x;
+    uint32_t prefix = 0;
+    if (b > 0) {
+      if (lane == 0) atomicExch(&st[b], tag | ST_AGG | tot);
+      for (int32_t j = (int32_t)b - 1;; j -= 32) {  // warp-uniform
+        const int32_t idx = j - (int32_t)lane;
+        unsigned long long w = tag | ST_INCL;  // before chunk 0: an inclusive prefix of 0
+        if (idx >= 0) {
+          uint32_t it = 0;
+          for (; it < SCAN_WAIT_LIMIT; it++) {
+            w = atomicAdd(&st[idx], 0ull);
+            if ((w >> 34) == (tag >> 34) && (w & ST_FLAGS)) break;
+          }
+          if (it == SCAN_WAIT_LIMIT) {
+            atomicOr(&H->err, ERR_WAIT);
+            w = tag | ST_INCL;
+          }
+        }
+        const uint32_t im = __ballot_sync(FULL, (w & ST_FLAGS) == ST_INCL);
+        const uint32_t upto = im ? (uint32_t)__ffs(im) - 1u : 31u;  // the nearest inclusive prefix ends the walk
+        prefix += __reduce_add_sync(FULL, lane <= upto ? (uint32_t)w : 0u);
+        if (im) break;
+      }
+    }
+    if (lane == 0) {
+      atomicExch(&st[b], tag | ST_INCL | (uint32_t)(prefix + tot));
+      sm[34] = prefix;
+    }
+  }
+  __syncthreads();
+  const uint32_t carry = sm[34];
+  ex += carry;
+  if (vec) {
+    uint32_t o[SCAN_LARGE_PER_THREAD];
+#pragma unroll
+    for (uint32_t k = 0; k < SCAN_LARGE_PER_THREAD; k++) {
+      o[k] = ex;
+      ex += v[k];
+    }
+    *reinterpret_cast<uint4*>(out + i0) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4*>(out + i0 + 4) = make_uint4(o[4], o[5], o[6], o[7]);
+  } else {
+#pragma unroll
+    for (uint32_t k = 0; k < SCAN_LARGE_PER_THREAD; k++) {
+      if (i0 + k < hi) out[i0 + k] = ex;
+      ex += v[k];
+    }
+  }
+  if (b == nch - 1 && threadIdx.x == 0) {
+    const uint32_t total = carry + tot;
+    out[n] = total;
+    if (tot_idx >= 0) {
+      H->tot[tot_idx] = total;
+      if (total > cap) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + tot_idx));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_large(const uint32_t* __restrict__ in, const uint32_t* nptr,
+                                                     uint32_t mul, BufView B, uint32_t* __restrict__ out, int tot_idx,
+                                                     uint32_t cap, uint32_t slot) {
+  pdl_wait();
+  Hdr* H = B.hdr;
+  if (H->err) return;
+  __shared__ uint32_t sm[35];
+  scan_large_body(in, (*nptr) * mul, out, H, tot_idx, cap, slot, B, sm);
+}
+
 // Up to four independent scans in one launch (blockIdx.y picks the array).
 struct ScanJob {
   const uint32_t* in;
@@ -462,51 +508,14 @@ __global__ void __launch_bounds__(1024) k_scan_mid_multi(ScanJobs J, Hdr* H, uin
   scan_mid_body(q.in, *q.nptr, q.out, H, q.tot, q.cap, slot0 + blockIdx.y, sm);
 }
 
-__global__ void k_scan_reduce_multi(ScanJobs J, const Hdr* H, uint32_t* part) {
+// The single-pass scan of several large arrays (blockIdx.y picks the array and its slot).
+__global__ void __launch_bounds__(1024) k_scan_large_multi(ScanJobs J, BufView B, uint32_t slot0) {
   pdl_wait();
+  Hdr* H = B.hdr;
   if (H->err) return;
-  __shared__ uint32_t sm[33];
+  __shared__ uint32_t sm[35];
   const ScanJob& q = J.j[blockIdx.y];
-  const uint32_t n = *q.nptr;
-  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const uint32_t lo = blockIdx.x * chunk;
-  const uint32_t hi = min(n, lo + chunk);
-  uint32_t s = 0;
-  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += q.in[i];
-  uint32_t tot;
-  block_excl_scan(s, sm, tot);
-  if (threadIdx.x == 0) part[blockIdx.y * 1024 + blockIdx.x] = tot;
-}
-
-__global__ void k_scan_apply_multi(ScanJobs J, Hdr* H, const uint32_t* part) {
-  pdl_wait();
-  if (H->err) return;
-  __shared__ uint32_t sm[33];
-  const ScanJob& q = J.j[blockIdx.y];
-  const uint32_t n = *q.nptr;
-  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const uint32_t lo = blockIdx.x * chunk;
-  const uint32_t hi = min(n, lo + chunk);
-  uint32_t carry = scan_carry(part + blockIdx.y * 1024, sm, n, q.out, H, q.tot, q.cap);
-  const uint32_t tile = blockDim.x * 4;
-  for (uint32_t t = lo; t < hi; t += tile) {
-    const uint32_t i0 = t + threadIdx.x * 4;
-    uint32_t v[4];
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      v[k] = (i0 + k < hi) ? q.in[i0 + k] : 0u;
-      s += v[k];
-    }
-    uint32_t tot;
-    uint32_t ex = block_excl_scan(s, sm, tot) + carry;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      if (i0 + k < hi) q.out[i0 + k] = ex;
-      ex += v[k];
-    }
-    carry += tot;
-  }
+  scan_large_body(q.in, *q.nptr, q.out, H, q.tot, q.cap, slot0 + blockIdx.y, B, sm);
 }
 
 __global__ void k_zero(uint32_t* p, const uint32_t* nptr, uint32_t mul, uint32_t add) {
@@ -2537,7 +2546,7 @@ __global__ void k_tc_write(MethodConst C, GeoView G, BufView B) {
 // ------------------------------------------------------------------ host-side enqueue
 // Kernel names in launch order (profile mode records one CUDA event after each).
 const char* const kKernelNames[] = {
-    "zero_sensor_counts", "hits_count", "scan_reduce", "(unused)", "scan_apply", "hits_scatter", "hits_sort",
+    "zero_sensor_counts", "hits_count", "(unused)", "scan_large", "(unused)", "hits_scatter", "hits_sort",
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "(unused)", "md_lists_count", "md_lists_fill",
     "kill_pt5", "(unused)", "cross_pt3", "kill_pt3", "(unused)", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
@@ -2586,10 +2595,9 @@ static void scan(const BufView& B, const Launch& L, cudaStream_t s, const uint32
     mk(39);
     return;
   }
-  launch(k_scan_reduce, L.scan_grid, 512, 0, s, in, nptr, mul, B.hdr, B.scan_part);
-  mk(2);
-  launch(k_scan_apply, L.scan_grid, 512, 0, s, in, nptr, mul, B.hdr, B.scan_part, out, tot, cap);
-  mk(4);
+  launch(k_scan_large, (uint32_t)((bound + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK), 1024, 0, s, in, nptr, mul, B, out,
+         tot, cap, slot);
+  mk(3);
 }
 
 // pT3 item offsets and item -> pLS table.  May run on the side stream beside the main
@@ -2603,11 +2611,9 @@ static void pt3_items(const BufView& B, const Launch& L, cudaStream_t s, Marker&
            0xFFFFFFFFu, 5u);
     mk(39);
   } else {
-    launch(k_scan_reduce, L.scan_grid, 512, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2);
-    mk(2);
-    launch(k_scan_apply, L.scan_grid, 512, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.scan_part2, B.pt3_ioff,
-           T_PT3I, 0xFFFFFFFFu);
-    mk(4);
+    launch(k_scan_large, (B.cap_pls + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK, 1024, 0, s, B.pt3_icnt, &B.hdr->n_pls,
+           1, B, B.pt3_ioff, T_PT3I, 0xFFFFFFFFu, 5u);
+    mk(3);
   }
   launch(k_pt3_items, L.grid, 256, 0, s, B);
   mk(36);
@@ -2625,10 +2631,9 @@ static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const 
     mk(39);
     return;
   }
-  launch(k_scan_reduce_multi, dim3(L.scan_grid, n), 512, 0, s, J, B.hdr, B.scan_part);
-  mk(2);
-  launch(k_scan_apply_multi, dim3(L.scan_grid, n), 512, 0, s, J, B.hdr, B.scan_part);
-  mk(4);
+  launch(k_scan_large_multi, dim3((uint32_t)((bound + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK), n), 1024, 0, s, J, B,
+         slot0);
+  mk(3);
 }
 
 // Lets the LS count kernel take the shared memory of the largest block (512 threads) on the
@@ -2643,9 +2648,8 @@ cudaError_t configure_kernels() {
 // later launches allocate nothing for code or module data.
 cudaError_t preload_kernels() {
   const void* ks[] = {
-      (const void*)k_scan_reduce, (const void*)k_scan_apply, (const void*)k_scan_reduce_multi,
-      (const void*)k_scan_apply_multi, (const void*)k_scan_small, (const void*)k_scan_small_multi,
-      (const void*)k_scan_mid, (const void*)k_scan_mid_multi, (const void*)k_zero, (const void*)k_hits_count, (const void*)k_hits_scatter,
+      (const void*)k_scan_small, (const void*)k_scan_small_multi,
+      (const void*)k_scan_mid, (const void*)k_scan_mid_multi, (const void*)k_scan_large, (const void*)k_scan_large_multi, (const void*)k_zero, (const void*)k_hits_count, (const void*)k_hits_scatter,
       (const void*)k_hits_sort, (const void*)k_md_count, (const void*)k_md_fill, (const void*)k_ls_fill,
       (const void*)k_ls_count, (const void*)k_t3_count, (const void*)k_t3_fill, (const void*)k_t5_count,
       (const void*)k_t5_fill, (const void*)k_t5_count_mlp, (const void*)k_t5_fill_mlp, (const void*)k_pls_prep, (const void*)k_pls_sort, (const void*)k_md_box,

@@ -166,8 +166,6 @@ constexpr size_t carve_layout(Sink& c, BufView& B) {
   c.take(B.sat, MAX_T5 + 1);
   c.take(B.sap, MAX_PLS + 1);
   c.take(B.tc_ev_off, 2);
-  c.take(B.scan_part, 4 * 1024);  // partials of up to four scans per launch
-  c.take(B.scan_part2, 1024);
   c.take(B.mask_off, MAX_MD);
   B.cap_mask = MASK_WORDS;
   c.take(B.mask, MASK_WORDS);

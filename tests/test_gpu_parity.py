@@ -111,6 +111,17 @@ def test_batch_equals_oracle_per_event(sess_full, ora_full):
         assert sess_full.candidates(a).tobytes() == sess_full.candidates(b).tobytes()
 
 
+def test_dense_batch_parity(sess_full, ora_full):
+    """A batch of 8 events of more than 100 000 hits each: the LS count pass hands its units
+    out one at a time there (dense events), and every event of the batch equals the oracle."""
+    evs = [S.make_event("highocc", 60 + i, n_tracks=7000) for i in range(8)]
+    assert sum(e.n_hits for e in evs) >= 100_000 * len(evs)
+    ids = sess_full.run_batch(evs)
+    for i, (ev, rid) in enumerate(zip(evs, ids)):
+        compare(sess_full, rid, oracle.run(ora_full, ev), ev, f"dense batch event {i}")
+        sess_full.release(rid)
+
+
 def test_bench_workload_sampled_parity(sess_full, ora_full):
     # the benchmark's batch (PU200-like events with pixel seeds), 3 events checked in full
     evs = [S.make_event("pu200", i, with_pls=True) for i in range(16)]

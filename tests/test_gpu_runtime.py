@@ -113,3 +113,25 @@ def test_exhausted_partner_arena_rejoins_anchors(full_geom, ora_full, monkeypatc
             compare(s, rid, refs[i], ev, f"arena batch {rep} event {i}")
             s.release(rid)
     s.close()
+
+
+def test_bounded_large_scan_wait_reports_timeout(full_geom, ora_full, monkeypatch):
+    """The single-pass scans of a batch's lists (one block per 8192 elements) look back over
+    the chunks before their own, every wait bounded.  With the test hook, the first run's
+    tickets start past chunk 31, so the blocks wait for states that nothing writes: their
+    polls run out, the run returns LST_ERR_TIMEOUT, and the next run on the same context
+    equals the oracle."""
+    import oracle
+    from test_gpu_parity import compare
+    monkeypatch.setenv("LST_TEST_STALL_SCAN", "1")
+    s = lst.Session(full_geom.modules, keep_objects=True)
+    monkeypatch.delenv("LST_TEST_STALL_SCAN")
+    evs = [S.make_event("pu200", 70 + i, with_pls=True) for i in range(16)]
+    assert sum(e.n_hits for e in evs) > 32 * 8192  # the hit scan takes more than 32 chunks
+    with pytest.raises(lst.LstError) as e:
+        s.run_batch(evs)
+    assert e.value.status == -7 and "wait ran out" in str(e.value)
+    ids = s.run_batch(evs)
+    for i in (0, 15):
+        compare(s, ids[i], oracle.run(ora_full, evs[i]), evs[i], f"after the stalled run, event {i}")
+    s.close()
