@@ -122,6 +122,39 @@ def test_dense_batch_parity(sess_full, ora_full):
         sess_full.release(rid)
 
 
+def _first_hits(ev, n):
+    """The event's first n hits (no seeds): a valid event of exactly n hits."""
+    return E.Event(ev.x[:n].copy(), ev.y[:n].copy(), ev.z[:n].copy(), ev.det[:n].copy(), ev.sim[:n].copy(), ev.tracks)
+
+
+def test_large_scans_at_chunk_boundaries(built, full_geom, ora_full):
+    """After a 32-event batch the pipeline's capacities send every scan of later runs to the
+    single-pass large form (one block per 8192 elements): runs whose hit count is an exact
+    multiple of 8192, one more, one less, a single hit and no hit all equal the oracle."""
+    s = lst.Session(full_geom.modules, keep_objects=True)
+    for rid in s.run_batch([S.make_event("pu200", 80 + i, with_pls=True) for i in range(32)]):
+        s.release(rid)
+    base = S.make_event("pu200", 120)
+    for n in (3 * 8192, 3 * 8192 + 1, 3 * 8192 - 1, 1, 0):
+        ev = _first_hits(base, n)
+        rid = s.run_event(ev)
+        compare(s, rid, oracle.run(ora_full, ev), ev, f"{n} hits")
+        s.release(rid)
+    s.close()
+
+
+def test_seed_item_scan_in_large_form(built, full_geom, ora_full):
+    """A batch of more than 262 144 pixel seeds scans its pT3 items per seed in the large
+    single-pass form too; sampled events equal the oracle."""
+    evs = [S.make_event("pu200", 200 + i, with_pls=True) for i in range(104)]
+    assert sum(e.n_pls for e in evs) > 262_144
+    s = lst.Session(full_geom.modules, keep_objects=True)
+    ids = s.run_batch(evs)
+    for i in (0, 51, 103):
+        compare(s, ids[i], oracle.run(ora_full, evs[i]), evs[i], f"seed-heavy batch event {i}")
+    s.close()
+
+
 def test_bench_workload_sampled_parity(sess_full, ora_full):
     # the benchmark's batch (PU200-like events with pixel seeds), 3 events checked in full
     evs = [S.make_event("pu200", i, with_pls=True) for i in range(16)]
