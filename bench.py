@@ -488,6 +488,21 @@ def workload_legs(local, dev, flush, stream, pending):
                                    "mean_hits_per_event": float(np.mean([e.n_hits for e in evs])),
                                    "geometry": "tilted inner-barrel rows (|z| >= 45 cm, layers 1-3)"}
     sess.close()
+    # the geometry whose outer endcap rings are 2S modules (r known to half a 5 cm strip there):
+    # events of 1000 tracks, since the half-strip tolerance multiplies the T3 and T5 combinatorics
+    g2 = S.geometry(False, False, True)
+    evs = [S.make_event("pu200", i, n_tracks=1000, with_pls=True, endcap_2s=True) for i in range(32)]
+    sess = lst.Session(g2.modules, device=local)
+    db = [to_device(evs, dev)]
+    ms, st = time_device_batches(sess, db, 32, stream, flush, 10, 3)
+    objs = sum(st[k] for k in OBJ_KEYS)
+    phys = sampled_candidates(sess, db[0][0], 32, evs, [3], stream, "endcap_2s_1000trk_batch32", g2.modules, pending)
+    out["endcap_2s_1000trk_batch32"] = {"events_per_s": 32 / (ms * 1e-3), "objects_per_s": objs / (ms * 1e-3),
+                                        "ms_per_batch": ms, "objects_per_batch": {k: st[k] for k in OBJ_KEYS},
+                                        "mean_hits_per_event": float(np.mean([e.n_hits for e in evs])),
+                                        "physics": phys,
+                                        "geometry": "2S endcap rings (r >= 60 cm), 1000 tracks per event"}
+    sess.close()
     return out
 
 

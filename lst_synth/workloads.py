@@ -39,9 +39,10 @@ def seed_of(workload: str, i: int) -> int:
 
 
 def make_event(workload: str, i: int = 0, *, n_tracks=None, with_pls=None, exact=False,
-               realistic=False, triplet_frac=0.0) -> E.Event:
+               realistic=False, triplet_frac=0.0, endcap_2s=False) -> E.Event:
     """Event ``i`` of ``workload`` (``n_tracks``/``with_pls`` override the recipe;
     ``realistic`` simulates it in the geometry with tilted inner-barrel modules;
+    ``endcap_2s`` in the geometry whose outer endcap rings are 2S modules;
     ``triplet_frac`` of the pixel seeds are triplets, three hits instead of four)."""
     seed = seed_of(workload, i)
     rng = np.random.default_rng(seed + 7)
@@ -51,7 +52,7 @@ def make_event(workload: str, i: int = 0, *, n_tracks=None, with_pls=None, exact
         t = E.random_tracks(rng, n, pt_mode="uniform", pt_lo=1.0, pt_hi=10.0, eta_max=1.0)
         return E.event_from_tracks(geom, t, seed, noise_frac=0.0, exact=exact,
                                    with_pls=bool(with_pls), triplet_frac=triplet_frac)
-    geom = geometry(False, realistic)
+    geom = geometry(False, realistic, endcap_2s)
     if workload == "pu200":
         n, noise, pls = 4000, 0.20, False
     elif workload == "serving":

@@ -46,3 +46,15 @@ def tilted_geom():
 def ora_tilted(tilted_geom):
     import oracle
     return oracle.Geometry(tilted_geom.modules)
+
+
+@pytest.fixture(scope="session")
+def ec2s_geom():
+    import lst_synth
+    return lst_synth.geometry(False, False, True)
+
+
+@pytest.fixture(scope="session")
+def ora_ec2s(ec2s_geom):
+    import oracle
+    return oracle.Geometry(ec2s_geom.modules)

@@ -509,6 +509,24 @@ def test_tilted_batch_parity(sess_tilted, ora_tilted):
 
 
 # ---------------------------------------------------------------- LST as a seeder
+def test_endcap_2s_parity(built, ec2s_geom, ora_ec2s):
+    """The geometry whose outer endcap rings are 2S modules: per event and in a batch, every
+    object list equals the oracle (events of up to 1000 tracks -- the half-strip radial
+    tolerance multiplies the T3 and T5 combinatorics, 23 k T5s at 1000 tracks)."""
+    s = lst.Session(ec2s_geom.modules, keep_objects=True)
+    evs = [S.make_event("pu200", 90 + i, n_tracks=n, with_pls=True, endcap_2s=True)
+           for i, n in enumerate((400, 800, 1000))]
+    refs = [oracle.run(ora_ec2s, ev) for ev in evs]
+    assert len(refs[2]["t5"]) > 10_000
+    for i, (ev, ref) in enumerate(zip(evs, refs)):
+        rid = s.run_event(ev)
+        compare(s, rid, ref, ev, f"2S event {i}")
+        s.release(rid)
+    for i, (ev, ref, rid) in enumerate(zip(evs, refs, s.run_batch(evs))):
+        compare(s, rid, ref, ev, f"2S batch event {i}")
+    s.close()
+
+
 def test_triplet_seeds_parity_and_seeder_output(sess_full, ora_full):
     """Events whose pixel seeds are 20 % triplets: every list equals the oracle's, and
     lst_get_seeds returns exactly the unlinked seeds (pLS candidates), quads only or quads

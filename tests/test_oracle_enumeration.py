@@ -80,9 +80,14 @@ def _brute(geom, og, ev):
         np.array([kfull[k] for k in idx], np.float32)
 
 
-@pytest.mark.parametrize("case", ["tiny", "barrel_res", "pu200_small", "tilted_small", "pu200_learned_t5"])
-def test_ls_t3_t5_equal_brute_force(case, barrel_geom, full_geom, ora_barrel, ora_full, tilted_geom, ora_tilted):
-    if case == "pu200_learned_t5":  # the T5 step with the shipped network in place of the kappa cuts
+@pytest.mark.parametrize("case", ["tiny", "barrel_res", "pu200_small", "tilted_small", "endcap_2s_small",
+                                  "pu200_learned_t5"])
+def test_ls_t3_t5_equal_brute_force(case, barrel_geom, full_geom, ora_barrel, ora_full, tilted_geom, ora_tilted,
+                                    ec2s_geom, ora_ec2s):
+    if case == "endcap_2s_small":
+        geom, og = ec2s_geom, ora_ec2s
+        ev = S.make_event("pu200", 9, n_tracks=80, endcap_2s=True)
+    elif case == "pu200_learned_t5":  # the T5 step with the shipped network in place of the kappa cuts
         import paper_2407_18231_gb300 as lst
         geom, og = full_geom, oracle.Geometry(full_geom.modules)
         oracle.set_t5_mlp(og, lst.load_t5_mlp())

@@ -4,7 +4,7 @@ Each mutation below is one plausible slip in the oracle's source (a dropped term
 flipped sign, a transposed operand, a wrong index or bound).  The test builds a copy of
 lst_oracle.c with that one change (on the CPU, in a temporary directory), runs the oracle
 pins (test_oracle_pins.py, test_oracle_cuts.py, test_oracle_enumeration.py,
-test_oracle_tilted.py, test_oracle_t5_mlp.py) against the
+test_oracle_tilted.py, test_oracle_endcap_2s.py, test_oracle_t5_mlp.py) against the
 copy in a child process, and requires at least one of them to fail.  A mutation that no
 pin catches would be a part of the oracle that nothing but the oracle itself vouches for.
 """
@@ -19,7 +19,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lst_oracle.c")
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_cuts.py", "tests/test_oracle_enumeration.py",
-        "tests/test_oracle_tilted.py", "tests/test_oracle_t5_mlp.py"]
+        "tests/test_oracle_tilted.py", "tests/test_oracle_endcap_2s.py", "tests/test_oracle_t5_mlp.py"]
 
 # Two widening terms are left out on purpose: the endcap part of the bending slack
 # (rho_a + rho_b) (|sin dphi| + 0.05) and the sensor gap in a barrel module's r_max.  No
@@ -123,6 +123,7 @@ MUTATIONS = [
      "rmax = (double)m->surf + (double)m->gap * cos(t);"),
     ("tilted: radial tolerance dropped", "*rho = (float)(0.15 * fabs(sin((double)m->tilt)));", "*rho = 0.0f;"),
     ("tilted: z tolerance of a 2S strip", "*zeta = (float)(0.15 * fabs(cos((double)m->tilt)));", "*zeta = 1.30f;"),
+    ("endcap 2S: radial tolerance of a PS ring", "*rho = m->stype == 0 ? 0.15f : 2.55f;", "*rho = 0.15f;"),
     # duplicate removal and candidates
     ("dedup: pT5 overlap threshold 2", "if (count_shared(pls_md5 + 5 * x, 5, pls_md5 + 5 * y, 5) >= 3 && better",
      "if (count_shared(pls_md5 + 5 * x, 5, pls_md5 + 5 * y, 5) >= 2 && better"),
