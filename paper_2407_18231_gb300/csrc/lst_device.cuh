@@ -15,7 +15,6 @@ constexpr uint32_t PLS_MD_CAP = 64;  // MDs passing a pLS's first-anchor test, k
 constexpr uint32_t PLS_ITEMS = PLS_MD_CAP > (uint32_t)MAX_CAND ? PLS_MD_CAP : (uint32_t)MAX_CAND;
 
 constexpr int N_SCAN_SLOTS = 16;          // scans of one run that can take the single-pass form
-constexpr uint32_t SCAN_MID_BLOCKS = 32;   // blocks of a single-pass scan
 constexpr uint32_t SCAN_LARGE_CHUNK = 8192; // elements per block of a large single-pass scan
 
 // Totals written by the scans into the batch header.
@@ -50,10 +49,9 @@ struct Hdr {
                           // arena's end), [2] words of the lists that found it exhausted
   unsigned long long ls_cand;  // MD pairs the LS count pass tested (connection-map candidates)
   uint32_t work[16];           // work counters of the dynamically scheduled kernels (W_*)
-  // single-pass scans of mid-size arrays: per scan, the block tickets and the chunk totals
-  // each block publishes (bit 32 set once written)
+  // single-pass scans: per scan, the ticket counter that hands out its chunks in block start
+  // order (the chunk states themselves are in BufView::scan_state)
   uint32_t scan_ticket[N_SCAN_SLOTS];
-  unsigned long long scan_agg[N_SCAN_SLOTS][SCAN_MID_BLOCKS];
 };
 
 // Work counters in Hdr::work, one per dynamically scheduled kernel and pass.

@@ -540,8 +540,9 @@ struct Pipeline {
   uint64_t byte_cap = 0;  // 0: none; otherwise learn_mask keeps dev_bytes within it
   bool auto_list_cap = true;  // the LS list cap is the library's choice (learn may raise it)
   // test hook for the bounded device waits: the next stall_scan_runs launches start every
-  // single-pass scan's tickets past its last chunk, so its blocks wait for chunk totals that
-  // nothing publishes until their polls run out (LST_TEST_STALL_SCAN at context creation)
+  // single-pass scan's tickets at 1, so no block takes chunk 0 and the blocks of the later
+  // chunks wait for a state that nothing writes until their polls run out
+  // (LST_TEST_STALL_SCAN at context creation)
   uint32_t stall_scan_runs = 0;
   // test hook for the LS partner-list arena: when set, the arena holds this many words and
   // never grows, so that most anchors find it exhausted and are joined again by the fill
@@ -966,7 +967,7 @@ struct Pipeline {
     h_hdr->scan_epoch = ++epoch;
     if (stall_scan_runs) {
       stall_scan_runs--;
-      for (uint32_t& t : h_hdr->scan_ticket) t = SCAN_MID_BLOCKS;
+      for (uint32_t& t : h_hdr->scan_ticket) t = 1;  // no block takes chunk 0
     }
     L.t5_mlp = geo->has_t5_mlp ? &geo->t5_mlp : nullptr;
     if (graph_sel_version != geo->sel_version) {

@@ -245,12 +245,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sm, ui
   return r;
 }
 
-// One block scans a whole array when the array's capacity is at most SCAN_SMALL_MAX (the
-// lists of a small event): tiles of 16 elements per thread with a running carry, the same
-// outputs as k_scan_reduce + k_scan_apply (out[0..n), out[n] = total, the header total and
-// its overflow bit) in one launch instead of two.  Measured: 7 us for one tile against
-// about 15 us for the two launches; at 60 k elements (4 tiles) 22 us against 17 us, so the
-// bound is one tile.
+// Every scan writes out[0..n) (exclusive), out[n] = total, the header total and its
+// overflow bit.  One block scans a whole array when the array's capacity is at most
+// SCAN_SMALL_MAX (the lists of a small event): tiles of 16 elements per thread with a
+// running carry, no waiting on other blocks.  Measured: 7 us for one tile; at 60 k elements
+// (4 tiles) 22 us, slower than the multi-block single pass below, so the bound is one tile.
 constexpr uint32_t SCAN_SMALL_MAX = 1u << 14;
 constexpr uint32_t SCAN_SMALL_PER_THREAD = 16;
 __device__ __forceinline__ void scan_small_body(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ out,
@@ -292,81 +291,10 @@ __global__ void __launch_bounds__(1024) k_scan_small(const uint32_t* __restrict_
   scan_small_body(in, (*nptr) * mul, out, H, tot_idx, cap, sm);
 }
 
-// Mid-size arrays (capacity up to SCAN_MID_MAX, one event's lists): a single pass of
-// SCAN_MID_BLOCKS blocks of 1024 threads, each scanning one chunk of at most 8 elements per
-// thread.  A block takes a ticket when it starts (the chunk it scans, so chunks are handed
-// out in start order), publishes its chunk's total, and adds the totals of the chunks before
-// its own: it waits only for blocks that started before it, so every wait ends.  Each wait
-// is still bounded (SCAN_WAIT_LIMIT polls); a block whose wait runs out sets ERR_WAIT, and
-// the host reports the run as failed.
-constexpr uint32_t SCAN_MID_PER_THREAD = 8;
-constexpr uint32_t SCAN_MID_MAX = SCAN_MID_BLOCKS * 1024u * SCAN_MID_PER_THREAD;
 constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 20;  // about a second of polls
 static_assert(11 + 4 <= N_SCAN_SLOTS, "scan slots: eight single scans, then three and four arrays");
-static_assert(SCAN_MID_BLOCKS == 32, "one look-back lane per chunk");
-__device__ __forceinline__ void scan_mid_body(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ out,
-                                              Hdr* H, int tot_idx, uint32_t cap, uint32_t slot, uint32_t* sm) {
-  if (threadIdx.x == 0) sm[33] = atomicAdd(&H->scan_ticket[slot], 1u);
-  __syncthreads();
-  const uint32_t b = sm[33];
-  const uint32_t chunk = (n + SCAN_MID_BLOCKS - 1) / SCAN_MID_BLOCKS;
-  const uint32_t lo = min(n, b * chunk), hi = min(n, lo + chunk);
-  const uint32_t i0 = lo + threadIdx.x * SCAN_MID_PER_THREAD;
-  uint32_t v[SCAN_MID_PER_THREAD];
-  uint32_t s = 0;
-#pragma unroll
-  for (uint32_t k = 0; k < SCAN_MID_PER_THREAD; k++) {
-    v[k] = (i0 + k < hi) ? in[i0 + k] : 0u;
-    s += v[k];
-  }
-  uint32_t tot;
-  uint32_t ex = block_excl_scan(s, sm, tot);
-  unsigned long long* agg = H->scan_agg[slot];
-  // (a ticket past the last chunk -- only the test hook that stalls the scans makes one --
-  // scans and publishes nothing and waits for every chunk)
-  if (threadIdx.x == 0 && b < SCAN_MID_BLOCKS) atomicExch(&agg[b], (1ull << 32) | tot);
-  if (threadIdx.x < 32) {  // look-back: lane j adds chunk j's total, for every j < b
-    uint32_t x = 0;
-    if (threadIdx.x < b) {  // threadIdx.x < 32 = SCAN_MID_BLOCKS: within agg
-      unsigned long long w = 0;
-      for (uint32_t it = 0; it < SCAN_WAIT_LIMIT; it++) {
-        w = atomicAdd(&agg[threadIdx.x], 0ull);
-        if (w >> 32) break;
-      }
-      if (!(w >> 32)) atomicOr(&H->err, ERR_WAIT);
-      x = (uint32_t)w;
-    }
-    const uint32_t carry = __shfl_sync(FULL, warp_incl_scan(x), 31);
-    if (threadIdx.x == 0) sm[34] = carry;
-  }
-  __syncthreads();
-  const uint32_t carry = sm[34];
-  ex += carry;
-#pragma unroll
-  for (uint32_t k = 0; k < SCAN_MID_PER_THREAD; k++) {
-    if (i0 + k < hi) out[i0 + k] = ex;
-    ex += v[k];
-  }
-  if (b == SCAN_MID_BLOCKS - 1 && threadIdx.x == 0) {
-    const uint32_t total = carry + tot;
-    out[n] = total;
-    if (tot_idx >= 0) {
-      H->tot[tot_idx] = total;
-      if (total > cap) atomicOr(&H->err, 1u << (ERR_OVERFLOW_SHIFT + tot_idx));
-    }
-  }
-}
 
-__global__ void __launch_bounds__(1024) k_scan_mid(const uint32_t* __restrict__ in, const uint32_t* nptr, uint32_t mul,
-                                                   Hdr* H, uint32_t* __restrict__ out, int tot_idx, uint32_t cap,
-                                                   uint32_t slot) {
-  pdl_wait();
-  if (H->err) return;
-  __shared__ uint32_t sm[35];
-  scan_mid_body(in, (*nptr) * mul, out, H, tot_idx, cap, slot, sm);
-}
-
-// Large arrays (capacity above SCAN_MID_MAX: the lists of a batch): a single pass with one
+// Larger arrays (capacity above SCAN_SMALL_MAX: one event's or a batch's lists): a single pass with one
 // chunk of SCAN_LARGE_CHUNK elements (1024 threads x 8) per block.  A block takes a ticket
 // when it starts (its chunk, so chunks are handed out in start order), publishes its chunk's
 // total at once, then looks back over the chunks before its own, 32 at a time, adding their
@@ -497,15 +425,6 @@ __global__ void __launch_bounds__(1024) k_scan_small_multi(ScanJobs J, Hdr* H) {
   __shared__ uint32_t sm[33];
   const ScanJob& q = J.j[blockIdx.x];
   scan_small_body(q.in, *q.nptr, q.out, H, q.tot, q.cap, sm);
-}
-
-// The single-pass scan of several mid-size arrays (blockIdx.y picks the array and its slot).
-__global__ void __launch_bounds__(1024) k_scan_mid_multi(ScanJobs J, Hdr* H, uint32_t slot0) {
-  pdl_wait();
-  if (H->err) return;
-  __shared__ uint32_t sm[35];
-  const ScanJob& q = J.j[blockIdx.y];
-  scan_mid_body(q.in, *q.nptr, q.out, H, q.tot, q.cap, slot0 + blockIdx.y, sm);
 }
 
 // The single-pass scan of several large arrays (blockIdx.y picks the array and its slot).
@@ -2550,7 +2469,7 @@ const char* const kKernelNames[] = {
     "md_count", "md_fill", "ls_count", "ls_fill", "t3_count", "t3_fill", "t5_count", "t5_fill", "pls_prep",
     "pt3_count", "pt3_fill", "pt5_count", "pt5_fill", "(unused)", "md_lists_count", "md_lists_fill",
     "kill_pt5", "(unused)", "cross_pt3", "kill_pt3", "(unused)", "cross_t5", "kill_t5", "tc_offsets", "tc_write",
-    "(unused)", "(unused)", "pt3_first_anchor", "pls_sort", "pt3_items", "md_boxes", "scan_small", "scan_mid"};
+    "(unused)", "(unused)", "pt3_first_anchor", "pls_sort", "pt3_items", "md_boxes", "scan_small", "(unused)"};
 const int kNumKernelNames = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 struct Marker {
@@ -2590,26 +2509,17 @@ static void scan(const BufView& B, const Launch& L, cudaStream_t s, const uint32
     mk(38);
     return;
   }
-  if (bound <= SCAN_MID_MAX) {
-    launch(k_scan_mid, SCAN_MID_BLOCKS, 1024, 0, s, in, nptr, mul, B.hdr, out, tot, cap, slot);
-    mk(39);
-    return;
-  }
   launch(k_scan_large, (uint32_t)((bound + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK), 1024, 0, s, in, nptr, mul, B, out,
          tot, cap, slot);
   mk(3);
 }
 
 // pT3 item offsets and item -> pLS table.  May run on the side stream beside the main
-// chain's scans, so its scan keeps its partials in a buffer of its own.
+// chain's scans, so its scan has a slot of its own (5).
 static void pt3_items(const BufView& B, const Launch& L, cudaStream_t s, Marker& mk) {
   if (B.cap_pls <= SCAN_SMALL_MAX) {
     launch(k_scan_small, 1, 1024, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.pt3_ioff, T_PT3I, 0xFFFFFFFFu);
     mk(38);
-  } else if (B.cap_pls <= SCAN_MID_MAX) {
-    launch(k_scan_mid, SCAN_MID_BLOCKS, 1024, 0, s, B.pt3_icnt, &B.hdr->n_pls, 1, B.hdr, B.pt3_ioff, T_PT3I,
-           0xFFFFFFFFu, 5u);
-    mk(39);
   } else {
     launch(k_scan_large, (B.cap_pls + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK, 1024, 0, s, B.pt3_icnt, &B.hdr->n_pls,
            1, B, B.pt3_ioff, T_PT3I, 0xFFFFFFFFu, 5u);
@@ -2624,11 +2534,6 @@ static void scan_multi(const BufView& B, const Launch& L, cudaStream_t s, const 
   if (bound <= SCAN_SMALL_MAX) {
     launch(k_scan_small_multi, n, 1024, 0, s, J, B.hdr);
     mk(38);
-    return;
-  }
-  if (bound <= SCAN_MID_MAX) {
-    launch(k_scan_mid_multi, dim3(SCAN_MID_BLOCKS, n), 1024, 0, s, J, B.hdr, slot0);
-    mk(39);
     return;
   }
   launch(k_scan_large_multi, dim3((uint32_t)((bound + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK), n), 1024, 0, s, J, B,
@@ -2649,7 +2554,7 @@ cudaError_t configure_kernels() {
 cudaError_t preload_kernels() {
   const void* ks[] = {
       (const void*)k_scan_small, (const void*)k_scan_small_multi,
-      (const void*)k_scan_mid, (const void*)k_scan_mid_multi, (const void*)k_scan_large, (const void*)k_scan_large_multi, (const void*)k_zero, (const void*)k_hits_count, (const void*)k_hits_scatter,
+      (const void*)k_scan_large, (const void*)k_scan_large_multi, (const void*)k_zero, (const void*)k_hits_count, (const void*)k_hits_scatter,
       (const void*)k_hits_sort, (const void*)k_md_count, (const void*)k_md_fill, (const void*)k_ls_fill,
       (const void*)k_ls_count, (const void*)k_t3_count, (const void*)k_t3_fill, (const void*)k_t5_count,
       (const void*)k_t5_fill, (const void*)k_t5_count_mlp, (const void*)k_t5_fill_mlp, (const void*)k_pls_prep, (const void*)k_pls_sort, (const void*)k_md_box,

@@ -9,6 +9,7 @@
 // and connection map) and pass their own input and output buffers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -41,6 +42,11 @@ constexpr uint32_t MAX_PT3 = 16384;
 constexpr uint32_t MAX_PT5 = 16384;
 constexpr uint32_t MASK_WORDS = 65536;  // LS partner lists; a fuller event joins again in the fill pass
 constexpr size_t SCRATCH_BYTES = size_t(8) << 20;  // every GPU that loads the library holds this until exit
+// chunk states per scan slot of the single-pass scans: the largest bound a scan of one call
+// is launched with (2 x modules for the hit bins, pLS x items for the pT3 items, ...)
+constexpr uint32_t STATIC_SCAN_BOUND =
+    std::max({2 * MAX_MODULES, MAX_HITS, MAX_MD, MAX_LS, MAX_T3, MAX_T5, MAX_PT3, MAX_PT5, MAX_PLS * PLS_ITEMS});
+constexpr uint32_t STATIC_SCAN_CHUNKS = (STATIC_SCAN_BOUND + SCAN_LARGE_CHUNK - 1) / SCAN_LARGE_CHUNK;
 
 // The scratch.  In host code `g_scratch` is only a stand-in symbol: its device address
 // comes from cudaGetSymbolAddress, once per device.
@@ -49,6 +55,9 @@ static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void* g_scratch_dev[MAX_DEVICES] = {};
+// per device, the calls made so far: tags the single-pass scans' chunk states (30 bits),
+// which the zero-initialised array holds from earlier calls
+uint32_t g_scan_epoch[MAX_DEVICES] = {};
 
 // Sinks for carve_layout: Sizer only adds up the 256-byte aligned extents (usable in a
 // constant expression), Placer also points every list into the scratch.
@@ -167,6 +176,8 @@ constexpr size_t carve_layout(Sink& c, BufView& B) {
   c.take(B.sap, MAX_PLS + 1);
   c.take(B.tc_ev_off, 2);
   c.take(B.mask_off, MAX_MD);
+  c.take(B.scan_state, (size_t)N_SCAN_SLOTS * STATIC_SCAN_CHUNKS);
+  B.scan_chunks = STATIC_SCAN_CHUNKS;
   B.cap_mask = MASK_WORDS;
   c.take(B.mask, MASK_WORDS);
   return c.off;
@@ -271,6 +282,22 @@ extern "C" lst_status lst_run_event_static(lst_ctx* ctx, const lst_batch_dev* ev
   h.x = ev->x; h.y = ev->y; h.z = ev->z; h.det = ev->det; h.hit_off = ev->hit_off;
   h.pls = (const PlsIn*)ev->pls; h.pls_off = ev->pls_off;
   h.n_ev = 1; h.n_hits = ev->n_hits; h.n_pls = ev->n_pls;
+  bool clear_states = false;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_scan_epoch[dev] == 0x3FFFFFFFu) {  // the tags would repeat: start again from clear states
+      g_scan_epoch[dev] = 0;
+      clear_states = true;
+    }
+    h.scan_epoch = ++g_scan_epoch[dev];
+  }
+  if (clear_states) {
+    e = cudaMemsetAsync(B.scan_state, 0, (size_t)N_SCAN_SLOTS * STATIC_SCAN_CHUNKS * sizeof(*B.scan_state), s);
+    if (e != cudaSuccess) {
+      ctx_set_error(ctx, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+      return LST_ERR_CUDA;
+    }
+  }
   // the header (and with it every total and the error word) starts from zero on each call
   k_static_header<<<1, 32, 0, s>>>(B.hdr, h);
   const int launched = enqueue_pipeline(C, G, B, L, s, nullptr, nullptr);

@@ -76,10 +76,10 @@ def test_autotuner_picks_a_configuration(full_geom, tmp_path):
 
 
 def test_bounded_scan_wait_reports_timeout(full_geom, monkeypatch):
-    """The single-pass scans wait for the chunk totals of blocks that started earlier, every
-    wait bounded.  The test hook makes the first run's scan blocks wait for totals that
-    nothing publishes: their polls run out (about a second), the run returns
-    LST_ERR_TIMEOUT, and the next run on the same context equals the oracle."""
+    """The single-pass scans wait for the chunk states of blocks that started earlier, every
+    wait bounded.  The test hook makes the first run's scan blocks wait for a state that
+    nothing writes (no block takes chunk 0): their polls run out (about a second), the run
+    returns LST_ERR_TIMEOUT, and the next run on the same context equals the oracle."""
     import oracle
     monkeypatch.setenv("LST_TEST_STALL_SCAN", "1")
     s = lst.Session(full_geom.modules)
@@ -116,10 +116,9 @@ def test_exhausted_partner_arena_rejoins_anchors(full_geom, ora_full, monkeypatc
 
 
 def test_bounded_large_scan_wait_reports_timeout(full_geom, ora_full, monkeypatch):
-    """The single-pass scans of a batch's lists (one block per 8192 elements) look back over
-    the chunks before their own, every wait bounded.  With the test hook, the first run's
-    tickets start past chunk 31, so the blocks wait for states that nothing writes: their
-    polls run out, the run returns LST_ERR_TIMEOUT, and the next run on the same context
+    """The same on a batch, whose scans span hundreds of chunks (one block per 8192
+    elements), each looking back over the chunks before its own: with the test hook no block
+    takes chunk 0, the run returns LST_ERR_TIMEOUT, and the next run on the same context
     equals the oracle."""
     import oracle
     from test_gpu_parity import compare
@@ -127,7 +126,7 @@ def test_bounded_large_scan_wait_reports_timeout(full_geom, ora_full, monkeypatc
     s = lst.Session(full_geom.modules, keep_objects=True)
     monkeypatch.delenv("LST_TEST_STALL_SCAN")
     evs = [S.make_event("pu200", 70 + i, with_pls=True) for i in range(16)]
-    assert sum(e.n_hits for e in evs) > 32 * 8192  # the hit scan takes more than 32 chunks
+    assert sum(e.n_hits for e in evs) > 100 * 8192  # the hit scan takes more than 100 chunks
     with pytest.raises(lst.LstError) as e:
         s.run_batch(evs)
     assert e.value.status == -7 and "wait ran out" in str(e.value)
