@@ -205,14 +205,16 @@ __device__ __forceinline__ bool t5_select(const MethodConst& C, const PointTol& 
   return c1 && c2 && c3 && c4;
 }
 
-// Same decision as t5_select without the score: stops at the first failing condition
-// (inner/outer curvatures first), so most rejected candidates skip half the circles.
-__device__ __forceinline__ bool t5_accept(const MethodConst& C, const PointTol& A, const PointTol& B, const PointTol& Cc,
-                                          const PointTol& D, const PointTol& E) {
-  const Circle3 in = circle3(A, B, Cc);
-  const Circle3 out = circle3(Cc, D, E);
+// The first condition of t5_select: the inner (a, b, c) and outer (c, d, e) curvatures agree.
+__device__ __forceinline__ bool t5_in_out_agree(const MethodConst& C, const Circle3& in, const Circle3& out) {
   const float d1 = fabsf(in.k - out.k);
-  if (!(d1 <= C.KAPPA * (fabsf(in.k) + fabsf(out.k)) + in.tol + out.tol + C.KAPPA0)) return false;
+  return d1 <= C.KAPPA * (fabsf(in.k) + fabsf(out.k)) + in.tol + out.tol + C.KAPPA0;
+}
+
+// The conditions of t5_select after the first, in its order, stopping at the first failure:
+// with t5_in_out_agree, the decision of t5_select without the score.
+__device__ __forceinline__ bool t5_accept_rest(const MethodConst& C, const PointTol& A, const PointTol& B,
+                                               const PointTol& Cc, const PointTol& D, const PointTol& E) {
   const Circle3 br = circle3(B, Cc, D);
   const Circle3 fu = circle3(A, Cc, E);
   const float d2 = fabsf(br.k - fu.k);

@@ -1196,10 +1196,15 @@ __global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufV
     const uint32_t t = grp * 32 + lane;
     const bool valid = t < n;
     uint32_t s0 = 0, c = 0;
+    Circle3 in_t{};  // this lane's T3 (a, b, c): its circle, the inner circle of all its candidates
     if (valid) {
       const uint32_t m = B.t3_c[t];
       s0 = B.t3_off[m];
       c = B.t3_off[m + 1] - s0;
+      if (c) {
+        const uint4 abc = B.t3_md4[t];
+        in_t = circle3(md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z));
+      }
     }
     const uint32_t incl = warp_incl_scan(c);
     const uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -1210,11 +1215,15 @@ __global__ void __launch_bounds__(512) k_t5_count(MethodConst C, GeoView G, BufV
       const uint32_t cc = cand < total ? cand : total - 1;
       const uint32_t o = owner_lane(incl, cc);
       const uint32_t t2 = __shfl_sync(FULL, s0, o) + (cc - __shfl_sync(FULL, start, o));
+      Circle3 in;  // the owner's inner circle
+      in.k = __shfl_sync(FULL, in_t.k, o);
+      in.tol = __shfl_sync(FULL, in_t.tol, o);
       bool pass = false;
       if (cand < total) {
         const uint4 abc = B.t3_md4[grp * 32 + o];
-        pass = t5_accept(C, md_point(B, abc.x), md_point(B, abc.y), md_point(B, abc.z), md_point(B, B.t3_b[t2]),
-                         md_point(B, B.t3_c[t2]));
+        const PointTol Cc = md_point(B, abc.z), D = md_point(B, B.t3_b[t2]), E = md_point(B, B.t3_c[t2]);
+        if (t5_in_out_agree(C, in, circle3(Cc, D, E)))
+          pass = t5_accept_rest(C, md_point(B, abc.x), md_point(B, abc.y), Cc, D, E);
       }
       const uint32_t bal = __ballot_sync(FULL, pass);
       const uint32_t lo = start > t0 ? min(start - t0, 32u) : 0u;
