@@ -26,6 +26,7 @@ namespace lst {
 int enqueue_pipeline(const MethodConst& C, const GeoView& G, const BufView& B, const Launch& L, cudaStream_t s,
                      MarkFn mark, void* arg, const SideBranch* side = nullptr);
 cudaError_t static_scratch_prepare(int device);  // lst_static.cu
+void static_scan_epoch_set(int device, uint32_t e);  // lst_static.cu
 cudaError_t configure_kernels();
 }
 
@@ -1413,6 +1414,13 @@ lst_status lst_load_geometry(const lst_module_desc* mods, uint32_t n_mods, const
     c->main.init(&c->geo, c->cfg, c->n_sm);
     if (const char* v = std::getenv("LST_TEST_STALL_SCAN")) c->main.stall_scan_runs = (uint32_t)std::atoi(v);
     if (const char* v = std::getenv("LST_TEST_MASK_WORDS")) c->main.test_mask_words = (uint32_t)std::atoi(v);
+    // test hook: the scans' run tags start at this value (the next run takes it + 1), here
+    // and in the allocation-free entry point on this device
+    if (const char* v = std::getenv("LST_TEST_SCAN_EPOCH")) {
+      const uint32_t e = (uint32_t)std::strtoul(v, nullptr, 0) & 0x3FFFFFFFu;
+      c->main.epoch = e;
+      static_scan_epoch_set(c->device, e);
+    }
     // the allocation-free entry point's array and kernels, loaded now so that its calls allocate nothing
     CK(static_scratch_prepare(c->device));
     return LST_OK;

@@ -231,6 +231,14 @@ cudaError_t static_scratch_prepare(int device) {
   if (e == cudaSuccess) e = preload_kernels();
   return e;
 }
+
+// Test hook: the next call on `device` takes run tag e + 1 (LST_TEST_SCAN_EPOCH at context
+// creation), so that tests can run across the point where the tags start again.
+void static_scan_epoch_set(int device, uint32_t e) {
+  if (device < 0 || device >= MAX_DEVICES) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_scan_epoch[device] = e & 0x3FFFFFFFu;
+}
 }  // namespace lst
 
 extern "C" lst_status lst_run_event_static(lst_ctx* ctx, const lst_batch_dev* ev, lst_tc* tc_out, uint32_t tc_cap,

@@ -146,3 +146,34 @@ def test_static_entry_point_follows_the_t5_selection():
         assert np.array_equal(tc["ot"], ora["tc_ot"]) and np.array_equal(tc["pix"], ora["tc_pix"])
         assert tc["score"].tobytes() == ora["tc_score"].tobytes()
     sess.close()
+
+
+def test_scan_run_tags_start_again(monkeypatch):
+    """The single-pass scans tag their chunk states with a 30-bit run number; when the tags
+    would repeat, the states are cleared and the numbering starts again.  The test hook
+    starts the tags two runs before that point: four runs of the pipeline and four calls of
+    the allocation-free entry point across it all equal the oracle."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    L = lst.load_library()
+    dev = torch.device("cuda:0")
+    geom = S.geometry(False)
+    monkeypatch.setenv("LST_TEST_SCAN_EPOCH", str(0x3FFFFFFD))
+    sess = lst.Session(geom.modules)
+    monkeypatch.delenv("LST_TEST_SCAN_EPOCH")
+    ev = S.make_event("pu200", 26, n_tracks=220, with_pls=True)
+    ora = oracle.run(oracle.Geometry(geom.modules), ev)
+    for i in range(4):
+        rid = sess.run_event(ev)
+        tc = sess.candidates(rid)
+        sess.release(rid)
+        assert np.array_equal(tc["ot"], ora["tc_ot"]) and tc["score"].tobytes() == ora["tc_score"].tobytes(), i
+    desc, keep = _device_event(torch, ev, dev)
+    cap = 4096
+    out = torch.zeros(cap * lst.TC_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    for i in range(4):
+        n = C.c_uint32(0)
+        assert L.lst_run_event_static(sess.ctx, C.byref(desc), out.data_ptr(), cap, C.byref(n), None) == 0
+        tc = np.frombuffer(out[: n.value * lst.TC_DTYPE.itemsize].cpu().numpy().tobytes(), lst.TC_DTYPE)
+        assert np.array_equal(tc["ot"], ora["tc_ot"]) and tc["score"].tobytes() == ora["tc_score"].tobytes(), i
+    sess.close()
